@@ -1,0 +1,27 @@
+"""CPU oracle for the ParaDiag-II all-at-once solver (test infrastructure).
+
+This package is the plain, slow, FP64 statement of what the GPU library
+computes, written from the paper (Gander, Liu, Wu, Yue, Zhou, "ParaDiag:
+Parallel-in-Time Algorithms Based on the Diagonalization Technique",
+arXiv:2005.09158).  It is test infrastructure only: the tests, the smoke
+check and the CPU-baseline leg of the benchmark import it; the product path
+never does, and it shares no code with the CUDA library.
+
+Modules
+  operators     K (centred finite differences), the Toeplitz B1/B2 (eq. 2.5b,
+                eq. 3.2b), the alpha-circulants C1/C2 (eq. 2.11b, eq. 3.4),
+                apply-A (eq. 1.1) and the right-hand side b.
+  stepping      O1: exact solution of A u = b by sequential block forward
+                substitution in time; the adjoint by backward substitution.
+  paradiag      O2: P_alpha^{-1} r by the three steps of eq. 1.3 with the
+                Fourier matrix of Lemma 1 written out densely; the stationary
+                iteration eq. 5.1; flexible GMRES on A with P_alpha^{-1}.
+  dense         O3: dense Kronecker A and P_alpha for tiny sizes.
+  closed_forms  O4: Lemma 1 eigenvalues, spatial eigenvalues, the per-mode
+                contraction of eq. 5.1, the spectrum of Theorem 3.1.
+  control       O5: the heat source inversion functional and its gradient.
+
+Every function is pinned by a test in tests/test_oracle_*.py against a
+closed form, an invariant, a bound of the paper, a worked example the paper
+prints, or brute force.  No function here is parity-unpinned.
+"""
