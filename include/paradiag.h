@@ -1,0 +1,158 @@
+/*
+ * paradiag.h -- C ABI of the GB300 (sm_103a) ParaDiag-II library.
+ *
+ * Problem (Gander, Liu, Wu, Yue, Zhou, "ParaDiag: Parallel-in-Time Algorithms
+ * Based on the Diagonalization Technique", arXiv:2005.09158):
+ *   the all-at-once system A u = b,  A = B1 (x) M + B2 (x) K        (eq. 1.1)
+ * of a linear multistep discretisation of M U' + K U = f with M = I (finite
+ * differences), lower-triangular Toeplitz B1, B2 (theta-method, eq. 2.5b;
+ * implicit leap-frog, eq. 3.2b), and its block alpha-circulant preconditioner
+ *   P_alpha = C1^(alpha) (x) M + C2^(alpha) (x) K                   (eq. 1.2)
+ * applied through the three steps of eq. 1.3 (Lemma 1): scale by Gamma_alpha
+ * and FFT along time, Nt independent complex-shifted spatial solves, inverse
+ * FFT and unscale.
+ *
+ * Conventions shared by every entry point
+ *   Layout.   Space-time arrays are real FP64, time-major, [Nt][ny][nx] with x
+ *             fastest: u = (U_1; ...; U_Nt) (eq. 2.5a), U_n = u at t_n.
+ *   Memory.   Unless a function says otherwise, array arguments are DEVICE
+ *             pointers owned by the caller; the plan owns its tables and
+ *             workspace (allocated once in pd_plan_create).
+ *   Streams.  All work is enqueued on the plan's stream.  Functions that need
+ *             a scalar on the host (solvers) synchronise that stream.
+ *   Aliasing. Inputs and outputs must not overlap, except where stated.
+ *   Errors.   Every function returns a pd_status; nothing throws.  The text of
+ *             the last error is available from pd_last_error(plan).
+ *   Threads.  A plan must not be used by two host threads at once; distinct
+ *             plans are independent.
+ */
+#ifndef PARADIAG_H
+#define PARADIAG_H
+
+#if defined(__GNUC__)
+#define PD_API __attribute__((visibility("default")))
+#else
+#define PD_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  PD_OK = 0,
+  PD_ERR_ARG = -1,            /* invalid argument (size, pointer, parameter) */
+  PD_ERR_CUDA = -2,           /* a CUDA runtime call failed */
+  PD_ERR_NOT_CONVERGED = -3,  /* the solver stopped at maxit above tol */
+  PD_ERR_NONFINITE = -4,      /* a NaN or Inf appeared in a kernel */
+  PD_ERR_UNSUPPORTED = -5,    /* valid problem that this library does not handle */
+  PD_ERR_NOMEM = -6           /* device allocation failed */
+} pd_status;
+
+/* Time integrators: backward Euler and Crank-Nicolson are the theta-method of
+ * eq. 2.4 with theta = 1 and 1/2; PD_THETA takes theta from the argument;
+ * PD_LEAPFROG is the implicit leap-frog scheme of eq. 3.2b. */
+typedef enum { PD_BE = 0, PD_CN = 1, PD_THETA = 2, PD_LEAPFROG = 3 } pd_scheme_kind;
+typedef enum { PD_DIRICHLET = 0, PD_PERIODIC = 1 } pd_bc;
+/* PD_MIXED: FP32 preconditioner (FFT, tridiagonal solves, x-transform) with the
+ * outer residual b - A u and the update u += du kept in double-float (FP32
+ * pairs, 48-bit significand).  PD_FP64: every step in FP64. */
+typedef enum { PD_FP64 = 0, PD_MIXED = 1 } pd_precision;
+typedef enum { PD_STATIONARY = 0, PD_GMRES = 1 } pd_mode;
+
+/* Spatial operator K = -nu Lap_h + (ax, ay).grad_h (centred second-order
+ * differences, eq. 2.2b in 1D; the 5-point stencil in 2D).  Dirichlet
+ * directions hold n interior points with h = L/(n+1); periodic directions hold
+ * n points with h = L/n.  dim = 2 requires bc_y = PD_DIRICHLET, and either
+ * bc_x = PD_PERIODIC or (bc_x = PD_DIRICHLET and ax = 0). */
+typedef struct {
+  int dim;        /* 1 or 2 */
+  int nx, ny;     /* grid points per direction (ny ignored for dim = 1) */
+  double nu;      /* diffusion coefficient */
+  double ax, ay;  /* advection velocity */
+  int bc_x, bc_y; /* pd_bc */
+  double lx, ly;  /* domain lengths */
+} pd_space;
+
+typedef struct pd_plan pd_plan;
+
+/* Create a plan for the all-at-once system on Nt uniform steps of size dt with
+ * preconditioner parameter alpha in (0, 1] (Lemma 1).  Nt must be a power of
+ * two (1 <= Nt <= 8192 for PD_MIXED, <= 4096 for PD_FP64).  alpha = 1 is
+ * accepted only when no shifted system is singular (checked here).
+ * stream: a cudaStream_t (NULL = legacy default stream).
+ * Builds on the host, in FP64: the eigenvalues lambda_{j,k} of Lemma 1, the
+ * Gamma tables, the FFT twiddles and (2D) the x-eigentransform; copies them to
+ * the device and allocates the workspace.  *out receives the plan. */
+PD_API pd_status pd_plan_create(const pd_space* sp, int nt, double dt, double alpha, int scheme,
+                         double theta, int precision, void* stream, pd_plan** out);
+PD_API pd_status pd_plan_destroy(pd_plan* plan);
+
+/* Bytes of device memory the plan holds (tables + workspace). */
+PD_API pd_status pd_plan_workspace(const pd_plan* plan, unsigned long long* bytes);
+
+/* z = P_alpha^{-1} r (eq. 1.3, steps (a)-(c)); r, z: [Nt][S] device FP64. */
+PD_API pd_status pd_apply_precond(pd_plan* plan, const double* r, double* z);
+
+/* r = b - A u (eq. 5.1); b, u, r: [Nt][S] device FP64, computed in FP64. */
+PD_API pd_status pd_residual(pd_plan* plan, const double* b, const double* u, double* r);
+
+/* y = A u (eq. 1.1) in FP64. */
+PD_API pd_status pd_apply_A(pd_plan* plan, const double* u, double* y);
+
+/* y = A^T u in FP64. */
+PD_API pd_status pd_apply_AT(pd_plan* plan, const double* u, double* y);
+
+/* b of the all-at-once system from the initial data and the source:
+ *   theta-method (eq. 2.4):  b_n = theta f(t_n) + (1-theta) f(t_{n-1}),
+ *                            b_1 += (I/dt - (1-theta) K) u0;
+ *   leap-frog (eq. 3.2b, ghost value U_{-1} = U_1 - 2 dt u1):
+ *      b_1 = u0/dt^2 + u1/dt + (dt/2) K u1 + f(t_0)/2,
+ *      b_2 = f(t_1) - u0/dt^2 - K u0/2,  b_n = f(t_{n-1}) for n >= 3.
+ * u0: [S]; u1: [S] or NULL (zero; leap-frog only); f: [Nt+1][S] (values at
+ * t_0..t_Nt) or NULL (zero source); b: [Nt][S].  All device FP64. */
+PD_API pd_status pd_build_rhs(pd_plan* plan, const double* u0, const double* u1, const double* f,
+                       double* b);
+
+/* Solve A u = b.  mode PD_STATIONARY: the iteration of eq. 5.1,
+ * u <- u + P_alpha^{-1}(b - A u); mode PD_GMRES: flexible GMRES(restart) on A
+ * right-preconditioned by P_alpha^{-1} (the Krylov variant of Section 3),
+ * FP64 Krylov vectors.  u holds the initial guess on entry and the solution
+ * on exit (device FP64).  Stops when ||b - A u||_2 <= tol ||b||_2 or after maxit
+ * preconditioner applications (PD_ERR_NOT_CONVERGED).  iters and relres may be
+ * NULL.  Synchronises the plan's stream. */
+PD_API pd_status pd_solve(pd_plan* plan, const double* b, double* u, int mode, double tol, int maxit,
+                   int restart, int* iters, double* relres);
+
+/* The same solve with HOST buffers: copies b and the initial guess to the
+ * device, solves, and copies u back (all on the plan's stream). */
+PD_API pd_status pd_solve_host(pd_plan* plan, const double* b_host, double* u_host, int mode,
+                        double tol, int maxit, int restart, int* iters, double* relres);
+
+/* Solve A^T lambda = g (the transposed all-at-once system, backward in time).
+ * Uses J A^T J = B1 (x) I + B2 (x) K^T (J = time reversal, B1, B2 Toeplitz):
+ * a forward ParaDiag solve with K^T on time-reversed data.  lambda: initial
+ * guess on entry (device FP64), solution on exit. */
+PD_API pd_status pd_adjoint_solve(pd_plan* plan, const double* g, double* lam, int mode, double tol,
+                           int maxit, int restart, int* iters, double* relres);
+
+/* Time the kernels of one preconditioned iteration of the stationary solver
+ * (residual + Gamma + FFT, x-transform forward, shifted tridiagonal solves,
+ * x-transform inverse, inverse FFT + update) with CUDA events on the plan's
+ * stream, averaged over reps >= 1 iterations started from the guess u with
+ * right-hand side b (device FP64; u is not modified).  ms[0..4] receive the
+ * average milliseconds per launch of these five kernels (0 where a kernel
+ * does not occur).  Synchronises the plan's stream. */
+PD_API pd_status pd_profile_iteration(pd_plan* plan, const double* b, const double* u, int reps,
+                                      float* ms);
+
+/* Number of kernels this plan (and its adjoint plan) has launched so far. */
+PD_API pd_status pd_plan_launches(const pd_plan* plan, unsigned long long* count);
+
+PD_API const char* pd_status_string(pd_status s);
+PD_API const char* pd_last_error(const pd_plan* plan);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PARADIAG_H */

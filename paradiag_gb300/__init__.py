@@ -1,0 +1,339 @@
+"""GB300-native ParaDiag-II: the alpha-circulant preconditioned all-at-once solver.
+
+The compute path is the CUDA library ``lib/libparadiag.so`` (sm_103a) behind
+the C ABI of ``include/paradiag.h``.  This module only marshals arguments:
+the functions ``pd_*`` below have the names and argument order of the C
+entry points and take raw device pointers; :class:`Plan` wraps them for torch
+tensors and :class:`PDSolve` makes the solve differentiable (its backward is
+the transposed all-at-once solve).  There is no CPU fallback: loading fails
+loudly when the library has not been built.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+from ._build import build, lib_path
+
+PD_OK, PD_ERR_ARG, PD_ERR_CUDA, PD_ERR_NOT_CONVERGED = 0, -1, -2, -3
+PD_ERR_NONFINITE, PD_ERR_UNSUPPORTED, PD_ERR_NOMEM = -4, -5, -6
+PD_BE, PD_CN, PD_THETA, PD_LEAPFROG = 0, 1, 2, 3
+PD_DIRICHLET, PD_PERIODIC = 0, 1
+PD_FP64, PD_MIXED = 0, 1
+PD_STATIONARY, PD_GMRES = 0, 1
+
+
+class pd_space(ctypes.Structure):
+    _fields_ = [("dim", ctypes.c_int), ("nx", ctypes.c_int), ("ny", ctypes.c_int),
+                ("nu", ctypes.c_double), ("ax", ctypes.c_double), ("ay", ctypes.c_double),
+                ("bc_x", ctypes.c_int), ("bc_y", ctypes.c_int),
+                ("lx", ctypes.c_double), ("ly", ctypes.c_double)]
+
+
+class PDError(RuntimeError):
+    def __init__(self, status, msg=""):
+        self.status = status
+        super().__init__(f"{pd_status_string(status)} ({status}): {msg}")
+
+
+_P = ctypes.c_void_p
+_D = ctypes.POINTER(ctypes.c_double)
+_I = ctypes.POINTER(ctypes.c_int)
+_SIGS = {
+    "pd_plan_create": (ctypes.c_int, [ctypes.POINTER(pd_space), ctypes.c_int, ctypes.c_double,
+                                      ctypes.c_double, ctypes.c_int, ctypes.c_double, ctypes.c_int,
+                                      _P, ctypes.POINTER(_P)]),
+    "pd_plan_destroy": (ctypes.c_int, [_P]),
+    "pd_plan_workspace": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_ulonglong)]),
+    "pd_apply_precond": (ctypes.c_int, [_P, _P, _P]),
+    "pd_residual": (ctypes.c_int, [_P, _P, _P, _P]),
+    "pd_apply_A": (ctypes.c_int, [_P, _P, _P]),
+    "pd_apply_AT": (ctypes.c_int, [_P, _P, _P]),
+    "pd_build_rhs": (ctypes.c_int, [_P, _P, _P, _P, _P]),
+    "pd_solve": (ctypes.c_int, [_P, _P, _P, ctypes.c_int, ctypes.c_double, ctypes.c_int,
+                                ctypes.c_int, _I, _D]),
+    "pd_solve_host": (ctypes.c_int, [_P, _P, _P, ctypes.c_int, ctypes.c_double, ctypes.c_int,
+                                     ctypes.c_int, _I, _D]),
+    "pd_adjoint_solve": (ctypes.c_int, [_P, _P, _P, ctypes.c_int, ctypes.c_double, ctypes.c_int,
+                                        ctypes.c_int, _I, _D]),
+    "pd_profile_iteration": (ctypes.c_int, [_P, _P, _P, ctypes.c_int,
+                                            ctypes.POINTER(ctypes.c_float)]),
+    "pd_plan_launches": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_ulonglong)]),
+    "pd_status_string": (ctypes.c_char_p, [ctypes.c_int]),
+    "pd_last_error": (ctypes.c_char_p, [_P]),
+}
+
+_lib = None
+
+
+def load(path: str | None = None):
+    """Load the CUDA library (raises if it is missing; there is no fallback)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = path or lib_path()
+    if not os.path.exists(path):
+        raise RuntimeError(f"ParaDiag CUDA library not built: {path} is missing "
+                           "(run paradiag_gb300.build())")
+    lib = ctypes.CDLL(path)
+    for name, (res, args) in _SIGS.items():
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    _lib = lib
+    return lib
+
+
+def exported_symbols():
+    return list(_SIGS)
+
+
+# --- the C entry points, same names and argument order ---------------------
+def pd_status_string(status: int) -> str:
+    return load().pd_status_string(status).decode()
+
+
+def pd_last_error(plan) -> str:
+    return load().pd_last_error(plan).decode()
+
+
+def pd_plan_create(space: pd_space, nt, dt, alpha, scheme, theta, precision, stream):
+    out = _P()
+    st = load().pd_plan_create(ctypes.byref(space), nt, dt, alpha, scheme, theta, precision,
+                               _P(stream), ctypes.byref(out))
+    return st, out.value
+
+
+def pd_plan_destroy(plan):
+    return load().pd_plan_destroy(plan)
+
+
+def pd_plan_workspace(plan):
+    v = ctypes.c_ulonglong(0)
+    st = load().pd_plan_workspace(plan, ctypes.byref(v))
+    return st, v.value
+
+
+def pd_profile_iteration(plan, b, u, reps):
+    ms = (ctypes.c_float * 5)()
+    st = load().pd_profile_iteration(plan, b, u, reps, ms)
+    return st, list(ms)
+
+
+def pd_plan_launches(plan):
+    v = ctypes.c_ulonglong(0)
+    st = load().pd_plan_launches(plan, ctypes.byref(v))
+    return st, v.value
+
+
+def pd_apply_precond(plan, r, z):
+    return load().pd_apply_precond(plan, r, z)
+
+
+def pd_residual(plan, b, u, r):
+    return load().pd_residual(plan, b, u, r)
+
+
+def pd_apply_A(plan, u, y):
+    return load().pd_apply_A(plan, u, y)
+
+
+def pd_apply_AT(plan, u, y):
+    return load().pd_apply_AT(plan, u, y)
+
+
+def pd_build_rhs(plan, u0, u1, f, b):
+    return load().pd_build_rhs(plan, u0, u1, f, b)
+
+
+def _solve_call(fn, plan, b, u, mode, tol, maxit, restart):
+    it = ctypes.c_int(0)
+    rel = ctypes.c_double(0.0)
+    st = fn(plan, b, u, mode, tol, maxit, restart, ctypes.byref(it), ctypes.byref(rel))
+    return st, it.value, rel.value
+
+
+def pd_solve(plan, b, u, mode, tol, maxit, restart):
+    return _solve_call(load().pd_solve, plan, b, u, mode, tol, maxit, restart)
+
+
+def pd_solve_host(plan, b, u, mode, tol, maxit, restart):
+    return _solve_call(load().pd_solve_host, plan, b, u, mode, tol, maxit, restart)
+
+
+def pd_adjoint_solve(plan, g, lam, mode, tol, maxit, restart):
+    return _solve_call(load().pd_adjoint_solve, plan, g, lam, mode, tol, maxit, restart)
+
+
+# --- torch convenience layer ----------------------------------------------
+def _ptr(t):
+    return None if t is None else ctypes.c_void_p(t.data_ptr())
+
+
+class Plan:
+    """A ParaDiag-II plan on the current CUDA device and stream.
+
+    ``space`` is a mapping or object with the pd_space fields (dim, nx, ny, nu,
+    ax, ay, bc_x, bc_y, lx, ly).  Tensors passed to the methods are CUDA float64
+    tensors of shape (nt, S) (or anything with nt*S contiguous elements).
+    """
+
+    def __init__(self, space, nt, dt, alpha, scheme=PD_BE, theta=1.0, precision=PD_MIXED,
+                 stream=None):
+        import torch
+        g = (lambda k, d=0: space.get(k, d)) if isinstance(space, dict) else \
+            (lambda k, d=0: getattr(space, k, d))
+        self.space = pd_space(int(g("dim", 1)), int(g("nx")), int(g("ny", 1) or 1),
+                              float(g("nu", 1.0)), float(g("ax", 0.0)), float(g("ay", 0.0)),
+                              int(g("bc_x", 0)), int(g("bc_y", 0)), float(g("lx", 1.0)),
+                              float(g("ly", 1.0)))
+        self.nt, self.dt, self.alpha = int(nt), float(dt), float(alpha)
+        self.scheme, self.theta, self.precision = int(scheme), float(theta), int(precision)
+        self.S = self.space.nx * (self.space.ny if self.space.dim == 2 else 1)
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        st, h = pd_plan_create(self.space, self.nt, self.dt, self.alpha, self.scheme, self.theta,
+                               self.precision, self.stream.cuda_stream)
+        if st != PD_OK:
+            raise PDError(st, "pd_plan_create")
+        self._h = h
+
+    @property
+    def handle(self):
+        return self._h
+
+    def close(self):
+        if getattr(self, "_h", None):
+            pd_plan_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _check(self, st, what):
+        if st != PD_OK:
+            raise PDError(st, f"{what}: {pd_last_error(self._h)}")
+
+    def _check_t(self, t, n=None):
+        import torch
+        n = self.nt * self.S if n is None else n
+        if not (t.is_cuda and t.dtype == torch.float64 and t.is_contiguous() and t.numel() == n):
+            raise ValueError(f"expected a contiguous CUDA float64 tensor with {n} elements")
+
+    def workspace_bytes(self):
+        st, v = pd_plan_workspace(self._h)
+        self._check(st, "pd_plan_workspace")
+        return v
+
+    def launches(self):
+        st, v = pd_plan_launches(self._h)
+        self._check(st, "pd_plan_launches")
+        return v
+
+    def profile_iteration(self, b, u, reps=5):
+        """Average ms per launch of [K1 residual+FFT, x-fwd, tridiagonal, x-inv, K3]."""
+        self._check_t(b); self._check_t(u)
+        st, ms = pd_profile_iteration(self._h, _ptr(b), _ptr(u), reps)
+        self._check(st, "pd_profile_iteration")
+        return ms
+
+    def apply_precond(self, r, z=None):
+        import torch
+        self._check_t(r)
+        z = torch.empty_like(r) if z is None else z
+        self._check(pd_apply_precond(self._h, _ptr(r), _ptr(z)), "pd_apply_precond")
+        return z
+
+    def residual(self, b, u, r=None):
+        import torch
+        self._check_t(b); self._check_t(u)
+        r = torch.empty_like(b) if r is None else r
+        self._check(pd_residual(self._h, _ptr(b), _ptr(u), _ptr(r)), "pd_residual")
+        return r
+
+    def apply_A(self, u, y=None, transpose=False):
+        import torch
+        self._check_t(u)
+        y = torch.empty_like(u) if y is None else y
+        fn = pd_apply_AT if transpose else pd_apply_A
+        self._check(fn(self._h, _ptr(u), _ptr(y)), "pd_apply_A")
+        return y
+
+    def build_rhs(self, u0, u1=None, f=None, b=None):
+        import torch
+        self._check_t(u0, self.S)
+        if u1 is not None:
+            self._check_t(u1, self.S)
+        if f is not None:
+            self._check_t(f, (self.nt + 1) * self.S)
+        b = torch.empty((self.nt, self.S), dtype=torch.float64, device=u0.device) if b is None else b
+        self._check(pd_build_rhs(self._h, _ptr(u0), _ptr(u1), _ptr(f), _ptr(b)), "pd_build_rhs")
+        return b
+
+    def solve(self, b, u=None, mode=PD_STATIONARY, tol=1e-10, maxit=50, restart=30,
+              allow_not_converged=False):
+        import torch
+        self._check_t(b)
+        u = torch.zeros_like(b) if u is None else u
+        self._check_t(u)
+        st, it, rel = pd_solve(self._h, _ptr(b), _ptr(u), mode, tol, maxit, restart)
+        if not (st == PD_OK or (allow_not_converged and st == PD_ERR_NOT_CONVERGED)):
+            self._check(st, "pd_solve")
+        return u, it, rel
+
+    def solve_host(self, b_host, u_host, mode=PD_STATIONARY, tol=1e-10, maxit=50, restart=30):
+        st, it, rel = pd_solve_host(self._h, _ptr(b_host), _ptr(u_host), mode, tol, maxit, restart)
+        if st != PD_OK:
+            self._check(st, "pd_solve_host")
+        return u_host, it, rel
+
+    def adjoint_solve(self, g, lam=None, mode=PD_STATIONARY, tol=1e-10, maxit=50, restart=30):
+        import torch
+        self._check_t(g)
+        lam = torch.zeros_like(g) if lam is None else lam
+        st, it, rel = pd_adjoint_solve(self._h, _ptr(g), _ptr(lam), mode, tol, maxit, restart)
+        self._check(st, "pd_adjoint_solve")
+        return lam, it, rel
+
+
+def _make_pdsolve():
+    import torch
+
+    class PDSolve(torch.autograd.Function):
+        """u = A^{-1} b with the ParaDiag-II solver; backward: dL/db = A^{-T} dL/du.
+
+        forward(plan, b, mode, tol, maxit) -> u.  The backward pass solves the
+        transposed all-at-once system (backward in time) with the same plan's
+        kernels (pd_adjoint_solve).
+        """
+
+        @staticmethod
+        def forward(ctx, plan, b, mode=PD_STATIONARY, tol=1e-10, maxit=50):
+            ctx.plan, ctx.mode, ctx.tol, ctx.maxit = plan, mode, tol, maxit
+            u, _, _ = plan.solve(b.detach().contiguous(), mode=mode, tol=tol, maxit=maxit)
+            return u
+
+        @staticmethod
+        def backward(ctx, g):
+            lam, _, _ = ctx.plan.adjoint_solve(g.contiguous(), mode=ctx.mode, tol=ctx.tol,
+                                              maxit=ctx.maxit)
+            return None, lam, None, None, None
+
+    return PDSolve
+
+
+class _Lazy:
+    _cls = None
+
+    def __getattr__(self, k):
+        if _Lazy._cls is None:
+            _Lazy._cls = _make_pdsolve()
+        return getattr(_Lazy._cls, k)
+
+
+PDSolve = _Lazy()
+
+__all__ = ["build", "lib_path", "load", "Plan", "PDSolve", "PDError", "pd_space",
+           "exported_symbols"] + [k for k in _SIGS]

@@ -1,0 +1,802 @@
+// Plans, solvers and the C ABI of the ParaDiag-II library (include/paradiag.h).
+//
+// Plan creation evaluates, on the host in FP64, everything that depends only
+// on the problem: the first columns c1, c2 of the Toeplitz B1, B2 (eq. 2.5b,
+// eq. 3.2b), the eigenvalues of the alpha-circulants C1, C2 (Lemma 1)
+//   lambda_{j,k} = sum_m c_j[m] w_k^m,  w_k = alpha^{1/Nt} exp(-2 pi i k/Nt),
+// which equal the diagonal of D_j for the forward transform with
+// exp(-2 pi i k n/Nt) used by the kernels, the Gamma_alpha tables
+// (gamma_n = alpha^{n/Nt}, n = 0..Nt-1), the FFT twiddles and, for 2D, the
+// eigenvectors and eigenvalues of K_x.  Only k = 0..Nt/2 is kept: real data
+// give a Hermitian spectrum, so the shifted solve at Nt-k is the conjugate of
+// the one at k.
+#include <algorithm>
+#include <cmath>
+#include <complex>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "pd_internal.h"
+
+using cd = std::complex<double>;
+
+struct pd_plan {
+  pd_space sp;
+  int nt = 0, nh = 0, S = 0, logN = 0, TX = 0;
+  int scheme = 0;
+  double theta = 1.0, dt = 0.0, alpha = 0.0;
+  int precision = 0;
+  bool fp64 = false;
+  Stencil st;
+  TimeBand tb;
+  double s_scale = 1.0;
+  cudaStream_t stream = nullptr;
+  // step (b) layout
+  bool xform = false;
+  int J = 1, tri_n = 0, tri_stride = 1;
+  double tri_cl = 0, tri_cd = 0, tri_cu = 0;
+  // device tables
+  void* lam = nullptr;
+  void* gam = nullptr;
+  void* igam = nullptr;
+  void* igam_s = nullptr;
+  void* tw = nullptr;
+  void* Qf = nullptr;
+  void* Qi = nullptr;
+  void* mu = nullptr;
+  // workspace
+  void* spec = nullptr;
+  void* spec2 = nullptr;
+  float2* Udf = nullptr;
+  float2* Bdf = nullptr;
+  double* w64a = nullptr;
+  double* w64b = nullptr;
+  double* dsc = nullptr;   // device scalars
+  int* dflag = nullptr;
+  double* hsc = nullptr;   // pinned host scalars
+  double* V = nullptr;
+  double* Z = nullptr;
+  double* dh = nullptr;
+  int gm_cap = 0;
+  pd_plan* adj = nullptr;
+  size_t bytes = 0;
+  unsigned long long launches = 0;
+  char msg[256] = {0};
+};
+
+namespace {
+
+constexpr int NSC = 96;  // device / host scalar slots
+
+pd_status set_err(pd_plan* p, pd_status s, const char* what) {
+  if (p) snprintf(p->msg, sizeof(p->msg), "%s", what);
+  return s;
+}
+
+pd_status fail_cuda(pd_plan* p, cudaError_t e, const char* what) {
+  if (p) snprintf(p->msg, sizeof(p->msg), "%s: %s", what, cudaGetErrorString(e));
+  cudaGetLastError();
+  return e == cudaErrorMemoryAllocation ? PD_ERR_NOMEM : PD_ERR_CUDA;
+}
+
+#define CU(call)                                         \
+  do {                                                   \
+    cudaError_t e_ = (call);                             \
+    if (e_ != cudaSuccess) return fail_cuda(p, e_, #call); \
+  } while (0)
+
+// a kernel launch through one of the launch_* wrappers (counted per plan)
+#define LK(call)                                           \
+  do {                                                     \
+    cudaError_t e_ = (call);                               \
+    ++p->launches;                                         \
+    if (e_ != cudaSuccess) return fail_cuda(p, e_, #call); \
+  } while (0)
+
+#define CHK(call)                      \
+  do {                                 \
+    pd_status s_ = (call);             \
+    if (s_ != PD_OK) return s_;        \
+  } while (0)
+
+pd_status dalloc(pd_plan* p, void** ptr, size_t bytes) {
+  if (bytes == 0) bytes = 16;
+  cudaError_t e = cudaMalloc(ptr, bytes);
+  if (e != cudaSuccess) {
+    *ptr = nullptr;
+    return fail_cuda(p, e, "cudaMalloc");
+  }
+  p->bytes += bytes;
+  return PD_OK;
+}
+
+template <typename T>
+pd_status upload(pd_plan* p, void** dst, const std::vector<T>& v) {
+  CHK(dalloc(p, dst, v.size() * sizeof(T)));
+  CU(cudaMemcpy(*dst, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice));
+  return PD_OK;
+}
+
+// upload complex values as float2 or double2
+pd_status upload_cplx(pd_plan* p, void** dst, const std::vector<cd>& v, bool fp64) {
+  if (fp64) {
+    std::vector<double2> h(v.size());
+    for (size_t i = 0; i < v.size(); ++i) h[i] = make_double2(v[i].real(), v[i].imag());
+    return upload(p, dst, h);
+  }
+  std::vector<float2> h(v.size());
+  for (size_t i = 0; i < v.size(); ++i) h[i] = make_float2((float)v[i].real(), (float)v[i].imag());
+  return upload(p, dst, h);
+}
+
+pd_status upload_real(pd_plan* p, void** dst, const std::vector<double>& v, bool fp64) {
+  if (fp64) return upload(p, dst, v);
+  std::vector<float> h(v.size());
+  for (size_t i = 0; i < v.size(); ++i) h[i] = (float)v[i];
+  return upload(p, dst, h);
+}
+
+void free_plan(pd_plan* p) {
+  if (!p) return;
+  void* ptrs[] = {p->lam, p->gam, p->igam, p->igam_s, p->tw, p->Qf, p->Qi, p->mu, p->spec,
+                  p->spec2, p->Udf, p->Bdf, p->w64a, p->w64b, p->dsc, p->dflag, p->V, p->Z, p->dh};
+  for (void* q : ptrs)
+    if (q) cudaFree(q);
+  if (p->hsc) cudaFreeHost(p->hsc);
+  if (p->adj) free_plan(p->adj);
+  delete p;
+}
+
+size_t NS(const pd_plan* p) { return (size_t)p->nt * p->S; }
+size_t cbytes(const pd_plan* p) { return p->fp64 ? sizeof(double2) : sizeof(float2); }
+
+FwdArgs fwd_base(const pd_plan* p) {
+  FwdArgs a;
+  memset(&a, 0, sizeof(a));
+  a.N = p->nt; a.logN = p->logN; a.nh = p->nh; a.S = p->S; a.TX = p->TX;
+  a.st = p->st; a.tb = p->tb;
+  const double s = p->s_scale;
+  const double kap[5] = {p->st.kc, p->st.kxl, p->st.kxu, p->st.kyl, p->st.kyu};
+  for (int i = 0; i < 5; ++i) {
+    const dfc c = dfc_from(s * kap[i]);
+    a.kap[i].hi = c.hi; a.kap[i].lo = c.lo;
+  }
+  for (int m = 0; m < 3; ++m) {
+    const dfc c = dfc_from(p->tb.c2[m]);
+    a.e2[m].hi = c.hi; a.e2[m].lo = c.lo;
+  }
+  a.rscale2 = 1.0 / (s * s);
+  a.gam = p->gam;
+  a.tw = p->tw;
+  a.out = p->spec;
+  return a;
+}
+
+InvArgs inv_base(const pd_plan* p) {
+  InvArgs a;
+  memset(&a, 0, sizeof(a));
+  a.N = p->nt; a.logN = p->logN; a.nh = p->nh; a.S = p->S; a.TX = p->TX;
+  a.in = p->spec;
+  a.igam = p->igam;
+  a.tw = p->tw;
+  a.flag = p->dflag;
+  return a;
+}
+
+// step (b), with the x-eigentransform around it for 2D / periodic-x problems
+pd_status step_b(pd_plan* p) {
+  void* data = p->spec;
+  if (p->xform) {
+    XformArgs xa;
+    xa.rows = p->nh * (p->S / p->sp.nx);
+    xa.nx = p->sp.nx;
+    xa.Q = p->Qf; xa.in = p->spec; xa.out = p->spec2;
+    LK(launch_xform(xa, p->fp64, p->stream));
+    data = p->spec2;
+  }
+  TriArgs ta;
+  ta.nh = p->nh; ta.J = p->J; ta.n = p->tri_n; ta.S = p->S; ta.stride = p->tri_stride;
+  ta.cl = p->tri_cl; ta.cd = p->tri_cd; ta.cu = p->tri_cu;
+  ta.lam = p->lam; ta.mu = p->xform ? p->mu : nullptr; ta.data = data; ta.flag = p->dflag;
+  LK(launch_tridiag(ta, p->fp64, p->stream));
+  if (p->xform) {
+    XformArgs xa;
+    xa.rows = p->nh * (p->S / p->sp.nx);
+    xa.nx = p->sp.nx;
+    xa.Q = p->Qi; xa.in = p->spec2; xa.out = p->spec;
+    LK(launch_xform(xa, p->fp64, p->stream));
+  }
+  return PD_OK;
+}
+
+pd_status precond_into(pd_plan* p, const double* r, double* z) {
+  FwdArgs fa = fwd_base(p);
+  fa.mode = FWD_STANDALONE;
+  fa.r64 = r;
+  LK(launch_time_fwd(fa, p->fp64, p->stream));
+  CHK(step_b(p));
+  InvArgs ia = inv_base(p);
+  ia.mode = INV_OUT64;
+  ia.out64 = z;
+  LK(launch_time_inv(ia, p->fp64, p->stream));
+  return PD_OK;
+}
+
+pd_status sync_scalars(pd_plan* p, int nscal) {
+  CU(cudaMemcpyAsync(p->hsc, p->dsc, nscal * sizeof(double), cudaMemcpyDeviceToHost, p->stream));
+  CU(cudaMemcpyAsync(p->hsc + NSC - 1, p->dflag, sizeof(int), cudaMemcpyDeviceToHost, p->stream));
+  CU(cudaStreamSynchronize(p->stream));
+  return PD_OK;
+}
+
+bool flag_set(const pd_plan* p) {
+  int f;
+  memcpy(&f, p->hsc + NSC - 1, sizeof(int));
+  return f != 0;
+}
+
+pd_status solve_stationary(pd_plan* p, const double* b, double* u, double tol, int maxit,
+                           int* iters, double* relres) {
+  const size_t ns = NS(p);
+  CU(cudaMemsetAsync(p->dsc, 0, 2 * sizeof(double), p->stream));
+  CU(cudaMemsetAsync(p->dflag, 0, sizeof(int), p->stream));
+  LK(launch_norm2(b, ns, p->dsc, p->stream));
+  if (!p->fp64) {
+    LK(launch_to_df(u, 1.0, p->Udf, ns, p->stream));
+    LK(launch_to_df(b, p->s_scale, p->Bdf, ns, p->stream));
+  }
+  int it = 0;
+  double rel = 0.0;
+  pd_status st = PD_OK;
+  for (;;) {
+    CU(cudaMemsetAsync(p->dsc + 1, 0, sizeof(double), p->stream));
+    FwdArgs fa = fwd_base(p);
+    fa.mode = FWD_RESIDUAL;
+    fa.norm2 = p->dsc + 1;
+    if (p->fp64) { fa.U64 = u; fa.B64 = b; }
+    else { fa.Udf = p->Udf; fa.Bdf = p->Bdf; }
+    LK(launch_time_fwd(fa, p->fp64, p->stream));
+    CHK(sync_scalars(p, 2));
+    const double nb = std::sqrt(p->hsc[0]);
+    if (nb == 0.0) {
+      CU(cudaMemsetAsync(u, 0, ns * sizeof(double), p->stream));
+      CU(cudaStreamSynchronize(p->stream));
+      rel = 0.0;
+      break;
+    }
+    rel = std::sqrt(p->hsc[1]) / nb;
+    if (!std::isfinite(rel) || flag_set(p)) {
+      st = set_err(p, PD_ERR_NONFINITE, "non-finite value in the stationary iteration");
+      break;
+    }
+    if (rel <= tol) break;
+    if (it >= maxit) {
+      st = set_err(p, PD_ERR_NOT_CONVERGED, "stationary iteration reached maxit");
+      break;
+    }
+    CHK(step_b(p));
+    InvArgs ia = inv_base(p);
+    if (p->fp64) { ia.mode = INV_UPDATE64; ia.out64 = u; }
+    else { ia.mode = INV_UPDATE_DF; ia.Udf = p->Udf; ia.igam = p->igam_s; }
+    LK(launch_time_inv(ia, p->fp64, p->stream));
+    ++it;
+  }
+  if (!p->fp64 && p->hsc[0] != 0.0) LK(launch_from_df(p->Udf, u, ns, p->stream));
+  CU(cudaStreamSynchronize(p->stream));
+  if (iters) *iters = it;
+  if (relres) *relres = rel;
+  return st;
+}
+
+pd_status ensure_gmres(pd_plan* p, int m) {
+  if (p->gm_cap >= m) return PD_OK;
+  const size_t ns = NS(p);
+  if (p->V) { cudaFree(p->V); p->V = nullptr; }
+  if (p->Z) { cudaFree(p->Z); p->Z = nullptr; }
+  if (p->dh) { cudaFree(p->dh); p->dh = nullptr; }
+  CHK(dalloc(p, (void**)&p->V, (size_t)(m + 1) * ns * sizeof(double)));
+  CHK(dalloc(p, (void**)&p->Z, (size_t)m * ns * sizeof(double)));
+  CHK(dalloc(p, (void**)&p->dh, (size_t)(m + 2) * sizeof(double)));
+  p->gm_cap = m;
+  return PD_OK;
+}
+
+// Flexible GMRES(m), right preconditioned: u = u0 + Z y, Z_j = P^{-1} V_j;
+// classical Gram-Schmidt applied twice; Givens rotations on the host.
+pd_status solve_gmres(pd_plan* p, const double* b, double* u, double tol, int maxit, int restart,
+                      int* iters, double* relres) {
+  const size_t ns = NS(p);
+  int m = restart > 0 ? restart : 30;
+  m = std::min(m, std::max(1, maxit));
+  CHK(ensure_gmres(p, m));
+  CU(cudaMemsetAsync(p->dsc, 0, 2 * sizeof(double), p->stream));
+  CU(cudaMemsetAsync(p->dflag, 0, sizeof(int), p->stream));
+  LK(launch_norm2(b, ns, p->dsc, p->stream));
+  CHK(sync_scalars(p, 1));
+  const double nb = std::sqrt(p->hsc[0]);
+  if (nb == 0.0) {
+    CU(cudaMemsetAsync(u, 0, ns * sizeof(double), p->stream));
+    CU(cudaStreamSynchronize(p->stream));
+    if (iters) *iters = 0;
+    if (relres) *relres = 0.0;
+    return PD_OK;
+  }
+  std::vector<double> H((size_t)(m + 1) * m), cs(m), sn(m), g(m + 1), y(m);
+  auto Hat = [&](int i, int j) -> double& { return H[(size_t)i * m + j]; };
+  int total = 0;
+  double rel = 0.0;
+  pd_status st = PD_OK;
+  for (;;) {
+    CU(cudaMemsetAsync(p->dsc + 1, 0, sizeof(double), p->stream));
+    CU(launch_apply_A(p->st, p->tb, p->nt, u, b, p->V, p->dsc + 1, 0, p->stream));
+    CHK(sync_scalars(p, 2));
+    const double beta = std::sqrt(p->hsc[1]);
+    rel = beta / nb;
+    if (!std::isfinite(rel) || flag_set(p)) {
+      st = set_err(p, PD_ERR_NONFINITE, "non-finite value in GMRES");
+      break;
+    }
+    if (rel <= tol) break;
+    if (total >= maxit) {
+      st = set_err(p, PD_ERR_NOT_CONVERGED, "GMRES reached maxit");
+      break;
+    }
+    LK(launch_scale_copy(1.0 / beta, p->V, p->V, ns, p->stream));
+    std::fill(H.begin(), H.end(), 0.0);
+    std::fill(g.begin(), g.end(), 0.0);
+    g[0] = beta;
+    int jdone = 0;
+    for (int j = 0; j < m; ++j) {
+      double* Vj = p->V + (size_t)j * ns;
+      double* Zj = p->Z + (size_t)j * ns;
+      double* w = p->V + (size_t)(j + 1) * ns;
+      CHK(precond_into(p, Vj, Zj));
+      CU(launch_apply_A(p->st, p->tb, p->nt, Zj, nullptr, w, nullptr, 0, p->stream));
+      for (int pass = 0; pass < 2; ++pass) {
+        CU(cudaMemsetAsync(p->dh, 0, (j + 1) * sizeof(double), p->stream));
+        LK(launch_dots(p->V, j + 1, ns, w, p->dh, p->stream));
+        LK(launch_gemv_sub(p->V, j + 1, ns, p->dh, w, p->stream));
+        CU(cudaMemcpyAsync(p->hsc + 8, p->dh, (j + 1) * sizeof(double), cudaMemcpyDeviceToHost,
+                           p->stream));
+        CU(cudaStreamSynchronize(p->stream));
+        for (int i = 0; i <= j; ++i) Hat(i, j) += p->hsc[8 + i];
+      }
+      CU(cudaMemsetAsync(p->dsc + 2, 0, sizeof(double), p->stream));
+      LK(launch_norm2(w, ns, p->dsc + 2, p->stream));
+      CU(cudaMemcpyAsync(p->hsc + 2, p->dsc + 2, sizeof(double), cudaMemcpyDeviceToHost, p->stream));
+      CU(cudaMemcpyAsync(p->hsc + NSC - 1, p->dflag, sizeof(int), cudaMemcpyDeviceToHost, p->stream));
+      CU(cudaStreamSynchronize(p->stream));
+      if (flag_set(p)) return set_err(p, PD_ERR_NONFINITE, "non-finite value in the preconditioner");
+      const double hn = std::sqrt(p->hsc[2]);
+      Hat(j + 1, j) = hn;
+      if (hn > 0.0) LK(launch_scale_copy(1.0 / hn, w, w, ns, p->stream));
+      for (int i = 0; i < j; ++i) {
+        const double t = cs[i] * Hat(i, j) + sn[i] * Hat(i + 1, j);
+        Hat(i + 1, j) = -sn[i] * Hat(i, j) + cs[i] * Hat(i + 1, j);
+        Hat(i, j) = t;
+      }
+      const double den = std::hypot(Hat(j, j), Hat(j + 1, j));
+      cs[j] = den > 0 ? Hat(j, j) / den : 1.0;
+      sn[j] = den > 0 ? Hat(j + 1, j) / den : 0.0;
+      Hat(j, j) = den;
+      Hat(j + 1, j) = 0.0;
+      g[j + 1] = -sn[j] * g[j];
+      g[j] = cs[j] * g[j];
+      ++total;
+      jdone = j + 1;
+      if (std::fabs(g[j + 1]) <= tol * nb || total >= maxit || hn == 0.0) break;
+    }
+    for (int i = jdone - 1; i >= 0; --i) {
+      double s = g[i];
+      for (int k = i + 1; k < jdone; ++k) s -= Hat(i, k) * y[k];
+      y[i] = Hat(i, i) != 0.0 ? s / Hat(i, i) : 0.0;
+    }
+    for (int i = 0; i < jdone; ++i) p->hsc[8 + i] = y[i];
+    CU(cudaMemcpyAsync(p->dh, p->hsc + 8, jdone * sizeof(double), cudaMemcpyHostToDevice, p->stream));
+    LK(launch_combine(p->Z, jdone, ns, p->dh, u, p->stream));
+  }
+  CU(cudaStreamSynchronize(p->stream));
+  if (iters) *iters = total;
+  if (relres) *relres = rel;
+  return st;
+}
+
+pd_status solve_any(pd_plan* p, const double* b, double* u, int mode, double tol, int maxit,
+                    int restart, int* iters, double* relres) {
+  if (!p || !b || !u) return set_err(p, PD_ERR_ARG, "null argument");
+  if (!(tol >= 0.0) || maxit < 0) return set_err(p, PD_ERR_ARG, "tol must be >= 0 and maxit >= 0");
+  if (mode == PD_STATIONARY) return solve_stationary(p, b, u, tol, maxit, iters, relres);
+  if (mode == PD_GMRES) {
+    if (restart < 0 || restart > 64) return set_err(p, PD_ERR_ARG, "restart must be in [0, 64]");
+    return solve_gmres(p, b, u, tol, maxit, restart, iters, relres);
+  }
+  return set_err(p, PD_ERR_ARG, "unknown solver mode");
+}
+
+double hstep(int n, double L, int bc) { return L / (bc == PD_PERIODIC ? n : n + 1); }
+
+}  // namespace
+
+extern "C" {
+
+pd_status pd_plan_launches(const pd_plan* plan, unsigned long long* count) {
+  if (!plan || !count) return PD_ERR_ARG;
+  *count = plan->launches + (plan->adj ? plan->adj->launches : 0);
+  return PD_OK;
+}
+
+pd_status pd_profile_iteration(pd_plan* p, const double* b, const double* u, int reps,
+                               float* ms) {
+  if (!p || !b || !u || !ms || reps < 1) return set_err(p, PD_ERR_ARG, "bad argument");
+  const size_t ns = NS(p);
+  double* u64 = nullptr;
+  if (p->fp64) {
+    if (!p->w64b) CHK(dalloc(p, (void**)&p->w64b, ns * sizeof(double)));
+    CU(cudaMemcpyAsync(p->w64b, u, ns * sizeof(double), cudaMemcpyDeviceToDevice, p->stream));
+    u64 = p->w64b;
+  } else {
+    LK(launch_to_df(u, 1.0, p->Udf, ns, p->stream));
+    LK(launch_to_df(b, p->s_scale, p->Bdf, ns, p->stream));
+  }
+  cudaEvent_t ev[6];
+  for (int i = 0; i < 6; ++i) CU(cudaEventCreate(&ev[i]));
+  double acc[5] = {0, 0, 0, 0, 0};
+  for (int r = 0; r < reps; ++r) {
+    CU(cudaEventRecord(ev[0], p->stream));
+    FwdArgs fa = fwd_base(p);
+    fa.mode = FWD_RESIDUAL;
+    fa.norm2 = p->dsc + 1;
+    if (p->fp64) { fa.U64 = u64; fa.B64 = b; }
+    else { fa.Udf = p->Udf; fa.Bdf = p->Bdf; }
+    LK(launch_time_fwd(fa, p->fp64, p->stream));
+    CU(cudaEventRecord(ev[1], p->stream));
+    void* data = p->spec;
+    XformArgs xa;
+    xa.rows = p->nh * (p->S / p->sp.nx);
+    xa.nx = p->sp.nx;
+    if (p->xform) {
+      xa.Q = p->Qf; xa.in = p->spec; xa.out = p->spec2;
+      LK(launch_xform(xa, p->fp64, p->stream));
+      data = p->spec2;
+    }
+    CU(cudaEventRecord(ev[2], p->stream));
+    TriArgs ta;
+    ta.nh = p->nh; ta.J = p->J; ta.n = p->tri_n; ta.S = p->S; ta.stride = p->tri_stride;
+    ta.cl = p->tri_cl; ta.cd = p->tri_cd; ta.cu = p->tri_cu;
+    ta.lam = p->lam; ta.mu = p->xform ? p->mu : nullptr; ta.data = data; ta.flag = p->dflag;
+    LK(launch_tridiag(ta, p->fp64, p->stream));
+    CU(cudaEventRecord(ev[3], p->stream));
+    if (p->xform) {
+      xa.Q = p->Qi; xa.in = p->spec2; xa.out = p->spec;
+      LK(launch_xform(xa, p->fp64, p->stream));
+    }
+    CU(cudaEventRecord(ev[4], p->stream));
+    InvArgs ia = inv_base(p);
+    if (p->fp64) { ia.mode = INV_UPDATE64; ia.out64 = u64; }
+    else { ia.mode = INV_UPDATE_DF; ia.Udf = p->Udf; ia.igam = p->igam_s; }
+    LK(launch_time_inv(ia, p->fp64, p->stream));
+    CU(cudaEventRecord(ev[5], p->stream));
+    CU(cudaEventSynchronize(ev[5]));
+    for (int i = 0; i < 5; ++i) {
+      float t = 0.f;
+      CU(cudaEventElapsedTime(&t, ev[i], ev[i + 1]));
+      acc[i] += t;
+    }
+  }
+  for (int i = 0; i < 6; ++i) cudaEventDestroy(ev[i]);
+  for (int i = 0; i < 5; ++i) ms[i] = (float)(acc[i] / reps);
+  if (!p->xform) { ms[1] = 0.f; ms[3] = 0.f; }
+  return PD_OK;
+}
+
+const char* pd_status_string(pd_status s) {
+  switch (s) {
+    case PD_OK: return "ok";
+    case PD_ERR_ARG: return "invalid argument";
+    case PD_ERR_CUDA: return "CUDA error";
+    case PD_ERR_NOT_CONVERGED: return "not converged";
+    case PD_ERR_NONFINITE: return "non-finite value";
+    case PD_ERR_UNSUPPORTED: return "unsupported problem";
+    case PD_ERR_NOMEM: return "out of device memory";
+  }
+  return "unknown status";
+}
+
+const char* pd_last_error(const pd_plan* plan) { return plan ? plan->msg : "null plan"; }
+
+pd_status pd_plan_create(const pd_space* sp, int nt, double dt, double alpha, int scheme,
+                         double theta, int precision, void* stream, pd_plan** out) {
+  if (!out) return PD_ERR_ARG;
+  *out = nullptr;
+  if (!sp) return PD_ERR_ARG;
+  if (sp->dim != 1 && sp->dim != 2) return PD_ERR_ARG;
+  if (sp->nx < 1 || (sp->dim == 2 && sp->ny < 1)) return PD_ERR_ARG;
+  if (!(sp->nu >= 0.0) || !(sp->lx > 0.0) || (sp->dim == 2 && !(sp->ly > 0.0))) return PD_ERR_ARG;
+  if (!std::isfinite(sp->ax) || (sp->dim == 2 && !std::isfinite(sp->ay))) return PD_ERR_ARG;
+  if (sp->bc_x != PD_DIRICHLET && sp->bc_x != PD_PERIODIC) return PD_ERR_ARG;
+  if (sp->dim == 2 && sp->bc_y != PD_DIRICHLET && sp->bc_y != PD_PERIODIC) return PD_ERR_ARG;
+  if (sp->bc_x == PD_PERIODIC && sp->nx < 2) return PD_ERR_ARG;
+  if (!(dt > 0.0) || !std::isfinite(dt)) return PD_ERR_ARG;
+  if (!(alpha > 0.0 && alpha <= 1.0)) return PD_ERR_ARG;
+  if (scheme < PD_BE || scheme > PD_LEAPFROG) return PD_ERR_ARG;
+  if (scheme == PD_THETA && !(theta >= 0.0 && theta <= 1.0)) return PD_ERR_ARG;
+  if (precision != PD_FP64 && precision != PD_MIXED) return PD_ERR_ARG;
+  if (nt < 1) return PD_ERR_ARG;
+  const int nmax = precision == PD_MIXED ? 8192 : 4096;
+  if (!is_pow2(nt) || nt > nmax) return PD_ERR_UNSUPPORTED;
+  if (sp->dim == 2) {
+    if (sp->bc_y != PD_DIRICHLET) return PD_ERR_UNSUPPORTED;
+    if (sp->bc_x == PD_DIRICHLET && sp->ax != 0.0) return PD_ERR_UNSUPPORTED;
+  }
+  const long long S = (long long)sp->nx * (sp->dim == 2 ? sp->ny : 1);
+  if (S > (1LL << 30) || S * nt > (1LL << 40)) return PD_ERR_ARG;
+
+  pd_plan* p = new (std::nothrow) pd_plan();
+  if (!p) return PD_ERR_NOMEM;
+  p->sp = *sp;
+  if (sp->dim == 1) { p->sp.ny = 1; p->sp.ay = 0.0; p->sp.bc_y = PD_DIRICHLET; p->sp.ly = 1.0; }
+  p->nt = nt;
+  p->nh = nt / 2 + 1;
+  p->S = (int)S;
+  p->logN = ilog2(nt);
+  p->scheme = scheme;
+  p->theta = scheme == PD_BE ? 1.0 : scheme == PD_CN ? 0.5 : theta;
+  p->dt = dt;
+  p->alpha = alpha;
+  p->precision = precision;
+  p->fp64 = precision == PD_FP64;
+  p->stream = (cudaStream_t)stream;
+  const int budget = p->fp64 ? 8192 : 16384;
+  p->TX = std::max(2, std::min(32, budget / nt));
+
+  // spatial stencil
+  Stencil& st = p->st;
+  st.dim = sp->dim;
+  st.nx = sp->nx;
+  st.ny = p->sp.ny;
+  st.S = (int)S;
+  st.bcx = sp->bc_x;
+  st.bcy = p->sp.bc_y;
+  const double hx = hstep(sp->nx, sp->lx, sp->bc_x);
+  const double kcx = 2.0 * sp->nu / (hx * hx);
+  st.kxl = -sp->nu / (hx * hx) - sp->ax / (2.0 * hx);
+  st.kxu = -sp->nu / (hx * hx) + sp->ax / (2.0 * hx);
+  double kcy = 0.0;
+  st.kyl = st.kyu = 0.0;
+  if (sp->dim == 2) {
+    const double hy = hstep(sp->ny, sp->ly, sp->bc_y);
+    kcy = 2.0 * sp->nu / (hy * hy);
+    st.kyl = -sp->nu / (hy * hy) - sp->ay / (2.0 * hy);
+    st.kyu = -sp->nu / (hy * hy) + sp->ay / (2.0 * hy);
+  }
+  st.kc = kcx + kcy;
+
+  // time band (first columns of B1, B2)
+  TimeBand& tb = p->tb;
+  memset(&tb, 0, sizeof(tb));
+  if (scheme == PD_LEAPFROG) {
+    tb.band = 2;
+    tb.c1[0] = 1.0 / (dt * dt); tb.c1[1] = -2.0 / (dt * dt); tb.c1[2] = 1.0 / (dt * dt);
+    tb.c2[0] = 0.5; tb.c2[1] = 0.0; tb.c2[2] = 0.5;
+  } else {
+    tb.band = 1;
+    tb.c1[0] = 1.0 / dt; tb.c1[1] = -1.0 / dt;
+    tb.c2[0] = p->theta; tb.c2[1] = 1.0 - p->theta;
+  }
+  p->s_scale = 1.0 / tb.c1[0];
+
+  // step (b) layout
+  std::vector<cd> mux;
+  if (sp->dim == 2 || sp->bc_x == PD_PERIODIC) {
+    p->xform = true;
+    p->J = sp->nx;
+    const int n = sp->nx;
+    std::vector<cd> Qf((size_t)n * n), Qi((size_t)n * n);
+    mux.resize(n);
+    const double PI = 3.14159265358979323846;
+    if (sp->bc_x == PD_PERIODIC) {
+      // K_x v = mu_j v for v_x = exp(2 pi i j x / n); forward: exp(-2 pi i j x / n)
+      for (int j = 0; j < n; ++j) {
+        for (int x = 0; x < n; ++x) {
+          const long long jx = ((long long)j * x) % n;
+          const double th = 2.0 * PI * (double)jx / n;
+          Qf[(size_t)j * n + x] = cd(std::cos(th), -std::sin(th));
+          Qi[(size_t)x * n + j] = cd(std::cos(th), std::sin(th)) / (double)n;
+        }
+        const double th = 2.0 * PI * j / n;
+        mux[j] = kcx + st.kxl * cd(std::cos(th), -std::sin(th)) + st.kxu * cd(std::cos(th), std::sin(th));
+      }
+    } else {
+      // symmetric Dirichlet: sine eigenvectors sin(pi (j+1)(x+1)/(n+1)), Q^{-1} = 2/(n+1) Q
+      for (int j = 0; j < n; ++j) {
+        for (int x = 0; x < n; ++x) {
+          const double v = std::sin(PI * (double)(j + 1) * (double)(x + 1) / (n + 1));
+          Qf[(size_t)j * n + x] = cd(v, 0.0);
+          Qi[(size_t)x * n + j] = cd(2.0 * v / (n + 1), 0.0);
+        }
+        mux[j] = kcx + 2.0 * st.kxl * std::cos(PI * (j + 1) / (n + 1));
+      }
+    }
+    pd_status s1 = upload_cplx(p, &p->Qf, Qf, p->fp64);
+    if (s1 == PD_OK) s1 = upload_cplx(p, &p->Qi, Qi, p->fp64);
+    if (s1 == PD_OK) s1 = upload_cplx(p, &p->mu, mux, p->fp64);
+    if (s1 != PD_OK) { free_plan(p); return s1; }
+    if (sp->dim == 2) {
+      p->tri_n = p->sp.ny; p->tri_stride = sp->nx;
+      p->tri_cl = st.kyl; p->tri_cd = kcy; p->tri_cu = st.kyu;
+    } else {
+      p->tri_n = 1; p->tri_stride = sp->nx;
+      p->tri_cl = 0; p->tri_cd = 0; p->tri_cu = 0;
+    }
+  } else {
+    p->xform = false;
+    p->J = 1;
+    p->tri_n = sp->nx; p->tri_stride = 1;
+    p->tri_cl = st.kxl; p->tri_cd = kcx; p->tri_cu = st.kxu;
+  }
+
+  // Lemma 1 eigenvalues (half spectrum) and the singularity check
+  std::vector<cd> lam((size_t)2 * p->nh);
+  const double PI = 3.14159265358979323846;
+  const double ar = std::pow(alpha, 1.0 / nt);
+  for (int k = 0; k < p->nh; ++k) {
+    const double th = -2.0 * PI * k / nt;
+    const cd w = ar * cd(std::cos(th), std::sin(th));
+    cd l1 = 0, l2 = 0, wm = 1;
+    // only the first min(band+1, Nt) entries of the first column exist
+    for (int m = 0; m <= tb.band && m < nt; ++m) {
+      l1 += tb.c1[m] * wm;
+      l2 += tb.c2[m] * wm;
+      wm *= w;
+    }
+    lam[2 * k] = l1;
+    lam[2 * k + 1] = l2;
+  }
+  if (alpha == 1.0) {
+    // eigenvalues of the tridiagonal direction: cd + 2 sqrt(cl cu) cos(pi i/(n+1))
+    std::vector<cd> mut;
+    const int n = p->tri_n;
+    for (int i = 1; i <= n; ++i)
+      mut.push_back(p->tri_cd + 2.0 * std::sqrt(cd(p->tri_cl * p->tri_cu, 0.0)) * std::cos(PI * i / (n + 1)));
+    if (p->xform && n == 1) mut.assign(1, cd(0.0, 0.0));
+    const std::vector<cd> mx = p->xform ? mux : std::vector<cd>(1, cd(0.0, 0.0));
+    for (int k = 0; k < p->nh; ++k)
+      for (const cd& a : mx)
+        for (const cd& b : mut) {
+          const cd z = lam[2 * k] + lam[2 * k + 1] * (a + b);
+          const double sc = std::abs(lam[2 * k]) + std::abs(lam[2 * k + 1]) * std::abs(a + b) + 1e-300;
+          if (std::abs(z) <= 1e-12 * sc) {
+            free_plan(p);
+            return PD_ERR_ARG;
+          }
+        }
+  }
+
+  std::vector<double> gam(nt), igam(nt), igs(nt);
+  for (int n = 0; n < nt; ++n) {
+    gam[n] = std::pow(alpha, (double)n / nt);
+    igam[n] = std::pow(alpha, -(double)n / nt) / nt;
+    igs[n] = igam[n] / p->s_scale;
+  }
+  std::vector<cd> tw(nt);
+  for (int m = 0; m < nt; ++m) {
+    const double th = -2.0 * PI * m / nt;
+    tw[m] = cd(std::cos(th), std::sin(th));
+  }
+  pd_status s2 = upload_cplx(p, &p->lam, lam, p->fp64);
+  if (s2 == PD_OK) s2 = upload_real(p, &p->gam, gam, p->fp64);
+  if (s2 == PD_OK) s2 = upload_real(p, &p->igam, igam, p->fp64);
+  if (s2 == PD_OK) s2 = upload_real(p, &p->igam_s, igs, p->fp64);
+  if (s2 == PD_OK) s2 = upload_cplx(p, &p->tw, tw, p->fp64);
+  const size_t specb = (size_t)p->nh * S * cbytes(p);
+  if (s2 == PD_OK) s2 = dalloc(p, &p->spec, specb);
+  if (s2 == PD_OK && p->xform) s2 = dalloc(p, &p->spec2, specb);
+  if (s2 == PD_OK && !p->fp64) s2 = dalloc(p, (void**)&p->Udf, NS(p) * sizeof(float2));
+  if (s2 == PD_OK && !p->fp64) s2 = dalloc(p, (void**)&p->Bdf, NS(p) * sizeof(float2));
+  if (s2 == PD_OK) s2 = dalloc(p, (void**)&p->dsc, NSC * sizeof(double));
+  if (s2 == PD_OK) s2 = dalloc(p, (void**)&p->dflag, sizeof(int));
+  if (s2 == PD_OK) {
+    cudaError_t e = cudaMallocHost((void**)&p->hsc, NSC * sizeof(double));
+    if (e != cudaSuccess) s2 = fail_cuda(p, e, "cudaMallocHost");
+  }
+  if (s2 != PD_OK) {
+    free_plan(p);
+    return s2;
+  }
+  *out = p;
+  return PD_OK;
+}
+
+pd_status pd_plan_destroy(pd_plan* plan) {
+  if (!plan) return PD_ERR_ARG;
+  if (plan->stream) cudaStreamSynchronize(plan->stream);
+  else cudaDeviceSynchronize();
+  free_plan(plan);
+  return PD_OK;
+}
+
+pd_status pd_plan_workspace(const pd_plan* plan, unsigned long long* bytes) {
+  if (!plan || !bytes) return PD_ERR_ARG;
+  *bytes = plan->bytes + (plan->adj ? plan->adj->bytes : 0);
+  return PD_OK;
+}
+
+pd_status pd_apply_precond(pd_plan* p, const double* r, double* z) {
+  if (!p || !r || !z) return set_err(p, PD_ERR_ARG, "null argument");
+  return precond_into(p, r, z);
+}
+
+pd_status pd_residual(pd_plan* p, const double* b, const double* u, double* r) {
+  if (!p || !b || !u || !r) return set_err(p, PD_ERR_ARG, "null argument");
+  CU(launch_apply_A(p->st, p->tb, p->nt, u, b, r, nullptr, 0, p->stream));
+  return PD_OK;
+}
+
+pd_status pd_apply_A(pd_plan* p, const double* u, double* y) {
+  if (!p || !u || !y) return set_err(p, PD_ERR_ARG, "null argument");
+  CU(launch_apply_A(p->st, p->tb, p->nt, u, nullptr, y, nullptr, 0, p->stream));
+  return PD_OK;
+}
+
+pd_status pd_apply_AT(pd_plan* p, const double* u, double* y) {
+  if (!p || !u || !y) return set_err(p, PD_ERR_ARG, "null argument");
+  CU(launch_apply_A(p->st, p->tb, p->nt, u, nullptr, y, nullptr, 1, p->stream));
+  return PD_OK;
+}
+
+pd_status pd_build_rhs(pd_plan* p, const double* u0, const double* u1, const double* f,
+                       double* b) {
+  if (!p || !u0 || !b) return set_err(p, PD_ERR_ARG, "null argument");
+  LK(launch_build_rhs(p->st, p->tb, p->scheme, p->nt, p->dt, u0, u1, f, b, p->stream));
+  return PD_OK;
+}
+
+pd_status pd_solve(pd_plan* p, const double* b, double* u, int mode, double tol, int maxit,
+                   int restart, int* iters, double* relres) {
+  return solve_any(p, b, u, mode, tol, maxit, restart, iters, relres);
+}
+
+pd_status pd_solve_host(pd_plan* p, const double* b_host, double* u_host, int mode, double tol,
+                        int maxit, int restart, int* iters, double* relres) {
+  if (!p || !b_host || !u_host) return set_err(p, PD_ERR_ARG, "null argument");
+  const size_t bytes = NS(p) * sizeof(double);
+  if (!p->w64a) CHK(dalloc(p, (void**)&p->w64a, bytes));
+  if (!p->w64b) CHK(dalloc(p, (void**)&p->w64b, bytes));
+  CU(cudaMemcpyAsync(p->w64a, b_host, bytes, cudaMemcpyHostToDevice, p->stream));
+  CU(cudaMemcpyAsync(p->w64b, u_host, bytes, cudaMemcpyHostToDevice, p->stream));
+  pd_status st = solve_any(p, p->w64a, p->w64b, mode, tol, maxit, restart, iters, relres);
+  if (st != PD_OK && st != PD_ERR_NOT_CONVERGED) return st;
+  CU(cudaMemcpyAsync(u_host, p->w64b, bytes, cudaMemcpyDeviceToHost, p->stream));
+  CU(cudaStreamSynchronize(p->stream));
+  return st;
+}
+
+pd_status pd_adjoint_solve(pd_plan* p, const double* g, double* lam, int mode, double tol,
+                           int maxit, int restart, int* iters, double* relres) {
+  if (!p || !g || !lam) return set_err(p, PD_ERR_ARG, "null argument");
+  if (!p->adj) {
+    pd_space sp2 = p->sp;
+    sp2.ax = -sp2.ax;  // centred advection: K^T is K with the velocity reversed
+    sp2.ay = -sp2.ay;
+    pd_status s = pd_plan_create(&sp2, p->nt, p->dt, p->alpha, p->scheme, p->theta,
+                                 p->precision, (void*)p->stream, &p->adj);
+    if (s != PD_OK) return set_err(p, s, "creating the adjoint plan failed");
+  }
+  const size_t bytes = NS(p) * sizeof(double);
+  if (!p->w64a) CHK(dalloc(p, (void**)&p->w64a, bytes));
+  if (!p->w64b) CHK(dalloc(p, (void**)&p->w64b, bytes));
+  LK(launch_flip_time(g, p->w64a, p->nt, p->S, p->stream));
+  LK(launch_flip_time(lam, p->w64b, p->nt, p->S, p->stream));
+  pd_status st = solve_any(p->adj, p->w64a, p->w64b, mode, tol, maxit, restart, iters, relres);
+  if (st != PD_OK && st != PD_ERR_NOT_CONVERGED) {
+    snprintf(p->msg, sizeof(p->msg), "adjoint: %.200s", p->adj->msg);
+    return st;
+  }
+  LK(launch_flip_time(p->w64b, lam, p->nt, p->S, p->stream));
+  CU(cudaStreamSynchronize(p->stream));
+  return st;
+}
+
+}  // extern "C"

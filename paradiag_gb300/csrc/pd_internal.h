@@ -1,0 +1,112 @@
+// Internal definitions shared by the host API and the kernel launchers.
+#pragma once
+#include <cuda_runtime.h>
+#include <cstddef>
+#include <cstdint>
+#include "../../include/paradiag.h"
+#include "pd_common.cuh"
+
+// Double-float constant (value = hi + lo) prepared on the host.
+struct dfc { float hi, lo; };
+static inline dfc dfc_from(double v) {
+  dfc c; c.hi = (float)v; c.lo = (float)(v - (double)c.hi); return c;
+}
+
+// Spatial operator K of the all-at-once system (M = I), constant coefficients:
+// K u(s) = kc u(s) + kxl u(x-1) + kxu u(x+1) + kyl u(y-1) + kyu u(y+1).
+struct Stencil {
+  int dim, nx, ny, S, bcx, bcy;
+  double kc, kxl, kxu, kyl, kyu;
+};
+
+// Time-band coefficients: (A u)_n = sum_{m<=band} c1[m] U_{n-m} + K sum_m c2[m] U_{n-m}.
+struct TimeBand {
+  int band;          // 1 (theta-method) or 2 (leap-frog)
+  double c1[3], c2[3];
+};
+
+// Arguments of the forward time kernel (K1).
+struct FwdArgs {
+  int N, logN, nh, S, TX;
+  Stencil st;
+  TimeBand tb;
+  int mode;                       // FWD_STANDALONE or FWD_RESIDUAL
+  const double* r64;              // standalone input r (FP64, [N][S])
+  const float2* Udf;              // mixed residual: iterate as double-float [N][S]
+  const float2* Bdf;              // mixed residual: s*b as double-float [N][S]
+  const double* U64;              // FP64 residual: iterate
+  const double* B64;              // FP64 residual: b
+  dfc kap[5];                     // mixed: s*K coefficients (c, xl, xu, yl, yu)
+  dfc e2[3];                      // mixed: c2[m]
+  double rscale2;                 // mixed: 1/s^2 (norm of r' = s r)
+  const void* gam;                // gamma_n (float or double)
+  const void* tw;                 // e^{-2 pi i m / N}, m < N (float2 or double2)
+  void* out;                      // half spectrum [nh][S] (float2 or double2)
+  double* norm2;                  // += ||r||_2^2 (may be null)
+  int flip;                       // read the input time-reversed (adjoint)
+};
+
+// Arguments of the inverse time kernel (K3).
+struct InvArgs {
+  int N, logN, nh, S, TX;
+  int mode;                       // INV_UPDATE_DF, INV_OUT64, INV_UPDATE64
+  const void* in;                 // half spectrum [nh][S]
+  const void* igam;               // gamma_n^{-1} / N (float or double)
+  const void* tw;
+  float2* Udf;                    // mixed: iterate (double-float), updated in place
+  double* out64;                  // FP64 output (z) or FP64 iterate (updated)
+  int* flag;                      // set to 1 on a non-finite value (may be null)
+  int flip;                       // write the output time-reversed (adjoint)
+};
+
+enum { FWD_STANDALONE = 0, FWD_RESIDUAL = 1 };
+enum { INV_UPDATE_DF = 0, INV_OUT64 = 1, INV_UPDATE64 = 2 };
+
+// Arguments of the batched shifted tridiagonal solve (K2, step (b)).
+// System q = k*J + j (k < nh time frequencies, j < J spatial modes) of length n:
+//   l z_{i-1} + d z_i + u z_{i+1} = s_i, l = lam2_k cl, d = lam1_k + lam2_k (cd + mu_j),
+//   u = lam2_k cu; element i lives at base + k*S + j + i*stride.
+struct TriArgs {
+  int nh, J, n, S, stride;
+  double cl, cd, cu;
+  const void* lam;                // [nh] complex pairs (lam1, lam2) as 2 complex each
+  const void* mu;                 // [J] complex spatial eigenvalues (or null: 0)
+  void* data;                     // in: right-hand sides, out: solutions
+  int* flag;
+};
+
+// Arguments of the dense x-eigentransform (2D, step (a') / (c')): along x, for
+// every row of the half spectrum: out[row][j] = sum_x Q[j][x] in[row][x].
+struct XformArgs {
+  int rows, nx;
+  const void* Q;                  // [nx][nx] complex
+  const void* in;
+  void* out;
+};
+
+// Launchers (return a cudaError_t).
+cudaError_t launch_time_fwd(const FwdArgs& a, bool fp64, cudaStream_t st);
+cudaError_t launch_time_inv(const InvArgs& a, bool fp64, cudaStream_t st);
+cudaError_t launch_tridiag(const TriArgs& a, bool fp64, cudaStream_t st);
+cudaError_t launch_xform(const XformArgs& a, bool fp64, cudaStream_t st);
+
+// Auxiliary kernels (pd_ops.cu)
+cudaError_t launch_apply_A(const Stencil& st, const TimeBand& tb, int N, const double* u,
+                           const double* b, double* y, double* norm2, int transpose,
+                           cudaStream_t s);
+cudaError_t launch_build_rhs(const Stencil& st, const TimeBand& tb, int scheme, int N, double dt,
+                             const double* u0, const double* u1, const double* f, double* b,
+                             cudaStream_t s);
+cudaError_t launch_to_df(const double* x, double scale, float2* y, size_t n, cudaStream_t s);
+cudaError_t launch_from_df(const float2* x, double* y, size_t n, cudaStream_t s);
+cudaError_t launch_norm2(const double* x, size_t n, double* out, cudaStream_t s);
+cudaError_t launch_flip_time(const double* x, double* y, int N, int S, cudaStream_t s);
+cudaError_t launch_dots(const double* V, int nv, size_t n, const double* w, double* h,
+                        cudaStream_t s);
+cudaError_t launch_gemv_sub(const double* V, int nv, size_t n, const double* h, double* w,
+                            cudaStream_t s);
+cudaError_t launch_axpby(double a, const double* x, double b, double* y, size_t n,
+                         cudaStream_t s);
+cudaError_t launch_scale_copy(double a, const double* x, double* y, size_t n, cudaStream_t s);
+cudaError_t launch_combine(const double* Z, int nz, size_t n, const double* y, double* u,
+                           cudaStream_t s);

@@ -1,0 +1,445 @@
+// Time-axis kernels of the ParaDiag-II preconditioner (steps (a) and (c) of
+// eq. 1.3 / eq. 2.12):
+//   K1  r -> Gamma_alpha r -> FFT along t (half spectrum of a real signal),
+//       optionally fused with the all-at-once residual r = b - A u (eq. 5.1);
+//   K3  inverse FFT along t -> Gamma_alpha^{-1}/Nt -> write z or update u += z.
+// One block owns a tile of TX consecutive spatial columns over all Nt time
+// levels.  Two real columns are packed into one complex column (even x -> real,
+// odd x -> imaginary part), transformed by a shared-memory Stockham FFT
+// (radix 4 with one radix-2 pass when log2 Nt is odd), and separated with
+// A_k = (Z_k + conj Z_{N-k})/2, B_k = (Z_k - conj Z_{N-k})/(2i).
+// The transform convention is the forward DFT with exp(-2 pi i k n / Nt); the
+// eigenvalues used in step (b) follow the same convention (see pd_api.cu).
+#include "pd_internal.h"
+
+namespace {
+
+constexpr int TT = 256;  // threads per block
+
+template <typename C, bool INV>
+PD_D C twid(const C* tw, int idx) {
+  C w = tw[idx];
+  if (INV) w.y = -w.y;
+  return w;
+}
+
+// in-register DFT of size R with the exp(-+2 pi i / R) root
+template <typename C, bool INV, int R>
+PD_D void dft_r(C* v) {
+  if constexpr (R == 2) {
+    C a = cadd(v[0], v[1]), b = csub(v[0], v[1]);
+    v[0] = a; v[1] = b;
+  } else {
+    C s02 = cadd(v[0], v[2]), d02 = csub(v[0], v[2]);
+    C s13 = cadd(v[1], v[3]), d13 = csub(v[1], v[3]);
+    C jd13 = INV ? cmul_pi(d13) : cmul_mi(d13);  // (-+i)(x1 - x3)
+    v[0] = cadd(s02, s13);
+    v[1] = cadd(d02, jd13);
+    v[2] = csub(s02, s13);
+    v[3] = csub(d02, jd13);
+  }
+}
+
+// One Stockham pass of radix R over TXc interleaved columns stored [N][TXc].
+// Every butterfly is read into registers before the barrier and written after
+// it, so the pass runs in place.
+template <typename C, bool INV, int R, int BPT>
+PD_D void fft_pass(C* sm, int N, int lgTXc, int Ns, const C* tw) {
+  const int TXc = 1 << lgTXc;
+  const int nb = (N / R) << lgTXc;
+  const int step = N / (Ns * R);
+  C v[BPT][R];
+  int dst[BPT];
+#pragma unroll
+  for (int t = 0; t < BPT; ++t) {
+    const int b = threadIdx.x + t * TT;
+    dst[t] = -1;
+    if (b < nb) {
+      const int c = b & (TXc - 1), j = b >> lgTXc;
+      const int q = j % Ns;
+#pragma unroll
+      for (int r = 0; r < R; ++r) {
+        C x = sm[((j + r * (N / R)) << lgTXc) + c];
+        if (r > 0) x = cmul(x, twid<C, INV>(tw, q * r * step));
+        v[t][r] = x;
+      }
+      dft_r<C, INV, R>(v[t]);
+      dst[t] = (((j / Ns) * Ns * R + q) << lgTXc) + c;
+    }
+  }
+  __syncthreads();
+#pragma unroll
+  for (int t = 0; t < BPT; ++t) {
+    if (dst[t] >= 0) {
+#pragma unroll
+      for (int r = 0; r < R; ++r) sm[dst[t] + ((r * Ns) << lgTXc)] = v[t][r];
+    }
+  }
+  __syncthreads();
+}
+
+// Full complex FFT of length N (power of two) on TXc columns; EPT is the
+// maximum number of complex elements per thread (N * TXc <= EPT * TT).
+template <typename C, bool INV, int EPT>
+PD_D void fft_tile(C* sm, int N, int logN, int lgTXc, const C* tw) {
+  int Ns = 1;
+  if (logN & 1) {
+    fft_pass<C, INV, 2, EPT / 2>(sm, N, lgTXc, Ns, tw);
+    Ns = 2;
+  }
+  for (int p = 0; p < logN / 2; ++p) {
+    fft_pass<C, INV, 4, EPT / 4>(sm, N, lgTXc, Ns, tw);
+    Ns *= 4;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Spatial stencil of one time row at this thread's column, x-neighbours from
+// the lanes of the same TX-wide segment (warp shuffles), y-neighbours and
+// segment edges from global memory.
+// ---------------------------------------------------------------------------
+struct ColGeom {
+  int s;          // spatial index (may be >= S for padding columns)
+  bool valid;
+  int left;       // 0: zero, 1: from lane - 1, 2: load s_left
+  int right;
+  int s_left, s_right;
+  bool down, up;  // y neighbours present (2D)
+};
+
+PD_D ColGeom col_geom(const Stencil& st, int s, int lane_in_seg, int TX) {
+  ColGeom g;
+  g.s = s;
+  g.valid = s < st.S;
+  g.left = g.right = 0;
+  g.s_left = g.s_right = 0;
+  g.down = g.up = false;
+  if (!g.valid) return g;
+  const int xg = s % st.nx;
+  const int y = s / st.nx;
+  if (xg > 0) {
+    g.left = lane_in_seg > 0 ? 1 : 2;
+    g.s_left = s - 1;
+  } else if (st.bcx == PD_PERIODIC && st.nx > 1) {
+    g.left = 2;
+    g.s_left = s + st.nx - 1;
+  }
+  if (xg < st.nx - 1) {
+    g.right = lane_in_seg < TX - 1 ? 1 : 2;
+    g.s_right = s + 1;
+  } else if (st.bcx == PD_PERIODIC && st.nx > 1) {
+    g.right = 2;
+    g.s_right = s - (st.nx - 1);
+  }
+  if (st.dim == 2) {
+    g.down = y > 0;
+    g.up = y < st.ny - 1;
+  }
+  return g;
+}
+
+struct Acc {  // compensated sum: value = s + e
+  float s, e;
+};
+PD_D void acc_add(Acc& A, float h, float l) {
+  const float t = __fadd_rn(A.s, h);
+  const float bb = __fsub_rn(t, A.s);
+  const float err = __fadd_rn(__fsub_rn(A.s, __fsub_rn(t, bb)), __fsub_rn(h, bb));
+  A.s = t;
+  A.e += err + l;
+}
+// A += k * u for a double-float constant k and a double-float value u
+PD_D void acc_add_prod(Acc& A, dfc k, float uh, float ul) {
+  const float p = __fmul_rn(uh, k.hi);
+  float pe = __fmaf_rn(uh, k.hi, -p);
+  pe = __fmaf_rn(uh, k.lo, pe);
+  pe = __fmaf_rn(ul, k.hi, pe);
+  acc_add(A, p, pe);
+}
+PD_D df acc_val(const Acc& A) { return fast_two_sum(A.s, A.e); }
+
+// (U(s), (sK U)(s)) of row n in double-float; zeros for n outside [0, N).
+// Must be executed by all lanes of the warp (uniform control flow).
+PD_D void stencil_row_df(const FwdArgs& a, const ColGeom& g, int n, int TX, df& Uc, df& KU) {
+  const bool inrow = n >= 0 && n < a.N;
+  const size_t base = (size_t)(inrow ? n : 0) * a.S;
+  float2 c = make_float2(0.f, 0.f);
+  if (inrow && g.valid) c = __ldg(&a.Udf[base + g.s]);
+  const unsigned FULL = 0xffffffffu;
+  const float lh = __shfl_up_sync(FULL, c.x, 1, TX);
+  const float ll = __shfl_up_sync(FULL, c.y, 1, TX);
+  const float rh = __shfl_down_sync(FULL, c.x, 1, TX);
+  const float rl = __shfl_down_sync(FULL, c.y, 1, TX);
+  Uc = df_make(c.x, c.y);
+  Acc A = {0.f, 0.f};
+  if (inrow && g.valid) {
+    acc_add_prod(A, a.kap[0], c.x, c.y);
+    float2 v;
+    if (g.left == 1) acc_add_prod(A, a.kap[1], lh, ll);
+    else if (g.left == 2) { v = __ldg(&a.Udf[base + g.s_left]); acc_add_prod(A, a.kap[1], v.x, v.y); }
+    if (g.right == 1) acc_add_prod(A, a.kap[2], rh, rl);
+    else if (g.right == 2) { v = __ldg(&a.Udf[base + g.s_right]); acc_add_prod(A, a.kap[2], v.x, v.y); }
+    if (g.down) { v = __ldg(&a.Udf[base + g.s - a.st.nx]); acc_add_prod(A, a.kap[3], v.x, v.y); }
+    if (g.up) { v = __ldg(&a.Udf[base + g.s + a.st.nx]); acc_add_prod(A, a.kap[4], v.x, v.y); }
+  }
+  KU = acc_val(A);
+}
+
+PD_D void stencil_row_64(const FwdArgs& a, const ColGeom& g, int n, int TX, double& Uc,
+                         double& KU) {
+  const bool inrow = n >= 0 && n < a.N;
+  const size_t base = (size_t)(inrow ? n : 0) * a.S;
+  double c = 0.0;
+  if (inrow && g.valid) c = __ldg(&a.U64[base + g.s]);
+  const unsigned FULL = 0xffffffffu;
+  const double lv = __shfl_up_sync(FULL, c, 1, TX);
+  const double rv = __shfl_down_sync(FULL, c, 1, TX);
+  Uc = c;
+  double k = 0.0;
+  if (inrow && g.valid) {
+    const Stencil& st = a.st;
+    k = st.kc * c;
+    if (g.left == 1) k = fma(st.kxl, lv, k);
+    else if (g.left == 2) k = fma(st.kxl, __ldg(&a.U64[base + g.s_left]), k);
+    if (g.right == 1) k = fma(st.kxu, rv, k);
+    else if (g.right == 2) k = fma(st.kxu, __ldg(&a.U64[base + g.s_right]), k);
+    if (g.down) k = fma(st.kyl, __ldg(&a.U64[base + g.s - st.nx]), k);
+    if (g.up) k = fma(st.kyu, __ldg(&a.U64[base + g.s + st.nx]), k);
+  }
+  KU = k;
+}
+
+template <typename T>
+PD_D T block_sum(T v, T* red) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  __syncthreads();
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+  __syncthreads();
+  T s = 0;
+  if (threadIdx.x == 0)
+    for (int w = 0; w < TT / 32; ++w) s += red[w];
+  return s;
+}
+
+// ---------------------------------------------------------------------------
+// K1: residual (optional) + Gamma scaling + forward real FFT along t.
+// PREC 0: mixed (double-float residual, FP32 transform); PREC 1: FP64.
+// ---------------------------------------------------------------------------
+template <int PREC, int BAND>
+__global__ void __launch_bounds__(TT) k_time_fwd(FwdArgs a) {
+  using R = typename std::conditional<PREC == 0, float, double>::type;
+  using C = cplx_t<R>;
+  constexpr int EPT = PREC == 0 ? 32 : 16;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  C* sm = reinterpret_cast<C*>(smraw);
+  R* smr = reinterpret_cast<R*>(smraw);
+  __shared__ double red[TT / 32];
+
+  const int TX = a.TX, N = a.N, S = a.S;
+  const int lgTX = ilog2(TX);
+  const int x0 = blockIdx.x * TX;
+  const int x = threadIdx.x & (TX - 1);
+  const int chunk = threadIdx.x >> lgTX;
+  const int nchunks = TT / TX;
+  const int rpc = (N + nchunks - 1) / nchunks;
+  const int n_beg = chunk * rpc;
+  const int s = x0 + x;
+  const R* gam = reinterpret_cast<const R*>(a.gam);
+  double nrm = 0.0;
+
+  if (a.mode == FWD_STANDALONE) {
+    for (int i = 0; i < rpc; ++i) {
+      const int n = n_beg + i;
+      if (n >= N) break;
+      R v = 0;
+      if (s < S) {
+        const double rv = a.r64[(size_t)n * S + s];
+        if constexpr (PREC == 0) {
+          const df r = df_from_double(rv);
+          const float g = gam[n];
+          v = fmaf(r.hi, g, r.lo * g);
+        } else {
+          v = gam[n] * rv;
+        }
+      }
+      smr[n * TX + x] = v;
+    }
+  } else {
+    const ColGeom g = col_geom(a.st, s, x, TX);
+    if constexpr (PREC == 0) {
+      df U1 = df_make(0.f, 0.f), U2 = U1, K1 = U1, K2 = U1, U0, K0;
+      if (BAND == 2) stencil_row_df(a, g, n_beg - 2, TX, U2, K2);
+      stencil_row_df(a, g, n_beg - 1, TX, U1, K1);
+      float part = 0.f;
+      for (int i = 0; i < rpc; ++i) {
+        const int n = n_beg + i;
+        stencil_row_df(a, g, n, TX, U0, K0);  // uniform across the warp
+        if (n < N) {
+          float v = 0.f;
+          if (g.valid) {
+            const float2 bb = __ldg(&a.Bdf[(size_t)n * S + s]);
+            Acc A = {bb.x, bb.y};
+            acc_add(A, -U0.hi, -U0.lo);
+            if (BAND == 1) {
+              if (n >= 1) acc_add(A, U1.hi, U1.lo);
+            } else {
+              if (n >= 1) acc_add(A, 2.f * U1.hi, 2.f * U1.lo);
+              if (n >= 2) acc_add(A, -U2.hi, -U2.lo);
+            }
+            dfc m0 = a.e2[0];
+            m0.hi = -m0.hi; m0.lo = -m0.lo;
+            acc_add_prod(A, m0, K0.hi, K0.lo);
+            if (BAND == 1) {
+              if (n >= 1) { dfc m1 = a.e2[1]; m1.hi = -m1.hi; m1.lo = -m1.lo; acc_add_prod(A, m1, K1.hi, K1.lo); }
+            } else {
+              if (n >= 2) { dfc m2 = a.e2[2]; m2.hi = -m2.hi; m2.lo = -m2.lo; acc_add_prod(A, m2, K2.hi, K2.lo); }
+            }
+            const df r = acc_val(A);
+            part = fmaf(r.hi, r.hi, part);
+            const float gm = gam[n];
+            v = fmaf(r.hi, gm, r.lo * gm);
+          }
+          smr[n * TX + x] = v;
+        }
+        U2 = U1; K2 = K1; U1 = U0; K1 = K0;
+      }
+      nrm = (double)part * a.rscale2;
+    } else {
+      double U1 = 0, U2 = 0, K1 = 0, K2 = 0, U0, K0;
+      const TimeBand& tb = a.tb;
+      if (BAND == 2) stencil_row_64(a, g, n_beg - 2, TX, U2, K2);
+      stencil_row_64(a, g, n_beg - 1, TX, U1, K1);
+      for (int i = 0; i < rpc; ++i) {
+        const int n = n_beg + i;
+        stencil_row_64(a, g, n, TX, U0, K0);
+        if (n < N) {
+          double v = 0.0;
+          if (g.valid) {
+            double r = __ldg(&a.B64[(size_t)n * S + s]);
+            r = fma(-tb.c1[0], U0, r);
+            r = fma(-tb.c2[0], K0, r);
+            if (n >= 1) { r = fma(-tb.c1[1], U1, r); r = fma(-tb.c2[1], K1, r); }
+            if (BAND == 2 && n >= 2) { r = fma(-tb.c1[2], U2, r); r = fma(-tb.c2[2], K2, r); }
+            nrm = fma(r, r, nrm);
+            v = gam[n] * r;
+          }
+          smr[n * TX + x] = v;
+        }
+        U2 = U1; K2 = K1; U1 = U0; K1 = K0;
+      }
+    }
+  }
+  if (a.norm2 != nullptr) {
+    const double bs = block_sum<double>(nrm, red);
+    if (threadIdx.x == 0) atomicAdd(a.norm2, bs);
+  }
+  __syncthreads();
+
+  const int lgTXc = lgTX - 1;
+  const int TXc = TX / 2;
+  fft_tile<C, false, EPT>(sm, N, a.logN, lgTXc, reinterpret_cast<const C*>(a.tw));
+
+  C* out = reinterpret_cast<C*>(a.out);
+  const R half = (R)0.5;
+  for (int item = threadIdx.x; item < a.nh * TXc; item += TT) {
+    const int c = item & (TXc - 1), k = item >> lgTXc;
+    const C Zk = sm[(k << lgTXc) + c];
+    const C Zm = cconj(sm[(((N - k) & (N - 1)) << lgTXc) + c]);
+    const C A = cscale(cadd(Zk, Zm), half);
+    const C B = cscale(cmul_mi(csub(Zk, Zm)), half);
+    const int sa = x0 + 2 * c;
+    if (sa < S) out[(size_t)k * S + sa] = A;
+    if (sa + 1 < S) out[(size_t)k * S + sa + 1] = B;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// K3: inverse real FFT along t + Gamma^{-1}/Nt + write or update.
+// ---------------------------------------------------------------------------
+template <int PREC>
+__global__ void __launch_bounds__(TT) k_time_inv(InvArgs a) {
+  using R = typename std::conditional<PREC == 0, float, double>::type;
+  using C = cplx_t<R>;
+  constexpr int EPT = PREC == 0 ? 32 : 16;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  C* sm = reinterpret_cast<C*>(smraw);
+  R* smr = reinterpret_cast<R*>(smraw);
+
+  const int TX = a.TX, N = a.N, S = a.S;
+  const int lgTX = ilog2(TX), lgTXc = lgTX - 1, TXc = TX / 2;
+  const int x0 = blockIdx.x * TX;
+  const C* in = reinterpret_cast<const C*>(a.in);
+  for (int item = threadIdx.x; item < a.nh * TXc; item += TT) {
+    const int c = item & (TXc - 1), k = item >> lgTXc;
+    const int sa = x0 + 2 * c;
+    C A = czero<C>(), B = czero<C>();
+    if (sa < S) A = in[(size_t)k * S + sa];
+    if (sa + 1 < S) B = in[(size_t)k * S + sa + 1];
+    if (k == 0 || 2 * k == N) { A.y = 0; B.y = 0; }
+    sm[(k << lgTXc) + c] = mk(A.x - B.y, A.y + B.x);            // A + i B
+    if (k > 0 && 2 * k < N)
+      sm[((N - k) << lgTXc) + c] = mk(A.x + B.y, B.x - A.y);    // conj(A) + i conj(B)
+  }
+  __syncthreads();
+  fft_tile<C, true, EPT>(sm, N, a.logN, lgTXc, reinterpret_cast<const C*>(a.tw));
+
+  const R* ig = reinterpret_cast<const R*>(a.igam);
+  bool bad = false;
+  for (int e = threadIdx.x; e < N * TX; e += TT) {
+    const int n = e >> lgTX, x = e & (TX - 1);
+    const int s = x0 + x;
+    if (s >= S) continue;
+    const R dz = smr[e] * ig[n];
+    const size_t idx = (size_t)n * S + s;
+    if constexpr (PREC == 0) {
+      if (!isfinite(dz)) bad = true;
+      if (a.mode == INV_UPDATE_DF) {
+        const float2 u = a.Udf[idx];
+        df t = two_sum(u.x, dz);
+        t = fast_two_sum(t.hi, t.lo + u.y);
+        a.Udf[idx] = make_float2(t.hi, t.lo);
+      } else {
+        a.out64[idx] = double_from_float(dz);
+      }
+    } else {
+      if (!isfinite(dz)) bad = true;
+      if (a.mode == INV_UPDATE64) a.out64[idx] += dz;
+      else a.out64[idx] = dz;
+    }
+  }
+  if (bad && a.flag != nullptr) atomicExch(a.flag, 1);
+}
+
+template <int PREC, int BAND>
+cudaError_t launch_fwd_t(const FwdArgs& a, cudaStream_t st) {
+  const size_t smem = (size_t)a.N * (a.TX / 2) * (PREC == 0 ? sizeof(float2) : sizeof(double2));
+  auto kern = k_time_fwd<PREC, BAND>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  const int grid = ceil_div(a.S, a.TX);
+  kern<<<grid, TT, smem, st>>>(a);
+  return cudaGetLastError();
+}
+
+template <int PREC>
+cudaError_t launch_inv_t(const InvArgs& a, cudaStream_t st) {
+  const size_t smem = (size_t)a.N * (a.TX / 2) * (PREC == 0 ? sizeof(float2) : sizeof(double2));
+  auto kern = k_time_inv<PREC>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  const int grid = ceil_div(a.S, a.TX);
+  kern<<<grid, TT, smem, st>>>(a);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t launch_time_fwd(const FwdArgs& a, bool fp64, cudaStream_t st) {
+  const bool lf = a.tb.band == 2;
+  if (fp64) return lf ? launch_fwd_t<1, 2>(a, st) : launch_fwd_t<1, 1>(a, st);
+  return lf ? launch_fwd_t<0, 2>(a, st) : launch_fwd_t<0, 1>(a, st);
+}
+
+cudaError_t launch_time_inv(const InvArgs& a, bool fp64, cudaStream_t st) {
+  return fp64 ? launch_inv_t<1>(a, st) : launch_inv_t<0>(a, st);
+}

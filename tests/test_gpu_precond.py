@@ -1,0 +1,88 @@
+"""Parity of z = P_alpha^{-1} r (eq. 1.3) between the CUDA path and the oracle's
+naive Lemma-1 application (dense Fourier matrix, sparse LU per frequency).
+
+Tolerances.  The transform has Cond_2(V) <= 1/alpha (eq. 2.13) and each
+shifted system lambda_1 I + lambda_2 K has a 2-norm condition number kappa_k,
+so a backward-stable evaluation in precision eps gives a relative error of
+order eps * kappa / alpha with kappa = max_k kappa_k (computed here from the
+dense shifted matrices).  FP64 path: tolerance 64 eps64 kappa / alpha (at least
+1e-12).  Mixed path (FP32 transform and solves): 64 eps32 kappa / alpha.
+The invariant P z = r is checked relative to |P| |z| (entrywise absolute
+values), the natural scale of the rounding error of the product.
+"""
+import numpy as np
+import pytest
+
+import workloads as W
+from helpers import EPS32, dev, host, lib_ready, make_plan, relerr
+from oracle import closed_forms as CF
+from oracle import operators as O
+from oracle import paradiag as PD
+
+pytestmark = pytest.mark.gpu
+
+
+def P(dim=1, nx=15, ny=1, nu=0.1, ax=0.0, ay=0.0, bcx=W.DIRICHLET, nt=16, T=1.0,
+      scheme=W.BE, alpha=1e-2):
+    sp = W.Space(dim=dim, nx=nx, ny=ny, nu=nu, ax=ax, ay=ay, bc_x=bcx)
+    return W.Problem(space=sp, nt=nt, dt=T / nt, scheme=scheme, alpha=alpha)
+
+
+CASES = {
+    "1d_be_ade_127x64": P(nx=127, nu=1e-2, ax=1.0, nt=64, alpha=1e-2),
+    "1d_cn_ragged_37x16": P(nx=37, nu=3e-2, ax=0.7, nt=16, scheme=W.CN, alpha=1e-3),
+    "1d_leapfrog_63x32": P(nx=63, nu=1.0, nt=32, T=2.0, scheme=W.LEAPFROG, alpha=0.1),
+    "1d_leapfrog_alpha1": P(nx=31, nu=1.0, nt=16, T=2.0, scheme=W.LEAPFROG, alpha=1.0),
+    "1d_periodic_be_24x8": P(nx=24, nu=1e-2, ax=1.0, bcx=W.PERIODIC, nt=8, alpha=1e-2),
+    "1d_nt1": P(nx=20, nt=1, alpha=0.5),
+    "1d_nt2": P(nx=20, nt=2, scheme=W.CN, alpha=0.05),
+    "1d_nx1": P(nx=1, nt=8),
+    "1d_nx600_multiwarp": P(nx=600, nu=1e-3, ax=1.0, nt=8, alpha=1e-2),
+    "1d_nx1023_multiwarp": P(nx=1023, nu=1.0, nt=16, T=2.0, scheme=W.LEAPFROG, alpha=0.1),
+    "1d_nt512": P(nx=33, nu=0.05, ax=1.0, nt=512, alpha=1e-2),
+    "2d_cn_periodic_x_15x13x16": P(dim=2, nx=15, ny=13, nu=1e-2, ax=1.0, ay=0.5,
+                                    bcx=W.PERIODIC, nt=16, scheme=W.CN, alpha=1e-3),
+    "2d_be_dirichlet_sym_11x9x8": P(dim=2, nx=11, ny=9, nu=1.0, nt=8, alpha=1e-2),
+    "2d_lf_dirichlet_sym_9x7x8": P(dim=2, nx=9, ny=7, nu=1.0, nt=8, T=2.0,
+                                   scheme=W.LEAPFROG, alpha=0.1),
+}
+
+
+@pytest.fixture(scope="module")
+def pd():
+    return lib_ready()
+
+
+def kappa(pb):
+    """max_k cond_2(lambda_1k I + lambda_2k K) over the Lemma 1 eigenvalues."""
+    K = O.stencil(pb.space).toarray()
+    l1, l2 = CF.lemma1_eigenvalues(pb)
+    I = np.eye(K.shape[0])
+    return max(np.linalg.cond(l1[k] * I + l2[k] * K) for k in range(pb.nt // 2 + 1))
+
+
+def abs_product_scale(pb, z):
+    """max of |C1| (x) I + |C2| (x) |K| applied to |z|: the scale of P z."""
+    K = abs(O.stencil(pb.space))
+    C1, C2 = O.circulant_matrices(pb)
+    return np.abs(O.apply_kron(np.abs(C1), np.abs(C2), K, np.abs(z))).max()
+
+
+@pytest.mark.parametrize("name", sorted(CASES))
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_precond_matches_oracle(pd, name, prec):
+    pb = CASES[name]
+    r = W.uniform(hash(name) % 1000 + 11, pb.unknowns, -1.0, 1.0).reshape(pb.nt, -1)
+    zref = PD.precond_apply(pb, r)
+    plan = make_plan(pb, pd.PD_FP64 if prec == "fp64" else pd.PD_MIXED)
+    z = host(plan.apply_precond(dev(r)))
+    kap = kappa(pb)
+    eps = 2.0 ** -53 if prec == "fp64" else EPS32
+    tol = max(64 * eps * kap / pb.alpha, 1e-12)
+    err = relerr(z, zref)
+    assert err <= tol, (name, prec, err, tol, kap)
+    # invariant P z = r, evaluated by the oracle in FP64, relative to |P||z|
+    pz = O.apply_P(pb, z)
+    res = np.abs(pz - r).max() / abs_product_scale(pb, z)
+    assert res <= tol, (res, tol)
+    plan.close()

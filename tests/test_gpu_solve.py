@@ -1,0 +1,112 @@
+"""Parity of the converged all-at-once solution u = A^{-1} b (eq. 5.1 stationary
+iteration and flexible GMRES) with the oracle's sequential time stepping.
+
+Tolerance: 1e-10 relative (2-norm over all space-time unknowns), the accuracy
+target of the mixed-precision and FP64 paths.  The stopping test on the
+residual is 1e-12 or below, and ||u - u*|| <= ||A^{-1}|| ||r||, where the
+time-stepping inverse is bounded for these dissipative / unitary schemes.
+"""
+import numpy as np
+import pytest
+
+import workloads as W
+from helpers import dev, host, lib_ready, make_plan, rel2
+from oracle import operators as O
+from oracle import stepping as S
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def pd():
+    return lib_ready()
+
+
+def _rhs(w):
+    return O.build_rhs(w.problem, w.u0, w.u1, w.f)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_ade1d_full_config_stationary(pd, prec):
+    # 1D advection-diffusion, nx = 127, Nt = 64, BE, alpha = 1e-2, residual 1e-12
+    w = W.ade1d()
+    pb = w.problem
+    b = _rhs(w)
+    uref = S.solve_sequential(pb, b)
+    plan = make_plan(pb, pd.PD_FP64 if prec == "fp64" else pd.PD_MIXED)
+    bd = dev(b)
+    bg = plan.build_rhs(dev(w.u0), None, dev(w.f))
+    assert rel2(host(bg), b) <= 1e-14
+    u, it, rel = plan.solve(bg, tol=1e-12, maxit=30)
+    assert rel <= 1e-12
+    assert rel2(host(u), uref) <= 1e-10, (rel2(host(u), uref), it)
+    if prec == "fp64":
+        assert it <= 3     # per-mode rate ~1e-11: two or three sweeps
+    plan.close()
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+@pytest.mark.parametrize("scheme", [W.BE, W.CN])
+def test_ade2d_small_stationary(pd, prec, scheme):
+    w = W.ade2d(nx=31, ny=29, nt=32, scheme=scheme, alpha=1e-3)
+    pb = w.problem
+    b = _rhs(w)
+    uref = S.solve_sequential(pb, b)
+    plan = make_plan(pb, pd.PD_FP64 if prec == "fp64" else pd.PD_MIXED)
+    u, it, rel = plan.solve(dev(b), tol=1e-12, maxit=30)
+    assert rel2(host(u), uref) <= 1e-10, (rel2(host(u), uref), it, rel)
+    plan.close()
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_wave1d_gmres(pd, prec):
+    w = W.wave1d(nx=255, nt=256, alpha=0.1)
+    pb = w.problem
+    b = _rhs(w)
+    uref = S.solve_sequential(pb, b)
+    plan = make_plan(pb, pd.PD_FP64 if prec == "fp64" else pd.PD_MIXED)
+    u, it, rel = plan.solve(dev(b), mode=pd.PD_GMRES, tol=1e-10, maxit=60, restart=30)
+    assert rel <= 1e-10
+    assert rel2(host(u), uref) <= 1e-9, (rel2(host(u), uref), it)
+    plan.close()
+
+
+def test_solve_host_buffers(pd):
+    import torch
+    w = W.ade1d(nx=63, nt=32)
+    pb = w.problem
+    b = _rhs(w)
+    uref = S.solve_sequential(pb, b)
+    plan = make_plan(pb, pd.PD_MIXED)
+    bh = torch.from_numpy(b.copy()).pin_memory()
+    uh = torch.zeros_like(bh).pin_memory()
+    _, it, rel = plan.solve_host(bh, uh, tol=1e-12, maxit=30)
+    assert rel2(uh.numpy(), uref) <= 1e-10
+    plan.close()
+
+
+def test_not_converged_and_zero_rhs(pd):
+    import torch
+    w = W.ade1d(nx=31, nt=16)
+    pb = w.problem
+    plan = make_plan(pb, pd.PD_MIXED)
+    b = dev(_rhs(w))
+    u, it, rel = plan.solve(b, tol=1e-14, maxit=0, allow_not_converged=True)
+    assert it == 0 and rel > 1e-14
+    with pytest.raises(pd.PDError) as ei:
+        plan.solve(b, tol=1e-30, maxit=1)
+    assert ei.value.status == pd.PD_ERR_NOT_CONVERGED
+    z, it, rel = plan.solve(torch.zeros_like(b), tol=1e-12)
+    assert float(z.abs().max()) == 0.0 and rel == 0.0
+    plan.close()
+
+
+def test_nonfinite_input_is_reported(pd):
+    w = W.ade1d(nx=31, nt=16)
+    plan = make_plan(w.problem, pd.PD_MIXED)
+    b = _rhs(w)
+    b[3, 5] = np.nan
+    with pytest.raises(pd.PDError) as ei:
+        plan.solve(dev(b), tol=1e-12, maxit=5)
+    assert ei.value.status == pd.PD_ERR_NONFINITE
+    plan.close()
