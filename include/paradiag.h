@@ -149,6 +149,35 @@ PD_API pd_status pd_profile_iteration(pd_plan* plan, const double* b, const doub
 /* Number of kernels this plan (and its adjoint plan) has launched so far. */
 PD_API pd_status pd_plan_launches(const pd_plan* plan, unsigned long long* count);
 
+/* Size of the device array used by pd_apply_precond_noalloc (8 MiB). */
+#define PD_NOALLOC_SCRATCH_BYTES (8u << 20)
+
+/* z = P_alpha^{-1} r for a 1D Dirichlet problem (sp->dim == 1, bc_x Dirichlet),
+ * mixed precision, WITHOUT any device allocation.  The paper has no
+ * counterpart: this entry point exists for callers that cannot call
+ * cudaMalloc -- code running while an application's memory pool is frozen,
+ * plug-ins whose host application owns every device allocation, or code in a
+ * region where allocation is not allowed.  Such callers cannot create a plan
+ * (pd_plan_create allocates its tables and workspace).
+ *   Scratch.  The half spectrum and the eigenvalue, Gamma and twiddle tables
+ *             live in one file-scope __device__ array of
+ *             PD_NOALLOC_SCRATCH_BYTES that every GPU loading this library
+ *             holds until the process exits.  Problems needing more (about
+ *             8 (Nt/2+1) nx bytes plus small tables) are rejected with
+ *             PD_ERR_ARG; *scratch_needed (if not NULL) receives the bytes the
+ *             problem needs in every case.
+ *   Set-up.   The first call on a device looks up the array's device address
+ *             (cudaGetSymbolAddress) with that device current; make that first
+ *             call before any stream capture.
+ *   Sharing.  All calls share the one array and leave their data in it; calls
+ *             whose work overlaps on the GPU (other streams or host threads)
+ *             race and must be serialised by the caller.
+ * r, z: [Nt][nx] device FP64 (caller-owned); stream: cudaStream_t.  Work is
+ * enqueued on the stream; the tables are copied from host memory first. */
+PD_API pd_status pd_apply_precond_noalloc(const pd_space* sp, int nt, double dt, double alpha,
+                                          int scheme, double theta, const double* r, double* z,
+                                          void* stream, unsigned long long* scratch_needed);
+
 PD_API const char* pd_status_string(pd_status s);
 PD_API const char* pd_last_error(const pd_plan* plan);
 

@@ -59,6 +59,10 @@ _SIGS = {
     "pd_profile_iteration": (ctypes.c_int, [_P, _P, _P, ctypes.c_int,
                                             ctypes.POINTER(ctypes.c_float)]),
     "pd_plan_launches": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_ulonglong)]),
+    "pd_apply_precond_noalloc": (ctypes.c_int, [ctypes.POINTER(pd_space), ctypes.c_int,
+                                                ctypes.c_double, ctypes.c_double, ctypes.c_int,
+                                                ctypes.c_double, _P, _P, _P,
+                                                ctypes.POINTER(ctypes.c_ulonglong)]),
     "pd_status_string": (ctypes.c_char_p, [ctypes.c_int]),
     "pd_last_error": (ctypes.c_char_p, [_P]),
 }
@@ -128,6 +132,15 @@ def pd_plan_launches(plan):
 
 def pd_apply_precond(plan, r, z):
     return load().pd_apply_precond(plan, r, z)
+
+
+def pd_apply_precond_noalloc(space, nt, dt, alpha, scheme, theta, r, z, stream):
+    """Plan-free, allocation-free P^{-1} r for 1D Dirichlet problems; returns
+    (status, scratch bytes the problem needs)."""
+    need = ctypes.c_ulonglong(0)
+    st = load().pd_apply_precond_noalloc(ctypes.byref(space), nt, dt, alpha, scheme, theta, r, z,
+                                         _P(stream), ctypes.byref(need))
+    return st, need.value
 
 
 def pd_residual(plan, b, u, r):
