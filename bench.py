@@ -36,7 +36,7 @@ KERNELS = ["resid_gamma_fft", "xform_fwd", "tridiag", "xform_inv", "ifft_gamma_u
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=30)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-check", action="store_true", help="skip the oracle error check")
@@ -69,7 +69,7 @@ class ClockSampler:
             self.f = open(self.path, "w")
             self.proc = subprocess.Popen(
                 ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}",
-                 "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.f,
+                 "--format=csv,noheader,nounits", "-lms", "50"], stdout=self.f,
                 stderr=subprocess.DEVNULL)
         except Exception:
             self.proc = None
@@ -234,12 +234,12 @@ def main():
     u = torch.zeros_like(b)
     torch.cuda.synchronize()
 
+    clk = ClockSampler(local)
+    clk.start()
     for _ in range(max(args.warmup, 3)):
         u.zero_()
         _, iters, rel = plan.solve(b, u, tol=TOL, maxit=40)
 
-    clk = ClockSampler(local)
-    clk.start()
     l0 = plan.launches()
     barrier(ws)
     torch.cuda.synchronize()

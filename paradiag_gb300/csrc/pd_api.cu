@@ -33,8 +33,16 @@ struct pd_plan {
   TimeBand tb;
   double s_scale = 1.0;
   cudaStream_t stream = nullptr;
+  // spectrum layout (padded grid lines for x-transformed problems)
+  SpecGeom sg;
   // step (b) layout
   bool xform = false;
+  bool xform_tc = false;          // mixed path: tcgen05 x-transform
+  XformTc xtc_fwd, xtc_inv;
+  void* Gf_hi = nullptr;
+  void* Gf_lo = nullptr;
+  void* Gi_hi = nullptr;
+  void* Gi_lo = nullptr;
   int J = 1, tri_n = 0, tri_stride = 1;
   double tri_cl = 0, tri_cd = 0, tri_cu = 0;
   // device tables
@@ -140,8 +148,10 @@ pd_status upload_real(pd_plan* p, void** dst, const std::vector<double>& v, bool
 
 void free_plan(pd_plan* p) {
   if (!p) return;
-  void* ptrs[] = {p->lam, p->gam, p->igam, p->igam_s, p->tw, p->Qf, p->Qi, p->mu, p->spec,
-                  p->spec2, p->Udf, p->Bdf, p->w64a, p->w64b, p->dsc, p->dflag, p->V, p->Z, p->dh};
+  void* ptrs[] = {p->lam,  p->gam,  p->igam, p->igam_s, p->tw,    p->Qf,    p->Qi,
+                  p->mu,   p->spec, p->spec2, p->Udf,  p->Bdf,   p->w64a,  p->w64b,
+                  p->dsc,  p->dflag, p->V,   p->Z,      p->dh,    p->Gf_hi, p->Gf_lo,
+                  p->Gi_hi, p->Gi_lo};
   for (void* q : ptrs)
     if (q) cudaFree(q);
   if (p->hsc) cudaFreeHost(p->hsc);
@@ -156,6 +166,7 @@ FwdArgs fwd_base(const pd_plan* p) {
   FwdArgs a;
   memset(&a, 0, sizeof(a));
   a.N = p->nt; a.logN = p->logN; a.nh = p->nh; a.S = p->S; a.TX = p->TX;
+  a.sg = p->sg;
   a.st = p->st; a.tb = p->tb;
   const double s = p->s_scale;
   const double kap[5] = {p->st.kc, p->st.kxl, p->st.kxu, p->st.kyl, p->st.kyu};
@@ -178,6 +189,7 @@ InvArgs inv_base(const pd_plan* p) {
   InvArgs a;
   memset(&a, 0, sizeof(a));
   a.N = p->nt; a.logN = p->logN; a.nh = p->nh; a.S = p->S; a.TX = p->TX;
+  a.sg = p->sg;
   a.in = p->spec;
   a.igam = p->igam;
   a.tw = p->tw;
@@ -185,29 +197,41 @@ InvArgs inv_base(const pd_plan* p) {
   return a;
 }
 
+// x-eigentransform of every spectrum row: forward (spec -> spec2) or inverse
+// (spec2 -> spec); tensor cores on the mixed path, CUDA cores on the FP64 path
+pd_status xform_dir(pd_plan* p, bool fwd) {
+  if (p->xform_tc) {
+    LK(launch_xform_tc(fwd ? p->xtc_fwd : p->xtc_inv, p->dflag, p->stream));
+    return PD_OK;
+  }
+  XformArgs xa;
+  xa.rows = p->nh * (p->S / p->sp.nx);
+  xa.nx = p->sp.nx;
+  xa.ld = p->sg.nxp;
+  xa.Q = fwd ? p->Qf : p->Qi;
+  xa.in = fwd ? p->spec : p->spec2;
+  xa.out = fwd ? p->spec2 : p->spec;
+  LK(launch_xform(xa, p->fp64, p->stream));
+  return PD_OK;
+}
+
+TriArgs tri_args(const pd_plan* p, void* data) {
+  TriArgs ta;
+  ta.nh = p->nh; ta.J = p->J; ta.n = p->tri_n; ta.S = p->sg.specS; ta.stride = p->tri_stride;
+  ta.cl = p->tri_cl; ta.cd = p->tri_cd; ta.cu = p->tri_cu;
+  ta.lam = p->lam; ta.mu = p->xform ? p->mu : nullptr; ta.data = data; ta.flag = p->dflag;
+  return ta;
+}
+
 // step (b), with the x-eigentransform around it for 2D / periodic-x problems
 pd_status step_b(pd_plan* p) {
   void* data = p->spec;
   if (p->xform) {
-    XformArgs xa;
-    xa.rows = p->nh * (p->S / p->sp.nx);
-    xa.nx = p->sp.nx;
-    xa.Q = p->Qf; xa.in = p->spec; xa.out = p->spec2;
-    LK(launch_xform(xa, p->fp64, p->stream));
+    CHK(xform_dir(p, true));
     data = p->spec2;
   }
-  TriArgs ta;
-  ta.nh = p->nh; ta.J = p->J; ta.n = p->tri_n; ta.S = p->S; ta.stride = p->tri_stride;
-  ta.cl = p->tri_cl; ta.cd = p->tri_cd; ta.cu = p->tri_cu;
-  ta.lam = p->lam; ta.mu = p->xform ? p->mu : nullptr; ta.data = data; ta.flag = p->dflag;
-  LK(launch_tridiag(ta, p->fp64, p->stream));
-  if (p->xform) {
-    XformArgs xa;
-    xa.rows = p->nh * (p->S / p->sp.nx);
-    xa.nx = p->sp.nx;
-    xa.Q = p->Qi; xa.in = p->spec2; xa.out = p->spec;
-    LK(launch_xform(xa, p->fp64, p->stream));
-  }
+  LK(launch_tridiag(tri_args(p, data), p->fp64, p->stream));
+  if (p->xform) CHK(xform_dir(p, false));
   return PD_OK;
 }
 
@@ -231,10 +255,19 @@ pd_status sync_scalars(pd_plan* p, int nscal) {
   return PD_OK;
 }
 
-bool flag_set(const pd_plan* p) {
+int flag_value(const pd_plan* p) {
   int f;
   memcpy(&f, p->hsc + NSC - 1, sizeof(int));
-  return f != 0;
+  return f;
+}
+bool flag_set(const pd_plan* p) { return flag_value(p) != 0; }
+
+// status for a raised device flag: bit 1 = a bounded wait of the tensor-core
+// pipeline expired, bit 0 = a non-finite value
+pd_status flag_status(pd_plan* p) {
+  const int f = flag_value(p);
+  if (f & 2) return set_err(p, PD_ERR_CUDA, "tensor-core x-transform pipeline timed out");
+  return set_err(p, PD_ERR_NONFINITE, "non-finite value in the solver");
 }
 
 pd_status solve_stationary(pd_plan* p, const double* b, double* u, double tol, int maxit,
@@ -267,7 +300,8 @@ pd_status solve_stationary(pd_plan* p, const double* b, double* u, double tol, i
       break;
     }
     rel = std::sqrt(p->hsc[1]) / nb;
-    if (!std::isfinite(rel) || flag_set(p)) {
+    if (flag_set(p)) { st = flag_status(p); break; }
+    if (!std::isfinite(rel)) {
       st = set_err(p, PD_ERR_NONFINITE, "non-finite value in the stationary iteration");
       break;
     }
@@ -334,7 +368,8 @@ pd_status solve_gmres(pd_plan* p, const double* b, double* u, double tol, int ma
     CHK(sync_scalars(p, 2));
     const double beta = std::sqrt(p->hsc[1]);
     rel = beta / nb;
-    if (!std::isfinite(rel) || flag_set(p)) {
+    if (flag_set(p)) { st = flag_status(p); break; }
+    if (!std::isfinite(rel)) {
       st = set_err(p, PD_ERR_NONFINITE, "non-finite value in GMRES");
       break;
     }
@@ -368,7 +403,7 @@ pd_status solve_gmres(pd_plan* p, const double* b, double* u, double tol, int ma
       CU(cudaMemcpyAsync(p->hsc + 2, p->dsc + 2, sizeof(double), cudaMemcpyDeviceToHost, p->stream));
       CU(cudaMemcpyAsync(p->hsc + NSC - 1, p->dflag, sizeof(int), cudaMemcpyDeviceToHost, p->stream));
       CU(cudaStreamSynchronize(p->stream));
-      if (flag_set(p)) return set_err(p, PD_ERR_NONFINITE, "non-finite value in the preconditioner");
+      if (flag_set(p)) return flag_status(p);
       const double hn = std::sqrt(p->hsc[2]);
       Hat(j + 1, j) = hn;
       if (hn > 0.0) LK(launch_scale_copy(1.0 / hn, w, w, ns, p->stream));
@@ -453,25 +488,14 @@ pd_status pd_profile_iteration(pd_plan* p, const double* b, const double* u, int
     LK(launch_time_fwd(fa, p->fp64, p->stream));
     CU(cudaEventRecord(ev[1], p->stream));
     void* data = p->spec;
-    XformArgs xa;
-    xa.rows = p->nh * (p->S / p->sp.nx);
-    xa.nx = p->sp.nx;
     if (p->xform) {
-      xa.Q = p->Qf; xa.in = p->spec; xa.out = p->spec2;
-      LK(launch_xform(xa, p->fp64, p->stream));
+      CHK(xform_dir(p, true));
       data = p->spec2;
     }
     CU(cudaEventRecord(ev[2], p->stream));
-    TriArgs ta;
-    ta.nh = p->nh; ta.J = p->J; ta.n = p->tri_n; ta.S = p->S; ta.stride = p->tri_stride;
-    ta.cl = p->tri_cl; ta.cd = p->tri_cd; ta.cu = p->tri_cu;
-    ta.lam = p->lam; ta.mu = p->xform ? p->mu : nullptr; ta.data = data; ta.flag = p->dflag;
-    LK(launch_tridiag(ta, p->fp64, p->stream));
+    LK(launch_tridiag(tri_args(p, data), p->fp64, p->stream));
     CU(cudaEventRecord(ev[3], p->stream));
-    if (p->xform) {
-      xa.Q = p->Qi; xa.in = p->spec2; xa.out = p->spec;
-      LK(launch_xform(xa, p->fp64, p->stream));
-    }
+    if (p->xform) CHK(xform_dir(p, false));
     CU(cudaEventRecord(ev[4], p->stream));
     InvArgs ia = inv_base(p);
     if (p->fp64) { ia.mode = INV_UPDATE64; ia.out64 = u64; }
@@ -548,7 +572,9 @@ pd_status pd_plan_create(const pd_space* sp, int nt, double dt, double alpha, in
   p->precision = precision;
   p->fp64 = precision == PD_FP64;
   p->stream = (cudaStream_t)stream;
-  const int budget = p->fp64 ? 8192 : 16384;
+  // tile of TX columns x Nt rows: at most 32 KB of shared memory (16 complex
+  // elements per thread), so several blocks stay resident per SM
+  const int budget = p->fp64 ? 4096 : 8192;
   p->TX = std::max(2, std::min(32, budget / nt));
 
   // spatial stencil
@@ -619,20 +645,58 @@ pd_status pd_plan_create(const pd_space* sp, int nt, double dt, double alpha, in
         mux[j] = kcx + 2.0 * st.kxl * std::cos(PI * (j + 1) / (n + 1));
       }
     }
+    // grid lines padded to an even length: 16-byte aligned rows for TMA
+    p->sg.nx = n;
+    p->sg.nxp = n + (n & 1);
+    p->sg.specS = (int)(S / n) * p->sg.nxp;
     pd_status s1 = upload_cplx(p, &p->Qf, Qf, p->fp64);
     if (s1 == PD_OK) s1 = upload_cplx(p, &p->Qi, Qi, p->fp64);
     if (s1 == PD_OK) s1 = upload_cplx(p, &p->mu, mux, p->fp64);
+    const int rows = p->nh * (int)(S / n);
+    p->xform_tc = !p->fp64 && n >= 16 && rows >= 128;
+    if (s1 == PD_OK && p->xform_tc) {
+      // real form of the complex operators, split into TF32 high and low parts:
+      // G[2o][2i] = Re Q[o][i], G[2o][2i+1] = -Im, G[2o+1][2i] = Im, G[2o+1][2i+1] = Re
+      const size_t P = xform_tc_bpad(n);
+      for (int dir = 0; dir < 2; ++dir) {
+        const std::vector<cd>& Qm = dir == 0 ? Qf : Qi;
+        std::vector<float> hi(P * P, 0.f), lo(P * P, 0.f);
+        for (int o = 0; o < n; ++o)
+          for (int i = 0; i < n; ++i) {
+            const cd q = Qm[(size_t)o * n + i];
+            const float v[2][2] = {{(float)q.real(), (float)-q.imag()},
+                                   {(float)q.imag(), (float)q.real()}};
+            for (int a = 0; a < 2; ++a)
+              for (int b = 0; b < 2; ++b) {
+                const float g = v[a][b];
+                uint32_t bits;
+                memcpy(&bits, &g, 4);
+                bits &= 0xFFFFE000u;
+                float gh;
+                memcpy(&gh, &bits, 4);
+                const size_t idx = (size_t)(2 * o + a) * P + (2 * i + b);
+                hi[idx] = gh;
+                lo[idx] = g - gh;
+              }
+          }
+        if (s1 == PD_OK) s1 = upload(p, dir == 0 ? &p->Gf_hi : &p->Gi_hi, hi);
+        if (s1 == PD_OK) s1 = upload(p, dir == 0 ? &p->Gf_lo : &p->Gi_lo, lo);
+      }
+    }
     if (s1 != PD_OK) { free_plan(p); return s1; }
     if (sp->dim == 2) {
-      p->tri_n = p->sp.ny; p->tri_stride = sp->nx;
+      p->tri_n = p->sp.ny; p->tri_stride = p->sg.nxp;
       p->tri_cl = st.kyl; p->tri_cd = kcy; p->tri_cu = st.kyu;
     } else {
-      p->tri_n = 1; p->tri_stride = sp->nx;
+      p->tri_n = 1; p->tri_stride = p->sg.nxp;
       p->tri_cl = 0; p->tri_cd = 0; p->tri_cu = 0;
     }
   } else {
     p->xform = false;
     p->J = 1;
+    p->sg.nx = sp->nx;
+    p->sg.nxp = sp->nx;
+    p->sg.specS = (int)S;
     p->tri_n = sp->nx; p->tri_stride = 1;
     p->tri_cl = st.kxl; p->tri_cd = kcx; p->tri_cu = st.kxu;
   }
@@ -690,9 +754,20 @@ pd_status pd_plan_create(const pd_space* sp, int nt, double dt, double alpha, in
   if (s2 == PD_OK) s2 = upload_real(p, &p->igam, igam, p->fp64);
   if (s2 == PD_OK) s2 = upload_real(p, &p->igam_s, igs, p->fp64);
   if (s2 == PD_OK) s2 = upload_cplx(p, &p->tw, tw, p->fp64);
-  const size_t specb = (size_t)p->nh * S * cbytes(p);
+  const size_t specb = (size_t)p->nh * p->sg.specS * cbytes(p);
   if (s2 == PD_OK) s2 = dalloc(p, &p->spec, specb);
   if (s2 == PD_OK && p->xform) s2 = dalloc(p, &p->spec2, specb);
+  if (s2 == PD_OK && p->xform_tc) {
+    const int rows = p->nh * (int)(S / sp->nx);
+    const int ldo = 2 * p->sg.nxp;
+    cudaError_t e = xform_tc_prepare(&p->xtc_fwd, rows, sp->nx, ldo, (const float*)p->spec,
+                                     (float*)p->spec2, (const float*)p->Gf_hi,
+                                     (const float*)p->Gf_lo);
+    if (e == cudaSuccess)
+      e = xform_tc_prepare(&p->xtc_inv, rows, sp->nx, ldo, (const float*)p->spec2,
+                           (float*)p->spec, (const float*)p->Gi_hi, (const float*)p->Gi_lo);
+    if (e != cudaSuccess) s2 = fail_cuda(p, e, "tensor map encoding");
+  }
   if (s2 == PD_OK && !p->fp64) s2 = dalloc(p, (void**)&p->Udf, NS(p) * sizeof(float2));
   if (s2 == PD_OK && !p->fp64) s2 = dalloc(p, (void**)&p->Bdf, NS(p) * sizeof(float2));
   if (s2 == PD_OK) s2 = dalloc(p, (void**)&p->dsc, NSC * sizeof(double));

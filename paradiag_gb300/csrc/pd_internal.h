@@ -25,9 +25,21 @@ struct TimeBand {
   double c1[3], c2[3];
 };
 
+// Spectrum layout: entry (k, s) of the half spectrum lives at
+// k * specS + (s / nx) * nxp + s % nx (nxp >= nx pads every grid line of the
+// x-transformed problems to an even length so rows are 16-byte aligned).
+struct SpecGeom {
+  int specS, nx, nxp;
+};
+PD_HD size_t spec_index(const SpecGeom& g, int k, int s) {
+  const int off = (g.nxp == g.nx) ? s : (s / g.nx) * g.nxp + (s % g.nx);
+  return (size_t)k * g.specS + off;
+}
+
 // Arguments of the forward time kernel (K1).
 struct FwdArgs {
   int N, logN, nh, S, TX;
+  SpecGeom sg;
   Stencil st;
   TimeBand tb;
   int mode;                       // FWD_STANDALONE or FWD_RESIDUAL
@@ -43,20 +55,19 @@ struct FwdArgs {
   const void* tw;                 // e^{-2 pi i m / N}, m < N (float2 or double2)
   void* out;                      // half spectrum [nh][S] (float2 or double2)
   double* norm2;                  // += ||r||_2^2 (may be null)
-  int flip;                       // read the input time-reversed (adjoint)
 };
 
 // Arguments of the inverse time kernel (K3).
 struct InvArgs {
   int N, logN, nh, S, TX;
+  SpecGeom sg;
   int mode;                       // INV_UPDATE_DF, INV_OUT64, INV_UPDATE64
   const void* in;                 // half spectrum [nh][S]
   const void* igam;               // gamma_n^{-1} / N (float or double)
   const void* tw;
   float2* Udf;                    // mixed: iterate (double-float), updated in place
   double* out64;                  // FP64 output (z) or FP64 iterate (updated)
-  int* flag;                      // set to 1 on a non-finite value (may be null)
-  int flip;                       // write the output time-reversed (adjoint)
+  int* flag;                      // bit 0 set on a non-finite value (may be null)
 };
 
 enum { FWD_STANDALONE = 0, FWD_RESIDUAL = 1 };
@@ -78,7 +89,7 @@ struct TriArgs {
 // Arguments of the dense x-eigentransform (2D, step (a') / (c')): along x, for
 // every row of the half spectrum: out[row][j] = sum_x Q[j][x] in[row][x].
 struct XformArgs {
-  int rows, nx;
+  int rows, nx, ld;                // ld: row stride in complex elements
   const void* Q;                  // [nx][nx] complex
   const void* in;
   void* out;
@@ -89,6 +100,7 @@ cudaError_t launch_time_fwd(const FwdArgs& a, bool fp64, cudaStream_t st);
 cudaError_t launch_time_inv(const InvArgs& a, bool fp64, cudaStream_t st);
 cudaError_t launch_tridiag(const TriArgs& a, bool fp64, cudaStream_t st);
 cudaError_t launch_xform(const XformArgs& a, bool fp64, cudaStream_t st);
+#include "pd_xform_tc.h"
 
 // Auxiliary kernels (pd_ops.cu)
 cudaError_t launch_apply_A(const Stencil& st, const TimeBand& tb, int N, const double* u,

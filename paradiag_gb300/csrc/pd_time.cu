@@ -158,54 +158,64 @@ PD_D void acc_add_prod(Acc& A, dfc k, float uh, float ul) {
 }
 PD_D df acc_val(const Acc& A) { return fast_two_sum(A.s, A.e); }
 
-// (U(s), (sK U)(s)) of row n in double-float; zeros for n outside [0, N).
-// Must be executed by all lanes of the warp (uniform control flow).
-PD_D void stencil_row_df(const FwdArgs& a, const ColGeom& g, int n, int TX, df& Uc, df& KU) {
-  const bool inrow = n >= 0 && n < a.N;
-  const size_t base = (size_t)(inrow ? n : 0) * a.S;
-  float2 c = make_float2(0.f, 0.f);
-  if (inrow && g.valid) c = __ldg(&a.Udf[base + g.s]);
-  const unsigned FULL = 0xffffffffu;
-  const float lh = __shfl_up_sync(FULL, c.x, 1, TX);
-  const float ll = __shfl_up_sync(FULL, c.y, 1, TX);
-  const float rh = __shfl_down_sync(FULL, c.x, 1, TX);
-  const float rl = __shfl_down_sync(FULL, c.y, 1, TX);
-  Uc = df_make(c.x, c.y);
-  Acc A = {0.f, 0.f};
-  if (inrow && g.valid) {
-    acc_add_prod(A, a.kap[0], c.x, c.y);
-    float2 v;
-    if (g.left == 1) acc_add_prod(A, a.kap[1], lh, ll);
-    else if (g.left == 2) { v = __ldg(&a.Udf[base + g.s_left]); acc_add_prod(A, a.kap[1], v.x, v.y); }
-    if (g.right == 1) acc_add_prod(A, a.kap[2], rh, rl);
-    else if (g.right == 2) { v = __ldg(&a.Udf[base + g.s_right]); acc_add_prod(A, a.kap[2], v.x, v.y); }
-    if (g.down) { v = __ldg(&a.Udf[base + g.s - a.st.nx]); acc_add_prod(A, a.kap[3], v.x, v.y); }
-    if (g.up) { v = __ldg(&a.Udf[base + g.s + a.st.nx]); acc_add_prod(A, a.kap[4], v.x, v.y); }
+// Global loads of one time row at this thread's column (centre, segment-edge
+// x-neighbours, y-neighbours); zeros outside [0, N) or outside the grid.
+template <typename V>
+struct RowLd {
+  V c, l, r, d, u;
+};
+
+template <typename V>
+PD_D RowLd<V> load_row(const V* U, const FwdArgs& a, const ColGeom& g, int n) {
+  RowLd<V> L;
+  L.c = L.l = L.r = L.d = L.u = V{};
+  if (n >= 0 && n < a.N && g.valid) {
+    const size_t base = (size_t)n * a.S;
+    L.c = __ldg(&U[base + g.s]);
+    if (g.left == 2) L.l = __ldg(&U[base + g.s_left]);
+    if (g.right == 2) L.r = __ldg(&U[base + g.s_right]);
+    if (g.down) L.d = __ldg(&U[base + g.s - a.st.nx]);
+    if (g.up) L.u = __ldg(&U[base + g.s + a.st.nx]);
   }
+  return L;
+}
+
+// (U(s), (sK U)(s)) in double-float from a loaded row; the x-neighbours of
+// interior lanes come from the neighbouring lanes.  Must be executed by all
+// lanes of the warp (uniform control flow).
+PD_D void stencil_df(const FwdArgs& a, const ColGeom& g, const RowLd<float2>& L, int TX, df& Uc,
+                     df& KU) {
+  const unsigned FULL = 0xffffffffu;
+  const float lh = __shfl_up_sync(FULL, L.c.x, 1, TX);
+  const float ll = __shfl_up_sync(FULL, L.c.y, 1, TX);
+  const float rh = __shfl_down_sync(FULL, L.c.x, 1, TX);
+  const float rl = __shfl_down_sync(FULL, L.c.y, 1, TX);
+  Uc = df_make(L.c.x, L.c.y);
+  Acc A = {0.f, 0.f};
+  acc_add_prod(A, a.kap[0], L.c.x, L.c.y);
+  if (g.left == 1) acc_add_prod(A, a.kap[1], lh, ll);
+  else if (g.left == 2) acc_add_prod(A, a.kap[1], L.l.x, L.l.y);
+  if (g.right == 1) acc_add_prod(A, a.kap[2], rh, rl);
+  else if (g.right == 2) acc_add_prod(A, a.kap[2], L.r.x, L.r.y);
+  if (g.down) acc_add_prod(A, a.kap[3], L.d.x, L.d.y);
+  if (g.up) acc_add_prod(A, a.kap[4], L.u.x, L.u.y);
   KU = acc_val(A);
 }
 
-PD_D void stencil_row_64(const FwdArgs& a, const ColGeom& g, int n, int TX, double& Uc,
-                         double& KU) {
-  const bool inrow = n >= 0 && n < a.N;
-  const size_t base = (size_t)(inrow ? n : 0) * a.S;
-  double c = 0.0;
-  if (inrow && g.valid) c = __ldg(&a.U64[base + g.s]);
+PD_D void stencil_64(const FwdArgs& a, const ColGeom& g, const RowLd<double>& L, int TX,
+                     double& Uc, double& KU) {
   const unsigned FULL = 0xffffffffu;
-  const double lv = __shfl_up_sync(FULL, c, 1, TX);
-  const double rv = __shfl_down_sync(FULL, c, 1, TX);
-  Uc = c;
-  double k = 0.0;
-  if (inrow && g.valid) {
-    const Stencil& st = a.st;
-    k = st.kc * c;
-    if (g.left == 1) k = fma(st.kxl, lv, k);
-    else if (g.left == 2) k = fma(st.kxl, __ldg(&a.U64[base + g.s_left]), k);
-    if (g.right == 1) k = fma(st.kxu, rv, k);
-    else if (g.right == 2) k = fma(st.kxu, __ldg(&a.U64[base + g.s_right]), k);
-    if (g.down) k = fma(st.kyl, __ldg(&a.U64[base + g.s - st.nx]), k);
-    if (g.up) k = fma(st.kyu, __ldg(&a.U64[base + g.s + st.nx]), k);
-  }
+  const double lv = __shfl_up_sync(FULL, L.c, 1, TX);
+  const double rv = __shfl_down_sync(FULL, L.c, 1, TX);
+  const Stencil& st = a.st;
+  Uc = L.c;
+  double k = st.kc * L.c;
+  if (g.left == 1) k = fma(st.kxl, lv, k);
+  else if (g.left == 2) k = fma(st.kxl, L.l, k);
+  if (g.right == 1) k = fma(st.kxu, rv, k);
+  else if (g.right == 2) k = fma(st.kxu, L.r, k);
+  if (g.down) k = fma(st.kyl, L.d, k);
+  if (g.up) k = fma(st.kyu, L.u, k);
   KU = k;
 }
 
@@ -225,11 +235,10 @@ PD_D T block_sum(T v, T* red) {
 // K1: residual (optional) + Gamma scaling + forward real FFT along t.
 // PREC 0: mixed (double-float residual, FP32 transform); PREC 1: FP64.
 // ---------------------------------------------------------------------------
-template <int PREC, int BAND>
-__global__ void __launch_bounds__(TT) k_time_fwd(FwdArgs a) {
+template <int PREC, int BAND, int EPT>
+__global__ void __launch_bounds__(TT, 3) k_time_fwd(FwdArgs a) {
   using R = typename std::conditional<PREC == 0, float, double>::type;
   using C = cplx_t<R>;
-  constexpr int EPT = PREC == 0 ? 32 : 16;
   extern __shared__ __align__(16) unsigned char smraw[];
   C* sm = reinterpret_cast<C*>(smraw);
   R* smr = reinterpret_cast<R*>(smraw);
@@ -268,17 +277,23 @@ __global__ void __launch_bounds__(TT) k_time_fwd(FwdArgs a) {
     const ColGeom g = col_geom(a.st, s, x, TX);
     if constexpr (PREC == 0) {
       df U1 = df_make(0.f, 0.f), U2 = U1, K1 = U1, K2 = U1, U0, K0;
-      if (BAND == 2) stencil_row_df(a, g, n_beg - 2, TX, U2, K2);
-      stencil_row_df(a, g, n_beg - 1, TX, U1, K1);
+      if (BAND == 2) stencil_df(a, g, load_row(a.Udf, a, g, n_beg - 2), TX, U2, K2);
+      stencil_df(a, g, load_row(a.Udf, a, g, n_beg - 1), TX, U1, K1);
+      RowLd<float2> cur = load_row(a.Udf, a, g, n_beg);
+      float2 bcur = (n_beg < N && g.valid) ? __ldg(&a.Bdf[(size_t)n_beg * S + s])
+                                           : make_float2(0.f, 0.f);
       float part = 0.f;
       for (int i = 0; i < rpc; ++i) {
         const int n = n_beg + i;
-        stencil_row_df(a, g, n, TX, U0, K0);  // uniform across the warp
+        // prefetch the next row before computing this one
+        const RowLd<float2> nxt = load_row(a.Udf, a, g, i + 1 < rpc ? n + 1 : -1);
+        const float2 bnxt = (i + 1 < rpc && n + 1 < N && g.valid)
+                                ? __ldg(&a.Bdf[(size_t)(n + 1) * S + s]) : make_float2(0.f, 0.f);
+        stencil_df(a, g, cur, TX, U0, K0);  // uniform across the warp
         if (n < N) {
           float v = 0.f;
           if (g.valid) {
-            const float2 bb = __ldg(&a.Bdf[(size_t)n * S + s]);
-            Acc A = {bb.x, bb.y};
+            Acc A = {bcur.x, bcur.y};
             acc_add(A, -U0.hi, -U0.lo);
             if (BAND == 1) {
               if (n >= 1) acc_add(A, U1.hi, U1.lo);
@@ -302,20 +317,27 @@ __global__ void __launch_bounds__(TT) k_time_fwd(FwdArgs a) {
           smr[n * TX + x] = v;
         }
         U2 = U1; K2 = K1; U1 = U0; K1 = K0;
+        cur = nxt;
+        bcur = bnxt;
       }
       nrm = (double)part * a.rscale2;
     } else {
       double U1 = 0, U2 = 0, K1 = 0, K2 = 0, U0, K0;
       const TimeBand& tb = a.tb;
-      if (BAND == 2) stencil_row_64(a, g, n_beg - 2, TX, U2, K2);
-      stencil_row_64(a, g, n_beg - 1, TX, U1, K1);
+      if (BAND == 2) stencil_64(a, g, load_row(a.U64, a, g, n_beg - 2), TX, U2, K2);
+      stencil_64(a, g, load_row(a.U64, a, g, n_beg - 1), TX, U1, K1);
+      RowLd<double> cur = load_row(a.U64, a, g, n_beg);
+      double bcur = (n_beg < N && g.valid) ? __ldg(&a.B64[(size_t)n_beg * S + s]) : 0.0;
       for (int i = 0; i < rpc; ++i) {
         const int n = n_beg + i;
-        stencil_row_64(a, g, n, TX, U0, K0);
+        const RowLd<double> nxt = load_row(a.U64, a, g, i + 1 < rpc ? n + 1 : -1);
+        const double bnxt = (i + 1 < rpc && n + 1 < N && g.valid)
+                                ? __ldg(&a.B64[(size_t)(n + 1) * S + s]) : 0.0;
+        stencil_64(a, g, cur, TX, U0, K0);
         if (n < N) {
           double v = 0.0;
           if (g.valid) {
-            double r = __ldg(&a.B64[(size_t)n * S + s]);
+            double r = bcur;
             r = fma(-tb.c1[0], U0, r);
             r = fma(-tb.c2[0], K0, r);
             if (n >= 1) { r = fma(-tb.c1[1], U1, r); r = fma(-tb.c2[1], K1, r); }
@@ -326,6 +348,8 @@ __global__ void __launch_bounds__(TT) k_time_fwd(FwdArgs a) {
           smr[n * TX + x] = v;
         }
         U2 = U1; K2 = K1; U1 = U0; K1 = K0;
+        cur = nxt;
+        bcur = bnxt;
       }
     }
   }
@@ -348,19 +372,18 @@ __global__ void __launch_bounds__(TT) k_time_fwd(FwdArgs a) {
     const C A = cscale(cadd(Zk, Zm), half);
     const C B = cscale(cmul_mi(csub(Zk, Zm)), half);
     const int sa = x0 + 2 * c;
-    if (sa < S) out[(size_t)k * S + sa] = A;
-    if (sa + 1 < S) out[(size_t)k * S + sa + 1] = B;
+    if (sa < S) out[spec_index(a.sg, k, sa)] = A;
+    if (sa + 1 < S) out[spec_index(a.sg, k, sa + 1)] = B;
   }
 }
 
 // ---------------------------------------------------------------------------
 // K3: inverse real FFT along t + Gamma^{-1}/Nt + write or update.
 // ---------------------------------------------------------------------------
-template <int PREC>
-__global__ void __launch_bounds__(TT) k_time_inv(InvArgs a) {
+template <int PREC, int EPT>
+__global__ void __launch_bounds__(TT, 3) k_time_inv(InvArgs a) {
   using R = typename std::conditional<PREC == 0, float, double>::type;
   using C = cplx_t<R>;
-  constexpr int EPT = PREC == 0 ? 32 : 16;
   extern __shared__ __align__(16) unsigned char smraw[];
   C* sm = reinterpret_cast<C*>(smraw);
   R* smr = reinterpret_cast<R*>(smraw);
@@ -373,8 +396,8 @@ __global__ void __launch_bounds__(TT) k_time_inv(InvArgs a) {
     const int c = item & (TXc - 1), k = item >> lgTXc;
     const int sa = x0 + 2 * c;
     C A = czero<C>(), B = czero<C>();
-    if (sa < S) A = in[(size_t)k * S + sa];
-    if (sa + 1 < S) B = in[(size_t)k * S + sa + 1];
+    if (sa < S) A = in[spec_index(a.sg, k, sa)];
+    if (sa + 1 < S) B = in[spec_index(a.sg, k, sa + 1)];
     if (k == 0 || 2 * k == N) { A.y = 0; B.y = 0; }
     sm[(k << lgTXc) + c] = mk(A.x - B.y, A.y + B.x);            // A + i B
     if (k > 0 && 2 * k < N)
@@ -407,13 +430,40 @@ __global__ void __launch_bounds__(TT) k_time_inv(InvArgs a) {
       else a.out64[idx] = dz;
     }
   }
-  if (bad && a.flag != nullptr) atomicExch(a.flag, 1);
+  if (bad && a.flag != nullptr) atomicOr(a.flag, 1);
+}
+
+// complex elements per thread needed by a tile of N x TX/2 columns
+inline int ept_for(int N, int TX) {
+  const int e = (N * (TX / 2) + TT - 1) / TT;
+  return e <= 4 ? 4 : e <= 8 ? 8 : e <= 16 ? 16 : 32;
+}
+
+template <int PREC, int BAND, int EPT>
+cudaError_t launch_fwd_e(const FwdArgs& a, cudaStream_t st) {
+  const size_t smem = (size_t)a.N * (a.TX / 2) * (PREC == 0 ? sizeof(float2) : sizeof(double2));
+  auto kern = k_time_fwd<PREC, BAND, EPT>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  const int grid = ceil_div(a.S, a.TX);
+  kern<<<grid, TT, smem, st>>>(a);
+  return cudaGetLastError();
 }
 
 template <int PREC, int BAND>
 cudaError_t launch_fwd_t(const FwdArgs& a, cudaStream_t st) {
+  switch (ept_for(a.N, a.TX)) {
+    case 4: return launch_fwd_e<PREC, BAND, 4>(a, st);
+    case 8: return launch_fwd_e<PREC, BAND, 8>(a, st);
+    case 16: return launch_fwd_e<PREC, BAND, 16>(a, st);
+    default: return launch_fwd_e<PREC, BAND, 32>(a, st);
+  }
+}
+
+template <int PREC, int EPT>
+cudaError_t launch_inv_e(const InvArgs& a, cudaStream_t st) {
   const size_t smem = (size_t)a.N * (a.TX / 2) * (PREC == 0 ? sizeof(float2) : sizeof(double2));
-  auto kern = k_time_fwd<PREC, BAND>;
+  auto kern = k_time_inv<PREC, EPT>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   const int grid = ceil_div(a.S, a.TX);
@@ -423,13 +473,12 @@ cudaError_t launch_fwd_t(const FwdArgs& a, cudaStream_t st) {
 
 template <int PREC>
 cudaError_t launch_inv_t(const InvArgs& a, cudaStream_t st) {
-  const size_t smem = (size_t)a.N * (a.TX / 2) * (PREC == 0 ? sizeof(float2) : sizeof(double2));
-  auto kern = k_time_inv<PREC>;
-  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (e != cudaSuccess) return e;
-  const int grid = ceil_div(a.S, a.TX);
-  kern<<<grid, TT, smem, st>>>(a);
-  return cudaGetLastError();
+  switch (ept_for(a.N, a.TX)) {
+    case 4: return launch_inv_e<PREC, 4>(a, st);
+    case 8: return launch_inv_e<PREC, 8>(a, st);
+    case 16: return launch_inv_e<PREC, 16>(a, st);
+    default: return launch_inv_e<PREC, 32>(a, st);
+  }
 }
 
 }  // namespace

@@ -21,7 +21,7 @@ template <typename C>
 struct Row4 { C a, b, c, d; };
 
 template <typename R, int W>
-__global__ void k_tridiag(TriArgs a, int m, int SB) {
+__global__ void __launch_bounds__(512) k_tridiag(TriArgs a, int m, int SB) {
   using C = cplx_t<R>;
   extern __shared__ __align__(16) unsigned char smraw[];
   const int rows_pad = 32 * W * (m + 1);
@@ -75,20 +75,16 @@ __global__ void k_tridiag(TriArgs a, int m, int SB) {
     ud = cmul(u, invd);
   }
 
-  // ---- lane rows
-  C rhs[MMAX], lrow[MMAX], urow[MMAX];
+  // ---- lane rows: right-hand sides scaled by 1/d; the coefficients of row i
+  // are (ld, 1, ud) except at the ends (no z_{-1}, no z_n) and on padding rows
+  C rhs[MMAX];
   const int i0 = G * m;
   C* my = tile + (size_t)sb * rows_pad + G * (m + 1);
 #pragma unroll
-  for (int t = 0; t < MMAX; ++t) {
-    if (t < m) {
-      const int i = i0 + t;
-      const bool in = i < n;
-      rhs[t] = in ? cmul(my[t], invd) : czero<C>();
-      lrow[t] = (in && i > 0) ? ld : czero<C>();
-      urow[t] = (in && i < n - 1) ? ud : czero<C>();
-    }
-  }
+  for (int t = 0; t < MMAX; ++t)
+    if (t < m) rhs[t] = (i0 + t < n) ? cmul(my[t], invd) : czero<C>();
+  auto lrow = [&](int t) -> C { const int i = i0 + t; return (i > 0 && i < n) ? ld : czero<C>(); };
+  auto urow = [&](int t) -> C { const int i = i0 + t; return (i < n - 1) ? ud : czero<C>(); };
 
   // ---- interior elimination (rows 1..m-2 of the chunk)
   const int mi = m - 2;
@@ -98,14 +94,16 @@ __global__ void k_tridiag(TriArgs a, int m, int SB) {
 #pragma unroll
   for (int t = 1; t < MMAX - 1; ++t) {
     if (t <= mi) {
-      const C den = csub(mk((R)1, (R)0), cmul(lrow[t], cc[t - 1]));
+      const C lt = lrow(t);
+      const C den = csub(mk((R)1, (R)0), cmul(lt, cc[t - 1]));
       const C iden = crcp(den);
-      cc[t] = cmul(urow[t], iden);
-      Y[t] = cmul(csub(rhs[t], cmul(lrow[t], Y[t - 1])), iden);
-      const C pr = (t == 1) ? mk(-lrow[1].x, -lrow[1].y) : czero<C>();
-      P[t] = cmul(csub(pr, cmul(lrow[t], P[t - 1])), iden);
-      const C qr = (t == mi) ? mk(-urow[t].x, -urow[t].y) : czero<C>();
-      Q[t] = cmul(csub(qr, cmul(lrow[t], Q[t - 1])), iden);
+      cc[t] = cmul(urow(t), iden);
+      Y[t] = cmul(csub(rhs[t], cmul(lt, Y[t - 1])), iden);
+      const C pr = (t == 1) ? mk(-lt.x, -lt.y) : czero<C>();
+      P[t] = cmul(csub(pr, cmul(lt, P[t - 1])), iden);
+      const C ut = urow(t);
+      const C qr = (t == mi) ? mk(-ut.x, -ut.y) : czero<C>();
+      Q[t] = cmul(csub(qr, cmul(lt, Q[t - 1])), iden);
     }
   }
 #pragma unroll
@@ -120,16 +118,17 @@ __global__ void k_tridiag(TriArgs a, int m, int SB) {
   // ---- reduced rows (f_G at 2G, g_G at 2G+1)
   Row4<C> rf, rg;
   const C one = mk((R)1, (R)0);
-  C u0 = urow[0], lm = czero<C>(), um = czero<C>(), rm = czero<C>();
+  const C u0 = urow(0), lm = lrow(m - 1), um = urow(m - 1);
+  C rm = czero<C>();
 #pragma unroll
   for (int t = 1; t < MMAX; ++t)
-    if (t == m - 1) { lm = lrow[t]; um = urow[t]; rm = rhs[t]; }
+    if (t == m - 1) rm = rhs[t];
   if (mi >= 1) {
     C Y1 = Y[1], P1 = P[1], Q1 = Q[1], Ym = czero<C>(), Pm = czero<C>(), Qm = czero<C>();
 #pragma unroll
     for (int t = 1; t < MMAX - 1; ++t)
       if (t == mi) { Ym = Y[t]; Pm = P[t]; Qm = Q[t]; }
-    rf.a = lrow[0];
+    rf.a = lrow(0);
     rf.b = cadd(one, cmul(u0, P1));
     rf.c = cmul(u0, Q1);
     rf.d = csub(rhs[0], cmul(u0, Y1));
@@ -138,7 +137,7 @@ __global__ void k_tridiag(TriArgs a, int m, int SB) {
     rg.c = um;
     rg.d = csub(rm, cmul(lm, Ym));
   } else {
-    rf.a = lrow[0]; rf.b = one; rf.c = u0; rf.d = rhs[0];
+    rf.a = lrow(0); rf.b = one; rf.c = u0; rf.d = rhs[0];
     rg.a = lm; rg.b = one; rg.c = um; rg.d = rm;
   }
 
@@ -197,7 +196,7 @@ __global__ void k_tridiag(TriArgs a, int m, int SB) {
       my[t] = z;
     }
   }
-  if (bad && active && a.flag != nullptr) atomicExch(a.flag, 1);
+  if (bad && active && a.flag != nullptr) atomicOr(a.flag, 1);
   __syncthreads();
 
   for (long long e = threadIdx.x; e < nel; e += nthreads) {
@@ -217,7 +216,7 @@ template <typename R, int W>
 cudaError_t launch_w(const TriArgs& a, cudaStream_t st) {
   using C = cplx_t<R>;
   const int m = std::max(2, ceil_div(a.n, 32 * W));
-  const int SB = std::max(1, (sizeof(R) == 4 ? 16 : 8) / W);
+  const int SB = std::max(1, (sizeof(R) == 4 ? 8 : 4) / W);
   const size_t smem = (size_t)SB * (32 * W * (m + 1) + 4 * 64 * W) * sizeof(C);
   auto kern = k_tridiag<R, W>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);

@@ -30,7 +30,7 @@ __global__ void __launch_bounds__(256) k_xform_simt(XformArgs a) {
     for (int e = threadIdx.x; e < BR * BK; e += 256) {
       const int rr = e / BK, kk = e % BK;
       const int r = r0 + rr, k = k0 + kk;
-      sx[rr][kk] = (r < a.rows && k < a.nx) ? X[(size_t)r * a.nx + k] : czero<C>();
+      sx[rr][kk] = (r < a.rows && k < a.nx) ? X[(size_t)r * a.ld + k] : czero<C>();
     }
     for (int e = threadIdx.x; e < BJ * BK; e += 256) {
       const int jj = e / BK, kk = e % BK;
@@ -62,7 +62,7 @@ __global__ void __launch_bounds__(256) k_xform_simt(XformArgs a) {
 #pragma unroll
     for (int v = 0; v < 4; ++v) {
       const int r = r0 + tr + 16 * u, j = j0 + tj + 16 * v;
-      if (r < a.rows && j < a.nx) Y[(size_t)r * a.nx + j] = acc[u][v];
+      if (r < a.rows && j < a.nx) Y[(size_t)r * a.ld + j] = acc[u][v];
     }
 }
 

@@ -45,6 +45,13 @@ CASES = {
     "2d_be_dirichlet_sym_11x9x8": P(dim=2, nx=11, ny=9, nu=1.0, nt=8, alpha=1e-2),
     "2d_lf_dirichlet_sym_9x7x8": P(dim=2, nx=9, ny=7, nu=1.0, nt=8, T=2.0,
                                    scheme=W.LEAPFROG, alpha=0.1),
+    # x-transform on the tensor cores in the mixed path (nx >= 16, >= 128 spectrum rows)
+    "2d_tc_cn_periodic_33x20x32": P(dim=2, nx=33, ny=20, nu=1e-2, ax=1.0, ay=0.5,
+                                    bcx=W.PERIODIC, nt=32, scheme=W.CN, alpha=1e-3),
+    "2d_tc_be_dirichlet_sym_40x17x16": P(dim=2, nx=40, ny=17, nu=1.0, nt=16, alpha=1e-2),
+    "2d_tc_cn_periodic_255x4x64": P(dim=2, nx=255, ny=4, nu=1e-3, ax=1.0, ay=0.5,
+                                    bcx=W.PERIODIC, nt=64, scheme=W.CN, alpha=1e-3),
+    "1d_tc_periodic_200x256": P(nx=200, nu=1e-2, ax=1.0, bcx=W.PERIODIC, nt=256, alpha=1e-2),
 }
 
 
