@@ -77,8 +77,11 @@ typedef struct {
 typedef struct pd_plan pd_plan;
 
 /* Create a plan for the all-at-once system on Nt uniform steps of size dt with
- * preconditioner parameter alpha in (0, 1] (Lemma 1).  Nt must be a power of
- * two (1 <= Nt <= 8192 for PD_MIXED, <= 4096 for PD_FP64).  alpha = 1 is
+ * preconditioner parameter alpha in (0, 1] (Lemma 1).  Any Nt >= 1: powers of
+ * two use a radix-4/2 Stockham FFT (Nt <= 4096 for PD_MIXED, <= 2048 for
+ * PD_FP64), other lengths Bluestein's chirp-z transform of length
+ * M = 2^ceil(log2(2 Nt - 1)) within the same limits (Nt <= 2048 / 1024);
+ * larger Nt gives PD_ERR_UNSUPPORTED.  alpha = 1 is
  * accepted only when no shifted system is singular (checked here).
  * stream: a cudaStream_t (NULL = legacy default stream).
  * Builds on the host, in FP64: the eigenvalues lambda_{j,k} of Lemma 1, the
@@ -148,6 +151,46 @@ PD_API pd_status pd_profile_iteration(pd_plan* plan, const double* b, const doub
 
 /* Number of kernels this plan (and its adjoint plan) has launched so far. */
 PD_API pd_status pd_plan_launches(const pd_plan* plan, unsigned long long* count);
+
+/* ---- batched solves: many independent problems of uneven size ----------
+ * One problem of a batch (1D, Dirichlet, any scheme; all members of one batch
+ * must share the time band: theta-method or leap-frog). */
+typedef struct {
+  pd_space space;
+  int nt;
+  double dt;
+  double alpha;
+  int scheme;
+  double theta;
+} pd_problem;
+
+typedef struct pd_batch pd_batch;
+
+/* Create a batch of nprob problems (1 <= nprob <= 4096).  Each problem gets
+ * its own Lemma 1 tables and half spectrum; the iterate is packed.  Problem i
+ * occupies elements [off_i, off_{i+1}) of the packed arrays, laid out
+ * [Nt_i][nx_i] (see pd_batch_offsets).  The kernels of one iteration run as one
+ * launch per kernel type over all problems (the tridiagonal solve: one launch
+ * per class of system length), driven by per-problem descriptors and a
+ * block-to-(problem, tile) work table in device memory. */
+PD_API pd_status pd_batch_create(const pd_problem* probs, int nprob, int precision, void* stream,
+                                 pd_batch** out);
+PD_API pd_status pd_batch_destroy(pd_batch* batch);
+/* offsets[0..nprob]: element offsets of the problems in the packed arrays. */
+PD_API pd_status pd_batch_offsets(const pd_batch* batch, unsigned long long* offsets);
+/* Right-hand sides of all problems (pd_build_rhs per member): u0 packed with
+ * problem i at sum_{j<i} nx_j; f packed ([Nt_i+1][nx_i] each) or NULL; b packed. */
+PD_API pd_status pd_batch_build_rhs(pd_batch* batch, const double* u0, const double* f,
+                                    double* b);
+/* Stationary iteration (eq. 5.1) on all problems together until every
+ * problem has ||b_i - A_i u_i|| <= tol ||b_i|| (relres_max receives the largest
+ * relative residual) or maxit sweeps.  u: packed initial guess / solution. */
+PD_API pd_status pd_batch_solve(pd_batch* batch, const double* b, double* u, double tol,
+                                int maxit, int* iters, double* relres_max);
+/* relres[0..nprob): relative residual of every problem at the last check. */
+PD_API pd_status pd_batch_relres(const pd_batch* batch, double* relres);
+PD_API pd_status pd_batch_launches(const pd_batch* batch, unsigned long long* count);
+PD_API const char* pd_batch_last_error(const pd_batch* batch);
 
 /* Size of the device array used by pd_apply_precond_noalloc (8 MiB). */
 #define PD_NOALLOC_SCRATCH_BYTES (8u << 20)

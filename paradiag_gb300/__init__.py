@@ -30,6 +30,11 @@ class pd_space(ctypes.Structure):
                 ("lx", ctypes.c_double), ("ly", ctypes.c_double)]
 
 
+class pd_problem(ctypes.Structure):
+    _fields_ = [("space", pd_space), ("nt", ctypes.c_int), ("dt", ctypes.c_double),
+                ("alpha", ctypes.c_double), ("scheme", ctypes.c_int), ("theta", ctypes.c_double)]
+
+
 class PDError(RuntimeError):
     def __init__(self, status, msg=""):
         self.status = status
@@ -63,6 +68,15 @@ _SIGS = {
                                                 ctypes.c_double, ctypes.c_double, ctypes.c_int,
                                                 ctypes.c_double, _P, _P, _P,
                                                 ctypes.POINTER(ctypes.c_ulonglong)]),
+    "pd_batch_create": (ctypes.c_int, [ctypes.POINTER(pd_problem), ctypes.c_int, ctypes.c_int, _P,
+                                       ctypes.POINTER(_P)]),
+    "pd_batch_destroy": (ctypes.c_int, [_P]),
+    "pd_batch_offsets": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_ulonglong)]),
+    "pd_batch_build_rhs": (ctypes.c_int, [_P, _P, _P, _P]),
+    "pd_batch_solve": (ctypes.c_int, [_P, _P, _P, ctypes.c_double, ctypes.c_int, _I, _D]),
+    "pd_batch_launches": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_ulonglong)]),
+    "pd_batch_relres": (ctypes.c_int, [_P, _D]),
+    "pd_batch_last_error": (ctypes.c_char_p, [_P]),
     "pd_status_string": (ctypes.c_char_p, [ctypes.c_int]),
     "pd_last_error": (ctypes.c_char_p, [_P]),
 }
@@ -141,6 +155,50 @@ def pd_apply_precond_noalloc(space, nt, dt, alpha, scheme, theta, r, z, stream):
     st = load().pd_apply_precond_noalloc(ctypes.byref(space), nt, dt, alpha, scheme, theta, r, z,
                                          _P(stream), ctypes.byref(need))
     return st, need.value
+
+
+def pd_batch_create(problems, precision, stream):
+    arr = (pd_problem * len(problems))(*problems)
+    out = _P()
+    st = load().pd_batch_create(arr, len(problems), precision, _P(stream), ctypes.byref(out))
+    return st, out.value
+
+
+def pd_batch_destroy(batch):
+    return load().pd_batch_destroy(batch)
+
+
+def pd_batch_offsets(batch, nprob):
+    off = (ctypes.c_ulonglong * (nprob + 1))()
+    st = load().pd_batch_offsets(batch, off)
+    return st, list(off)
+
+
+def pd_batch_build_rhs(batch, u0, f, b):
+    return load().pd_batch_build_rhs(batch, u0, f, b)
+
+
+def pd_batch_solve(batch, b, u, tol, maxit):
+    it = ctypes.c_int(0)
+    rel = ctypes.c_double(0.0)
+    st = load().pd_batch_solve(batch, b, u, tol, maxit, ctypes.byref(it), ctypes.byref(rel))
+    return st, it.value, rel.value
+
+
+def pd_batch_launches(batch):
+    v = ctypes.c_ulonglong(0)
+    st = load().pd_batch_launches(batch, ctypes.byref(v))
+    return st, v.value
+
+
+def pd_batch_relres(batch, nprob):
+    arr = (ctypes.c_double * nprob)()
+    st = load().pd_batch_relres(batch, arr)
+    return st, list(arr)
+
+
+def pd_batch_last_error(batch):
+    return load().pd_batch_last_error(batch).decode()
 
 
 def pd_residual(plan, b, u, r):
@@ -311,6 +369,67 @@ class Plan:
         return lam, it, rel
 
 
+class Batch:
+    """Many independent 1D problems solved together (packed FP64 arrays).
+
+    ``problems``: list of dicts with keys space (pd_space fields), nt, dt, alpha,
+    scheme, theta.  Problem i occupies ``offsets[i]:offsets[i+1]`` of the packed
+    arrays ([nt_i][nx_i] each)."""
+
+    def __init__(self, problems, precision=PD_MIXED, stream=None):
+        import torch
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        items = []
+        for q in problems:
+            sp = q["space"]
+            items.append(pd_problem(pd_space(1, int(sp["nx"]), 1, float(sp.get("nu", 1.0)),
+                                             float(sp.get("ax", 0.0)), 0.0, PD_DIRICHLET,
+                                             PD_DIRICHLET, float(sp.get("lx", 1.0)), 1.0),
+                                    int(q["nt"]), float(q["dt"]), float(q["alpha"]),
+                                    int(q.get("scheme", PD_BE)), float(q.get("theta", 1.0))))
+        st, h = pd_batch_create(items, precision, self.stream.cuda_stream)
+        if st != PD_OK:
+            raise PDError(st, "pd_batch_create")
+        self._h = h
+        self.np = len(items)
+        st, self.offsets = pd_batch_offsets(h, self.np)
+        self.total = self.offsets[-1]
+
+    def close(self):
+        if getattr(self, "_h", None):
+            pd_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def launches(self):
+        return pd_batch_launches(self._h)[1]
+
+    def build_rhs(self, u0, f=None):
+        import torch
+        b = torch.empty(self.total, dtype=torch.float64, device=u0.device)
+        st = pd_batch_build_rhs(self._h, _ptr(u0), _ptr(f), _ptr(b))
+        if st != PD_OK:
+            raise PDError(st, pd_batch_last_error(self._h))
+        return b
+
+    def solve(self, b, u=None, tol=1e-10, maxit=50, allow_not_converged=False):
+        import torch
+        u = torch.zeros_like(b) if u is None else u
+        st, it, rel = pd_batch_solve(self._h, _ptr(b), _ptr(u), tol, maxit)
+        if not (st == PD_OK or (allow_not_converged and st == PD_ERR_NOT_CONVERGED)):
+            raise PDError(st, pd_batch_last_error(self._h))
+        return u, it, rel
+
+    def relres(self):
+        """Relative residual of every problem at the last check of solve()."""
+        return pd_batch_relres(self._h, self.np)[1]
+
+
 def _make_pdsolve():
     import torch
 
@@ -348,5 +467,6 @@ class _Lazy:
 
 PDSolve = _Lazy()
 
-__all__ = ["build", "lib_path", "load", "Plan", "PDSolve", "PDError", "pd_space",
+__all__ = ["build", "lib_path", "load", "Plan", "Batch", "PDSolve", "PDError", "pd_space",
+           "pd_problem",
            "exported_symbols"] + [k for k in _SIGS]

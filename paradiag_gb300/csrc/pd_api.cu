@@ -22,57 +22,7 @@
 
 using cd = std::complex<double>;
 
-struct pd_plan {
-  pd_space sp;
-  int nt = 0, nh = 0, S = 0, logN = 0, TX = 0;
-  int scheme = 0;
-  double theta = 1.0, dt = 0.0, alpha = 0.0;
-  int precision = 0;
-  bool fp64 = false;
-  Stencil st;
-  TimeBand tb;
-  double s_scale = 1.0;
-  cudaStream_t stream = nullptr;
-  // spectrum layout (padded grid lines for x-transformed problems)
-  SpecGeom sg;
-  // step (b) layout
-  bool xform = false;
-  bool xform_tc = false;          // mixed path: tcgen05 x-transform
-  XformTc xtc_fwd, xtc_inv;
-  void* Gf_hi = nullptr;
-  void* Gf_lo = nullptr;
-  void* Gi_hi = nullptr;
-  void* Gi_lo = nullptr;
-  int J = 1, tri_n = 0, tri_stride = 1;
-  double tri_cl = 0, tri_cd = 0, tri_cu = 0;
-  // device tables
-  void* lam = nullptr;
-  void* gam = nullptr;
-  void* igam = nullptr;
-  void* igam_s = nullptr;
-  void* tw = nullptr;
-  void* Qf = nullptr;
-  void* Qi = nullptr;
-  void* mu = nullptr;
-  // workspace
-  void* spec = nullptr;
-  void* spec2 = nullptr;
-  float2* Udf = nullptr;
-  float2* Bdf = nullptr;
-  double* w64a = nullptr;
-  double* w64b = nullptr;
-  double* dsc = nullptr;   // device scalars
-  int* dflag = nullptr;
-  double* hsc = nullptr;   // pinned host scalars
-  double* V = nullptr;
-  double* Z = nullptr;
-  double* dh = nullptr;
-  int gm_cap = 0;
-  pd_plan* adj = nullptr;
-  size_t bytes = 0;
-  unsigned long long launches = 0;
-  char msg[256] = {0};
-};
+#include "pd_plan.h"
 
 namespace {
 
@@ -151,7 +101,8 @@ void free_plan(pd_plan* p) {
   void* ptrs[] = {p->lam,  p->gam,  p->igam, p->igam_s, p->tw,    p->Qf,    p->Qi,
                   p->mu,   p->spec, p->spec2, p->Udf,  p->Bdf,   p->w64a,  p->w64b,
                   p->dsc,  p->dflag, p->V,   p->Z,      p->dh,    p->Gf_hi, p->Gf_lo,
-                  p->Gi_hi, p->Gi_lo};
+                  p->Gi_hi, p->Gi_lo, const_cast<void*>(p->xf.chirp),
+                  const_cast<void*>(p->xf.bhat)};
   for (void* q : ptrs)
     if (q) cudaFree(q);
   if (p->hsc) cudaFreeHost(p->hsc);
@@ -162,11 +113,12 @@ void free_plan(pd_plan* p) {
 size_t NS(const pd_plan* p) { return (size_t)p->nt * p->S; }
 size_t cbytes(const pd_plan* p) { return p->fp64 ? sizeof(double2) : sizeof(float2); }
 
-FwdArgs fwd_base(const pd_plan* p) {
+FwdArgs fwd_base_impl(const pd_plan* p) {
   FwdArgs a;
   memset(&a, 0, sizeof(a));
   a.N = p->nt; a.logN = p->logN; a.nh = p->nh; a.S = p->S; a.TX = p->TX;
   a.sg = p->sg;
+  a.xf = p->xf;
   a.st = p->st; a.tb = p->tb;
   const double s = p->s_scale;
   const double kap[5] = {p->st.kc, p->st.kxl, p->st.kxu, p->st.kyl, p->st.kyu};
@@ -185,11 +137,12 @@ FwdArgs fwd_base(const pd_plan* p) {
   return a;
 }
 
-InvArgs inv_base(const pd_plan* p) {
+InvArgs inv_base_impl(const pd_plan* p) {
   InvArgs a;
   memset(&a, 0, sizeof(a));
   a.N = p->nt; a.logN = p->logN; a.nh = p->nh; a.S = p->S; a.TX = p->TX;
   a.sg = p->sg;
+  a.xf = p->xf;
   a.in = p->spec;
   a.igam = p->igam;
   a.tw = p->tw;
@@ -215,7 +168,7 @@ pd_status xform_dir(pd_plan* p, bool fwd) {
   return PD_OK;
 }
 
-TriArgs tri_args(const pd_plan* p, void* data) {
+TriArgs tri_args_impl(const pd_plan* p, void* data) {
   TriArgs ta;
   ta.nh = p->nh; ta.J = p->J; ta.n = p->tri_n; ta.S = p->sg.specS; ta.stride = p->tri_stride;
   ta.cl = p->tri_cl; ta.cd = p->tri_cd; ta.cu = p->tri_cu;
@@ -230,18 +183,18 @@ pd_status step_b(pd_plan* p) {
     CHK(xform_dir(p, true));
     data = p->spec2;
   }
-  LK(launch_tridiag(tri_args(p, data), p->fp64, p->stream));
+  LK(launch_tridiag(tri_args_impl(p, data), p->fp64, p->stream));
   if (p->xform) CHK(xform_dir(p, false));
   return PD_OK;
 }
 
 pd_status precond_into(pd_plan* p, const double* r, double* z) {
-  FwdArgs fa = fwd_base(p);
+  FwdArgs fa = fwd_base_impl(p);
   fa.mode = FWD_STANDALONE;
   fa.r64 = r;
   LK(launch_time_fwd(fa, p->fp64, p->stream));
   CHK(step_b(p));
-  InvArgs ia = inv_base(p);
+  InvArgs ia = inv_base_impl(p);
   ia.mode = INV_OUT64;
   ia.out64 = z;
   LK(launch_time_inv(ia, p->fp64, p->stream));
@@ -285,7 +238,7 @@ pd_status solve_stationary(pd_plan* p, const double* b, double* u, double tol, i
   pd_status st = PD_OK;
   for (;;) {
     CU(cudaMemsetAsync(p->dsc + 1, 0, sizeof(double), p->stream));
-    FwdArgs fa = fwd_base(p);
+    FwdArgs fa = fwd_base_impl(p);
     fa.mode = FWD_RESIDUAL;
     fa.norm2 = p->dsc + 1;
     if (p->fp64) { fa.U64 = u; fa.B64 = b; }
@@ -311,7 +264,7 @@ pd_status solve_stationary(pd_plan* p, const double* b, double* u, double tol, i
       break;
     }
     CHK(step_b(p));
-    InvArgs ia = inv_base(p);
+    InvArgs ia = inv_base_impl(p);
     if (p->fp64) { ia.mode = INV_UPDATE64; ia.out64 = u; }
     else { ia.mode = INV_UPDATE_DF; ia.Udf = p->Udf; ia.igam = p->igam_s; }
     LK(launch_time_inv(ia, p->fp64, p->stream));
@@ -450,9 +403,40 @@ pd_status solve_any(pd_plan* p, const double* b, double* u, int mode, double tol
   return set_err(p, PD_ERR_ARG, "unknown solver mode");
 }
 
+// in-place radix-2 FFT (forward: exp(-2 pi i / n)) on the host in FP64, used
+// to build the Bluestein filter
+void host_fft(std::vector<cd>& a) {
+  const size_t n = a.size();
+  for (size_t i = 1, j = 0; i < n; ++i) {
+    size_t bit = n >> 1;
+    for (; j & bit; bit >>= 1) j ^= bit;
+    j ^= bit;
+    if (i < j) std::swap(a[i], a[j]);
+  }
+  const double PI = 3.14159265358979323846;
+  for (size_t len = 2; len <= n; len <<= 1) {
+    for (size_t i = 0; i < n; i += len)
+      for (size_t k = 0; k < len / 2; ++k) {
+        const double th = -2.0 * PI * (double)k / (double)len;
+        const cd w(std::cos(th), std::sin(th));
+        const cd u = a[i + k], v = a[i + k + len / 2] * w;
+        a[i + k] = u + v;
+        a[i + k + len / 2] = u - v;
+      }
+  }
+}
+
 double hstep(int n, double L, int bc) { return L / (bc == PD_PERIODIC ? n : n + 1); }
 
 }  // namespace
+
+// internal helpers shared with the batched solver (pd_batch.cu)
+FwdArgs plan_fwd_args(const pd_plan* p) { return fwd_base_impl(p); }
+InvArgs plan_inv_args(const pd_plan* p) { return inv_base_impl(p); }
+TriArgs plan_tri_args(const pd_plan* p, void* data) { return tri_args_impl(p, data); }
+pd_status plan_create_internal(const pd_space* sp, int nt, double dt, double alpha, int scheme,
+                               double theta, int precision, void* stream, bool with_state,
+                               pd_plan** out);
 
 extern "C" {
 
@@ -480,7 +464,7 @@ pd_status pd_profile_iteration(pd_plan* p, const double* b, const double* u, int
   double acc[5] = {0, 0, 0, 0, 0};
   for (int r = 0; r < reps; ++r) {
     CU(cudaEventRecord(ev[0], p->stream));
-    FwdArgs fa = fwd_base(p);
+    FwdArgs fa = fwd_base_impl(p);
     fa.mode = FWD_RESIDUAL;
     fa.norm2 = p->dsc + 1;
     if (p->fp64) { fa.U64 = u64; fa.B64 = b; }
@@ -493,11 +477,11 @@ pd_status pd_profile_iteration(pd_plan* p, const double* b, const double* u, int
       data = p->spec2;
     }
     CU(cudaEventRecord(ev[2], p->stream));
-    LK(launch_tridiag(tri_args(p, data), p->fp64, p->stream));
+    LK(launch_tridiag(tri_args_impl(p, data), p->fp64, p->stream));
     CU(cudaEventRecord(ev[3], p->stream));
     if (p->xform) CHK(xform_dir(p, false));
     CU(cudaEventRecord(ev[4], p->stream));
-    InvArgs ia = inv_base(p);
+    InvArgs ia = inv_base_impl(p);
     if (p->fp64) { ia.mode = INV_UPDATE64; ia.out64 = u64; }
     else { ia.mode = INV_UPDATE_DF; ia.Udf = p->Udf; ia.igam = p->igam_s; }
     LK(launch_time_inv(ia, p->fp64, p->stream));
@@ -532,6 +516,16 @@ const char* pd_last_error(const pd_plan* plan) { return plan ? plan->msg : "null
 
 pd_status pd_plan_create(const pd_space* sp, int nt, double dt, double alpha, int scheme,
                          double theta, int precision, void* stream, pd_plan** out) {
+  return plan_create_internal(sp, nt, dt, alpha, scheme, theta, precision, stream, true, out);
+}
+
+}  // extern "C"
+
+// with_state = false skips the double-float iterate/right-hand side buffers
+// (the batched solver keeps those packed for all problems)
+pd_status plan_create_internal(const pd_space* sp, int nt, double dt, double alpha, int scheme,
+                               double theta, int precision, void* stream, bool with_state,
+                               pd_plan** out) {
   if (!out) return PD_ERR_ARG;
   *out = nullptr;
   if (!sp) return PD_ERR_ARG;
@@ -548,8 +542,15 @@ pd_status pd_plan_create(const pd_space* sp, int nt, double dt, double alpha, in
   if (scheme == PD_THETA && !(theta >= 0.0 && theta <= 1.0)) return PD_ERR_ARG;
   if (precision != PD_FP64 && precision != PD_MIXED) return PD_ERR_ARG;
   if (nt < 1) return PD_ERR_ARG;
-  const int nmax = precision == PD_MIXED ? 8192 : 4096;
-  if (!is_pow2(nt) || nt > nmax) return PD_ERR_UNSUPPORTED;
+  // power-of-two Nt: Stockham FFT (tile rows = Nt); otherwise Bluestein with
+  // M = 2^ceil(log2(2 Nt - 1)) rows; the tile must hold 2 columns at least
+  const int budget_rows = precision == PD_MIXED ? 4096 : 2048;
+  int Mb = 0;
+  if (!is_pow2(nt)) {
+    Mb = 1;
+    while (Mb < 2 * nt - 1) Mb <<= 1;
+  }
+  if ((Mb ? Mb : nt) > budget_rows) return PD_ERR_UNSUPPORTED;
   if (sp->dim == 2) {
     if (sp->bc_y != PD_DIRICHLET) return PD_ERR_UNSUPPORTED;
     if (sp->bc_x == PD_DIRICHLET && sp->ax != 0.0) return PD_ERR_UNSUPPORTED;
@@ -575,7 +576,7 @@ pd_status pd_plan_create(const pd_space* sp, int nt, double dt, double alpha, in
   // tile of TX columns x Nt rows: at most 32 KB of shared memory (16 complex
   // elements per thread), so several blocks stay resident per SM
   const int budget = p->fp64 ? 4096 : 8192;
-  p->TX = std::max(2, std::min(32, budget / nt));
+  p->TX = std::max(2, std::min(32, budget / (Mb ? Mb : nt)));
 
   // spatial stencil
   Stencil& st = p->st;
@@ -744,16 +745,42 @@ pd_status pd_plan_create(const pd_space* sp, int nt, double dt, double alpha, in
     igam[n] = std::pow(alpha, -(double)n / nt) / nt;
     igs[n] = igam[n] / p->s_scale;
   }
-  std::vector<cd> tw(nt);
-  for (int m = 0; m < nt; ++m) {
-    const double th = -2.0 * PI * m / nt;
+  const int ntw = Mb ? Mb : nt;
+  std::vector<cd> tw(ntw);
+  for (int m = 0; m < ntw; ++m) {
+    const double th = -2.0 * PI * m / ntw;
     tw[m] = cd(std::cos(th), std::sin(th));
+  }
+  std::vector<cd> chirp, bhat;
+  if (Mb) {
+    // w_n = exp(-i pi n^2 / Nt) with n^2 reduced mod 2 Nt for an accurate angle
+    chirp.resize(nt);
+    for (int n = 0; n < nt; ++n) {
+      const long long q = ((long long)n * n) % (2LL * nt);
+      const double th = -PI * (double)q / nt;
+      chirp[n] = cd(std::cos(th), std::sin(th));
+    }
+    bhat.assign(Mb, cd(0.0, 0.0));
+    bhat[0] = std::conj(chirp[0]);
+    for (int m = 1; m < nt; ++m) bhat[m] = bhat[Mb - m] = std::conj(chirp[m]);
+    host_fft(bhat);
+    for (cd& v : bhat) v /= (double)Mb;
+    p->xf.M = Mb;
+    p->xf.logM = ilog2(Mb);
   }
   pd_status s2 = upload_cplx(p, &p->lam, lam, p->fp64);
   if (s2 == PD_OK) s2 = upload_real(p, &p->gam, gam, p->fp64);
   if (s2 == PD_OK) s2 = upload_real(p, &p->igam, igam, p->fp64);
   if (s2 == PD_OK) s2 = upload_real(p, &p->igam_s, igs, p->fp64);
   if (s2 == PD_OK) s2 = upload_cplx(p, &p->tw, tw, p->fp64);
+  if (s2 == PD_OK && Mb) {
+    void* c = nullptr;
+    void* bh = nullptr;
+    s2 = upload_cplx(p, &c, chirp, p->fp64);
+    p->xf.chirp = c;
+    if (s2 == PD_OK) s2 = upload_cplx(p, &bh, bhat, p->fp64);
+    p->xf.bhat = bh;
+  }
   const size_t specb = (size_t)p->nh * p->sg.specS * cbytes(p);
   if (s2 == PD_OK) s2 = dalloc(p, &p->spec, specb);
   if (s2 == PD_OK && p->xform) s2 = dalloc(p, &p->spec2, specb);
@@ -768,8 +795,8 @@ pd_status pd_plan_create(const pd_space* sp, int nt, double dt, double alpha, in
                            (float*)p->spec, (const float*)p->Gi_hi, (const float*)p->Gi_lo);
     if (e != cudaSuccess) s2 = fail_cuda(p, e, "tensor map encoding");
   }
-  if (s2 == PD_OK && !p->fp64) s2 = dalloc(p, (void**)&p->Udf, NS(p) * sizeof(float2));
-  if (s2 == PD_OK && !p->fp64) s2 = dalloc(p, (void**)&p->Bdf, NS(p) * sizeof(float2));
+  if (s2 == PD_OK && !p->fp64 && with_state) s2 = dalloc(p, (void**)&p->Udf, NS(p) * sizeof(float2));
+  if (s2 == PD_OK && !p->fp64 && with_state) s2 = dalloc(p, (void**)&p->Bdf, NS(p) * sizeof(float2));
   if (s2 == PD_OK) s2 = dalloc(p, (void**)&p->dsc, NSC * sizeof(double));
   if (s2 == PD_OK) s2 = dalloc(p, (void**)&p->dflag, sizeof(int));
   if (s2 == PD_OK) {
@@ -783,6 +810,8 @@ pd_status pd_plan_create(const pd_space* sp, int nt, double dt, double alpha, in
   *out = p;
   return PD_OK;
 }
+
+extern "C" {
 
 pd_status pd_plan_destroy(pd_plan* plan) {
   if (!plan) return PD_ERR_ARG;

@@ -1,0 +1,397 @@
+// Batched ParaDiag-II: many independent 1D problems of uneven (nx, Nt, nu)
+// solved together by the stationary iteration (eq. 5.1), every kernel type
+// launched once per iteration over all problems.
+//
+// Problem i owns the slice [off_i, off_{i+1}) of the packed FP64 arrays b and
+// u ([Nt_i][nx_i] each).  Its Lemma 1 tables and its half spectrum come from an
+// internal per-problem plan; the double-float state is packed like b and u.
+// The time kernels and the tridiagonal kernels read per-problem argument
+// descriptors from device memory, and a work table maps every block (time
+// kernels) or tile (tridiagonal) to (problem, tile).  Problems are grouped by
+// the number of warps per tridiagonal system (W = 1 for nx <= 256, 2, 4, ...),
+// one launch per group.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "pd_plan.h"
+
+pd_status plan_create_internal(const pd_space* sp, int nt, double dt, double alpha, int scheme,
+                               double theta, int precision, void* stream, bool with_state,
+                               pd_plan** out);
+
+struct pd_batch {
+  int np = 0;
+  bool fp64 = false;
+  int band = 1;
+  cudaStream_t stream = nullptr;
+  std::vector<pd_plan*> plans;
+  std::vector<unsigned long long> off;
+  unsigned long long total = 0;
+  unsigned long long* d_off = nullptr;
+  float2* d_bscale = nullptr;   // per problem: s_i (b is stored as s_i b)
+  float2* d_one = nullptr;      // per problem: 1
+  float2* Udf = nullptr;
+  float2* Bdf = nullptr;
+  std::vector<FwdArgs> h_fwd;
+  std::vector<InvArgs> h_inv;
+  std::vector<TriArgs> h_tri;
+  FwdArgs* d_fwd = nullptr;
+  InvArgs* d_inv = nullptr;
+  TriArgs* d_tri = nullptr;
+  int2* d_work_time = nullptr;
+  int nblk_time = 0;
+  size_t smem_time = 0;
+  int ept = 4;
+  int2* d_work_tri[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
+  int ntiles_tri[5] = {0, 0, 0, 0, 0};
+  int mmax_tri[5] = {0, 0, 0, 0, 0};
+  double* d_norms = nullptr;    // [0, np): ||b_i||^2, [np, 2np): ||r_i||^2
+  double* h_norms = nullptr;    // pinned, 2np doubles + flag
+  int* d_flag = nullptr;
+  size_t bytes = 0;
+  unsigned long long launches = 0;
+  std::vector<double> relres;   // per problem, from the last residual evaluation
+  char msg[256] = {0};
+};
+
+namespace {
+
+constexpr int TB = 256;
+
+__device__ __forceinline__ int find_problem(const unsigned long long* off, int np,
+                                            unsigned long long e) {
+  int lo = 0, hi = np - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (off[mid] <= e) lo = mid;
+    else hi = mid - 1;
+  }
+  return lo;
+}
+
+// y = df(x) * scale[problem of the element]
+__global__ void k_batch_to_df(const double* __restrict__ x, float2* __restrict__ y,
+                              const unsigned long long* __restrict__ off,
+                              const float2* __restrict__ scale, int np, unsigned long long total) {
+  for (unsigned long long e = blockIdx.x * (unsigned long long)TB + threadIdx.x; e < total;
+       e += (unsigned long long)gridDim.x * TB) {
+    const int p = find_problem(off, np, e);
+    const float2 sc = scale[p];
+    const df v = df_mul(df_from_double(x[e]), df_make(sc.x, sc.y));
+    y[e] = make_float2(v.hi, v.lo);
+  }
+}
+
+// out[p] += ||x_p||^2, with a per-block shared accumulator for every problem
+__global__ void k_batch_norm2(const double* __restrict__ x, const unsigned long long* __restrict__ off,
+                              int np, unsigned long long total, double* out) {
+  extern __shared__ double acc[];
+  for (int i = threadIdx.x; i < np; i += TB) acc[i] = 0.0;
+  __syncthreads();
+  for (unsigned long long e = blockIdx.x * (unsigned long long)TB + threadIdx.x; e < total;
+       e += (unsigned long long)gridDim.x * TB) {
+    const int p = find_problem(off, np, e);
+    atomicAdd(&acc[p], x[e] * x[e]);
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < np; i += TB)
+    if (acc[i] != 0.0) atomicAdd(&out[i], acc[i]);
+}
+
+int grid_for(unsigned long long n) {
+  unsigned long long g = (n + TB - 1) / TB;
+  if (g > 152ull * 8) g = 152ull * 8;
+  return g == 0 ? 1 : (int)g;
+}
+
+pd_status berr(pd_batch* b, pd_status s, const char* what) {
+  if (b) snprintf(b->msg, sizeof(b->msg), "%s", what);
+  return s;
+}
+
+pd_status bcuda(pd_batch* b, cudaError_t e, const char* what) {
+  if (b) snprintf(b->msg, sizeof(b->msg), "%s: %s", what, cudaGetErrorString(e));
+  cudaGetLastError();
+  return e == cudaErrorMemoryAllocation ? PD_ERR_NOMEM : PD_ERR_CUDA;
+}
+
+#define BCU(call)                                          \
+  do {                                                     \
+    cudaError_t e_ = (call);                               \
+    if (e_ != cudaSuccess) return bcuda(b, e_, #call);     \
+  } while (0)
+#define BLK(call)                                          \
+  do {                                                     \
+    cudaError_t e_ = (call);                               \
+    ++b->launches;                                         \
+    if (e_ != cudaSuccess) return bcuda(b, e_, #call);     \
+  } while (0)
+
+template <typename T>
+pd_status balloc(pd_batch* b, T** p, size_t bytes) {
+  if (bytes == 0) bytes = 16;
+  cudaError_t e = cudaMalloc((void**)p, bytes);
+  if (e != cudaSuccess) {
+    *p = nullptr;
+    return bcuda(b, e, "cudaMalloc");
+  }
+  b->bytes += bytes;
+  return PD_OK;
+}
+
+void free_batch(pd_batch* b) {
+  if (!b) return;
+  for (pd_plan* p : b->plans)
+    if (p) pd_plan_destroy(p);
+  void* ptrs[] = {b->d_off, b->d_bscale, b->d_one, b->Udf,     b->Bdf,
+                  b->d_fwd, b->d_inv,    b->d_tri, b->d_work_time, b->d_norms, b->d_flag};
+  for (void* q : ptrs)
+    if (q) cudaFree(q);
+  for (int w = 0; w < 5; ++w)
+    if (b->d_work_tri[w]) cudaFree(b->d_work_tri[w]);
+  if (b->h_norms) cudaFreeHost(b->h_norms);
+  delete b;
+}
+
+int w_class(int n) { return n <= 256 ? 0 : n <= 512 ? 1 : n <= 1024 ? 2 : n <= 2048 ? 3 : 4; }
+
+}  // namespace
+
+extern "C" {
+
+pd_status pd_batch_create(const pd_problem* probs, int nprob, int precision, void* stream,
+                          pd_batch** out) {
+  if (!out) return PD_ERR_ARG;
+  *out = nullptr;
+  if (!probs || nprob < 1 || nprob > 4096) return PD_ERR_ARG;
+  if (precision != PD_FP64 && precision != PD_MIXED) return PD_ERR_ARG;
+  const int band0 = probs[0].scheme == PD_LEAPFROG ? 2 : 1;
+  for (int i = 0; i < nprob; ++i) {
+    const pd_problem& q = probs[i];
+    if (q.space.dim != 1 || q.space.bc_x != PD_DIRICHLET) return PD_ERR_UNSUPPORTED;
+    if ((q.scheme == PD_LEAPFROG ? 2 : 1) != band0) return PD_ERR_UNSUPPORTED;
+  }
+  pd_batch* b = new (std::nothrow) pd_batch();
+  if (!b) return PD_ERR_NOMEM;
+  b->np = nprob;
+  b->fp64 = precision == PD_FP64;
+  b->band = band0;
+  b->stream = (cudaStream_t)stream;
+  b->off.assign(nprob + 1, 0);
+  for (int i = 0; i < nprob; ++i) {
+    const pd_problem& q = probs[i];
+    pd_plan* p = nullptr;
+    pd_status s = plan_create_internal(&q.space, q.nt, q.dt, q.alpha, q.scheme, q.theta,
+                                       precision, stream, false, &p);
+    if (s != PD_OK) {
+      free_batch(b);
+      return s;
+    }
+    b->plans.push_back(p);
+    b->off[i + 1] = b->off[i] + (unsigned long long)q.nt * q.space.nx;
+  }
+  b->total = b->off[nprob];
+  const bool fp64 = b->fp64;
+  const size_t cb = fp64 ? sizeof(double2) : sizeof(float2);
+
+  // descriptors, time-kernel work table and tridiagonal work tables
+  std::vector<int2> wt;
+  std::vector<int2> wtri[5];
+  std::vector<float2> bscale(nprob), one(nprob, make_float2(1.f, 0.f));
+  b->h_fwd.resize(nprob);
+  b->h_inv.resize(nprob);
+  b->h_tri.resize(nprob);
+  for (int i = 0; i < nprob; ++i) {
+    pd_plan* p = b->plans[i];
+    const dfc sc = dfc_from(p->s_scale);
+    bscale[i] = make_float2(sc.hi, sc.lo);
+    b->h_fwd[i] = plan_fwd_args(p);
+    b->h_fwd[i].mode = FWD_RESIDUAL;
+    b->h_inv[i] = plan_inv_args(p);
+    b->h_tri[i] = plan_tri_args(p, p->spec);
+    const int tiles = ceil_div(p->S, p->TX);
+    for (int t = 0; t < tiles; ++t) wt.push_back(make_int2(i, t));
+    const int rows = p->xf.M ? p->xf.M : p->nt;
+    b->smem_time = std::max(b->smem_time, (size_t)rows * (p->TX / 2) * cb);
+    b->ept = std::max(b->ept, time_tile_ept(rows, p->TX));
+    const int wc = w_class(p->tri_n), W = 1 << wc;
+    const int SB = tridiag_batch_sb(W, fp64);
+    const long long systems = (long long)p->nh * p->J;
+    const int ttiles = (int)((systems + SB - 1) / SB);
+    for (int t = 0; t < ttiles; ++t) wtri[wc].push_back(make_int2(i, t));
+    b->mmax_tri[wc] = std::max(b->mmax_tri[wc], std::max(2, ceil_div(p->tri_n, 32 * W)));
+  }
+  b->nblk_time = (int)wt.size();
+  pd_status s = PD_OK;
+  auto up = [&](void** dst, const void* src, size_t bytes) {
+    if (s != PD_OK) return;
+    s = balloc(b, (char**)dst, bytes);
+    if (s == PD_OK) {
+      cudaError_t e = cudaMemcpy(*dst, src, bytes, cudaMemcpyHostToDevice);
+      if (e != cudaSuccess) s = bcuda(b, e, "cudaMemcpy");
+    }
+  };
+  up((void**)&b->d_off, b->off.data(), b->off.size() * sizeof(unsigned long long));
+  up((void**)&b->d_bscale, bscale.data(), nprob * sizeof(float2));
+  up((void**)&b->d_one, one.data(), nprob * sizeof(float2));
+  up((void**)&b->d_work_time, wt.data(), wt.size() * sizeof(int2));
+  for (int w = 0; w < 5; ++w) {
+    b->ntiles_tri[w] = (int)wtri[w].size();
+    if (!wtri[w].empty()) up((void**)&b->d_work_tri[w], wtri[w].data(), wtri[w].size() * sizeof(int2));
+  }
+  up((void**)&b->d_tri, b->h_tri.data(), nprob * sizeof(TriArgs));
+  if (s == PD_OK) s = balloc(b, &b->d_fwd, nprob * sizeof(FwdArgs));
+  if (s == PD_OK) s = balloc(b, &b->d_inv, nprob * sizeof(InvArgs));
+  if (s == PD_OK) s = balloc(b, &b->d_norms, 2 * nprob * sizeof(double));
+  if (s == PD_OK) s = balloc(b, &b->d_flag, sizeof(int));
+  if (s == PD_OK && !fp64) s = balloc(b, &b->Udf, b->total * sizeof(float2));
+  if (s == PD_OK && !fp64) s = balloc(b, &b->Bdf, b->total * sizeof(float2));
+  if (s == PD_OK) {
+    cudaError_t e = cudaMallocHost((void**)&b->h_norms, (2 * nprob + 1) * sizeof(double));
+    if (e != cudaSuccess) s = bcuda(b, e, "cudaMallocHost");
+  }
+  if (s != PD_OK) {
+    free_batch(b);
+    return s;
+  }
+  *out = b;
+  return PD_OK;
+}
+
+pd_status pd_batch_destroy(pd_batch* b) {
+  if (!b) return PD_ERR_ARG;
+  if (b->stream) cudaStreamSynchronize(b->stream);
+  else cudaDeviceSynchronize();
+  free_batch(b);
+  return PD_OK;
+}
+
+pd_status pd_batch_offsets(const pd_batch* b, unsigned long long* offsets) {
+  if (!b || !offsets) return PD_ERR_ARG;
+  for (int i = 0; i <= b->np; ++i) offsets[i] = b->off[i];
+  return PD_OK;
+}
+
+pd_status pd_batch_launches(const pd_batch* b, unsigned long long* count) {
+  if (!b || !count) return PD_ERR_ARG;
+  unsigned long long c = b->launches;
+  for (pd_plan* p : b->plans) c += p->launches;
+  *count = c;
+  return PD_OK;
+}
+
+const char* pd_batch_last_error(const pd_batch* b) { return b ? b->msg : "null batch"; }
+
+pd_status pd_batch_relres(const pd_batch* b, double* relres) {
+  if (!b || !relres) return PD_ERR_ARG;
+  for (int i = 0; i < b->np; ++i) relres[i] = i < (int)b->relres.size() ? b->relres[i] : 0.0;
+  return PD_OK;
+}
+
+pd_status pd_batch_build_rhs(pd_batch* b, const double* u0, const double* f, double* rhs) {
+  if (!b || !u0 || !rhs) return berr(b, PD_ERR_ARG, "null argument");
+  unsigned long long ou = 0, of = 0;
+  for (int i = 0; i < b->np; ++i) {
+    pd_plan* p = b->plans[i];
+    pd_status s = pd_build_rhs(p, u0 + ou, nullptr, f ? f + of : nullptr, rhs + b->off[i]);
+    if (s != PD_OK) return berr(b, s, "pd_build_rhs failed for a batch member");
+    ou += (unsigned long long)p->S;
+    of += (unsigned long long)(p->nt + 1) * p->S;
+  }
+  return PD_OK;
+}
+
+pd_status pd_batch_solve(pd_batch* b, const double* bvec, double* u, double tol, int maxit,
+                         int* iters, double* relres_max) {
+  if (!b || !bvec || !u) return berr(b, PD_ERR_ARG, "null argument");
+  if (!(tol >= 0.0) || maxit < 0) return berr(b, PD_ERR_ARG, "tol must be >= 0 and maxit >= 0");
+  const int np = b->np;
+  const bool fp64 = b->fp64;
+  cudaStream_t st = b->stream;
+  // descriptors for this call (FP64: they point into the caller's arrays)
+  for (int i = 0; i < np; ++i) {
+    FwdArgs& fa = b->h_fwd[i];
+    InvArgs& ia = b->h_inv[i];
+    fa.norm2 = b->d_norms + np + i;
+    if (fp64) {
+      fa.U64 = u + b->off[i];
+      fa.B64 = bvec + b->off[i];
+      ia.mode = INV_UPDATE64;
+      ia.out64 = u + b->off[i];
+    } else {
+      fa.Udf = b->Udf + b->off[i];
+      fa.Bdf = b->Bdf + b->off[i];
+      ia.mode = INV_UPDATE_DF;
+      ia.Udf = b->Udf + b->off[i];
+      ia.igam = b->plans[i]->igam_s;
+    }
+    ia.flag = b->d_flag;
+  }
+  BCU(cudaMemcpyAsync(b->d_fwd, b->h_fwd.data(), np * sizeof(FwdArgs), cudaMemcpyHostToDevice, st));
+  BCU(cudaMemcpyAsync(b->d_inv, b->h_inv.data(), np * sizeof(InvArgs), cudaMemcpyHostToDevice, st));
+  for (int i = 0; i < np; ++i) b->h_tri[i].flag = b->d_flag;
+  BCU(cudaMemcpyAsync(b->d_tri, b->h_tri.data(), np * sizeof(TriArgs), cudaMemcpyHostToDevice, st));
+  BCU(cudaMemsetAsync(b->d_norms, 0, 2 * np * sizeof(double), st));
+  BCU(cudaMemsetAsync(b->d_flag, 0, sizeof(int), st));
+  k_batch_norm2<<<grid_for(b->total), TB, np * sizeof(double), st>>>(bvec, b->d_off, np, b->total,
+                                                                      b->d_norms);
+  BLK(cudaGetLastError());
+  if (!fp64) {
+    k_batch_to_df<<<grid_for(b->total), TB, 0, st>>>(u, b->Udf, b->d_off, b->d_one, np, b->total);
+    BLK(cudaGetLastError());
+    k_batch_to_df<<<grid_for(b->total), TB, 0, st>>>(bvec, b->Bdf, b->d_off, b->d_bscale, np,
+                                                     b->total);
+    BLK(cudaGetLastError());
+  }
+  int it = 0;
+  double rmax = 0.0;
+  pd_status status = PD_OK;
+  for (;;) {
+    BCU(cudaMemsetAsync(b->d_norms + np, 0, np * sizeof(double), st));
+    BLK(launch_time_fwd_batch(b->d_fwd, b->d_work_time, b->nblk_time, b->band, b->smem_time, b->ept,
+                              fp64, st));
+    BCU(cudaMemcpyAsync(b->h_norms, b->d_norms, 2 * np * sizeof(double), cudaMemcpyDeviceToHost, st));
+    BCU(cudaMemcpyAsync(b->h_norms + 2 * np, b->d_flag, sizeof(int), cudaMemcpyDeviceToHost, st));
+    BCU(cudaStreamSynchronize(st));
+    int flag;
+    memcpy(&flag, b->h_norms + 2 * np, sizeof(int));
+    rmax = 0.0;
+    bool finite = true;
+    b->relres.assign(np, 0.0);
+    for (int i = 0; i < np; ++i) {
+      const double nb = std::sqrt(b->h_norms[i]);
+      const double nr = std::sqrt(b->h_norms[np + i]);
+      const double rel = nb > 0 ? nr / nb : (nr > 0 ? INFINITY : 0.0);
+      if (!std::isfinite(rel)) finite = false;
+      b->relres[i] = rel;
+      rmax = std::max(rmax, rel);
+    }
+    if (flag || !finite) {
+      status = berr(b, PD_ERR_NONFINITE, "non-finite value in the batched iteration");
+      break;
+    }
+    if (rmax <= tol) break;
+    if (it >= maxit) {
+      status = berr(b, PD_ERR_NOT_CONVERGED, "batched iteration reached maxit");
+      break;
+    }
+    for (int w = 0; w < 5; ++w)
+      if (b->ntiles_tri[w] > 0)
+        BLK(launch_tridiag_batch(b->d_tri, b->d_work_tri[w], b->ntiles_tri[w], 1 << w,
+                                 b->mmax_tri[w], fp64, st));
+    BLK(launch_time_inv_batch(b->d_inv, b->d_work_time, b->nblk_time, b->smem_time, b->ept, fp64,
+                              st));
+    ++it;
+  }
+  if (!fp64) BLK(launch_from_df(b->Udf, u, b->total, st));
+  BCU(cudaStreamSynchronize(st));
+  if (iters) *iters = it;
+  if (relres_max) *relres_max = rmax;
+  return status;
+}
+
+}  // extern "C"

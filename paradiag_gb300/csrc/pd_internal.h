@@ -37,8 +37,20 @@ PD_HD size_t spec_index(const SpecGeom& g, int k, int s) {
 }
 
 // Arguments of the forward time kernel (K1).
+// Time transform of length N: a power-of-two Stockham FFT when M == 0;
+// otherwise Bluestein's chirp-z form, two power-of-two FFTs of length
+// M >= 2N - 1 (logM) with the chirp w_n = exp(-i pi n^2 / N) and the
+// transformed filter bhat = FFT_M(conj chirp, wrapped) / M; tw then holds the
+// M-point twiddles.
+struct TimeXf {
+  int M, logM;
+  const void* chirp;
+  const void* bhat;
+};
+
 struct FwdArgs {
   int N, logN, nh, S, TX;
+  TimeXf xf;
   SpecGeom sg;
   Stencil st;
   TimeBand tb;
@@ -60,6 +72,7 @@ struct FwdArgs {
 // Arguments of the inverse time kernel (K3).
 struct InvArgs {
   int N, logN, nh, S, TX;
+  TimeXf xf;
   SpecGeom sg;
   int mode;                       // INV_UPDATE_DF, INV_OUT64, INV_UPDATE64
   const void* in;                 // half spectrum [nh][S]
@@ -100,6 +113,17 @@ cudaError_t launch_time_fwd(const FwdArgs& a, bool fp64, cudaStream_t st);
 cudaError_t launch_time_inv(const InvArgs& a, bool fp64, cudaStream_t st);
 cudaError_t launch_tridiag(const TriArgs& a, bool fp64, cudaStream_t st);
 cudaError_t launch_xform(const XformArgs& a, bool fp64, cudaStream_t st);
+
+// Batched launches: work[b] = (problem, tile) for block b; descs in device memory.
+int time_tile_ept(int N, int TX);
+cudaError_t launch_time_fwd_batch(const FwdArgs* descs, const int2* work, int nblocks, int band,
+                                  size_t smem, int ept, bool fp64, cudaStream_t st);
+cudaError_t launch_time_inv_batch(const InvArgs* descs, const int2* work, int nblocks,
+                                  size_t smem, int ept, bool fp64, cudaStream_t st);
+// tiles of SB = tridiag_batch_sb(W) systems of one W-warp class (W = 1: n <= 256)
+int tridiag_batch_sb(int W, bool fp64);
+cudaError_t launch_tridiag_batch(const TriArgs* descs, const int2* work, int ntiles, int W,
+                                 int mmax, bool fp64, cudaStream_t st);
 #include "pd_xform_tc.h"
 
 // Auxiliary kernels (pd_ops.cu)

@@ -132,7 +132,7 @@ extern "C" pd_status pd_apply_precond_noalloc(const pd_space* sp, int nt, double
   memset(&fa, 0, sizeof(fa));
   fa.N = nt; fa.logN = ilog2(nt); fa.nh = nh; fa.S = S;
   fa.sg.specS = S; fa.sg.nx = nx; fa.sg.nxp = nx;
-  fa.TX = std::max(2, std::min(32, 16384 / nt));
+  fa.TX = std::max(2, std::min(32, 8192 / nt));
   fa.st.dim = 1; fa.st.nx = nx; fa.st.ny = 1; fa.st.S = S; fa.st.bcx = PD_DIRICHLET;
   fa.st.bcy = PD_DIRICHLET; fa.st.kc = kc; fa.st.kxl = kl; fa.st.kxu = ku;
   fa.tb.band = band;

@@ -1,0 +1,61 @@
+// Internal plan structure (shared by pd_api.cu and pd_batch.cu).
+#pragma once
+#include "pd_internal.h"
+
+struct pd_plan {
+  pd_space sp;
+  int nt = 0, nh = 0, S = 0, logN = 0, TX = 0;
+  int scheme = 0;
+  double theta = 1.0, dt = 0.0, alpha = 0.0;
+  int precision = 0;
+  bool fp64 = false;
+  Stencil st;
+  TimeBand tb;
+  double s_scale = 1.0;
+  cudaStream_t stream = nullptr;
+  // spectrum layout (padded grid lines for x-transformed problems)
+  SpecGeom sg;
+  // step (b) layout
+  bool xform = false;
+  bool xform_tc = false;          // mixed path: tcgen05 x-transform
+  XformTc xtc_fwd, xtc_inv;
+  void* Gf_hi = nullptr;
+  void* Gf_lo = nullptr;
+  void* Gi_hi = nullptr;
+  void* Gi_lo = nullptr;
+  int J = 1, tri_n = 0, tri_stride = 1;
+  double tri_cl = 0, tri_cd = 0, tri_cu = 0;
+  // device tables
+  void* lam = nullptr;
+  void* gam = nullptr;
+  void* igam = nullptr;
+  void* igam_s = nullptr;
+  void* tw = nullptr;
+  TimeXf xf = {0, 0, nullptr, nullptr};   // Bluestein tables for non-power-of-two Nt
+  void* Qf = nullptr;
+  void* Qi = nullptr;
+  void* mu = nullptr;
+  // workspace
+  void* spec = nullptr;
+  void* spec2 = nullptr;
+  float2* Udf = nullptr;
+  float2* Bdf = nullptr;
+  double* w64a = nullptr;
+  double* w64b = nullptr;
+  double* dsc = nullptr;   // device scalars
+  int* dflag = nullptr;
+  double* hsc = nullptr;   // pinned host scalars
+  double* V = nullptr;
+  double* Z = nullptr;
+  double* dh = nullptr;
+  int gm_cap = 0;
+  pd_plan* adj = nullptr;
+  size_t bytes = 0;
+  unsigned long long launches = 0;
+  char msg[256] = {0};
+};
+
+// helpers implemented in pd_api.cu
+FwdArgs plan_fwd_args(const pd_plan* p);
+InvArgs plan_inv_args(const pd_plan* p);
+TriArgs plan_tri_args(const pd_plan* p, void* data);

@@ -44,8 +44,9 @@ PD_D void dft_r(C* v) {
 // Every butterfly is read into registers before the barrier and written after
 // it, so the pass runs in place.
 template <typename C, bool INV, int R, int BPT>
-PD_D void fft_pass(C* sm, int N, int lgTXc, int Ns, const C* tw) {
+PD_D void fft_pass(C* sm, int N, int lgTXc, int lgNs, const C* tw) {
   const int TXc = 1 << lgTXc;
+  const int Ns = 1 << lgNs;
   const int nb = (N / R) << lgTXc;
   const int step = N / (Ns * R);
   C v[BPT][R];
@@ -56,7 +57,7 @@ PD_D void fft_pass(C* sm, int N, int lgTXc, int Ns, const C* tw) {
     dst[t] = -1;
     if (b < nb) {
       const int c = b & (TXc - 1), j = b >> lgTXc;
-      const int q = j % Ns;
+      const int q = j & (Ns - 1);
 #pragma unroll
       for (int r = 0; r < R; ++r) {
         C x = sm[((j + r * (N / R)) << lgTXc) + c];
@@ -64,7 +65,7 @@ PD_D void fft_pass(C* sm, int N, int lgTXc, int Ns, const C* tw) {
         v[t][r] = x;
       }
       dft_r<C, INV, R>(v[t]);
-      dst[t] = (((j / Ns) * Ns * R + q) << lgTXc) + c;
+      dst[t] = (((((j >> lgNs) * R) << lgNs) + q) << lgTXc) + c;
     }
   }
   __syncthreads();
@@ -82,15 +83,47 @@ PD_D void fft_pass(C* sm, int N, int lgTXc, int Ns, const C* tw) {
 // maximum number of complex elements per thread (N * TXc <= EPT * TT).
 template <typename C, bool INV, int EPT>
 PD_D void fft_tile(C* sm, int N, int logN, int lgTXc, const C* tw) {
-  int Ns = 1;
+  int lgNs = 0;
   if (logN & 1) {
-    fft_pass<C, INV, 2, EPT / 2>(sm, N, lgTXc, Ns, tw);
-    Ns = 2;
+    fft_pass<C, INV, 2, EPT / 2>(sm, N, lgTXc, lgNs, tw);
+    lgNs = 1;
   }
   for (int p = 0; p < logN / 2; ++p) {
-    fft_pass<C, INV, 4, EPT / 4>(sm, N, lgTXc, Ns, tw);
-    Ns *= 4;
+    fft_pass<C, INV, 4, EPT / 4>(sm, N, lgTXc, lgNs, tw);
+    lgNs += 2;
   }
+}
+
+// Length-N DFT of TXc columns by Bluestein's algorithm: a_n = z_n w_n (zero
+// padded to M), A = FFT_M(a), A *= bhat, c = inverse FFT_M(A) (the 1/M is in
+// bhat), Z_k = w_k c_k.  CONJ computes conj(DFT(conj(z))), the unnormalised
+// inverse DFT.  Rows N..M-1 of the tile are scratch.
+template <typename C, bool CONJ, int EPT>
+PD_D void bluestein_tile(C* sm, int N, const TimeXf& xf, int lgTXc, const C* twM) {
+  const C* chirp = reinterpret_cast<const C*>(xf.chirp);
+  const C* bhat = reinterpret_cast<const C*>(xf.bhat);
+  const int tot = xf.M << lgTXc;
+  for (int e = threadIdx.x; e < tot; e += TT) {
+    const int n = e >> lgTXc;
+    C v = czero<C>();
+    if (n < N) {
+      v = sm[e];
+      if (CONJ) v = cconj(v);
+      v = cmul(v, chirp[n]);
+    }
+    sm[e] = v;
+  }
+  __syncthreads();
+  fft_tile<C, false, EPT>(sm, xf.M, xf.logM, lgTXc, twM);
+  for (int e = threadIdx.x; e < tot; e += TT) sm[e] = cmul(sm[e], bhat[e >> lgTXc]);
+  __syncthreads();
+  fft_tile<C, true, EPT>(sm, xf.M, xf.logM, lgTXc, twM);
+  for (int e = threadIdx.x; e < (N << lgTXc); e += TT) {
+    C v = cmul(sm[e], chirp[e >> lgTXc]);
+    if (CONJ) v = cconj(v);
+    sm[e] = v;
+  }
+  __syncthreads();
 }
 
 // ---------------------------------------------------------------------------
@@ -184,22 +217,25 @@ PD_D RowLd<V> load_row(const V* U, const FwdArgs& a, const ColGeom& g, int n) {
 // interior lanes come from the neighbouring lanes.  Must be executed by all
 // lanes of the warp (uniform control flow).
 PD_D void stencil_df(const FwdArgs& a, const ColGeom& g, const RowLd<float2>& L, int TX, df& Uc,
-                     df& KU) {
+                     Acc& KU) {
   const unsigned FULL = 0xffffffffu;
   const float lh = __shfl_up_sync(FULL, L.c.x, 1, TX);
   const float ll = __shfl_up_sync(FULL, L.c.y, 1, TX);
   const float rh = __shfl_down_sync(FULL, L.c.x, 1, TX);
   const float rl = __shfl_down_sync(FULL, L.c.y, 1, TX);
   Uc = df_make(L.c.x, L.c.y);
+  // neighbour values: from the lanes beside this one, or the loaded halo / wrap
+  // value (zero where the grid has no neighbour), so the sum has no branches
+  const bool sl = g.left == 1, sr = g.right == 1;
   Acc A = {0.f, 0.f};
   acc_add_prod(A, a.kap[0], L.c.x, L.c.y);
-  if (g.left == 1) acc_add_prod(A, a.kap[1], lh, ll);
-  else if (g.left == 2) acc_add_prod(A, a.kap[1], L.l.x, L.l.y);
-  if (g.right == 1) acc_add_prod(A, a.kap[2], rh, rl);
-  else if (g.right == 2) acc_add_prod(A, a.kap[2], L.r.x, L.r.y);
-  if (g.down) acc_add_prod(A, a.kap[3], L.d.x, L.d.y);
-  if (g.up) acc_add_prod(A, a.kap[4], L.u.x, L.u.y);
-  KU = acc_val(A);
+  acc_add_prod(A, a.kap[1], sl ? lh : L.l.x, sl ? ll : L.l.y);
+  acc_add_prod(A, a.kap[2], sr ? rh : L.r.x, sr ? rl : L.r.y);
+  if (a.st.dim == 2) {
+    acc_add_prod(A, a.kap[3], L.d.x, L.d.y);
+    acc_add_prod(A, a.kap[4], L.u.x, L.u.y);
+  }
+  KU = A;
 }
 
 PD_D void stencil_64(const FwdArgs& a, const ColGeom& g, const RowLd<double>& L, int TX,
@@ -236,7 +272,7 @@ PD_D T block_sum(T v, T* red) {
 // PREC 0: mixed (double-float residual, FP32 transform); PREC 1: FP64.
 // ---------------------------------------------------------------------------
 template <int PREC, int BAND, int EPT>
-__global__ void __launch_bounds__(TT, 3) k_time_fwd(FwdArgs a) {
+PD_D void time_fwd_body(const FwdArgs& a, int tile) {
   using R = typename std::conditional<PREC == 0, float, double>::type;
   using C = cplx_t<R>;
   extern __shared__ __align__(16) unsigned char smraw[];
@@ -246,7 +282,7 @@ __global__ void __launch_bounds__(TT, 3) k_time_fwd(FwdArgs a) {
 
   const int TX = a.TX, N = a.N, S = a.S;
   const int lgTX = ilog2(TX);
-  const int x0 = blockIdx.x * TX;
+  const int x0 = tile * TX;
   const int x = threadIdx.x & (TX - 1);
   const int chunk = threadIdx.x >> lgTX;
   const int nchunks = TT / TX;
@@ -276,12 +312,19 @@ __global__ void __launch_bounds__(TT, 3) k_time_fwd(FwdArgs a) {
   } else {
     const ColGeom g = col_geom(a.st, s, x, TX);
     if constexpr (PREC == 0) {
-      df U1 = df_make(0.f, 0.f), U2 = U1, K1 = U1, K2 = U1, U0, K0;
+      // rows before the first level are zero, so the carried terms need no checks
+      df U1 = df_make(0.f, 0.f), U2 = U1, U0;
+      Acc K1 = {0.f, 0.f}, K2 = K1, K0;
       if (BAND == 2) stencil_df(a, g, load_row(a.Udf, a, g, n_beg - 2), TX, U2, K2);
       stencil_df(a, g, load_row(a.Udf, a, g, n_beg - 1), TX, U1, K1);
       RowLd<float2> cur = load_row(a.Udf, a, g, n_beg);
       float2 bcur = (n_beg < N && g.valid) ? __ldg(&a.Bdf[(size_t)n_beg * S + s])
                                            : make_float2(0.f, 0.f);
+      // the c2 weights (theta, 1 - theta, 1/2, ...) negated once
+      dfc m0 = a.e2[0], m1 = a.e2[1], m2 = a.e2[2];
+      m0.hi = -m0.hi; m0.lo = -m0.lo;
+      m1.hi = -m1.hi; m1.lo = -m1.lo;
+      m2.hi = -m2.hi; m2.lo = -m2.lo;
       float part = 0.f;
       for (int i = 0; i < rpc; ++i) {
         const int n = n_beg + i;
@@ -291,30 +334,24 @@ __global__ void __launch_bounds__(TT, 3) k_time_fwd(FwdArgs a) {
                                 ? __ldg(&a.Bdf[(size_t)(n + 1) * S + s]) : make_float2(0.f, 0.f);
         stencil_df(a, g, cur, TX, U0, K0);  // uniform across the warp
         if (n < N) {
-          float v = 0.f;
-          if (g.valid) {
-            Acc A = {bcur.x, bcur.y};
-            acc_add(A, -U0.hi, -U0.lo);
-            if (BAND == 1) {
-              if (n >= 1) acc_add(A, U1.hi, U1.lo);
-            } else {
-              if (n >= 1) acc_add(A, 2.f * U1.hi, 2.f * U1.lo);
-              if (n >= 2) acc_add(A, -U2.hi, -U2.lo);
-            }
-            dfc m0 = a.e2[0];
-            m0.hi = -m0.hi; m0.lo = -m0.lo;
-            acc_add_prod(A, m0, K0.hi, K0.lo);
-            if (BAND == 1) {
-              if (n >= 1) { dfc m1 = a.e2[1]; m1.hi = -m1.hi; m1.lo = -m1.lo; acc_add_prod(A, m1, K1.hi, K1.lo); }
-            } else {
-              if (n >= 2) { dfc m2 = a.e2[2]; m2.hi = -m2.hi; m2.lo = -m2.lo; acc_add_prod(A, m2, K2.hi, K2.lo); }
-            }
-            const df r = acc_val(A);
-            part = fmaf(r.hi, r.hi, part);
-            const float gm = gam[n];
-            v = fmaf(r.hi, gm, r.lo * gm);
+          // r' = s b - U_n + U_{n-1} - c2[0] (sK)U_n - c2[1] (sK)U_{n-1}        (theta)
+          // r' = s b - U_n + 2 U_{n-1} - U_{n-2} - c2[0] (sK)U_n - c2[2] (sK)U_{n-2} (leap-frog)
+          Acc A = {bcur.x, bcur.y};
+          acc_add(A, -U0.hi, -U0.lo);
+          if (BAND == 1) {
+            acc_add(A, U1.hi, U1.lo);
+            acc_add_prod(A, m0, K0.s, K0.e);
+            acc_add_prod(A, m1, K1.s, K1.e);
+          } else {
+            acc_add(A, 2.f * U1.hi, 2.f * U1.lo);
+            acc_add(A, -U2.hi, -U2.lo);
+            acc_add_prod(A, m0, K0.s, K0.e);
+            acc_add_prod(A, m2, K2.s, K2.e);
           }
-          smr[n * TX + x] = v;
+          const df r = acc_val(A);
+          part = fmaf(r.hi, r.hi, part);
+          const float gm = gam[n];
+          smr[n * TX + x] = g.valid ? fmaf(r.hi, gm, r.lo * gm) : 0.f;
         }
         U2 = U1; K2 = K1; U1 = U0; K1 = K0;
         cur = nxt;
@@ -361,27 +398,49 @@ __global__ void __launch_bounds__(TT, 3) k_time_fwd(FwdArgs a) {
 
   const int lgTXc = lgTX - 1;
   const int TXc = TX / 2;
-  fft_tile<C, false, EPT>(sm, N, a.logN, lgTXc, reinterpret_cast<const C*>(a.tw));
+  if (a.xf.M == 0) fft_tile<C, false, EPT>(sm, N, a.logN, lgTXc, reinterpret_cast<const C*>(a.tw));
+  else bluestein_tile<C, false, EPT>(sm, N, a.xf, lgTXc, reinterpret_cast<const C*>(a.tw));
 
   C* out = reinterpret_cast<C*>(a.out);
   const R half = (R)0.5;
-  for (int item = threadIdx.x; item < a.nh * TXc; item += TT) {
-    const int c = item & (TXc - 1), k = item >> lgTXc;
-    const C Zk = sm[(k << lgTXc) + c];
-    const C Zm = cconj(sm[(((N - k) & (N - 1)) << lgTXc) + c]);
-    const C A = cscale(cadd(Zk, Zm), half);
-    const C B = cscale(cmul_mi(csub(Zk, Zm)), half);
+  {
+    // TT is a multiple of TXc: every item of this thread has the same column
+    // pair, so the (padded) spectrum offsets are computed once
+    const int c = threadIdx.x & (TXc - 1);
     const int sa = x0 + 2 * c;
-    if (sa < S) out[spec_index(a.sg, k, sa)] = A;
-    if (sa + 1 < S) out[spec_index(a.sg, k, sa + 1)] = B;
+    const bool va = sa < S, vb = sa + 1 < S;
+    const size_t oa = va ? spec_index(a.sg, 0, sa) : 0;
+    const size_t ob = vb ? spec_index(a.sg, 0, sa + 1) : 0;
+    const size_t kst = (size_t)a.sg.specS;
+    for (int k = threadIdx.x >> lgTXc; k < a.nh; k += TT >> lgTXc) {
+      const C Zk = sm[(k << lgTXc) + c];
+      const C Zm = cconj(sm[((k == 0 ? 0 : N - k) << lgTXc) + c]);
+      const C A = cscale(cadd(Zk, Zm), half);
+      const C B = cscale(cmul_mi(csub(Zk, Zm)), half);
+      if (va) out[k * kst + oa] = A;
+      if (vb) out[k * kst + ob] = B;
+    }
   }
+}
+
+// single problem: block b owns tile b; batch: the work table maps each block to
+// (problem, tile) and the arguments come from the per-problem descriptors
+template <int PREC, int BAND, int EPT>
+__global__ void __launch_bounds__(TT, 3) k_time_fwd(FwdArgs a) {
+  time_fwd_body<PREC, BAND, EPT>(a, blockIdx.x);
+}
+template <int PREC, int BAND, int EPT>
+__global__ void __launch_bounds__(TT, 3) k_time_fwd_batch(const FwdArgs* __restrict__ descs,
+                                                          const int2* __restrict__ work) {
+  const int2 w = work[blockIdx.x];
+  time_fwd_body<PREC, BAND, EPT>(descs[w.x], w.y);
 }
 
 // ---------------------------------------------------------------------------
 // K3: inverse real FFT along t + Gamma^{-1}/Nt + write or update.
 // ---------------------------------------------------------------------------
 template <int PREC, int EPT>
-__global__ void __launch_bounds__(TT, 3) k_time_inv(InvArgs a) {
+PD_D void time_inv_body(const InvArgs& a, int tile) {
   using R = typename std::conditional<PREC == 0, float, double>::type;
   using C = cplx_t<R>;
   extern __shared__ __align__(16) unsigned char smraw[];
@@ -390,47 +449,113 @@ __global__ void __launch_bounds__(TT, 3) k_time_inv(InvArgs a) {
 
   const int TX = a.TX, N = a.N, S = a.S;
   const int lgTX = ilog2(TX), lgTXc = lgTX - 1, TXc = TX / 2;
-  const int x0 = blockIdx.x * TX;
+  const int x0 = tile * TX;
   const C* in = reinterpret_cast<const C*>(a.in);
-  for (int item = threadIdx.x; item < a.nh * TXc; item += TT) {
-    const int c = item & (TXc - 1), k = item >> lgTXc;
+  {
+    const int c = threadIdx.x & (TXc - 1);
     const int sa = x0 + 2 * c;
-    C A = czero<C>(), B = czero<C>();
-    if (sa < S) A = in[spec_index(a.sg, k, sa)];
-    if (sa + 1 < S) B = in[spec_index(a.sg, k, sa + 1)];
-    if (k == 0 || 2 * k == N) { A.y = 0; B.y = 0; }
-    sm[(k << lgTXc) + c] = mk(A.x - B.y, A.y + B.x);            // A + i B
-    if (k > 0 && 2 * k < N)
-      sm[((N - k) << lgTXc) + c] = mk(A.x + B.y, B.x - A.y);    // conj(A) + i conj(B)
+    const bool va = sa < S, vb = sa + 1 < S;
+    const size_t oa = va ? spec_index(a.sg, 0, sa) : 0;
+    const size_t ob = vb ? spec_index(a.sg, 0, sa + 1) : 0;
+    const size_t kst = (size_t)a.sg.specS;
+    const int k0 = threadIdx.x >> lgTXc, kstep = TT >> lgTXc;
+    constexpr int U = 8;  // loads in flight per thread
+    for (int kb = k0; kb < a.nh; kb += U * kstep) {
+      C A[U], B[U];
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const int k = kb + u * kstep;
+        A[u] = czero<C>();
+        B[u] = czero<C>();
+        if (k < a.nh) {
+          if (va) A[u] = in[k * kst + oa];
+          if (vb) B[u] = in[k * kst + ob];
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const int k = kb + u * kstep;
+        if (k >= a.nh) break;
+        C Au = A[u], Bu = B[u];
+        if (k == 0 || 2 * k == N) { Au.y = 0; Bu.y = 0; }
+        sm[(k << lgTXc) + c] = mk(Au.x - Bu.y, Au.y + Bu.x);            // A + i B
+        if (k > 0 && 2 * k < N)
+          sm[((N - k) << lgTXc) + c] = mk(Au.x + Bu.y, Bu.x - Au.y);    // conj(A) + i conj(B)
+      }
+    }
   }
   __syncthreads();
-  fft_tile<C, true, EPT>(sm, N, a.logN, lgTXc, reinterpret_cast<const C*>(a.tw));
+  if (a.xf.M == 0) fft_tile<C, true, EPT>(sm, N, a.logN, lgTXc, reinterpret_cast<const C*>(a.tw));
+  else bluestein_tile<C, true, EPT>(sm, N, a.xf, lgTXc, reinterpret_cast<const C*>(a.tw));
 
   const R* ig = reinterpret_cast<const R*>(a.igam);
   bool bad = false;
-  for (int e = threadIdx.x; e < N * TX; e += TT) {
-    const int n = e >> lgTX, x = e & (TX - 1);
+  {
+    // every element of this thread lies in the same column x (TT % TX == 0)
+    const int x = threadIdx.x & (TX - 1);
     const int s = x0 + x;
-    if (s >= S) continue;
-    const R dz = smr[e] * ig[n];
-    const size_t idx = (size_t)n * S + s;
-    if constexpr (PREC == 0) {
-      if (!isfinite(dz)) bad = true;
-      if (a.mode == INV_UPDATE_DF) {
-        const float2 u = a.Udf[idx];
-        df t = two_sum(u.x, dz);
-        t = fast_two_sum(t.hi, t.lo + u.y);
-        a.Udf[idx] = make_float2(t.hi, t.lo);
-      } else {
-        a.out64[idx] = double_from_float(dz);
+    const int n0 = threadIdx.x >> lgTX, nstep = TT >> lgTX;
+    constexpr int U = 8;
+    if (s < S) {
+      for (int nb = n0; nb < N; nb += U * nstep) {
+        if constexpr (PREC == 0) {
+          float2 uv[U];
+          if (a.mode == INV_UPDATE_DF) {
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+              const int n = nb + u * nstep;
+              uv[u] = n < N ? a.Udf[(size_t)n * S + s] : make_float2(0.f, 0.f);
+            }
+          }
+#pragma unroll
+          for (int u = 0; u < U; ++u) {
+            const int n = nb + u * nstep;
+            if (n >= N) break;
+            const float dz = smr[n * TX + x] * ig[n];
+            if (!isfinite(dz)) bad = true;
+            const size_t idx = (size_t)n * S + s;
+            if (a.mode == INV_UPDATE_DF) {
+              df t = two_sum(uv[u].x, dz);
+              t = fast_two_sum(t.hi, t.lo + uv[u].y);
+              a.Udf[idx] = make_float2(t.hi, t.lo);
+            } else {
+              a.out64[idx] = double_from_float(dz);
+            }
+          }
+        } else {
+          double uv[U];
+          if (a.mode == INV_UPDATE64) {
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+              const int n = nb + u * nstep;
+              uv[u] = n < N ? a.out64[(size_t)n * S + s] : 0.0;
+            }
+          }
+#pragma unroll
+          for (int u = 0; u < U; ++u) {
+            const int n = nb + u * nstep;
+            if (n >= N) break;
+            const double dz = smr[n * TX + x] * ig[n];
+            if (!isfinite(dz)) bad = true;
+            const size_t idx = (size_t)n * S + s;
+            a.out64[idx] = (a.mode == INV_UPDATE64) ? uv[u] + dz : dz;
+          }
+        }
       }
-    } else {
-      if (!isfinite(dz)) bad = true;
-      if (a.mode == INV_UPDATE64) a.out64[idx] += dz;
-      else a.out64[idx] = dz;
     }
   }
   if (bad && a.flag != nullptr) atomicOr(a.flag, 1);
+}
+
+template <int PREC, int EPT>
+__global__ void __launch_bounds__(TT, 3) k_time_inv(InvArgs a) {
+  time_inv_body<PREC, EPT>(a, blockIdx.x);
+}
+template <int PREC, int EPT>
+__global__ void __launch_bounds__(TT, 3) k_time_inv_batch(const InvArgs* __restrict__ descs,
+                                                         const int2* __restrict__ work) {
+  const int2 w = work[blockIdx.x];
+  time_inv_body<PREC, EPT>(descs[w.x], w.y);
 }
 
 // complex elements per thread needed by a tile of N x TX/2 columns
@@ -441,7 +566,8 @@ inline int ept_for(int N, int TX) {
 
 template <int PREC, int BAND, int EPT>
 cudaError_t launch_fwd_e(const FwdArgs& a, cudaStream_t st) {
-  const size_t smem = (size_t)a.N * (a.TX / 2) * (PREC == 0 ? sizeof(float2) : sizeof(double2));
+  const int rows = a.xf.M ? a.xf.M : a.N;
+  const size_t smem = (size_t)rows * (a.TX / 2) * (PREC == 0 ? sizeof(float2) : sizeof(double2));
   auto kern = k_time_fwd<PREC, BAND, EPT>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
@@ -452,7 +578,7 @@ cudaError_t launch_fwd_e(const FwdArgs& a, cudaStream_t st) {
 
 template <int PREC, int BAND>
 cudaError_t launch_fwd_t(const FwdArgs& a, cudaStream_t st) {
-  switch (ept_for(a.N, a.TX)) {
+  switch (ept_for(a.xf.M ? a.xf.M : a.N, a.TX)) {
     case 4: return launch_fwd_e<PREC, BAND, 4>(a, st);
     case 8: return launch_fwd_e<PREC, BAND, 8>(a, st);
     case 16: return launch_fwd_e<PREC, BAND, 16>(a, st);
@@ -462,7 +588,8 @@ cudaError_t launch_fwd_t(const FwdArgs& a, cudaStream_t st) {
 
 template <int PREC, int EPT>
 cudaError_t launch_inv_e(const InvArgs& a, cudaStream_t st) {
-  const size_t smem = (size_t)a.N * (a.TX / 2) * (PREC == 0 ? sizeof(float2) : sizeof(double2));
+  const int rows = a.xf.M ? a.xf.M : a.N;
+  const size_t smem = (size_t)rows * (a.TX / 2) * (PREC == 0 ? sizeof(float2) : sizeof(double2));
   auto kern = k_time_inv<PREC, EPT>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
@@ -473,7 +600,7 @@ cudaError_t launch_inv_e(const InvArgs& a, cudaStream_t st) {
 
 template <int PREC>
 cudaError_t launch_inv_t(const InvArgs& a, cudaStream_t st) {
-  switch (ept_for(a.N, a.TX)) {
+  switch (ept_for(a.xf.M ? a.xf.M : a.N, a.TX)) {
     case 4: return launch_inv_e<PREC, 4>(a, st);
     case 8: return launch_inv_e<PREC, 8>(a, st);
     case 16: return launch_inv_e<PREC, 16>(a, st);
@@ -491,4 +618,57 @@ cudaError_t launch_time_fwd(const FwdArgs& a, bool fp64, cudaStream_t st) {
 
 cudaError_t launch_time_inv(const InvArgs& a, bool fp64, cudaStream_t st) {
   return fp64 ? launch_inv_t<1>(a, st) : launch_inv_t<0>(a, st);
+}
+
+namespace {
+template <int PREC, int BAND>
+cudaError_t launch_fwd_batch_t(const FwdArgs* descs, const int2* work, int nblocks, size_t smem,
+                               int ept, cudaStream_t st) {
+#define PD_FWD_B(E)                                                                              \
+  {                                                                                              \
+    auto kern = k_time_fwd_batch<PREC, BAND, E>;                                                 \
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem); \
+    if (e != cudaSuccess) return e;                                                              \
+    kern<<<nblocks, TT, smem, st>>>(descs, work);                                                \
+    return cudaGetLastError();                                                                   \
+  }
+  if (ept <= 4) PD_FWD_B(4)
+  if (ept <= 8) PD_FWD_B(8)
+  PD_FWD_B(16)
+#undef PD_FWD_B
+}
+template <int PREC>
+cudaError_t launch_inv_batch_t(const InvArgs* descs, const int2* work, int nblocks, size_t smem,
+                               int ept, cudaStream_t st) {
+#define PD_INV_B(E)                                                                              \
+  {                                                                                              \
+    auto kern = k_time_inv_batch<PREC, E>;                                                       \
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem); \
+    if (e != cudaSuccess) return e;                                                              \
+    kern<<<nblocks, TT, smem, st>>>(descs, work);                                                \
+    return cudaGetLastError();                                                                   \
+  }
+  if (ept <= 4) PD_INV_B(4)
+  if (ept <= 8) PD_INV_B(8)
+  PD_INV_B(16)
+#undef PD_INV_B
+}
+}  // namespace
+
+int time_tile_ept(int N, int TX) { return ept_for(N, TX); }
+
+cudaError_t launch_time_fwd_batch(const FwdArgs* descs, const int2* work, int nblocks, int band,
+                                  size_t smem, int ept, bool fp64, cudaStream_t st) {
+  if (nblocks == 0) return cudaSuccess;
+  if (fp64) return band == 2 ? launch_fwd_batch_t<1, 2>(descs, work, nblocks, smem, ept, st)
+                             : launch_fwd_batch_t<1, 1>(descs, work, nblocks, smem, ept, st);
+  return band == 2 ? launch_fwd_batch_t<0, 2>(descs, work, nblocks, smem, ept, st)
+                   : launch_fwd_batch_t<0, 1>(descs, work, nblocks, smem, ept, st);
+}
+
+cudaError_t launch_time_inv_batch(const InvArgs* descs, const int2* work, int nblocks,
+                                  size_t smem, int ept, bool fp64, cudaStream_t st) {
+  if (nblocks == 0) return cudaSuccess;
+  return fp64 ? launch_inv_batch_t<1>(descs, work, nblocks, smem, ept, st)
+              : launch_inv_batch_t<0>(descs, work, nblocks, smem, ept, st);
 }

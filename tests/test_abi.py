@@ -46,7 +46,8 @@ def test_plan_create_rejects_bad_arguments_without_gpu():
     assert pd.pd_plan_create(sp, 16, 0.1, 0.0, 0, 1.0, 1, None)[0] == pd.PD_ERR_ARG     # alpha = 0
     assert pd.pd_plan_create(sp, 16, 0.1, 1.5, 0, 1.0, 1, None)[0] == pd.PD_ERR_ARG     # alpha > 1
     assert pd.pd_plan_create(sp, 16, -0.1, 0.1, 0, 1.0, 1, None)[0] == pd.PD_ERR_ARG    # dt < 0
-    assert pd.pd_plan_create(sp, 12, 0.1, 0.1, 0, 1.0, 1, None)[0] == pd.PD_ERR_UNSUPPORTED
+    # Nt = 5000 needs a Bluestein length of 16384 > 4096 rows
+    assert pd.pd_plan_create(sp, 5000, 0.1, 0.1, 0, 1.0, 1, None)[0] == pd.PD_ERR_UNSUPPORTED
     assert pd.pd_plan_create(sp, 16, 0.1, 0.1, 7, 1.0, 1, None)[0] == pd.PD_ERR_ARG     # scheme
     sp2 = pd.pd_space(2, 15, 15, 0.1, 1.0, 0.0, 0, 0, 1.0, 1.0)   # Dirichlet x with advection
     assert pd.pd_plan_create(sp2, 16, 0.1, 0.1, 0, 1.0, 1, None)[0] == pd.PD_ERR_UNSUPPORTED

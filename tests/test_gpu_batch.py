@@ -1,0 +1,98 @@
+"""Parity of the batched solve (many 1D problems of uneven nx, Nt and nu in one
+set of launches) with the oracle's sequential time stepping, problem by
+problem.  Tolerance 1e-10 relative per problem (the solver stops at a relative
+residual of 1e-11 mixed / 1e-12 FP64)."""
+import numpy as np
+import pytest
+
+import workloads as W
+from helpers import dev, host, lib_ready, rel2
+from oracle import operators as O
+from oracle import stepping as S
+
+pytestmark = pytest.mark.gpu
+
+
+def _problems(count, seed, pow2=True):
+    return W.batched(count=count, seed=seed, pow2=pow2)
+
+
+@pytest.mark.parametrize("prec", ["mixed", "fp64"])
+def test_batch_matches_sequential(prec):
+    pd = lib_ready()
+    import torch
+    wls = _problems(10, 4242)
+    # make sure every tridiagonal class (nx <= 256, <= 512, <= 1024) is present
+    wls.append(W.ade1d(nx=1023, nt=64, nu=1e-3, scheme=W.BE, alpha=1e-2, seed=9, name="big"))
+    wls.append(W.ade1d(nx=400, nt=32, nu=1e-2, scheme=W.BE, alpha=1e-2, seed=10, name="mid"))
+    wls.append(W.ade1d(nx=63, nt=1024, nu=1e-1, scheme=W.BE, alpha=1e-2, seed=11, name="long"))
+    probs = [dict(space=dict(nx=w.problem.space.nx, nu=w.problem.space.nu, ax=w.problem.space.ax),
+                  nt=w.problem.nt, dt=w.problem.dt, alpha=w.problem.alpha, scheme=0, theta=1.0)
+             for w in wls]
+    batch = pd.Batch(probs, pd.PD_MIXED if prec == "mixed" else pd.PD_FP64)
+    u0 = np.concatenate([w.u0 for w in wls])
+    f = np.concatenate([w.f.reshape(-1) for w in wls])
+    b = batch.build_rhs(dev(u0), dev(f))
+    l0 = batch.launches()
+    # The mixed path forms the residual in double-float (48-bit significand), so
+    # member i bottoms out near 2^-48 (1 + dt_i ||K_i||_inf) relative; it runs to
+    # that floor (tol 0, 12 sweeps) and every member must be within 16x of it.
+    # The FP64 path stops at 1e-12.
+    if prec == "mixed":
+        u, it, rel = batch.solve(b, tol=0.0, maxit=12, allow_not_converged=True)
+        for i, w in enumerate(wls):
+            K = O.stencil(w.problem.space)
+            floor = 2.0 ** -48 * (1.0 + w.problem.dt * abs(K).sum(axis=1).max())
+            assert batch.relres()[i] <= 16 * floor, (i, batch.relres()[i], floor)
+    else:
+        u, it, rel = batch.solve(b, tol=1e-12, maxit=30)
+        assert rel <= 1e-12
+    # one launch per kernel type per sweep: time forward, 3 tridiagonal classes, time inverse
+    per_sweep = 1 + 3 + 1
+    assert batch.launches() - l0 <= per_sweep * it + 1 + 3 + 2
+    uh = host(u)
+    bh = host(b)
+    off = batch.offsets
+    for i, w in enumerate(wls):
+        pb = w.problem
+        bref = O.build_rhs(pb, w.u0, None, w.f)
+        assert rel2(bh[off[i]:off[i + 1]].reshape(pb.nt, -1), bref) <= 1e-14
+        uref = S.solve_sequential(pb, bref)
+        err = rel2(uh[off[i]:off[i + 1]].reshape(pb.nt, -1), uref)
+        assert err <= 1e-10, (i, pb.space.nx, pb.nt, err)
+    batch.close()
+
+
+def test_batch_rejects_mixed_bands_and_2d():
+    pd = lib_ready()
+    base = dict(space=dict(nx=31, nu=0.1), nt=16, dt=1 / 16, alpha=0.1, theta=1.0)
+    with pytest.raises(pd.PDError) as ei:
+        pd.Batch([dict(base, scheme=0), dict(base, scheme=3)])
+    assert ei.value.status == pd.PD_ERR_UNSUPPORTED
+
+
+@pytest.mark.parametrize("prec", ["mixed", "fp64"])
+def test_batch_integer_nt_reading(prec):
+    # Nt drawn uniformly from the integers (non-powers of two use Bluestein)
+    pd = lib_ready()
+    wls = W.batched(count=8, seed=777, pow2=False)
+    assert any((w.problem.nt & (w.problem.nt - 1)) != 0 for w in wls)
+    probs = [dict(space=dict(nx=w.problem.space.nx, nu=w.problem.space.nu, ax=w.problem.space.ax),
+                  nt=w.problem.nt, dt=w.problem.dt, alpha=w.problem.alpha, scheme=0, theta=1.0)
+             for w in wls]
+    batch = pd.Batch(probs, pd.PD_MIXED if prec == "mixed" else pd.PD_FP64)
+    u0 = np.concatenate([w.u0 for w in wls])
+    f = np.concatenate([w.f.reshape(-1) for w in wls])
+    b = batch.build_rhs(dev(u0), dev(f))
+    if prec == "mixed":
+        u, it, rel = batch.solve(b, tol=0.0, maxit=12, allow_not_converged=True)
+    else:
+        u, it, rel = batch.solve(b, tol=1e-12, maxit=30)
+    uh = host(u)
+    off = batch.offsets
+    for i, w in enumerate(wls):
+        pb = w.problem
+        uref = S.solve_sequential(pb, O.build_rhs(pb, w.u0, None, w.f))
+        err = rel2(uh[off[i]:off[i + 1]].reshape(pb.nt, -1), uref)
+        assert err <= 1e-10, (i, pb.space.nx, pb.nt, err)
+    batch.close()

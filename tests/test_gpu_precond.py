@@ -38,8 +38,18 @@ CASES = {
     "1d_nt2": P(nx=20, nt=2, scheme=W.CN, alpha=0.05),
     "1d_nx1": P(nx=1, nt=8),
     "1d_nx600_multiwarp": P(nx=600, nu=1e-3, ax=1.0, nt=8, alpha=1e-2),
+    "1d_nx400_two_warps": P(nx=400, nu=1e-2, ax=1.0, nt=32, alpha=1e-2),
+    "1d_nx511_two_warps": P(nx=511, nu=1e-2, ax=1.0, nt=16, alpha=1e-2),
     "1d_nx1023_multiwarp": P(nx=1023, nu=1.0, nt=16, T=2.0, scheme=W.LEAPFROG, alpha=0.1),
     "1d_nt512": P(nx=33, nu=0.05, ax=1.0, nt=512, alpha=1e-2),
+    # non-power-of-two Nt (Bluestein): even, odd, prime, and the largest class
+    "1d_bluestein_nt12": P(nx=31, nu=0.05, ax=1.0, nt=12, alpha=1e-2),
+    "1d_bluestein_nt3": P(nx=17, nu=0.05, ax=1.0, nt=3, scheme=W.CN, alpha=1e-2),
+    "1d_bluestein_nt63_cn": P(nx=40, nu=0.02, ax=1.0, nt=63, scheme=W.CN, alpha=1e-3),
+    "1d_bluestein_nt97_leapfrog": P(nx=63, nu=1.0, nt=97, T=2.0, scheme=W.LEAPFROG, alpha=0.1),
+    "1d_bluestein_nt1000": P(nx=47, nu=0.05, ax=1.0, nt=1000, alpha=1e-2),
+    "2d_bluestein_cn_periodic_20x9x20": P(dim=2, nx=20, ny=9, nu=1e-2, ax=1.0, ay=0.5,
+                                          bcx=W.PERIODIC, nt=20, scheme=W.CN, alpha=1e-3),
     "2d_cn_periodic_x_15x13x16": P(dim=2, nx=15, ny=13, nu=1e-2, ax=1.0, ay=0.5,
                                     bcx=W.PERIODIC, nt=16, scheme=W.CN, alpha=1e-3),
     "2d_be_dirichlet_sym_11x9x8": P(dim=2, nx=11, ny=9, nu=1.0, nt=8, alpha=1e-2),
