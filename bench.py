@@ -42,6 +42,7 @@ def parse():
     ap.add_argument("--no-check", action="store_true", help="skip the oracle error check")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU baseline leg")
     ap.add_argument("--small", action="store_true", help="a small case (profiling runs)")
+    ap.add_argument("--no-batch", action="store_true", help="skip the batched-workload leg")
     return ap.parse_args()
 
 
@@ -170,6 +171,47 @@ def cpu_oracle_sample(w, seconds_hint=20.0):
     desc = (f"oracle sequential time stepping (sparse LU per step) on the first {nts} of "
             f"{pb.nt} time steps of the same grid, {reps} repetitions, {el:.1f} s")
     return rate, desc, 1
+
+
+def batched_leg(pd, torch, dev, args):
+    """64 independent 1D advection-diffusion problems (nx uniform on 63..1023,
+    Nt uniform on 32..1024, nu = 10^U[-3,-1], BE, alpha = 1e-2) solved together
+    to a relative residual of 1e-10 per problem (mixed path)."""
+    import numpy as np
+    import workloads as W
+    wls = W.batched(count=64, pow2=False)
+    probs = [dict(space=dict(nx=w.problem.space.nx, nu=w.problem.space.nu,
+                             ax=w.problem.space.ax),
+                  nt=w.problem.nt, dt=w.problem.dt, alpha=w.problem.alpha, scheme=0, theta=1.0)
+             for w in wls]
+    batch = pd.Batch(probs, pd.PD_MIXED)
+    u0 = torch.from_numpy(np.concatenate([w.u0 for w in wls])).to(dev)
+    f = torch.from_numpy(np.concatenate([w.f.reshape(-1) for w in wls])).to(dev)
+    b = batch.build_rhs(u0, f)
+    u = torch.zeros_like(b)
+    for _ in range(3):
+        u.zero_()
+        batch.solve(b, u, tol=1e-10, maxit=40)
+    stream = torch.cuda.current_stream()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    k = max(1, min(args.steps, 10))
+    l0 = batch.launches()
+    e0.record(stream)
+    for _ in range(k):
+        u.zero_()
+        _, it, rel = batch.solve(b, u, tol=1e-10, maxit=40)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / k
+    out = {"workload": "64 x 1D advection-diffusion, nx ~ U{63..1023}, Nt ~ U{32..1024} "
+                       "(Bluestein for non-powers of two), BE, alpha = 1e-2",
+           "unknowns": int(batch.total), "ms_per_step": ms,
+           "value": batch.total / (ms / 1e3), "unit": UNIT, "iterations": it,
+           "relres_max": rel, "residual_tol": 1e-10,
+           "gpu_launches": (batch.launches() - l0) // k}
+    batch.close()
+    return out
 
 
 def run_reference(args):
@@ -313,6 +355,10 @@ def main():
     ms64 = max_over_ranks(ws, e0.elapsed_time(e1) / k64, dev)
     kms64 = plan64.profile_iteration(b, torch.zeros_like(b), reps=1)
 
+    batched = None
+    if not args.no_batch:
+        batched = batched_leg(pd, torch, dev, args)
+
     err = err64 = None
     if rank == 0 and not args.no_check:
         from oracle import operators as O
@@ -347,6 +393,7 @@ def main():
                "kernel_ms": {k: v["ms"] for k, v in per_kernel.items()},
                "kernel_GBps": {k: v["GB/s"] for k, v in per_kernel.items()},
                "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
+               "batched": batched,
                "gpu_launches": launches}
         print(json.dumps(out), flush=True)
     plan.close()

@@ -64,7 +64,9 @@ typedef enum { PD_STATIONARY = 0, PD_GMRES = 1 } pd_mode;
  * differences, eq. 2.2b in 1D; the 5-point stencil in 2D).  Dirichlet
  * directions hold n interior points with h = L/(n+1); periodic directions hold
  * n points with h = L/n.  dim = 2 requires bc_y = PD_DIRICHLET, and either
- * bc_x = PD_PERIODIC or (bc_x = PD_DIRICHLET and ax = 0). */
+ * bc_x = PD_PERIODIC or (bc_x = PD_DIRICHLET and ax = 0).  The direction
+ * solved by tridiagonal systems in step (b) (y in 2D, x for a Dirichlet 1D
+ * problem) holds at most 4096 points (PD_ERR_UNSUPPORTED otherwise). */
 typedef struct {
   int dim;        /* 1 or 2 */
   int nx, ny;     /* grid points per direction (ny ignored for dim = 1) */

@@ -557,6 +557,9 @@ pd_status plan_create_internal(const pd_space* sp, int nt, double dt, double alp
   }
   const long long S = (long long)sp->nx * (sp->dim == 2 ? sp->ny : 1);
   if (S > (1LL << 30) || S * nt > (1LL << 40)) return PD_ERR_ARG;
+  // length of the tridiagonal direction of step (b)
+  const int tri_len = sp->dim == 2 ? sp->ny : (sp->bc_x == PD_PERIODIC ? 1 : sp->nx);
+  if (tri_len > TRI_NMAX) return PD_ERR_UNSUPPORTED;
 
   pd_plan* p = new (std::nothrow) pd_plan();
   if (!p) return PD_ERR_NOMEM;
@@ -573,9 +576,9 @@ pd_status plan_create_internal(const pd_space* sp, int nt, double dt, double alp
   p->precision = precision;
   p->fp64 = precision == PD_FP64;
   p->stream = (cudaStream_t)stream;
-  // tile of TX columns x Nt rows: at most 32 KB of shared memory (16 complex
-  // elements per thread), so several blocks stay resident per SM
-  const int budget = p->fp64 ? 4096 : 8192;
+  // tile of TX columns x Nt rows: at most 16 KB of shared memory (8 complex
+  // elements per thread, <= 64 registers), so four blocks stay resident per SM
+  const int budget = p->fp64 ? 2048 : 4096;
   p->TX = std::max(2, std::min(32, budget / (Mb ? Mb : nt)));
 
   // spatial stencil

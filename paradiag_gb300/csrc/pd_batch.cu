@@ -8,8 +8,8 @@
 // The time kernels and the tridiagonal kernels read per-problem argument
 // descriptors from device memory, and a work table maps every block (time
 // kernels) or tile (tridiagonal) to (problem, tile).  Problems are grouped by
-// the number of warps per tridiagonal system (W = 1 for nx <= 256, 2, 4, ...),
-// one launch per group.
+// the number of lanes per tridiagonal system (a power of two, chunks of at
+// most 32 rows in FP32 and 16 in FP64), one launch per group.
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
@@ -45,10 +45,10 @@ struct pd_batch {
   int2* d_work_time = nullptr;
   int nblk_time = 0;
   size_t smem_time = 0;
+  size_t smem_inv = 0;
   int ept = 4;
-  int2* d_work_tri[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
-  int ntiles_tri[5] = {0, 0, 0, 0, 0};
-  int mmax_tri[5] = {0, 0, 0, 0, 0};
+  int2* d_work_tri[TRI_NCLASS] = {};
+  int ntiles_tri[TRI_NCLASS] = {};
   double* d_norms = nullptr;    // [0, np): ||b_i||^2, [np, 2np): ||r_i||^2
   double* h_norms = nullptr;    // pinned, 2np doubles + flag
   int* d_flag = nullptr;
@@ -151,13 +151,11 @@ void free_batch(pd_batch* b) {
                   b->d_fwd, b->d_inv,    b->d_tri, b->d_work_time, b->d_norms, b->d_flag};
   for (void* q : ptrs)
     if (q) cudaFree(q);
-  for (int w = 0; w < 5; ++w)
+  for (int w = 0; w < TRI_NCLASS; ++w)
     if (b->d_work_tri[w]) cudaFree(b->d_work_tri[w]);
   if (b->h_norms) cudaFreeHost(b->h_norms);
   delete b;
 }
-
-int w_class(int n) { return n <= 256 ? 0 : n <= 512 ? 1 : n <= 1024 ? 2 : n <= 2048 ? 3 : 4; }
 
 }  // namespace
 
@@ -200,7 +198,7 @@ pd_status pd_batch_create(const pd_problem* probs, int nprob, int precision, voi
 
   // descriptors, time-kernel work table and tridiagonal work tables
   std::vector<int2> wt;
-  std::vector<int2> wtri[5];
+  std::vector<int2> wtri[TRI_NCLASS];
   std::vector<float2> bscale(nprob), one(nprob, make_float2(1.f, 0.f));
   b->h_fwd.resize(nprob);
   b->h_inv.resize(nprob);
@@ -216,14 +214,14 @@ pd_status pd_batch_create(const pd_problem* probs, int nprob, int precision, voi
     const int tiles = ceil_div(p->S, p->TX);
     for (int t = 0; t < tiles; ++t) wt.push_back(make_int2(i, t));
     const int rows = p->xf.M ? p->xf.M : p->nt;
-    b->smem_time = std::max(b->smem_time, (size_t)rows * (p->TX / 2) * cb);
+    b->smem_time = std::max(b->smem_time, (size_t)rows * (p->TX / 2 + 1) * cb);
+    b->smem_inv = std::max(b->smem_inv, time_inv_smem(p->nt, rows, p->TX, fp64, true));
     b->ept = std::max(b->ept, time_tile_ept(rows, p->TX));
-    const int wc = w_class(p->tri_n), W = 1 << wc;
-    const int SB = tridiag_batch_sb(W, fp64);
+    const int wc = tridiag_class(p->tri_n, fp64);
+    const int SB = tridiag_batch_sb(wc, fp64);
     const long long systems = (long long)p->nh * p->J;
     const int ttiles = (int)((systems + SB - 1) / SB);
     for (int t = 0; t < ttiles; ++t) wtri[wc].push_back(make_int2(i, t));
-    b->mmax_tri[wc] = std::max(b->mmax_tri[wc], std::max(2, ceil_div(p->tri_n, 32 * W)));
   }
   b->nblk_time = (int)wt.size();
   pd_status s = PD_OK;
@@ -239,7 +237,7 @@ pd_status pd_batch_create(const pd_problem* probs, int nprob, int precision, voi
   up((void**)&b->d_bscale, bscale.data(), nprob * sizeof(float2));
   up((void**)&b->d_one, one.data(), nprob * sizeof(float2));
   up((void**)&b->d_work_time, wt.data(), wt.size() * sizeof(int2));
-  for (int w = 0; w < 5; ++w) {
+  for (int w = 0; w < TRI_NCLASS; ++w) {
     b->ntiles_tri[w] = (int)wtri[w].size();
     if (!wtri[w].empty()) up((void**)&b->d_work_tri[w], wtri[w].data(), wtri[w].size() * sizeof(int2));
   }
@@ -379,11 +377,10 @@ pd_status pd_batch_solve(pd_batch* b, const double* bvec, double* u, double tol,
       status = berr(b, PD_ERR_NOT_CONVERGED, "batched iteration reached maxit");
       break;
     }
-    for (int w = 0; w < 5; ++w)
+    for (int w = 0; w < TRI_NCLASS; ++w)
       if (b->ntiles_tri[w] > 0)
-        BLK(launch_tridiag_batch(b->d_tri, b->d_work_tri[w], b->ntiles_tri[w], 1 << w,
-                                 b->mmax_tri[w], fp64, st));
-    BLK(launch_time_inv_batch(b->d_inv, b->d_work_time, b->nblk_time, b->smem_time, b->ept, fp64,
+        BLK(launch_tridiag_batch(b->d_tri, b->d_work_tri[w], b->ntiles_tri[w], w, fp64, st));
+    BLK(launch_time_inv_batch(b->d_inv, b->d_work_time, b->nblk_time, b->smem_inv, b->ept, fp64,
                               st));
     ++it;
   }

@@ -116,14 +116,20 @@ cudaError_t launch_xform(const XformArgs& a, bool fp64, cudaStream_t st);
 
 // Batched launches: work[b] = (problem, tile) for block b; descs in device memory.
 int time_tile_ept(int N, int TX);
+size_t time_inv_smem(int N, int rows, int TX, bool fp64, bool upd);
 cudaError_t launch_time_fwd_batch(const FwdArgs* descs, const int2* work, int nblocks, int band,
                                   size_t smem, int ept, bool fp64, cudaStream_t st);
 cudaError_t launch_time_inv_batch(const InvArgs* descs, const int2* work, int nblocks,
-                                  size_t smem, int ept, bool fp64, cudaStream_t st);
-// tiles of SB = tridiag_batch_sb(W) systems of one W-warp class (W = 1: n <= 256)
-int tridiag_batch_sb(int W, bool fp64);
-cudaError_t launch_tridiag_batch(const TriArgs* descs, const int2* work, int ntiles, int W,
-                                 int mmax, bool fp64, cudaStream_t st);
+                                  size_t smem, int ept, bool fp64, cudaStream_t st);  // smem: time_inv_smem
+// Tridiagonal systems of length n <= TRI_NMAX are solved by 2^cls lanes each,
+// cls = tridiag_class(n, fp64) < TRI_NCLASS; a batch groups its problems by
+// class and launches tiles of tridiag_batch_sb(cls) systems of one problem.
+constexpr int TRI_NMAX = 4096;
+constexpr int TRI_NCLASS = 9;
+int tridiag_class(int n, bool fp64);
+int tridiag_batch_sb(int cls, bool fp64);
+cudaError_t launch_tridiag_batch(const TriArgs* descs, const int2* work, int ntiles, int cls,
+                                 bool fp64, cudaStream_t st);
 #include "pd_xform_tc.h"
 
 // Auxiliary kernels (pd_ops.cu)

@@ -16,6 +16,15 @@ namespace {
 
 constexpr int TT = 256;  // threads per block
 
+template <int BYTES>
+PD_D void cp_async(void* dst, const void* src) {
+  const uint32_t d = (uint32_t)__cvta_generic_to_shared(dst);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], %2;" ::"r"(d), "l"(src), "n"(BYTES) : "memory");
+}
+PD_D void cp_async_commit_wait_all() {
+  asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;" ::: "memory");
+}
+
 template <typename C, bool INV>
 PD_D C twid(const C* tw, int idx) {
   C w = tw[idx];
@@ -284,6 +293,10 @@ PD_D void time_fwd_body(const FwdArgs& a, int tile) {
   const int lgTX = ilog2(TX);
   const int x0 = tile * TX;
   const int x = threadIdx.x & (TX - 1);
+  // the transform's twiddle table, staged in shared memory after the tile
+  const int rows_fft = a.xf.M ? a.xf.M : N;
+  C* stw = sm + (size_t)rows_fft * (TX / 2);
+  for (int i = threadIdx.x; i < rows_fft; i += TT) stw[i] = reinterpret_cast<const C*>(a.tw)[i];
   const int chunk = threadIdx.x >> lgTX;
   const int nchunks = TT / TX;
   const int rpc = (N + nchunks - 1) / nchunks;
@@ -293,21 +306,31 @@ PD_D void time_fwd_body(const FwdArgs& a, int tile) {
   double nrm = 0.0;
 
   if (a.mode == FWD_STANDALONE) {
-    for (int i = 0; i < rpc; ++i) {
-      const int n = n_beg + i;
-      if (n >= N) break;
-      R v = 0;
-      if (s < S) {
-        const double rv = a.r64[(size_t)n * S + s];
-        if constexpr (PREC == 0) {
-          const df r = df_from_double(rv);
-          const float g = gam[n];
-          v = fmaf(r.hi, g, r.lo * g);
-        } else {
-          v = gam[n] * rv;
-        }
+    // every element of the tile: consecutive threads take consecutive columns,
+    // eight loads in flight per thread
+    constexpr int U = 8;
+    const int n0 = threadIdx.x >> lgTX, nstep = TT >> lgTX;
+    for (int nb = n0; nb < N; nb += U * nstep) {
+      double rv[U];
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const int n = nb + u * nstep;
+        rv[u] = (n < N && s < S) ? a.r64[(size_t)n * S + s] : 0.0;
       }
-      smr[n * TX + x] = v;
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const int n = nb + u * nstep;
+        if (n >= N) break;
+        R v;
+        if constexpr (PREC == 0) {
+          const df r = df_from_double(rv[u]);
+          const float gg = gam[n];
+          v = fmaf(r.hi, gg, r.lo * gg);
+        } else {
+          v = gam[n] * rv[u];
+        }
+        smr[n * TX + x] = v;
+      }
     }
   } else {
     const ColGeom g = col_geom(a.st, s, x, TX);
@@ -317,9 +340,13 @@ PD_D void time_fwd_body(const FwdArgs& a, int tile) {
       Acc K1 = {0.f, 0.f}, K2 = K1, K0;
       if (BAND == 2) stencil_df(a, g, load_row(a.Udf, a, g, n_beg - 2), TX, U2, K2);
       stencil_df(a, g, load_row(a.Udf, a, g, n_beg - 1), TX, U1, K1);
+      // two rows of loads in flight ahead of the row being computed
       RowLd<float2> cur = load_row(a.Udf, a, g, n_beg);
       float2 bcur = (n_beg < N && g.valid) ? __ldg(&a.Bdf[(size_t)n_beg * S + s])
                                            : make_float2(0.f, 0.f);
+      RowLd<float2> nx1 = load_row(a.Udf, a, g, 1 < rpc ? n_beg + 1 : -1);
+      float2 bnx1 = (1 < rpc && n_beg + 1 < N && g.valid)
+                        ? __ldg(&a.Bdf[(size_t)(n_beg + 1) * S + s]) : make_float2(0.f, 0.f);
       // the c2 weights (theta, 1 - theta, 1/2, ...) negated once
       dfc m0 = a.e2[0], m1 = a.e2[1], m2 = a.e2[2];
       m0.hi = -m0.hi; m0.lo = -m0.lo;
@@ -328,10 +355,9 @@ PD_D void time_fwd_body(const FwdArgs& a, int tile) {
       float part = 0.f;
       for (int i = 0; i < rpc; ++i) {
         const int n = n_beg + i;
-        // prefetch the next row before computing this one
-        const RowLd<float2> nxt = load_row(a.Udf, a, g, i + 1 < rpc ? n + 1 : -1);
-        const float2 bnxt = (i + 1 < rpc && n + 1 < N && g.valid)
-                                ? __ldg(&a.Bdf[(size_t)(n + 1) * S + s]) : make_float2(0.f, 0.f);
+        const RowLd<float2> nxt = load_row(a.Udf, a, g, i + 2 < rpc ? n + 2 : -1);
+        const float2 bnxt = (i + 2 < rpc && n + 2 < N && g.valid)
+                                ? __ldg(&a.Bdf[(size_t)(n + 2) * S + s]) : make_float2(0.f, 0.f);
         stencil_df(a, g, cur, TX, U0, K0);  // uniform across the warp
         if (n < N) {
           // r' = s b - U_n + U_{n-1} - c2[0] (sK)U_n - c2[1] (sK)U_{n-1}        (theta)
@@ -354,8 +380,10 @@ PD_D void time_fwd_body(const FwdArgs& a, int tile) {
           smr[n * TX + x] = g.valid ? fmaf(r.hi, gm, r.lo * gm) : 0.f;
         }
         U2 = U1; K2 = K1; U1 = U0; K1 = K0;
-        cur = nxt;
-        bcur = bnxt;
+        cur = nx1;
+        bcur = bnx1;
+        nx1 = nxt;
+        bnx1 = bnxt;
       }
       nrm = (double)part * a.rscale2;
     } else {
@@ -398,8 +426,8 @@ PD_D void time_fwd_body(const FwdArgs& a, int tile) {
 
   const int lgTXc = lgTX - 1;
   const int TXc = TX / 2;
-  if (a.xf.M == 0) fft_tile<C, false, EPT>(sm, N, a.logN, lgTXc, reinterpret_cast<const C*>(a.tw));
-  else bluestein_tile<C, false, EPT>(sm, N, a.xf, lgTXc, reinterpret_cast<const C*>(a.tw));
+  if (a.xf.M == 0) fft_tile<C, false, EPT>(sm, N, a.logN, lgTXc, stw);
+  else bluestein_tile<C, false, EPT>(sm, N, a.xf, lgTXc, stw);
 
   C* out = reinterpret_cast<C*>(a.out);
   const R half = (R)0.5;
@@ -426,11 +454,11 @@ PD_D void time_fwd_body(const FwdArgs& a, int tile) {
 // single problem: block b owns tile b; batch: the work table maps each block to
 // (problem, tile) and the arguments come from the per-problem descriptors
 template <int PREC, int BAND, int EPT>
-__global__ void __launch_bounds__(TT, 3) k_time_fwd(FwdArgs a) {
+__global__ void __launch_bounds__(TT, PREC == 0 ? 4 : 2) k_time_fwd(FwdArgs a) {
   time_fwd_body<PREC, BAND, EPT>(a, blockIdx.x);
 }
 template <int PREC, int BAND, int EPT>
-__global__ void __launch_bounds__(TT, 3) k_time_fwd_batch(const FwdArgs* __restrict__ descs,
+__global__ void __launch_bounds__(TT, PREC == 0 ? 4 : 2) k_time_fwd_batch(const FwdArgs* __restrict__ descs,
                                                           const int2* __restrict__ work) {
   const int2 w = work[blockIdx.x];
   time_fwd_body<PREC, BAND, EPT>(descs[w.x], w.y);
@@ -451,6 +479,9 @@ PD_D void time_inv_body(const InvArgs& a, int tile) {
   const int lgTX = ilog2(TX), lgTXc = lgTX - 1, TXc = TX / 2;
   const int x0 = tile * TX;
   const C* in = reinterpret_cast<const C*>(a.in);
+  const int rows_fft = a.xf.M ? a.xf.M : N;
+  C* stw = sm + (size_t)rows_fft * TXc;
+  for (int i = threadIdx.x; i < rows_fft; i += TT) stw[i] = reinterpret_cast<const C*>(a.tw)[i];
   {
     const int c = threadIdx.x & (TXc - 1);
     const int sa = x0 + 2 * c;
@@ -485,8 +516,8 @@ PD_D void time_inv_body(const InvArgs& a, int tile) {
     }
   }
   __syncthreads();
-  if (a.xf.M == 0) fft_tile<C, true, EPT>(sm, N, a.logN, lgTXc, reinterpret_cast<const C*>(a.tw));
-  else bluestein_tile<C, true, EPT>(sm, N, a.xf, lgTXc, reinterpret_cast<const C*>(a.tw));
+  if (a.xf.M == 0) fft_tile<C, true, EPT>(sm, N, a.logN, lgTXc, stw);
+  else bluestein_tile<C, true, EPT>(sm, N, a.xf, lgTXc, stw);
 
   const R* ig = reinterpret_cast<const R*>(a.igam);
   bool bad = false;
@@ -548,11 +579,11 @@ PD_D void time_inv_body(const InvArgs& a, int tile) {
 }
 
 template <int PREC, int EPT>
-__global__ void __launch_bounds__(TT, 3) k_time_inv(InvArgs a) {
+__global__ void __launch_bounds__(TT, PREC == 0 ? 4 : 2) k_time_inv(InvArgs a) {
   time_inv_body<PREC, EPT>(a, blockIdx.x);
 }
 template <int PREC, int EPT>
-__global__ void __launch_bounds__(TT, 3) k_time_inv_batch(const InvArgs* __restrict__ descs,
+__global__ void __launch_bounds__(TT, PREC == 0 ? 4 : 2) k_time_inv_batch(const InvArgs* __restrict__ descs,
                                                          const int2* __restrict__ work) {
   const int2 w = work[blockIdx.x];
   time_inv_body<PREC, EPT>(descs[w.x], w.y);
@@ -567,7 +598,7 @@ inline int ept_for(int N, int TX) {
 template <int PREC, int BAND, int EPT>
 cudaError_t launch_fwd_e(const FwdArgs& a, cudaStream_t st) {
   const int rows = a.xf.M ? a.xf.M : a.N;
-  const size_t smem = (size_t)rows * (a.TX / 2) * (PREC == 0 ? sizeof(float2) : sizeof(double2));
+  const size_t smem = (size_t)rows * (a.TX / 2 + 1) * (PREC == 0 ? sizeof(float2) : sizeof(double2));
   auto kern = k_time_fwd<PREC, BAND, EPT>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
@@ -586,10 +617,18 @@ cudaError_t launch_fwd_t(const FwdArgs& a, cudaStream_t st) {
   }
 }
 
+// shared memory of the time kernels: the FFT tile and the twiddle table
+inline size_t inv_smem(int N, int rows, int TX, bool fp64, bool upd) {
+  (void)N;
+  (void)upd;
+  return (size_t)rows * (TX / 2 + 1) * (fp64 ? sizeof(double2) : sizeof(float2));
+}
+
 template <int PREC, int EPT>
 cudaError_t launch_inv_e(const InvArgs& a, cudaStream_t st) {
   const int rows = a.xf.M ? a.xf.M : a.N;
-  const size_t smem = (size_t)rows * (a.TX / 2) * (PREC == 0 ? sizeof(float2) : sizeof(double2));
+  const bool upd = PREC == 0 ? a.mode == INV_UPDATE_DF : a.mode == INV_UPDATE64;
+  const size_t smem = inv_smem(a.N, rows, a.TX, PREC == 1, upd);
   auto kern = k_time_inv<PREC, EPT>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
@@ -656,6 +695,9 @@ cudaError_t launch_inv_batch_t(const InvArgs* descs, const int2* work, int nbloc
 }  // namespace
 
 int time_tile_ept(int N, int TX) { return ept_for(N, TX); }
+size_t time_inv_smem(int N, int rows, int TX, bool fp64, bool upd) {
+  return inv_smem(N, rows, TX, fp64, upd);
+}
 
 cudaError_t launch_time_fwd_batch(const FwdArgs* descs, const int2* work, int nblocks, int band,
                                   size_t smem, int ept, bool fp64, cudaStream_t st) {

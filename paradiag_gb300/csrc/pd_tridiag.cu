@@ -3,48 +3,83 @@
 // tridiagonal K of one direction (1D problems, or y after the x-eigentransform
 // of 2D problems, where the shift also carries the x-eigenvalue mu_j).
 //
-// Partitioned solver, no pivoting.  W warps cooperate on one system of length
-// n; lane G (0 <= G < 32W) owns the m = max(2, ceil(n/32W)) <= 8 consecutive
-// rows i0 = G m .. i0+m-1.  Each lane eliminates its interior rows in
-// registers, expressing them as z_i = Y_i + P_i f_G + Q_i g_G in terms of its
-// first (f_G) and last (g_G) unknown; the first and last rows then form a
-// tridiagonal reduced system of 64W unknowns (f_0, g_0, f_1, g_1, ...), solved
-// by parallel cyclic reduction in shared memory.  Rows are scaled by 1/d so
-// the diagonal is one; padding rows (i >= n) are identity rows with z = 0.
+// Partitioned solver, no pivoting.  L lanes cooperate on one system of length
+// n; lane G owns the m = ceil(n / L) consecutive rows i0 = G m .. i0 + m - 1
+// (the last lanes own fewer, possibly none).  Rows are scaled by 1/d so the
+// diagonal is one: l z_{i-1} + z_i + u z_{i+1} = s_i / d.
+//
+// Every system is Toeplitz, so the elimination of the interior rows
+// t = 1 .. m-2 of a chunk, in terms of the chunk's first unknown f and last
+// unknown g, uses the same factors in every chunk:
+//   forward   yh_t = s_t a_t - b_t yh_{t-1},   a_t = iden_t / d, b_t = l iden_t,
+//             iden_t = 1 / (1 - l cc_{t-1}),   cc_t = u iden_t,
+//             ph_t = -b_t ph_{t-1} (ph_0 = 1)  (the dependence on f),
+//   backward  z_t = yh_t + ph_t f - cc_t z_{t+1},  z_{mi+1} = g.
+// Unrolling the backward sweep, z_1 = sum_t w_t yh_t + P_1 f + Q_1 g with
+// w_t = prod_{s<t} (-cc_s), P_1 = sum_{t<=mi} w_t ph_t and Q_1 = w_{mi+1}.
+// One thread per system builds the table (a, b, ph, cc, w) in shared memory;
+// the L lanes of the system then run one forward sweep over their registers,
+// form the two reduced rows of the chunk (f at 2G, g at 2G+1), solve the
+// reduced tridiagonal system of 2L unknowns by parallel cyclic reduction
+// (warp shuffles for L <= 32, shared memory otherwise), and finish with the
+// backward sweep.  A chunk that ends at row n-1 early (the boundary lane) is
+// the leading part of a full chunk, so it uses the same table and only its own
+// P_1, Q_1.
+#include <algorithm>
 #include <cstring>
 
 #include "pd_internal.h"
 
 namespace {
 
-constexpr int MMAX = 8;
+// rows per chunk held in registers (compile-time bound of the unrolled sweeps)
+template <typename R> struct ChunkRows;
+template <> struct ChunkRows<float> { static constexpr int MM = 32; };
+template <> struct ChunkRows<double> { static constexpr int MM = 16; };
+
+// threads per block and systems per block for L lanes per system
+__host__ __device__ constexpr int tri_threads(int L) { return L >= 128 ? L : (16 * L < 32 ? 32 : (16 * L > 128 ? 128 : 16 * L)); }
+__host__ __device__ constexpr int tri_sb(int L) { return tri_threads(L) / L; }
 
 template <typename C>
 struct Row4 { C a, b, c, d; };
 
+// one entry of the per-system elimination table (interior row t)
 template <typename C>
+struct alignas(16) TabRow { C a, b, ph, cc, w, pad; };
+
+template <typename C>
+struct SysInfo {
+  C ld, ud, invd;
+  C P1, Q1;      // full chunks
+  C P1b, Q1b;    // the boundary chunk (rows up to n-1)
+  long long base;
+};
+
+template <int L, typename C>
 PD_D C shfl_up_c(C v, int d) {
-  v.x = __shfl_up_sync(0xffffffffu, v.x, d);
-  v.y = __shfl_up_sync(0xffffffffu, v.y, d);
+  v.x = __shfl_up_sync(0xffffffffu, v.x, d, L);
+  v.y = __shfl_up_sync(0xffffffffu, v.y, d, L);
   return v;
 }
-template <typename C>
+template <int L, typename C>
 PD_D C shfl_down_c(C v, int d) {
-  v.x = __shfl_down_sync(0xffffffffu, v.x, d);
-  v.y = __shfl_down_sync(0xffffffffu, v.y, d);
+  v.x = __shfl_down_sync(0xffffffffu, v.x, d, L);
+  v.y = __shfl_down_sync(0xffffffffu, v.y, d, L);
   return v;
 }
-template <typename C>
+template <int L, typename C>
 PD_D Row4<C> shfl_up_r(const Row4<C>& r, int d) {
   Row4<C> o;
-  o.a = shfl_up_c(r.a, d); o.b = shfl_up_c(r.b, d); o.c = shfl_up_c(r.c, d); o.d = shfl_up_c(r.d, d);
+  o.a = shfl_up_c<L>(r.a, d); o.b = shfl_up_c<L>(r.b, d);
+  o.c = shfl_up_c<L>(r.c, d); o.d = shfl_up_c<L>(r.d, d);
   return o;
 }
-template <typename C>
+template <int L, typename C>
 PD_D Row4<C> shfl_down_r(const Row4<C>& r, int d) {
   Row4<C> o;
-  o.a = shfl_down_c(r.a, d); o.b = shfl_down_c(r.b, d); o.c = shfl_down_c(r.c, d);
-  o.d = shfl_down_c(r.d, d);
+  o.a = shfl_down_c<L>(r.a, d); o.b = shfl_down_c<L>(r.b, d);
+  o.c = shfl_down_c<L>(r.c, d); o.d = shfl_down_c<L>(r.d, d);
   return o;
 }
 
@@ -69,184 +104,185 @@ PD_D Row4<C> pcr_step(const Row4<C>& x, const Row4<C>& m, bool hm, const Row4<C>
   return o;
 }
 
-// element i of system q (q = k*J + j) in global memory
 template <typename C>
-PD_D C* sys_elem(const TriArgs& a, C* data, long long q, int i) {
-  const long long k = q / a.J, j = q % a.J;
-  return data + k * a.S + j + (long long)i * a.stride;
+PD_D Row4<C> ident_row() {
+  Row4<C> r;
+  r.a = czero<C>(); r.c = czero<C>(); r.d = czero<C>();
+  r.b = czero<C>(); r.b.x = 1;
+  return r;
 }
 
-// Shared tile layout: system sb, row i at sb * rows_pad + i + i / m (chunks of
-// m rows padded to m + 1).  i / m by a 16-bit reciprocal cm = ceil(2^16 / m),
-// exact for m <= 8 and i < 8192.
-PD_D int tile_slot(int i, unsigned cm) { return i + (int)(((unsigned)i * cm) >> 16); }
-
-template <typename C, bool ASYNC>
-PD_D void put_elem(C* dst, const C* src);
-
-// Copy the SB systems q0 .. q0+SB-1 between global memory and the shared tile
-// (IN: global -> shared, zeros for systems past the end; OUT: shared -> global).
-// Contiguous 1D systems are copied as one run (e -> (system, row) by an exact
-// 32-bit reciprocal of n); strided systems give each thread one system and a
-// fixed row step (blockDim.x is a multiple of SB).
-template <typename C, bool IN, bool ASYNC>
-PD_D void tile_copy(const TriArgs& a, C* tile, int rows_pad, int m, long long q0, int SB) {
-  C* data = reinterpret_cast<C*>(a.data);
-  const int n = a.n;
-  const long long total = (long long)a.nh * a.J;
-  const unsigned cm = (65536u + (unsigned)m - 1u) / (unsigned)m;
-  if (a.stride == 1 && a.J == 1 && a.S == n) {
-    const int nsys = (int)min((long long)SB, total - q0);
-    const int nel = SB * n;
-    C* g = data + q0 * n;
-    const unsigned mn = n > 1 ? (unsigned)((0x100000000ull + (unsigned long long)n - 1) / (unsigned long long)n) : 0u;
-    for (int e = threadIdx.x; e < nel; e += blockDim.x) {
-      const int sb = n > 1 ? (int)__umulhi((unsigned)e, mn) : e;
-      const int i = e - sb * n;
-      C* t = tile + (size_t)sb * rows_pad + tile_slot(i, cm);
-      if (IN) {
-        if (sb < nsys) put_elem<C, ASYNC>(t, g + e);
-        else *t = czero<C>();
-      } else if (sb < nsys) {
-        g[e] = *t;
-      }
-    }
-  } else {
-    const int sb = threadIdx.x % SB;
-    const long long q = q0 + sb;
-    const bool ok = q < total;
-    C* g = ok ? data + (q / a.J) * a.S + (q % a.J) : data;
-    const int step = blockDim.x / SB;
-    C* t0 = tile + (size_t)sb * rows_pad;
-    for (int i = threadIdx.x / SB; i < n; i += step) {
-      C* t = t0 + tile_slot(i, cm);
-      if (IN) {
-        if (ok) put_elem<C, ASYNC>(t, g + (long long)i * a.stride);
-        else *t = czero<C>();
-      } else if (ok) {
-        g[(long long)i * a.stride] = *t;
-      }
-    }
-  }
-}
-
-// Solve the SB systems q0 .. q0+SB-1 held in the padded shared tile (one
-// system per 32W threads); the solutions overwrite the tile.  pa..pd: PCR
-// scratch (W > 1 only).
-template <typename R, int W>
-PD_D void solve_tile(const TriArgs& a, int m, int SB, cplx_t<R>* tile, cplx_t<R>* pa,
-                     cplx_t<R>* pb, cplx_t<R>* pc, cplx_t<R>* pd, long long q0) {
+// Table of one system (one thread): coefficients, the interior factors of a
+// chunk of m rows and the P_1, Q_1 of full and boundary chunks.
+template <typename R>
+PD_D void build_table(const TriArgs& a, long long q, int m, TabRow<cplx_t<R>>* tab,
+                      SysInfo<cplx_t<R>>* info) {
   using C = cplx_t<R>;
-  const int rows_pad = 32 * W * (m + 1);
-  const int R2 = 64 * W;
-  const int n = a.n, J = a.J;
-  const long long total = (long long)a.nh * J;
-  const int sb = threadIdx.x / (32 * W);
-  const int G = threadIdx.x % (32 * W);
+  const long long k = q / a.J, j = q % a.J;
+  const C* lam = reinterpret_cast<const C*>(a.lam);
+  const C l1 = lam[2 * k], l2 = lam[2 * k + 1];
+  C mu = czero<C>();
+  if (a.mu != nullptr) mu = reinterpret_cast<const C*>(a.mu)[j];
+  const C d = cadd(l1, cmul(l2, cadd(mk((R)a.cd, (R)0), mu)));
+  const C invd = crcp(d);
+  const C ld = cmul(cscale(l2, (R)a.cl), invd);
+  const C ud = cmul(cscale(l2, (R)a.cu), invd);
+  const int n = a.n;
+  const int mi = m - 2;
+  const int mob = n - ((n - 1) / m) * m;  // rows of the boundary chunk (1 .. m)
+  const int mib = mob - 2;
+  const C one = mk((R)1, (R)0);
+  C cc = czero<C>(), ph = one, w = one, pp = czero<C>();
+  C P1 = czero<C>(), Q1 = czero<C>(), P1b = czero<C>(), Q1b = czero<C>();
+  for (int t = 1; t <= mi; ++t) {
+    const C iden = crcp(csub(one, cmul(ld, cc)));
+    TabRow<C> e;
+    e.a = cmul(iden, invd);
+    e.b = cmul(ld, iden);
+    cc = cmul(ud, iden);
+    ph = cmul(e.b, ph);
+    ph.x = -ph.x; ph.y = -ph.y;
+    pp = cadd(pp, cmul(w, ph));
+    e.ph = ph;
+    e.cc = cc;
+    e.w = w;
+    e.pad = czero<C>();
+    tab[t - 1] = e;
+    w = cmul(w, cc);
+    w.x = -w.x; w.y = -w.y;  // w_{t+1}
+    if (t == mi) { P1 = pp; Q1 = w; }
+    if (t == mib) { P1b = pp; Q1b = w; }
+  }
+  info->ld = ld; info->ud = ud; info->invd = invd;
+  info->P1 = P1; info->Q1 = Q1; info->P1b = P1b; info->Q1b = Q1b;
+  info->base = k * a.S + j;
+}
+
+template <typename C>
+PD_D void ld_pair(const C* p, C& x, C& y);
+template <>
+PD_D void ld_pair<float2>(const float2* p, float2& x, float2& y) {
+  const float4 v = *reinterpret_cast<const float4*>(p);
+  x = make_float2(v.x, v.y);
+  y = make_float2(v.z, v.w);
+}
+template <>
+PD_D void ld_pair<double2>(const double2* p, double2& x, double2& y) {
+  x = p[0];
+  y = p[1];
+}
+
+// Solve the SB systems of one tile: q0 + sb for sb < SB.  Block threads:
+// sb = threadIdx.x / L, lane G = threadIdx.x % L.
+template <typename R, int L>
+PD_D void solve_tile(const TriArgs& a, long long q0, unsigned char* smraw) {
+  using C = cplx_t<R>;
+  constexpr int MM = ChunkRows<R>::MM;
+  constexpr int SB = tri_sb(L);
+  TabRow<C>* tab = reinterpret_cast<TabRow<C>*>(smraw);                   // [SB][MM-2]
+  SysInfo<C>* sinfo = reinterpret_cast<SysInfo<C>*>(tab + SB * (MM - 2));  // [SB]
+  C* pcr = reinterpret_cast<C*>(sinfo + SB);                                // [4][SB][2L] (L > 32)
+
+  const int n = a.n;
+  const int m = max(2, (n + L - 1) / L);
+  const long long total = (long long)a.nh * a.J;
+  const int sb = threadIdx.x / L, G = threadIdx.x % L;
   const long long q = q0 + sb;
   const bool active = q < total;
-
-  // ---- system coefficients, normalised by the diagonal
-  C ld = czero<C>(), ud = czero<C>(), invd = mk((R)1, (R)0);
-  if (active) {
-    const long long k = q / J, j = q % J;
-    const C* lam = reinterpret_cast<const C*>(a.lam);
-    const C l1 = lam[2 * k], l2 = lam[2 * k + 1];
-    C mu = czero<C>();
-    if (a.mu != nullptr) mu = reinterpret_cast<const C*>(a.mu)[j];
-    const C l = cscale(l2, (R)a.cl);
-    const C u = cscale(l2, (R)a.cu);
-    const C d = cadd(l1, cmul(l2, cadd(mk((R)a.cd, (R)0), mu)));
-    invd = crcp(d);
-    ld = cmul(l, invd);
-    ud = cmul(u, invd);
-  }
-
-  // ---- lane rows: right-hand sides scaled by 1/d; the coefficients of row i
-  // are (ld, 1, ud) except at the ends (no z_{-1}, no z_n) and on padding rows
-  C rhs[MMAX];
   const int i0 = G * m;
-  C* my = tile + (size_t)sb * rows_pad + G * (m + 1);
-#pragma unroll
-  for (int t = 0; t < MMAX; ++t)
-    if (t < m) rhs[t] = (i0 + t < n) ? cmul(my[t], invd) : czero<C>();
-  auto lrow = [&](int t) -> C { const int i = i0 + t; return (i > 0 && i < n) ? ld : czero<C>(); };
-  auto urow = [&](int t) -> C { const int i = i0 + t; return (i < n - 1) ? ud : czero<C>(); };
+  const int mown = active ? max(0, min(m, n - i0)) : 0;
+  C* data = reinterpret_cast<C*>(a.data);
 
-  // ---- interior elimination (rows 1..m-2 of the chunk)
-  const int mi = m - 2;
-  C cc[MMAX], Y[MMAX], P[MMAX], Q[MMAX];
-#pragma unroll
-  for (int t = 0; t < MMAX; ++t) { cc[t] = czero<C>(); Y[t] = P[t] = Q[t] = czero<C>(); }
-#pragma unroll
-  for (int t = 1; t < MMAX - 1; ++t) {
-    if (t <= mi) {
-      const C lt = lrow(t);
-      const C den = csub(mk((R)1, (R)0), cmul(lt, cc[t - 1]));
-      const C iden = crcp(den);
-      cc[t] = cmul(urow(t), iden);
-      Y[t] = cmul(csub(rhs[t], cmul(lt, Y[t - 1])), iden);
-      const C pr = (t == 1) ? mk(-lt.x, -lt.y) : czero<C>();
-      P[t] = cmul(csub(pr, cmul(lt, P[t - 1])), iden);
-      const C ut = urow(t);
-      const C qr = (t == mi) ? mk(-ut.x, -ut.y) : czero<C>();
-      Q[t] = cmul(csub(qr, cmul(lt, Q[t - 1])), iden);
-    }
+  // right-hand side of this chunk into registers (all loads in flight while
+  // the tables are built)
+  C sv[MM];
+  long long base = 0;
+  if (active) {
+    const long long k = q / a.J, j = q % a.J;
+    base = k * a.S + j;
   }
+  const C* src = data + base + (long long)i0 * a.stride;
 #pragma unroll
-  for (int t = MMAX - 2; t >= 1; --t) {
-    if (t < mi) {
-      Y[t] = csub(Y[t], cmul(cc[t], Y[t + 1]));
-      P[t] = csub(P[t], cmul(cc[t], P[t + 1]));
-      Q[t] = csub(Q[t], cmul(cc[t], Q[t + 1]));
-    }
+  for (int t = 0; t < MM; ++t)
+    sv[t] = (t < mown) ? src[(long long)t * a.stride] : czero<C>();
+  C slast = czero<C>();
+  if (mown >= 2) slast = src[(long long)(mown - 1) * a.stride];
+
+  for (int s = threadIdx.x; s < SB; s += blockDim.x)
+    if (q0 + s < total) build_table<R>(a, q0 + s, m, tab + s * (MM - 2), sinfo + s);
+  __syncthreads();
+
+  const TabRow<C>* tb = tab + sb * (MM - 2);
+  C ld = czero<C>(), ud = czero<C>(), invd = czero<C>(), P1x = czero<C>(), Q1x = czero<C>();
+  if (active) {
+    const SysInfo<C>& si = sinfo[sb];
+    ld = si.ld; ud = si.ud; invd = si.invd;
+    P1x = (mown == m) ? si.P1 : si.P1b;
+    Q1x = (mown == m) ? si.Q1 : si.Q1b;
+  }
+  const int mi = mown - 2;
+
+  // ---- forward sweep over the interior rows (yh overwrites s)
+  C y = czero<C>(), Y1 = czero<C>();
+#pragma unroll
+  for (int t = 1; t < MM - 1; ++t) {
+    if (t > mi) break;
+    C at, bt;
+    ld_pair(&tb[t - 1].a, at, bt);
+    const C wt = tb[t - 1].w;
+    const C s = sv[t];
+    y = mk(s.x * at.x - s.y * at.y - (bt.x * y.x - bt.y * y.y),
+           s.x * at.y + s.y * at.x - (bt.x * y.y + bt.y * y.x));
+    sv[t] = y;
+    Y1 = cadd(Y1, cmul(wt, y));
   }
 
-  // ---- reduced rows (f_G at 2G, g_G at 2G+1)
-  Row4<C> rf, rg;
+  // ---- reduced rows
   const C one = mk((R)1, (R)0);
-  const C u0 = urow(0), lm = lrow(m - 1), um = urow(m - 1);
-  C rm = czero<C>();
-#pragma unroll
-  for (int t = 1; t < MMAX; ++t)
-    if (t == m - 1) rm = rhs[t];
-  if (mi >= 1) {
-    C Y1 = Y[1], P1 = P[1], Q1 = Q[1], Ym = czero<C>(), Pm = czero<C>(), Qm = czero<C>();
-#pragma unroll
-    for (int t = 1; t < MMAX - 1; ++t)
-      if (t == mi) { Ym = Y[t]; Pm = P[t]; Qm = Q[t]; }
-    rf.a = lrow(0);
-    rf.b = cadd(one, cmul(u0, P1));
-    rf.c = cmul(u0, Q1);
-    rf.d = csub(rhs[0], cmul(u0, Y1));
-    rg.a = cmul(lm, Pm);
-    rg.b = cadd(one, cmul(lm, Qm));
-    rg.c = um;
-    rg.d = csub(rm, cmul(lm, Ym));
-  } else {
-    rf.a = lrow(0); rf.b = one; rf.c = u0; rf.d = rhs[0];
-    rg.a = lm; rg.b = one; rg.c = um; rg.d = rm;
+  Row4<C> rf = ident_row<C>(), rg = ident_row<C>();
+  if (mown >= 1) {
+    const C s0 = cmul(sv[0], invd);
+    const C l0 = G > 0 ? ld : czero<C>();
+    if (mown == 1) {
+      rf.a = l0; rf.b = one; rf.c = czero<C>(); rf.d = s0;
+    } else {
+      const C sl = cmul(slast, invd);
+      const C ul = (i0 + mown < n) ? ud : czero<C>();
+      if (mi >= 1) {
+        C phm, ccm;
+        ld_pair(&tb[mi - 1].ph, phm, ccm);
+        rf.a = l0;
+        rf.b = cadd(one, cmul(ud, P1x));
+        rf.c = cmul(ud, Q1x);
+        rf.d = csub(s0, cmul(ud, Y1));
+        rg.a = cmul(ld, phm);
+        rg.b = csub(one, cmul(ld, ccm));
+        rg.c = ul;
+        rg.d = csub(sl, cmul(ld, y));
+      } else {
+        rf.a = l0; rf.b = one; rf.c = ud; rf.d = s0;
+        rg.a = ld; rg.b = one; rg.c = ul; rg.d = sl;
+      }
+    }
   }
 
-  // ---- PCR on the reduced system (64W rows per system)
+  // ---- PCR on the reduced system of 2L rows
   C f, g;
-  if constexpr (W == 1) {
-    // one warp per system: lane G holds rows 2G (f) and 2G+1 (g); the
-    // neighbours come from warp shuffles, no shared memory or block barrier
-    for (int s = 1; s < 64; s <<= 1) {
+  if constexpr (L <= 32) {
+    for (int s = 1; s < 2 * L; s <<= 1) {
       Row4<C> mf, pf, mg, pg;
       bool hmf, hpf, hmg, hpg;
       if (s == 1) {
-        const Row4<C> gm = shfl_up_r(rg, 1);    // row 2G-1
-        const Row4<C> fp = shfl_down_r(rf, 1);  // row 2G+2
+        const Row4<C> gm = shfl_up_r<L>(rg, 1);    // row 2G-1
+        const Row4<C> fp = shfl_down_r<L>(rf, 1);  // row 2G+2
         mf = gm; hmf = G > 0;  pf = rg; hpf = true;
-        mg = rf; hmg = true;   pg = fp; hpg = G < 31;
+        mg = rf; hmg = true;   pg = fp; hpg = G < L - 1;
       } else {
         const int d = s >> 1;
-        mf = shfl_up_r(rf, d); mg = shfl_up_r(rg, d);
-        pf = shfl_down_r(rf, d); pg = shfl_down_r(rg, d);
+        mf = shfl_up_r<L>(rf, d); mg = shfl_up_r<L>(rg, d);
+        pf = shfl_down_r<L>(rf, d); pg = shfl_down_r<L>(rg, d);
         hmf = hmg = G >= d;
-        hpf = hpg = G + d < 32;
+        hpf = hpg = G + d < L;
       }
       const Row4<C> nf = pcr_step(rf, mf, hmf, pf, hpf);
       const Row4<C> ng = pcr_step(rg, mg, hmg, pg, hpg);
@@ -256,10 +292,11 @@ PD_D void solve_tile(const TriArgs& a, int m, int SB, cplx_t<R>* tile, cplx_t<R>
     f = cmul(rf.d, crcp(rf.b));
     g = cmul(rg.d, crcp(rg.b));
   } else {
-    C* A_ = pa + (size_t)sb * R2;
-    C* B_ = pb + (size_t)sb * R2;
-    C* C_ = pc + (size_t)sb * R2;
-    C* D_ = pd + (size_t)sb * R2;
+    constexpr int R2 = 2 * L;
+    C* A_ = pcr + (size_t)sb * R2;
+    C* B_ = A_ + (size_t)SB * R2;
+    C* C_ = B_ + (size_t)SB * R2;
+    C* D_ = C_ + (size_t)SB * R2;
     const int rf_i = 2 * G, rg_i = 2 * G + 1;
     A_[rf_i] = rf.a; B_[rf_i] = rf.b; C_[rf_i] = rf.c; D_[rf_i] = rf.d;
     A_[rg_i] = rg.a; B_[rg_i] = rg.b; C_[rg_i] = rg.c; D_[rg_i] = rg.d;
@@ -270,12 +307,12 @@ PD_D void solve_tile(const TriArgs& a, int m, int SB, cplx_t<R>* tile, cplx_t<R>
       for (int h = 0; h < 2; ++h) {
         const int i = 2 * G + h;
         const int im = i - s, ip = i + s;
-        Row4<C> x, m, p;
+        Row4<C> x, mr, pr;
         x.a = A_[i]; x.b = B_[i]; x.c = C_[i]; x.d = D_[i];
-        m = x; p = x;
-        if (im >= 0) { m.a = A_[im]; m.b = B_[im]; m.c = C_[im]; m.d = D_[im]; }
-        if (ip < R2) { p.a = A_[ip]; p.b = B_[ip]; p.c = C_[ip]; p.d = D_[ip]; }
-        nw[h] = pcr_step(x, m, im >= 0, p, ip < R2);
+        mr = x; pr = x;
+        if (im >= 0) { mr.a = A_[im]; mr.b = B_[im]; mr.c = C_[im]; mr.d = D_[im]; }
+        if (ip < R2) { pr.a = A_[ip]; pr.b = B_[ip]; pr.c = C_[ip]; pr.d = D_[ip]; }
+        nw[h] = pcr_step(x, mr, im >= 0, pr, ip < R2);
       }
       __syncthreads();
 #pragma unroll
@@ -289,205 +326,119 @@ PD_D void solve_tile(const TriArgs& a, int m, int SB, cplx_t<R>* tile, cplx_t<R>
     g = cmul(D_[rg_i], crcp(B_[rg_i]));
   }
 
-  // ---- back-substitute the interior and write the chunk
+  // ---- backward sweep and store
   bool bad = false;
+  C* dst = data + base + (long long)i0 * a.stride;
+  C z = g;
 #pragma unroll
-  for (int t = 0; t < MMAX; ++t) {
-    if (t < m) {
-      C z;
-      if (t == 0) z = f;
-      else if (t == m - 1) z = g;
-      else z = cadd(Y[t], cadd(cmul(P[t], f), cmul(Q[t], g)));
-      if (!(isfinite(z.x) && isfinite(z.y))) bad = true;
-      my[t] = z;
+  for (int t = MM - 2; t >= 1; --t) {
+    if (t <= mi) {
+      C ph, cc;
+      ld_pair(&tb[t - 1].ph, ph, cc);
+      const C yh = sv[t];
+      z = mk(yh.x + ph.x * f.x - ph.y * f.y - (cc.x * z.x - cc.y * z.y),
+             yh.y + ph.x * f.y + ph.y * f.x - (cc.x * z.y + cc.y * z.x));
+      sv[t] = z;
     }
   }
-  if (bad && active && a.flag != nullptr) atomicOr(a.flag, 1);
-
+#pragma unroll
+  for (int t = 1; t < MM - 1; ++t) {
+    if (t <= mi) {
+      const C v = sv[t];
+      bad |= !(isfinite(v.x) && isfinite(v.y));
+      dst[(long long)t * a.stride] = v;
+    }
+  }
+  if (mown >= 1) {
+    bad |= !(isfinite(f.x) && isfinite(f.y));
+    dst[0] = f;
+  }
+  if (mown >= 2) {
+    bad |= !(isfinite(g.x) && isfinite(g.y));
+    dst[(long long)(mown - 1) * a.stride] = g;
+  }
+  if (bad && a.flag != nullptr) atomicOr(a.flag, 1);
 }
 
-// Non-persistent form (W > 1): load one tile of SB systems, solve, store.
-// Batch: work[block] = (problem, tile) selects the descriptor.
-template <typename R, int W, bool BATCH>
-__global__ void __launch_bounds__(512) k_tridiag(TriArgs a1, const TriArgs* __restrict__ descs,
-                                                 const int2* __restrict__ work, int SB) {
-  using C = cplx_t<R>;
+// One tile of SB systems per block.  Batch: work[block] = (problem, tile)
+// selects the descriptor.
+template <typename R, int L, bool BATCH>
+__global__ void __launch_bounds__(tri_threads(L), L >= 64 ? 1 : (sizeof(R) == 4 ? 4 : 2))
+    k_tridiag(TriArgs a1, const TriArgs* __restrict__ descs, const int2* __restrict__ work) {
+  extern __shared__ __align__(16) unsigned char smraw[];
   const TriArgs& a = BATCH ? descs[work[blockIdx.x].x] : a1;
-  const int tile_id = BATCH ? work[blockIdx.x].y : (int)blockIdx.x;
-  const int m = max(2, (a.n + 32 * W - 1) / (32 * W));
-  extern __shared__ __align__(16) unsigned char smraw[];
-  const int rows_pad = 32 * W * (m + 1);
-  C* tile = reinterpret_cast<C*>(smraw);                       // [SB][rows_pad]
-  C* pa = tile + (size_t)SB * rows_pad;                         // [SB][64W] x 4
-  const int R2 = 64 * W;
-  C* pb = pa + (size_t)SB * R2;
-  C* pc = pb + (size_t)SB * R2;
-  C* pd = pc + (size_t)SB * R2;
-  const long long q0 = (long long)tile_id * SB;
-  tile_copy<C, true, false>(a, tile, rows_pad, m, q0, SB);
-  __syncthreads();
-  solve_tile<R, W>(a, m, SB, tile, pa, pb, pc, pd, q0);
-  __syncthreads();
-  tile_copy<C, false, false>(a, tile, rows_pad, m, q0, SB);
+  const long long tile = BATCH ? work[blockIdx.x].y : (long long)blockIdx.x;
+  solve_tile<R, L>(a, tile * tri_sb(L), smraw);
 }
 
-// cp.async copy of one complex value (8 or 16 bytes) global -> shared
-template <typename C>
-PD_D void cp_async_c(C* dst, const C* src) {
-  const uint32_t d = (uint32_t)__cvta_generic_to_shared(dst);
-  if constexpr (sizeof(C) == 8)
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(d), "l"(src) : "memory");
-  else
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(d), "l"(src) : "memory");
-}
-template <typename C, bool ASYNC>
-PD_D void put_elem(C* dst, const C* src) {
-  if constexpr (ASYNC) cp_async_c(dst, src);
-  else *dst = *src;
-}
-PD_D void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
-template <int N>
-PD_D void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
-
-// Persistent, double-buffered form for one warp per system (n <= 256): every
-// block walks over tiles of SB systems; the next tile is copied into the other
-// shared buffer with cp.async while the current one is solved.  Batch: tile g
-// is (problem, tile) = work[g] and may change problem from tile to tile.
-template <typename R, bool BATCH>
-__global__ void __launch_bounds__(256, 2) k_tridiag_pipe(TriArgs a1, const TriArgs* __restrict__ descs,
-                                                         const int2* __restrict__ work, int SB,
-                                                         int ntiles, int mmax) {
+template <typename R, int L>
+size_t tile_smem() {
   using C = cplx_t<R>;
-  extern __shared__ __align__(16) unsigned char smraw[];
-  C* buf[2] = {reinterpret_cast<C*>(smraw),
-               reinterpret_cast<C*>(smraw) + (size_t)SB * 32 * (mmax + 1)};
-  auto args = [&](int g) -> const TriArgs& { return BATCH ? descs[work[g].x] : a1; };
-  auto tid_of = [&](int g) -> int { return BATCH ? work[g].y : g; };
-  auto issue = [&](int g, C* tile) {
-    const TriArgs& a = args(g);
-    const int m = max(2, (a.n + 31) / 32);
-    tile_copy<C, true, true>(a, tile, 32 * (m + 1), m, (long long)tid_of(g) * SB, SB);
-    cp_async_commit();
-  };
-  int g = blockIdx.x;
-  if (g < ntiles) issue(g, buf[0]);
-  for (int it = 0; g < ntiles; g += gridDim.x, ++it) {
-    C* cur = buf[it & 1];
-    const int gn = g + gridDim.x;
-    if (gn < ntiles) {
-      issue(gn, buf[(it + 1) & 1]);
-      cp_async_wait<1>();
-    } else {
-      cp_async_wait<0>();
-    }
-    __syncthreads();
-    const TriArgs& a = args(g);
-    const int n = a.n, m = max(2, (n + 31) / 32), rows_pad = 32 * (m + 1);
-    const long long q0 = (long long)tid_of(g) * SB;
-    solve_tile<R, 1>(a, m, SB, cur, nullptr, nullptr, nullptr, nullptr, q0);
-    __syncthreads();
-    tile_copy<C, false, false>(a, cur, rows_pad, m, q0, SB);
-    __syncthreads();
-  }
+  constexpr int MM = ChunkRows<R>::MM;
+  constexpr int SB = tri_sb(L);
+  size_t b = (size_t)SB * (MM - 2) * sizeof(TabRow<C>) + (size_t)SB * sizeof(SysInfo<C>);
+  if (L > 32) b += (size_t)4 * SB * 2 * L * sizeof(C);
+  return b;
 }
 
-constexpr int PIPE_SB = 8;  // one-warp systems per 256-thread block
-
-template <typename R>
-cudaError_t launch_pipe(const TriArgs& a1, const TriArgs* descs, const int2* work, int ntiles,
-                        int mmax, cudaStream_t st) {
-  using C = cplx_t<R>;
-  const size_t smem = (size_t)2 * PIPE_SB * 32 * (mmax + 1) * sizeof(C);
-  auto kern = descs ? k_tridiag_pipe<R, true> : k_tridiag_pipe<R, false>;
+template <typename R, int L>
+cudaError_t launch_l(const TriArgs& a1, const TriArgs* descs, const int2* work, long long ntiles,
+                     cudaStream_t st) {
+  if (ntiles == 0) return cudaSuccess;
+  const size_t smem = tile_smem<R, L>();
+  auto kern = descs ? k_tridiag<R, L, true> : k_tridiag<R, L, false>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  int dev = 0, nsm = 152, per = 2;
-  cudaGetDevice(&dev);
-  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kern, 256, smem);
-  const int grid = std::max(1, std::min(ntiles, nsm * std::max(per, 1)));
-  kern<<<grid, 256, smem, st>>>(a1, descs, work, PIPE_SB, ntiles, mmax);
-  return cudaGetLastError();
-}
-
-template <typename R, int W>
-cudaError_t launch_w(const TriArgs& a, cudaStream_t st) {
-  using C = cplx_t<R>;
-  const int m = std::max(2, ceil_div(a.n, 32 * W));
-  const long long total = (long long)a.nh * a.J;
-  if (total == 0) return cudaSuccess;
-  if constexpr (W == 1) {
-    const int ntiles = (int)((total + PIPE_SB - 1) / PIPE_SB);
-    return launch_pipe<R>(a, nullptr, nullptr, ntiles, m, st);
-  } else {
-    const int SB = std::max(1, (sizeof(R) == 4 ? 8 : 4) / W);
-    const size_t smem = (size_t)SB * (32 * W * (m + 1) + 4 * 64 * W) * sizeof(C);
-    auto kern = k_tridiag<R, W, false>;
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    const int grid = (int)((total + SB - 1) / SB);
-    kern<<<grid, SB * 32 * W, smem, st>>>(a, nullptr, nullptr, SB);
-    return cudaGetLastError();
-  }
-}
-
-// batched W-warp class (W > 1): tiles of SB systems, work[t] = (problem, tile)
-template <typename R, int W>
-cudaError_t launch_wb(const TriArgs* descs, const int2* work, int ntiles, int mmax,
-                      cudaStream_t st) {
-  using C = cplx_t<R>;
-  const int SB = std::max(1, (sizeof(R) == 4 ? 8 : 4) / W);
-  const size_t smem = (size_t)SB * (32 * W * (mmax + 1) + 4 * 64 * W) * sizeof(C);
-  auto kern = k_tridiag<R, W, true>;
-  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (e != cudaSuccess) return e;
-  TriArgs dummy;
-  memset(&dummy, 0, sizeof(dummy));
-  kern<<<ntiles, SB * 32 * W, smem, st>>>(dummy, descs, work, SB);
+  kern<<<(unsigned)ntiles, tri_threads(L), smem, st>>>(a1, descs, work);
   return cudaGetLastError();
 }
 
 template <typename R>
-cudaError_t launch_r(const TriArgs& a, cudaStream_t st) {
-  if (a.n <= 256) return launch_w<R, 1>(a, st);
-  if (a.n <= 512) return launch_w<R, 2>(a, st);
-  if (a.n <= 1024) return launch_w<R, 4>(a, st);
-  if (a.n <= 2048) return launch_w<R, 8>(a, st);
-  if (a.n <= 4096) return launch_w<R, 16>(a, st);
+cudaError_t launch_cls(int cls, const TriArgs& a1, const TriArgs* descs, const int2* work,
+                       long long ntiles, cudaStream_t st) {
+  switch (cls) {
+    case 0: return launch_l<R, 1>(a1, descs, work, ntiles, st);
+    case 1: return launch_l<R, 2>(a1, descs, work, ntiles, st);
+    case 2: return launch_l<R, 4>(a1, descs, work, ntiles, st);
+    case 3: return launch_l<R, 8>(a1, descs, work, ntiles, st);
+    case 4: return launch_l<R, 16>(a1, descs, work, ntiles, st);
+    case 5: return launch_l<R, 32>(a1, descs, work, ntiles, st);
+    case 6: return launch_l<R, 64>(a1, descs, work, ntiles, st);
+    case 7: return launch_l<R, 128>(a1, descs, work, ntiles, st);
+    case 8: return launch_l<R, 256>(a1, descs, work, ntiles, st);
+  }
   return cudaErrorInvalidValue;
 }
 
 }  // namespace
 
+int tridiag_class(int n, bool fp64) {
+  const int mm = fp64 ? ChunkRows<double>::MM : ChunkRows<float>::MM;
+  if (n < 1 || n > TRI_NMAX) return -1;
+  int cls = 0;
+  while ((1 << cls) * mm < n) ++cls;
+  return cls < TRI_NCLASS ? cls : -1;
+}
+
+int tridiag_batch_sb(int cls, bool fp64) {
+  (void)fp64;
+  return tri_sb(1 << cls);
+}
+
 cudaError_t launch_tridiag(const TriArgs& a, bool fp64, cudaStream_t st) {
-  return fp64 ? launch_r<double>(a, st) : launch_r<float>(a, st);
+  const int cls = tridiag_class(a.n, fp64);
+  if (cls < 0) return cudaErrorInvalidValue;
+  const long long total = (long long)a.nh * a.J;
+  const long long ntiles = (total + tri_sb(1 << cls) - 1) / tri_sb(1 << cls);
+  return fp64 ? launch_cls<double>(cls, a, nullptr, nullptr, ntiles, st)
+              : launch_cls<float>(cls, a, nullptr, nullptr, ntiles, st);
 }
 
-int tridiag_batch_sb(int W, bool fp64) {
-  return W == 1 ? PIPE_SB : std::max(1, (fp64 ? 4 : 8) / W);
-}
-
-cudaError_t launch_tridiag_batch(const TriArgs* descs, const int2* work, int ntiles, int W,
-                                 int mmax, bool fp64, cudaStream_t st) {
+cudaError_t launch_tridiag_batch(const TriArgs* descs, const int2* work, int ntiles, int cls,
+                                 bool fp64, cudaStream_t st) {
   if (ntiles == 0) return cudaSuccess;
   TriArgs dummy;
   memset(&dummy, 0, sizeof(dummy));
-  if (fp64) {
-    switch (W) {
-      case 1: return launch_pipe<double>(dummy, descs, work, ntiles, mmax, st);
-      case 2: return launch_wb<double, 2>(descs, work, ntiles, mmax, st);
-      case 4: return launch_wb<double, 4>(descs, work, ntiles, mmax, st);
-      case 8: return launch_wb<double, 8>(descs, work, ntiles, mmax, st);
-      case 16: return launch_wb<double, 16>(descs, work, ntiles, mmax, st);
-    }
-  } else {
-    switch (W) {
-      case 1: return launch_pipe<float>(dummy, descs, work, ntiles, mmax, st);
-      case 2: return launch_wb<float, 2>(descs, work, ntiles, mmax, st);
-      case 4: return launch_wb<float, 4>(descs, work, ntiles, mmax, st);
-      case 8: return launch_wb<float, 8>(descs, work, ntiles, mmax, st);
-      case 16: return launch_wb<float, 16>(descs, work, ntiles, mmax, st);
-    }
-  }
-  return cudaErrorInvalidValue;
+  return fp64 ? launch_cls<double>(cls, dummy, descs, work, ntiles, st)
+              : launch_cls<float>(cls, dummy, descs, work, ntiles, st);
 }

@@ -22,7 +22,7 @@ def test_batch_matches_sequential(prec):
     pd = lib_ready()
     import torch
     wls = _problems(10, 4242)
-    # make sure every tridiagonal class (nx <= 256, <= 512, <= 1024) is present
+    # systems from 63 to 1023 rows, so several tridiagonal lane classes are present
     wls.append(W.ade1d(nx=1023, nt=64, nu=1e-3, scheme=W.BE, alpha=1e-2, seed=9, name="big"))
     wls.append(W.ade1d(nx=400, nt=32, nu=1e-2, scheme=W.BE, alpha=1e-2, seed=10, name="mid"))
     wls.append(W.ade1d(nx=63, nt=1024, nu=1e-1, scheme=W.BE, alpha=1e-2, seed=11, name="long"))
@@ -47,9 +47,14 @@ def test_batch_matches_sequential(prec):
     else:
         u, it, rel = batch.solve(b, tol=1e-12, maxit=30)
         assert rel <= 1e-12
-    # one launch per kernel type per sweep: time forward, 3 tridiagonal classes, time inverse
-    per_sweep = 1 + 3 + 1
-    assert batch.launches() - l0 <= per_sweep * it + 1 + 3 + 2
+    # one launch per kernel type per sweep: time forward, one per tridiagonal
+    # lane class, time inverse.  A system of n rows is split over the smallest
+    # power-of-two number of lanes that holds it in chunks of at most 32 rows
+    # (mixed) or 16 rows (FP64).
+    rows = 32 if prec == "mixed" else 16
+    classes = {int(np.ceil(np.log2(max(1, -(-w.problem.space.nx // rows))))) for w in wls}
+    per_sweep = 1 + len(classes) + 1
+    assert batch.launches() - l0 <= per_sweep * it + 1 + len(classes) + 2
     uh = host(u)
     bh = host(b)
     off = batch.offsets
