@@ -102,7 +102,7 @@ void free_plan(pd_plan* p) {
                   p->mu,   p->spec, p->spec2, p->Udf,  p->Bdf,   p->w64a,  p->w64b,
                   p->dsc,  p->dflag, p->V,   p->Z,      p->dh,    p->Gf_hi, p->Gf_lo,
                   p->Gi_hi, p->Gi_lo, const_cast<void*>(p->xf.chirp),
-                  const_cast<void*>(p->xf.bhat)};
+                  const_cast<void*>(p->xf.bhat), p->amax};
   for (void* q : ptrs)
     if (q) cudaFree(q);
   if (p->hsc) cudaFreeHost(p->hsc);
@@ -134,6 +134,10 @@ FwdArgs fwd_base_impl(const pd_plan* p) {
   a.gam = p->gam;
   a.tw = p->tw;
   a.out = p->spec;
+  if (p->xform_tc) {
+    a.amax = p->amax;
+    a.amax_reset = p->amax + 1;
+  }
   return a;
 }
 
@@ -173,6 +177,8 @@ TriArgs tri_args_impl(const pd_plan* p, void* data) {
   ta.nh = p->nh; ta.J = p->J; ta.n = p->tri_n; ta.S = p->sg.specS; ta.stride = p->tri_stride;
   ta.cl = p->tri_cl; ta.cd = p->tri_cd; ta.cu = p->tri_cu;
   ta.lam = p->lam; ta.mu = p->xform ? p->mu : nullptr; ta.data = data; ta.flag = p->dflag;
+  ta.amax = p->xform_tc ? p->amax + 1 : nullptr;
+  ta.amax_reset = p->xform_tc ? p->amax : nullptr;
   return ta;
 }
 
@@ -659,32 +665,32 @@ pd_status plan_create_internal(const pd_space* sp, int nt, double dt, double alp
     const int rows = p->nh * (int)(S / n);
     p->xform_tc = !p->fp64 && n >= 16 && rows >= 128;
     if (s1 == PD_OK && p->xform_tc) {
-      // real form of the complex operators, split into TF32 high and low parts:
+      // real form of the complex operators, split into FP16 high and low parts:
       // G[2o][2i] = Re Q[o][i], G[2o][2i+1] = -Im, G[2o+1][2i] = Im, G[2o+1][2i+1] = Re
       const size_t P = xform_tc_bpad(n);
       for (int dir = 0; dir < 2; ++dir) {
         const std::vector<cd>& Qm = dir == 0 ? Qf : Qi;
-        std::vector<float> hi(P * P, 0.f), lo(P * P, 0.f);
+        std::vector<float> G(P * P, 0.f);
         for (int o = 0; o < n; ++o)
           for (int i = 0; i < n; ++i) {
             const cd q = Qm[(size_t)o * n + i];
             const float v[2][2] = {{(float)q.real(), (float)-q.imag()},
                                    {(float)q.imag(), (float)q.real()}};
             for (int a = 0; a < 2; ++a)
-              for (int b = 0; b < 2; ++b) {
-                const float g = v[a][b];
-                uint32_t bits;
-                memcpy(&bits, &g, 4);
-                bits &= 0xFFFFE000u;
-                float gh;
-                memcpy(&gh, &bits, 4);
-                const size_t idx = (size_t)(2 * o + a) * P + (2 * i + b);
-                hi[idx] = gh;
-                lo[idx] = g - gh;
-              }
+              for (int b = 0; b < 2; ++b) G[(size_t)(2 * o + a) * P + (2 * i + b)] = v[a][b];
           }
+        std::vector<uint16_t> hi, lo;
+        const float ginv = xform_tc_split(G, hi, lo);
+        (dir == 0 ? p->gf_inv : p->gi_inv) = ginv;
         if (s1 == PD_OK) s1 = upload(p, dir == 0 ? &p->Gf_hi : &p->Gi_hi, hi);
         if (s1 == PD_OK) s1 = upload(p, dir == 0 ? &p->Gf_lo : &p->Gi_lo, lo);
+      }
+      // max |value| words of the two transform inputs: [0] written by the
+      // forward time kernel, [1] by the tridiagonal solver
+      if (s1 == PD_OK) s1 = dalloc(p, (void**)&p->amax, 2 * sizeof(unsigned));
+      if (s1 == PD_OK) {
+        cudaError_t e = cudaMemset(p->amax, 0, 2 * sizeof(unsigned));
+        if (e != cudaSuccess) s1 = fail_cuda(p, e, "cudaMemset");
       }
     }
     if (s1 != PD_OK) { free_plan(p); return s1; }
@@ -791,11 +797,10 @@ pd_status plan_create_internal(const pd_space* sp, int nt, double dt, double alp
     const int rows = p->nh * (int)(S / sp->nx);
     const int ldo = 2 * p->sg.nxp;
     cudaError_t e = xform_tc_prepare(&p->xtc_fwd, rows, sp->nx, ldo, (const float*)p->spec,
-                                     (float*)p->spec2, (const float*)p->Gf_hi,
-                                     (const float*)p->Gf_lo);
+                                     (float*)p->spec2, p->Gf_hi, p->Gf_lo, p->gf_inv, p->amax);
     if (e == cudaSuccess)
       e = xform_tc_prepare(&p->xtc_inv, rows, sp->nx, ldo, (const float*)p->spec2,
-                           (float*)p->spec, (const float*)p->Gi_hi, (const float*)p->Gi_lo);
+                           (float*)p->spec, p->Gi_hi, p->Gi_lo, p->gi_inv, p->amax + 1);
     if (e != cudaSuccess) s2 = fail_cuda(p, e, "tensor map encoding");
   }
   if (s2 == PD_OK && !p->fp64 && with_state) s2 = dalloc(p, (void**)&p->Udf, NS(p) * sizeof(float2));

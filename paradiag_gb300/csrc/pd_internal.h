@@ -67,6 +67,10 @@ struct FwdArgs {
   const void* tw;                 // e^{-2 pi i m / N}, m < N (float2 or double2)
   void* out;                      // half spectrum [nh][S] (float2 or double2)
   double* norm2;                  // += ||r||_2^2 (may be null)
+  // mixed path with the tensor-core x-transform: max |out| (float bits) is
+  // raised into *amax, and *amax_reset (the other transform's word) is zeroed
+  unsigned* amax = nullptr;
+  unsigned* amax_reset = nullptr;
 };
 
 // Arguments of the inverse time kernel (K3).
@@ -97,6 +101,9 @@ struct TriArgs {
   const void* mu;                 // [J] complex spatial eigenvalues (or null: 0)
   void* data;                     // in: right-hand sides, out: solutions
   int* flag;
+  // as in FwdArgs: max |solution| raised into *amax, *amax_reset zeroed (FP32 only)
+  unsigned* amax = nullptr;
+  unsigned* amax_reset = nullptr;
 };
 
 // Arguments of the dense x-eigentransform (2D, step (a') / (c')): along x, for

@@ -23,6 +23,8 @@ struct pd_plan {
   void* Gf_lo = nullptr;
   void* Gi_hi = nullptr;
   void* Gi_lo = nullptr;
+  float gf_inv = 1.f, gi_inv = 1.f;   // scales of the FP16 operator splits
+  unsigned* amax = nullptr;           // max |input| of the forward / inverse transform
   int J = 1, tri_n = 0, tri_stride = 1;
   double tri_cl = 0, tri_cd = 0, tri_cu = 0;
   // device tables

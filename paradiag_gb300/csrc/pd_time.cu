@@ -440,6 +440,7 @@ PD_D void time_fwd_body(const FwdArgs& a, int tile) {
     const size_t oa = va ? spec_index(a.sg, 0, sa) : 0;
     const size_t ob = vb ? spec_index(a.sg, 0, sa + 1) : 0;
     const size_t kst = (size_t)a.sg.specS;
+    R mx = 0;
     for (int k = threadIdx.x >> lgTXc; k < a.nh; k += TT >> lgTXc) {
       const C Zk = sm[(k << lgTXc) + c];
       const C Zm = cconj(sm[((k == 0 ? 0 : N - k) << lgTXc) + c]);
@@ -447,6 +448,15 @@ PD_D void time_fwd_body(const FwdArgs& a, int tile) {
       const C B = cscale(cmul_mi(csub(Zk, Zm)), half);
       if (va) out[k * kst + oa] = A;
       if (vb) out[k * kst + ob] = B;
+      mx = fmax(mx, fmax(fmax(fabs(A.x), fabs(A.y)), fmax(fabs(B.x), fabs(B.y))));
+    }
+    if constexpr (PREC == 0) {
+      // largest |value| for the scaling of the tensor-core x-transform
+      if (a.amax != nullptr) {
+        for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+        if ((threadIdx.x & 31) == 0) atomicMax(a.amax, __float_as_uint(mx));
+        if (a.amax_reset != nullptr && blockIdx.x == 0 && threadIdx.x == 0) *a.amax_reset = 0u;
+      }
     }
   }
 }

@@ -44,6 +44,15 @@ __host__ __device__ constexpr int tri_sb(int L) { return tri_threads(L) / L; }
 template <typename C>
 struct Row4 { C a, b, c, d; };
 
+// complex reciprocal; in FP32 with the hardware reciprocal (rcp.approx, a few
+// ulp), which is ample for a preconditioner whose residual is formed apart
+PD_D float2 trcp(float2 a) {
+  float s;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(s) : "f"(fmaf(a.x, a.x, a.y * a.y)));
+  return make_float2(a.x * s, -a.y * s);
+}
+PD_D double2 trcp(double2 a) { return crcp(a); }
+
 // one entry of the per-system elimination table (interior row t)
 template <typename C>
 struct alignas(16) TabRow { C a, b, ph, cc, w, pad; };
@@ -90,13 +99,13 @@ PD_D Row4<C> pcr_step(const Row4<C>& x, const Row4<C>& m, bool hm, const Row4<C>
   Row4<C> o;
   o.a = czero<C>(); o.c = czero<C>(); o.b = x.b; o.d = x.d;
   if (hm) {
-    const C k1 = cmul(x.a, crcp(m.b));
+    const C k1 = cmul(x.a, trcp(m.b));
     o.a = mk(-(m.a.x * k1.x - m.a.y * k1.y), -(m.a.x * k1.y + m.a.y * k1.x));
     o.b = csub(o.b, cmul(m.c, k1));
     o.d = csub(o.d, cmul(m.d, k1));
   }
   if (hp) {
-    const C k2 = cmul(x.c, crcp(p.b));
+    const C k2 = cmul(x.c, trcp(p.b));
     o.c = mk(-(p.c.x * k2.x - p.c.y * k2.y), -(p.c.x * k2.y + p.c.y * k2.x));
     o.b = csub(o.b, cmul(p.a, k2));
     o.d = csub(o.d, cmul(p.d, k2));
@@ -124,7 +133,7 @@ PD_D void build_table(const TriArgs& a, long long q, int m, TabRow<cplx_t<R>>* t
   C mu = czero<C>();
   if (a.mu != nullptr) mu = reinterpret_cast<const C*>(a.mu)[j];
   const C d = cadd(l1, cmul(l2, cadd(mk((R)a.cd, (R)0), mu)));
-  const C invd = crcp(d);
+  const C invd = trcp(d);
   const C ld = cmul(cscale(l2, (R)a.cl), invd);
   const C ud = cmul(cscale(l2, (R)a.cu), invd);
   const int n = a.n;
@@ -135,7 +144,7 @@ PD_D void build_table(const TriArgs& a, long long q, int m, TabRow<cplx_t<R>>* t
   C cc = czero<C>(), ph = one, w = one, pp = czero<C>();
   C P1 = czero<C>(), Q1 = czero<C>(), P1b = czero<C>(), Q1b = czero<C>();
   for (int t = 1; t <= mi; ++t) {
-    const C iden = crcp(csub(one, cmul(ld, cc)));
+    const C iden = trcp(csub(one, cmul(ld, cc)));
     TabRow<C> e;
     e.a = cmul(iden, invd);
     e.b = cmul(ld, iden);
@@ -289,8 +298,8 @@ PD_D void solve_tile(const TriArgs& a, long long q0, unsigned char* smraw) {
       rf = nf;
       rg = ng;
     }
-    f = cmul(rf.d, crcp(rf.b));
-    g = cmul(rg.d, crcp(rg.b));
+    f = cmul(rf.d, trcp(rf.b));
+    g = cmul(rg.d, trcp(rg.b));
   } else {
     constexpr int R2 = 2 * L;
     C* A_ = pcr + (size_t)sb * R2;
@@ -322,8 +331,8 @@ PD_D void solve_tile(const TriArgs& a, long long q0, unsigned char* smraw) {
       }
       __syncthreads();
     }
-    f = cmul(D_[rf_i], crcp(B_[rf_i]));
-    g = cmul(D_[rg_i], crcp(B_[rg_i]));
+    f = cmul(D_[rf_i], trcp(B_[rf_i]));
+    g = cmul(D_[rg_i], trcp(B_[rg_i]));
   }
 
   // ---- backward sweep and store
@@ -358,6 +367,20 @@ PD_D void solve_tile(const TriArgs& a, long long q0, unsigned char* smraw) {
     dst[(long long)(mown - 1) * a.stride] = g;
   }
   if (bad && a.flag != nullptr) atomicOr(a.flag, 1);
+  if constexpr (sizeof(R) == 4) {
+    // largest |solution| for the scaling of the tensor-core x-transform
+    if (a.amax != nullptr) {
+      float mx = 0.f;
+      if (mown >= 1) mx = fmaxf(fabsf(f.x), fabsf(f.y));
+      if (mown >= 2) mx = fmaxf(mx, fmaxf(fabsf(g.x), fabsf(g.y)));
+#pragma unroll
+      for (int t = 1; t < MM - 1; ++t)
+        if (t <= mi) mx = fmaxf(mx, fmaxf(fabsf(sv[t].x), fabsf(sv[t].y)));
+      for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+      if ((threadIdx.x & 31) == 0) atomicMax(a.amax, __float_as_uint(mx));
+      if (a.amax_reset != nullptr && blockIdx.x == 0 && threadIdx.x == 0) *a.amax_reset = 0u;
+    }
+  }
 }
 
 // One tile of SB systems per block.  Batch: work[block] = (problem, tile)

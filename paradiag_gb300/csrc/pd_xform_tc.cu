@@ -9,33 +9,50 @@
 //     D[r][n] = sum_k A[r][k] G[n][k],   A = spectrum rows, G = real form of Q,
 // with M = rows, N = K = 2nx, both operands K-major.
 //
-// Precision: split TF32 ("3xTF32").  A = A_hi + A_lo with A_hi the FP32 value
-// with its 13 low significand bits cleared and A_lo = A - A_hi (exact), and the
-// same for G (split on the host).  D = A_hi G_hi + A_hi G_lo + A_lo G_hi with
-// FP32 accumulation, a relative error of about 2^-21, comparable to an FP32
-// GEMM.  A is split in shared memory after its TMA load (the split is
-// elementwise, so it does not depend on the swizzled layout).
+// Precision: FP16 operands split in two terms, FP32 accumulation.  With power-
+// of-two scales sA (from the largest |A|, recorded by the kernel that wrote A)
+// and sG, a = sA A = a_hi + a_lo and g = sG G = g_hi + g_lo with a_hi = fp16(a),
+// a_lo = fp16(a - a_hi); D = (a_hi g_hi + a_hi g_lo + a_lo g_hi) / (sA sG).
+// Each term carries 11 significand bits, so values within 2^-18 of the largest
+// keep about 22 bits (the dropped a_lo g_lo is ~2^-22 relative) and smaller
+// ones an absolute error below 2^-40 of the largest: an FP32-level transform in
+// the 2-norm, at twice the TF32 MMA rate and half the operand bytes of split
+// TF32.  A is loaded by TMA as FP32 and split in place in shared memory; G is
+// split on the host.
 //
-// CTA tile 128 x 256 (M x N), K chunks of 32 (one 128-byte swizzle row),
-// two pipeline stages.  Warp roles: warp 0 issues TMA loads, warp 1 allocates
-// TMEM and issues the MMAs (one elected thread), warps 2-5 split A and then
-// drain the accumulator (tcgen05.ld) to global memory.  Every mbarrier wait is
-// bounded; on a timeout the CTA records an error bit, drains, frees its TMEM and
-// returns.
+// Persistent kernel, one CTA per SM walking tiles of 128 x 256 (M x N); K
+// chunks of 32 (one 64-byte swizzle row of FP16) through four pipeline stages
+// that keep streaming across tile boundaries.  Warp roles: warp 0 issues TMA
+// loads, warp 1 allocates TMEM and issues the MMAs (one elected thread) into
+// one of two accumulators, warps 2-5 split A (one row per thread), warps 6-9
+// drain the other accumulator (tcgen05.ld) to global memory, so the epilogue of
+// a tile runs under the MMAs of the next.  The N blocks of one row block are
+// consecutive tiles, so A comes from DRAM once.  Every mbarrier wait is
+// bounded; on a timeout the CTA records an error bit, waits for its MMAs and
+// loads in flight, frees its TMEM and returns.
 #include <cuda.h>
+#include <cuda_fp16.h>
+
+#include <cmath>
+#include <vector>
 
 #include "pd_internal.h"
 #include "pd_xform_tc.h"
 
 namespace {
 
-constexpr int BM = 128, BN = 256, BK = 32;
-constexpr int STAGES = 2;
-constexpr int A_BYTES = BM * BK * 4;   // 16 KB
-constexpr int B_BYTES = BN * BK * 4;   // 32 KB
-constexpr int STAGE_BYTES = 2 * A_BYTES + 2 * B_BYTES;
-constexpr int TMEM_COLS = 256;
-constexpr int NTHREADS = 192;
+constexpr int BM = 128, BN = 256;
+constexpr int KH = 32;                  // FP16 K elements per stage (64 bytes)
+constexpr int AF_BOX = 16;              // FP32 K elements per TMA box of A (64 bytes)
+constexpr int A_BYTES = BM * KH * 4;    // 16 KB: FP32 A, then A_hi | A_lo in FP16
+constexpr int B_BYTES = BN * KH * 2;    // 16 KB per operand half
+constexpr int STAGE_BYTES = A_BYTES + 2 * B_BYTES;
+constexpr int STAGES = 4;
+// unused shared memory after the last stage, so that every operand read of the
+// tensor cores stays inside the CTA's allocation
+constexpr int GUARD_BYTES = 32 * 1024;
+constexpr int TMEM_COLS = 2 * BN;   // two accumulators: epilogue of one tile under the MMAs of the next
+constexpr int NTHREADS = 320;
 constexpr long long WAIT_LIMIT = 1LL << 22;
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
@@ -72,6 +89,13 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t phase, volatile
   return false;
 }
 
+// bounded wait for work already issued (loads or MMAs in flight) before the
+// CTA frees its resources; does not stop early on the abort flag
+__device__ __forceinline__ void mbar_drain(uint32_t bar, uint32_t phase) {
+  for (long long i = 0; i < WAIT_LIMIT; ++i)
+    if (mbar_try(bar, phase)) return;
+}
+
 __device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map, int c0, int c1,
                                             uint32_t bar) {
   asm volatile(
@@ -81,29 +105,28 @@ __device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map
       : "memory");
 }
 
-// shared-memory matrix descriptor: K-major, 128-byte swizzle, 8-row groups
-// 1024 bytes apart (tcgen05 descriptor format: start >> 4 in bits 0-13, leading
+// shared-memory matrix descriptor: K-major, 64-byte swizzle, 8-row groups
+// 512 bytes apart (tcgen05 descriptor format: start >> 4 in bits 0-13, leading
 // offset >> 4 in 16-29, stride offset >> 4 in 32-45, version 1 in 46-47,
-// swizzle mode in 61-63 with 2 = 128-byte swizzle)
+// swizzle mode in 61-63 with 4 = 64-byte swizzle)
 __device__ __forceinline__ uint64_t sdesc(uint32_t addr) {
   uint64_t d = 0;
   d |= (uint64_t)((addr & 0x3FFFF) >> 4);
   d |= (uint64_t)1 << 16;
-  d |= (uint64_t)(1024 >> 4) << 32;
+  d |= (uint64_t)(512 >> 4) << 32;
   d |= (uint64_t)1 << 46;
-  d |= (uint64_t)2 << 61;
+  d |= (uint64_t)4 << 61;
   return d;
 }
 
-// instruction descriptor of kind::tf32: D f32 (bits 4-5 = 1), A and B tf32
-// (bits 7-9 and 10-12 = 2), both K-major, N >> 3 in bits 17-22, M >> 4 in 24-28
-constexpr uint32_t IDESC = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(BN >> 3) << 17) |
-                           ((uint32_t)(BM >> 4) << 24);
+// instruction descriptor of kind::f16: D f32 (bits 4-5 = 1), A and B f16
+// (bits 7-9 and 10-12 = 0), both K-major, N >> 3 in bits 17-22, M >> 4 in 24-28
+constexpr uint32_t IDESC = (1u << 4) | ((uint32_t)(BN >> 3) << 17) | ((uint32_t)(BM >> 4) << 24);
 
-__device__ __forceinline__ void mma_tf32(uint32_t tmem, uint64_t a, uint64_t b, uint32_t acc) {
+__device__ __forceinline__ void mma_f16(uint32_t tmem, uint64_t a, uint64_t b, uint32_t acc) {
   asm volatile(
       "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
-      "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}" ::"r"(tmem),
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}" ::"r"(tmem),
       "l"(a), "l"(b), "r"(IDESC), "r"(acc)
       : "memory");
 }
@@ -114,19 +137,47 @@ __device__ __forceinline__ void mma_commit(uint32_t bar) {
       : "memory");
 }
 
+// power-of-two scale s with s |x| < 2^15 for |x| <= amax (1 when amax is 0 or
+// not finite)
+__device__ __forceinline__ float a_scale(float amax) {
+  if (!(amax > 0.f) || !isfinite(amax)) return 1.f;
+  int e;
+  frexpf(amax, &e);  // amax < 2^e
+  e = max(-100, min(100, e));
+  return ldexpf(1.f, 15 - e);
+}
+
+// split 8 scaled FP32 values into FP16 high and low parts (8 halves each)
+__device__ __forceinline__ void split8(const float* v, float s, uint4& hi, uint4& lo) {
+  uint32_t h[4], l[4];
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const float x0 = v[2 * q] * s, x1 = v[2 * q + 1] * s;
+    const __half2 hh = __floats2half2_rn(x0, x1);
+    const float2 hf = __half22float2(hh);
+    const __half2 ll = __floats2half2_rn(x0 - hf.x, x1 - hf.y);
+    h[q] = *reinterpret_cast<const uint32_t*>(&hh);
+    l[q] = *reinterpret_cast<const uint32_t*>(&ll);
+  }
+  hi = make_uint4(h[0], h[1], h[2], h[3]);
+  lo = make_uint4(l[0], l[1], l[2], l[3]);
+}
+
 __global__ void __launch_bounds__(NTHREADS, 1)
     k_xform_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmBhi,
                const __grid_constant__ CUtensorMap tmBlo, float* __restrict__ out, int rows,
-               int ncols, int ldo, int kchunks, int* err) {
+               int ncols, int ldo, int kchunks, int nblk_n, int ntiles,
+               const unsigned* __restrict__ amax_bits, float g_inv, int* err) {
   extern __shared__ __align__(1024) unsigned char smraw[];
-  // 1024-byte aligned operand stages (required by the 128-byte swizzle)
+  // 1024-byte aligned operand stages (the swizzle patterns repeat every 512 bytes)
   unsigned char* base = (unsigned char*)(((uintptr_t)smraw + 1023) & ~(uintptr_t)1023);
-  __shared__ __align__(8) uint64_t bar_full[STAGES], bar_split[STAGES], bar_empty[STAGES], bar_acc;
+  __shared__ __align__(8) uint64_t bar_full[STAGES], bar_split[STAGES], bar_empty[STAGES];
+  __shared__ __align__(8) uint64_t bar_accf[2], bar_acce[2], bar_done;
   __shared__ uint32_t tmem_slot;
   __shared__ int abort_flag;
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int r0 = blockIdx.x * BM, n0 = blockIdx.y * BN;
+  const float sa = a_scale(__uint_as_float(*amax_bits));
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < STAGES; ++s) {
@@ -134,7 +185,11 @@ __global__ void __launch_bounds__(NTHREADS, 1)
       mbar_init(smem_u32(&bar_split[s]), 4);
       mbar_init(smem_u32(&bar_empty[s]), 1);
     }
-    mbar_init(smem_u32(&bar_acc), 1);
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(smem_u32(&bar_accf[b]), 1);
+      mbar_init(smem_u32(&bar_acce[b]), 4);
+    }
+    mbar_init(smem_u32(&bar_done), 1);
     abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
@@ -151,88 +206,128 @@ __global__ void __launch_bounds__(NTHREADS, 1)
   const uint32_t tmem = tmem_slot;
   volatile int* abortp = &abort_flag;
 
+  // stage layout: [A: FP32 boxes 0 | 1, split in place to A_hi | A_lo] [G_hi] [G_lo]
   auto stage_ptr = [&](int s, int which) -> unsigned char* {
-    // which: 0 A_hi (raw A loaded here), 1 A_lo, 2 B_hi, 3 B_lo
-    const int off[4] = {0, A_BYTES, 2 * A_BYTES, 2 * A_BYTES + B_BYTES};
+    const int off[4] = {0, A_BYTES / 2, A_BYTES, A_BYTES + B_BYTES};
     return base + (size_t)s * STAGE_BYTES + off[which];
   };
+  // tiles of this CTA: T = blockIdx.x + i gridDim.x; T -> (row block, N block)
+  // with the N blocks of one row block consecutive
+  const int my_tiles = blockIdx.x < ntiles ? (ntiles - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
 
   if (warp == 0) {
-    // ---------------- TMA producer
+    // ---------------- TMA producer: one chunk counter g over all tiles
     if (lane == 0) {
-      int issued = 0;
-      for (int c = 0; c < kchunks; ++c) {
-        const int s = c % STAGES;
-        const uint32_t ph = (uint32_t)((c / STAGES) & 1);
-        if (c >= STAGES && !mbar_wait(smem_u32(&bar_empty[s]), ph ^ 1u, abortp)) break;
-        const uint32_t fb = smem_u32(&bar_full[s]);
-        mbar_expect_tx(fb, (uint32_t)(A_BYTES + 2 * B_BYTES));
-        tma_load_2d(smem_u32(stage_ptr(s, 0)), &tmA, c * BK, r0, fb);
-        tma_load_2d(smem_u32(stage_ptr(s, 2)), &tmBhi, c * BK, n0, fb);
-        tma_load_2d(smem_u32(stage_ptr(s, 3)), &tmBlo, c * BK, n0, fb);
-        issued = c + 1;
+      int g = 0;
+      bool ok = true;
+      for (int i = 0; i < my_tiles && ok; ++i) {
+        const int T = blockIdx.x + i * gridDim.x;
+        const int r0 = (T / nblk_n) * BM, n0 = (T % nblk_n) * BN;
+        for (int c = 0; c < kchunks; ++c, ++g) {
+          const int s = g % STAGES;
+          const uint32_t u = (uint32_t)(g / STAGES);
+          if (g >= STAGES && !mbar_wait(smem_u32(&bar_empty[s]), (u & 1u) ^ 1u, abortp)) {
+            ok = false;
+            break;
+          }
+          const uint32_t fb = smem_u32(&bar_full[s]);
+          mbar_expect_tx(fb, (uint32_t)(A_BYTES + 2 * B_BYTES));
+          tma_load_2d(smem_u32(stage_ptr(s, 0)), &tmA, c * KH, r0, fb);
+          tma_load_2d(smem_u32(stage_ptr(s, 1)), &tmA, c * KH + AF_BOX, r0, fb);
+          tma_load_2d(smem_u32(stage_ptr(s, 2)), &tmBhi, c * KH, n0, fb);
+          tma_load_2d(smem_u32(stage_ptr(s, 3)), &tmBlo, c * KH, n0, fb);
+        }
       }
       // drain: wait for the loads still in flight before the CTA may exit
-      for (int c = (issued > STAGES ? issued - STAGES : 0); c < issued; ++c)
-        mbar_wait(smem_u32(&bar_full[c % STAGES]), (uint32_t)((c / STAGES) & 1), abortp);
+      for (int q = (g > STAGES ? g - STAGES : 0); q < g; ++q)
+        mbar_drain(smem_u32(&bar_full[q % STAGES]), (uint32_t)((q / STAGES) & 1));
     }
   } else if (warp == 1) {
-    // ---------------- MMA issuer
+    // ---------------- MMA issuer: accumulator buffer i & 1 for local tile i
     if (lane == 0) {
+      int g = 0;
       bool ok = true;
-      for (int c = 0; c < kchunks && ok; ++c) {
-        const int s = c % STAGES;
-        const uint32_t ph = (uint32_t)((c / STAGES) & 1);
-        if (!mbar_wait(smem_u32(&bar_split[s]), ph, abortp)) { ok = false; break; }
-        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        const uint32_t ahi = smem_u32(stage_ptr(s, 0)), alo = smem_u32(stage_ptr(s, 1));
-        const uint32_t bhi = smem_u32(stage_ptr(s, 2)), blo = smem_u32(stage_ptr(s, 3));
-#pragma unroll
-        for (int kk = 0; kk < BK / 8; ++kk) {
-          const uint32_t koff = kk * 32;  // 8 tf32 = 32 bytes along the swizzled row
-          const uint32_t first = (c == 0 && kk == 0) ? 0u : 1u;
-          mma_tf32(tmem, sdesc(ahi + koff), sdesc(bhi + koff), first);
-          mma_tf32(tmem, sdesc(ahi + koff), sdesc(blo + koff), 1u);
-          mma_tf32(tmem, sdesc(alo + koff), sdesc(bhi + koff), 1u);
+      for (int i = 0; i < my_tiles && ok; ++i) {
+        const int ab = i & 1;
+        const uint32_t v = (uint32_t)(i >> 1);
+        if (i >= 2 && !mbar_wait(smem_u32(&bar_acce[ab]), (v & 1u) ^ 1u, abortp)) {
+          ok = false;
+          break;
         }
-        mma_commit(smem_u32(&bar_empty[s]));
-      }
-      mma_commit(smem_u32(&bar_acc));
-    }
-  } else {
-    // ---------------- A split (warps 2-5), then the epilogue
-    const int t = threadIdx.x - 64;  // 0..127
-    for (int c = 0; c < kchunks; ++c) {
-      const int s = c % STAGES;
-      const uint32_t ph = (uint32_t)((c / STAGES) & 1);
-      if (!mbar_wait(smem_u32(&bar_full[s]), ph, abortp)) break;
-      float4* hi = reinterpret_cast<float4*>(stage_ptr(s, 0));
-      float4* lo = reinterpret_cast<float4*>(stage_ptr(s, 1));
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        const uint32_t acc = tmem + (uint32_t)(ab * BN);
+        for (int c = 0; c < kchunks; ++c, ++g) {
+          const int s = g % STAGES;
+          const uint32_t u = (uint32_t)(g / STAGES);
+          if (!mbar_wait(smem_u32(&bar_split[s]), u & 1u, abortp)) { ok = false; break; }
+          asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+          const uint32_t ahi = smem_u32(stage_ptr(s, 0)), alo = smem_u32(stage_ptr(s, 1));
+          const uint32_t bhi = smem_u32(stage_ptr(s, 2)), blo = smem_u32(stage_ptr(s, 3));
 #pragma unroll
-      for (int q = 0; q < A_BYTES / 16 / 128; ++q) {
-        const int i = t + q * 128;
-        float4 v = hi[i], h, l;
-        h.x = __uint_as_float(__float_as_uint(v.x) & 0xFFFFE000u);
-        h.y = __uint_as_float(__float_as_uint(v.y) & 0xFFFFE000u);
-        h.z = __uint_as_float(__float_as_uint(v.z) & 0xFFFFE000u);
-        h.w = __uint_as_float(__float_as_uint(v.w) & 0xFFFFE000u);
-        l.x = v.x - h.x; l.y = v.y - h.y; l.z = v.z - h.z; l.w = v.w - h.w;
-        hi[i] = h;
-        lo[i] = l;
+          for (int kk = 0; kk < KH / 16; ++kk) {
+            const uint32_t koff = kk * 32;  // 16 halves = 32 bytes along the 64-byte row
+            const uint32_t first = (c == 0 && kk == 0) ? 0u : 1u;
+            mma_f16(acc, sdesc(ahi + koff), sdesc(bhi + koff), first);
+            mma_f16(acc, sdesc(ahi + koff), sdesc(blo + koff), 1u);
+            mma_f16(acc, sdesc(alo + koff), sdesc(bhi + koff), 1u);
+          }
+          mma_commit(smem_u32(&bar_empty[s]));
+        }
+        if (ok) mma_commit(smem_u32(&bar_accf[ab]));
+      }
+      // every MMA issued so far has completed once bar_done fires
+      mma_commit(smem_u32(&bar_done));
+      mbar_drain(smem_u32(&bar_done), 0u);
+    }
+  } else if (warp < 6) {
+    // ---------------- A split (warps 2-5, thread t owns row t of the block)
+    const int t = threadIdx.x - 64;  // 0..127
+    // 64-byte swizzle of 64-byte rows: 16-byte chunk c of row t sits at
+    // c ^ ((t >> 1) & 3)
+    const int sw = (t >> 1) & 3;
+    const int nchunks = my_tiles * kchunks;
+    for (int g = 0; g < nchunks; ++g) {
+      const int s = g % STAGES;
+      const uint32_t u = (uint32_t)(g / STAGES);
+      if (!mbar_wait(smem_u32(&bar_full[s]), u & 1u, abortp)) break;
+      unsigned char* a0 = stage_ptr(s, 0) + t * 64;  // row t of box 0 / of A_hi
+      unsigned char* a1 = stage_ptr(s, 1) + t * 64;  // row t of box 1 / of A_lo
+      // the whole row (32 FP32 values) into registers before it is overwritten
+      float v[32];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const float4 x0 = *reinterpret_cast<const float4*>(a0 + ((q ^ sw) << 4));
+        const float4 x1 = *reinterpret_cast<const float4*>(a1 + ((q ^ sw) << 4));
+        v[4 * q] = x0.x; v[4 * q + 1] = x0.y; v[4 * q + 2] = x0.z; v[4 * q + 3] = x0.w;
+        v[16 + 4 * q] = x1.x; v[17 + 4 * q] = x1.y; v[18 + 4 * q] = x1.z; v[19 + 4 * q] = x1.w;
+      }
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        uint4 h, l;
+        split8(v + 8 * q, sa, h, l);
+        *reinterpret_cast<uint4*>(a0 + ((q ^ sw) << 4)) = h;
+        *reinterpret_cast<uint4*>(a1 + ((q ^ sw) << 4)) = l;
       }
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
       __syncwarp();
       if (lane == 0) mbar_arrive(smem_u32(&bar_split[s]));
     }
-    // epilogue: TMEM lanes 32*(warp % 4) .. +31 hold rows r0 + that range
-    const bool acc_ok = mbar_wait(smem_u32(&bar_acc), 0u, abortp);
-    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  } else {
+    // ---------------- epilogue (warps 6-9): TMEM lanes 32*(warp % 4) .. +31
+    // hold rows r0 + that range of the tile
+    const float oscale = g_inv / sa;  // exact: both are powers of two
     const int q4 = warp & 3;
-    const int row = r0 + q4 * 32 + lane;
-    if (acc_ok) {
+    for (int i = 0; i < my_tiles; ++i) {
+      const int ab = i & 1;
+      const uint32_t v2 = (uint32_t)(i >> 1);
+      if (!mbar_wait(smem_u32(&bar_accf[ab]), v2 & 1u, abortp)) break;
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      const int T = blockIdx.x + i * gridDim.x;
+      const int r0 = (T / nblk_n) * BM, n0 = (T % nblk_n) * BN;
+      const int row = r0 + q4 * 32 + lane;
       for (int j = 0; j < BN; j += 16) {
         uint32_t v[16];
-        const uint32_t taddr = tmem + ((uint32_t)(q4 * 32) << 16) + (uint32_t)j;
+        const uint32_t taddr = tmem + ((uint32_t)(q4 * 32) << 16) + (uint32_t)(ab * BN + j);
         asm volatile(
             "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,"
             "%13,%14,%15}, [%16];"
@@ -247,16 +342,20 @@ __global__ void __launch_bounds__(NTHREADS, 1)
           if (n + 16 <= ncols) {
 #pragma unroll
             for (int u = 0; u < 4; ++u)
-              reinterpret_cast<float4*>(o)[u] =
-                  make_float4(__uint_as_float(v[4 * u]), __uint_as_float(v[4 * u + 1]),
-                              __uint_as_float(v[4 * u + 2]), __uint_as_float(v[4 * u + 3]));
+              reinterpret_cast<float4*>(o)[u] = make_float4(
+                  __uint_as_float(v[4 * u]) * oscale, __uint_as_float(v[4 * u + 1]) * oscale,
+                  __uint_as_float(v[4 * u + 2]) * oscale, __uint_as_float(v[4 * u + 3]) * oscale);
           } else {
 #pragma unroll
             for (int u = 0; u < 16; ++u)
-              if (n + u < ncols) o[u] = __uint_as_float(v[u]);
+              if (n + u < ncols) o[u] = __uint_as_float(v[u]) * oscale;
           }
         }
       }
+      // this warp's reads of accumulator ab are complete: hand it back
+      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+      __syncwarp();
+      if (lane == 0) mbar_arrive(smem_u32(&bar_acce[ab]));
     }
   }
 
@@ -291,16 +390,16 @@ EncodeTiledFn encode_fn() {
   return fn;
 }
 
-bool encode_2d(CUtensorMap* m, const void* ptr, uint64_t inner, uint64_t outer,
-               uint64_t row_bytes, uint32_t box_inner, uint32_t box_outer) {
+bool encode_2d(CUtensorMap* m, CUtensorMapDataType dt, const void* ptr, uint64_t inner,
+               uint64_t outer, uint64_t row_bytes, uint32_t box_inner, uint32_t box_outer) {
   EncodeTiledFn fn = encode_fn();
   if (!fn) return false;
   const cuuint64_t dims[2] = {inner, outer};
   const cuuint64_t strides[1] = {row_bytes};
   const cuuint32_t box[2] = {box_inner, box_outer};
   const cuuint32_t estr[2] = {1, 1};
-  return fn(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<void*>(ptr), dims, strides, box, estr,
-            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+  return fn(m, dt, 2, const_cast<void*>(ptr), dims, strides, box, estr,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B,
             CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
@@ -308,32 +407,66 @@ bool encode_2d(CUtensorMap* m, const void* ptr, uint64_t inner, uint64_t outer,
 
 size_t xform_tc_bpad(int nx) { return (size_t)(((2 * nx + BN - 1) / BN) * BN); }
 
+float xform_tc_split(const std::vector<float>& G, std::vector<uint16_t>& hi,
+                     std::vector<uint16_t>& lo) {
+  float gmax = 0.f;
+  for (float g : G) gmax = std::max(gmax, std::fabs(g));
+  int e = 0;
+  if (gmax > 0.f) std::frexp(gmax, &e);
+  const float sg = std::ldexp(1.f, 14 - e);  // sg |G| < 2^14
+  hi.assign(G.size(), 0);
+  lo.assign(G.size(), 0);
+  for (size_t i = 0; i < G.size(); ++i) {
+    const float g = G[i] * sg;
+    const __half h = __float2half_rn(g);
+    const __half l = __float2half_rn(g - __half2float(h));
+    memcpy(&hi[i], &h, 2);
+    memcpy(&lo[i], &l, 2);
+  }
+  return 1.f / sg;
+}
+
 cudaError_t xform_tc_prepare(XformTc* x, int rows, int nx, int ldo_floats, const float* in,
-                             float* out, const float* Bhi, const float* Blo) {
+                             float* out, const void* Ghi, const void* Glo, float g_inv,
+                             const unsigned* amax) {
   const uint64_t K2 = 2 * (uint64_t)nx;
   const uint64_t P = xform_tc_bpad(nx);
   x->rows = rows;
   x->ncols = (int)K2;
   x->ldo = ldo_floats;
-  x->kchunks = (int)((K2 + BK - 1) / BK);
+  x->kchunks = (int)((K2 + KH - 1) / KH);
   x->nblk_n = (int)(P / BN);
   x->out = out;
+  x->amax = amax;
+  x->g_inv = g_inv;
   if ((ldo_floats * 4) % 16 != 0) return cudaErrorInvalidValue;
-  if (!encode_2d(&x->tmA, in, K2, (uint64_t)rows, (uint64_t)ldo_floats * 4, BK, BM))
+  if (!encode_2d(&x->tmA, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, in, K2, (uint64_t)rows,
+                 (uint64_t)ldo_floats * 4, AF_BOX, BM))
     return cudaErrorInvalidValue;
-  if (!encode_2d(&x->tmBhi, Bhi, P, P, P * 4, BK, BN)) return cudaErrorInvalidValue;
-  if (!encode_2d(&x->tmBlo, Blo, P, P, P * 4, BK, BN)) return cudaErrorInvalidValue;
+  if (!encode_2d(&x->tmBhi, CU_TENSOR_MAP_DATA_TYPE_FLOAT16, Ghi, P, P, P * 2, KH, BN))
+    return cudaErrorInvalidValue;
+  if (!encode_2d(&x->tmBlo, CU_TENSOR_MAP_DATA_TYPE_FLOAT16, Glo, P, P, P * 2, KH, BN))
+    return cudaErrorInvalidValue;
   return cudaSuccess;
 }
 
 cudaError_t launch_xform_tc(const XformTc& x, int* err, cudaStream_t st) {
-  const size_t smem = (size_t)STAGES * STAGE_BYTES + 1024;
+  const size_t smem = (size_t)STAGES * STAGE_BYTES + 1024 + GUARD_BYTES;
   cudaError_t e =
       cudaFuncSetAttribute(k_xform_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   if (x.rows == 0) return cudaSuccess;
-  dim3 grid((x.rows + BM - 1) / BM, x.nblk_n);
+  // persistent: one CTA per SM over all tiles
+  static int nsm = 0;
+  if (nsm == 0) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    if (nsm <= 0) nsm = 1;
+  }
+  const int ntiles = x.nblk_n * ((x.rows + BM - 1) / BM);
+  const int grid = ntiles < nsm ? ntiles : nsm;
   k_xform_tc<<<grid, NTHREADS, smem, st>>>(x.tmA, x.tmBhi, x.tmBlo, x.out, x.rows, x.ncols, x.ldo,
-                                           x.kchunks, err);
+                                           x.kchunks, x.nblk_n, ntiles, x.amax, x.g_inv, err);
   return cudaGetLastError();
 }
