@@ -36,7 +36,7 @@ KERNELS = ["resid_gamma_fft", "xform_fwd", "tridiag", "xform_inv", "ifft_gamma_u
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=30)
+    ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-check", action="store_true", help="skip the oracle error check")

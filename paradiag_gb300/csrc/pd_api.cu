@@ -126,9 +126,13 @@ FwdArgs fwd_base_impl(const pd_plan* p) {
     const dfc c = dfc_from(s * kap[i]);
     a.kap[i].hi = c.hi; a.kap[i].lo = c.lo;
   }
+  a.c2exact = 1;
   for (int m = 0; m < 3; ++m) {
     const dfc c = dfc_from(p->tb.c2[m]);
     a.e2[m].hi = c.hi; a.e2[m].lo = c.lo;
+    int e = 0;
+    const double fr = std::frexp(std::fabs(p->tb.c2[m]), &e);
+    if (!(p->tb.c2[m] == 0.0 || fr == 0.5)) a.c2exact = 0;
   }
   a.rscale2 = 1.0 / (s * s);
   a.gam = p->gam;
@@ -582,9 +586,10 @@ pd_status plan_create_internal(const pd_space* sp, int nt, double dt, double alp
   p->precision = precision;
   p->fp64 = precision == PD_FP64;
   p->stream = (cudaStream_t)stream;
-  // tile of TX columns x Nt rows: at most 16 KB of shared memory (8 complex
-  // elements per thread, <= 64 registers), so four blocks stay resident per SM
-  const int budget = p->fp64 ? 2048 : 4096;
+  // tile of TX columns x Nt rows: 16 complex elements per thread in the mixed
+  // path (one radix-16 butterfly per thread and pass, 32 KB of shared memory
+  // for Nt >= 256), 4 in the FP64 path
+  const int budget = p->fp64 ? 2048 : 8192;
   p->TX = std::max(2, std::min(32, budget / (Mb ? Mb : nt)));
 
   // spatial stencil

@@ -62,6 +62,7 @@ struct FwdArgs {
   const double* B64;              // FP64 residual: b
   dfc kap[5];                     // mixed: s*K coefficients (c, xl, xu, yl, yu)
   dfc e2[3];                      // mixed: c2[m]
+  int c2exact = 0;                // mixed: every c2[m] is 0 or a power of two
   double rscale2;                 // mixed: 1/s^2 (norm of r' = s r)
   const void* gam;                // gamma_n (float or double)
   const void* tw;                 // e^{-2 pi i m / N}, m < N (float2 or double2)

@@ -10,6 +10,8 @@
 // A_k = (Z_k + conj Z_{N-k})/2, B_k = (Z_k - conj Z_{N-k})/(2i).
 // The transform convention is the forward DFT with exp(-2 pi i k n / Nt); the
 // eigenvalues used in step (b) follow the same convention (see pd_api.cu).
+#include <type_traits>
+
 #include "pd_internal.h"
 
 namespace {
@@ -32,13 +34,42 @@ PD_D C twid(const C* tw, int idx) {
   return w;
 }
 
-// in-register DFT of size R with the exp(-+2 pi i / R) root
+// v * exp(-+2 pi i e / 16) for a compile-time e (INV: the + sign)
+template <typename C, bool INV, int E>
+PD_D C w16(C v) {
+  using R = decltype(v.x);
+  constexpr int e = E & 15;
+  if constexpr (e == 0) {
+    return v;
+  } else if constexpr (e == 4) {
+    return INV ? cmul_pi(v) : cmul_mi(v);
+  } else if constexpr (e == 8) {
+    return mk(-v.x, -v.y);
+  } else if constexpr (e == 12) {
+    return INV ? cmul_mi(v) : cmul_pi(v);
+  } else {
+    // cos and sin of 2 pi e / 16 from the values at pi/8, pi/4 and 3 pi/8
+    constexpr double C1 = 0.92387953251128675613, S1 = 0.38268343236508977173;
+    constexpr double H = 0.70710678118654752440;
+    constexpr int q = e & 3;  // position inside the quadrant
+    constexpr double cb = q == 1 ? C1 : q == 2 ? H : S1;
+    constexpr double sb = q == 1 ? S1 : q == 2 ? H : C1;
+    // rotate the first-quadrant angle by the quadrant index e / 4
+    constexpr int quad = e >> 2;
+    constexpr double c0 = quad == 0 ? cb : quad == 1 ? -sb : quad == 2 ? -cb : sb;
+    constexpr double s0 = quad == 0 ? sb : quad == 1 ? cb : quad == 2 ? -sb : -cb;
+    const R c = (R)c0, s = INV ? (R)s0 : (R)-s0;
+    return mk(v.x * c - v.y * s, v.x * s + v.y * c);
+  }
+}
+
+// in-register DFT of size R (2, 4, 8, 16) with the exp(-+2 pi i / R) root
 template <typename C, bool INV, int R>
 PD_D void dft_r(C* v) {
   if constexpr (R == 2) {
     C a = cadd(v[0], v[1]), b = csub(v[0], v[1]);
     v[0] = a; v[1] = b;
-  } else {
+  } else if constexpr (R == 4) {
     C s02 = cadd(v[0], v[2]), d02 = csub(v[0], v[2]);
     C s13 = cadd(v[1], v[3]), d13 = csub(v[1], v[3]);
     C jd13 = INV ? cmul_pi(d13) : cmul_mi(d13);  // (-+i)(x1 - x3)
@@ -46,18 +77,60 @@ PD_D void dft_r(C* v) {
     v[1] = cadd(d02, jd13);
     v[2] = csub(s02, s13);
     v[3] = csub(d02, jd13);
+  } else if constexpr (R == 8) {
+    // n = 2 n1 + n2, k = k1 + 4 k2: DFT-4 over n1, twiddle W8^(n2 k1), DFT-2 over n2
+    C e[4] = {v[0], v[2], v[4], v[6]}, o[4] = {v[1], v[3], v[5], v[7]};
+    dft_r<C, INV, 4>(e);
+    dft_r<C, INV, 4>(o);
+    o[1] = w16<C, INV, 2>(o[1]);
+    o[2] = w16<C, INV, 4>(o[2]);
+    o[3] = w16<C, INV, 6>(o[3]);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      v[k] = cadd(e[k], o[k]);
+      v[k + 4] = csub(e[k], o[k]);
+    }
+  } else {
+    // n = 4 n1 + n2, k = k1 + 4 k2: DFT-4 over n1, twiddle W16^(n2 k1), DFT-4 over n2
+    C y[4][4];
+#pragma unroll
+    for (int n2 = 0; n2 < 4; ++n2) {
+      y[n2][0] = v[n2]; y[n2][1] = v[4 + n2]; y[n2][2] = v[8 + n2]; y[n2][3] = v[12 + n2];
+      dft_r<C, INV, 4>(y[n2]);
+    }
+    y[1][1] = w16<C, INV, 1>(y[1][1]);
+    y[1][2] = w16<C, INV, 2>(y[1][2]);
+    y[1][3] = w16<C, INV, 3>(y[1][3]);
+    y[2][1] = w16<C, INV, 2>(y[2][1]);
+    y[2][2] = w16<C, INV, 4>(y[2][2]);
+    y[2][3] = w16<C, INV, 6>(y[2][3]);
+    y[3][1] = w16<C, INV, 3>(y[3][1]);
+    y[3][2] = w16<C, INV, 6>(y[3][2]);
+    y[3][3] = w16<C, INV, 9>(y[3][3]);
+#pragma unroll
+    for (int k1 = 0; k1 < 4; ++k1) {
+      C z[4] = {y[0][k1], y[1][k1], y[2][k1], y[3][k1]};
+      dft_r<C, INV, 4>(z);
+      v[k1] = z[0]; v[k1 + 4] = z[1]; v[k1 + 8] = z[2]; v[k1 + 12] = z[3];
+    }
   }
 }
 
-// One Stockham pass of radix R over TXc interleaved columns stored [N][TXc].
-// Every butterfly is read into registers before the barrier and written after
-// it, so the pass runs in place.
-template <typename C, bool INV, int R, int BPT>
-PD_D void fft_pass(C* sm, int N, int lgTXc, int lgNs, const C* tw) {
-  const int TXc = 1 << lgTXc;
-  const int Ns = 1 << lgNs;
-  const int nb = (N / R) << lgTXc;
-  const int step = N / (Ns * R);
+// One Stockham pass of radix R = 2^LR over TXc interleaved columns stored
+// [N][TXc].  Butterfly b = (j << lgTXc) + c (column c, index j < N/R) reads
+// rows j + r N/R, applies the twiddles w_N^(q r N/(R Ns)) with q = j mod Ns,
+// and writes rows (j - q) R + q + k Ns; with every size a power of two all the
+// index arithmetic is shifts and masks.  Every butterfly is read into
+// registers before the barrier and written after it, so the pass runs in place.
+template <typename C, bool INV, int LR, int BPT>
+PD_D void fft_pass(C* sm, int lgN, int lgTXc, int lgNs, const C* tw) {
+  constexpr int R = 1 << LR;
+  const int lgNB = lgN - LR + lgTXc;        // butterflies: (N / R) TXc
+  const int nb = 1 << lgNB;
+  const int lgStep = lgN - LR - lgNs;
+  const int lgOut = lgNs + lgTXc;
+  const int lomask = (1 << lgOut) - 1;
+  const int qmask = (1 << lgNs) - 1;
   C v[BPT][R];
   int dst[BPT];
 #pragma unroll
@@ -65,16 +138,16 @@ PD_D void fft_pass(C* sm, int N, int lgTXc, int lgNs, const C* tw) {
     const int b = threadIdx.x + t * TT;
     dst[t] = -1;
     if (b < nb) {
-      const int c = b & (TXc - 1), j = b >> lgTXc;
-      const int q = j & (Ns - 1);
+      const int tq = ((b >> lgTXc) & qmask) << lgStep;
 #pragma unroll
       for (int r = 0; r < R; ++r) {
-        C x = sm[((j + r * (N / R)) << lgTXc) + c];
-        if (r > 0) x = cmul(x, twid<C, INV>(tw, q * r * step));
+        C x = sm[b + (r << lgNB)];
+        if (r > 0) x = cmul(x, twid<C, INV>(tw, tq * r));
         v[t][r] = x;
       }
       dft_r<C, INV, R>(v[t]);
-      dst[t] = (((((j >> lgNs) * R) << lgNs) + q) << lgTXc) + c;
+      const int lo = b & lomask;
+      dst[t] = ((b - lo) << LR) + lo;
     }
   }
   __syncthreads();
@@ -82,25 +155,29 @@ PD_D void fft_pass(C* sm, int N, int lgTXc, int lgNs, const C* tw) {
   for (int t = 0; t < BPT; ++t) {
     if (dst[t] >= 0) {
 #pragma unroll
-      for (int r = 0; r < R; ++r) sm[dst[t] + ((r * Ns) << lgTXc)] = v[t][r];
+      for (int r = 0; r < R; ++r) sm[dst[t] + (r << lgOut)] = v[t][r];
     }
   }
   __syncthreads();
 }
 
-// Full complex FFT of length N (power of two) on TXc columns; EPT is the
-// maximum number of complex elements per thread (N * TXc <= EPT * TT).
+// Full complex FFT of length N = 2^logN on TXc columns: one pass of radix
+// 2, 4 or 8 for logN mod 4, then radix-16 passes; EPT is the maximum number of
+// complex elements per thread (N TXc <= EPT TT).
 template <typename C, bool INV, int EPT>
 PD_D void fft_tile(C* sm, int N, int logN, int lgTXc, const C* tw) {
+  (void)N;
+  constexpr int B16 = EPT / 16 > 0 ? EPT / 16 : 1;
+  constexpr int B8 = EPT / 8 > 0 ? EPT / 8 : 1;
+  constexpr int B4 = EPT / 4 > 0 ? EPT / 4 : 1;
+  constexpr int B2 = EPT / 2 > 0 ? EPT / 2 : 1;
   int lgNs = 0;
-  if (logN & 1) {
-    fft_pass<C, INV, 2, EPT / 2>(sm, N, lgTXc, lgNs, tw);
-    lgNs = 1;
-  }
-  for (int p = 0; p < logN / 2; ++p) {
-    fft_pass<C, INV, 4, EPT / 4>(sm, N, lgTXc, lgNs, tw);
-    lgNs += 2;
-  }
+  const int rem = logN & 3;
+  if (rem == 1) fft_pass<C, INV, 1, B2>(sm, logN, lgTXc, lgNs, tw);
+  else if (rem == 2) fft_pass<C, INV, 2, B4>(sm, logN, lgTXc, lgNs, tw);
+  else if (rem == 3) fft_pass<C, INV, 3, B8>(sm, logN, lgTXc, lgNs, tw);
+  lgNs = rem;
+  for (; lgNs < logN; lgNs += 4) fft_pass<C, INV, 4, B16>(sm, logN, lgTXc, lgNs, tw);
 }
 
 // Length-N DFT of TXc columns by Bluestein's algorithm: a_n = z_n w_n (zero
@@ -200,6 +277,61 @@ PD_D void acc_add_prod(Acc& A, dfc k, float uh, float ul) {
 }
 PD_D df acc_val(const Acc& A) { return fast_two_sum(A.s, A.e); }
 
+// ---- the same compensated arithmetic on two independent values at once (the
+// lanes of a float2), with the paired FP32 instructions of sm_100+
+PD_D float2 f2add(float2 a, float2 b) { return __fadd2_rn(a, b); }
+PD_D float2 f2mul(float2 a, float2 b) { return __fmul2_rn(a, b); }
+PD_D float2 f2fma(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+PD_D float2 f2sub(float2 a, float2 b) {
+  unsigned long long x = *reinterpret_cast<unsigned long long*>(&a);
+  unsigned long long y = *reinterpret_cast<unsigned long long*>(&b);
+  unsigned long long d;
+  asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(x), "l"(y));
+  return *reinterpret_cast<float2*>(&d);
+}
+struct DF2 {    // two double-float values: (hi_A, hi_B), (lo_A, lo_B)
+  float2 hi, lo;
+};
+struct Acc2 {   // two compensated sums
+  float2 s, e;
+};
+PD_D DF2 df2_pack(float2 a, float2 b) { return DF2{make_float2(a.x, b.x), make_float2(a.y, b.y)}; }
+// A += h + l (two-sum on the high parts)
+PD_D void acc2_add(Acc2& A, float2 h, float2 l) {
+  const float2 t = f2add(A.s, h);
+  const float2 bb = f2sub(t, A.s);
+  const float2 err = f2add(f2sub(A.s, f2sub(t, bb)), f2sub(h, bb));
+  A.s = t;
+  A.e = f2add(A.e, f2add(err, l));
+}
+// A -= h + l
+PD_D void acc2_sub(Acc2& A, float2 h, float2 l) {
+  const float2 t = f2sub(A.s, h);
+  const float2 bb = f2sub(t, A.s);
+  const float2 err = f2sub(f2sub(A.s, f2sub(t, bb)), f2add(h, bb));
+  A.s = t;
+  A.e = f2sub(f2add(A.e, err), l);
+}
+// coefficient k = kh + kl broadcast to both lanes, with its negation
+struct K2 {
+  float2 h, nh, nl;
+};
+PD_D K2 k2_of(dfc k) {
+  return K2{make_float2(k.hi, k.hi), make_float2(-k.hi, -k.hi), make_float2(-k.lo, -k.lo)};
+}
+// A += k u (two-product of the high parts, the cross terms into the error)
+PD_D void acc2_add_prod(Acc2& A, const K2& k, const DF2& u) {
+  const float2 p = f2mul(u.hi, k.h);
+  float2 npe = f2fma(u.hi, k.nh, p);   // p - u.hi k.hi = -(rounding error of p)
+  npe = f2fma(u.hi, k.nl, npe);
+  npe = f2fma(u.lo, k.nh, npe);
+  const float2 t = f2add(A.s, p);
+  const float2 bb = f2sub(t, A.s);
+  const float2 err = f2add(f2sub(A.s, f2sub(t, bb)), f2sub(p, bb));
+  A.s = t;
+  A.e = f2sub(f2add(A.e, err), npe);
+}
+
 // Global loads of one time row at this thread's column (centre, segment-edge
 // x-neighbours, y-neighbours); zeros outside [0, N) or outside the grid.
 template <typename V>
@@ -243,6 +375,33 @@ PD_D void stencil_df(const FwdArgs& a, const ColGeom& g, const RowLd<float2>& L,
   if (a.st.dim == 2) {
     acc_add_prod(A, a.kap[3], L.d.x, L.d.y);
     acc_add_prod(A, a.kap[4], L.u.x, L.u.y);
+  }
+  KU = A;
+}
+
+// Packed form of stencil_df: two time rows (lanes A, B) of this thread's column.
+PD_D void stencil_df2(const FwdArgs& a, const ColGeom& g, const RowLd<float2>& LA,
+                      const RowLd<float2>& LB, int TX, const K2* kk, DF2& Uc, Acc2& KU) {
+  const unsigned FULL = 0xffffffffu;
+  Uc = df2_pack(LA.c, LB.c);
+  DF2 lf, rt;
+  lf.hi.x = __shfl_up_sync(FULL, Uc.hi.x, 1, TX);
+  lf.hi.y = __shfl_up_sync(FULL, Uc.hi.y, 1, TX);
+  lf.lo.x = __shfl_up_sync(FULL, Uc.lo.x, 1, TX);
+  lf.lo.y = __shfl_up_sync(FULL, Uc.lo.y, 1, TX);
+  rt.hi.x = __shfl_down_sync(FULL, Uc.hi.x, 1, TX);
+  rt.hi.y = __shfl_down_sync(FULL, Uc.hi.y, 1, TX);
+  rt.lo.x = __shfl_down_sync(FULL, Uc.lo.x, 1, TX);
+  rt.lo.y = __shfl_down_sync(FULL, Uc.lo.y, 1, TX);
+  if (g.left != 1) lf = df2_pack(LA.l, LB.l);
+  if (g.right != 1) rt = df2_pack(LA.r, LB.r);
+  Acc2 A = {make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
+  acc2_add_prod(A, kk[0], Uc);
+  acc2_add_prod(A, kk[1], lf);
+  acc2_add_prod(A, kk[2], rt);
+  if (a.st.dim == 2) {
+    acc2_add_prod(A, kk[3], df2_pack(LA.d, LB.d));
+    acc2_add_prod(A, kk[4], df2_pack(LA.u, LB.u));
   }
   KU = A;
 }
@@ -335,57 +494,84 @@ PD_D void time_fwd_body(const FwdArgs& a, int tile) {
   } else {
     const ColGeom g = col_geom(a.st, s, x, TX);
     if constexpr (PREC == 0) {
-      // rows before the first level are zero, so the carried terms need no checks
-      df U1 = df_make(0.f, 0.f), U2 = U1, U0;
-      Acc K1 = {0.f, 0.f}, K2 = K1, K0;
-      if (BAND == 2) stencil_df(a, g, load_row(a.Udf, a, g, n_beg - 2), TX, U2, K2);
-      stencil_df(a, g, load_row(a.Udf, a, g, n_beg - 1), TX, U1, K1);
-      // two rows of loads in flight ahead of the row being computed
-      RowLd<float2> cur = load_row(a.Udf, a, g, n_beg);
-      float2 bcur = (n_beg < N && g.valid) ? __ldg(&a.Bdf[(size_t)n_beg * S + s])
-                                           : make_float2(0.f, 0.f);
-      RowLd<float2> nx1 = load_row(a.Udf, a, g, 1 < rpc ? n_beg + 1 : -1);
-      float2 bnx1 = (1 < rpc && n_beg + 1 < N && g.valid)
-                        ? __ldg(&a.Bdf[(size_t)(n_beg + 1) * S + s]) : make_float2(0.f, 0.f);
-      // the c2 weights (theta, 1 - theta, 1/2, ...) negated once
-      dfc m0 = a.e2[0], m1 = a.e2[1], m2 = a.e2[2];
+      // Two row chunks per thread, computed together in the two lanes of
+      // float2 values: lane A rows nA + i, lane B rows nB + i (i < rpc2).
+      // Rows before the first level are zero, so the carried terms need no checks.
+      const int rpc2 = (N + 2 * nchunks - 1) / (2 * nchunks);
+      const int nA = chunk * rpc2, nB = nA + nchunks * rpc2;
+      K2 kk[5];
+#pragma unroll
+      for (int q = 0; q < 5; ++q) kk[q] = k2_of(a.kap[q]);
+      DF2 U1 = {make_float2(0.f, 0.f), make_float2(0.f, 0.f)}, U2 = U1, U0;
+      Acc2 K1 = {make_float2(0.f, 0.f), make_float2(0.f, 0.f)}, K2v = K1, K0;
+      if (BAND == 2)
+        stencil_df2(a, g, load_row(a.Udf, a, g, nA - 2), load_row(a.Udf, a, g, nB - 2), TX, kk,
+                    U2, K2v);
+      stencil_df2(a, g, load_row(a.Udf, a, g, nA - 1), load_row(a.Udf, a, g, nB - 1), TX, kk, U1,
+                  K1);
+      auto ldb = [&](int n) -> float2 {
+        return (n >= 0 && n < N && g.valid) ? __ldg(&a.Bdf[(size_t)n * S + s])
+                                            : make_float2(0.f, 0.f);
+      };
+      // one row of loads in flight ahead of the row being computed
+      RowLd<float2> cA = load_row(a.Udf, a, g, nA), cB = load_row(a.Udf, a, g, nB);
+      float2 bA = ldb(nA), bB = ldb(nB);
+      // the c2 weights negated once; when every c2[m] is 0 or a power of two
+      // (backward Euler, Crank-Nicolson, leap-frog) the weighted terms are exact
+      // scalings
+      dfc m0 = a.e2[0], mb = BAND == 1 ? a.e2[1] : a.e2[2];
       m0.hi = -m0.hi; m0.lo = -m0.lo;
-      m1.hi = -m1.hi; m1.lo = -m1.lo;
-      m2.hi = -m2.hi; m2.lo = -m2.lo;
-      float part = 0.f;
-      for (int i = 0; i < rpc; ++i) {
-        const int n = n_beg + i;
-        const RowLd<float2> nxt = load_row(a.Udf, a, g, i + 2 < rpc ? n + 2 : -1);
-        const float2 bnxt = (i + 2 < rpc && n + 2 < N && g.valid)
-                                ? __ldg(&a.Bdf[(size_t)(n + 2) * S + s]) : make_float2(0.f, 0.f);
-        stencil_df(a, g, cur, TX, U0, K0);  // uniform across the warp
-        if (n < N) {
-          // r' = s b - U_n + U_{n-1} - c2[0] (sK)U_n - c2[1] (sK)U_{n-1}        (theta)
-          // r' = s b - U_n + 2 U_{n-1} - U_{n-2} - c2[0] (sK)U_n - c2[2] (sK)U_{n-2} (leap-frog)
-          Acc A = {bcur.x, bcur.y};
-          acc_add(A, -U0.hi, -U0.lo);
-          if (BAND == 1) {
-            acc_add(A, U1.hi, U1.lo);
-            acc_add_prod(A, m0, K0.s, K0.e);
-            acc_add_prod(A, m1, K1.s, K1.e);
-          } else {
-            acc_add(A, 2.f * U1.hi, 2.f * U1.lo);
-            acc_add(A, -U2.hi, -U2.lo);
-            acc_add_prod(A, m0, K0.s, K0.e);
-            acc_add_prod(A, m2, K2.s, K2.e);
-          }
-          const df r = acc_val(A);
-          part = fmaf(r.hi, r.hi, part);
-          const float gm = gam[n];
-          smr[n * TX + x] = g.valid ? fmaf(r.hi, gm, r.lo * gm) : 0.f;
+      mb.hi = -mb.hi; mb.lo = -mb.lo;
+      const bool exact = a.c2exact != 0;
+      const K2 km0 = k2_of(m0), kmb = k2_of(mb);
+      const float2 sm0 = make_float2(m0.hi, m0.hi), smb = make_float2(mb.hi, mb.hi);
+      const float2 two = make_float2(2.f, 2.f);
+      float2 part = make_float2(0.f, 0.f);
+      for (int i = 0; i < rpc2; ++i) {
+        const int na = nA + i, nb = nB + i;
+        const bool more = i + 1 < rpc2;
+        const RowLd<float2> xA = load_row(a.Udf, a, g, more ? na + 1 : -1);
+        const RowLd<float2> xB = load_row(a.Udf, a, g, more ? nb + 1 : -1);
+        const float2 yA = ldb(more ? na + 1 : -1), yB = ldb(more ? nb + 1 : -1);
+        stencil_df2(a, g, cA, cB, TX, kk, U0, K0);  // uniform across the warp
+        // r' = s b - U_n + U_{n-1} - c2[0] (sK)U_n - c2[1] (sK)U_{n-1}        (theta)
+        // r' = s b - U_n + 2 U_{n-1} - U_{n-2} - c2[0] (sK)U_n - c2[2] (sK)U_{n-2} (leap-frog)
+        const DF2 Bv = df2_pack(bA, bB);
+        Acc2 A = {Bv.hi, Bv.lo};
+        acc2_sub(A, U0.hi, U0.lo);
+        if (BAND == 1) {
+          acc2_add(A, U1.hi, U1.lo);
+        } else {
+          acc2_add(A, f2mul(two, U1.hi), f2mul(two, U1.lo));
+          acc2_sub(A, U2.hi, U2.lo);
         }
-        U2 = U1; K2 = K1; U1 = U0; K1 = K0;
-        cur = nx1;
-        bcur = bnx1;
-        nx1 = nxt;
-        bnx1 = bnxt;
+        const Acc2& Kb = BAND == 1 ? K1 : K2v;
+        if (exact) {
+          acc2_add(A, f2mul(sm0, K0.s), f2mul(sm0, K0.e));
+          if (mb.hi != 0.f) acc2_add(A, f2mul(smb, Kb.s), f2mul(smb, Kb.e));
+        } else {
+          acc2_add_prod(A, km0, DF2{K0.s, K0.e});
+          acc2_add_prod(A, kmb, DF2{Kb.s, Kb.e});
+        }
+        // value = s + e, renormalised
+        const float2 rh = f2add(A.s, A.e);
+        const float2 rl = f2sub(A.e, f2sub(rh, A.s));
+        // rows at or past N (lane B of the last chunks) add nothing
+        const float2 rn = make_float2(na < N && g.valid ? rh.x : 0.f, nb < N && g.valid ? rh.y : 0.f);
+        part = f2fma(rn, rn, part);
+        if (g.valid) {
+          if (na < N) smr[na * TX + x] = fmaf(rh.x, gam[na], rl.x * gam[na]);
+          if (nb < N) smr[nb * TX + x] = fmaf(rh.y, gam[nb], rl.y * gam[nb]);
+        } else {
+          if (na < N) smr[na * TX + x] = 0.f;
+          if (nb < N) smr[nb * TX + x] = 0.f;
+        }
+        U2 = U1; K2v = K1; U1 = U0; K1 = K0;
+        cA = xA; cB = xB;
+        bA = yA; bB = yB;
       }
-      nrm = (double)part * a.rscale2;
+      const float part1 = part.x + part.y;
+      nrm = (double)part1 * a.rscale2;
     } else {
       double U1 = 0, U2 = 0, K1 = 0, K2 = 0, U0, K0;
       const TimeBand& tb = a.tb;
@@ -464,11 +650,11 @@ PD_D void time_fwd_body(const FwdArgs& a, int tile) {
 // single problem: block b owns tile b; batch: the work table maps each block to
 // (problem, tile) and the arguments come from the per-problem descriptors
 template <int PREC, int BAND, int EPT>
-__global__ void __launch_bounds__(TT, PREC == 0 ? 4 : 2) k_time_fwd(FwdArgs a) {
+__global__ void __launch_bounds__(TT, PREC == 0 ? 3 : 2) k_time_fwd(FwdArgs a) {
   time_fwd_body<PREC, BAND, EPT>(a, blockIdx.x);
 }
 template <int PREC, int BAND, int EPT>
-__global__ void __launch_bounds__(TT, PREC == 0 ? 4 : 2) k_time_fwd_batch(const FwdArgs* __restrict__ descs,
+__global__ void __launch_bounds__(TT, PREC == 0 ? 3 : 2) k_time_fwd_batch(const FwdArgs* __restrict__ descs,
                                                           const int2* __restrict__ work) {
   const int2 w = work[blockIdx.x];
   time_fwd_body<PREC, BAND, EPT>(descs[w.x], w.y);
@@ -600,9 +786,11 @@ __global__ void __launch_bounds__(TT, PREC == 0 ? 4 : 2) k_time_inv_batch(const 
 }
 
 // complex elements per thread needed by a tile of N x TX/2 columns
+// complex elements per thread of a tile; the tile budgets of the plans
+// (N TX <= 8192 mixed, <= 2048 FP64) keep it at 16 or less
 inline int ept_for(int N, int TX) {
   const int e = (N * (TX / 2) + TT - 1) / TT;
-  return e <= 4 ? 4 : e <= 8 ? 8 : e <= 16 ? 16 : 32;
+  return e <= 4 ? 4 : e <= 8 ? 8 : 16;
 }
 
 template <int PREC, int BAND, int EPT>
@@ -622,8 +810,7 @@ cudaError_t launch_fwd_t(const FwdArgs& a, cudaStream_t st) {
   switch (ept_for(a.xf.M ? a.xf.M : a.N, a.TX)) {
     case 4: return launch_fwd_e<PREC, BAND, 4>(a, st);
     case 8: return launch_fwd_e<PREC, BAND, 8>(a, st);
-    case 16: return launch_fwd_e<PREC, BAND, 16>(a, st);
-    default: return launch_fwd_e<PREC, BAND, 32>(a, st);
+    default: return launch_fwd_e<PREC, BAND, 16>(a, st);
   }
 }
 
@@ -652,8 +839,7 @@ cudaError_t launch_inv_t(const InvArgs& a, cudaStream_t st) {
   switch (ept_for(a.xf.M ? a.xf.M : a.N, a.TX)) {
     case 4: return launch_inv_e<PREC, 4>(a, st);
     case 8: return launch_inv_e<PREC, 8>(a, st);
-    case 16: return launch_inv_e<PREC, 16>(a, st);
-    default: return launch_inv_e<PREC, 32>(a, st);
+    default: return launch_inv_e<PREC, 16>(a, st);
   }
 }
 
