@@ -238,24 +238,27 @@ pd_status solve_stationary(pd_plan* p, const double* b, double* u, double tol, i
   const size_t ns = NS(p);
   CU(cudaMemsetAsync(p->dsc, 0, 2 * sizeof(double), p->stream));
   CU(cudaMemsetAsync(p->dflag, 0, sizeof(int), p->stream));
-  LK(launch_norm2(b, ns, p->dsc, p->stream));
-  if (!p->fp64) {
-    LK(launch_to_df(u, 1.0, p->Udf, ns, p->stream));
-    LK(launch_to_df(b, p->s_scale, p->Bdf, ns, p->stream));
-  }
+  // ||b||^2 into dsc[0]: FP64 on the FP64 path; on the mixed path ||s b||^2
+  // from the split (rescaled after the copy to the host)
+  if (p->fp64) LK(launch_norm2(b, ns, p->dsc, p->stream));
+  else LK(launch_entry_df(u, b, p->s_scale, p->Udf, p->Bdf, ns, p->dsc, p->stream));
   int it = 0;
-  double rel = 0.0;
+  double rel = 0.0, prev_rel = -1.0;
+  // when the observed contraction predicts that the next residual meets the
+  // tolerance with margin, the next forward kernel computes the residual norm
+  // only; if the prediction fails it is run again with the transform
+  bool norm_only = false;
   pd_status st = PD_OK;
   for (;;) {
     CU(cudaMemsetAsync(p->dsc + 1, 0, sizeof(double), p->stream));
     FwdArgs fa = fwd_base_impl(p);
-    fa.mode = FWD_RESIDUAL;
+    fa.mode = norm_only ? FWD_RESIDUAL_NORM : FWD_RESIDUAL;
     fa.norm2 = p->dsc + 1;
     if (p->fp64) { fa.U64 = u; fa.B64 = b; }
     else { fa.Udf = p->Udf; fa.Bdf = p->Bdf; }
     LK(launch_time_fwd(fa, p->fp64, p->stream));
     CHK(sync_scalars(p, 2));
-    const double nb = std::sqrt(p->hsc[0]);
+    const double nb = std::sqrt(p->hsc[0]) / (p->fp64 ? 1.0 : p->s_scale);
     if (nb == 0.0) {
       CU(cudaMemsetAsync(u, 0, ns * sizeof(double), p->stream));
       CU(cudaStreamSynchronize(p->stream));
@@ -273,12 +276,21 @@ pd_status solve_stationary(pd_plan* p, const double* b, double* u, double tol, i
       st = set_err(p, PD_ERR_NOT_CONVERGED, "stationary iteration reached maxit");
       break;
     }
+    if (norm_only) {  // predicted convergence missed: redo this residual with the transform
+      norm_only = false;
+      continue;
+    }
     CHK(step_b(p));
     InvArgs ia = inv_base_impl(p);
     if (p->fp64) { ia.mode = INV_UPDATE64; ia.out64 = u; }
     else { ia.mode = INV_UPDATE_DF; ia.Udf = p->Udf; ia.igam = p->igam_s; }
     LK(launch_time_inv(ia, p->fp64, p->stream));
     ++it;
+    if (prev_rel > 0.0) {
+      const double rho = rel / prev_rel;
+      norm_only = rho < 1.0 && rel * rho <= 0.25 * tol;
+    }
+    prev_rel = rel;
   }
   if (!p->fp64 && p->hsc[0] != 0.0) LK(launch_from_df(p->Udf, u, ns, p->stream));
   CU(cudaStreamSynchronize(p->stream));

@@ -88,7 +88,8 @@ struct InvArgs {
   int* flag;                      // bit 0 set on a non-finite value (may be null)
 };
 
-enum { FWD_STANDALONE = 0, FWD_RESIDUAL = 1 };
+// FWD_RESIDUAL_NORM: the residual and its norm only (no transform, no spectrum)
+enum { FWD_STANDALONE = 0, FWD_RESIDUAL = 1, FWD_RESIDUAL_NORM = 2 };
 enum { INV_UPDATE_DF = 0, INV_OUT64 = 1, INV_UPDATE64 = 2 };
 
 // Arguments of the batched shifted tridiagonal solve (K2, step (b)).
@@ -149,6 +150,9 @@ cudaError_t launch_build_rhs(const Stencil& st, const TimeBand& tb, int scheme, 
                              cudaStream_t s);
 cudaError_t launch_to_df(const double* x, double scale, float2* y, size_t n, cudaStream_t s);
 cudaError_t launch_from_df(const float2* x, double* y, size_t n, cudaStream_t s);
+// U = split(u), B = split(scale b), *norm2 += ||scale b||^2 (FP32 partial sums)
+cudaError_t launch_entry_df(const double* u, const double* b, double scale, float2* U, float2* B,
+                            size_t n, double* norm2, cudaStream_t s);
 cudaError_t launch_norm2(const double* x, size_t n, double* out, cudaStream_t s);
 cudaError_t launch_flip_time(const double* x, double* y, int N, int S, cudaStream_t s);
 cudaError_t launch_dots(const double* V, int nv, size_t n, const double* w, double* h,

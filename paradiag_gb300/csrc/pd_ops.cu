@@ -93,6 +93,33 @@ __global__ void k_to_df(const double* __restrict__ x, dfc scale, float2* __restr
   }
 }
 
+// Entry of the mixed stationary solve in one pass: U = split(u), B = split(s b)
+// and ||s b||^2 accumulated from the FP32 high parts (FP64 arithmetic is slow
+// on this GPU; a few significant digits suffice for the relative residual).
+__global__ void k_entry_df(const double* __restrict__ u, const double* __restrict__ b, dfc scale,
+                           float2* __restrict__ U, float2* __restrict__ B, size_t n,
+                           double* norm2) {
+  __shared__ double red[TB / 32];
+  float part = 0.f;
+  for (size_t i = blockIdx.x * (size_t)TB + threadIdx.x; i < n; i += (size_t)gridDim.x * TB) {
+    const double ui = u[i], bi = b[i];
+    const df uv = df_from_double(ui);
+    const df bv = df_mul(df_from_double(bi), df_make(scale.hi, scale.lo));
+    U[i] = make_float2(uv.hi, uv.lo);
+    B[i] = make_float2(bv.hi, bv.lo);
+    part = fmaf(bv.hi, bv.hi, part);
+  }
+  double pd = (double)part;
+  for (int o = 16; o > 0; o >>= 1) pd += __shfl_down_sync(0xffffffffu, pd, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = pd;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double s = 0;
+    for (int w = 0; w < TB / 32; ++w) s += red[w];
+    atomicAdd(norm2, s);
+  }
+}
+
 __global__ void k_from_df(const float2* __restrict__ x, double* __restrict__ y, size_t n) {
   for (size_t i = blockIdx.x * (size_t)TB + threadIdx.x; i < n; i += (size_t)gridDim.x * TB) {
     const float2 v = x[i];
@@ -198,6 +225,12 @@ cudaError_t launch_build_rhs(const Stencil& st, const TimeBand& tb, int scheme, 
 
 cudaError_t launch_to_df(const double* x, double scale, float2* y, size_t n, cudaStream_t s) {
   k_to_df<<<grid_for(n), TB, 0, s>>>(x, dfc_from(scale), y, n);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_entry_df(const double* u, const double* b, double scale, float2* U, float2* B,
+                            size_t n, double* norm2, cudaStream_t s) {
+  k_entry_df<<<grid_for(n), TB, 0, s>>>(u, b, dfc_from(scale), U, B, n, norm2);
   return cudaGetLastError();
 }
 

@@ -608,6 +608,7 @@ PD_D void time_fwd_body(const FwdArgs& a, int tile) {
     const double bs = block_sum<double>(nrm, red);
     if (threadIdx.x == 0) atomicAdd(a.norm2, bs);
   }
+  if (a.mode == FWD_RESIDUAL_NORM) return;  // uniform across the block
   __syncthreads();
 
   const int lgTXc = lgTX - 1;
