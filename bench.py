@@ -410,7 +410,8 @@ def main():
                           "alpha": pb.alpha, "nu": sp.nu, "velocity": [sp.ax, sp.ay],
                           "bc": "x periodic, y Dirichlet", "unknowns": NS,
                           "residual_tol": TOL, "iterations": iters_all[-1],
-                          "l2": "working set ~400 MB > 129 MB L2, no flush",
+                          "l2": "working set ~0.8 GB > 129 MB L2, no flush",
+                          "cuda_graph": plan.uses_graph(),
                           "parallelism": f"{ws} independent replica(s)"},
                "error_vs_oracle": err,
                "fp64_path": {"value": ws * NS / (ms64 / 1e3), "ms_per_step": ms64,

@@ -154,6 +154,13 @@ PD_API pd_status pd_profile_iteration(pd_plan* plan, const double* b, const doub
 /* Number of kernels this plan (and its adjoint plan) has launched so far. */
 PD_API pd_status pd_plan_launches(const pd_plan* plan, unsigned long long* count);
 
+/* *uses = 1 if this plan's stationary solves run as one CUDA graph (mixed
+ * precision: the whole iteration, convergence test included, is a graph
+ * with a device-side WHILE loop; the first stationary solve builds it), else
+ * 0 (FP64 plans, plans not yet solved, or a graph that could not be built:
+ * the solver then loops on the host).  No paper counterpart; introspection. */
+PD_API pd_status pd_plan_uses_graph(const pd_plan* plan, int* uses);
+
 /* ---- batched solves: many independent problems of uneven size ----------
  * One problem of a batch (1D, Dirichlet, any scheme; all members of one batch
  * must share the time band: theta-method or leap-frog). */

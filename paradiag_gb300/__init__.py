@@ -64,6 +64,7 @@ _SIGS = {
     "pd_profile_iteration": (ctypes.c_int, [_P, _P, _P, ctypes.c_int,
                                             ctypes.POINTER(ctypes.c_float)]),
     "pd_plan_launches": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_ulonglong)]),
+    "pd_plan_uses_graph": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int)]),
     "pd_apply_precond_noalloc": (ctypes.c_int, [ctypes.POINTER(pd_space), ctypes.c_int,
                                                 ctypes.c_double, ctypes.c_double, ctypes.c_int,
                                                 ctypes.c_double, _P, _P, _P,
@@ -141,6 +142,12 @@ def pd_profile_iteration(plan, b, u, reps):
 def pd_plan_launches(plan):
     v = ctypes.c_ulonglong(0)
     st = load().pd_plan_launches(plan, ctypes.byref(v))
+    return st, v.value
+
+
+def pd_plan_uses_graph(plan):
+    v = ctypes.c_int(0)
+    st = load().pd_plan_uses_graph(plan, ctypes.byref(v))
     return st, v.value
 
 
@@ -302,6 +309,11 @@ class Plan:
         st, v = pd_plan_launches(self._h)
         self._check(st, "pd_plan_launches")
         return v
+
+    def uses_graph(self):
+        st, v = pd_plan_uses_graph(self._h)
+        self._check(st, "pd_plan_uses_graph")
+        return bool(v)
 
     def profile_iteration(self, b, u, reps=5):
         """Average ms per launch of [K1 residual+FFT, x-fwd, tridiagonal, x-inv, K3]."""

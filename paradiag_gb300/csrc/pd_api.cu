@@ -24,6 +24,32 @@ using cd = std::complex<double>;
 
 #include "pd_plan.h"
 
+// solver graph state (see solve_stationary_graph)
+struct LoopState {
+  double tol, s_scale, prev_rel, rel;
+  int maxit, it, status, norm_only, n_body, n_update;
+  int kmode;  // mode of the next forward kernel (read by it from device memory)
+};
+struct SolveGraph {
+  cudaGraph_t g = nullptr;
+  cudaGraphExec_t ge = nullptr;
+  cudaStream_t cs = nullptr;
+  LoopState* dst = nullptr;   // device loop state
+  LoopState* hst = nullptr;   // pinned host copy
+  int update_kernels = 0;     // kernels in one update (IF body)
+};
+
+void destroy_graph(SolveGraph* G) {
+  if (!G) return;
+  if (G->ge) cudaGraphExecDestroy(G->ge);
+  if (G->g) cudaGraphDestroy(G->g);
+  if (G->cs) cudaStreamDestroy(G->cs);
+  if (G->dst) cudaFree(G->dst);
+  if (G->hst) cudaFreeHost(G->hst);
+  delete G;
+}
+
+
 namespace {
 
 constexpr int NSC = 96;  // device / host scalar slots
@@ -106,6 +132,7 @@ void free_plan(pd_plan* p) {
   for (void* q : ptrs)
     if (q) cudaFree(q);
   if (p->hsc) cudaFreeHost(p->hsc);
+  if (p->graph) destroy_graph(p->graph);
   if (p->adj) free_plan(p->adj);
   delete p;
 }
@@ -233,8 +260,220 @@ pd_status flag_status(pd_plan* p) {
   return set_err(p, PD_ERR_NONFINITE, "non-finite value in the solver");
 }
 
+// ---------------------------------------------------------------------------
+// The mixed stationary iteration (eq. 5.1) as one CUDA graph: a WHILE node
+// whose body is [forward kernel (residual, norm) -> check kernel -> IF node
+// [step (b), inverse kernel + update]].  The check kernel takes the decisions
+// of the host loop below (tolerance, maxit, device error flags, the norm-only
+// prediction) on the device, so a solve has no host round trip per iteration.
+// The entry and exit kernels touch the caller's arrays and stay outside.
+// ---------------------------------------------------------------------------
+enum { LS_RUNNING = 0, LS_CONVERGED, LS_MAXIT, LS_NONFINITE, LS_TIMEOUT, LS_ZERO_RHS };
+
+__global__ void k_loop_check(LoopState* st, double* dsc, const int* flag,
+                             cudaGraphConditionalHandle hw, cudaGraphConditionalHandle hif) {
+  if (threadIdx.x != 0) return;
+  LoopState s = *st;
+  ++s.n_body;
+  bool stop = true, update = false;
+  const double nb = sqrt(dsc[0]) / s.s_scale;
+  if (nb == 0.0) {
+    s.status = LS_ZERO_RHS;
+    s.rel = 0.0;
+  } else {
+    const double rel = sqrt(dsc[1]) / nb;
+    s.rel = rel;
+    const int f = *flag;
+    if (f != 0) {
+      s.status = (f & 2) ? LS_TIMEOUT : LS_NONFINITE;
+    } else if (!isfinite(rel)) {
+      s.status = LS_NONFINITE;
+    } else if (rel <= s.tol) {
+      s.status = LS_CONVERGED;
+    } else if (s.it >= s.maxit) {
+      s.status = LS_MAXIT;
+    } else if (s.norm_only) {  // predicted convergence missed: redo with the transform
+      s.norm_only = 0;
+      stop = false;
+    } else {
+      update = true;
+      stop = false;
+      ++s.it;
+      ++s.n_update;
+      if (s.prev_rel > 0.0) {
+        const double rho = rel / s.prev_rel;
+        s.norm_only = (rho < 1.0 && rel * rho <= 0.25 * s.tol) ? 1 : 0;
+      }
+      s.prev_rel = rel;
+    }
+  }
+  dsc[1] = 0.0;  // accumulator of the next forward kernel
+  s.kmode = s.norm_only ? FWD_RESIDUAL_NORM : FWD_RESIDUAL;
+  *st = s;
+  cudaGraphSetConditional(hif, update ? 1u : 0u);
+  cudaGraphSetConditional(hw, stop ? 0u : 1u);
+}
+
+// the leaf node of a graph built by one stream capture (a chain)
+cudaGraphNode_t graph_leaf(cudaGraph_t g) {
+  size_t n = 0;
+  if (cudaGraphGetNodes(g, nullptr, &n) != cudaSuccess || n == 0) return nullptr;
+  std::vector<cudaGraphNode_t> nodes(n);
+  if (cudaGraphGetNodes(g, nodes.data(), &n) != cudaSuccess) return nullptr;
+  for (cudaGraphNode_t v : nodes) {
+    size_t d = 0;
+    if (cudaGraphNodeGetDependentNodes(v, nullptr, nullptr, &d) == cudaSuccess && d == 0) return v;
+  }
+  return nullptr;
+}
+
+pd_status build_graph_impl(pd_plan* p, SolveGraph* G) {
+  CU(cudaStreamCreateWithFlags(&G->cs, cudaStreamNonBlocking));
+  CU(cudaMalloc(&G->dst, sizeof(LoopState)));
+  CU(cudaMallocHost(&G->hst, sizeof(LoopState)));
+  CU(cudaGraphCreate(&G->g, 0));
+  cudaGraphConditionalHandle hw, hif;
+  CU(cudaGraphConditionalHandleCreate(&hw, G->g, 1u, cudaGraphCondAssignDefault));
+  alignas(cudaGraphNodeParams) unsigned char wbuf[sizeof(cudaGraphNodeParams)];
+  memset(wbuf, 0, sizeof(wbuf));
+  cudaGraphNodeParams& wp = *reinterpret_cast<cudaGraphNodeParams*>(wbuf);
+  wp.type = cudaGraphNodeTypeConditional;
+  wp.conditional.handle = hw;
+  wp.conditional.type = cudaGraphCondTypeWhile;
+  wp.conditional.size = 1;
+  cudaGraphNode_t wnode;
+  CU(cudaGraphAddNode(&wnode, G->g, nullptr, nullptr, 0, &wp));
+  cudaGraph_t body = wp.conditional.phGraph_out[0];
+  CU(cudaGraphConditionalHandleCreate(&hif, body, 0u, cudaGraphCondAssignDefault));
+
+  // body: forward kernel (mode from the device word) + check
+  const cudaStream_t saved = p->stream;
+  const unsigned long long launches = p->launches;
+  p->stream = G->cs;
+  pd_status st = PD_OK;
+  cudaError_t e = cudaStreamBeginCaptureToGraph(G->cs, body, nullptr, nullptr, 0,
+                                                cudaStreamCaptureModeRelaxed);
+  if (e == cudaSuccess) {
+    FwdArgs fa = fwd_base_impl(p);
+    fa.mode = FWD_RESIDUAL;
+    fa.mode_dev = &G->dst->kmode;
+    fa.norm2 = p->dsc + 1;
+    fa.Udf = p->Udf;
+    fa.Bdf = p->Bdf;
+    e = launch_time_fwd(fa, false, G->cs);
+    if (e == cudaSuccess) {
+      k_loop_check<<<1, 32, 0, G->cs>>>(G->dst, p->dsc, p->dflag, hw, hif);
+      e = cudaGetLastError();
+    }
+    cudaGraph_t out = nullptr;
+    const cudaError_t e2 = cudaStreamEndCapture(G->cs, &out);
+    if (e == cudaSuccess) e = e2;
+  }
+  cudaGraphNode_t leaf = e == cudaSuccess ? graph_leaf(body) : nullptr;
+  if (e == cudaSuccess && leaf == nullptr) e = cudaErrorUnknown;
+  cudaGraph_t ubody = nullptr;
+  if (e == cudaSuccess) {
+    alignas(cudaGraphNodeParams) unsigned char ibuf[sizeof(cudaGraphNodeParams)];
+    memset(ibuf, 0, sizeof(ibuf));
+    cudaGraphNodeParams& ip = *reinterpret_cast<cudaGraphNodeParams*>(ibuf);
+    ip.type = cudaGraphNodeTypeConditional;
+    ip.conditional.handle = hif;
+    ip.conditional.type = cudaGraphCondTypeIf;
+    ip.conditional.size = 1;
+    cudaGraphNode_t inode;
+    e = cudaGraphAddNode(&inode, body, &leaf, nullptr, 1, &ip);
+    if (e == cudaSuccess) ubody = ip.conditional.phGraph_out[0];
+  }
+  // IF body: step (b) and the inverse kernel with the update
+  if (e == cudaSuccess) e = cudaStreamBeginCaptureToGraph(G->cs, ubody, nullptr, nullptr, 0,
+                                                          cudaStreamCaptureModeRelaxed);
+  if (e == cudaSuccess) {
+    const unsigned long long l0 = p->launches;
+    st = step_b(p);
+    if (st == PD_OK) {
+      InvArgs ia = inv_base_impl(p);
+      ia.mode = INV_UPDATE_DF;
+      ia.Udf = p->Udf;
+      ia.igam = p->igam_s;
+      const cudaError_t e3 = launch_time_inv(ia, false, G->cs);
+      ++p->launches;
+      if (e3 != cudaSuccess) st = fail_cuda(p, e3, "inverse kernel capture");
+    }
+    G->update_kernels = (int)(p->launches - l0);
+    cudaGraph_t out = nullptr;
+    e = cudaStreamEndCapture(G->cs, &out);
+  }
+  p->stream = saved;
+  p->launches = launches;
+  if (st != PD_OK) return st;
+  if (e != cudaSuccess) return fail_cuda(p, e, "solver graph capture");
+  CU(cudaGraphInstantiate(&G->ge, G->g, 0));
+  return PD_OK;
+}
+
+// the graph of plan p, built on first use; null if it cannot be built (the
+// stationary solve then runs its host loop)
+SolveGraph* plan_graph(pd_plan* p) {
+  if (p->graph_state == 1) return p->graph;
+  if (p->graph_state < 0) return nullptr;
+  SolveGraph* G = new (std::nothrow) SolveGraph();
+  if (!G) {
+    p->graph_state = -1;
+    return nullptr;
+  }
+  if (build_graph_impl(p, G) != PD_OK) {
+    destroy_graph(G);
+    cudaGetLastError();
+    p->graph_state = -1;
+    return nullptr;
+  }
+  p->graph = G;
+  p->graph_state = 1;
+  return G;
+}
+
+pd_status solve_stationary_graph(pd_plan* p, SolveGraph* G, const double* b, double* u,
+                                 double tol, int maxit, int* iters, double* relres) {
+  const size_t ns = NS(p);
+  CU(cudaMemsetAsync(p->dsc, 0, 2 * sizeof(double), p->stream));
+  CU(cudaMemsetAsync(p->dflag, 0, sizeof(int), p->stream));
+  LK(launch_entry_df(u, b, p->s_scale, p->Udf, p->Bdf, ns, p->dsc, p->stream));
+  LoopState* h = G->hst;
+  memset(h, 0, sizeof(LoopState));
+  h->tol = tol;
+  h->s_scale = p->s_scale;
+  h->prev_rel = -1.0;
+  h->maxit = maxit;
+  h->kmode = FWD_RESIDUAL;
+  CU(cudaMemcpyAsync(G->dst, h, sizeof(LoopState), cudaMemcpyHostToDevice, p->stream));
+  CU(cudaGraphLaunch(G->ge, p->stream));
+  CU(cudaMemcpyAsync(h, G->dst, sizeof(LoopState), cudaMemcpyDeviceToHost, p->stream));
+  CU(cudaStreamSynchronize(p->stream));
+  p->launches += (unsigned long long)h->n_body * 2 + (unsigned long long)h->n_update * G->update_kernels;
+  if (h->status == LS_ZERO_RHS) {
+    CU(cudaMemsetAsync(u, 0, ns * sizeof(double), p->stream));
+  } else {
+    LK(launch_from_df(p->Udf, u, ns, p->stream));
+  }
+  CU(cudaStreamSynchronize(p->stream));
+  if (iters) *iters = h->it;
+  if (relres) *relres = h->rel;
+  switch (h->status) {
+    case LS_CONVERGED:
+    case LS_ZERO_RHS: return PD_OK;
+    case LS_MAXIT: return set_err(p, PD_ERR_NOT_CONVERGED, "stationary iteration reached maxit");
+    case LS_TIMEOUT: return set_err(p, PD_ERR_CUDA, "tensor-core x-transform pipeline timed out");
+    case LS_NONFINITE: return set_err(p, PD_ERR_NONFINITE, "non-finite value in the solver");
+    default: return set_err(p, PD_ERR_CUDA, "solver graph ended without a decision");
+  }
+}
+
 pd_status solve_stationary(pd_plan* p, const double* b, double* u, double tol, int maxit,
                            int* iters, double* relres) {
+  if (!p->fp64) {
+    SolveGraph* G = plan_graph(p);
+    if (G) return solve_stationary_graph(p, G, b, u, tol, maxit, iters, relres);
+  }
   const size_t ns = NS(p);
   CU(cudaMemsetAsync(p->dsc, 0, 2 * sizeof(double), p->stream));
   CU(cudaMemsetAsync(p->dflag, 0, sizeof(int), p->stream));
@@ -465,6 +704,12 @@ extern "C" {
 pd_status pd_plan_launches(const pd_plan* plan, unsigned long long* count) {
   if (!plan || !count) return PD_ERR_ARG;
   *count = plan->launches + (plan->adj ? plan->adj->launches : 0);
+  return PD_OK;
+}
+
+pd_status pd_plan_uses_graph(const pd_plan* plan, int* uses) {
+  if (!plan || !uses) return PD_ERR_ARG;
+  *uses = plan->graph_state == 1 ? 1 : 0;
   return PD_OK;
 }
 

@@ -72,6 +72,7 @@ struct FwdArgs {
   // raised into *amax, and *amax_reset (the other transform's word) is zeroed
   unsigned* amax = nullptr;
   unsigned* amax_reset = nullptr;
+  const int* mode_dev = nullptr;  // if set, the mode is read from device memory
 };
 
 // Arguments of the inverse time kernel (K3).

@@ -52,6 +52,10 @@ struct pd_plan {
   double* dh = nullptr;
   int gm_cap = 0;
   pd_plan* adj = nullptr;
+  // the mixed stationary iteration as one CUDA graph (built on first use;
+  // graph_state 0 untried, 1 ready, -1 unavailable: the host loop runs)
+  struct SolveGraph* graph = nullptr;
+  int graph_state = 0;
   size_t bytes = 0;
   unsigned long long launches = 0;
   char msg[256] = {0};

@@ -464,7 +464,9 @@ PD_D void time_fwd_body(const FwdArgs& a, int tile) {
   const R* gam = reinterpret_cast<const R*>(a.gam);
   double nrm = 0.0;
 
-  if (a.mode == FWD_STANDALONE) {
+  // the mode may come from device memory (the solver's graph decides it)
+  const int mode = a.mode_dev != nullptr ? *a.mode_dev : a.mode;
+  if (mode == FWD_STANDALONE) {
     // every element of the tile: consecutive threads take consecutive columns,
     // eight loads in flight per thread
     constexpr int U = 8;
@@ -608,7 +610,7 @@ PD_D void time_fwd_body(const FwdArgs& a, int tile) {
     const double bs = block_sum<double>(nrm, red);
     if (threadIdx.x == 0) atomicAdd(a.norm2, bs);
   }
-  if (a.mode == FWD_RESIDUAL_NORM) return;  // uniform across the block
+  if (mode == FWD_RESIDUAL_NORM) return;  // uniform across the block
   __syncthreads();
 
   const int lgTXc = lgTX - 1;

@@ -55,6 +55,13 @@ def test_ade2d_small_stationary(pd, prec, scheme):
     plan = make_plan(pb, pd.PD_FP64 if prec == "fp64" else pd.PD_MIXED)
     u, it, rel = plan.solve(dev(b), tol=1e-12, maxit=30)
     assert rel2(host(u), uref) <= 1e-10, (rel2(host(u), uref), it, rel)
+    # the mixed stationary iteration runs as one CUDA graph (device-side loop)
+    assert plan.uses_graph() == (prec == "mixed")
+    if prec == "mixed":
+        # a second solve reuses the graph and reproduces the first bit for bit
+        u2, it2, rel2_ = plan.solve(dev(b), tol=1e-12, maxit=30)
+        assert it2 == it and rel2_ == rel
+        assert float((u2 - u).abs().max()) == 0.0
     plan.close()
 
 
