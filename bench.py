@@ -45,6 +45,9 @@ def parse():
     ap.add_argument("--no-batch", action="store_true", help="skip the batched-workload leg")
     ap.add_argument("--profile-iteration", action="store_true",
                     help="only time the kernels of one iteration (the driver of ncu captures)")
+    ap.add_argument("--sweep", action="store_true",
+                    help="roofline sweep of the iteration kernels over 1D sizes "
+                         "nx in {255, 1023, 4095} x Nt in {256, 1024, 4096}")
     return ap.parse_args()
 
 
@@ -224,6 +227,37 @@ def batched_leg(pd, torch, dev, args):
     return out
 
 
+def run_sweep(pd, torch, dev):
+    """Per-kernel time and algorithmic HBM throughput of one mixed iteration on
+    1D advection-diffusion problems (nu = 1e-2, a = 1, BE, alpha = 1e-2) of
+    growing size, so that the working set passes the 129 MB L2."""
+    import workloads as W
+    hbm, _, src = peaks()
+    rows = []
+    for nx in (255, 1023, 4095):
+        for nt in (256, 1024, 4096):
+            w = W.ade1d(nx=nx, nt=nt, nu=1e-2, a=1.0, scheme=W.BE, alpha=1e-2)
+            pb = w.problem
+            sp = pb.space
+            plan = pd.Plan(dict(dim=1, nx=sp.nx, nu=sp.nu, ax=sp.ax), pb.nt, pb.dt, pb.alpha,
+                           pd.PD_BE, 1.0, pd.PD_MIXED, torch.cuda.current_stream())
+            b = plan.build_rhs(torch.from_numpy(w.u0).to(dev), None,
+                               torch.from_numpy(w.f).to(dev))
+            u = torch.zeros_like(b)
+            plan.profile_iteration(b, u, reps=2)
+            kms = plan.profile_iteration(b, u, reps=5)
+            bpu = bytes_per_unknown(nt, False)
+            ns = nx * nt
+            ker = {}
+            for name, t in zip(KERNELS, kms):
+                if t > 0:
+                    gbs = bpu[name] * ns / (t / 1e3) / 1e9
+                    ker[name] = {"ms": t, "GB/s": gbs, "frac": gbs / hbm}
+            rows.append({"nx": nx, "nt": nt, "unknowns": ns, "kernels": ker})
+            plan.close()
+    return {"sweep": rows, "peak_GBps": hbm, "peak_source": src}
+
+
 def run_reference(args):
     ws, rank, _ = dist_setup()
     if rank != 0:
@@ -285,6 +319,11 @@ def main():
     b = plan.build_rhs(u0)
     u = torch.zeros_like(b)
     torch.cuda.synchronize()
+    if args.sweep:
+        out = run_sweep(pd, torch, dev)
+        if rank == 0:
+            print(json.dumps(out), flush=True)
+        return
     if args.profile_iteration:
         # the residual-mode iteration of the solver, kernel by kernel (ncu driver)
         for _ in range(2):
