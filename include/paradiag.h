@@ -199,6 +199,11 @@ PD_API pd_status pd_batch_solve(pd_batch* batch, const double* b, double* u, dou
 /* relres[0..nprob): relative residual of every problem at the last check. */
 PD_API pd_status pd_batch_relres(const pd_batch* batch, double* relres);
 PD_API pd_status pd_batch_launches(const pd_batch* batch, unsigned long long* count);
+
+/* *uses = 1 if this batch's solves run as one CUDA graph (mixed precision:
+ * the sweep loop with its convergence test is a graph with a device-side
+ * WHILE loop; the first solve builds it), else 0.  No paper counterpart. */
+PD_API pd_status pd_batch_uses_graph(const pd_batch* batch, int* uses);
 PD_API const char* pd_batch_last_error(const pd_batch* batch);
 
 /* Size of the device array used by pd_apply_precond_noalloc (8 MiB). */

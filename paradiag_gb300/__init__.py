@@ -76,6 +76,7 @@ _SIGS = {
     "pd_batch_build_rhs": (ctypes.c_int, [_P, _P, _P, _P]),
     "pd_batch_solve": (ctypes.c_int, [_P, _P, _P, ctypes.c_double, ctypes.c_int, _I, _D]),
     "pd_batch_launches": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_ulonglong)]),
+    "pd_batch_uses_graph": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int)]),
     "pd_batch_relres": (ctypes.c_int, [_P, _D]),
     "pd_batch_last_error": (ctypes.c_char_p, [_P]),
     "pd_status_string": (ctypes.c_char_p, [ctypes.c_int]),
@@ -148,6 +149,12 @@ def pd_plan_launches(plan):
 def pd_plan_uses_graph(plan):
     v = ctypes.c_int(0)
     st = load().pd_plan_uses_graph(plan, ctypes.byref(v))
+    return st, v.value
+
+
+def pd_batch_uses_graph(batch):
+    v = ctypes.c_int(0)
+    st = load().pd_batch_uses_graph(batch, ctypes.byref(v))
     return st, v.value
 
 
@@ -420,6 +427,12 @@ class Batch:
 
     def launches(self):
         return pd_batch_launches(self._h)[1]
+
+    def uses_graph(self):
+        st, v = pd_batch_uses_graph(self._h)
+        if st != PD_OK:
+            raise PDError(st, "pd_batch_uses_graph")
+        return bool(v)
 
     def build_rhs(self, u0, f=None):
         import torch

@@ -56,7 +56,36 @@ struct pd_batch {
   unsigned long long launches = 0;
   std::vector<double> relres;   // per problem, from the last residual evaluation
   char msg[256] = {0};
+  // the mixed sweep as one CUDA graph (built on first use; graph_state 0
+  // untried, 1 ready, -1 unavailable: the host loop runs)
+  struct BatchGraph* graph = nullptr;
+  int graph_state = 0;
 };
+
+// Loop state of the batched sweep graph (device copy and pinned host copy).
+struct BLoop {
+  double tol, rmax, prev;
+  int maxit, it, status, norm_only, n_body, n_update, kmode;
+};
+struct BatchGraph {
+  cudaGraph_t g = nullptr;
+  cudaGraphExec_t ge = nullptr;
+  cudaStream_t cs = nullptr;
+  BLoop* dst = nullptr;
+  BLoop* hst = nullptr;
+  double* d_rel = nullptr;   // per-problem relative residual of the last check
+  int update_kernels = 0;
+};
+void destroy_batch_graph(BatchGraph* G) {
+  if (!G) return;
+  if (G->ge) cudaGraphExecDestroy(G->ge);
+  if (G->g) cudaGraphDestroy(G->g);
+  if (G->cs) cudaStreamDestroy(G->cs);
+  if (G->dst) cudaFree(G->dst);
+  if (G->d_rel) cudaFree(G->d_rel);
+  if (G->hst) cudaFreeHost(G->hst);
+  delete G;
+}
 
 namespace {
 
@@ -154,7 +183,168 @@ void free_batch(pd_batch* b) {
   for (int w = 0; w < TRI_NCLASS; ++w)
     if (b->d_work_tri[w]) cudaFree(b->d_work_tri[w]);
   if (b->h_norms) cudaFreeHost(b->h_norms);
+  if (b->graph) destroy_batch_graph(b->graph);
   delete b;
+}
+
+enum { BS_RUNNING = 0, BS_CONVERGED, BS_MAXIT, BS_NONFINITE };
+
+// Decisions of one batched sweep on the device (one block): per-problem
+// relative residuals, their maximum, the stopping test, the norm-only
+// prediction for the next forward pass, and the two graph conditions.
+__global__ void k_batch_check(BLoop* st, double* norms, int np, const int* flag, double* rel,
+                              cudaGraphConditionalHandle hw, cudaGraphConditionalHandle hif) {
+  __shared__ double smax[TB];
+  __shared__ int sbad[TB];
+  double mx = 0.0;
+  int bad = 0;
+  for (int i = threadIdx.x; i < np; i += TB) {
+    const double nb = sqrt(norms[i]), nr = sqrt(norms[np + i]);
+    const double r = nb > 0.0 ? nr / nb : (nr > 0.0 ? INFINITY : 0.0);
+    if (!isfinite(r)) bad = 1;
+    else mx = fmax(mx, r);
+    rel[i] = r;
+    norms[np + i] = 0.0;  // accumulator of the next forward pass
+  }
+  smax[threadIdx.x] = mx;
+  sbad[threadIdx.x] = bad;
+  __syncthreads();
+  for (int o = TB / 2; o > 0; o >>= 1) {
+    if (threadIdx.x < o) {
+      smax[threadIdx.x] = fmax(smax[threadIdx.x], smax[threadIdx.x + o]);
+      sbad[threadIdx.x] |= sbad[threadIdx.x + o];
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x != 0) return;
+  BLoop s = *st;
+  ++s.n_body;
+  const double rmax = smax[0];
+  s.rmax = rmax;
+  bool stop = true, update = false;
+  if (*flag != 0 || sbad[0]) {
+    s.status = BS_NONFINITE;
+  } else if (rmax <= s.tol) {
+    s.status = BS_CONVERGED;
+  } else if (s.it >= s.maxit) {
+    s.status = BS_MAXIT;
+  } else if (s.norm_only) {  // predicted convergence missed: redo with the transform
+    s.norm_only = 0;
+    stop = false;
+  } else {
+    update = true;
+    stop = false;
+    ++s.it;
+    ++s.n_update;
+    if (s.prev > 0.0) {
+      const double rho = rmax / s.prev;
+      s.norm_only = (rho < 1.0 && rmax * rho <= 0.25 * s.tol) ? 1 : 0;
+    }
+    s.prev = rmax;
+  }
+  s.kmode = s.norm_only ? FWD_RESIDUAL_NORM : FWD_RESIDUAL;
+  *st = s;
+  cudaGraphSetConditional(hif, update ? 1u : 0u);
+  cudaGraphSetConditional(hw, stop ? 0u : 1u);
+}
+
+// the leaf node of a graph built by one stream capture (a chain)
+cudaGraphNode_t batch_graph_leaf(cudaGraph_t g) {
+  size_t n = 0;
+  if (cudaGraphGetNodes(g, nullptr, &n) != cudaSuccess || n == 0) return nullptr;
+  std::vector<cudaGraphNode_t> nodes(n);
+  if (cudaGraphGetNodes(g, nodes.data(), &n) != cudaSuccess) return nullptr;
+  for (cudaGraphNode_t v : nodes) {
+    size_t d = 0;
+    if (cudaGraphNodeGetDependentNodes(v, nullptr, nullptr, &d) == cudaSuccess && d == 0) return v;
+  }
+  return nullptr;
+}
+
+// WHILE [batched forward pass -> check -> IF [tridiagonal classes, batched
+// inverse pass with the update]]; the descriptors (uploaded by every solve)
+// point at the batch's own buffers, so the graph does not depend on the call.
+pd_status build_batch_graph(pd_batch* b, BatchGraph* G) {
+  BCU(cudaStreamCreateWithFlags(&G->cs, cudaStreamNonBlocking));
+  BCU(cudaMalloc(&G->dst, sizeof(BLoop)));
+  BCU(cudaMalloc(&G->d_rel, b->np * sizeof(double)));
+  BCU(cudaMallocHost(&G->hst, sizeof(BLoop)));
+  BCU(cudaGraphCreate(&G->g, 0));
+  cudaGraphConditionalHandle hw, hif;
+  BCU(cudaGraphConditionalHandleCreate(&hw, G->g, 1u, cudaGraphCondAssignDefault));
+  alignas(cudaGraphNodeParams) unsigned char wbuf[sizeof(cudaGraphNodeParams)];
+  memset(wbuf, 0, sizeof(wbuf));
+  cudaGraphNodeParams& wp = *reinterpret_cast<cudaGraphNodeParams*>(wbuf);
+  wp.type = cudaGraphNodeTypeConditional;
+  wp.conditional.handle = hw;
+  wp.conditional.type = cudaGraphCondTypeWhile;
+  wp.conditional.size = 1;
+  cudaGraphNode_t wnode;
+  BCU(cudaGraphAddNode(&wnode, G->g, nullptr, nullptr, 0, &wp));
+  cudaGraph_t body = wp.conditional.phGraph_out[0];
+  BCU(cudaGraphConditionalHandleCreate(&hif, body, 0u, cudaGraphCondAssignDefault));
+  const int np = b->np;
+  BCU(cudaStreamBeginCaptureToGraph(G->cs, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
+  cudaError_t e = launch_time_fwd_batch(b->d_fwd, b->d_work_time, b->nblk_time, b->band,
+                                        b->smem_time, b->ept, false, G->cs);
+  if (e == cudaSuccess) {
+    k_batch_check<<<1, TB, 0, G->cs>>>(G->dst, b->d_norms, np, b->d_flag, G->d_rel, hw, hif);
+    e = cudaGetLastError();
+  }
+  cudaGraph_t out = nullptr;
+  const cudaError_t e2 = cudaStreamEndCapture(G->cs, &out);
+  if (e == cudaSuccess) e = e2;
+  if (e != cudaSuccess) return bcuda(b, e, "batch graph capture");
+  cudaGraphNode_t leaf = batch_graph_leaf(body);
+  if (!leaf) return berr(b, PD_ERR_CUDA, "batch graph capture");
+  alignas(cudaGraphNodeParams) unsigned char ibuf[sizeof(cudaGraphNodeParams)];
+  memset(ibuf, 0, sizeof(ibuf));
+  cudaGraphNodeParams& ip = *reinterpret_cast<cudaGraphNodeParams*>(ibuf);
+  ip.type = cudaGraphNodeTypeConditional;
+  ip.conditional.handle = hif;
+  ip.conditional.type = cudaGraphCondTypeIf;
+  ip.conditional.size = 1;
+  cudaGraphNode_t inode;
+  BCU(cudaGraphAddNode(&inode, body, &leaf, nullptr, 1, &ip));
+  cudaGraph_t ubody = ip.conditional.phGraph_out[0];
+  BCU(cudaStreamBeginCaptureToGraph(G->cs, ubody, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
+  int nk = 0;
+  e = cudaSuccess;
+  for (int w = 0; w < TRI_NCLASS && e == cudaSuccess; ++w)
+    if (b->ntiles_tri[w] > 0) {
+      e = launch_tridiag_batch(b->d_tri, b->d_work_tri[w], b->ntiles_tri[w], w, false, G->cs);
+      ++nk;
+    }
+  if (e == cudaSuccess) {
+    e = launch_time_inv_batch(b->d_inv, b->d_work_time, b->nblk_time, b->smem_inv, b->ept, false,
+                              G->cs);
+    ++nk;
+  }
+  const cudaError_t e3 = cudaStreamEndCapture(G->cs, &out);
+  if (e == cudaSuccess) e = e3;
+  if (e != cudaSuccess) return bcuda(b, e, "batch graph capture");
+  G->update_kernels = nk;
+  BCU(cudaGraphInstantiate(&G->ge, G->g, 0));
+  return PD_OK;
+}
+
+BatchGraph* batch_graph(pd_batch* b) {
+  if (b->graph_state == 1) return b->graph;
+  if (b->graph_state < 0) return nullptr;
+  BatchGraph* G = new (std::nothrow) BatchGraph();
+  if (!G) {
+    b->graph_state = -1;
+    return nullptr;
+  }
+  if (build_batch_graph(b, G) != PD_OK) {
+    destroy_batch_graph(G);
+    cudaGetLastError();
+    b->graph_state = -1;
+    return nullptr;
+  }
+  b->graph = G;
+  b->graph_state = 1;
+  return G;
 }
 
 }  // namespace
@@ -274,6 +464,12 @@ pd_status pd_batch_offsets(const pd_batch* b, unsigned long long* offsets) {
   return PD_OK;
 }
 
+pd_status pd_batch_uses_graph(const pd_batch* b, int* uses) {
+  if (!b || !uses) return PD_ERR_ARG;
+  *uses = b->graph_state == 1 ? 1 : 0;
+  return PD_OK;
+}
+
 pd_status pd_batch_launches(const pd_batch* b, unsigned long long* count) {
   if (!b || !count) return PD_ERR_ARG;
   unsigned long long c = b->launches;
@@ -344,6 +540,35 @@ pd_status pd_batch_solve(pd_batch* b, const double* bvec, double* u, double tol,
     k_batch_to_df<<<grid_for(b->total), TB, 0, st>>>(bvec, b->Bdf, b->d_off, b->d_bscale, np,
                                                      b->total);
     BLK(cudaGetLastError());
+  }
+  BatchGraph* G = fp64 ? nullptr : batch_graph(b);
+  if (G) {
+    // the whole sweep loop as one graph launch; the forward passes read
+    // their mode (with or without the transform) from the loop state
+    for (int i = 0; i < np; ++i) b->h_fwd[i].mode_dev = &G->dst->kmode;
+    BCU(cudaMemcpyAsync(b->d_fwd, b->h_fwd.data(), np * sizeof(FwdArgs), cudaMemcpyHostToDevice,
+                        st));
+    for (int i = 0; i < np; ++i) b->h_fwd[i].mode_dev = nullptr;
+    BLoop* h = G->hst;
+    memset(h, 0, sizeof(BLoop));
+    h->tol = tol;
+    h->prev = -1.0;
+    h->maxit = maxit;
+    h->kmode = FWD_RESIDUAL;
+    BCU(cudaMemcpyAsync(G->dst, h, sizeof(BLoop), cudaMemcpyHostToDevice, st));
+    BCU(cudaGraphLaunch(G->ge, st));
+    BCU(cudaMemcpyAsync(h, G->dst, sizeof(BLoop), cudaMemcpyDeviceToHost, st));
+    b->relres.assign(np, 0.0);
+    BCU(cudaMemcpyAsync(b->relres.data(), G->d_rel, np * sizeof(double), cudaMemcpyDeviceToHost,
+                        st));
+    BLK(launch_from_df(b->Udf, u, b->total, st));
+    BCU(cudaStreamSynchronize(st));
+    b->launches += (unsigned long long)h->n_body * 2 + (unsigned long long)h->n_update * G->update_kernels;
+    if (iters) *iters = h->it;
+    if (relres_max) *relres_max = h->rmax;
+    if (h->status == BS_CONVERGED) return PD_OK;
+    if (h->status == BS_MAXIT) return berr(b, PD_ERR_NOT_CONVERGED, "batched iteration reached maxit");
+    return berr(b, PD_ERR_NONFINITE, "non-finite value in the batched iteration");
   }
   int it = 0;
   double rmax = 0.0;

@@ -47,14 +47,16 @@ def test_batch_matches_sequential(prec):
     else:
         u, it, rel = batch.solve(b, tol=1e-12, maxit=30)
         assert rel <= 1e-12
-    # one launch per kernel type per sweep: time forward, one per tridiagonal
-    # lane class, time inverse.  A system of n rows is split over the smallest
+    # one launch per kernel type per sweep: time forward, the device-side
+    # convergence check of the graph (mixed path), one per tridiagonal lane
+    # class, time inverse.  A system of n rows is split over the smallest
     # power-of-two number of lanes that holds it in chunks of at most 32 rows
     # (mixed) or 16 rows (FP64).
     rows = 32 if prec == "mixed" else 16
     classes = {int(np.ceil(np.log2(max(1, -(-w.problem.space.nx // rows))))) for w in wls}
-    per_sweep = 1 + len(classes) + 1
-    assert batch.launches() - l0 <= per_sweep * it + 1 + len(classes) + 2
+    per_sweep = 1 + 1 + len(classes) + 1
+    assert batch.launches() - l0 <= per_sweep * it + len(classes) + 6
+    assert batch.uses_graph() == (prec == "mixed")
     uh = host(u)
     bh = host(b)
     off = batch.offsets
