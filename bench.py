@@ -451,6 +451,7 @@ def main():
                           "residual_tol": TOL, "iterations": iters_all[-1],
                           "l2": "working set ~0.8 GB > 129 MB L2, no flush",
                           "cuda_graph": plan.uses_graph(),
+                          "autotuned": dict(zip(("tile_columns", "tri_lanes"), plan.tuning())),
                           "parallelism": f"{ws} independent replica(s)"},
                "error_vs_oracle": err,
                "fp64_path": {"value": ws * NS / (ms64 / 1e3), "ms_per_step": ms64,

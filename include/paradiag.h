@@ -161,6 +161,14 @@ PD_API pd_status pd_plan_launches(const pd_plan* plan, unsigned long long* count
  * the solver then loops on the host).  No paper counterpart; introspection. */
 PD_API pd_status pd_plan_uses_graph(const pd_plan* plan, int* uses);
 
+/* The kernel shapes of this plan: *tile_columns = spatial columns per block of
+ * the time kernels, *tri_lanes = lanes per shifted tridiagonal system.  Mixed
+ * plans with at least 2^18 unknowns choose both at creation by timing two
+ * candidates each on the GPU (8 or 16 complex elements per thread; the
+ * default lane count or twice it); others use the default rules.  No paper
+ * counterpart; introspection. */
+PD_API pd_status pd_plan_tuning(const pd_plan* plan, int* tile_columns, int* tri_lanes);
+
 /* ---- batched solves: many independent problems of uneven size ----------
  * One problem of a batch (1D, Dirichlet, any scheme; all members of one batch
  * must share the time band: theta-method or leap-frog). */

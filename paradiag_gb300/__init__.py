@@ -65,6 +65,7 @@ _SIGS = {
                                             ctypes.POINTER(ctypes.c_float)]),
     "pd_plan_launches": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_ulonglong)]),
     "pd_plan_uses_graph": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int)]),
+    "pd_plan_tuning": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]),
     "pd_apply_precond_noalloc": (ctypes.c_int, [ctypes.POINTER(pd_space), ctypes.c_int,
                                                 ctypes.c_double, ctypes.c_double, ctypes.c_int,
                                                 ctypes.c_double, _P, _P, _P,
@@ -150,6 +151,13 @@ def pd_plan_uses_graph(plan):
     v = ctypes.c_int(0)
     st = load().pd_plan_uses_graph(plan, ctypes.byref(v))
     return st, v.value
+
+
+def pd_plan_tuning(plan):
+    tx = ctypes.c_int(0)
+    lanes = ctypes.c_int(0)
+    st = load().pd_plan_tuning(plan, ctypes.byref(tx), ctypes.byref(lanes))
+    return st, tx.value, lanes.value
 
 
 def pd_batch_uses_graph(batch):
@@ -316,6 +324,12 @@ class Plan:
         st, v = pd_plan_launches(self._h)
         self._check(st, "pd_plan_launches")
         return v
+
+    def tuning(self):
+        """(spatial columns per time-kernel block, lanes per tridiagonal system)"""
+        st, tx, lanes = pd_plan_tuning(self._h)
+        self._check(st, "pd_plan_tuning")
+        return tx, lanes
 
     def uses_graph(self):
         st, v = pd_plan_uses_graph(self._h)

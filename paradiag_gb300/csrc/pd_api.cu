@@ -15,6 +15,7 @@
 #include <complex>
 #include <cstdio>
 #include <cstring>
+#include <functional>
 #include <new>
 #include <vector>
 
@@ -210,6 +211,7 @@ TriArgs tri_args_impl(const pd_plan* p, void* data) {
   ta.lam = p->lam; ta.mu = p->xform ? p->mu : nullptr; ta.data = data; ta.flag = p->dflag;
   ta.amax = p->xform_tc ? p->amax + 1 : nullptr;
   ta.amax_reset = p->xform_tc ? p->amax : nullptr;
+  ta.cls = p->tri_cls;
   return ta;
 }
 
@@ -258,6 +260,90 @@ pd_status flag_status(pd_plan* p) {
   const int f = flag_value(p);
   if (f & 2) return set_err(p, PD_ERR_CUDA, "tensor-core x-transform pipeline timed out");
   return set_err(p, PD_ERR_NONFINITE, "non-finite value in the solver");
+}
+
+// ---------------------------------------------------------------------------
+// Plan-time autotuner (mixed plans with a solver state of at least 2^18
+// unknowns): times, on the plan's own (zeroed) buffers with CUDA events, the
+// iteration's time kernels for two tile widths (8 or 16 complex elements per
+// thread) and the tridiagonal solve for two lane classes (the default and one
+// more PCR level), and keeps the faster of each.  Both candidates of either
+// choice are exact implementations of the same step, so results stay within
+// the tolerances of the tests whichever is kept.
+// ---------------------------------------------------------------------------
+pd_status time_ms(pd_plan* p, int reps, float* ms, const std::function<pd_status()>& body) {
+  cudaEvent_t e0, e1;
+  CU(cudaEventCreate(&e0));
+  CU(cudaEventCreate(&e1));
+  pd_status st = body();  // warm-up (and attribute setup)
+  if (st == PD_OK) {
+    cudaEventRecord(e0, p->stream);
+    for (int r = 0; r < reps && st == PD_OK; ++r) st = body();
+    cudaEventRecord(e1, p->stream);
+    cudaEventSynchronize(e1);
+    cudaEventElapsedTime(ms, e0, e1);
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  return st;
+}
+
+pd_status autotune_plan(pd_plan* p) {
+  if (p->fp64 || !p->Udf || NS(p) < (1u << 18)) return PD_OK;
+  const unsigned long long launches = p->launches;
+  CU(cudaMemsetAsync(p->Udf, 0, NS(p) * sizeof(float2), p->stream));
+  CU(cudaMemsetAsync(p->Bdf, 0, NS(p) * sizeof(float2), p->stream));
+  const int rows = p->xf.M ? p->xf.M : p->nt;
+  // time kernels: tile budgets of 4096 and 8192 reals
+  const int tx_a = std::max(2, std::min(32, 4096 / rows)), tx_b = std::max(2, std::min(32, 8192 / rows));
+  if (tx_a != tx_b) {
+    float best = 0.f;
+    int best_tx = p->TX;
+    for (int tx : {tx_b, tx_a}) {
+      p->TX = tx;
+      float ms = 0.f;
+      CHK(time_ms(p, 3, &ms, [&]() -> pd_status {
+        FwdArgs fa = fwd_base_impl(p);
+        fa.mode = FWD_RESIDUAL;
+        fa.Udf = p->Udf;
+        fa.Bdf = p->Bdf;
+        LK(launch_time_fwd(fa, false, p->stream));
+        InvArgs ia = inv_base_impl(p);
+        ia.mode = INV_UPDATE_DF;
+        ia.Udf = p->Udf;
+        ia.igam = p->igam_s;
+        LK(launch_time_inv(ia, false, p->stream));
+        return PD_OK;
+      }));
+      if (best == 0.f || ms < best) { best = ms; best_tx = tx; }
+    }
+    p->TX = best_tx;
+  }
+  // tridiagonal: the default lane class and one more PCR level (chunks of at
+  // least two rows)
+  const int c0 = tridiag_class(p->tri_n, false);
+  if (c0 >= 0 && c0 + 1 < TRI_NCLASS && (2 << c0) * 2 <= p->tri_n) {
+    void* data = p->xform ? p->spec2 : p->spec;
+    const size_t specb = (size_t)p->nh * p->sg.specS * sizeof(float2);
+    CU(cudaMemsetAsync(data, 0, specb, p->stream));
+    float best = 0.f;
+    int best_c = -1;
+    for (int c : {c0, c0 + 1}) {
+      p->tri_cls = c;
+      float ms = 0.f;
+      CHK(time_ms(p, 3, &ms, [&]() -> pd_status {
+        LK(launch_tridiag(tri_args_impl(p, data), false, p->stream));
+        return PD_OK;
+      }));
+      if (best == 0.f || ms < best) { best = ms; best_c = c; }
+    }
+    p->tri_cls = best_c == c0 ? -1 : best_c;
+  }
+  CU(cudaMemsetAsync(p->dflag, 0, sizeof(int), p->stream));
+  CU(cudaStreamSynchronize(p->stream));
+  p->launches = launches;
+  p->tuned = 1;
+  return PD_OK;
 }
 
 // ---------------------------------------------------------------------------
@@ -707,6 +793,15 @@ pd_status pd_plan_launches(const pd_plan* plan, unsigned long long* count) {
   return PD_OK;
 }
 
+pd_status pd_plan_tuning(const pd_plan* plan, int* tile_columns, int* tri_lanes) {
+  if (!plan || !tile_columns || !tri_lanes) return PD_ERR_ARG;
+  *tile_columns = plan->TX;
+  const int c0 = tridiag_class(plan->tri_n, plan->fp64);
+  const int c = plan->tri_cls > c0 ? plan->tri_cls : c0;
+  *tri_lanes = c >= 0 ? 1 << c : 0;
+  return PD_OK;
+}
+
 pd_status pd_plan_uses_graph(const pd_plan* plan, int* uses) {
   if (!plan || !uses) return PD_ERR_ARG;
   *uses = plan->graph_state == 1 ? 1 : 0;
@@ -1073,6 +1168,7 @@ pd_status plan_create_internal(const pd_space* sp, int nt, double dt, double alp
     cudaError_t e = cudaMallocHost((void**)&p->hsc, NSC * sizeof(double));
     if (e != cudaSuccess) s2 = fail_cuda(p, e, "cudaMallocHost");
   }
+  if (s2 == PD_OK) s2 = autotune_plan(p);
   if (s2 != PD_OK) {
     free_plan(p);
     return s2;

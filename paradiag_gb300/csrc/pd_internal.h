@@ -107,6 +107,9 @@ struct TriArgs {
   // as in FwdArgs: max |solution| raised into *amax, *amax_reset zeroed (FP32 only)
   unsigned* amax = nullptr;
   unsigned* amax_reset = nullptr;
+  // lane class (2^cls lanes per system) chosen by the plan's autotuner, or -1
+  // for the default tridiag_class(n); never below the default
+  int cls = -1;
 };
 
 // Arguments of the dense x-eigentransform (2D, step (a') / (c')): along x, for

@@ -26,6 +26,8 @@ struct pd_plan {
   float gf_inv = 1.f, gi_inv = 1.f;   // scales of the FP16 operator splits
   unsigned* amax = nullptr;           // max |input| of the forward / inverse transform
   int J = 1, tri_n = 0, tri_stride = 1;
+  int tri_cls = -1;                   // tridiagonal lane class (autotuned, -1: default)
+  int tuned = 0;                      // 1 once the plan-time autotuner has run
   double tri_cl = 0, tri_cd = 0, tri_cu = 0;
   // device tables
   void* lam = nullptr;

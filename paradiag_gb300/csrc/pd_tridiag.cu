@@ -449,8 +449,9 @@ int tridiag_batch_sb(int cls, bool fp64) {
 }
 
 cudaError_t launch_tridiag(const TriArgs& a, bool fp64, cudaStream_t st) {
-  const int cls = tridiag_class(a.n, fp64);
-  if (cls < 0) return cudaErrorInvalidValue;
+  const int c0 = tridiag_class(a.n, fp64);
+  if (c0 < 0) return cudaErrorInvalidValue;
+  const int cls = a.cls > c0 && a.cls < TRI_NCLASS ? a.cls : c0;
   const long long total = (long long)a.nh * a.J;
   const long long ntiles = (total + tri_sb(1 << cls) - 1) / tri_sb(1 << cls);
   return fp64 ? launch_cls<double>(cls, a, nullptr, nullptr, ntiles, st)

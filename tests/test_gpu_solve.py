@@ -117,3 +117,27 @@ def test_nonfinite_input_is_reported(pd):
         plan.solve(dev(b), tol=1e-12, maxit=5)
     assert ei.value.status == pd.PD_ERR_NONFINITE
     plan.close()
+
+
+def test_plan_autotuner_choices(pd):
+    # mixed plans of >= 2^18 unknowns time two tile widths and two lane classes
+    # at creation; the choices must be among the candidates, and a solve with
+    # them must still reach the oracle's solution
+    w = W.ade2d(nx=63, ny=63, nt=128, scheme=W.CN, alpha=1e-3)
+    pb = w.problem
+    plan = make_plan(pb, pd.PD_MIXED)
+    tx, lanes = plan.tuning()
+    rows = pb.nt
+    assert tx in (max(2, min(32, 4096 // rows)), max(2, min(32, 8192 // rows)))
+    default_lanes = 1 << int(np.ceil(np.log2(-(-pb.space.ny // 32))))
+    assert lanes in (default_lanes, 2 * default_lanes)
+    b = _rhs(w)
+    uref = S.solve_sequential(pb, b)
+    u, it, rel = plan.solve(dev(b), tol=1e-12, maxit=30)
+    assert rel2(host(u), uref) <= 1e-10, (rel2(host(u), uref), it, tx, lanes)
+    plan.close()
+    # FP64 plans keep the default rules (chunks of at most 16 rows)
+    plan64 = make_plan(pb, pd.PD_FP64)
+    assert plan64.tuning()[1] == 1 << int(np.ceil(np.log2(-(-pb.space.ny // 16))))
+    plan64.close()
+
