@@ -20,6 +20,9 @@ Modules
   closed_forms  O4: Lemma 1 eigenvalues, spatial eigenvalues, the per-mode
                 contraction of eq. 5.1, the spectrum of Theorem 3.1.
   control       O5: the heat source inversion functional and its gradient.
+  paradiag1     O6: ParaDiag-I with geometric time steps (Section 2.1.1):
+                closed-form V, V^{-1}, the column scaling D~, the three steps
+                of eq. 2.7, and the exact variable-step solution by stepping.
 
 Every function is pinned by a test in tests/test_oracle_*.py against a
 closed form, an invariant, a bound of the paper, a worked example the paper

@@ -13,7 +13,8 @@ the output times 2^-53.
 
 Problem families (the paper's model problems):
   * advection-diffusion u_t = nu*Lap(u) - a.grad(u) + f  (Section 2, eq. 2.1 and
-    eq. 2.14), theta-method in time (eq. 2.4);
+    eq. 2.14), theta-method in time (eq. 2.4), with uniform steps or with the
+    geometrically increasing steps of ParaDiag-I (Section 2.1.1, eq. 2.8);
   * wave equation u_tt = Lap(u) + f (Section 3, eq. 3.1), implicit leap-frog
     in time (eq. 3.2b).
 """
@@ -118,6 +119,29 @@ class Problem:
         if self.scheme == CN:
             return 0.5
         return self.theta
+
+
+@dataclasses.dataclass(frozen=True)
+class GeometricProblem:
+    """All-at-once theta-method system with geometrically increasing steps
+    (Section 2.1.1), the problem ParaDiag-I solves directly: ``nt`` steps, the
+    last one of length ``dt_last``, consecutive steps in the ratio ``tau > 1``
+    (eq. 2.8).  ``scaled`` selects the column-scaled eigenvector matrix
+    V D~ of the same section."""
+    space: Space
+    nt: int
+    dt_last: float
+    tau: float
+    scheme: int
+    scaled: bool = True
+
+    @property
+    def unknowns(self) -> int:
+        return self.space.size * self.nt
+
+    @property
+    def theta_eff(self) -> float:
+        return 1.0 if self.scheme == BE else 0.5
 
 
 @dataclasses.dataclass
@@ -239,6 +263,32 @@ def wave1d(nx=1023, nt=1024, T=2.0, alpha=0.1, seed=SEED_BASE + 4, name="wave1d"
     return Workload(name, pb, u0, u1, None, seed)
 
 
+def pd1_ade1d(nx=128, nt=32, tau=1.16, dt_last=0.05, nu=1e-3, scheme=CN, scaled=True,
+              seed=SEED_BASE + 5, name="pd1_ade1d") -> Workload:
+    """The ParaDiag-I example of Section 2.1.1: u_t - nu u_xx + u_x = 0 on (-1, 1),
+    periodic (eq. 2.1, the grid x_j = -1 + j h, h = 2/nx), u0 = exp(-30 x^2),
+    geometric steps (eq. 2.8).  Defaults: the window of the windowing figure
+    (Nt = 32, tau = 1.16, dt_Nt = 0.05, nu = 1e-3, trapezoidal rule)."""
+    sp = Space(dim=1, nx=nx, nu=nu, ax=1.0, bc_x=PERIODIC, lx=2.0)
+    pb = GeometricProblem(space=sp, nt=nt, dt_last=dt_last, tau=tau, scheme=scheme, scaled=scaled)
+    x = sp.xs() - 1.0
+    u0 = np.exp(-30.0 * x * x)
+    return Workload(name, pb, u0, None, None, seed)
+
+
+def pd1_ade2d(nx=255, ny=255, nt=32, tau=1.16, dt_last=0.05, nu=1e-3, ax=1.0, ay=0.5,
+              scheme=BE, scaled=True, seed=SEED_BASE + 6, name="pd1_ade2d") -> Workload:
+    """One ParaDiag-I window on the 2D advection-diffusion grid of ``ade2d``
+    (x periodic, y Dirichlet, seeded Gaussian bump, zero source) with geometric
+    steps (eq. 2.8); backward Euler by default."""
+    sp = Space(dim=2, nx=nx, ny=ny, nu=nu, ax=ax, ay=ay, bc_x=PERIODIC, bc_y=DIRICHLET)
+    pb = GeometricProblem(space=sp, nt=nt, dt_last=dt_last, tau=tau, scheme=scheme, scaled=scaled)
+    x0, y0 = uniform(seed, 2, 0.3, 0.7)
+    X, Y = sp.mesh()
+    u0 = np.exp(-20.0 * ((X - x0) ** 2 + (Y - y0) ** 2)).reshape(-1)
+    return Workload(name, pb, u0, None, None, seed, extra={"center": (x0, y0)})
+
+
 def named(name: str, **kw) -> Workload:
     """The five named workloads at their full sizes (keyword overrides allowed)."""
     table = {
@@ -246,6 +296,8 @@ def named(name: str, **kw) -> Workload:
         "ade2d_cn": lambda: ade2d(**kw),
         "heat2d_control": lambda: heat2d_control(**kw),
         "wave1d_leapfrog": lambda: wave1d(**kw),
+        "pd1_ade1d": lambda: pd1_ade1d(**kw),
+        "pd1_ade2d": lambda: pd1_ade2d(**kw),
     }
     return table[name]()
 
@@ -253,6 +305,11 @@ def named(name: str, **kw) -> Workload:
 def workload_summary(w: Workload) -> dict:
     p = w.problem
     s = p.space
+    if isinstance(p, GeometricProblem):
+        return {"name": w.name, "dim": s.dim, "nx": s.nx, "ny": s.ny if s.dim == 2 else 1,
+                "nt": p.nt, "dt_last": p.dt_last, "tau": p.tau, "scheme": SCHEME_NAMES[p.scheme],
+                "column_scaling": p.scaled, "nu": s.nu, "ax": s.ax, "ay": s.ay,
+                "unknowns": p.unknowns, "seed": w.seed}
     return {"name": w.name, "dim": s.dim, "nx": s.nx, "ny": s.ny if s.dim == 2 else 1,
             "nt": p.nt, "dt": p.dt, "scheme": SCHEME_NAMES[p.scheme], "alpha": p.alpha,
             "nu": s.nu, "ax": s.ax, "ay": s.ay, "unknowns": p.unknowns, "seed": w.seed}
