@@ -243,6 +243,68 @@ PD_API pd_status pd_apply_precond_noalloc(const pd_space* sp, int nt, double dt,
                                           int scheme, double theta, const double* r, double* z,
                                           void* stream, unsigned long long* scratch_needed);
 
+/* ---------------------------------------------------------------------------
+ * ParaDiag-I with geometrically increasing time steps (Section 2.1.1): a
+ * direct solver of the theta-method all-at-once system eq. 2.5a,
+ *   (B1 (x) I + B2 (x) K) u = b,
+ * B1, B2 the lower-bidiagonal matrices of eq. 2.5b for the steps of eq. 2.8,
+ *   dt_n = dt_last * tau^(n - nt), n = 1..nt,
+ * by the three steps of eq. 2.7 with the closed-form eigenvector matrix V of
+ * B2^{-1} B1 (theorem of Section 2.1.1; for theta = 1/2 the printed factor
+ * q^{-n} of q_n is read as tau^{-n}, the reading that makes V V^{-1} = I).
+ * Layout of u and b as for pd_plan: [nt][S] device FP64, caller-owned.
+ * --------------------------------------------------------------------------- */
+typedef struct pd1_plan pd1_plan;
+
+/* Plan for one window.  scheme: PD_BE (theta = 1) or PD_CN (theta = 1/2,
+ * the trapezoidal rule); column_scaling: 1 uses V D~ with
+ * D~ = diag((1 + sum_{j<=nt-n} p_j^2)^{-1/2}) (Section 2.1.1), 0 uses V.
+ * precision PD_FP64: steps (a)-(c) and the residual in FP64; PD_MIXED: steps
+ * (a)-(c) in FP32 (the tensor-core x-transform in 2D) and the residual of the
+ * refinement sweeps in double-float.  sp: as for pd_plan_create (2D: x
+ * Dirichlet needs ax = 0, y Dirichlet).  1 <= nt <= 32 (PD_ERR_UNSUPPORTED
+ * above: the windows of Section 2.1.1 hold 20 to 32 steps, and Cond_2(V)
+ * passes 1e9 beyond), dt_last > 0, tau > 1.  stream: cudaStream_t (NULL: the
+ * default stream).  Allocates all device memory the solves need. */
+PD_API pd_status pd1_plan_create(const pd_space* sp, int nt, double dt_last, double tau,
+                                 int scheme, int column_scaling, int precision, void* stream,
+                                 pd1_plan** out);
+PD_API pd_status pd1_plan_destroy(pd1_plan* plan);
+
+/* dts[0..nt): the step sizes dt_1..dt_nt of eq. 2.8 (host array). */
+PD_API pd_status pd1_step_sizes(const pd1_plan* plan, double* dts);
+
+/* *cond: ||V D~||_F ||(V D~)^{-1}||_F (an upper bound of Cond_2 of the
+ * eigenvector matrix the plan uses; the roundoff of the direct solve grows
+ * with it). */
+PD_API pd_status pd1_condition(const pd1_plan* plan, double* cond);
+
+/* y = A u (eq. 2.5a), FP64. */
+PD_API pd_status pd1_apply_A(pd1_plan* plan, const double* u, double* y);
+
+/* b of eq. 2.5a: b_n = theta f(t_n) + (1-theta) f(t_{n-1}), plus
+ * (I/dt_1 - (1-theta) K) u0 in the first row.  u0: [S]; f: [nt+1][S] values
+ * at t_0..t_nt, or NULL for f = 0; b: [nt][S]. */
+PD_API pd_status pd1_build_rhs(pd1_plan* plan, const double* u0, const double* f, double* b);
+
+/* u = A^{-1} b: the direct solve of eq. 2.7 (u on entry is ignored), then up
+ * to max_refine sweeps u <- u + P^{-1}(b - A u) with the same solve P^{-1}
+ * (residual in FP64 / double-float), stopping early once
+ * ||b - A u||_2 <= tol ||b||_2.  max_refine = 0 is the paper's direct solver.
+ * relres (may be NULL) receives ||b - A u||_2 / ||b||_2 of the returned u;
+ * it costs one residual pass, skipped when relres is NULL and max_refine = 0.
+ * refinements (may be NULL) receives the sweeps taken.  Returns
+ * PD_ERR_NOT_CONVERGED when max_refine > 0, tol > 0 and the tolerance was not
+ * reached, PD_ERR_NONFINITE on a NaN or Inf.  Synchronises the plan's stream
+ * when a residual is formed. */
+PD_API pd_status pd1_solve(pd1_plan* plan, const double* b, double* u, double tol,
+                           int max_refine, int* refinements, double* relres);
+
+/* Kernel launches made through the plan so far; device bytes it holds. */
+PD_API pd_status pd1_launches(const pd1_plan* plan, unsigned long long* count);
+PD_API pd_status pd1_workspace(const pd1_plan* plan, unsigned long long* bytes);
+PD_API const char* pd1_last_error(const pd1_plan* plan);
+
 PD_API const char* pd_status_string(pd_status s);
 PD_API const char* pd_last_error(const pd_plan* plan);
 

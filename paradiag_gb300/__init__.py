@@ -80,6 +80,18 @@ _SIGS = {
     "pd_batch_uses_graph": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int)]),
     "pd_batch_relres": (ctypes.c_int, [_P, _D]),
     "pd_batch_last_error": (ctypes.c_char_p, [_P]),
+    "pd1_plan_create": (ctypes.c_int, [ctypes.POINTER(pd_space), ctypes.c_int, ctypes.c_double,
+                                       ctypes.c_double, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                       _P, ctypes.POINTER(_P)]),
+    "pd1_plan_destroy": (ctypes.c_int, [_P]),
+    "pd1_step_sizes": (ctypes.c_int, [_P, _D]),
+    "pd1_condition": (ctypes.c_int, [_P, _D]),
+    "pd1_apply_A": (ctypes.c_int, [_P, _P, _P]),
+    "pd1_build_rhs": (ctypes.c_int, [_P, _P, _P, _P]),
+    "pd1_solve": (ctypes.c_int, [_P, _P, _P, ctypes.c_double, ctypes.c_int, _I, _D]),
+    "pd1_launches": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_ulonglong)]),
+    "pd1_workspace": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_ulonglong)]),
+    "pd1_last_error": (ctypes.c_char_p, [_P]),
     "pd_status_string": (ctypes.c_char_p, [ctypes.c_int]),
     "pd_last_error": (ctypes.c_char_p, [_P]),
 }
@@ -259,6 +271,70 @@ def pd_adjoint_solve(plan, g, lam, mode, tol, maxit, restart):
 
 
 # --- torch convenience layer ----------------------------------------------
+def pd1_plan_create(space: pd_space, nt, dt_last, tau, scheme, column_scaling, precision, stream):
+    out = _P()
+    st = load().pd1_plan_create(ctypes.byref(space), nt, dt_last, tau, scheme, column_scaling,
+                                precision, _P(stream), ctypes.byref(out))
+    return st, out.value
+
+
+def pd1_plan_destroy(plan):
+    return load().pd1_plan_destroy(plan)
+
+
+def pd1_step_sizes(plan, nt):
+    buf = (ctypes.c_double * nt)()
+    st = load().pd1_step_sizes(plan, buf)
+    return st, list(buf)
+
+
+def pd1_condition(plan):
+    v = ctypes.c_double(0.0)
+    st = load().pd1_condition(plan, ctypes.byref(v))
+    return st, v.value
+
+
+def pd1_apply_A(plan, u, y):
+    return load().pd1_apply_A(plan, u, y)
+
+
+def pd1_build_rhs(plan, u0, f, b):
+    return load().pd1_build_rhs(plan, u0, f, b)
+
+
+def pd1_solve(plan, b, u, tol, max_refine):
+    it = ctypes.c_int(0)
+    rr = ctypes.c_double(0.0)
+    st = load().pd1_solve(plan, b, u, tol, max_refine, ctypes.byref(it), ctypes.byref(rr))
+    return st, it.value, rr.value
+
+
+def pd1_launches(plan):
+    v = ctypes.c_ulonglong(0)
+    st = load().pd1_launches(plan, ctypes.byref(v))
+    return st, v.value
+
+
+def pd1_workspace(plan):
+    v = ctypes.c_ulonglong(0)
+    st = load().pd1_workspace(plan, ctypes.byref(v))
+    return st, v.value
+
+
+def pd1_last_error(plan) -> str:
+    return load().pd1_last_error(plan).decode()
+
+
+def _space_of(space) -> pd_space:
+    """pd_space from a mapping or an object with the pd_space fields."""
+    g = (lambda k, d=0: space.get(k, d)) if isinstance(space, dict) else \
+        (lambda k, d=0: getattr(space, k, d))
+    return pd_space(int(g("dim", 1)), int(g("nx")), int(g("ny", 1) or 1),
+                    float(g("nu", 1.0)), float(g("ax", 0.0)), float(g("ay", 0.0)),
+                    int(g("bc_x", 0)), int(g("bc_y", 0)), float(g("lx", 1.0)),
+                    float(g("ly", 1.0)))
+
+
 def _ptr(t):
     return None if t is None else ctypes.c_void_p(t.data_ptr())
 
@@ -274,12 +350,7 @@ class Plan:
     def __init__(self, space, nt, dt, alpha, scheme=PD_BE, theta=1.0, precision=PD_MIXED,
                  stream=None):
         import torch
-        g = (lambda k, d=0: space.get(k, d)) if isinstance(space, dict) else \
-            (lambda k, d=0: getattr(space, k, d))
-        self.space = pd_space(int(g("dim", 1)), int(g("nx")), int(g("ny", 1) or 1),
-                              float(g("nu", 1.0)), float(g("ax", 0.0)), float(g("ay", 0.0)),
-                              int(g("bc_x", 0)), int(g("bc_y", 0)), float(g("lx", 1.0)),
-                              float(g("ly", 1.0)))
+        self.space = _space_of(space)
         self.nt, self.dt, self.alpha = int(nt), float(dt), float(alpha)
         self.scheme, self.theta, self.precision = int(scheme), float(theta), int(precision)
         self.S = self.space.nx * (self.space.ny if self.space.dim == 2 else 1)
@@ -402,6 +473,102 @@ class Plan:
         return lam, it, rel
 
 
+class Plan1:
+    """A ParaDiag-I plan (geometric time steps, Section 2.1.1) on the current
+    CUDA device and stream: the direct all-at-once solver of eq. 2.7 for one
+    window of ``nt`` theta-method steps dt_n = dt_last tau^(n - nt).
+
+    ``space`` as for Plan; tensors are CUDA float64 of shape (nt, S).
+    """
+
+    def __init__(self, space, nt, dt_last, tau, scheme=PD_BE, column_scaling=True,
+                 precision=PD_FP64, stream=None):
+        import torch
+        self.space = _space_of(space)
+        self.nt, self.dt_last, self.tau = int(nt), float(dt_last), float(tau)
+        self.scheme, self.precision = int(scheme), int(precision)
+        self.column_scaling = bool(column_scaling)
+        self.S = self.space.nx * (self.space.ny if self.space.dim == 2 else 1)
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        st, h = pd1_plan_create(self.space, self.nt, self.dt_last, self.tau, self.scheme,
+                                int(self.column_scaling), self.precision, self.stream.cuda_stream)
+        if st != PD_OK:
+            raise PDError(st, "pd1_plan_create")
+        self._h = h
+
+    @property
+    def handle(self):
+        return self._h
+
+    def close(self):
+        if getattr(self, "_h", None):
+            pd1_plan_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _check(self, st, what):
+        if st != PD_OK:
+            raise PDError(st, f"{what}: {pd1_last_error(self._h)}")
+
+    def _check_t(self, t, n=None):
+        import torch
+        n = self.nt * self.S if n is None else n
+        if not (t.is_cuda and t.dtype == torch.float64 and t.is_contiguous() and t.numel() == n):
+            raise ValueError(f"expected a contiguous CUDA float64 tensor with {n} elements")
+
+    def step_sizes(self):
+        st, v = pd1_step_sizes(self._h, self.nt)
+        self._check(st, "pd1_step_sizes")
+        return v
+
+    def condition(self):
+        st, v = pd1_condition(self._h)
+        self._check(st, "pd1_condition")
+        return v
+
+    def launches(self):
+        st, v = pd1_launches(self._h)
+        self._check(st, "pd1_launches")
+        return v
+
+    def workspace_bytes(self):
+        st, v = pd1_workspace(self._h)
+        self._check(st, "pd1_workspace")
+        return v
+
+    def apply_A(self, u, y=None):
+        import torch
+        self._check_t(u)
+        y = torch.empty_like(u) if y is None else y
+        self._check(pd1_apply_A(self._h, _ptr(u), _ptr(y)), "pd1_apply_A")
+        return y
+
+    def build_rhs(self, u0, f=None, b=None):
+        import torch
+        self._check_t(u0, self.S)
+        if f is not None:
+            self._check_t(f, (self.nt + 1) * self.S)
+        b = torch.empty((self.nt, self.S), dtype=torch.float64, device=u0.device) if b is None else b
+        self._check(pd1_build_rhs(self._h, _ptr(u0), _ptr(f), _ptr(b)), "pd1_build_rhs")
+        return b
+
+    def solve(self, b, u=None, tol=0.0, max_refine=0, allow_not_converged=False):
+        """u = A^{-1} b; returns (u, refinement sweeps, relative residual)."""
+        import torch
+        self._check_t(b)
+        u = torch.empty_like(b) if u is None else u
+        self._check_t(u)
+        st, it, rel = pd1_solve(self._h, _ptr(b), _ptr(u), tol, max_refine)
+        if not (st == PD_OK or (allow_not_converged and st == PD_ERR_NOT_CONVERGED)):
+            self._check(st, "pd1_solve")
+        return u, it, rel
+
+
 class Batch:
     """Many independent 1D problems solved together (packed FP64 arrays).
 
@@ -506,6 +673,6 @@ class _Lazy:
 
 PDSolve = _Lazy()
 
-__all__ = ["build", "lib_path", "load", "Plan", "Batch", "PDSolve", "PDError", "pd_space",
+__all__ = ["build", "lib_path", "load", "Plan", "Plan1", "Batch", "PDSolve", "PDError", "pd_space",
            "pd_problem",
            "exported_symbols"] + [k for k in _SIGS]

@@ -781,9 +781,8 @@ double hstep(int n, double L, int bc) { return L / (bc == PD_PERIODIC ? n : n + 
 FwdArgs plan_fwd_args(const pd_plan* p) { return fwd_base_impl(p); }
 InvArgs plan_inv_args(const pd_plan* p) { return inv_base_impl(p); }
 TriArgs plan_tri_args(const pd_plan* p, void* data) { return tri_args_impl(p, data); }
-pd_status plan_create_internal(const pd_space* sp, int nt, double dt, double alpha, int scheme,
-                               double theta, int precision, void* stream, bool with_state,
-                               pd_plan** out);
+pd_status plan_step_b(pd_plan* p) { return step_b(p); }
+pd_status plan_fail_cuda(pd_plan* p, cudaError_t e, const char* what) { return fail_cuda(p, e, what); }
 
 extern "C" {
 
@@ -878,7 +877,8 @@ const char* pd_last_error(const pd_plan* plan) { return plan ? plan->msg : "null
 
 pd_status pd_plan_create(const pd_space* sp, int nt, double dt, double alpha, int scheme,
                          double theta, int precision, void* stream, pd_plan** out) {
-  return plan_create_internal(sp, nt, dt, alpha, scheme, theta, precision, stream, true, out);
+  return plan_create_internal(sp, nt, dt, alpha, scheme, theta, precision, stream, true, out,
+                              nullptr);
 }
 
 }  // extern "C"
@@ -887,7 +887,7 @@ pd_status pd_plan_create(const pd_space* sp, int nt, double dt, double alpha, in
 // (the batched solver keeps those packed for all problems)
 pd_status plan_create_internal(const pd_space* sp, int nt, double dt, double alpha, int scheme,
                                double theta, int precision, void* stream, bool with_state,
-                               pd_plan** out) {
+                               pd_plan** out, const double* row_lam) {
   if (!out) return PD_ERR_ARG;
   *out = nullptr;
   if (!sp) return PD_ERR_ARG;
@@ -908,7 +908,7 @@ pd_status plan_create_internal(const pd_space* sp, int nt, double dt, double alp
   // M = 2^ceil(log2(2 Nt - 1)) rows; the tile must hold 2 columns at least
   const int budget_rows = precision == PD_MIXED ? 4096 : 2048;
   int Mb = 0;
-  if (!is_pow2(nt)) {
+  if (!is_pow2(nt) && !row_lam) {
     Mb = 1;
     while (Mb < 2 * nt - 1) Mb <<= 1;
   }
@@ -928,7 +928,8 @@ pd_status plan_create_internal(const pd_space* sp, int nt, double dt, double alp
   p->sp = *sp;
   if (sp->dim == 1) { p->sp.ny = 1; p->sp.ay = 0.0; p->sp.bc_y = PD_DIRICHLET; p->sp.ly = 1.0; }
   p->nt = nt;
-  p->nh = nt / 2 + 1;
+  // ParaDiag-I plans (row_lam given) solve one shifted system per time row
+  p->nh = row_lam ? nt : nt / 2 + 1;
   p->S = (int)S;
   p->logN = ilog2(nt);
   p->scheme = scheme;
@@ -1068,8 +1069,45 @@ pd_status plan_create_internal(const pd_space* sp, int nt, double dt, double alp
     p->tri_cl = st.kxl; p->tri_cd = kcx; p->tri_cu = st.kxu;
   }
 
-  // Lemma 1 eigenvalues (half spectrum) and the singularity check
+  // Lemma 1 eigenvalues (half spectrum) and the singularity check, or the
+  // caller's per-row shifts (pairs lambda_1, lambda_2 as re, im)
   std::vector<cd> lam((size_t)2 * p->nh);
+  if (row_lam) {
+    for (int k = 0; k < 2 * p->nh; ++k) lam[k] = cd(row_lam[2 * k], row_lam[2 * k + 1]);
+    pd_status s2 = upload_cplx(p, &p->lam, lam, p->fp64);
+    const size_t specb = (size_t)p->nh * p->sg.specS * cbytes(p);
+    if (s2 == PD_OK) s2 = dalloc(p, &p->spec, specb);
+    if (s2 == PD_OK && p->xform) s2 = dalloc(p, &p->spec2, specb);
+    if (s2 == PD_OK && p->xform_tc) {
+      const int rows = p->nh * (int)(S / sp->nx);
+      const int ldo = 2 * p->sg.nxp;
+      cudaError_t e = xform_tc_prepare(&p->xtc_fwd, rows, sp->nx, ldo, (const float*)p->spec,
+                                       (float*)p->spec2, p->Gf_hi, p->Gf_lo, p->gf_inv, p->amax);
+      if (e == cudaSuccess)
+        e = xform_tc_prepare(&p->xtc_inv, rows, sp->nx, ldo, (const float*)p->spec2,
+                             (float*)p->spec, p->Gi_hi, p->Gi_lo, p->gi_inv, p->amax + 1);
+      if (e != cudaSuccess) s2 = fail_cuda(p, e, "tensor map encoding");
+    }
+    if (s2 == PD_OK && !p->fp64 && with_state) s2 = dalloc(p, (void**)&p->Udf, NS(p) * sizeof(float2));
+    if (s2 == PD_OK && !p->fp64 && with_state) s2 = dalloc(p, (void**)&p->Bdf, NS(p) * sizeof(float2));
+    if (s2 == PD_OK) s2 = dalloc(p, (void**)&p->dsc, NSC * sizeof(double));
+    if (s2 == PD_OK) s2 = dalloc(p, (void**)&p->dflag, sizeof(int));
+    if (s2 == PD_OK) {
+      cudaError_t e = cudaMallocHost((void**)&p->hsc, NSC * sizeof(double));
+      if (e != cudaSuccess) s2 = fail_cuda(p, e, "cudaMallocHost");
+    }
+    if (s2 == PD_OK) {
+      cudaError_t e = cudaMemset(p->dflag, 0, sizeof(int));
+      if (e != cudaSuccess) s2 = fail_cuda(p, e, "cudaMemset");
+    }
+    if (s2 != PD_OK) {
+      free_plan(p);
+      return s2;
+    }
+    p->tuned = 1;
+    *out = p;
+    return PD_OK;
+  }
   const double PI = 3.14159265358979323846;
   const double ar = std::pow(alpha, 1.0 / nt);
   for (int k = 0; k < p->nh; ++k) {

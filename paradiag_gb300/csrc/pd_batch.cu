@@ -19,10 +19,6 @@
 
 #include "pd_plan.h"
 
-pd_status plan_create_internal(const pd_space* sp, int nt, double dt, double alpha, int scheme,
-                               double theta, int precision, void* stream, bool with_state,
-                               pd_plan** out);
-
 struct pd_batch {
   int np = 0;
   bool fp64 = false;

@@ -67,3 +67,14 @@ struct pd_plan {
 FwdArgs plan_fwd_args(const pd_plan* p);
 InvArgs plan_inv_args(const pd_plan* p);
 TriArgs plan_tri_args(const pd_plan* p, void* data);
+// step (b) of the plan (x-eigentransform, shifted tridiagonal solves, inverse
+// x-transform) on p->spec
+pd_status plan_step_b(pd_plan* p);
+pd_status plan_fail_cuda(pd_plan* p, cudaError_t e, const char* what);
+// Plan creation.  With row_lam (2 nt complex numbers as re, im pairs) the plan
+// holds no time transform: its step (b) solves one system per time row n,
+// (lambda_1n I + lambda_2n K) z_n = s_n, with lambda_1n = row_lam[4n] +
+// i row_lam[4n+1] and lambda_2n = row_lam[4n+2] + i row_lam[4n+3].
+pd_status plan_create_internal(const pd_space* sp, int nt, double dt, double alpha, int scheme,
+                               double theta, int precision, void* stream, bool with_state,
+                               pd_plan** out, const double* row_lam = nullptr);
