@@ -43,6 +43,11 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU baseline leg")
     ap.add_argument("--small", action="store_true", help="a small case (profiling runs)")
     ap.add_argument("--no-batch", action="store_true", help="skip the batched-workload leg")
+    ap.add_argument("--no-pd1", action="store_true", help="skip the ParaDiag-I leg")
+    ap.add_argument("--pd1-only", action="store_true",
+                    help="only the ParaDiag-I leg (one JSON object; profiling runs)")
+    ap.add_argument("--pd1-kernels", action="store_true",
+                    help="only the ParaDiag-I mixed kernel profile (ncu driver)")
     ap.add_argument("--profile-iteration", action="store_true",
                     help="only time the kernels of one iteration (the driver of ncu captures)")
     ap.add_argument("--sweep", action="store_true",
@@ -227,6 +232,123 @@ def batched_leg(pd, torch, dev, args):
     return out
 
 
+# DRAM bytes per launch of the ParaDiag-I kernels from ncu (None until captured)
+PD1_NCU_TRAFFIC = {}
+
+
+def pd1_bytes_per_unknown(fp64):
+    """Algorithmic DRAM bytes per space-time unknown of the ParaDiag-I kernels
+    of one refinement sweep: step (a) reads the iterate and b and writes one
+    complex spectrum value; step (c) reads the spectrum and updates the iterate."""
+    st = 8.0
+    c = 16.0 if fp64 else 8.0
+    return {"pd1_resid_step_a": 2 * st + c, "pd1_step_c_update": c + 2 * st}
+
+
+def pd1_kernel_profile(pd, torch, dev, precisions):
+    """Per-kernel times of a ParaDiag-I refinement sweep on a 255 x 1023 x 32
+    window (8.3 M unknowns; the sweep's working set exceeds the 129 MB L2),
+    as algorithmic HBM throughput against the measured copy peak."""
+    import workloads as W
+    wl = W.pd1_ade2d()
+    pb = wl.problem
+    sp = pb.space
+    big = dict(dim=2, nx=sp.nx, ny=1023, nu=sp.nu, ax=sp.ax, ay=sp.ay, bc_x=sp.bc_x,
+               bc_y=sp.bc_y)
+    stream = torch.cuda.current_stream()
+    hbm, _, src = peaks()
+    nsb = sp.nx * 1023 * pb.nt
+    kern = {}
+    for prec in precisions:
+        tag = "fp64" if prec == pd.PD_FP64 else "mixed"
+        pl = pd.Plan1(big, pb.nt, pb.dt_last, pb.tau, pd.PD_BE, True, prec, stream)
+        u0b = torch.exp(-torch.linspace(-3.0, 3.0, sp.nx * 1023, dtype=torch.float64,
+                                        device=dev) ** 2)
+        bb = pl.build_rhs(u0b)
+        ub = torch.empty_like(bb)
+        pl.profile_sweep(bb, ub, reps=2)
+        kms = pl.profile_sweep(bb, ub, reps=5)
+        bpu = pd1_bytes_per_unknown(prec == pd.PD_FP64)
+        ent = {}
+        for name, t in (("pd1_resid_step_a", kms[0]), ("pd1_step_c_update", kms[2])):
+            gbs = bpu[name] * nsb / (t / 1e3) / 1e9
+            ent[name] = {"ms": t, "bound": "hbm", "achieved": gbs, "peak": hbm, "unit": "GB/s",
+                         "frac": gbs / hbm, "algorithmic_bytes": bpu[name] * nsb,
+                         "traffic": PD1_NCU_TRAFFIC.get((tag, name)),
+                         "peak_source": f"{src} (MEASURED_PEAKS.json)"}
+        ent["step_b_ms"] = kms[1]
+        kern[tag] = ent
+        pl.close()
+    return kern
+
+
+def pd1_leg(pd, torch, dev, args):
+    """ParaDiag-I (geometric steps, Section 2.1.1): one window of the 2D grid,
+    255 x 255, Nt = 32, tau = 1.16, dt_Nt = 0.05, backward Euler.  Timed: the
+    mixed solve (FP32 steps, double-float residual sweeps) to a relative
+    residual of 1e-12, L2 flushed before every solve (the window's working set,
+    ~0.1 GB, fits in L2); beside it the FP64 direct solve (the paper's
+    method) and the FP64 solve refined to the same residual.  The per-kernel
+    rooflines come from a 255 x 1023 x 32 window (working set above L2)."""
+    import workloads as W
+    wl = W.pd1_ade2d()
+    pb = wl.problem
+    sp = pb.space
+    space = dict(dim=2, nx=sp.nx, ny=sp.ny, nu=sp.nu, ax=sp.ax, ay=sp.ay, bc_x=sp.bc_x,
+                 bc_y=sp.bc_y)
+    stream = torch.cuda.current_stream()
+    NS = pb.unknowns
+    flush = torch.empty(64 << 20, dtype=torch.float32, device=dev)   # 256 MB > L2
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+
+    def timed(plan, b, u, k, **kw):
+        tot = 0.0
+        res = None
+        for i in range(k):
+            flush.fill_(float(i))
+            e0.record(stream)
+            res = plan.solve(b, u, **kw)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            tot += e0.elapsed_time(e1)
+        return tot / k, res
+
+    plan = pd.Plan1(space, pb.nt, pb.dt_last, pb.tau, pd.PD_BE, True, pd.PD_MIXED, stream)
+    b = plan.build_rhs(torch.from_numpy(wl.u0).to(dev))
+    u = torch.empty_like(b)
+    for _ in range(3):
+        plan.solve(b, u, tol=1e-12, max_refine=20)
+    k = max(1, min(args.steps, 20))
+    l0 = plan.launches()
+    ms, (_, sweeps, rel) = timed(plan, b, u, k, tol=1e-12, max_refine=20)
+    launches = (plan.launches() - l0) // k
+    r64 = float(torch.linalg.norm(b - plan.apply_A(u)) / torch.linalg.norm(b))
+
+    plan64 = pd.Plan1(space, pb.nt, pb.dt_last, pb.tau, pd.PD_BE, True, pd.PD_FP64, stream)
+    u64 = torch.empty_like(b)
+    plan64.solve(b, u64)
+    k64 = max(1, min(args.steps, 3))
+    ms_direct, (_, _, rel_direct) = timed(plan64, b, u64, k64)
+    ms64, (_, sweeps64, rel64) = timed(plan64, b, u64, k64, tol=1e-12, max_refine=20)
+    plan.close()
+    plan64.close()
+
+    kern = pd1_kernel_profile(pd, torch, dev, (pd.PD_MIXED, pd.PD_FP64))
+    del flush
+    return {"workload": "pd1_ade2d_be_255x255x32: 2D advection-diffusion (x periodic, "
+                        "y Dirichlet, nu = 1e-3, velocity (1, 0.5)), backward Euler, "
+                        "geometric steps dt_n = 0.05 * 1.16^(n-32), column-scaled V",
+            "unknowns": NS, "ms_per_solve": ms, "value": NS / (ms / 1e3), "unit": UNIT,
+            "refinement_sweeps": sweeps, "relres": rel, "relres_fp64_apply_A": r64,
+            "gpu_launches": launches, "l2": "flushed (256 MB write) before every solve",
+            "fp64_direct": {"ms_per_solve": ms_direct, "value": NS / (ms_direct / 1e3),
+                            "relres": rel_direct},
+            "fp64_refined": {"ms_per_solve": ms64, "value": NS / (ms64 / 1e3),
+                             "refinement_sweeps": sweeps64, "relres": rel64},
+            "kernel_roofline_255x1023x32": kern}
+
+
 def run_sweep(pd, torch, dev):
     """Per-kernel time and algorithmic HBM throughput of one mixed iteration on
     1D advection-diffusion problems (nu = 1e-2, a = 1, BE, alpha = 1e-2) of
@@ -319,6 +441,18 @@ def main():
     b = plan.build_rhs(u0)
     u = torch.zeros_like(b)
     torch.cuda.synchronize()
+    if args.pd1_kernels:
+        out = pd1_kernel_profile(pd, torch, dev, (pd.PD_MIXED,))
+        if rank == 0:
+            print(json.dumps(out), flush=True)
+        plan.close()
+        return
+    if args.pd1_only:
+        out = pd1_leg(pd, torch, dev, args)
+        if rank == 0:
+            print(json.dumps(out), flush=True)
+        plan.close()
+        return
     if args.sweep:
         out = run_sweep(pd, torch, dev)
         if rank == 0:
@@ -423,6 +557,9 @@ def main():
     batched = None
     if not args.no_batch:
         batched = batched_leg(pd, torch, dev, args)
+    pd1 = None
+    if not args.no_pd1:
+        pd1 = pd1_leg(pd, torch, dev, args)
 
     err = err64 = None
     if rank == 0 and not args.no_check:
@@ -462,6 +599,7 @@ def main():
                "kernel_roofline": roofs,
                "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
                "batched": batched,
+               "paradiag1": pd1,
                "gpu_launches": launches}
         print(json.dumps(out), flush=True)
     plan.close()

@@ -300,6 +300,14 @@ PD_API pd_status pd1_build_rhs(pd1_plan* plan, const double* u0, const double* f
 PD_API pd_status pd1_solve(pd1_plan* plan, const double* b, double* u, double tol,
                            int max_refine, int* refinements, double* relres);
 
+/* Measurement aid (no paper counterpart): from the direct solve of b, reps
+ * refinement sweeps, each timed with CUDA events on the plan's stream;
+ * ms[0] = step (a) fused with the residual, ms[1] = step (b) (with the
+ * x-eigentransforms in 2D), ms[2] = step (c) fused with the update, averages
+ * in milliseconds.  u receives the last iterate. */
+PD_API pd_status pd1_profile_sweep(pd1_plan* plan, const double* b, double* u, int reps,
+                                   float* ms);
+
 /* Kernel launches made through the plan so far; device bytes it holds. */
 PD_API pd_status pd1_launches(const pd1_plan* plan, unsigned long long* count);
 PD_API pd_status pd1_workspace(const pd1_plan* plan, unsigned long long* bytes);

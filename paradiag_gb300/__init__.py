@@ -90,6 +90,7 @@ _SIGS = {
     "pd1_build_rhs": (ctypes.c_int, [_P, _P, _P, _P]),
     "pd1_solve": (ctypes.c_int, [_P, _P, _P, ctypes.c_double, ctypes.c_int, _I, _D]),
     "pd1_launches": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_ulonglong)]),
+    "pd1_profile_sweep": (ctypes.c_int, [_P, _P, _P, ctypes.c_int, ctypes.POINTER(ctypes.c_float)]),
     "pd1_workspace": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_ulonglong)]),
     "pd1_last_error": (ctypes.c_char_p, [_P]),
     "pd_status_string": (ctypes.c_char_p, [ctypes.c_int]),
@@ -307,6 +308,12 @@ def pd1_solve(plan, b, u, tol, max_refine):
     rr = ctypes.c_double(0.0)
     st = load().pd1_solve(plan, b, u, tol, max_refine, ctypes.byref(it), ctypes.byref(rr))
     return st, it.value, rr.value
+
+
+def pd1_profile_sweep(plan, b, u, reps):
+    ms = (ctypes.c_float * 3)()
+    st = load().pd1_profile_sweep(plan, b, u, reps, ms)
+    return st, list(ms)
 
 
 def pd1_launches(plan):
@@ -556,6 +563,13 @@ class Plan1:
         b = torch.empty((self.nt, self.S), dtype=torch.float64, device=u0.device) if b is None else b
         self._check(pd1_build_rhs(self._h, _ptr(u0), _ptr(f), _ptr(b)), "pd1_build_rhs")
         return b
+
+    def profile_sweep(self, b, u, reps=5):
+        """Average ms of [step (a) + residual, step (b), step (c) + update]."""
+        self._check_t(b); self._check_t(u)
+        st, ms = pd1_profile_sweep(self._h, _ptr(b), _ptr(u), reps)
+        self._check(st, "pd1_profile_sweep")
+        return ms
 
     def solve(self, b, u=None, tol=0.0, max_refine=0, allow_not_converged=False):
         """u = A^{-1} b; returns (u, refinement sweeps, relative residual)."""

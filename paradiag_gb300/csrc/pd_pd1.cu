@@ -100,67 +100,6 @@ PD_D double ku_64(const Stencil& st, const Nb& g, const double* U, int s) {
   return k;
 }
 
-// compensated sum value = s + e (as in the ParaDiag-II residual)
-struct Acc {
-  float s, e;
-};
-PD_D void acc_add(Acc& A, float h, float l) {
-  const float t = __fadd_rn(A.s, h);
-  const float bb = __fsub_rn(t, A.s);
-  const float err = __fadd_rn(__fsub_rn(A.s, __fsub_rn(t, bb)), __fsub_rn(h, bb));
-  A.s = t;
-  A.e += err + l;
-}
-// A += k u, k and u double-float (two-product of the high parts)
-PD_D void acc_add_prod(Acc& A, dfc k, float2 u) {
-  const float p = __fmul_rn(u.x, k.hi);
-  float pe = __fmaf_rn(u.x, k.hi, -p);
-  pe = __fmaf_rn(u.x, k.lo, pe);
-  pe = __fmaf_rn(u.y, k.hi, pe);
-  acc_add(A, p, pe);
-}
-PD_D dfc neg(dfc k) { return dfc{-k.hi, -k.lo}; }
-
-// (K U)(s) of one time row in double-float
-PD_D float2 ku_df(const P1Fwd& a, const Nb& g, const float2* U, float2 uc) {
-  Acc A = {0.f, 0.f};
-  acc_add_prod(A, a.kap[0], uc);
-  if (g.l >= 0) acc_add_prod(A, a.kap[1], __ldg(&U[g.l]));
-  if (g.r >= 0) acc_add_prod(A, a.kap[2], __ldg(&U[g.r]));
-  if (g.d >= 0) acc_add_prod(A, a.kap[3], __ldg(&U[g.d]));
-  if (g.u >= 0) acc_add_prod(A, a.kap[4], __ldg(&U[g.u]));
-  const df v = fast_two_sum(A.s, A.e);
-  return make_float2(v.hi, v.lo);
-}
-
-template <typename R> struct Vec4;
-template <> struct Vec4<float> { using T = float4; static constexpr int W = 4; };
-template <> struct Vec4<double> { using T = double2; static constexpr int W = 2; };
-
-// acc[n] += M[m][n] r for n >= m (the shared-memory row m read in aligned
-// vectors; the entries below the diagonal are zero).  Called from fully
-// unrolled loops over m, so the loop bounds here are compile-time constants.
-template <typename R>
-PD_D void rank1_row(R (&acc)[P1_NT], const R* sM, R r, int m) {
-  using V = typename Vec4<R>::T;
-  constexpr int VW = Vec4<R>::W;
-  const V* row = reinterpret_cast<const V*>(sM + m * P1_NT);
-#pragma unroll
-  for (int v = 0; v < P1_NT / VW; ++v) {
-    if (v < m / VW) continue;
-    const V w = row[v];
-    if constexpr (VW == 4) {
-      acc[4 * v + 0] = fmaf(w.x, r, acc[4 * v + 0]);
-      acc[4 * v + 1] = fmaf(w.y, r, acc[4 * v + 1]);
-      acc[4 * v + 2] = fmaf(w.z, r, acc[4 * v + 2]);
-      acc[4 * v + 3] = fmaf(w.w, r, acc[4 * v + 3]);
-    } else {
-      acc[2 * v + 0] = fma(w.x, r, acc[2 * v + 0]);
-      acc[2 * v + 1] = fma(w.y, r, acc[2 * v + 1]);
-    }
-  }
-}
-
 template <typename R>
 PD_D void load_matrix(R* sM, const void* M, int N) {
   const R* g = reinterpret_cast<const R*>(M);
@@ -180,94 +119,155 @@ PD_D T warp_sum(T v) {
   return v;
 }
 
+// Loads of one time row at spatial point s: centre, the four neighbours and b.
+// Rows at or beyond N (and points beyond S) read as zero; the loads of all
+// rows are independent of the arithmetic, so the unrolled kernels below issue
+// them ahead of use.
+template <typename V>
+struct RowIn {
+  V b, c, l, r, d, u;
+};
+template <typename V>
+PD_D RowIn<V> load_row(const V* B, const V* U, const Nb& g, int s, size_t base, bool on) {
+  RowIn<V> x;
+  const V z{};
+  x.b = on ? __ldg(&B[base + s]) : z;
+  x.c = on ? __ldg(&U[base + s]) : z;
+  x.l = (on && g.l >= 0) ? __ldg(&U[base + g.l]) : z;
+  x.r = (on && g.r >= 0) ? __ldg(&U[base + g.r]) : z;
+  x.d = (on && g.d >= 0) ? __ldg(&U[base + g.d]) : z;
+  x.u = (on && g.u >= 0) ? __ldg(&U[base + g.u]) : z;
+  return x;
+}
+
+// acc2[j] = (acc[2j], acc[2j+1]) += (M[2j][m], M[2j+1][m]) r for 2j+1 >= m:
+// the shared-memory row m (transposed matrix) in aligned float4, paired FMAs
+template <int NT>
+PD_D void rank1_pair(float2 (&acc)[NT / 2], const float* sM, float r, int m) {
+  const float4* row = reinterpret_cast<const float4*>(sM + m * P1_NT);
+  const float2 rr = make_float2(r, r);
+#pragma unroll
+  for (int v = 0; v < NT / 4; ++v) {
+    if (4 * v + 3 < m) continue;
+    const float4 w = row[v];
+    acc[2 * v] = f2fma(make_float2(w.x, w.y), rr, acc[2 * v]);
+    acc[2 * v + 1] = f2fma(make_float2(w.z, w.w), rr, acc[2 * v + 1]);
+  }
+}
+template <int NT>
+PD_D void rank1_64(double (&acc)[NT], const double* sM, double r, int m) {
+  const double2* row = reinterpret_cast<const double2*>(sM + m * P1_NT);
+#pragma unroll
+  for (int v = 0; v < NT / 2; ++v) {
+    if (2 * v + 1 < m) continue;
+    const double2 w = row[v];
+    acc[2 * v] = fma(w.x, r, acc[2 * v]);
+    acc[2 * v + 1] = fma(w.y, r, acc[2 * v + 1]);
+  }
+}
+
 // ---------------------------------------------------------------------------
 // Step (a), fused with the residual.  MODE P1_DIRECT: r = b (and, mixed, the
 // double-float copy of b); P1_RESID: r = b - A u; P1_NORM: ||b - A u||^2 only.
-// PREC 0: mixed (double-float residual, FP32 transform); 1: FP64.
+// Windows of N <= NT rows; rows are handled in pairs (m, m+1).
+// Mixed (PREC 0): the residual in double-float on paired FP32 instructions
+// (lane x = row m, lane y = row m+1), the transform in FP32.
 // ---------------------------------------------------------------------------
-template <int PREC, int MODE>
-__global__ void __launch_bounds__(P1_TB) k_pd1_fwd(const P1Fwd a) {
-  using R = typename std::conditional<PREC == 0, float, double>::type;
-  using C = cplx_t<R>;
-  __shared__ __align__(16) R sW[P1_NT * P1_NT];
+template <int MODE, int NT>
+__global__ void __launch_bounds__(P1_TB) k_pd1_fwd_mixed(const P1Fwd a) {
+  __shared__ __align__(16) float sW[P1_NT * P1_NT];
   if constexpr (MODE != P1_NORM) {
-    load_matrix<R>(sW, a.W, a.N);
+    load_matrix<float>(sW, a.W, a.N);
     __syncthreads();
   }
   const int N = a.N, S = a.S;
   const int s = blockIdx.x * P1_TB + threadIdx.x;
   const bool valid = s < S;
-  const int sc = valid ? s : 0;
-  Nb g = neighbours(a.st, sc);
+  const Nb g = neighbours(a.st, valid ? s : 0);
+  const K2 kk[5] = {
+      {make_float2(a.kap[0].hi, a.kap[0].hi), make_float2(-a.kap[0].hi, -a.kap[0].hi),
+       make_float2(-a.kap[0].lo, -a.kap[0].lo)},
+      {make_float2(a.kap[1].hi, a.kap[1].hi), make_float2(-a.kap[1].hi, -a.kap[1].hi),
+       make_float2(-a.kap[1].lo, -a.kap[1].lo)},
+      {make_float2(a.kap[2].hi, a.kap[2].hi), make_float2(-a.kap[2].hi, -a.kap[2].hi),
+       make_float2(-a.kap[2].lo, -a.kap[2].lo)},
+      {make_float2(a.kap[3].hi, a.kap[3].hi), make_float2(-a.kap[3].hi, -a.kap[3].hi),
+       make_float2(-a.kap[3].lo, -a.kap[3].lo)},
+      {make_float2(a.kap[4].hi, a.kap[4].hi), make_float2(-a.kap[4].hi, -a.kap[4].hi),
+       make_float2(-a.kap[4].lo, -a.kap[4].lo)}};
+  const float2 th2 = make_float2(a.th_f, a.th_f), om2 = make_float2(a.omth_f, a.omth_f);
 
-  R acc[P1_NT];
+  float2 acc[NT / 2];
 #pragma unroll
-  for (int n = 0; n < P1_NT; ++n) acc[n] = (R)0;
-  R nrm = 0;
-  // the previous row's U(s) and (K U)(s)
-  double up64 = 0.0, kup64 = 0.0;
-  float2 updf = make_float2(0.f, 0.f), kupdf = make_float2(0.f, 0.f);
+  for (int j = 0; j < NT / 2; ++j) acc[j] = make_float2(0.f, 0.f);
+  float nrm = 0.f;
+  // row m-1 (the second row of the previous pair): U and K U (double-float)
+  df up = df_make(0.f, 0.f), kup = df_make(0.f, 0.f);
 
 #pragma unroll
-  for (int m = 0; m < P1_NT; ++m) {
-    if (m < N) {
-      const size_t base = (size_t)m * S;
-      R r = 0;
-      if (valid) {
-        if constexpr (PREC == 1) {
-          const double bm = __ldg(&a.b64[base + s]);
-          if constexpr (MODE == P1_DIRECT) {
-            r = bm;
-          } else {
-            const double* U = a.u64 + base;
-            const double um = __ldg(&U[s]);
-            const double kum = ku_64(a.st, g, U, s);
-            double v = bm - a.c1[m] * (um - up64);
-            v = fma(-a.theta, kum, v);
-            v = fma(-(1.0 - a.theta), kup64, v);
-            r = v;
-            up64 = um;
-            kup64 = kum;
-          }
-        } else {
-          if constexpr (MODE == P1_DIRECT) {
-            const df bd = df_from_double(__ldg(&a.b64[base + s]));
-            a.Bdf[base + s] = make_float2(bd.hi, bd.lo);
-            r = bd.hi;
-          } else {
-            const float2* U = a.Udf + base;
-            const float2 bm = __ldg(&a.Bdf[base + s]);
-            const float2 um = __ldg(&U[s]);
-            const float2 kum = ku_df(a, g, U, um);
-            Acc A = {bm.x, bm.y};
-            acc_add_prod(A, neg(a.c1d[m]), um);
-            acc_add_prod(A, a.c1d[m], updf);
-            acc_add(A, -a.th_f * kum.x, -a.th_f * kum.y);
-            acc_add(A, -a.omth_f * kupdf.x, -a.omth_f * kupdf.y);
-            r = fast_two_sum(A.s, A.e).hi;
-            updf = um;
-            kupdf = kum;
-          }
-        }
-      }
-      nrm += r * r;
-      if constexpr (MODE != P1_NORM) rank1_row<R>(acc, sW, r, m);
+  for (int m = 0; m < NT; m += 2) {
+    const bool onA = valid && m < N, onB = valid && m + 1 < N;
+    float2 r2;
+    if constexpr (MODE == P1_DIRECT) {
+      const double bA = onA ? __ldg(&a.b64[(size_t)m * S + s]) : 0.0;
+      const double bB = onB ? __ldg(&a.b64[(size_t)(m + 1) * S + s]) : 0.0;
+      const df dA = df_from_double(bA), dB = df_from_double(bB);
+      if (onA) a.Bdf[(size_t)m * S + s] = make_float2(dA.hi, dA.lo);
+      if (onB) a.Bdf[(size_t)(m + 1) * S + s] = make_float2(dB.hi, dB.lo);
+      r2 = make_float2(dA.hi, dB.hi);
+    } else {
+      const RowIn<float2> A = load_row(a.Bdf, a.Udf, g, s, (size_t)m * S, onA);
+      const RowIn<float2> B = load_row(a.Bdf, a.Udf, g, s, (size_t)(m + 1) * S, onB);
+      // (K U) of both rows
+      const DF2 uc = df2_pack(A.c, B.c);
+      Acc2 ku = {make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
+      acc2_add_prod(ku, kk[0], uc);
+      acc2_add_prod(ku, kk[1], df2_pack(A.l, B.l));
+      acc2_add_prod(ku, kk[2], df2_pack(A.r, B.r));
+      acc2_add_prod(ku, kk[3], df2_pack(A.d, B.d));
+      acc2_add_prod(ku, kk[4], df2_pack(A.u, B.u));
+      const df kuA = fast_two_sum(ku.s.x, ku.e.x), kuB = fast_two_sum(ku.s.y, ku.e.y);
+      // r = b - c1 (U_m - U_{m-1}) - theta K U_m - (1 - theta) K U_{m-1}
+      const dfc cA = a.c1d[m], cB = a.c1d[m + 1 < P1_NT ? m + 1 : m];
+      const K2 c1n = {make_float2(-cA.hi, -cB.hi), make_float2(cA.hi, cB.hi),
+                      make_float2(cA.lo, cB.lo)};
+      const K2 c1p = {make_float2(cA.hi, cB.hi), make_float2(-cA.hi, -cB.hi),
+                      make_float2(-cA.lo, -cB.lo)};
+      Acc2 R = {make_float2(A.b.x, B.b.x), make_float2(A.b.y, B.b.y)};
+      acc2_add_prod(R, c1n, uc);
+      acc2_add_prod(R, c1p, DF2{make_float2(up.hi, A.c.x), make_float2(up.lo, A.c.y)});
+      acc2_sub(R, f2mul(th2, make_float2(kuA.hi, kuB.hi)), f2mul(th2, make_float2(kuA.lo, kuB.lo)));
+      acc2_sub(R, f2mul(om2, make_float2(kup.hi, kuA.hi)), f2mul(om2, make_float2(kup.lo, kuA.lo)));
+      r2 = make_float2(fast_two_sum(R.s.x, R.e.x).hi, fast_two_sum(R.s.y, R.e.y).hi);
+      up = df_make(B.c.x, B.c.y);
+      kup = kuB;
+    }
+    if (!onA) r2.x = 0.f;
+    if (!onB) r2.y = 0.f;
+    nrm = fmaf(r2.x, r2.x, fmaf(r2.y, r2.y, nrm));
+    if constexpr (MODE != P1_NORM) {
+      rank1_pair<NT>(acc, sW, r2.x, m);
+      rank1_pair<NT>(acc, sW, r2.y, m + 1);
     }
   }
 
-  // ||r||^2: one FP64 atomic per warp
-  const R wn = warp_sum(nrm);
+  const float wn = warp_sum(nrm);
   if ((threadIdx.x & 31) == 0 && a.norm2 != nullptr) atomicAdd(a.norm2, (double)wn);
   if constexpr (MODE == P1_NORM) return;
 
-  C* out = reinterpret_cast<C*>(a.out);
+  float2* out = reinterpret_cast<float2*>(a.out);
   float amx = 0.f;
   if (valid) {
+    const size_t o = spec_index(a.sg, 0, s);
 #pragma unroll
-    for (int n = 0; n < P1_NT; ++n) {
-      if (n < N) {
-        out[spec_index(a.sg, n, s)] = mk(acc[n], (R)0);
-        amx = fmaxf(amx, fabsf((float)acc[n]));
+    for (int j = 0; j < NT / 2; ++j) {
+      if (2 * j < N) {
+        out[o + (size_t)(2 * j) * a.sg.specS] = make_float2(acc[j].x, 0.f);
+        amx = fmaxf(amx, fabsf(acc[j].x));
+      }
+      if (2 * j + 1 < N) {
+        out[o + (size_t)(2 * j + 1) * a.sg.specS] = make_float2(acc[j].y, 0.f);
+        amx = fmaxf(amx, fabsf(acc[j].y));
       }
     }
   }
@@ -278,50 +278,130 @@ __global__ void __launch_bounds__(P1_TB) k_pd1_fwd(const P1Fwd a) {
   }
 }
 
+// FP64 form (PREC 1): every step in FP64.
+template <int MODE, int NT>
+__global__ void __launch_bounds__(P1_TB) k_pd1_fwd_64(const P1Fwd a) {
+  __shared__ __align__(16) double sW[P1_NT * P1_NT];
+  if constexpr (MODE != P1_NORM) {
+    load_matrix<double>(sW, a.W, a.N);
+    __syncthreads();
+  }
+  const int N = a.N, S = a.S;
+  const int s = blockIdx.x * P1_TB + threadIdx.x;
+  const bool valid = s < S;
+  const Nb g = neighbours(a.st, valid ? s : 0);
+  const Stencil& st = a.st;
+  double acc[NT];
+#pragma unroll
+  for (int n = 0; n < NT; ++n) acc[n] = 0.0;
+  double nrm = 0.0, up = 0.0, kup = 0.0;
+#pragma unroll
+  for (int m = 0; m < NT; ++m) {
+    const bool on = valid && m < N;
+    double r;
+    if constexpr (MODE == P1_DIRECT) {
+      r = on ? __ldg(&a.b64[(size_t)m * S + s]) : 0.0;
+    } else {
+      const RowIn<double> x = load_row(a.b64, a.u64, g, s, (size_t)m * S, on);
+      double ku = st.kc * x.c;
+      ku = fma(st.kxl, x.l, ku);
+      ku = fma(st.kxu, x.r, ku);
+      ku = fma(st.kyl, x.d, ku);
+      ku = fma(st.kyu, x.u, ku);
+      double v = x.b - a.c1[m] * (x.c - up);
+      v = fma(-a.theta, ku, v);
+      v = fma(-(1.0 - a.theta), kup, v);
+      r = on ? v : 0.0;
+      up = x.c;
+      kup = ku;
+    }
+    nrm = fma(r, r, nrm);
+    if constexpr (MODE != P1_NORM) rank1_64<NT>(acc, sW, r, m);
+  }
+  const double wn = warp_sum(nrm);
+  if ((threadIdx.x & 31) == 0 && a.norm2 != nullptr) atomicAdd(a.norm2, wn);
+  if constexpr (MODE == P1_NORM) return;
+  if (valid) {
+    double2* out = reinterpret_cast<double2*>(a.out);
+    const size_t o = spec_index(a.sg, 0, s);
+#pragma unroll
+    for (int n = 0; n < NT; ++n)
+      if (n < N) out[o + (size_t)n * a.sg.specS] = make_double2(acc[n], 0.0);
+  }
+}
+
 // ---------------------------------------------------------------------------
 // Step (c), fused with the update: u = (V D~) S2 (P1_SET) or u += (V D~) S2
-// (P1_ADD); mixed: u is double-float, the transform FP32.
+// (P1_ADD).  All spectrum loads are issued first, then the rank-one updates.
+// Mixed: u is double-float, the transform FP32 (paired FMAs).
 // ---------------------------------------------------------------------------
-template <int PREC, int MODE>
-__global__ void __launch_bounds__(P1_TB) k_pd1_inv(const P1Inv a) {
-  using R = typename std::conditional<PREC == 0, float, double>::type;
-  using C = cplx_t<R>;
-  __shared__ __align__(16) R sV[P1_NT * P1_NT];
-  load_matrix<R>(sV, a.V, a.N);
+template <int MODE, int NT>
+__global__ void __launch_bounds__(P1_TB) k_pd1_inv_mixed(const P1Inv a) {
+  __shared__ __align__(16) float sV[P1_NT * P1_NT];
+  load_matrix<float>(sV, a.V, a.N);
   __syncthreads();
   const int N = a.N, S = a.S;
   const int s = blockIdx.x * P1_TB + threadIdx.x;
   if (s >= S) return;
-  const C* in = reinterpret_cast<const C*>(a.in);
-  R acc[P1_NT];
+  const float2* in = reinterpret_cast<const float2*>(a.in);
+  const size_t o = spec_index(a.sg, 0, s);
+  float z[NT];
 #pragma unroll
-  for (int n = 0; n < P1_NT; ++n) acc[n] = (R)0;
+  for (int m = 0; m < NT; ++m) z[m] = m < N ? in[o + (size_t)m * a.sg.specS].x : 0.f;
+  float2 acc[NT / 2];
 #pragma unroll
-  for (int m = 0; m < P1_NT; ++m) {
-    if (m < N) {
-      const R z = in[spec_index(a.sg, m, s)].x;
-      rank1_row<R>(acc, sV, z, m);
+  for (int j = 0; j < NT / 2; ++j) acc[j] = make_float2(0.f, 0.f);
+#pragma unroll
+  for (int m = 0; m < NT; ++m) rank1_pair<NT>(acc, sV, z[m], m);
+  bool bad = false;
+  float2 uo[NT];
+  if constexpr (MODE == P1_ADD) {
+#pragma unroll
+    for (int n = 0; n < NT; ++n) uo[n] = n < N ? a.Udf[(size_t)n * S + s] : make_float2(0.f, 0.f);
+  }
+#pragma unroll
+  for (int n = 0; n < NT; ++n) {
+    if (n < N) {
+      const float v = (n & 1) ? acc[n >> 1].y : acc[n >> 1].x;
+      bad |= !isfinite(v);
+      if constexpr (MODE == P1_SET) {
+        a.Udf[(size_t)n * S + s] = make_float2(v, 0.f);
+      } else {
+        df t = two_sum(uo[n].x, v);
+        t = fast_two_sum(t.hi, t.lo + uo[n].y);
+        a.Udf[(size_t)n * S + s] = make_float2(t.hi, t.lo);
+      }
     }
   }
+  if (bad && a.flag != nullptr) atomicOr(a.flag, 1);
+}
+
+template <int MODE, int NT>
+__global__ void __launch_bounds__(P1_TB) k_pd1_inv_64(const P1Inv a) {
+  __shared__ __align__(16) double sV[P1_NT * P1_NT];
+  load_matrix<double>(sV, a.V, a.N);
+  __syncthreads();
+  const int N = a.N, S = a.S;
+  const int s = blockIdx.x * P1_TB + threadIdx.x;
+  if (s >= S) return;
+  const double2* in = reinterpret_cast<const double2*>(a.in);
+  const size_t o = spec_index(a.sg, 0, s);
+  double z[NT];
+#pragma unroll
+  for (int m = 0; m < NT; ++m) z[m] = m < N ? in[o + (size_t)m * a.sg.specS].x : 0.0;
+  double acc[NT];
+#pragma unroll
+  for (int n = 0; n < NT; ++n) acc[n] = 0.0;
+#pragma unroll
+  for (int m = 0; m < NT; ++m) rank1_64<NT>(acc, sV, z[m], m);
   bool bad = false;
 #pragma unroll
-  for (int n = 0; n < P1_NT; ++n) {
+  for (int n = 0; n < NT; ++n) {
     if (n < N) {
-      const size_t i = (size_t)n * S + s;
       bad |= !isfinite(acc[n]);
-      if constexpr (PREC == 1) {
-        if constexpr (MODE == P1_SET) a.u64[i] = acc[n];
-        else a.u64[i] += acc[n];
-      } else {
-        if constexpr (MODE == P1_SET) {
-          a.Udf[i] = make_float2(acc[n], 0.f);
-        } else {
-          const float2 u = a.Udf[i];
-          df t = two_sum(u.x, acc[n]);
-          t = fast_two_sum(t.hi, t.lo + u.y);
-          a.Udf[i] = make_float2(t.hi, t.lo);
-        }
-      }
+      const size_t i = (size_t)n * S + s;
+      if constexpr (MODE == P1_SET) a.u64[i] = acc[n];
+      else a.u64[i] += acc[n];
     }
   }
   if (bad && a.flag != nullptr) atomicOr(a.flag, 1);
@@ -362,29 +442,46 @@ __global__ void k_pd1_rhs(const P1Fwd a, const double* u0, const double* f, doub
 
 int grid_of(int S) { return (S + P1_TB - 1) / P1_TB; }
 
-cudaError_t launch_pd1_fwd(const P1Fwd& a, int mode, bool fp64, cudaStream_t st) {
-  const dim3 grid(grid_of(a.S)), block(P1_TB);
+template <int NT>
+void fwd_nt(const P1Fwd& a, int mode, bool fp64, dim3 grid, cudaStream_t st) {
+  const dim3 block(P1_TB);
   if (fp64) {
-    if (mode == P1_DIRECT) k_pd1_fwd<1, P1_DIRECT><<<grid, block, 0, st>>>(a);
-    else if (mode == P1_RESID) k_pd1_fwd<1, P1_RESID><<<grid, block, 0, st>>>(a);
-    else k_pd1_fwd<1, P1_NORM><<<grid, block, 0, st>>>(a);
+    if (mode == P1_DIRECT) k_pd1_fwd_64<P1_DIRECT, NT><<<grid, block, 0, st>>>(a);
+    else if (mode == P1_RESID) k_pd1_fwd_64<P1_RESID, NT><<<grid, block, 0, st>>>(a);
+    else k_pd1_fwd_64<P1_NORM, NT><<<grid, block, 0, st>>>(a);
   } else {
-    if (mode == P1_DIRECT) k_pd1_fwd<0, P1_DIRECT><<<grid, block, 0, st>>>(a);
-    else if (mode == P1_RESID) k_pd1_fwd<0, P1_RESID><<<grid, block, 0, st>>>(a);
-    else k_pd1_fwd<0, P1_NORM><<<grid, block, 0, st>>>(a);
+    if (mode == P1_DIRECT) k_pd1_fwd_mixed<P1_DIRECT, NT><<<grid, block, 0, st>>>(a);
+    else if (mode == P1_RESID) k_pd1_fwd_mixed<P1_RESID, NT><<<grid, block, 0, st>>>(a);
+    else k_pd1_fwd_mixed<P1_NORM, NT><<<grid, block, 0, st>>>(a);
   }
+}
+
+template <int NT>
+void inv_nt(const P1Inv& a, int mode, bool fp64, dim3 grid, cudaStream_t st) {
+  const dim3 block(P1_TB);
+  if (fp64) {
+    if (mode == P1_SET) k_pd1_inv_64<P1_SET, NT><<<grid, block, 0, st>>>(a);
+    else k_pd1_inv_64<P1_ADD, NT><<<grid, block, 0, st>>>(a);
+  } else {
+    if (mode == P1_SET) k_pd1_inv_mixed<P1_SET, NT><<<grid, block, 0, st>>>(a);
+    else k_pd1_inv_mixed<P1_ADD, NT><<<grid, block, 0, st>>>(a);
+  }
+}
+
+// register arrays sized for the window: 8, 16 or 32 rows
+cudaError_t launch_pd1_fwd(const P1Fwd& a, int mode, bool fp64, cudaStream_t st) {
+  const dim3 grid(grid_of(a.S));
+  if (a.N <= 8) fwd_nt<8>(a, mode, fp64, grid, st);
+  else if (a.N <= 16) fwd_nt<16>(a, mode, fp64, grid, st);
+  else fwd_nt<32>(a, mode, fp64, grid, st);
   return cudaGetLastError();
 }
 
 cudaError_t launch_pd1_inv(const P1Inv& a, int mode, bool fp64, cudaStream_t st) {
-  const dim3 grid(grid_of(a.S)), block(P1_TB);
-  if (fp64) {
-    if (mode == P1_SET) k_pd1_inv<1, P1_SET><<<grid, block, 0, st>>>(a);
-    else k_pd1_inv<1, P1_ADD><<<grid, block, 0, st>>>(a);
-  } else {
-    if (mode == P1_SET) k_pd1_inv<0, P1_SET><<<grid, block, 0, st>>>(a);
-    else k_pd1_inv<0, P1_ADD><<<grid, block, 0, st>>>(a);
-  }
+  const dim3 grid(grid_of(a.S));
+  if (a.N <= 8) inv_nt<8>(a, mode, fp64, grid, st);
+  else if (a.N <= 16) inv_nt<16>(a, mode, fp64, grid, st);
+  else inv_nt<32>(a, mode, fp64, grid, st);
   return cudaGetLastError();
 }
 
@@ -711,6 +808,53 @@ pd_status pd1_solve(pd1_plan* q, const double* b, double* u, double tol, int max
   if (max_refine > 0 && tol > 0.0 && !(rel <= tol)) {
     return p1_err(q, PD_ERR_NOT_CONVERGED, "refinement sweeps did not reach the tolerance");
   }
+  return PD_OK;
+}
+
+pd_status pd1_profile_sweep(pd1_plan* q, const double* b, double* u, int reps, float* ms) {
+  if (!q || !b || !u || !ms || reps < 1) return PD_ERR_ARG;
+  pd_plan* p = q->sp;
+  cudaStream_t st = p->stream;
+  const bool fp64 = q->fp64;
+  P1Fwd fa = fwd_args(q);
+  fa.b64 = b;
+  fa.u64 = u;
+  fa.norm2 = q->dnorm;
+  P1Inv ia = inv_args(q);
+  ia.u64 = u;
+  // a state to sweep from: the direct solve
+  P1LK(launch_pd1_fwd(fa, P1_DIRECT, fp64, st));
+  {
+    const pd_status s = step_b(q);
+    if (s != PD_OK) return s;
+  }
+  P1LK(launch_pd1_inv(ia, P1_SET, fp64, st));
+  fa.norm2 = q->dnorm + 1;
+  cudaEvent_t ev[4];
+  for (int i = 0; i < 4; ++i) P1CU(cudaEventCreate(&ev[i]));
+  double acc[3] = {0, 0, 0};
+  for (int r = 0; r < reps; ++r) {
+    P1CU(cudaEventRecord(ev[0], st));
+    P1LK(launch_pd1_fwd(fa, P1_RESID, fp64, st));
+    P1CU(cudaEventRecord(ev[1], st));
+    const pd_status s = step_b(q);
+    if (s != PD_OK) return s;
+    P1CU(cudaEventRecord(ev[2], st));
+    P1LK(launch_pd1_inv(ia, P1_ADD, fp64, st));
+    P1CU(cudaEventRecord(ev[3], st));
+    P1CU(cudaEventSynchronize(ev[3]));
+    for (int i = 0; i < 3; ++i) {
+      float t = 0.f;
+      P1CU(cudaEventElapsedTime(&t, ev[i], ev[i + 1]));
+      acc[i] += t;
+    }
+  }
+  for (int i = 0; i < 4; ++i) cudaEventDestroy(ev[i]);
+  for (int i = 0; i < 3; ++i) ms[i] = (float)(acc[i] / reps);
+  if (!fp64) {
+    P1LK(launch_from_df(p->Udf, u, (size_t)q->nt * p->S, st));
+  }
+  P1CU(cudaStreamSynchronize(st));
   return PD_OK;
 }
 

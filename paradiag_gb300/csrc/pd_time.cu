@@ -277,59 +277,8 @@ PD_D void acc_add_prod(Acc& A, dfc k, float uh, float ul) {
 }
 PD_D df acc_val(const Acc& A) { return fast_two_sum(A.s, A.e); }
 
-// ---- the same compensated arithmetic on two independent values at once (the
-// lanes of a float2), with the paired FP32 instructions of sm_100+
-PD_D float2 f2add(float2 a, float2 b) { return __fadd2_rn(a, b); }
-PD_D float2 f2mul(float2 a, float2 b) { return __fmul2_rn(a, b); }
-PD_D float2 f2fma(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
-PD_D float2 f2sub(float2 a, float2 b) {
-  unsigned long long x = *reinterpret_cast<unsigned long long*>(&a);
-  unsigned long long y = *reinterpret_cast<unsigned long long*>(&b);
-  unsigned long long d;
-  asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(x), "l"(y));
-  return *reinterpret_cast<float2*>(&d);
-}
-struct DF2 {    // two double-float values: (hi_A, hi_B), (lo_A, lo_B)
-  float2 hi, lo;
-};
-struct Acc2 {   // two compensated sums
-  float2 s, e;
-};
-PD_D DF2 df2_pack(float2 a, float2 b) { return DF2{make_float2(a.x, b.x), make_float2(a.y, b.y)}; }
-// A += h + l (two-sum on the high parts)
-PD_D void acc2_add(Acc2& A, float2 h, float2 l) {
-  const float2 t = f2add(A.s, h);
-  const float2 bb = f2sub(t, A.s);
-  const float2 err = f2add(f2sub(A.s, f2sub(t, bb)), f2sub(h, bb));
-  A.s = t;
-  A.e = f2add(A.e, f2add(err, l));
-}
-// A -= h + l
-PD_D void acc2_sub(Acc2& A, float2 h, float2 l) {
-  const float2 t = f2sub(A.s, h);
-  const float2 bb = f2sub(t, A.s);
-  const float2 err = f2sub(f2sub(A.s, f2sub(t, bb)), f2add(h, bb));
-  A.s = t;
-  A.e = f2sub(f2add(A.e, err), l);
-}
-// coefficient k = kh + kl broadcast to both lanes, with its negation
-struct K2 {
-  float2 h, nh, nl;
-};
 PD_D K2 k2_of(dfc k) {
   return K2{make_float2(k.hi, k.hi), make_float2(-k.hi, -k.hi), make_float2(-k.lo, -k.lo)};
-}
-// A += k u (two-product of the high parts, the cross terms into the error)
-PD_D void acc2_add_prod(Acc2& A, const K2& k, const DF2& u) {
-  const float2 p = f2mul(u.hi, k.h);
-  float2 npe = f2fma(u.hi, k.nh, p);   // p - u.hi k.hi = -(rounding error of p)
-  npe = f2fma(u.hi, k.nl, npe);
-  npe = f2fma(u.lo, k.nh, npe);
-  const float2 t = f2add(A.s, p);
-  const float2 bb = f2sub(t, A.s);
-  const float2 err = f2add(f2sub(A.s, f2sub(t, bb)), f2sub(p, bb));
-  A.s = t;
-  A.e = f2sub(f2add(A.e, err), npe);
 }
 
 // Global loads of one time row at this thread's column (centre, segment-edge
