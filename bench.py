@@ -232,8 +232,10 @@ def batched_leg(pd, torch, dev, args):
     return out
 
 
-# DRAM bytes per launch of the ParaDiag-I kernels from ncu (None until captured)
-PD1_NCU_TRAFFIC = {}
+# DRAM bytes (read + write) per launch of the ParaDiag-I mixed kernels from the ncu
+# captures summarised in profiles/pd1_ade2d_be_255x1023x32_kernels.md; an entry goes
+# back to absent whenever its kernel changes.
+PD1_NCU_TRAFFIC = {("mixed", "pd1_resid_step_a"): 169.9e6, ("mixed", "pd1_step_c_update"): 155.0e6}
 
 
 def pd1_bytes_per_unknown(fp64):
