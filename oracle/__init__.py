@@ -23,6 +23,10 @@ Modules
   paradiag1     O6: ParaDiag-I with geometric time steps (Section 2.1.1):
                 closed-form V, V^{-1}, the column scaling D~, the three steps
                 of eq. 2.7, and the exact variable-step solution by stepping.
+  hybrid        O7: ParaDiag-I with the hybrid midpoint + backward-Euler
+                discretisation (Section 2.1.2): B, the Newton roots of the
+                Chebyshev characteristic equation, the closed-form V, the
+                three-step solve and the exact solution by a sparse LU.
 
 Every function is pinned by a test in tests/test_oracle_*.py against a
 closed form, an invariant, a bound of the paper, a worked example the paper

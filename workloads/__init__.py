@@ -14,7 +14,8 @@ the output times 2^-53.
 Problem families (the paper's model problems):
   * advection-diffusion u_t = nu*Lap(u) - a.grad(u) + f  (Section 2, eq. 2.1 and
     eq. 2.14), theta-method in time (eq. 2.4), with uniform steps or with the
-    geometrically increasing steps of ParaDiag-I (Section 2.1.1, eq. 2.8);
+    geometrically increasing steps of ParaDiag-I (Section 2.1.1, eq. 2.8), or the
+    hybrid midpoint + backward-Euler discretisation (Section 2.1.2, eq. neq2.9a);
   * wave equation u_tt = Lap(u) + f (Section 3, eq. 3.1), implicit leap-frog
     in time (eq. 3.2b).
 """
@@ -142,6 +143,20 @@ class GeometricProblem:
     @property
     def theta_eff(self) -> float:
         return 1.0 if self.scheme == BE else 0.5
+
+
+@dataclasses.dataclass(frozen=True)
+class HybridProblem:
+    """All-at-once system of the hybrid time discretisation of Section 2.1.2:
+    explicit midpoint steps for n = 1..Nt-1 and one backward-Euler step at the
+    end, uniform step ``dt`` (eq. neq2.9a)."""
+    space: Space
+    nt: int
+    dt: float
+
+    @property
+    def unknowns(self) -> int:
+        return self.space.size * self.nt
 
 
 @dataclasses.dataclass
@@ -289,6 +304,29 @@ def pd1_ade2d(nx=255, ny=255, nt=32, tau=1.16, dt_last=0.05, nu=1e-3, ax=1.0, ay
     return Workload(name, pb, u0, None, None, seed, extra={"center": (x0, y0)})
 
 
+def hybrid_ade1d(nx=256, nt=64, T=1.0, nu=1e-3, seed=SEED_BASE + 7,
+                  name="hybrid_ade1d") -> Workload:
+    """The hybrid ParaDiag-I example of Section 2.1.2: eq. 2.1 (periodic on (-1, 1),
+    u_t - nu u_xx + u_x = 0, u0 = exp(-30 x^2)) with dx = 1/128 (nx = 256), the
+    midpoint + backward-Euler discretisation with nt uniform steps over [0, T]."""
+    sp = Space(dim=1, nx=nx, nu=nu, ax=1.0, bc_x=PERIODIC, lx=2.0)
+    pb = HybridProblem(space=sp, nt=nt, dt=T / nt)
+    x = sp.xs() - 1.0
+    return Workload(name, pb, np.exp(-30.0 * x * x), None, None, seed)
+
+
+def hybrid_ade2d(nx=255, ny=255, nt=256, T=1.0, nu=1e-3, ax=1.0, ay=0.5, seed=SEED_BASE + 8,
+                 name="hybrid_ade2d") -> Workload:
+    """The hybrid ParaDiag-I discretisation on the 2D grid of ``ade2d`` (x periodic,
+    y Dirichlet, seeded Gaussian bump, zero source), nt uniform steps over [0, T]."""
+    sp = Space(dim=2, nx=nx, ny=ny, nu=nu, ax=ax, ay=ay, bc_x=PERIODIC, bc_y=DIRICHLET)
+    pb = HybridProblem(space=sp, nt=nt, dt=T / nt)
+    x0, y0 = uniform(seed, 2, 0.3, 0.7)
+    X, Y = sp.mesh()
+    u0 = np.exp(-20.0 * ((X - x0) ** 2 + (Y - y0) ** 2)).reshape(-1)
+    return Workload(name, pb, u0, None, None, seed, extra={"center": (x0, y0)})
+
+
 def named(name: str, **kw) -> Workload:
     """The five named workloads at their full sizes (keyword overrides allowed)."""
     table = {
@@ -298,6 +336,8 @@ def named(name: str, **kw) -> Workload:
         "wave1d_leapfrog": lambda: wave1d(**kw),
         "pd1_ade1d": lambda: pd1_ade1d(**kw),
         "pd1_ade2d": lambda: pd1_ade2d(**kw),
+        "hybrid_ade1d": lambda: hybrid_ade1d(**kw),
+        "hybrid_ade2d": lambda: hybrid_ade2d(**kw),
     }
     return table[name]()
 
@@ -305,6 +345,10 @@ def named(name: str, **kw) -> Workload:
 def workload_summary(w: Workload) -> dict:
     p = w.problem
     s = p.space
+    if isinstance(p, HybridProblem):
+        return {"name": w.name, "dim": s.dim, "nx": s.nx, "ny": s.ny if s.dim == 2 else 1,
+                "nt": p.nt, "dt": p.dt, "scheme": "midpoint + backward Euler (hybrid)",
+                "nu": s.nu, "ax": s.ax, "ay": s.ay, "unknowns": p.unknowns, "seed": w.seed}
     if isinstance(p, GeometricProblem):
         return {"name": w.name, "dim": s.dim, "nx": s.nx, "ny": s.ny if s.dim == 2 else 1,
                 "nt": p.nt, "dt_last": p.dt_last, "tau": p.tau, "scheme": SCHEME_NAMES[p.scheme],
