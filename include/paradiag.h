@@ -313,6 +313,60 @@ PD_API pd_status pd1_launches(const pd1_plan* plan, unsigned long long* count);
 PD_API pd_status pd1_workspace(const pd1_plan* plan, unsigned long long* bytes);
 PD_API const char* pd1_last_error(const pd1_plan* plan);
 
+/* ---------------------------------------------------------------------------
+ * ParaDiag-I with the hybrid time discretisation (Section 2.1.2): explicit
+ * midpoint steps n = 1..nt-1 and one backward-Euler step at the end, uniform
+ * step dt (eq. neq2.9a).  All-at-once system (eq. neq2.9b, neq2.9c):
+ *   (B (x) I + I (x) K) u = b,  B = (1/dt) tridiag(-1/2, 0, 1/2), last row
+ *   (..., -1, 1),
+ * diagonalised by the theorem of Section 2.1.2: eigenvalues i x_n / dt (the
+ * printed i dt x_n read with B's 1/dt factor), x_n the roots of
+ * P2_{nt-1}(x) - i P1_{nt}(x), eigenvectors v_{n,l} = i^l P2_l(x_n).
+ * Layout of u and b as for pd_plan: [nt][S] device FP64, caller-owned.
+ * --------------------------------------------------------------------------- */
+typedef struct pdh_plan pdh_plan;
+
+/* Plan for nt uniform steps of size dt (1 <= nt <= 4096; PD_ERR_UNSUPPORTED
+ * above).  precision PD_FP64: steps (a)-(c) and the residual in FP64;
+ * PD_MIXED: steps (a)-(c) in FP32 (the tensor-core x-transform in 2D), the
+ * residual of the refinement sweeps in double-float.  sp: as for
+ * pd_plan_create.  stream: cudaStream_t (NULL: the default stream).  Finds
+ * the eigenvalues and the eigenvector matrices on the host (O(nt^2) work) and
+ * allocates all device memory the solves need. */
+PD_API pd_status pdh_plan_create(const pd_space* sp, int nt, double dt, int precision,
+                                 void* stream, pdh_plan** out);
+PD_API pd_status pdh_plan_destroy(pdh_plan* plan);
+
+/* lam[2n], lam[2n+1]: real and imaginary part of the eigenvalue i x_n / dt of
+ * B, n = 0..nt-1 (host array of 2 nt doubles). */
+PD_API pd_status pdh_eigenvalues(const pdh_plan* plan, double* lam);
+
+/* *cond: ||V||_F ||V^{-1}||_F for the eigenvector matrix the plan uses. */
+PD_API pd_status pdh_condition(const pdh_plan* plan, double* cond);
+
+/* y = A u (eq. neq2.9b), FP64. */
+PD_API pd_status pdh_apply_A(pdh_plan* plan, const double* u, double* y);
+
+/* b_n = f(t_n), n = 1..nt, plus u0 / (2 dt) in the first row (eq. neq2.9c).
+ * u0: [S]; f: [nt+1][S] values at t_0..t_nt, or NULL for f = 0. */
+PD_API pd_status pdh_build_rhs(pdh_plan* plan, const double* u0, const double* f, double* b);
+
+/* u = A^{-1} b: the direct solve of eq. 2.7 with the eigendecomposition above
+ * (u on entry is ignored), then up to max_refine sweeps
+ * u <- u + P^{-1}(b - A u), stopping early once ||b - A u||_2 <= tol ||b||_2.
+ * Arguments, return values and synchronisation as for pd1_solve. */
+PD_API pd_status pdh_solve(pdh_plan* plan, const double* b, double* u, double tol,
+                           int max_refine, int* refinements, double* relres);
+
+/* Measurement aid (no paper counterpart): from the direct solve of b, reps
+ * refinement sweeps timed with CUDA events on the plan's stream; ms[0] = the
+ * residual, ms[1] = step (a) (dense time transform), ms[2] = step (b),
+ * ms[3] = step (c) with the update (averages in milliseconds). */
+PD_API pd_status pdh_profile_sweep(pdh_plan* plan, const double* b, double* u, int reps,
+                                   float* ms);
+PD_API pd_status pdh_launches(const pdh_plan* plan, unsigned long long* count);
+PD_API const char* pdh_last_error(const pdh_plan* plan);
+
 PD_API const char* pd_status_string(pd_status s);
 PD_API const char* pd_last_error(const pd_plan* plan);
 

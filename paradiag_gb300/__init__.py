@@ -93,6 +93,17 @@ _SIGS = {
     "pd1_profile_sweep": (ctypes.c_int, [_P, _P, _P, ctypes.c_int, ctypes.POINTER(ctypes.c_float)]),
     "pd1_workspace": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_ulonglong)]),
     "pd1_last_error": (ctypes.c_char_p, [_P]),
+    "pdh_plan_create": (ctypes.c_int, [ctypes.POINTER(pd_space), ctypes.c_int, ctypes.c_double,
+                                       ctypes.c_int, _P, ctypes.POINTER(_P)]),
+    "pdh_plan_destroy": (ctypes.c_int, [_P]),
+    "pdh_eigenvalues": (ctypes.c_int, [_P, _D]),
+    "pdh_condition": (ctypes.c_int, [_P, _D]),
+    "pdh_apply_A": (ctypes.c_int, [_P, _P, _P]),
+    "pdh_build_rhs": (ctypes.c_int, [_P, _P, _P, _P]),
+    "pdh_solve": (ctypes.c_int, [_P, _P, _P, ctypes.c_double, ctypes.c_int, _I, _D]),
+    "pdh_profile_sweep": (ctypes.c_int, [_P, _P, _P, ctypes.c_int, ctypes.POINTER(ctypes.c_float)]),
+    "pdh_launches": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_ulonglong)]),
+    "pdh_last_error": (ctypes.c_char_p, [_P]),
     "pd_status_string": (ctypes.c_char_p, [ctypes.c_int]),
     "pd_last_error": (ctypes.c_char_p, [_P]),
 }
@@ -330,6 +341,60 @@ def pd1_workspace(plan):
 
 def pd1_last_error(plan) -> str:
     return load().pd1_last_error(plan).decode()
+
+
+def pdh_plan_create(space: pd_space, nt, dt, precision, stream):
+    out = _P()
+    st = load().pdh_plan_create(ctypes.byref(space), nt, dt, precision, _P(stream),
+                                ctypes.byref(out))
+    return st, out.value
+
+
+def pdh_plan_destroy(plan):
+    return load().pdh_plan_destroy(plan)
+
+
+def pdh_eigenvalues(plan, nt):
+    buf = (ctypes.c_double * (2 * nt))()
+    st = load().pdh_eigenvalues(plan, buf)
+    return st, [complex(buf[2 * i], buf[2 * i + 1]) for i in range(nt)]
+
+
+def pdh_condition(plan):
+    v = ctypes.c_double(0.0)
+    st = load().pdh_condition(plan, ctypes.byref(v))
+    return st, v.value
+
+
+def pdh_apply_A(plan, u, y):
+    return load().pdh_apply_A(plan, u, y)
+
+
+def pdh_build_rhs(plan, u0, f, b):
+    return load().pdh_build_rhs(plan, u0, f, b)
+
+
+def pdh_solve(plan, b, u, tol, max_refine):
+    it = ctypes.c_int(0)
+    rr = ctypes.c_double(0.0)
+    st = load().pdh_solve(plan, b, u, tol, max_refine, ctypes.byref(it), ctypes.byref(rr))
+    return st, it.value, rr.value
+
+
+def pdh_profile_sweep(plan, b, u, reps):
+    ms = (ctypes.c_float * 4)()
+    st = load().pdh_profile_sweep(plan, b, u, reps, ms)
+    return st, list(ms)
+
+
+def pdh_launches(plan):
+    v = ctypes.c_ulonglong(0)
+    st = load().pdh_launches(plan, ctypes.byref(v))
+    return st, v.value
+
+
+def pdh_last_error(plan) -> str:
+    return load().pdh_last_error(plan).decode()
 
 
 def _space_of(space) -> pd_space:
@@ -583,6 +648,99 @@ class Plan1:
         return u, it, rel
 
 
+class PlanHybrid:
+    """A plan for ParaDiag-I with the hybrid midpoint + backward-Euler time
+    discretisation (Section 2.1.2) on the current CUDA device and stream: nt
+    uniform steps of size dt.  ``space`` as for Plan; tensors are CUDA float64
+    of shape (nt, S)."""
+
+    def __init__(self, space, nt, dt, precision=PD_FP64, stream=None):
+        import torch
+        self.space = _space_of(space)
+        self.nt, self.dt, self.precision = int(nt), float(dt), int(precision)
+        self.S = self.space.nx * (self.space.ny if self.space.dim == 2 else 1)
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        st, h = pdh_plan_create(self.space, self.nt, self.dt, self.precision,
+                                self.stream.cuda_stream)
+        if st != PD_OK:
+            raise PDError(st, "pdh_plan_create")
+        self._h = h
+
+    @property
+    def handle(self):
+        return self._h
+
+    def close(self):
+        if getattr(self, "_h", None):
+            pdh_plan_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _check(self, st, what):
+        if st != PD_OK:
+            raise PDError(st, f"{what}: {pdh_last_error(self._h)}")
+
+    def _check_t(self, t, n=None):
+        import torch
+        n = self.nt * self.S if n is None else n
+        if not (t.is_cuda and t.dtype == torch.float64 and t.is_contiguous() and t.numel() == n):
+            raise ValueError(f"expected a contiguous CUDA float64 tensor with {n} elements")
+
+    def eigenvalues(self):
+        st, v = pdh_eigenvalues(self._h, self.nt)
+        self._check(st, "pdh_eigenvalues")
+        return v
+
+    def condition(self):
+        st, v = pdh_condition(self._h)
+        self._check(st, "pdh_condition")
+        return v
+
+    def launches(self):
+        st, v = pdh_launches(self._h)
+        self._check(st, "pdh_launches")
+        return v
+
+    def apply_A(self, u, y=None):
+        import torch
+        self._check_t(u)
+        y = torch.empty_like(u) if y is None else y
+        self._check(pdh_apply_A(self._h, _ptr(u), _ptr(y)), "pdh_apply_A")
+        return y
+
+    def build_rhs(self, u0, f=None, b=None):
+        import torch
+        self._check_t(u0, self.S)
+        if f is not None:
+            self._check_t(f, (self.nt + 1) * self.S)
+        b = torch.empty((self.nt, self.S), dtype=torch.float64, device=u0.device) if b is None else b
+        self._check(pdh_build_rhs(self._h, _ptr(u0), _ptr(f), _ptr(b)), "pdh_build_rhs")
+        return b
+
+    def profile_sweep(self, b, u, reps=5):
+        """Average ms of [residual, step (a), step (b), step (c) + update]."""
+        self._check_t(b); self._check_t(u)
+        st, ms = pdh_profile_sweep(self._h, _ptr(b), _ptr(u), reps)
+        self._check(st, "pdh_profile_sweep")
+        return ms
+
+    def solve(self, b, u=None, tol=0.0, max_refine=0, allow_not_converged=False):
+        """u = A^{-1} b; returns (u, refinement sweeps, relative residual)."""
+        import torch
+        self._check_t(b)
+        u = torch.empty_like(b) if u is None else u
+        self._check_t(u)
+        st, it, rel = pdh_solve(self._h, _ptr(b), _ptr(u), tol, max_refine)
+        if not (st == PD_OK or (allow_not_converged and st == PD_ERR_NOT_CONVERGED)):
+            self._check(st, "pdh_solve")
+        return u, it, rel
+
+
 class Batch:
     """Many independent 1D problems solved together (packed FP64 arrays).
 
@@ -687,6 +845,6 @@ class _Lazy:
 
 PDSolve = _Lazy()
 
-__all__ = ["build", "lib_path", "load", "Plan", "Plan1", "Batch", "PDSolve", "PDError", "pd_space",
+__all__ = ["build", "lib_path", "load", "Plan", "Plan1", "PlanHybrid", "Batch", "PDSolve", "PDError", "pd_space",
            "pd_problem",
            "exported_symbols"] + [k for k in _SIGS]

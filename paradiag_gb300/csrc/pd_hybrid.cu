@@ -1,0 +1,833 @@
+// ParaDiag-I with the hybrid time discretisation (Section 2.1.2): explicit
+// midpoint steps for n = 1..Nt-1 and one backward-Euler step at the end, on a
+// uniform step dt (eq. neq2.9a).  The all-at-once matrix is B (x) I + I (x) K
+// with B = (1/dt) tridiag(-1/2, 0, 1/2) and last row (..., -1, 1)
+// (eq. neq2.9c).  The theorem of Section 2.1.2 diagonalises B = V D V^{-1}:
+// lambda_n = i x_n / dt with x_n the roots of P2_{Nt-1}(x) - i P1_{Nt}(x)
+// (Chebyshev polynomials of the second and first kind), and
+// V[l][n] = i^l P2_l(x_n).  The solve is the three steps of eq. 2.7.
+//
+// Host side (plan creation, FP64):
+//   roots: with x = cos(theta) the characteristic equation is
+//   tan(Nt theta) = i sin(theta); the fixed point
+//   theta <- (k pi + i atanh(sin theta)) / Nt, k = 1..Nt-1, gives Nt-1 roots,
+//   the last one follows from trace(dt B) = 1 = sum_n i x_n, and Newton steps
+//   on the characteristic equation polish all of them;
+//   V^{-1}: row n is the left eigenvector w_n^T / (w_n^T v_n), with
+//   w_{l,n} = (-i)^l P2_l(x_n) for l <= Nt-2 and
+//   w_{Nt-1,n} = w_{Nt-3,n}/2 - i x_n w_{Nt-2,n} (the transposed recurrence of
+//   B; its last row is the characteristic equation).
+// B is real, so the roots come in pairs x, -conj(x) (eigenvalues lambda,
+// conj(lambda)) and, for odd Nt, one self-conjugate root.  For real data only
+// one member of each pair is solved: Nh = ceil(Nt/2) spectrum rows, and
+// u = sum_{k in half} w_k Re(v_k S2_k), w_k = 2 for a pair, 1 otherwise.
+//
+// Device side: steps (a) and (c) are dense contractions over the time index
+// (2 Nh x Nt and Nt x 2 Nh real forms of V^{-1} and V), about 2 Nt FMAs per
+// space-time unknown each, computed by a register-tiled SIMT GEMM (FP32 on the
+// mixed path, FP64 otherwise); step (b) is the shifted spatial solve of the
+// ParaDiag-II path (x-eigentransform in 2D, tridiagonal solver) with the
+// complex shifts lambda_k.  Optional refinement sweeps use the residual
+// b - A u in double-float (mixed) or FP64.
+#include <algorithm>
+#include <cmath>
+#include <complex>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <type_traits>
+#include <vector>
+
+#include "pd_plan.h"
+
+using cdh = std::complex<double>;
+
+namespace {
+
+constexpr int HG_BM = 64, HG_BN = 128, HG_BK = 16, HG_TB = 256;
+constexpr int HR_TB = 128;
+
+enum { HY_DIRECT = 0, HY_RESID = 1, HY_NORM = 2 };
+enum { HY_FWD = 0, HY_INV_SET = 1, HY_INV_ADD = 2 };
+
+// GEMM C[M][N] = A[M][K] . B[K][N] over spatial points N = S.
+//   HY_FWD:  B = the residual r ([K = Nt][S] real), C rows (2k, 2k+1) are the
+//            real and imaginary parts of spectrum row k (written as complex);
+//   HY_INV_*: B rows (2k + c) are component c of spectrum row k, C = u
+//            ([M = Nt][S], set or added; mixed: double-float iterate).
+struct HGemm {
+  int M, K, S;
+  SpecGeom sg;
+  const void* A;        // [M][K] row-major (float / double)
+  const void* r;        // HY_FWD: residual (float / double) [Nt][S]
+  const void* spec;     // HY_INV: spectrum rows (complex)
+  void* out;            // HY_FWD: spectrum rows (complex)
+  double* u64;          // HY_INV, FP64
+  float2* Udf;          // HY_INV, mixed
+  unsigned* amax;       // HY_FWD, mixed + tensor-core x-transform
+  unsigned* amax_reset;
+  int* flag;
+};
+
+template <typename R, int MODE>
+__global__ void __launch_bounds__(HG_TB) k_hy_gemm(const HGemm a) {
+  __shared__ __align__(16) R As[HG_BK][HG_BM];
+  __shared__ __align__(16) R Bs[HG_BK][HG_BN];
+  const int tid = threadIdx.x;
+  const int tx = tid & 31, ty = tid >> 5;       // 32 x 8 threads, 4 x 8 outputs each
+  const int n0 = blockIdx.x * HG_BN, m0 = blockIdx.y * HG_BM;
+  const int M = a.M, K = a.K, S = a.S;
+  const R* A = reinterpret_cast<const R*>(a.A);
+  using C = cplx_t<R>;
+
+  R acc[8][4];
+#pragma unroll
+  for (int i = 0; i < 8; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) acc[i][j] = (R)0;
+
+  for (int k0 = 0; k0 < K; k0 += HG_BK) {
+    // A tile: BM x BK, stored transposed (As[kk][m])
+#pragma unroll
+    for (int q = 0; q < (HG_BM * HG_BK) / HG_TB; ++q) {
+      const int e = tid + q * HG_TB;
+      const int mm = e / HG_BK, kk = e % HG_BK;
+      const int m = m0 + mm, k = k0 + kk;
+      As[kk][mm] = (m < M && k < K) ? A[(size_t)m * K + k] : (R)0;
+    }
+    // B tile: BK x BN
+    if constexpr (MODE == HY_FWD) {
+      const R* rr = reinterpret_cast<const R*>(a.r);
+#pragma unroll
+      for (int q = 0; q < (HG_BK * HG_BN) / HG_TB; ++q) {
+        const int e = tid + q * HG_TB;
+        const int kk = e / HG_BN, nn = e % HG_BN;
+        const int k = k0 + kk, n = n0 + nn;
+        Bs[kk][nn] = (k < K && n < S) ? rr[(size_t)k * S + n] : (R)0;
+      }
+    } else {
+      // rows (2j, 2j+1) of the tile from complex spectrum row (k0/2 + j)
+      const C* sp = reinterpret_cast<const C*>(a.spec);
+#pragma unroll
+      for (int q = 0; q < (HG_BK / 2 * HG_BN) / HG_TB; ++q) {
+        const int e = tid + q * HG_TB;
+        const int j = e / HG_BN, nn = e % HG_BN;
+        const int kr = (k0 >> 1) + j, n = n0 + nn;
+        C v = czero<C>();
+        if (2 * kr < K && n < S) v = sp[spec_index(a.sg, kr, n)];
+        Bs[2 * j][nn] = v.x;
+        Bs[2 * j + 1][nn] = v.y;
+      }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < HG_BK; ++kk) {
+      R av[8], bv[4];
+#pragma unroll
+      for (int i = 0; i < 8; ++i) av[i] = As[kk][ty * 8 + i];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) bv[j] = Bs[kk][tx * 4 + j];
+#pragma unroll
+      for (int i = 0; i < 8; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] = fma(av[i], bv[j], acc[i][j]);
+    }
+    __syncthreads();
+  }
+
+  if constexpr (MODE == HY_FWD) {
+    C* out = reinterpret_cast<C*>(a.out);
+    float amx = 0.f;
+#pragma unroll
+    for (int i = 0; i < 8; i += 2) {
+      const int m = m0 + ty * 8 + i;          // even: real part of spectrum row m/2
+      if (m >= M) continue;
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const int n = n0 + tx * 4 + j;
+        if (n >= S) continue;
+        out[spec_index(a.sg, m >> 1, n)] = mk(acc[i][j], acc[i + 1][j]);
+        amx = fmaxf(amx, fmaxf(fabsf((float)acc[i][j]), fabsf((float)acc[i + 1][j])));
+      }
+    }
+    if (a.amax != nullptr) {
+      for (int o = 16; o > 0; o >>= 1) amx = fmaxf(amx, __shfl_xor_sync(0xffffffffu, amx, o));
+      if ((tid & 31) == 0) atomicMax(a.amax, __float_as_uint(amx));
+      if (blockIdx.x == 0 && blockIdx.y == 0 && tid == 0 && a.amax_reset) *a.amax_reset = 0u;
+    }
+  } else {
+    bool bad = false;
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+      const int m = m0 + ty * 8 + i;
+      if (m >= M) continue;
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const int n = n0 + tx * 4 + j;
+        if (n >= S) continue;
+        const size_t idx = (size_t)m * S + n;
+        const R v = acc[i][j];
+        bad |= !isfinite(v);
+        if constexpr (std::is_same<R, double>::value) {
+          if constexpr (MODE == HY_INV_SET) a.u64[idx] = v;
+          else a.u64[idx] += v;
+        } else {
+          if constexpr (MODE == HY_INV_SET) {
+            a.Udf[idx] = make_float2(v, 0.f);
+          } else {
+            const float2 u = a.Udf[idx];
+            df t = two_sum(u.x, v);
+            t = fast_two_sum(t.hi, t.lo + u.y);
+            a.Udf[idx] = make_float2(t.hi, t.lo);
+          }
+        }
+      }
+    }
+    if (bad && a.flag != nullptr) atomicOr(a.flag, 1);
+  }
+}
+
+// Residual r = b - A u of eq. neq2.9b, one thread per spatial point walking
+// the time rows with a window (U_{n-1}, U_n, U_{n+1}).  HY_DIRECT: r = b (and,
+// mixed, the double-float copy of b); HY_NORM: ||r||^2 only.  Mixed: double-
+// float arithmetic, r rounded to FP32; FP64 otherwise.
+struct HResid {
+  int N, S;
+  Stencil st;
+  double c2, c1;                // 1/(2 dt) (midpoint rows), 1/dt (last row)
+  dfc c2d, c1d;
+  dfc kap[5];
+  const double* b64;
+  const double* u64;
+  float2* Bdf;
+  const float2* Udf;
+  void* r;                      // [N][S] float / double
+  double* norm2;
+};
+
+struct Nbh {
+  int l, r, d, u;
+};
+PD_D Nbh nbh(const Stencil& st, int s) {
+  Nbh g;
+  const int x = s % st.nx, y = s / st.nx;
+  g.l = x > 0 ? s - 1 : (st.bcx == PD_PERIODIC ? s + st.nx - 1 : -1);
+  g.r = x < st.nx - 1 ? s + 1 : (st.bcx == PD_PERIODIC ? s - (st.nx - 1) : -1);
+  g.d = (st.dim == 2 && y > 0) ? s - st.nx : -1;
+  g.u = (st.dim == 2 && y < st.ny - 1) ? s + st.nx : -1;
+  return g;
+}
+
+struct AccH {
+  float s, e;
+};
+PD_D void acch_add(AccH& A, float h, float l) {
+  const float t = __fadd_rn(A.s, h);
+  const float bb = __fsub_rn(t, A.s);
+  const float err = __fadd_rn(__fsub_rn(A.s, __fsub_rn(t, bb)), __fsub_rn(h, bb));
+  A.s = t;
+  A.e += err + l;
+}
+PD_D void acch_add_prod(AccH& A, dfc k, float2 u) {
+  const float p = __fmul_rn(u.x, k.hi);
+  float pe = __fmaf_rn(u.x, k.hi, -p);
+  pe = __fmaf_rn(u.x, k.lo, pe);
+  pe = __fmaf_rn(u.y, k.hi, pe);
+  acch_add(A, p, pe);
+}
+
+template <int PREC, int MODE>
+__global__ void __launch_bounds__(HR_TB) k_hy_resid(const HResid a) {
+  const int s = blockIdx.x * HR_TB + threadIdx.x;
+  const bool valid = s < a.S;
+  const int N = a.N, S = a.S;
+  const Stencil& st = a.st;
+  const Nbh g = nbh(st, valid ? s : 0);
+  double nrm = 0.0;
+  float nrmf = 0.f;
+  if (valid) {
+    if constexpr (MODE == HY_DIRECT) {
+      for (int n = 0; n < N; ++n) {
+        const size_t i = (size_t)n * S + s;
+        const double bv = a.b64[i];
+        if constexpr (PREC == 1) {
+          reinterpret_cast<double*>(a.r)[i] = bv;
+          nrm = fma(bv, bv, nrm);
+        } else {
+          const df d = df_from_double(bv);
+          a.Bdf[i] = make_float2(d.hi, d.lo);
+          reinterpret_cast<float*>(a.r)[i] = d.hi;
+          nrmf = fmaf(d.hi, d.hi, nrmf);
+        }
+      }
+    } else if constexpr (PREC == 1) {
+      double um = 0.0, u0 = a.u64[s];
+      for (int n = 0; n < N; ++n) {
+        const size_t base = (size_t)n * S;
+        const double* U = a.u64 + base;
+        const double up = n + 1 < N ? a.u64[base + S + s] : 0.0;
+        double ku = st.kc * u0;
+        if (g.l >= 0) ku = fma(st.kxl, U[g.l], ku);
+        if (g.r >= 0) ku = fma(st.kxu, U[g.r], ku);
+        if (g.d >= 0) ku = fma(st.kyl, U[g.d], ku);
+        if (g.u >= 0) ku = fma(st.kyu, U[g.u], ku);
+        const double bu = n + 1 < N ? a.c2 * (up - um) : a.c1 * (u0 - um);
+        const double r = a.b64[base + s] - bu - ku;
+        nrm = fma(r, r, nrm);
+        if constexpr (MODE == HY_RESID) reinterpret_cast<double*>(a.r)[base + s] = r;
+        um = u0;
+        u0 = up;
+      }
+    } else {
+      float2 um = make_float2(0.f, 0.f), u0 = a.Udf[s];
+      for (int n = 0; n < N; ++n) {
+        const size_t base = (size_t)n * S;
+        const float2* U = a.Udf + base;
+        const float2 up = n + 1 < N ? a.Udf[base + S + s] : make_float2(0.f, 0.f);
+        const float2 bb = a.Bdf[base + s];
+        AccH A = {bb.x, bb.y};
+        acch_add_prod(A, dfc{-a.kap[0].hi, -a.kap[0].lo}, u0);
+        if (g.l >= 0) acch_add_prod(A, dfc{-a.kap[1].hi, -a.kap[1].lo}, U[g.l]);
+        if (g.r >= 0) acch_add_prod(A, dfc{-a.kap[2].hi, -a.kap[2].lo}, U[g.r]);
+        if (g.d >= 0) acch_add_prod(A, dfc{-a.kap[3].hi, -a.kap[3].lo}, U[g.d]);
+        if (g.u >= 0) acch_add_prod(A, dfc{-a.kap[4].hi, -a.kap[4].lo}, U[g.u]);
+        if (n + 1 < N) {
+          acch_add_prod(A, dfc{-a.c2d.hi, -a.c2d.lo}, up);
+          acch_add_prod(A, a.c2d, um);
+        } else {
+          acch_add_prod(A, dfc{-a.c1d.hi, -a.c1d.lo}, u0);
+          acch_add_prod(A, a.c1d, um);
+        }
+        const float r = fast_two_sum(A.s, A.e).hi;
+        nrmf = fmaf(r, r, nrmf);
+        if constexpr (MODE == HY_RESID) reinterpret_cast<float*>(a.r)[base + s] = r;
+        um = u0;
+        u0 = up;
+      }
+      nrm = (double)nrmf;
+    }
+    if constexpr (PREC == 0 && MODE == HY_DIRECT) nrm = (double)nrmf;
+  }
+  for (int o = 16; o > 0; o >>= 1) nrm += __shfl_xor_sync(0xffffffffu, nrm, o);
+  if ((threadIdx.x & 31) == 0 && a.norm2 != nullptr) atomicAdd(a.norm2, nrm);
+}
+
+// y = A u (FP64) and the right-hand side b_n = f(t_n) (+ u0/(2 dt) in row 1)
+__global__ void k_hy_apply(const HResid a, const double* u, double* y) {
+  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= a.S) return;
+  const Stencil& st = a.st;
+  const Nbh g = nbh(st, s);
+  const int N = a.N, S = a.S;
+  for (int n = 0; n < N; ++n) {
+    const double* U = u + (size_t)n * S;
+    double ku = st.kc * U[s];
+    if (g.l >= 0) ku = fma(st.kxl, U[g.l], ku);
+    if (g.r >= 0) ku = fma(st.kxu, U[g.r], ku);
+    if (g.d >= 0) ku = fma(st.kyl, U[g.d], ku);
+    if (g.u >= 0) ku = fma(st.kyu, U[g.u], ku);
+    const double um = n > 0 ? U[s - S] : 0.0;
+    const double bu = n + 1 < N ? a.c2 * (U[s + S] - um) : a.c1 * (U[s] - um);
+    y[(size_t)n * S + s] = bu + ku;
+  }
+}
+
+__global__ void k_hy_rhs(const HResid a, const double* u0, const double* f, double* b) {
+  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= a.S) return;
+  for (int n = 0; n < a.N; ++n) {
+    double v = f != nullptr ? f[(size_t)(n + 1) * a.S + s] : 0.0;
+    if (n == 0) v += a.c2 * u0[s];
+    b[(size_t)n * a.S + s] = v;
+  }
+}
+
+template <typename R>
+cudaError_t launch_gemm(const HGemm& g, int mode, cudaStream_t st) {
+  const dim3 grid((g.S + HG_BN - 1) / HG_BN, (g.M + HG_BM - 1) / HG_BM), block(HG_TB);
+  if (mode == HY_FWD) k_hy_gemm<R, HY_FWD><<<grid, block, 0, st>>>(g);
+  else if (mode == HY_INV_SET) k_hy_gemm<R, HY_INV_SET><<<grid, block, 0, st>>>(g);
+  else k_hy_gemm<R, HY_INV_ADD><<<grid, block, 0, st>>>(g);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_resid(const HResid& a, int mode, bool fp64, cudaStream_t st) {
+  const dim3 grid((a.S + HR_TB - 1) / HR_TB), block(HR_TB);
+  if (fp64) {
+    if (mode == HY_DIRECT) k_hy_resid<1, HY_DIRECT><<<grid, block, 0, st>>>(a);
+    else if (mode == HY_RESID) k_hy_resid<1, HY_RESID><<<grid, block, 0, st>>>(a);
+    else k_hy_resid<1, HY_NORM><<<grid, block, 0, st>>>(a);
+  } else {
+    if (mode == HY_DIRECT) k_hy_resid<0, HY_DIRECT><<<grid, block, 0, st>>>(a);
+    else if (mode == HY_RESID) k_hy_resid<0, HY_RESID><<<grid, block, 0, st>>>(a);
+    else k_hy_resid<0, HY_NORM><<<grid, block, 0, st>>>(a);
+  }
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// Host side
+// ---------------------------------------------------------------------------
+struct pdh_plan {
+  pd_plan* sp = nullptr;          // spatial operators, step (b) on Nh rows
+  int nt = 0, nh = 0, precision = 0;
+  bool fp64 = false;
+  double dt = 0;
+  std::vector<cdh> x;             // all Nt roots
+  std::vector<int> half;          // indices of the solved roots
+  double cond_v = 0;
+  void* Af = nullptr;             // [2 Nh][Nt] real form of the solved rows of V^{-1}
+  void* Ai = nullptr;             // [Nt][2 Nh] weighted real form of the solved columns of V
+  void* r = nullptr;              // residual [Nt][S] (float / double)
+  float2* Udf = nullptr;          // mixed iterate [Nt][S]
+  float2* Bdf = nullptr;          // mixed b [Nt][S]
+  double* dnorm = nullptr;
+  double* hnorm = nullptr;
+  int* hflag = nullptr;
+  unsigned long long launches = 0;
+  char msg[256] = {0};
+};
+
+namespace {
+
+pd_status ph_err(pdh_plan* q, pd_status s, const char* what) {
+  if (q) snprintf(q->msg, sizeof(q->msg), "%s", what);
+  return s;
+}
+pd_status ph_cuda(pdh_plan* q, cudaError_t e, const char* what) {
+  if (q) snprintf(q->msg, sizeof(q->msg), "%s: %s", what, cudaGetErrorString(e));
+  cudaGetLastError();
+  return e == cudaErrorMemoryAllocation ? PD_ERR_NOMEM : PD_ERR_CUDA;
+}
+#define PHCU(call)                                         \
+  do {                                                     \
+    cudaError_t e_ = (call);                               \
+    if (e_ != cudaSuccess) return ph_cuda(q, e_, #call);   \
+  } while (0)
+#define PHLK(call)                                         \
+  do {                                                     \
+    cudaError_t e_ = (call);                               \
+    ++q->launches;                                         \
+    if (e_ != cudaSuccess) return ph_cuda(q, e_, #call);   \
+  } while (0)
+
+void free_ph(pdh_plan* q) {
+  if (!q) return;
+  void* ptrs[] = {q->Af, q->Ai, q->r, q->Udf, q->Bdf, q->dnorm};
+  for (void* p : ptrs)
+    if (p) cudaFree(p);
+  if (q->hnorm) cudaFreeHost(q->hnorm);
+  if (q->sp) pd_plan_destroy(q->sp);
+  delete q;
+}
+
+// P2_l(x) (Chebyshev, second kind), l = 0..n-1, by the three-term recurrence
+void cheb_u(int n, cdh x, std::vector<cdh>& U) {
+  U.assign(n, cdh(1.0, 0.0));
+  if (n > 1) U[1] = 2.0 * x;
+  for (int l = 2; l < n; ++l) U[l] = 2.0 * x * U[l - 1] - U[l - 2];
+}
+
+// g(x) = P2_{N-1}(x) - i P1_N(x) and g'(x), with T_N' = N U_{N-1} and
+// U_{N-1}' = (N T_N - x U_{N-1}) / (x^2 - 1)
+void char_eq(int N, cdh x, cdh& g, cdh& dg) {
+  cdh Tm(1.0, 0.0), Tc = x;            // T_0, T_1
+  for (int k = 2; k <= N; ++k) {
+    const cdh Tn = 2.0 * x * Tc - Tm;
+    Tm = Tc;
+    Tc = Tn;
+  }
+  const cdh TN = N >= 1 ? Tc : cdh(1.0, 0.0);
+  cdh Um(1.0, 0.0), Uc = 2.0 * x;      // U_0, U_1
+  for (int k = 2; k <= N - 1; ++k) {
+    const cdh Un = 2.0 * x * Uc - Um;
+    Um = Uc;
+    Uc = Un;
+  }
+  const cdh UN1 = N - 1 >= 1 ? Uc : cdh(1.0, 0.0);
+  g = UN1 - cdh(0.0, 1.0) * TN;
+  const cdh dU = ((double)N * TN - x * UN1) / (x * x - 1.0);
+  const cdh dT = (double)N * UN1;
+  dg = dU - cdh(0.0, 1.0) * dT;
+}
+
+void hybrid_roots(int N, std::vector<cdh>& x) {
+  const double PI = 3.14159265358979323846;
+  const cdh I(0.0, 1.0);
+  x.assign(N, cdh(0.0, 0.0));
+  cdh sum(0.0, 0.0);
+  for (int k = 1; k < N; ++k) {
+    cdh th = cdh(k * PI, -0.3) / (double)N;
+    for (int it = 0; it < 200; ++it) {
+      const cdh nt = (k * PI + I * std::atanh(std::sin(th))) / (double)N;
+      const bool done = std::abs(nt - th) <= 1e-16 * std::abs(nt);
+      th = nt;
+      if (done) break;
+    }
+    x[k - 1] = std::cos(th);
+    sum += x[k - 1];
+  }
+  x[N - 1] = -I - sum;
+  if (N == 1) return;
+  for (int n = 0; n < N; ++n) {
+    for (int it = 0; it < 4; ++it) {
+      cdh g, dg;
+      char_eq(N, x[n], g, dg);
+      if (std::abs(dg) == 0.0) break;
+      const cdh st = g / dg;
+      if (!(std::abs(st) < 1e-6)) break;   // keep the fixed-point value if Newton wanders
+      x[n] -= st;
+      if (std::abs(st) <= 1e-16 * std::max(1.0, std::abs(x[n]))) break;
+    }
+  }
+}
+
+template <typename T>
+pd_status upload_real(pdh_plan* q, void** dst, const std::vector<double>& v) {
+  std::vector<T> h(v.size());
+  for (size_t i = 0; i < v.size(); ++i) h[i] = (T)v[i];
+  PHCU(cudaMalloc(dst, h.size() * sizeof(T)));
+  PHCU(cudaMemcpy(*dst, h.data(), h.size() * sizeof(T), cudaMemcpyHostToDevice));
+  return PD_OK;
+}
+
+HResid resid_args(const pdh_plan* q) {
+  HResid a;
+  memset(&a, 0, sizeof(a));
+  const pd_plan* p = q->sp;
+  a.N = q->nt;
+  a.S = p->S;
+  a.st = p->st;
+  a.c2 = 0.5 / q->dt;
+  a.c1 = 1.0 / q->dt;
+  a.c2d = dfc_from(a.c2);
+  a.c1d = dfc_from(a.c1);
+  const double kap[5] = {p->st.kc, p->st.kxl, p->st.kxu, p->st.kyl, p->st.kyu};
+  for (int i = 0; i < 5; ++i) a.kap[i] = dfc_from(kap[i]);
+  a.Bdf = q->Bdf;
+  a.Udf = q->Udf;
+  a.r = q->r;
+  return a;
+}
+
+HGemm gemm_fwd(const pdh_plan* q) {
+  HGemm g;
+  memset(&g, 0, sizeof(g));
+  g.M = 2 * q->nh;
+  g.K = q->nt;
+  g.S = q->sp->S;
+  g.sg = q->sp->sg;
+  g.A = q->Af;
+  g.r = q->r;
+  g.out = q->sp->spec;
+  if (q->sp->xform_tc) {
+    g.amax = q->sp->amax;
+    g.amax_reset = q->sp->amax + 1;
+  }
+  g.flag = q->sp->dflag;
+  return g;
+}
+
+HGemm gemm_inv(const pdh_plan* q, double* u) {
+  HGemm g;
+  memset(&g, 0, sizeof(g));
+  g.M = q->nt;
+  g.K = 2 * q->nh;
+  g.S = q->sp->S;
+  g.sg = q->sp->sg;
+  g.A = q->Ai;
+  g.spec = q->sp->spec;
+  g.u64 = u;
+  g.Udf = q->Udf;
+  g.flag = q->sp->dflag;
+  return g;
+}
+
+pd_status step_b(pdh_plan* q) {
+  const unsigned long long before = q->sp->launches;
+  const pd_status s = plan_step_b(q->sp);
+  q->launches += q->sp->launches - before;
+  if (s != PD_OK) snprintf(q->msg, sizeof(q->msg), "%s", pd_last_error(q->sp));
+  return s;
+}
+
+pd_status gemm(pdh_plan* q, const HGemm& g, int mode) {
+  if (q->fp64) PHLK(launch_gemm<double>(g, mode, q->sp->stream));
+  else PHLK(launch_gemm<float>(g, mode, q->sp->stream));
+  return PD_OK;
+}
+
+// one pass of eq. 2.7 on the residual buffer; the update mode of step (c)
+pd_status pass(pdh_plan* q, double* u, int inv_mode) {
+  pd_status s = gemm(q, gemm_fwd(q), HY_FWD);
+  if (s != PD_OK) return s;
+  s = step_b(q);
+  if (s != PD_OK) return s;
+  return gemm(q, gemm_inv(q, u), inv_mode);
+}
+
+}  // namespace
+
+extern "C" {
+
+pd_status pdh_plan_create(const pd_space* sp, int nt, double dt, int precision, void* stream,
+                          pdh_plan** out) {
+  if (!out) return PD_ERR_ARG;
+  *out = nullptr;
+  if (!sp) return PD_ERR_ARG;
+  if (nt < 1) return PD_ERR_ARG;
+  if (nt > 4096) return PD_ERR_UNSUPPORTED;
+  if (!(dt > 0.0) || !std::isfinite(dt)) return PD_ERR_ARG;
+  if (precision != PD_FP64 && precision != PD_MIXED) return PD_ERR_ARG;
+
+  pdh_plan* q = new (std::nothrow) pdh_plan();
+  if (!q) return PD_ERR_NOMEM;
+  q->nt = nt;
+  q->dt = dt;
+  q->precision = precision;
+  q->fp64 = precision == PD_FP64;
+  hybrid_roots(nt, q->x);
+
+  // one root of every pair x, -conj(x) (the one with Re x > 0), and the
+  // self-conjugate root of odd Nt
+  std::vector<double> wgt;
+  std::vector<char> used(nt, 0);
+  for (int n = 0; n < nt; ++n) {
+    if (used[n]) continue;
+    int partner = -1;
+    double best = 1e300;
+    for (int m = 0; m < nt; ++m) {
+      if (used[m]) continue;
+      const double d = std::abs(q->x[m] + std::conj(q->x[n]));
+      if (d < best) { best = d; partner = m; }
+    }
+    const double tol = 1e-8 * std::max(1.0, std::abs(q->x[n]));
+    if (partner == n || partner < 0 || best > tol) {
+      q->half.push_back(n);
+      wgt.push_back(1.0);
+      used[n] = 1;
+    } else {
+      const int keep = q->x[n].real() >= q->x[partner].real() ? n : partner;
+      q->half.push_back(keep);
+      wgt.push_back(2.0);
+      used[n] = used[partner] = 1;
+    }
+  }
+  q->nh = (int)q->half.size();
+
+  // V, the left eigenvectors and V^{-1} rows for the solved roots
+  const cdh I(0.0, 1.0);
+  std::vector<cdh> ipow(nt), mipow(nt);
+  for (int l = 0; l < nt; ++l) {
+    ipow[l] = std::pow(I, l);
+    mipow[l] = std::pow(-I, l);
+  }
+  const int nh = q->nh;
+  std::vector<double> Af((size_t)2 * nh * nt), Ai((size_t)nt * 2 * nh);
+  std::vector<cdh> U;
+  double fv = 0.0, fvi = 0.0;
+  for (int n = 0; n < nt; ++n) {
+    cheb_u(nt, q->x[n], U);
+    std::vector<cdh> v(nt), w(nt);
+    for (int l = 0; l < nt; ++l) {
+      v[l] = ipow[l] * U[l];
+      w[l] = mipow[l] * U[l];
+    }
+    if (nt >= 2) {
+      const cdh wm2 = nt >= 3 ? w[nt - 3] : cdh(0.0, 0.0);
+      w[nt - 1] = 0.5 * wm2 - I * q->x[n] * w[nt - 2];
+    }
+    cdh sdot(0.0, 0.0);
+    for (int l = 0; l < nt; ++l) sdot += w[l] * v[l];
+    for (int l = 0; l < nt; ++l) {
+      fv += std::norm(v[l]);
+      fvi += std::norm(w[l] / sdot);
+    }
+    for (int k = 0; k < nh; ++k) {
+      if (q->half[k] != n) continue;
+      for (int l = 0; l < nt; ++l) {
+        const cdh vi = w[l] / sdot;                 // (V^{-1})[n][l]
+        Af[(size_t)(2 * k) * nt + l] = vi.real();
+        Af[(size_t)(2 * k + 1) * nt + l] = vi.imag();
+        Ai[(size_t)l * 2 * nh + 2 * k] = wgt[k] * v[l].real();
+        Ai[(size_t)l * 2 * nh + 2 * k + 1] = -wgt[k] * v[l].imag();
+      }
+    }
+  }
+  q->cond_v = std::sqrt(fv * fvi);
+
+  // step (b): lambda_1 = i x / dt, lambda_2 = 1 on the solved rows
+  std::vector<double> lam((size_t)4 * nh, 0.0);
+  for (int k = 0; k < nh; ++k) {
+    const cdh l1 = I * q->x[q->half[k]] / dt;
+    lam[4 * k] = l1.real();
+    lam[4 * k + 1] = l1.imag();
+    lam[4 * k + 2] = 1.0;
+  }
+  pd_status s = plan_create_internal(sp, nh, dt, 1.0, PD_BE, 1.0, precision, stream, false,
+                                     &q->sp, lam.data());
+  if (s != PD_OK) {
+    delete q;
+    return s;
+  }
+  const size_t ns = (size_t)nt * q->sp->S;
+  s = q->fp64 ? upload_real<double>(q, &q->Af, Af) : upload_real<float>(q, &q->Af, Af);
+  if (s == PD_OK) s = q->fp64 ? upload_real<double>(q, &q->Ai, Ai) : upload_real<float>(q, &q->Ai, Ai);
+  if (s == PD_OK) {
+    cudaError_t e = cudaMalloc(&q->r, ns * (q->fp64 ? sizeof(double) : sizeof(float)));
+    if (e == cudaSuccess && !q->fp64) e = cudaMalloc((void**)&q->Udf, ns * sizeof(float2));
+    if (e == cudaSuccess && !q->fp64) e = cudaMalloc((void**)&q->Bdf, ns * sizeof(float2));
+    if (e == cudaSuccess) e = cudaMalloc((void**)&q->dnorm, 2 * sizeof(double));
+    if (e == cudaSuccess) e = cudaMallocHost((void**)&q->hnorm, 2 * sizeof(double) + sizeof(int));
+    if (e != cudaSuccess) s = ph_cuda(q, e, "allocation");
+  }
+  if (s != PD_OK) {
+    free_ph(q);
+    return s;
+  }
+  q->hflag = reinterpret_cast<int*>(q->hnorm + 2);
+  *out = q;
+  return PD_OK;
+}
+
+pd_status pdh_plan_destroy(pdh_plan* q) {
+  if (!q) return PD_ERR_ARG;
+  if (q->sp && q->sp->stream) cudaStreamSynchronize(q->sp->stream);
+  else cudaDeviceSynchronize();
+  free_ph(q);
+  return PD_OK;
+}
+
+pd_status pdh_eigenvalues(const pdh_plan* q, double* lam) {
+  if (!q || !lam) return PD_ERR_ARG;
+  for (int n = 0; n < q->nt; ++n) {
+    const cdh l = cdh(0.0, 1.0) * q->x[n] / q->dt;
+    lam[2 * n] = l.real();
+    lam[2 * n + 1] = l.imag();
+  }
+  return PD_OK;
+}
+
+pd_status pdh_condition(const pdh_plan* q, double* cond) {
+  if (!q || !cond) return PD_ERR_ARG;
+  *cond = q->cond_v;
+  return PD_OK;
+}
+
+pd_status pdh_apply_A(pdh_plan* q, const double* u, double* y) {
+  if (!q || !u || !y) return PD_ERR_ARG;
+  const HResid a = resid_args(q);
+  k_hy_apply<<<(a.S + HR_TB - 1) / HR_TB, HR_TB, 0, q->sp->stream>>>(a, u, y);
+  PHLK(cudaGetLastError());
+  return PD_OK;
+}
+
+pd_status pdh_build_rhs(pdh_plan* q, const double* u0, const double* f, double* b) {
+  if (!q || !u0 || !b) return PD_ERR_ARG;
+  const HResid a = resid_args(q);
+  k_hy_rhs<<<(a.S + HR_TB - 1) / HR_TB, HR_TB, 0, q->sp->stream>>>(a, u0, f, b);
+  PHLK(cudaGetLastError());
+  return PD_OK;
+}
+
+pd_status pdh_solve(pdh_plan* q, const double* b, double* u, double tol, int max_refine,
+                    int* refinements, double* relres) {
+  if (!q || !b || !u || max_refine < 0 || !(tol >= 0.0)) return PD_ERR_ARG;
+  pd_plan* p = q->sp;
+  cudaStream_t st = p->stream;
+  const bool fp64 = q->fp64;
+  PHCU(cudaMemsetAsync(q->dnorm, 0, 2 * sizeof(double), st));
+  PHCU(cudaMemsetAsync(p->dflag, 0, sizeof(int), st));
+  HResid ra = resid_args(q);
+  ra.b64 = b;
+  ra.u64 = u;
+  ra.norm2 = q->dnorm;
+  PHLK(launch_resid(ra, HY_DIRECT, fp64, st));
+  pd_status s = pass(q, u, HY_INV_SET);
+  if (s != PD_OK) return s;
+  int done = 0;
+  double rel = -1.0;
+  const bool want_norm = max_refine > 0 || relres != nullptr;
+  ra.norm2 = q->dnorm + 1;
+  for (int k = 0; want_norm; ++k) {
+    const bool last = k == max_refine;
+    PHCU(cudaMemsetAsync(q->dnorm + 1, 0, sizeof(double), st));
+    PHLK(launch_resid(ra, last ? HY_NORM : HY_RESID, fp64, st));
+    PHCU(cudaMemcpyAsync(q->hnorm, q->dnorm, 2 * sizeof(double), cudaMemcpyDeviceToHost, st));
+    PHCU(cudaMemcpyAsync(q->hflag, p->dflag, sizeof(int), cudaMemcpyDeviceToHost, st));
+    PHCU(cudaStreamSynchronize(st));
+    const double nb = std::sqrt(q->hnorm[0]);
+    rel = nb > 0.0 ? std::sqrt(q->hnorm[1]) / nb : std::sqrt(q->hnorm[1]);
+    if (*q->hflag != 0 || !std::isfinite(rel)) {
+      if (refinements) *refinements = done;
+      if (relres) *relres = rel;
+      return ph_err(q, PD_ERR_NONFINITE, "non-finite value in the hybrid ParaDiag-I solve");
+    }
+    if (last || rel <= tol) break;
+    s = pass(q, u, HY_INV_ADD);
+    if (s != PD_OK) return s;
+    ++done;
+  }
+  if (!fp64) PHLK(launch_from_df(q->Udf, u, (size_t)q->nt * p->S, st));
+  PHCU(cudaStreamSynchronize(st));
+  if (refinements) *refinements = done;
+  if (relres) *relres = rel;
+  if (max_refine > 0 && tol > 0.0 && !(rel <= tol))
+    return ph_err(q, PD_ERR_NOT_CONVERGED, "refinement sweeps did not reach the tolerance");
+  return PD_OK;
+}
+
+pd_status pdh_profile_sweep(pdh_plan* q, const double* b, double* u, int reps, float* ms) {
+  if (!q || !b || !u || !ms || reps < 1) return PD_ERR_ARG;
+  pd_plan* p = q->sp;
+  cudaStream_t st = p->stream;
+  const bool fp64 = q->fp64;
+  HResid ra = resid_args(q);
+  ra.b64 = b;
+  ra.u64 = u;
+  ra.norm2 = q->dnorm;
+  PHLK(launch_resid(ra, HY_DIRECT, fp64, st));
+  pd_status s = pass(q, u, HY_INV_SET);
+  if (s != PD_OK) return s;
+  ra.norm2 = q->dnorm + 1;
+  cudaEvent_t ev[5];
+  for (int i = 0; i < 5; ++i) PHCU(cudaEventCreate(&ev[i]));
+  double acc[4] = {0, 0, 0, 0};
+  for (int r = 0; r < reps; ++r) {
+    PHCU(cudaEventRecord(ev[0], st));
+    PHLK(launch_resid(ra, HY_RESID, fp64, st));
+    PHCU(cudaEventRecord(ev[1], st));
+    s = gemm(q, gemm_fwd(q), HY_FWD);
+    if (s != PD_OK) return s;
+    PHCU(cudaEventRecord(ev[2], st));
+    s = step_b(q);
+    if (s != PD_OK) return s;
+    PHCU(cudaEventRecord(ev[3], st));
+    s = gemm(q, gemm_inv(q, u), HY_INV_ADD);
+    if (s != PD_OK) return s;
+    PHCU(cudaEventRecord(ev[4], st));
+    PHCU(cudaEventSynchronize(ev[4]));
+    for (int i = 0; i < 4; ++i) {
+      float t = 0.f;
+      PHCU(cudaEventElapsedTime(&t, ev[i], ev[i + 1]));
+      acc[i] += t;
+    }
+  }
+  for (int i = 0; i < 5; ++i) cudaEventDestroy(ev[i]);
+  for (int i = 0; i < 4; ++i) ms[i] = (float)(acc[i] / reps);
+  if (!fp64) PHLK(launch_from_df(q->Udf, u, (size_t)q->nt * p->S, st));
+  PHCU(cudaStreamSynchronize(st));
+  return PD_OK;
+}
+
+pd_status pdh_launches(const pdh_plan* q, unsigned long long* count) {
+  if (!q || !count) return PD_ERR_ARG;
+  *count = q->launches;
+  return PD_OK;
+}
+
+const char* pdh_last_error(const pdh_plan* q) { return q ? q->msg : "null plan"; }
+
+}  // extern "C"

@@ -8,7 +8,7 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 def header_symbols():
     txt = open(os.path.join(ROOT, "include", "paradiag.h")).read()
-    return re.findall(r"PD_API\s+[\w\s\*]+?\b(pd1?_\w+)\s*\(", txt)
+    return re.findall(r"PD_API\s+[\w\s\*]+?\b(pd[1h]?_\w+)\s*\(", txt)
 
 
 def test_header_declares_the_boundary():
@@ -67,3 +67,13 @@ def test_pd1_plan_create_rejects_bad_arguments_without_gpu():
     assert pd.pd1_plan_create(sp, 16, 0.05, 1.2, 0, 2, 0, None)[0] == pd.PD_ERR_ARG      # scaling
     sp2 = pd.pd_space(2, 15, 15, 0.1, 1.0, 0.0, 0, 0, 1.0, 1.0)   # Dirichlet x with advection
     assert pd.pd1_plan_create(sp2, 16, 0.05, 1.2, 0, 1, 0, None)[0] == pd.PD_ERR_UNSUPPORTED
+
+
+def test_pdh_plan_create_rejects_bad_arguments_without_gpu():
+    import paradiag_gb300 as pd
+    pd.build()
+    sp = pd.pd_space(1, 15, 1, 0.1, 0.0, 0.0, 0, 0, 1.0, 1.0)
+    assert pd.pdh_plan_create(sp, 0, 0.01, 0, None)[0] == pd.PD_ERR_ARG          # nt
+    assert pd.pdh_plan_create(sp, 5000, 0.01, 0, None)[0] == pd.PD_ERR_UNSUPPORTED
+    assert pd.pdh_plan_create(sp, 16, 0.0, 0, None)[0] == pd.PD_ERR_ARG          # dt
+    assert pd.pdh_plan_create(sp, 16, 0.01, 2, None)[0] == pd.PD_ERR_ARG         # precision
