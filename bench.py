@@ -48,6 +48,11 @@ def parse():
                     help="only the ParaDiag-I leg (one JSON object; profiling runs)")
     ap.add_argument("--pd1-kernels", action="store_true",
                     help="only the ParaDiag-I mixed kernel profile (ncu driver)")
+    ap.add_argument("--no-hybrid", action="store_true", help="skip the hybrid ParaDiag-I leg")
+    ap.add_argument("--hybrid-only", action="store_true",
+                    help="only the hybrid ParaDiag-I leg (one JSON object)")
+    ap.add_argument("--hybrid-kernels", action="store_true",
+                    help="only the hybrid ParaDiag-I mixed kernel profile (ncu driver)")
     ap.add_argument("--profile-iteration", action="store_true",
                     help="only time the kernels of one iteration (the driver of ncu captures)")
     ap.add_argument("--sweep", action="store_true",
@@ -351,6 +356,111 @@ def pd1_leg(pd, torch, dev, args):
             "kernel_roofline_255x1023x32": kern}
 
 
+FP32_ALU_PEAK = 152 * 128 * 2 * 2.07e9 / 1e12   # TFLOP/s: SMs x FP32 lanes x FMA x max SM clock
+
+
+def hybrid_kernel_profile(pd, torch, dev, precisions):
+    """Per-stage times of a hybrid ParaDiag-I refinement sweep on the bench
+    workload (255 x 255 x 256): the residual (HBM: 20 bytes per unknown on the
+    mixed path, 24 on the FP64 path), the two dense time GEMMs (FP32 / FP64
+    CUDA-core FLOPs: 2 Nt flops per unknown each) and step (b)."""
+    import workloads as W
+    wl = W.hybrid_ade2d()
+    pb = wl.problem
+    sp = pb.space
+    space = dict(dim=2, nx=sp.nx, ny=sp.ny, nu=sp.nu, ax=sp.ax, ay=sp.ay, bc_x=sp.bc_x,
+                 bc_y=sp.bc_y)
+    stream = torch.cuda.current_stream()
+    hbm, _, src = peaks()
+    ns = pb.unknowns
+    out = {}
+    for prec in precisions:
+        fp64 = prec == pd.PD_FP64
+        pl = pd.PlanHybrid(space, pb.nt, pb.dt, prec, stream)
+        b = pl.build_rhs(torch.from_numpy(wl.u0).to(dev))
+        u = torch.empty_like(b)
+        pl.profile_sweep(b, u, reps=1)
+        kms = pl.profile_sweep(b, u, reps=3 if fp64 else 5)
+        nh = (pb.nt + 1) // 2
+        flops = 2.0 * (2 * nh) * pb.nt * sp.nx * sp.ny
+        rb = (24.0 if fp64 else 20.0) * ns
+        gbs = rb / (kms[0] / 1e3) / 1e9
+        ent = {"resid": {"ms": kms[0], "bound": "hbm", "achieved": gbs, "peak": hbm,
+                         "unit": "GB/s", "frac": gbs / hbm, "algorithmic_bytes": rb,
+                         "peak_source": f"{src} (MEASURED_PEAKS.json)"},
+               "step_b_ms": kms[2]}
+        for name, t in (("gemm_step_a", kms[1]), ("gemm_step_c_update", kms[3])):
+            tf = flops / (t / 1e3) / 1e12
+            pk = FP32_ALU_PEAK / 64.0 if fp64 else FP32_ALU_PEAK
+            ent[name] = {"ms": t, "bound": "alu", "achieved": tf, "peak": pk, "unit": "TFLOP/s",
+                         "frac": tf / pk, "algorithmic_flops": flops,
+                         "peak_source": ("FP64 CUDA-core rate taken as 1/64 of " if fp64 else "")
+                         + "152 SMs x 128 FP32 lanes x 2 flops x 2070 MHz (derived, nominal)"}
+        out["fp64" if fp64 else "mixed"] = ent
+        pl.close()
+    return out
+
+
+def hybrid_leg(pd, torch, dev, args):
+    """ParaDiag-I with the hybrid midpoint + backward-Euler discretisation
+    (Section 2.1.2) on the bench grid: 255 x 255, Nt = 256, T = 1 (16.6 M
+    unknowns).  Timed: the mixed solve (direct + refinement sweeps) to a
+    relative residual of 1e-11 (the tolerance of the main metric); beside it
+    the FP64 direct solve and the FP64 solve refined to the same residual."""
+    import workloads as W
+    wl = W.hybrid_ade2d()
+    pb = wl.problem
+    sp = pb.space
+    space = dict(dim=2, nx=sp.nx, ny=sp.ny, nu=sp.nu, ax=sp.ax, ay=sp.ay, bc_x=sp.bc_x,
+                 bc_y=sp.bc_y)
+    stream = torch.cuda.current_stream()
+    NS = pb.unknowns
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+
+    def timed(plan, b, u, k, **kw):
+        res = None
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(k):
+            res = plan.solve(b, u, **kw)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / k, res
+
+    plan = pd.PlanHybrid(space, pb.nt, pb.dt, pd.PD_MIXED, stream)
+    b = plan.build_rhs(torch.from_numpy(wl.u0).to(dev))
+    u = torch.empty_like(b)
+    for _ in range(3):
+        plan.solve(b, u, tol=TOL, max_refine=20)
+    k = max(1, min(args.steps, 20))
+    l0 = plan.launches()
+    ms, (_, sweeps, rel) = timed(plan, b, u, k, tol=TOL, max_refine=20)
+    launches = (plan.launches() - l0) // k
+    r64 = float(torch.linalg.norm(b - plan.apply_A(u)) / torch.linalg.norm(b))
+    cond = plan.condition()
+    plan.close()
+    plan64 = pd.PlanHybrid(space, pb.nt, pb.dt, pd.PD_FP64, stream)
+    u64 = torch.empty_like(b)
+    plan64.solve(b, u64)
+    k64 = max(1, min(args.steps, 2))
+    ms_direct, (_, _, rel_direct) = timed(plan64, b, u64, k64)
+    ms64, (_, sweeps64, rel64) = timed(plan64, b, u64, k64, tol=TOL, max_refine=20)
+    plan64.close()
+    return {"workload": "hybrid_ade2d_255x255x256: 2D advection-diffusion (x periodic, "
+                        "y Dirichlet, nu = 1e-3, velocity (1, 0.5)), midpoint steps + one "
+                        "backward-Euler step, dt = 1/256",
+            "unknowns": NS, "ms_per_solve": ms, "value": NS / (ms / 1e3), "unit": UNIT,
+            "refinement_sweeps": sweeps, "relres": rel, "relres_fp64_apply_A": r64,
+            "residual_tol": TOL, "cond_V_frobenius": cond, "gpu_launches": launches,
+            "l2": "working set ~0.6 GB > 129 MB L2, no flush",
+            "fp64_direct": {"ms_per_solve": ms_direct, "value": NS / (ms_direct / 1e3),
+                            "relres": rel_direct},
+            "fp64_refined": {"ms_per_solve": ms64, "value": NS / (ms64 / 1e3),
+                             "refinement_sweeps": sweeps64, "relres": rel64},
+            "kernels": hybrid_kernel_profile(pd, torch, dev, (pd.PD_MIXED, pd.PD_FP64))}
+
+
 def run_sweep(pd, torch, dev):
     """Per-kernel time and algorithmic HBM throughput of one mixed iteration on
     1D advection-diffusion problems (nu = 1e-2, a = 1, BE, alpha = 1e-2) of
@@ -443,6 +553,13 @@ def main():
     b = plan.build_rhs(u0)
     u = torch.zeros_like(b)
     torch.cuda.synchronize()
+    if args.hybrid_kernels or args.hybrid_only:
+        out = (hybrid_kernel_profile(pd, torch, dev, (pd.PD_MIXED,)) if args.hybrid_kernels
+               else hybrid_leg(pd, torch, dev, args))
+        if rank == 0:
+            print(json.dumps(out), flush=True)
+        plan.close()
+        return
     if args.pd1_kernels:
         out = pd1_kernel_profile(pd, torch, dev, (pd.PD_MIXED,))
         if rank == 0:
@@ -562,6 +679,9 @@ def main():
     pd1 = None
     if not args.no_pd1:
         pd1 = pd1_leg(pd, torch, dev, args)
+    hybrid = None
+    if not args.no_hybrid:
+        hybrid = hybrid_leg(pd, torch, dev, args)
 
     err = err64 = None
     if rank == 0 and not args.no_check:
@@ -602,6 +722,7 @@ def main():
                "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
                "batched": batched,
                "paradiag1": pd1,
+               "paradiag1_hybrid": hybrid,
                "gpu_launches": launches}
         print(json.dumps(out), flush=True)
     plan.close()

@@ -44,13 +44,22 @@ using cdh = std::complex<double>;
 
 namespace {
 
-constexpr int HG_BM = 64, HG_BN = 128, HG_BK = 16, HG_TB = 256;
+// GEMM tiles: BM x BN outputs per block of 256 threads, 8 x TN per thread
+// (TN = 8 in FP32, 4 in FP64), K in slices of 16 staged in shared memory
+// with the next slice prefetched into registers
+constexpr int HG_BM = 128, HG_BK = 16, HG_TB = 256;
+template <typename R> struct GemmTile;
+template <> struct GemmTile<float> { static constexpr int TN = 8, BN = 128; };
+template <> struct GemmTile<double> { static constexpr int TN = 4, BN = 64; };
 constexpr int HR_TB = 128;
+constexpr int HR_CH = 16;   // time rows per thread of the residual kernel
 
 enum { HY_DIRECT = 0, HY_RESID = 1, HY_NORM = 2 };
 enum { HY_FWD = 0, HY_INV_SET = 1, HY_INV_ADD = 2 };
 
-// GEMM C[M][N] = A[M][K] . B[K][N] over spatial points N = S.
+// GEMM C[M][N] = A[M][K] . B[K][N] over spatial points N = S; A is passed
+// transposed (AT[K][M], so that the tile loads are coalesced and the shared-
+// memory stores conflict-free).
 //   HY_FWD:  B = the residual r ([K = Nt][S] real), C rows (2k, 2k+1) are the
 //            real and imaginary parts of spectrum row k (written as complex);
 //   HY_INV_*: B rows (2k + c) are component c of spectrum row k, C = u
@@ -58,7 +67,7 @@ enum { HY_FWD = 0, HY_INV_SET = 1, HY_INV_ADD = 2 };
 struct HGemm {
   int M, K, S;
   SpecGeom sg;
-  const void* A;        // [M][K] row-major (float / double)
+  const void* AT;       // [K][M] (float / double)
   const void* r;        // HY_FWD: residual (float / double) [Nt][S]
   const void* spec;     // HY_INV: spectrum rows (complex)
   void* out;            // HY_FWD: spectrum rows (complex)
@@ -70,83 +79,126 @@ struct HGemm {
 };
 
 template <typename R, int MODE>
-__global__ void __launch_bounds__(HG_TB) k_hy_gemm(const HGemm a) {
-  __shared__ __align__(16) R As[HG_BK][HG_BM];
-  __shared__ __align__(16) R Bs[HG_BK][HG_BN];
-  const int tid = threadIdx.x;
-  const int tx = tid & 31, ty = tid >> 5;       // 32 x 8 threads, 4 x 8 outputs each
-  const int n0 = blockIdx.x * HG_BN, m0 = blockIdx.y * HG_BM;
-  const int M = a.M, K = a.K, S = a.S;
-  const R* A = reinterpret_cast<const R*>(a.A);
+__global__ void __launch_bounds__(HG_TB, 2) k_hy_gemm(const HGemm a) {
+  constexpr int TN = GemmTile<R>::TN, BN = GemmTile<R>::BN;
+  constexpr int NTX = BN / TN;                   // threads along N (16)
+  constexpr int AL = HG_BK * HG_BM / HG_TB;      // A-tile values per thread (8)
+  constexpr int BL = HG_BK * BN / HG_TB;         // B-tile values per thread (8 / 4)
+  __shared__ __align__(16) R As[2][HG_BK][HG_BM];
+  __shared__ __align__(16) R Bs[2][HG_BK][BN];
   using C = cplx_t<R>;
+  const int tid = threadIdx.x;
+  const int tx = tid % NTX, ty = tid / NTX;      // 16 x 16 threads
+  const int n0 = blockIdx.x * BN, m0 = blockIdx.y * HG_BM;
+  const int M = a.M, K = a.K, S = a.S;
+  const R* AT = reinterpret_cast<const R*>(a.AT);
 
-  R acc[8][4];
+  // this thread's tile-load coordinates (fixed over the K loop)
+  int a_kk[AL], a_mm[AL];
 #pragma unroll
-  for (int i = 0; i < 8; ++i)
+  for (int q = 0; q < AL; ++q) {
+    const int e = tid + q * HG_TB;
+    a_kk[q] = e / HG_BM;
+    a_mm[q] = e % HG_BM;
+  }
+  int b_kk[BL], b_nn[BL];
+  int b_off[BL];                  // HY_FWD: column n; HY_INV: spectrum offset of column n
+  bool b_ok[BL];
 #pragma unroll
-    for (int j = 0; j < 4; ++j) acc[i][j] = (R)0;
-
-  for (int k0 = 0; k0 < K; k0 += HG_BK) {
-    // A tile: BM x BK, stored transposed (As[kk][m])
-#pragma unroll
-    for (int q = 0; q < (HG_BM * HG_BK) / HG_TB; ++q) {
-      const int e = tid + q * HG_TB;
-      const int mm = e / HG_BK, kk = e % HG_BK;
-      const int m = m0 + mm, k = k0 + kk;
-      As[kk][mm] = (m < M && k < K) ? A[(size_t)m * K + k] : (R)0;
+  for (int q = 0; q < BL; ++q) {
+    const int e = tid + q * HG_TB;
+    if constexpr (MODE == HY_FWD) {
+      b_kk[q] = e / BN;
+      b_nn[q] = e % BN;
+    } else {
+      // pairs of K rows (2j, 2j+1) come from one complex value: BL/2 loads
+      const int ee = tid + (q >> 1) * HG_TB;
+      b_kk[q] = 2 * (ee / BN) + (q & 1);
+      b_nn[q] = ee % BN;
     }
-    // B tile: BK x BN
+    const int n = n0 + b_nn[q];
+    b_ok[q] = n < S;
+    b_off[q] = (MODE == HY_FWD) ? n : (int)spec_index(a.sg, 0, b_ok[q] ? n : 0);
+  }
+
+  R areg[AL], breg[BL];
+  auto load_tile = [&](int k0) {
+#pragma unroll
+    for (int q = 0; q < AL; ++q) {
+      const int k = k0 + a_kk[q], m = m0 + a_mm[q];
+      areg[q] = (k < K && m < M) ? AT[(size_t)k * M + m] : (R)0;
+    }
     if constexpr (MODE == HY_FWD) {
       const R* rr = reinterpret_cast<const R*>(a.r);
 #pragma unroll
-      for (int q = 0; q < (HG_BK * HG_BN) / HG_TB; ++q) {
-        const int e = tid + q * HG_TB;
-        const int kk = e / HG_BN, nn = e % HG_BN;
-        const int k = k0 + kk, n = n0 + nn;
-        Bs[kk][nn] = (k < K && n < S) ? rr[(size_t)k * S + n] : (R)0;
+      for (int q = 0; q < BL; ++q) {
+        const int k = k0 + b_kk[q];
+        breg[q] = (k < K && b_ok[q]) ? rr[(size_t)k * S + b_off[q]] : (R)0;
       }
     } else {
-      // rows (2j, 2j+1) of the tile from complex spectrum row (k0/2 + j)
       const C* sp = reinterpret_cast<const C*>(a.spec);
 #pragma unroll
-      for (int q = 0; q < (HG_BK / 2 * HG_BN) / HG_TB; ++q) {
-        const int e = tid + q * HG_TB;
-        const int j = e / HG_BN, nn = e % HG_BN;
-        const int kr = (k0 >> 1) + j, n = n0 + nn;
+      for (int q = 0; q < BL; q += 2) {
+        const int kr = (k0 + b_kk[q]) >> 1;
         C v = czero<C>();
-        if (2 * kr < K && n < S) v = sp[spec_index(a.sg, kr, n)];
-        Bs[2 * j][nn] = v.x;
-        Bs[2 * j + 1][nn] = v.y;
+        if (2 * kr < K && b_ok[q]) v = sp[(size_t)kr * a.sg.specS + b_off[q]];
+        breg[q] = v.x;
+        breg[q + 1] = v.y;
       }
     }
-    __syncthreads();
+  };
+  auto store_tile = [&](int buf) {
+#pragma unroll
+    for (int q = 0; q < AL; ++q) As[buf][a_kk[q]][a_mm[q]] = areg[q];
+#pragma unroll
+    for (int q = 0; q < BL; ++q) Bs[buf][b_kk[q]][b_nn[q]] = breg[q];
+  };
+
+  R acc[8][TN];
+#pragma unroll
+  for (int i = 0; i < 8; ++i)
+#pragma unroll
+    for (int j = 0; j < TN; ++j) acc[i][j] = (R)0;
+
+  load_tile(0);
+  store_tile(0);
+  __syncthreads();
+  int buf = 0;
+  for (int k0 = 0; k0 < K; k0 += HG_BK) {
+    const bool more = k0 + HG_BK < K;
+    if (more) load_tile(k0 + HG_BK);
 #pragma unroll
     for (int kk = 0; kk < HG_BK; ++kk) {
-      R av[8], bv[4];
+      R av[8], bv[TN];
 #pragma unroll
-      for (int i = 0; i < 8; ++i) av[i] = As[kk][ty * 8 + i];
+      for (int i = 0; i < 8; ++i) av[i] = As[buf][kk][ty * 8 + i];
 #pragma unroll
-      for (int j = 0; j < 4; ++j) bv[j] = Bs[kk][tx * 4 + j];
+      for (int j = 0; j < TN; ++j) bv[j] = Bs[buf][kk][tx * TN + j];
 #pragma unroll
       for (int i = 0; i < 8; ++i)
 #pragma unroll
-        for (int j = 0; j < 4; ++j) acc[i][j] = fma(av[i], bv[j], acc[i][j]);
+        for (int j = 0; j < TN; ++j) acc[i][j] = fma(av[i], bv[j], acc[i][j]);
     }
-    __syncthreads();
+    if (more) {
+      store_tile(buf ^ 1);
+      __syncthreads();
+      buf ^= 1;
+    }
   }
 
   if constexpr (MODE == HY_FWD) {
     C* out = reinterpret_cast<C*>(a.out);
     float amx = 0.f;
 #pragma unroll
-    for (int i = 0; i < 8; i += 2) {
-      const int m = m0 + ty * 8 + i;          // even: real part of spectrum row m/2
-      if (m >= M) continue;
+    for (int j = 0; j < TN; ++j) {
+      const int n = n0 + tx * TN + j;
+      if (n >= S) continue;
+      const size_t o = spec_index(a.sg, 0, n);
 #pragma unroll
-      for (int j = 0; j < 4; ++j) {
-        const int n = n0 + tx * 4 + j;
-        if (n >= S) continue;
-        out[spec_index(a.sg, m >> 1, n)] = mk(acc[i][j], acc[i + 1][j]);
+      for (int i = 0; i < 8; i += 2) {
+        const int m = m0 + ty * 8 + i;        // even: real part of spectrum row m/2
+        if (m >= M) continue;
+        out[(size_t)(m >> 1) * a.sg.specS + o] = mk(acc[i][j], acc[i + 1][j]);
         amx = fmaxf(amx, fmaxf(fabsf((float)acc[i][j]), fabsf((float)acc[i + 1][j])));
       }
     }
@@ -162,8 +214,8 @@ __global__ void __launch_bounds__(HG_TB) k_hy_gemm(const HGemm a) {
       const int m = m0 + ty * 8 + i;
       if (m >= M) continue;
 #pragma unroll
-      for (int j = 0; j < 4; ++j) {
-        const int n = n0 + tx * 4 + j;
+      for (int j = 0; j < TN; ++j) {
+        const int n = n0 + tx * TN + j;
         if (n >= S) continue;
         const size_t idx = (size_t)m * S + n;
         const R v = acc[i][j];
@@ -236,18 +288,22 @@ PD_D void acch_add_prod(AccH& A, dfc k, float2 u) {
   acch_add(A, p, pe);
 }
 
+// One thread per spatial point and chunk of HR_CH time rows (grid.y: chunks),
+// so that many rows of a point are in flight at once.
 template <int PREC, int MODE>
 __global__ void __launch_bounds__(HR_TB) k_hy_resid(const HResid a) {
   const int s = blockIdx.x * HR_TB + threadIdx.x;
   const bool valid = s < a.S;
   const int N = a.N, S = a.S;
+  const int n0 = blockIdx.y * HR_CH;
+  const int n1 = min(N, n0 + HR_CH);
   const Stencil& st = a.st;
   const Nbh g = nbh(st, valid ? s : 0);
   double nrm = 0.0;
   float nrmf = 0.f;
   if (valid) {
     if constexpr (MODE == HY_DIRECT) {
-      for (int n = 0; n < N; ++n) {
+      for (int n = n0; n < n1; ++n) {
         const size_t i = (size_t)n * S + s;
         const double bv = a.b64[i];
         if constexpr (PREC == 1) {
@@ -261,8 +317,10 @@ __global__ void __launch_bounds__(HR_TB) k_hy_resid(const HResid a) {
         }
       }
     } else if constexpr (PREC == 1) {
-      double um = 0.0, u0 = a.u64[s];
-      for (int n = 0; n < N; ++n) {
+      double um = n0 > 0 ? a.u64[(size_t)(n0 - 1) * S + s] : 0.0;
+      double u0 = a.u64[(size_t)n0 * S + s];
+#pragma unroll 4
+      for (int n = n0; n < n1; ++n) {
         const size_t base = (size_t)n * S;
         const double* U = a.u64 + base;
         const double up = n + 1 < N ? a.u64[base + S + s] : 0.0;
@@ -279,8 +337,10 @@ __global__ void __launch_bounds__(HR_TB) k_hy_resid(const HResid a) {
         u0 = up;
       }
     } else {
-      float2 um = make_float2(0.f, 0.f), u0 = a.Udf[s];
-      for (int n = 0; n < N; ++n) {
+      float2 um = n0 > 0 ? a.Udf[(size_t)(n0 - 1) * S + s] : make_float2(0.f, 0.f);
+      float2 u0 = a.Udf[(size_t)n0 * S + s];
+#pragma unroll 4
+      for (int n = n0; n < n1; ++n) {
         const size_t base = (size_t)n * S;
         const float2* U = a.Udf + base;
         const float2 up = n + 1 < N ? a.Udf[base + S + s] : make_float2(0.f, 0.f);
@@ -304,9 +364,8 @@ __global__ void __launch_bounds__(HR_TB) k_hy_resid(const HResid a) {
         um = u0;
         u0 = up;
       }
-      nrm = (double)nrmf;
     }
-    if constexpr (PREC == 0 && MODE == HY_DIRECT) nrm = (double)nrmf;
+    if constexpr (PREC == 0) nrm = (double)nrmf;
   }
   for (int o = 16; o > 0; o >>= 1) nrm += __shfl_xor_sync(0xffffffffu, nrm, o);
   if ((threadIdx.x & 31) == 0 && a.norm2 != nullptr) atomicAdd(a.norm2, nrm);
@@ -344,7 +403,8 @@ __global__ void k_hy_rhs(const HResid a, const double* u0, const double* f, doub
 
 template <typename R>
 cudaError_t launch_gemm(const HGemm& g, int mode, cudaStream_t st) {
-  const dim3 grid((g.S + HG_BN - 1) / HG_BN, (g.M + HG_BM - 1) / HG_BM), block(HG_TB);
+  constexpr int BN = GemmTile<R>::BN;
+  const dim3 grid((g.S + BN - 1) / BN, (g.M + HG_BM - 1) / HG_BM), block(HG_TB);
   if (mode == HY_FWD) k_hy_gemm<R, HY_FWD><<<grid, block, 0, st>>>(g);
   else if (mode == HY_INV_SET) k_hy_gemm<R, HY_INV_SET><<<grid, block, 0, st>>>(g);
   else k_hy_gemm<R, HY_INV_ADD><<<grid, block, 0, st>>>(g);
@@ -352,7 +412,7 @@ cudaError_t launch_gemm(const HGemm& g, int mode, cudaStream_t st) {
 }
 
 cudaError_t launch_resid(const HResid& a, int mode, bool fp64, cudaStream_t st) {
-  const dim3 grid((a.S + HR_TB - 1) / HR_TB), block(HR_TB);
+  const dim3 grid((a.S + HR_TB - 1) / HR_TB, (a.N + HR_CH - 1) / HR_CH), block(HR_TB);
   if (fp64) {
     if (mode == HY_DIRECT) k_hy_resid<1, HY_DIRECT><<<grid, block, 0, st>>>(a);
     else if (mode == HY_RESID) k_hy_resid<1, HY_RESID><<<grid, block, 0, st>>>(a);
@@ -378,8 +438,8 @@ struct pdh_plan {
   std::vector<cdh> x;             // all Nt roots
   std::vector<int> half;          // indices of the solved roots
   double cond_v = 0;
-  void* Af = nullptr;             // [2 Nh][Nt] real form of the solved rows of V^{-1}
-  void* Ai = nullptr;             // [Nt][2 Nh] weighted real form of the solved columns of V
+  void* Af = nullptr;             // [Nt][2 Nh]: transposed real form of the solved rows of V^{-1}
+  void* Ai = nullptr;             // [2 Nh][Nt]: transposed weighted real form of the solved columns of V
   void* r = nullptr;              // residual [Nt][S] (float / double)
   float2* Udf = nullptr;          // mixed iterate [Nt][S]
   float2* Bdf = nullptr;          // mixed b [Nt][S]
@@ -519,7 +579,7 @@ HGemm gemm_fwd(const pdh_plan* q) {
   g.K = q->nt;
   g.S = q->sp->S;
   g.sg = q->sp->sg;
-  g.A = q->Af;
+  g.AT = q->Af;
   g.r = q->r;
   g.out = q->sp->spec;
   if (q->sp->xform_tc) {
@@ -537,7 +597,7 @@ HGemm gemm_inv(const pdh_plan* q, double* u) {
   g.K = 2 * q->nh;
   g.S = q->sp->S;
   g.sg = q->sp->sg;
-  g.A = q->Ai;
+  g.AT = q->Ai;
   g.spec = q->sp->spec;
   g.u64 = u;
   g.Udf = q->Udf;
@@ -673,8 +733,14 @@ pd_status pdh_plan_create(const pd_space* sp, int nt, double dt, int precision, 
     return s;
   }
   const size_t ns = (size_t)nt * q->sp->S;
-  s = q->fp64 ? upload_real<double>(q, &q->Af, Af) : upload_real<float>(q, &q->Af, Af);
-  if (s == PD_OK) s = q->fp64 ? upload_real<double>(q, &q->Ai, Ai) : upload_real<float>(q, &q->Ai, Ai);
+  // the GEMM kernels take A transposed: AT[k][m]
+  std::vector<double> AfT(Af.size()), AiT(Ai.size());
+  for (int m = 0; m < 2 * nh; ++m)
+    for (int k = 0; k < nt; ++k) AfT[(size_t)k * 2 * nh + m] = Af[(size_t)m * nt + k];
+  for (int m = 0; m < nt; ++m)
+    for (int k = 0; k < 2 * nh; ++k) AiT[(size_t)k * nt + m] = Ai[(size_t)m * 2 * nh + k];
+  s = q->fp64 ? upload_real<double>(q, &q->Af, AfT) : upload_real<float>(q, &q->Af, AfT);
+  if (s == PD_OK) s = q->fp64 ? upload_real<double>(q, &q->Ai, AiT) : upload_real<float>(q, &q->Ai, AiT);
   if (s == PD_OK) {
     cudaError_t e = cudaMalloc(&q->r, ns * (q->fp64 ? sizeof(double) : sizeof(float)));
     if (e == cudaSuccess && !q->fp64) e = cudaMalloc((void**)&q->Udf, ns * sizeof(float2));
