@@ -92,6 +92,11 @@ __global__ void __launch_bounds__(HG_TB, 2) k_hy_gemm(const HGemm a) {
   const int n0 = blockIdx.x * BN, m0 = blockIdx.y * HG_BM;
   const int M = a.M, K = a.K, S = a.S;
   const R* AT = reinterpret_cast<const R*>(a.AT);
+  // the thread's TN columns: TN/2 in each half of the tile, so that the 16
+  // threads of a row read one contiguous run of shared memory per vector load
+  auto col_of = [](int t, int j) {
+    return j < TN / 2 ? t * (TN / 2) + j : BN / 2 + t * (TN / 2) + (j - TN / 2);
+  };
 
   // this thread's tile-load coordinates (fixed over the K loop)
   int a_kk[AL], a_mm[AL];
@@ -173,11 +178,26 @@ __global__ void __launch_bounds__(HG_TB, 2) k_hy_gemm(const HGemm a) {
 #pragma unroll
       for (int i = 0; i < 8; ++i) av[i] = As[buf][kk][ty * 8 + i];
 #pragma unroll
-      for (int j = 0; j < TN; ++j) bv[j] = Bs[buf][kk][tx * TN + j];
+      for (int j = 0; j < TN; ++j) bv[j] = Bs[buf][kk][col_of(tx, j)];
+      if constexpr (std::is_same<R, float>::value) {
+        // paired FP32 FMAs: two output columns per instruction
 #pragma unroll
-      for (int i = 0; i < 8; ++i)
+        for (int i = 0; i < 8; ++i) {
+          const float2 ai = make_float2(av[i], av[i]);
 #pragma unroll
-        for (int j = 0; j < TN; ++j) acc[i][j] = fma(av[i], bv[j], acc[i][j]);
+          for (int j = 0; j < TN; j += 2) {
+            const float2 r2 = f2fma(ai, make_float2(bv[j], bv[j + 1]),
+                                    make_float2(acc[i][j], acc[i][j + 1]));
+            acc[i][j] = r2.x;
+            acc[i][j + 1] = r2.y;
+          }
+        }
+      } else {
+#pragma unroll
+        for (int i = 0; i < 8; ++i)
+#pragma unroll
+          for (int j = 0; j < TN; ++j) acc[i][j] = fma(av[i], bv[j], acc[i][j]);
+      }
     }
     if (more) {
       store_tile(buf ^ 1);
@@ -191,7 +211,7 @@ __global__ void __launch_bounds__(HG_TB, 2) k_hy_gemm(const HGemm a) {
     float amx = 0.f;
 #pragma unroll
     for (int j = 0; j < TN; ++j) {
-      const int n = n0 + tx * TN + j;
+      const int n = n0 + col_of(tx, j);
       if (n >= S) continue;
       const size_t o = spec_index(a.sg, 0, n);
 #pragma unroll
@@ -215,7 +235,7 @@ __global__ void __launch_bounds__(HG_TB, 2) k_hy_gemm(const HGemm a) {
       if (m >= M) continue;
 #pragma unroll
       for (int j = 0; j < TN; ++j) {
-        const int n = n0 + tx * TN + j;
+        const int n = n0 + col_of(tx, j);
         if (n >= S) continue;
         const size_t idx = (size_t)m * S + n;
         const R v = acc[i][j];
