@@ -134,6 +134,20 @@ PD_API pd_status pd_solve(pd_plan* plan, const double* b, double* u, int mode, d
 PD_API pd_status pd_solve_host(pd_plan* plan, const double* b_host, double* u_host, int mode,
                         double tol, int maxit, int restart, int* iters, double* relres);
 
+/* Windowing (Sections 2.1.1 and 2.2: long horizons as a sequence of time
+ * windows, each solved by ParaDiag): nwin consecutive windows of the plan's
+ * nt steps; window w starts from the last time level of window w-1 (u0 for
+ * w = 0) and is solved by pd_solve from a zero initial guess.  u0: [S];
+ * f: [nwin nt + 1][S] source values at t_0 .. t_{nwin nt}, or NULL for f = 0;
+ * u: [nwin][nt][S] output (device FP64, caller-owned).  theta-method plans only
+ * (leap-frog would need the velocity at every window start:
+ * PD_ERR_UNSUPPORTED).  iters_total: iterations summed over the windows;
+ * relres_max: the largest final relative residual (either may be NULL).  Stops
+ * at the first window that fails, returning its status. */
+PD_API pd_status pd_solve_windows(pd_plan* plan, const double* u0, const double* f, int nwin,
+                                  double* u, int mode, double tol, int maxit, int restart,
+                                  int* iters_total, double* relres_max);
+
 /* Solve A^T lambda = g (the transposed all-at-once system, backward in time).
  * Uses J A^T J = B1 (x) I + B2 (x) K^T (J = time reversal, B1, B2 Toeplitz):
  * a forward ParaDiag solve with K^T on time-reversed data.  lambda: initial
@@ -299,6 +313,16 @@ PD_API pd_status pd1_build_rhs(pd1_plan* plan, const double* u0, const double* f
  * when a residual is formed. */
 PD_API pd_status pd1_solve(pd1_plan* plan, const double* b, double* u, double tol,
                            int max_refine, int* refinements, double* relres);
+
+/* Windowing (Section 2.1.1: the windows of 20-30 steps that keep ParaDiag-I's
+ * roundoff bounded): nwin consecutive windows, each with the plan's geometric
+ * steps; window w starts from the last time level of window w-1 (u0 for
+ * w = 0) and is solved by pd1_solve.  f: [nwin nt + 1][S] values at the time
+ * points of all windows, or NULL; u: [nwin][nt][S] output.  refinements_total
+ * and relres_max as for pd_solve_windows. */
+PD_API pd_status pd1_solve_windows(pd1_plan* plan, const double* u0, const double* f, int nwin,
+                                   double* u, double tol, int max_refine, int* refinements_total,
+                                   double* relres_max);
 
 /* Measurement aid (no paper counterpart): from the direct solve of b, reps
  * refinement sweeps, each timed with CUDA events on the plan's stream;

@@ -27,6 +27,8 @@ Modules
                 discretisation (Section 2.1.2): B, the Newton roots of the
                 Chebyshev characteristic equation, the closed-form V, the
                 three-step solve and the exact solution by a sparse LU.
+  windows       O8: windowing -- consecutive windows chained from the last
+                time level, each solved exactly.
 
 Every function is pinned by a test in tests/test_oracle_*.py against a
 closed form, an invariant, a bound of the paper, a worked example the paper

@@ -90,6 +90,10 @@ _SIGS = {
     "pd1_build_rhs": (ctypes.c_int, [_P, _P, _P, _P]),
     "pd1_solve": (ctypes.c_int, [_P, _P, _P, ctypes.c_double, ctypes.c_int, _I, _D]),
     "pd1_launches": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_ulonglong)]),
+    "pd1_solve_windows": (ctypes.c_int, [_P, _P, _P, ctypes.c_int, _P, ctypes.c_double, ctypes.c_int,
+                                         _I, _D]),
+    "pd_solve_windows": (ctypes.c_int, [_P, _P, _P, ctypes.c_int, _P, ctypes.c_int, ctypes.c_double,
+                                        ctypes.c_int, ctypes.c_int, _I, _D]),
     "pd1_profile_sweep": (ctypes.c_int, [_P, _P, _P, ctypes.c_int, ctypes.POINTER(ctypes.c_float)]),
     "pd1_workspace": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_ulonglong)]),
     "pd1_last_error": (ctypes.c_char_p, [_P]),
@@ -327,6 +331,22 @@ def pd1_profile_sweep(plan, b, u, reps):
     return st, list(ms)
 
 
+def pd1_solve_windows(plan, u0, f, nwin, u, tol, max_refine):
+    it = ctypes.c_int(0)
+    rr = ctypes.c_double(0.0)
+    st = load().pd1_solve_windows(plan, u0, f, nwin, u, tol, max_refine, ctypes.byref(it),
+                                  ctypes.byref(rr))
+    return st, it.value, rr.value
+
+
+def pd_solve_windows(plan, u0, f, nwin, u, mode, tol, maxit, restart):
+    it = ctypes.c_int(0)
+    rr = ctypes.c_double(0.0)
+    st = load().pd_solve_windows(plan, u0, f, nwin, u, mode, tol, maxit, restart,
+                                 ctypes.byref(it), ctypes.byref(rr))
+    return st, it.value, rr.value
+
+
 def pd1_launches(plan):
     v = ctypes.c_ulonglong(0)
     st = load().pd1_launches(plan, ctypes.byref(v))
@@ -536,6 +556,23 @@ class Plan:
             self._check(st, "pd_solve_host")
         return u_host, it, rel
 
+    def solve_windows(self, u0, nwin, f=None, u=None, mode=PD_STATIONARY, tol=1e-10, maxit=50,
+                      restart=30):
+        """nwin consecutive windows of the plan's nt steps (window w starts from
+        the last level of window w-1); returns (u [nwin, nt, S], total iterations,
+        largest relative residual)."""
+        import torch
+        self._check_t(u0, self.S)
+        if f is not None:
+            self._check_t(f, (nwin * self.nt + 1) * self.S)
+        u = torch.empty((nwin, self.nt, self.S), dtype=torch.float64, device=u0.device) \
+            if u is None else u
+        self._check_t(u, nwin * self.nt * self.S)
+        st, it, rel = pd_solve_windows(self._h, _ptr(u0), _ptr(f), nwin, _ptr(u), mode, tol,
+                                       maxit, restart)
+        self._check(st, "pd_solve_windows")
+        return u, it, rel
+
     def adjoint_solve(self, g, lam=None, mode=PD_STATIONARY, tol=1e-10, maxit=50, restart=30):
         import torch
         self._check_t(g)
@@ -628,6 +665,20 @@ class Plan1:
         b = torch.empty((self.nt, self.S), dtype=torch.float64, device=u0.device) if b is None else b
         self._check(pd1_build_rhs(self._h, _ptr(u0), _ptr(f), _ptr(b)), "pd1_build_rhs")
         return b
+
+    def solve_windows(self, u0, nwin, f=None, u=None, tol=0.0, max_refine=0):
+        """nwin consecutive windows (window w starts from the last level of
+        window w-1); returns (u [nwin, nt, S], total sweeps, largest relres)."""
+        import torch
+        self._check_t(u0, self.S)
+        if f is not None:
+            self._check_t(f, (nwin * self.nt + 1) * self.S)
+        u = torch.empty((nwin, self.nt, self.S), dtype=torch.float64, device=u0.device) \
+            if u is None else u
+        self._check_t(u, nwin * self.nt * self.S)
+        st, it, rel = pd1_solve_windows(self._h, _ptr(u0), _ptr(f), nwin, _ptr(u), tol, max_refine)
+        self._check(st, "pd1_solve_windows")
+        return u, it, rel
 
     def profile_sweep(self, b, u, reps=5):
         """Average ms of [step (a) + residual, step (b), step (c) + update]."""

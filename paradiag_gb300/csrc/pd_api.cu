@@ -1266,6 +1266,40 @@ pd_status pd_solve(pd_plan* p, const double* b, double* u, int mode, double tol,
   return solve_any(p, b, u, mode, tol, maxit, restart, iters, relres);
 }
 
+pd_status pd_solve_windows(pd_plan* p, const double* u0, const double* f, int nwin, double* u,
+                           int mode, double tol, int maxit, int restart, int* iters_total,
+                           double* relres_max) {
+  if (!p || !u0 || !u || nwin < 1) return set_err(p, PD_ERR_ARG, "bad argument");
+  if (p->scheme == PD_LEAPFROG)
+    return set_err(p, PD_ERR_UNSUPPORTED, "windowing needs a one-step scheme (theta-method)");
+  const size_t ns = NS(p);
+  const size_t S = (size_t)p->S;
+  if (!p->w64a) CHK(dalloc(p, (void**)&p->w64a, ns * sizeof(double)));
+  int total = 0;
+  double worst = 0.0;
+  for (int w = 0; w < nwin; ++w) {
+    double* uw = u + (size_t)w * ns;
+    const double* start = w == 0 ? u0 : uw - S;      // last time level of the previous window
+    const double* fw = f ? f + (size_t)w * p->nt * S : nullptr;
+    LK(launch_build_rhs(p->st, p->tb, p->scheme, p->nt, p->dt, start, nullptr, fw, p->w64a,
+                        p->stream));
+    CU(cudaMemsetAsync(uw, 0, ns * sizeof(double), p->stream));
+    int it = 0;
+    double rel = 0.0;
+    const pd_status st = solve_any(p, p->w64a, uw, mode, tol, maxit, restart, &it, &rel);
+    total += it;
+    worst = std::max(worst, rel);
+    if (st != PD_OK) {
+      if (iters_total) *iters_total = total;
+      if (relres_max) *relres_max = worst;
+      return st;
+    }
+  }
+  if (iters_total) *iters_total = total;
+  if (relres_max) *relres_max = worst;
+  return PD_OK;
+}
+
 pd_status pd_solve_host(pd_plan* p, const double* b_host, double* u_host, int mode, double tol,
                         int maxit, int restart, int* iters, double* relres) {
   if (!p || !b_host || !u_host) return set_err(p, PD_ERR_ARG, "null argument");

@@ -811,6 +811,45 @@ pd_status pd1_solve(pd1_plan* q, const double* b, double* u, double tol, int max
   return PD_OK;
 }
 
+pd_status pd1_solve_windows(pd1_plan* q, const double* u0, const double* f, int nwin, double* u,
+                            double tol, int max_refine, int* refinements_total,
+                            double* relres_max) {
+  if (!q || !u0 || !u || nwin < 1 || max_refine < 0 || !(tol >= 0.0)) return PD_ERR_ARG;
+  pd_plan* p = q->sp;
+  const size_t S = (size_t)p->S;
+  const size_t ns = (size_t)q->nt * S;
+  if (!p->w64a) {
+    cudaError_t e = cudaMalloc((void**)&p->w64a, ns * sizeof(double));
+    if (e != cudaSuccess) {
+      p->w64a = nullptr;
+      return p1_cuda(q, e, "cudaMalloc");
+    }
+  }
+  const P1Fwd a = fwd_args(q);
+  int total = 0;
+  double worst = 0.0;
+  for (int w = 0; w < nwin; ++w) {
+    double* uw = u + (size_t)w * ns;
+    const double* start = w == 0 ? u0 : uw - S;      // last time level of the previous window
+    const double* fw = f ? f + (size_t)w * q->nt * S : nullptr;
+    k_pd1_rhs<<<grid_of(a.S), P1_TB, 0, p->stream>>>(a, start, fw, p->w64a);
+    P1LK(cudaGetLastError());
+    int it = 0;
+    double rel = 0.0;
+    const pd_status st = pd1_solve(q, p->w64a, uw, tol, max_refine, &it, &rel);
+    total += it;
+    worst = std::max(worst, rel);
+    if (st != PD_OK) {
+      if (refinements_total) *refinements_total = total;
+      if (relres_max) *relres_max = worst;
+      return st;
+    }
+  }
+  if (refinements_total) *refinements_total = total;
+  if (relres_max) *relres_max = worst;
+  return PD_OK;
+}
+
 pd_status pd1_profile_sweep(pd1_plan* q, const double* b, double* u, int reps, float* ms) {
   if (!q || !b || !u || !ms || reps < 1) return PD_ERR_ARG;
   pd_plan* p = q->sp;
