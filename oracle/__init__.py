@@ -29,6 +29,9 @@ Modules
                 three-step solve and the exact solution by a sparse LU.
   windows       O8: windowing -- consecutive windows chained from the last
                 time level, each solved exactly.
+  control_wave  O9: optimal control of the wave equation (Section 4): the
+                saddle-point leap-frog system, the gamma-balanced block
+                circulant preconditioner by Theorem 4, flexible GMRES.
 
 Every function is pinned by a test in tests/test_oracle_*.py against a
 closed form, an invariant, a bound of the paper, a worked example the paper

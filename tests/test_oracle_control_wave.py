@@ -1,0 +1,105 @@
+"""Pins of O9, the ParaDiag-II preconditioner for the optimal control of the
+wave equation (Section 4), CPU only.
+
+The factorisation P = P~ (blockdiag(C2, C2^T) (x) I) (eq. 4.3), the per-frequency
+2 x 2 spectral decomposition of P~ (Theorem 4: real lam = d1/d2, eigenvalues
+lam +- i beta/|d2|, orthogonal eigenvector blocks, Cond_2(V) = 1), the
+preconditioner application against a sparse solve with P, the gamma balancing
+similarity, and the GMRES iteration counts printed in Table T2A.
+"""
+import json
+import os
+
+import numpy as np
+import pytest
+import scipy.sparse as sps
+import scipy.sparse.linalg as spla
+
+import workloads as W
+from oracle import control_wave as CW
+from oracle import operators as O
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def space(n):
+    return W.Space(dim=2, nx=n - 1, ny=n - 1, nu=1.0, bc_x=W.DIRICHLET, bc_y=W.DIRICHLET)
+
+
+@pytest.mark.parametrize("nt", [5, 9, 17])
+def test_factorisation_eq_4_3(nt):
+    dt, g = 2.0 / nt, 1e-4
+    _, _, c1, c2 = CW.time_blocks(nt, dt)
+    C1, C2 = CW.circulant(c1), CW.circulant(c2)
+    beta = dt * dt / np.sqrt(g)
+    C2i = np.linalg.inv(C2)
+    Pt = np.block([[C1 @ C2i, -beta * C2i.T], [beta * C2i, C1.T @ C2i.T]])
+    lhs = Pt @ np.block([[C2, np.zeros((nt, nt))], [np.zeros((nt, nt)), C2.T]])
+    ref = np.block([[C1, -beta * np.eye(nt)], [beta * np.eye(nt), C1.T]])
+    assert np.abs(lhs - ref).max() < 1e-12 * np.abs(ref).max()
+
+
+@pytest.mark.parametrize("nt", [5, 17, 33])
+def test_theorem4_block_decomposition(nt):
+    dt, g = 2.0 / nt, 1e-6
+    lam, s1, s2, Q, d2 = CW.block_eigen(nt, dt, g)
+    d1, _ = CW.spectra(nt, dt)
+    beta = dt * dt / np.sqrt(g)
+    assert np.abs((d1 / d2).imag).max() < 1e-12 * np.abs(d1 / d2).max()   # lam real
+    assert np.all(np.abs(d2) > 0)                                          # odd Nt
+    for k in range(nt):
+        M = np.array([[lam[k], -beta / np.conj(d2[k])], [beta / d2[k], lam[k]]])
+        D = np.diag([s1[k], s2[k]])
+        assert np.abs(M @ Q[k] - Q[k] @ D).max() < 1e-12 * np.abs(M).max()
+        assert abs(np.linalg.cond(Q[k]) - 1.0) < 1e-12                     # Cond_2(V) = 1
+    # the circulant spectra: C = F^* diag(d) F in the transform X_k = sum x_n w^{nk}
+    _, _, c1, c2 = CW.time_blocks(nt, dt)
+    x = W.uniform(W.SEED_BASE + 500, nt, -1, 1)
+    assert np.allclose(np.fft.fft(CW.circulant(c2) @ x), d2 * np.fft.fft(x), atol=1e-12)
+    assert np.allclose(np.fft.fft(CW.circulant(c2).T @ x), np.conj(d2) * np.fft.fft(x),
+                       atol=1e-12)
+
+
+def test_preconditioner_equals_sparse_solve():
+    sp = space(6)
+    K = O.stencil(sp)
+    nt, g = 9, 1e-4
+    dt = 2.0 / nt
+    P = CW.precond_matrix(nt, dt, g, K)
+    S = sp.size
+    r = W.uniform(W.SEED_BASE + 501, 2 * nt * S, -1, 1)
+    ref = spla.spsolve(P.tocsc(), r)
+    s1, s2 = CW.Preconditioner(nt, dt, g, K).apply(r[: nt * S].reshape(nt, S),
+                                                   r[nt * S:].reshape(nt, S))
+    got = np.concatenate([s1.reshape(-1), s2.reshape(-1)])
+    assert np.abs(got - ref).max() < 1e-11 * np.abs(ref).max()
+
+
+def test_balancing_similarity():
+    sp = space(5)
+    K = O.stencil(sp)
+    nt, g = 7, 1e-6
+    dt = 2.0 / nt
+    Ah = CW.saddle_matrix(nt, dt, g, K, balanced=False).toarray()
+    A = CW.saddle_matrix(nt, dt, g, K, balanced=True).toarray()
+    n = nt * sp.size
+    Sd = np.r_[np.full(n, np.sqrt(g)), np.ones(n)]
+    assert np.abs(Sd[:, None] * Ah / Sd[None, :] - A).max() < 1e-12 * np.abs(A).max()
+
+
+@pytest.mark.parametrize("mesh", [0, 1])
+def test_table_t2a_iterations(mesh):
+    gold = json.load(open(os.path.join(GOLDEN, "t2a_wave_control.json")))
+    n = (16, 32)[mesh]
+    nt = n + 1
+    sp = space(n)
+    K = O.stencil(sp)
+    ue, pe = CW.exact_solution(sp, nt, 2.0)
+    for g, it_ref in zip(gold["gammas"], gold["iterations"][mesh]):
+        Ah = CW.saddle_matrix(nt, 2.0 / nt, g, K, balanced=False)
+        rhs = Ah @ np.concatenate([ue.reshape(-1), pe.reshape(-1)])
+        m = nt * sp.size
+        u, p, it, rel = CW.solve(sp, nt, 2.0, g, rhs[:m].reshape(nt, -1),
+                                 rhs[m:].reshape(nt, -1), tol=1e-7, K=K)
+        assert rel <= 1e-7
+        assert it == it_ref, (n, g, it, it_ref)
