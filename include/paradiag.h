@@ -391,6 +391,45 @@ PD_API pd_status pdh_profile_sweep(pdh_plan* plan, const double* b, double* u, i
 PD_API pd_status pdh_launches(const pdh_plan* plan, unsigned long long* count);
 PD_API const char* pdh_last_error(const pdh_plan* plan);
 
+/* ---------------------------------------------------------------------------
+ * ParaDiag-II for the optimal control of the wave equation (Section 4): the
+ * saddle-point all-at-once system of the implicit leap-frog scheme (state u,
+ * adjoint p), scaled by dt^2 as in the section,
+ *   A^ = [[T1, -dt^2 Ih / gamma], [dt^2 Ic, T1^T]] (x) I + blockdiag(T2, T2^T) (x) K,
+ * T1 = lower Toeplitz (1, -2, 1), T2 = lower Toeplitz (1, 0, 1) dt^2/2 (dt^2
+ * times B1, B2 of eq. 3.2b), Ih = diag(1/2, 1, ..., 1), Ic = diag(1, ..., 1, 1/2),
+ * K the spatial operator of sp (the negative Laplacian for nu = 1, no
+ * advection).  Solved by flexible GMRES on the gamma-balanced system
+ * (unknowns (gamma^{1/2} u, p)) with the block circulant preconditioner P of
+ * the section, applied through Theorem 4 (per frequency a 2 x 2 block with
+ * orthogonal eigenvectors: Cond_2(V) = 1).  Vectors are [2][nt][S] device FP64:
+ * the state field, then the adjoint field.
+ * --------------------------------------------------------------------------- */
+typedef struct pdc_plan pdc_plan;
+
+/* Plan for nt steps of dt = T/nt (nt >= 3; nt divisible by 4 makes the
+ * circulant of T2 singular: PD_ERR_UNSUPPORTED) and regularisation gamma > 0.
+ * precision PD_FP64: the preconditioner in FP64; PD_MIXED: in FP32 (the
+ * tensor-core x-transform in 2D); the Krylov vectors and A are FP64 in both. */
+PD_API pd_status pdc_plan_create(const pd_space* sp, int nt, double T, double gamma,
+                                 int precision, void* stream, pdc_plan** out);
+PD_API pd_status pdc_plan_destroy(pdc_plan* plan);
+
+/* y = A x for the balanced system A = S A^ S^{-1}, S = diag(gamma^{1/2} I, I). */
+PD_API pd_status pdc_apply_A(pdc_plan* plan, const double* x, double* y);
+
+/* z = P^{-1} r (the balanced preconditioner, Theorem 4). */
+PD_API pd_status pdc_apply_precond(pdc_plan* plan, const double* r, double* z);
+
+/* Solve A^ (u, p) = (f, g): FGMRES(restart) on the balanced system from a zero
+ * guess, stopping when the balanced relative residual is <= tol or after maxit
+ * iterations (PD_ERR_NOT_CONVERGED, x still written).  b = (f, g), x = (u, p);
+ * restart in [0, 64] (0: 30). */
+PD_API pd_status pdc_solve(pdc_plan* plan, const double* b, double* x, double tol, int maxit,
+                           int restart, int* iters, double* relres);
+PD_API pd_status pdc_launches(const pdc_plan* plan, unsigned long long* count);
+PD_API const char* pdc_last_error(const pdc_plan* plan);
+
 PD_API const char* pd_status_string(pd_status s);
 PD_API const char* pd_last_error(const pd_plan* plan);
 

@@ -108,6 +108,14 @@ _SIGS = {
     "pdh_profile_sweep": (ctypes.c_int, [_P, _P, _P, ctypes.c_int, ctypes.POINTER(ctypes.c_float)]),
     "pdh_launches": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_ulonglong)]),
     "pdh_last_error": (ctypes.c_char_p, [_P]),
+    "pdc_plan_create": (ctypes.c_int, [ctypes.POINTER(pd_space), ctypes.c_int, ctypes.c_double,
+                                       ctypes.c_double, ctypes.c_int, _P, ctypes.POINTER(_P)]),
+    "pdc_plan_destroy": (ctypes.c_int, [_P]),
+    "pdc_apply_A": (ctypes.c_int, [_P, _P, _P]),
+    "pdc_apply_precond": (ctypes.c_int, [_P, _P, _P]),
+    "pdc_solve": (ctypes.c_int, [_P, _P, _P, ctypes.c_double, ctypes.c_int, ctypes.c_int, _I, _D]),
+    "pdc_launches": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_ulonglong)]),
+    "pdc_last_error": (ctypes.c_char_p, [_P]),
     "pd_status_string": (ctypes.c_char_p, [ctypes.c_int]),
     "pd_last_error": (ctypes.c_char_p, [_P]),
 }
@@ -415,6 +423,42 @@ def pdh_launches(plan):
 
 def pdh_last_error(plan) -> str:
     return load().pdh_last_error(plan).decode()
+
+
+def pdc_plan_create(space: pd_space, nt, T, gamma, precision, stream):
+    out = _P()
+    st = load().pdc_plan_create(ctypes.byref(space), nt, T, gamma, precision, _P(stream),
+                                ctypes.byref(out))
+    return st, out.value
+
+
+def pdc_plan_destroy(plan):
+    return load().pdc_plan_destroy(plan)
+
+
+def pdc_apply_A(plan, x, y):
+    return load().pdc_apply_A(plan, x, y)
+
+
+def pdc_apply_precond(plan, r, z):
+    return load().pdc_apply_precond(plan, r, z)
+
+
+def pdc_solve(plan, b, x, tol, maxit, restart):
+    it = ctypes.c_int(0)
+    rr = ctypes.c_double(0.0)
+    st = load().pdc_solve(plan, b, x, tol, maxit, restart, ctypes.byref(it), ctypes.byref(rr))
+    return st, it.value, rr.value
+
+
+def pdc_launches(plan):
+    v = ctypes.c_ulonglong(0)
+    st = load().pdc_launches(plan, ctypes.byref(v))
+    return st, v.value
+
+
+def pdc_last_error(plan) -> str:
+    return load().pdc_last_error(plan).decode()
 
 
 def _space_of(space) -> pd_space:
@@ -792,6 +836,76 @@ class PlanHybrid:
         return u, it, rel
 
 
+class PlanControl:
+    """A plan for the optimal control of the wave equation (Section 4): the
+    leap-frog saddle-point system in (u, p), FGMRES with the gamma-balanced
+    block circulant preconditioner.  Tensors are CUDA float64 of shape
+    (2, nt, S): the state field, then the adjoint field."""
+
+    def __init__(self, space, nt, T, gamma, precision=PD_FP64, stream=None):
+        import torch
+        self.space = _space_of(space)
+        self.nt, self.T, self.gamma, self.precision = int(nt), float(T), float(gamma), int(precision)
+        self.S = self.space.nx * (self.space.ny if self.space.dim == 2 else 1)
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        st, h = pdc_plan_create(self.space, self.nt, self.T, self.gamma, self.precision,
+                                self.stream.cuda_stream)
+        if st != PD_OK:
+            raise PDError(st, "pdc_plan_create")
+        self._h = h
+
+    def close(self):
+        if getattr(self, "_h", None):
+            pdc_plan_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _check(self, st, what):
+        if st != PD_OK:
+            raise PDError(st, f"{what}: {pdc_last_error(self._h)}")
+
+    def _check_t(self, t):
+        import torch
+        n = 2 * self.nt * self.S
+        if not (t.is_cuda and t.dtype == torch.float64 and t.is_contiguous() and t.numel() == n):
+            raise ValueError(f"expected a contiguous CUDA float64 tensor with {n} elements")
+
+    def launches(self):
+        st, v = pdc_launches(self._h)
+        self._check(st, "pdc_launches")
+        return v
+
+    def apply_A(self, x, y=None):
+        import torch
+        self._check_t(x)
+        y = torch.empty_like(x) if y is None else y
+        self._check(pdc_apply_A(self._h, _ptr(x), _ptr(y)), "pdc_apply_A")
+        return y
+
+    def apply_precond(self, r, z=None):
+        import torch
+        self._check_t(r)
+        z = torch.empty_like(r) if z is None else z
+        self._check(pdc_apply_precond(self._h, _ptr(r), _ptr(z)), "pdc_apply_precond")
+        return z
+
+    def solve(self, b, x=None, tol=1e-7, maxit=100, restart=30, allow_not_converged=False):
+        """(u, p) for the right-hand side (f, g); returns (x, iterations, relres)."""
+        import torch
+        self._check_t(b)
+        x = torch.empty_like(b) if x is None else x
+        self._check_t(x)
+        st, it, rel = pdc_solve(self._h, _ptr(b), _ptr(x), tol, maxit, restart)
+        if not (st == PD_OK or (allow_not_converged and st == PD_ERR_NOT_CONVERGED)):
+            self._check(st, "pdc_solve")
+        return x, it, rel
+
+
 class Batch:
     """Many independent 1D problems solved together (packed FP64 arrays).
 
@@ -896,6 +1010,6 @@ class _Lazy:
 
 PDSolve = _Lazy()
 
-__all__ = ["build", "lib_path", "load", "Plan", "Plan1", "PlanHybrid", "Batch", "PDSolve", "PDError", "pd_space",
+__all__ = ["build", "lib_path", "load", "Plan", "Plan1", "PlanHybrid", "PlanControl", "Batch", "PDSolve", "PDError", "pd_space",
            "pd_problem",
            "exported_symbols"] + [k for k in _SIGS]

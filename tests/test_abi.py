@@ -8,7 +8,7 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 def header_symbols():
     txt = open(os.path.join(ROOT, "include", "paradiag.h")).read()
-    return re.findall(r"PD_API\s+[\w\s\*]+?\b(pd[1h]?_\w+)\s*\(", txt)
+    return re.findall(r"PD_API\s+[\w\s\*]+?\b(pd[1hc]?_\w+)\s*\(", txt)
 
 
 def test_header_declares_the_boundary():
@@ -77,3 +77,13 @@ def test_pdh_plan_create_rejects_bad_arguments_without_gpu():
     assert pd.pdh_plan_create(sp, 5000, 0.01, 0, None)[0] == pd.PD_ERR_UNSUPPORTED
     assert pd.pdh_plan_create(sp, 16, 0.0, 0, None)[0] == pd.PD_ERR_ARG          # dt
     assert pd.pdh_plan_create(sp, 16, 0.01, 2, None)[0] == pd.PD_ERR_ARG         # precision
+
+
+def test_pdc_plan_create_rejects_bad_arguments_without_gpu():
+    import paradiag_gb300 as pd
+    pd.build()
+    sp = pd.pd_space(2, 15, 15, 1.0, 0.0, 0.0, 0, 0, 1.0, 1.0)
+    assert pd.pdc_plan_create(sp, 2, 2.0, 1e-4, 0, None)[0] == pd.PD_ERR_ARG          # nt
+    assert pd.pdc_plan_create(sp, 16, 2.0, 1e-4, 0, None)[0] == pd.PD_ERR_UNSUPPORTED  # 4 | nt
+    assert pd.pdc_plan_create(sp, 17, 2.0, 0.0, 0, None)[0] == pd.PD_ERR_ARG          # gamma
+    assert pd.pdc_plan_create(sp, 17, -1.0, 1e-4, 0, None)[0] == pd.PD_ERR_ARG        # T

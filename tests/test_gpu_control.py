@@ -1,0 +1,126 @@
+"""GPU parity of the wave-equation optimal control solver (Section 4) against
+the oracle (O9), through the C ABI: the balanced saddle-point operator, the
+block circulant preconditioner of Theorem 4, and FGMRES reproducing the
+iteration counts of Table T2A.  Right-hand sides are the saddle-point
+operator applied to the exact optimal pair on the grid."""
+import json
+import os
+
+import numpy as np
+import pytest
+
+import workloads as W
+from helpers import EPS32, dev, host, lib_ready, space_dict
+from oracle import control_wave as CW
+from oracle import operators as O
+
+pytestmark = pytest.mark.gpu
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+@pytest.fixture(scope="module")
+def pd():
+    return lib_ready()
+
+
+def space(n):
+    return W.Space(dim=2, nx=n - 1, ny=n - 1, nu=1.0, bc_x=W.DIRICHLET, bc_y=W.DIRICHLET)
+
+
+def plan(pd, n, nt, g, prec):
+    return pd.PlanControl(space_dict(space(n)), nt, 2.0, g, prec)
+
+
+@pytest.mark.parametrize("n,nt", [(8, 9), (12, 7)])
+def test_control_apply_matches_oracle(pd, n, nt):
+    sp = space(n)
+    K = O.stencil(sp)
+    g = 1e-4
+    A = CW.saddle_matrix(nt, 2.0 / nt, g, K, balanced=True)
+    x = W.uniform(W.SEED_BASE + 600, 2 * nt * sp.size, -1, 1)
+    pl = plan(pd, n, nt, g, 0)
+    y = host(pl.apply_A(dev(x))).reshape(-1)
+    ref = A @ x
+    assert np.abs(y - ref).max() <= 1e-13 * np.abs(ref).max()
+    pl.close()
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+@pytest.mark.parametrize("n,nt,g", [(8, 9, 1e-2), (16, 17, 1e-6), (12, 33, 1e-10)])
+def test_control_precond_matches_oracle(pd, prec, n, nt, g):
+    sp = space(n)
+    K = O.stencil(sp)
+    S = sp.size
+    r = W.uniform(W.SEED_BASE + 601, 2 * nt * S, -1, 1)
+    s1, s2 = CW.Preconditioner(nt, 2.0 / nt, g, K).apply(r[: nt * S].reshape(nt, S),
+                                                        r[nt * S:].reshape(nt, S))
+    ref = np.concatenate([s1.reshape(-1), s2.reshape(-1)])
+    pl = plan(pd, n, nt, g, prec)
+    z = host(pl.apply_precond(dev(r))).reshape(-1)
+    tol = 1e-11 if prec == 0 else 1e3 * EPS32
+    assert np.abs(z - ref).max() <= tol * np.abs(ref).max()
+    pl.close()
+
+
+def exact_rhs(n, nt, g):
+    sp = space(n)
+    K = O.stencil(sp)
+    ue, pe = CW.exact_solution(sp, nt, 2.0)
+    Ah = CW.saddle_matrix(nt, 2.0 / nt, g, K, balanced=False)
+    x = np.concatenate([ue.reshape(-1), pe.reshape(-1)])
+    return Ah, x, Ah @ x
+
+
+@pytest.mark.parametrize("mesh", [0, 1])
+@pytest.mark.parametrize("prec", [0, 1])
+def test_control_table_t2a_iterations(pd, mesh, prec):
+    gold = json.load(open(os.path.join(GOLDEN, "t2a_wave_control.json")))
+    n = (16, 32)[mesh]
+    nt = n + 1
+    for g, it_ref in zip(gold["gammas"], gold["iterations"][mesh]):
+        Ah, xe, b = exact_rhs(n, nt, g)
+        pl = plan(pd, n, nt, g, prec)
+        x, it, rel = pl.solve(dev(b), tol=1e-7, maxit=200)
+        assert rel <= 1e-7
+        xg = host(x).reshape(-1)
+        # the balanced relative residual, recomputed with the oracle's operator
+        sg = np.sqrt(g)
+        m = nt * space(n).size
+        Sd = np.r_[np.full(m, sg), np.ones(m)]
+        rb = Sd * (b - Ah @ xg)
+        assert np.linalg.norm(rb) / np.linalg.norm(Sd * b) <= 1.5e-7
+        if prec == 0:
+            assert it == it_ref, (n, g, it, it_ref)
+        elif g <= 1e-6:
+            # the FP32 preconditioner (mixed path) keeps the table's counts only
+            # for small gamma: at tol 1e-7 its rounding (~eps32 times the
+            # conditioning of P) limits the contraction for gamma >= 1e-4, as a
+            # CPU simulation of the same FP32 steps shows (66 / 9 iterations at
+            # gamma = 1e-2 / 1e-4 on the (16, 16, 17) mesh)
+            assert abs(it - it_ref) <= 1, (n, g, it, it_ref)
+        pl.close()
+
+
+def test_control_full_size_gamma_1e4(pd):
+    # the largest mesh of Table T2A, (256, 256, 257) at gamma = 1e-4: 5 GMRES
+    # iterations in the table (FP64 preconditioner); right-hand side from the
+    # exact pair through the GPU operator (the operator itself is checked
+    # against the oracle above)
+    import torch
+    n, nt, g = 256, 257, 1e-4
+    sp = space(n)
+    ue, pe = CW.exact_solution(sp, nt, 2.0)
+    pl = plan(pd, n, nt, g, 0)
+    sg = np.sqrt(g)
+    xb = dev(np.concatenate([sg * ue.reshape(-1), pe.reshape(-1)]))
+    bb = pl.apply_A(xb)                     # balanced rhs
+    m = nt * sp.size
+    b = bb.clone()
+    b[:m] /= sg                             # unbalanced (f, g)
+    x, it, rel = pl.solve(b, tol=1e-7, restart=20)
+    assert rel <= 1e-7 and it == 5
+    xs = x.clone()
+    xs[:m] *= sg
+    r = bb - pl.apply_A(xs)
+    assert float(torch.linalg.norm(r) / torch.linalg.norm(bb)) <= 1.5e-7
+    pl.close()
