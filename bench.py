@@ -49,6 +49,9 @@ def parse():
     ap.add_argument("--pd1-kernels", action="store_true",
                     help="only the ParaDiag-I mixed kernel profile (ncu driver)")
     ap.add_argument("--no-hybrid", action="store_true", help="skip the hybrid ParaDiag-I leg")
+    ap.add_argument("--no-control", action="store_true", help="skip the optimal-control leg")
+    ap.add_argument("--control-only", action="store_true",
+                    help="only the optimal-control leg (one JSON object)")
     ap.add_argument("--hybrid-only", action="store_true",
                     help="only the hybrid ParaDiag-I leg (one JSON object)")
     ap.add_argument("--hybrid-kernels", action="store_true",
@@ -461,6 +464,60 @@ def hybrid_leg(pd, torch, dev, args):
             "kernels": hybrid_kernel_profile(pd, torch, dev, (pd.PD_MIXED, pd.PD_FP64))}
 
 
+def control_leg(pd, torch, dev, args):
+    """Optimal control of the 2D wave equation (Section 4) on the largest mesh of
+    Table T2A, (256, 256, 257): 255 x 255 interior points, Nt = 257, T = 2,
+    gamma in {1e-2, 1e-4, 1e-8}; FGMRES(40) on the balanced saddle-point system
+    with the Theorem 4 preconditioner (FP64; FP32 as well at gamma = 1e-8),
+    tol 1e-7, zero initial guess.
+    The right-hand side is the saddle-point operator applied to the exact
+    optimal pair on the grid.  The table's CPU seconds are quoted as context."""
+    import numpy as np
+    import workloads as W
+    n, nt, T = 256, 257, 2.0
+    sp = W.Space(dim=2, nx=n - 1, ny=n - 1, nu=1.0, bc_x=W.DIRICHLET, bc_y=W.DIRICHLET)
+    space = dict(dim=2, nx=n - 1, ny=n - 1, nu=1.0, bc_x=0, bc_y=0)
+    X, Y = sp.mesh()
+    s = (np.sin(np.pi * X) * np.sin(np.pi * Y)).reshape(-1)
+    t = (T / nt) * np.arange(1, nt + 1)
+    stream = torch.cuda.current_stream()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    table = [(1e-2, pd.PD_FP64, 17, 226.6), (1e-4, pd.PD_FP64, 5, 59.6),
+             (1e-8, pd.PD_FP64, 5, 61.0), (1e-8, pd.PD_MIXED, 5, 61.0)]
+    rows = []
+    for g, prec, it_paper, cpu_paper in table:
+        pl = pd.PlanControl(space, nt, T, g, prec, stream)
+        sg = np.sqrt(g)
+        xb = torch.from_numpy(np.concatenate([sg * np.outer(np.exp(t), s).reshape(-1),
+                                              np.outer((t - T) ** 2, s).reshape(-1)])).to(dev)
+        b = pl.apply_A(xb)
+        m = nt * sp.size
+        b[:m] /= sg
+        x = torch.empty_like(b)
+        pl.solve(b, x, tol=1e-7, maxit=100, restart=40)
+        k = max(1, min(args.steps, 3))
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(k):
+            _, it, rel = pl.solve(b, x, tol=1e-7, maxit=100, restart=40)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / k
+        x[:m] *= sg
+        err = float(torch.linalg.norm(x - xb) / torch.linalg.norm(xb))
+        rows.append({"gamma": g, "preconditioner": "fp64" if prec == pd.PD_FP64 else "fp32",
+                     "ms_per_solve": ms, "gmres_iterations": it, "relres": rel,
+                     "rel_error_vs_exact_pair": err, "unknowns": 2 * m,
+                     "value": 2 * m / (ms / 1e3), "unit": UNIT,
+                     "paper_iterations": it_paper, "paper_cpu_seconds_context": cpu_paper})
+        pl.close()
+    return {"workload": "control_wave2d_256x256x257: optimal control of u_tt - Lap u = f + "
+                        "control on (0,1)^2 x (0,2), leap-frog saddle point (Table T2A's "
+                        "largest mesh)",
+            "solves": rows}
+
+
 def run_sweep(pd, torch, dev):
     """Per-kernel time and algorithmic HBM throughput of one mixed iteration on
     1D advection-diffusion problems (nu = 1e-2, a = 1, BE, alpha = 1e-2) of
@@ -553,6 +610,12 @@ def main():
     b = plan.build_rhs(u0)
     u = torch.zeros_like(b)
     torch.cuda.synchronize()
+    if args.control_only:
+        out = control_leg(pd, torch, dev, args)
+        if rank == 0:
+            print(json.dumps(out), flush=True)
+        plan.close()
+        return
     if args.hybrid_kernels or args.hybrid_only:
         out = (hybrid_kernel_profile(pd, torch, dev, (pd.PD_MIXED,)) if args.hybrid_kernels
                else hybrid_leg(pd, torch, dev, args))
@@ -682,6 +745,9 @@ def main():
     hybrid = None
     if not args.no_hybrid:
         hybrid = hybrid_leg(pd, torch, dev, args)
+    control = None
+    if not args.no_control:
+        control = control_leg(pd, torch, dev, args)
 
     err = err64 = None
     if rank == 0 and not args.no_check:
@@ -723,6 +789,7 @@ def main():
                "batched": batched,
                "paradiag1": pd1,
                "paradiag1_hybrid": hybrid,
+               "optimal_control_wave": control,
                "gpu_launches": launches}
         print(json.dumps(out), flush=True)
     plan.close()
