@@ -129,6 +129,20 @@ PD_API pd_status pd_build_rhs(pd_plan* plan, const double* u0, const double* u1,
 PD_API pd_status pd_solve(pd_plan* plan, const double* b, double* u, int mode, double tol, int maxit,
                    int restart, int* iters, double* relres);
 
+/* The stationary solve of pd_solve (mode PD_STATIONARY) without waiting for
+ * it: on mixed plans the whole solve (entry split, the CUDA graph of the
+ * iteration, exit) is enqueued on the plan's stream and the call returns at
+ * once, so consecutive solves run back to back on the GPU; plans without a
+ * graph (FP64) solve synchronously.  u must not be read, and b and u must not
+ * be changed, before pd_solve_result returns.  No paper counterpart. */
+PD_API pd_status pd_solve_async(pd_plan* plan, const double* b, double* u, double tol, int maxit);
+
+/* Waits for the plan's queued asynchronous solves and returns the status,
+ * iterations and relative residual of the last one (iters, relres may be
+ * NULL); the launch counter adds the kernels of every queued solve, counted
+ * as the last one's. */
+PD_API pd_status pd_solve_result(pd_plan* plan, int* iters, double* relres);
+
 /* The same solve with HOST buffers: copies b and the initial guess to the
  * device, solves, and copies u back (all on the plan's stream). */
 PD_API pd_status pd_solve_host(pd_plan* plan, const double* b_host, double* u_host, int mode,

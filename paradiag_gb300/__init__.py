@@ -57,6 +57,8 @@ _SIGS = {
     "pd_build_rhs": (ctypes.c_int, [_P, _P, _P, _P, _P]),
     "pd_solve": (ctypes.c_int, [_P, _P, _P, ctypes.c_int, ctypes.c_double, ctypes.c_int,
                                 ctypes.c_int, _I, _D]),
+    "pd_solve_async": (ctypes.c_int, [_P, _P, _P, ctypes.c_double, ctypes.c_int]),
+    "pd_solve_result": (ctypes.c_int, [_P, _I, _D]),
     "pd_solve_host": (ctypes.c_int, [_P, _P, _P, ctypes.c_int, ctypes.c_double, ctypes.c_int,
                                      ctypes.c_int, _I, _D]),
     "pd_adjoint_solve": (ctypes.c_int, [_P, _P, _P, ctypes.c_int, ctypes.c_double, ctypes.c_int,
@@ -284,6 +286,17 @@ def _solve_call(fn, plan, b, u, mode, tol, maxit, restart):
 
 def pd_solve(plan, b, u, mode, tol, maxit, restart):
     return _solve_call(load().pd_solve, plan, b, u, mode, tol, maxit, restart)
+
+
+def pd_solve_async(plan, b, u, tol, maxit):
+    return load().pd_solve_async(plan, b, u, tol, maxit)
+
+
+def pd_solve_result(plan):
+    it = ctypes.c_int(0)
+    rr = ctypes.c_double(0.0)
+    st = load().pd_solve_result(plan, ctypes.byref(it), ctypes.byref(rr))
+    return st, it.value, rr.value
 
 
 def pd_solve_host(plan, b, u, mode, tol, maxit, restart):
@@ -593,6 +606,19 @@ class Plan:
         if not (st == PD_OK or (allow_not_converged and st == PD_ERR_NOT_CONVERGED)):
             self._check(st, "pd_solve")
         return u, it, rel
+
+    def solve_async(self, b, u, tol=1e-10, maxit=50):
+        """Enqueue a stationary solve (no host wait on mixed plans); read the
+        outcome with result()."""
+        self._check_t(b); self._check_t(u)
+        self._check(pd_solve_async(self._h, _ptr(b), _ptr(u), tol, maxit), "pd_solve_async")
+
+    def result(self, allow_not_converged=False):
+        """(iterations, relative residual) of the last asynchronous solve."""
+        st, it, rel = pd_solve_result(self._h)
+        if not (st == PD_OK or (allow_not_converged and st == PD_ERR_NOT_CONVERGED)):
+            self._check(st, "pd_solve_result")
+        return it, rel
 
     def solve_host(self, b_host, u_host, mode=PD_STATIONARY, tol=1e-10, maxit=50, restart=30):
         st, it, rel = pd_solve_host(self._h, _ptr(b_host), _ptr(u_host), mode, tol, maxit, restart)

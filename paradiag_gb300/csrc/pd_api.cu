@@ -36,7 +36,8 @@ struct SolveGraph {
   cudaGraphExec_t ge = nullptr;
   cudaStream_t cs = nullptr;
   LoopState* dst = nullptr;   // device loop state
-  LoopState* hst = nullptr;   // pinned host copy
+  LoopState* res = nullptr;   // pinned copy of the final state of the last solve
+  int pending = 0;            // solves enqueued since the last finish
   int update_kernels = 0;     // kernels in one update (IF body)
 };
 
@@ -46,7 +47,7 @@ void destroy_graph(SolveGraph* G) {
   if (G->g) cudaGraphDestroy(G->g);
   if (G->cs) cudaStreamDestroy(G->cs);
   if (G->dst) cudaFree(G->dst);
-  if (G->hst) cudaFreeHost(G->hst);
+  if (G->res) cudaFreeHost(G->res);
   delete G;
 }
 
@@ -400,6 +401,30 @@ __global__ void k_loop_check(LoopState* st, double* dsc, const int* flag,
   cudaGraphSetConditional(hw, stop ? 0u : 1u);
 }
 
+// start of a graph solve: the loop state set on the device (no host buffer
+// that a queued copy could still be reading)
+__global__ void k_loop_init(LoopState* st, double tol, double s_scale, int maxit) {
+  LoopState s;
+  memset(&s, 0, sizeof(s));
+  s.tol = tol;
+  s.s_scale = s_scale;
+  s.prev_rel = -1.0;
+  s.maxit = maxit;
+  s.kmode = FWD_RESIDUAL;
+  *st = s;
+}
+
+// end of a graph solve: u = hi + lo of the double-float iterate, or zero when
+// the right-hand side was zero (decided on the device)
+__global__ void k_loop_exit(const LoopState* st, const float2* U, double* u, size_t n) {
+  const bool zero = st->status == LS_ZERO_RHS;
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (size_t)gridDim.x * blockDim.x) {
+    const float2 v = U[i];
+    u[i] = zero ? 0.0 : double_from_float(v.x) + double_from_float(v.y);
+  }
+}
+
 // the leaf node of a graph built by one stream capture (a chain)
 cudaGraphNode_t graph_leaf(cudaGraph_t g) {
   size_t n = 0;
@@ -416,7 +441,7 @@ cudaGraphNode_t graph_leaf(cudaGraph_t g) {
 pd_status build_graph_impl(pd_plan* p, SolveGraph* G) {
   CU(cudaStreamCreateWithFlags(&G->cs, cudaStreamNonBlocking));
   CU(cudaMalloc(&G->dst, sizeof(LoopState)));
-  CU(cudaMallocHost(&G->hst, sizeof(LoopState)));
+  CU(cudaMallocHost(&G->res, sizeof(LoopState)));
   CU(cudaGraphCreate(&G->g, 0));
   cudaGraphConditionalHandle hw, hif;
   CU(cudaGraphConditionalHandleCreate(&hw, G->g, 1u, cudaGraphCondAssignDefault));
@@ -518,30 +543,32 @@ SolveGraph* plan_graph(pd_plan* p) {
   return G;
 }
 
-pd_status solve_stationary_graph(pd_plan* p, SolveGraph* G, const double* b, double* u,
-                                 double tol, int maxit, int* iters, double* relres) {
+// Enqueue one graph solve (entry split, loop-state init, the graph, exit);
+// the final loop state is copied to G->res.  No host synchronisation.
+pd_status enqueue_graph_solve(pd_plan* p, SolveGraph* G, const double* b, double* u, double tol,
+                              int maxit) {
   const size_t ns = NS(p);
   CU(cudaMemsetAsync(p->dsc, 0, 2 * sizeof(double), p->stream));
   CU(cudaMemsetAsync(p->dflag, 0, sizeof(int), p->stream));
   LK(launch_entry_df(u, b, p->s_scale, p->Udf, p->Bdf, ns, p->dsc, p->stream));
-  LoopState* h = G->hst;
-  memset(h, 0, sizeof(LoopState));
-  h->tol = tol;
-  h->s_scale = p->s_scale;
-  h->prev_rel = -1.0;
-  h->maxit = maxit;
-  h->kmode = FWD_RESIDUAL;
-  CU(cudaMemcpyAsync(G->dst, h, sizeof(LoopState), cudaMemcpyHostToDevice, p->stream));
+  k_loop_init<<<1, 1, 0, p->stream>>>(G->dst, tol, p->s_scale, maxit);
+  LK(cudaGetLastError());
   CU(cudaGraphLaunch(G->ge, p->stream));
-  CU(cudaMemcpyAsync(h, G->dst, sizeof(LoopState), cudaMemcpyDeviceToHost, p->stream));
+  const int grid = (int)std::min<size_t>((ns + 255) / 256, (size_t)152 * 16);
+  k_loop_exit<<<grid, 256, 0, p->stream>>>(G->dst, p->Udf, u, ns);
+  LK(cudaGetLastError());
+  CU(cudaMemcpyAsync(G->res, G->dst, sizeof(LoopState), cudaMemcpyDeviceToHost, p->stream));
+  ++G->pending;
+  return PD_OK;
+}
+
+// Wait for the queued graph solves and report the last one.
+pd_status finish_graph_solves(pd_plan* p, SolveGraph* G, int* iters, double* relres) {
   CU(cudaStreamSynchronize(p->stream));
-  p->launches += (unsigned long long)h->n_body * 2 + (unsigned long long)h->n_update * G->update_kernels;
-  if (h->status == LS_ZERO_RHS) {
-    CU(cudaMemsetAsync(u, 0, ns * sizeof(double), p->stream));
-  } else {
-    LK(launch_from_df(p->Udf, u, ns, p->stream));
-  }
-  CU(cudaStreamSynchronize(p->stream));
+  const LoopState* h = G->res;
+  p->launches += (unsigned long long)G->pending *
+                 ((unsigned long long)h->n_body * 2 + (unsigned long long)h->n_update * G->update_kernels);
+  G->pending = 0;
   if (iters) *iters = h->it;
   if (relres) *relres = h->rel;
   switch (h->status) {
@@ -552,6 +579,12 @@ pd_status solve_stationary_graph(pd_plan* p, SolveGraph* G, const double* b, dou
     case LS_NONFINITE: return set_err(p, PD_ERR_NONFINITE, "non-finite value in the solver");
     default: return set_err(p, PD_ERR_CUDA, "solver graph ended without a decision");
   }
+}
+
+pd_status solve_stationary_graph(pd_plan* p, SolveGraph* G, const double* b, double* u,
+                                 double tol, int maxit, int* iters, double* relres) {
+  CHK(enqueue_graph_solve(p, G, b, u, tol, maxit));
+  return finish_graph_solves(p, G, iters, relres);
 }
 
 pd_status solve_stationary(pd_plan* p, const double* b, double* u, double tol, int maxit,
@@ -1298,6 +1331,27 @@ pd_status pd_solve_windows(pd_plan* p, const double* u0, const double* f, int nw
   if (iters_total) *iters_total = total;
   if (relres_max) *relres_max = worst;
   return PD_OK;
+}
+
+pd_status pd_solve_async(pd_plan* p, const double* b, double* u, double tol, int maxit) {
+  if (!p || !b || !u) return set_err(p, PD_ERR_ARG, "null argument");
+  if (!(tol >= 0.0) || maxit < 0) return set_err(p, PD_ERR_ARG, "tol must be >= 0 and maxit >= 0");
+  if (!p->fp64) {
+    SolveGraph* G = plan_graph(p);
+    if (G) return enqueue_graph_solve(p, G, b, u, tol, maxit);
+  }
+  // no graph (FP64 plans): the synchronous host loop; its result is kept for
+  // pd_solve_result
+  p->async_status = solve_stationary(p, b, u, tol, maxit, &p->async_iters, &p->async_relres);
+  return PD_OK;
+}
+
+pd_status pd_solve_result(pd_plan* p, int* iters, double* relres) {
+  if (!p) return PD_ERR_ARG;
+  if (p->graph && p->graph->pending > 0) return finish_graph_solves(p, p->graph, iters, relres);
+  if (iters) *iters = p->async_iters;
+  if (relres) *relres = p->async_relres;
+  return p->async_status;
 }
 
 pd_status pd_solve_host(pd_plan* p, const double* b_host, double* u_host, int mode, double tol,

@@ -58,6 +58,10 @@ struct pd_plan {
   // graph_state 0 untried, 1 ready, -1 unavailable: the host loop runs)
   struct SolveGraph* graph = nullptr;
   int graph_state = 0;
+  // result of the last pd_solve_async that ran synchronously (no graph)
+  pd_status async_status = PD_OK;
+  int async_iters = 0;
+  double async_relres = 0.0;
   size_t bytes = 0;
   unsigned long long launches = 0;
   char msg[256] = {0};

@@ -141,3 +141,25 @@ def test_plan_autotuner_choices(pd):
     assert plan64.tuning()[1] == 1 << int(np.ceil(np.log2(-(-pb.space.ny // 16))))
     plan64.close()
 
+
+
+def test_async_solves_match_synchronous(pd):
+    # queued solves on one plan give the same iterates as synchronous solves
+    import torch
+    sp = W.Space(dim=2, nx=33, ny=20, nu=1e-2, ax=1.0, ay=0.5, bc_x=W.PERIODIC)
+    pb = W.Problem(space=sp, nt=32, dt=1.0 / 32, scheme=W.CN, alpha=1e-3)
+    plan = make_plan(pb, pd.PD_MIXED)
+    n = pb.nt * pb.space.size
+    bs = [dev(W.uniform(W.SEED_BASE + 700 + i, n, -1, 1).reshape(pb.nt, -1)) for i in range(3)]
+    ref = []
+    for b in bs:
+        u, it, rel = plan.solve(b, torch.zeros_like(b), tol=1e-11, maxit=30)
+        ref.append((host(u).copy(), it, rel))
+    us = [torch.zeros_like(b) for b in bs]
+    for b, u in zip(bs, us):
+        plan.solve_async(b, u, tol=1e-11, maxit=30)
+    it, rel = plan.result()
+    assert it == ref[-1][1] and rel == ref[-1][2]
+    for u, (r, _, _) in zip(us, ref):
+        assert np.array_equal(host(u), r)
+    plan.close()
