@@ -58,9 +58,10 @@ def test_ade2d_small_stationary(pd, prec, scheme):
     # the mixed stationary iteration runs as one CUDA graph (device-side loop)
     assert plan.uses_graph() == (prec == "mixed")
     if prec == "mixed":
-        # a second solve reuses the graph and reproduces the first bit for bit
+        # a second solve reuses the graph and reproduces the iterate bit for bit
+        # (the residual norm is summed with atomics, so it agrees to rounding)
         u2, it2, rel2_ = plan.solve(dev(b), tol=1e-12, maxit=30)
-        assert it2 == it and rel2_ == rel
+        assert it2 == it and abs(rel2_ - rel) <= 1e-12 * rel
         assert float((u2 - u).abs().max()) == 0.0
     plan.close()
 
@@ -159,7 +160,8 @@ def test_async_solves_match_synchronous(pd):
     for b, u in zip(bs, us):
         plan.solve_async(b, u, tol=1e-11, maxit=30)
     it, rel = plan.result()
-    assert it == ref[-1][1] and rel == ref[-1][2]
+    # the residual norm is summed with atomics (order not fixed): equal to rounding
+    assert it == ref[-1][1] and abs(rel - ref[-1][2]) <= 1e-12 * ref[-1][2]
     for u, (r, _, _) in zip(us, ref):
         assert np.array_equal(host(u), r)
     plan.close()
