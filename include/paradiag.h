@@ -179,6 +179,14 @@ PD_API pd_status pd_adjoint_solve(pd_plan* plan, const double* g, double* lam, i
 PD_API pd_status pd_profile_iteration(pd_plan* plan, const double* b, const double* u, int reps,
                                       float* ms);
 
+/* Measurement aid (no paper counterpart): reps applications of z = P^{-1} r
+ * (pd_apply_precond), each kernel timed with CUDA events on the plan's
+ * stream; ms[0..4] = forward time kernel (Gamma + FFT, FP64 input), forward
+ * x-transform, tridiagonal solves, inverse x-transform, inverse time kernel
+ * (IFFT + Gamma^{-1}, FP64 output); averages in milliseconds. */
+PD_API pd_status pd_profile_precond(pd_plan* plan, const double* r, double* z, int reps,
+                                    float* ms);
+
 /* Number of kernels this plan (and its adjoint plan) has launched so far. */
 PD_API pd_status pd_plan_launches(const pd_plan* plan, unsigned long long* count);
 

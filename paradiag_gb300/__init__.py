@@ -66,6 +66,8 @@ _SIGS = {
     "pd_profile_iteration": (ctypes.c_int, [_P, _P, _P, ctypes.c_int,
                                             ctypes.POINTER(ctypes.c_float)]),
     "pd_plan_launches": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_ulonglong)]),
+    "pd_profile_precond": (ctypes.c_int, [_P, _P, _P, ctypes.c_int,
+                                          ctypes.POINTER(ctypes.c_float)]),
     "pd_plan_uses_graph": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int)]),
     "pd_plan_tuning": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]),
     "pd_apply_precond_noalloc": (ctypes.c_int, [ctypes.POINTER(pd_space), ctypes.c_int,
@@ -176,6 +178,12 @@ def pd_plan_workspace(plan):
 def pd_profile_iteration(plan, b, u, reps):
     ms = (ctypes.c_float * 5)()
     st = load().pd_profile_iteration(plan, b, u, reps, ms)
+    return st, list(ms)
+
+
+def pd_profile_precond(plan, r, z, reps):
+    ms = (ctypes.c_float * 5)()
+    st = load().pd_profile_precond(plan, r, z, reps, ms)
     return st, list(ms)
 
 
@@ -563,6 +571,14 @@ class Plan:
         self._check(st, "pd_profile_iteration")
         return ms
 
+    def profile_precond(self, r, z, reps=5):
+        """Average ms of [forward time kernel (standalone), x-fwd, tridiagonal,
+        x-inv, inverse time kernel (FP64 output)] of pd_apply_precond."""
+        self._check_t(r); self._check_t(z)
+        st, ms = pd_profile_precond(self._h, _ptr(r), _ptr(z), reps)
+        self._check(st, "pd_profile_precond")
+        return ms
+
     def apply_precond(self, r, z=None):
         import torch
         self._check_t(r)
@@ -912,6 +928,14 @@ class PlanControl:
         y = torch.empty_like(x) if y is None else y
         self._check(pdc_apply_A(self._h, _ptr(x), _ptr(y)), "pdc_apply_A")
         return y
+
+    def profile_precond(self, r, z, reps=5):
+        """Average ms of [forward time kernel (standalone), x-fwd, tridiagonal,
+        x-inv, inverse time kernel (FP64 output)] of pd_apply_precond."""
+        self._check_t(r); self._check_t(z)
+        st, ms = pd_profile_precond(self._h, _ptr(r), _ptr(z), reps)
+        self._check(st, "pd_profile_precond")
+        return ms
 
     def apply_precond(self, r, z=None):
         import torch

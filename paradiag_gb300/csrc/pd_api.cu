@@ -893,6 +893,46 @@ pd_status pd_profile_iteration(pd_plan* p, const double* b, const double* u, int
   return PD_OK;
 }
 
+pd_status pd_profile_precond(pd_plan* p, const double* r, double* z, int reps, float* ms) {
+  if (!p || !r || !z || !ms || reps < 1) return set_err(p, PD_ERR_ARG, "bad argument");
+  cudaEvent_t ev[6];
+  for (int i = 0; i < 6; ++i) CU(cudaEventCreate(&ev[i]));
+  double acc[5] = {0, 0, 0, 0, 0};
+  for (int rep = 0; rep < reps; ++rep) {
+    CU(cudaEventRecord(ev[0], p->stream));
+    FwdArgs fa = fwd_base_impl(p);
+    fa.mode = FWD_STANDALONE;
+    fa.r64 = r;
+    LK(launch_time_fwd(fa, p->fp64, p->stream));
+    CU(cudaEventRecord(ev[1], p->stream));
+    void* data = p->spec;
+    if (p->xform) {
+      CHK(xform_dir(p, true));
+      data = p->spec2;
+    }
+    CU(cudaEventRecord(ev[2], p->stream));
+    LK(launch_tridiag(tri_args_impl(p, data), p->fp64, p->stream));
+    CU(cudaEventRecord(ev[3], p->stream));
+    if (p->xform) CHK(xform_dir(p, false));
+    CU(cudaEventRecord(ev[4], p->stream));
+    InvArgs ia = inv_base_impl(p);
+    ia.mode = INV_OUT64;
+    ia.out64 = z;
+    LK(launch_time_inv(ia, p->fp64, p->stream));
+    CU(cudaEventRecord(ev[5], p->stream));
+    CU(cudaEventSynchronize(ev[5]));
+    for (int i = 0; i < 5; ++i) {
+      float t = 0.f;
+      CU(cudaEventElapsedTime(&t, ev[i], ev[i + 1]));
+      acc[i] += t;
+    }
+  }
+  for (int i = 0; i < 6; ++i) cudaEventDestroy(ev[i]);
+  for (int i = 0; i < 5; ++i) ms[i] = (float)(acc[i] / reps);
+  if (!p->xform) { ms[1] = 0.f; ms[3] = 0.f; }
+  return PD_OK;
+}
+
 const char* pd_status_string(pd_status s) {
   switch (s) {
     case PD_OK: return "ok";
