@@ -27,6 +27,15 @@ Readings:
     Euler at t_Nt.
   * V^{-1} is not given in closed form; it is formed by a dense LU solve.
 
+Second-order problems U'' + K U = f (Section 2.1.2, eq. neq2.14a/b): the hybrid
+scheme applied to the first-order system W' + [[0, -I], [K, 0]] W = (0, f) with
+W = (U, V) has the state rows (B U)_n - V_n = U_0/(2 dt) delta_{n1} and the
+velocity rows (B V)_n + K U_n = f(t_n) + V_0/(2 dt) delta_{n1}.  Eliminating V
+gives (B^2 (x) I + I (x) K) u = F_v + B F_u (B_2nd = B^2, eq. neq2.15), with
+F_u = (U_0/(2 dt), 0, ...) and F_v the velocity rows' right-hand side, and the
+same eigenvectors V with eigenvalues lambda_n^2.  (The elimination is the
+section's; the right-hand side is written out here, reading R24.)
+
 The exact solution of the all-at-once system (not a time-stepping recursion:
 the midpoint rule needs U_{n+1} before U_1 is known, so the scheme is a
 boundary value method) is a sparse LU solve of the whole system.
@@ -162,3 +171,55 @@ def solve_direct(problem: HybridProblem, b: np.ndarray, K=None, intermediates=Fa
     if intermediates:
         return U, (x, V, S1, S2)
     return U.real
+
+
+# ---------------------------------------------------------------------------
+# Second-order problems (B_2nd = B^2)
+# ---------------------------------------------------------------------------
+def time_matrix_2nd(nt: int, dt: float) -> np.ndarray:
+    """B_2nd = B^2 (eq. neq2.15)."""
+    B = time_matrix(nt, dt)
+    return B @ B
+
+
+def build_rhs_2nd(problem: HybridProblem, u0, v0, f=None) -> np.ndarray:
+    """b = F_v + B F_u of the eliminated system; f of shape (Nt+1, S) at t_0..t_Nt
+    or None; u0, v0 the initial value and velocity."""
+    nt, S, dt = problem.nt, problem.space.size, problem.dt
+    Fv = np.zeros((nt, S))
+    if f is not None:
+        Fv += np.asarray(f, dtype=np.float64)[1:]
+    Fv[0] += np.asarray(v0, dtype=np.float64) / (2.0 * dt)
+    Fu = np.zeros((nt, S))
+    Fu[0] = np.asarray(u0, dtype=np.float64) / (2.0 * dt)
+    return Fv + time_matrix(nt, dt) @ Fu
+
+
+def apply_A_2nd(problem: HybridProblem, U: np.ndarray, K=None) -> np.ndarray:
+    K = stencil(problem.space) if K is None else K
+    return time_matrix_2nd(problem.nt, problem.dt) @ U + (K @ np.asarray(U).T).T
+
+
+def solve_exact_2nd(problem: HybridProblem, b: np.ndarray, K=None) -> np.ndarray:
+    """Sparse LU of B^2 (x) I + I (x) K (small sizes)."""
+    K = stencil(problem.space) if K is None else K
+    B2 = sps.csr_matrix(time_matrix_2nd(problem.nt, problem.dt))
+    S = problem.space.size
+    A = (sps.kron(B2, sps.identity(S)) + sps.kron(sps.identity(problem.nt), K)).tocsc()
+    return spla.spsolve(A, np.asarray(b, dtype=np.float64).reshape(-1)).reshape(problem.nt, S)
+
+
+def solve_direct_2nd(problem: HybridProblem, b: np.ndarray, K=None) -> np.ndarray:
+    """The three steps of eq. 2.7 with B_2nd = V D^2 V^{-1}: shifts lambda_n^2."""
+    sp = problem.space
+    K = stencil(sp) if K is None else K
+    x = eigen_roots(problem.nt)
+    lam = 1j * x / problem.dt
+    V = eigvec_matrix(x)
+    S1 = np.linalg.solve(V, np.asarray(b, dtype=np.complex128))
+    I = sps.identity(sp.size, format="csc", dtype=np.complex128)
+    Kc = K.astype(np.complex128).tocsc()
+    S2 = np.zeros_like(S1)
+    for n in range(problem.nt):
+        S2[n] = spla.spsolve((lam[n] ** 2 * I + Kc).tocsc(), S1[n])
+    return (V @ S2).real

@@ -150,3 +150,51 @@ def test_steady_state_is_preserved():
     F = np.broadcast_to(phi, (12, 15))
     U = H.solve_exact(pb, H.build_rhs(pb, phi / mu, F))
     assert np.abs(U - phi / mu).max() < 1e-12
+
+
+# ---- second-order problems: B_2nd = B^2 (eq. neq2.15) ----
+
+def test_second_order_elimination_consistency():
+    # for the solution U of (B^2 + K) U = F_v + B F_u, the velocity V = B U - F_u
+    # solves the first-order velocity rows B V + K U = F_v (eq. neq2.14b)
+    pb = HP(dim=2, nx=7, ny=6, nu=1.0, nt=9, T=0.4)
+    K = O.stencil(pb.space)
+    S = pb.space.size
+    u0 = W.uniform(W.SEED_BASE + 110, S, -1, 1)
+    v0 = W.uniform(W.SEED_BASE + 111, S, -1, 1)
+    f = W.uniform(W.SEED_BASE + 112, (pb.nt + 1) * S, -1, 1).reshape(pb.nt + 1, S)
+    b = H.build_rhs_2nd(pb, u0, v0, f)
+    U = H.solve_exact_2nd(pb, b, K)
+    B = H.time_matrix(pb.nt, pb.dt)
+    Fu = np.zeros((pb.nt, S)); Fu[0] = u0 / (2 * pb.dt)
+    Fv = f[1:].copy(); Fv[0] += v0 / (2 * pb.dt)
+    Vv = B @ U - Fu
+    assert np.abs(B @ Vv + (K @ U.T).T - Fv).max() < 1e-10 * np.abs(Fv).max()
+
+
+@pytest.mark.parametrize("nt", [5, 12])
+def test_second_order_direct_matches_exact(nt):
+    pb = HP(dim=2, nx=8, ny=7, nu=1.0, nt=nt, T=0.5)
+    S = pb.space.size
+    b = H.build_rhs_2nd(pb, W.uniform(W.SEED_BASE + 113, S, -1, 1),
+                        W.uniform(W.SEED_BASE + 114, S, -1, 1))
+    ref = H.solve_exact_2nd(pb, b)
+    U = H.solve_direct_2nd(pb, b)
+    assert np.abs(U - ref).max() < 1e-11 * np.abs(ref).max()
+
+
+@pytest.mark.parametrize("nt", [4, 8, 16, 32, 64])
+def test_table_ex2tab1_errors(nt):
+    # the printed errors of the second-order hybrid ParaDiag-I (max over all grid
+    # points and time levels); the 5-point Laplacian is exact for the solution's
+    # spatial factor, so a 31 x 31 grid reproduces the dx = 1/512 column
+    gold = json.load(open(os.path.join(GOLDEN, "ex2tab1_wave_hybrid.json")))
+    err_ref = dict(zip(gold["nt"], gold["error"]))[nt]
+    wl = W.hybrid_wave2d(n=32, nt=nt)
+    pb = wl.problem
+    b = H.build_rhs_2nd(pb, wl.u0, wl.u1, wl.f)
+    U = H.solve_direct_2nd(pb, b)
+    t = pb.dt * np.arange(1, nt + 1)
+    ex = np.outer(np.sin(2 * np.pi * t), wl.extra["phi"])
+    err = np.abs(U - ex).max()
+    assert abs(err - err_ref) <= 0.01 * err_ref, (nt, err, err_ref)

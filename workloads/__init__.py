@@ -327,6 +327,23 @@ def hybrid_ade2d(nx=255, ny=255, nt=256, T=1.0, nu=1e-3, ax=1.0, ay=0.5, seed=SE
     return Workload(name, pb, u0, None, None, seed, extra={"center": (x0, y0)})
 
 
+def hybrid_wave2d(n=512, nt=512, T=2.0, seed=SEED_BASE + 9, name="hybrid_wave2d") -> Workload:
+    """The second-order hybrid ParaDiag-I experiment of Section 2.1.2: u_tt - Lap u = f
+    on (0,1)^2, Dirichlet, dx = dy = 1/n ((n-1)^2 interior points), T = 2,
+    u0 = 0, u_t(0) = 2 pi x(x-1)y(y-1), f such that u = x(x-1)y(y-1) sin(2 pi t).
+    ``f`` holds the source at t_0..t_nt; ``u1`` the initial velocity."""
+    sp = Space(dim=2, nx=n - 1, ny=n - 1, nu=1.0, bc_x=DIRICHLET, bc_y=DIRICHLET)
+    pb = HybridProblem(space=sp, nt=nt, dt=T / nt)
+    X, Y = sp.mesh()
+    phi = (X * (X - 1.0) * Y * (Y - 1.0)).reshape(-1)
+    q = (X * (X - 1.0) + Y * (Y - 1.0)).reshape(-1)
+    t = (T / nt) * np.arange(nt + 1)
+    st = np.sin(2.0 * np.pi * t)
+    f = np.outer(st, -4.0 * np.pi**2 * phi - 2.0 * q)
+    return Workload(name, pb, np.zeros_like(phi), 2.0 * np.pi * phi, f, seed,
+                    extra={"phi": phi, "T": T})
+
+
 def named(name: str, **kw) -> Workload:
     """The five named workloads at their full sizes (keyword overrides allowed)."""
     table = {
@@ -338,6 +355,7 @@ def named(name: str, **kw) -> Workload:
         "pd1_ade2d": lambda: pd1_ade2d(**kw),
         "hybrid_ade1d": lambda: hybrid_ade1d(**kw),
         "hybrid_ade2d": lambda: hybrid_ade2d(**kw),
+        "hybrid_wave2d": lambda: hybrid_wave2d(**kw),
     }
     return table[name]()
 
