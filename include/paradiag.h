@@ -383,6 +383,20 @@ PD_API pd_status pdh_plan_create(const pd_space* sp, int nt, double dt, int prec
                                  void* stream, pdh_plan** out);
 PD_API pd_status pdh_plan_destroy(pdh_plan* plan);
 
+/* Second-order problems U'' + K U = f, U(0) = u0, U'(0) = v0 (eq. neq2.14a):
+ * the hybrid scheme applied to the first-order form with the velocity
+ * eliminated, (B^2 (x) I + I (x) K) u = F_v + B F_u (B_2nd = B^2, eq. neq2.15),
+ * solved with the same eigenvectors and the eigenvalues (i x_n / dt)^2.  The
+ * plan works with pdh_solve, pdh_apply_A (then B^2), pdh_eigenvalues (the
+ * eigenvalues of B) and pdh_wave_build_rhs; arguments as pdh_plan_create. */
+PD_API pd_status pdh_wave_plan_create(const pd_space* sp, int nt, double dt, int precision,
+                                      void* stream, pdh_plan** out);
+
+/* b = F_v + B F_u: b_n = f(t_n) + v0/(2 dt) [n = 1] + (B)_{n,1} u0/(2 dt)
+ * (rows n = 1..nt); u0, v0: [S]; f: [nt+1][S] values at t_0..t_nt or NULL. */
+PD_API pd_status pdh_wave_build_rhs(pdh_plan* plan, const double* u0, const double* v0,
+                                    const double* f, double* b);
+
 /* lam[2n], lam[2n+1]: real and imaginary part of the eigenvalue i x_n / dt of
  * B, n = 0..nt-1 (host array of 2 nt doubles). */
 PD_API pd_status pdh_eigenvalues(const pdh_plan* plan, double* lam);

@@ -105,6 +105,9 @@ _SIGS = {
                                        ctypes.c_int, _P, ctypes.POINTER(_P)]),
     "pdh_plan_destroy": (ctypes.c_int, [_P]),
     "pdh_eigenvalues": (ctypes.c_int, [_P, _D]),
+    "pdh_wave_plan_create": (ctypes.c_int, [ctypes.POINTER(pd_space), ctypes.c_int, ctypes.c_double,
+                                            ctypes.c_int, _P, ctypes.POINTER(_P)]),
+    "pdh_wave_build_rhs": (ctypes.c_int, [_P, _P, _P, _P, _P]),
     "pdh_condition": (ctypes.c_int, [_P, _D]),
     "pdh_apply_A": (ctypes.c_int, [_P, _P, _P]),
     "pdh_build_rhs": (ctypes.c_int, [_P, _P, _P, _P]),
@@ -397,6 +400,17 @@ def pdh_plan_create(space: pd_space, nt, dt, precision, stream):
     st = load().pdh_plan_create(ctypes.byref(space), nt, dt, precision, _P(stream),
                                 ctypes.byref(out))
     return st, out.value
+
+
+def pdh_wave_plan_create(space: pd_space, nt, dt, precision, stream):
+    out = _P()
+    st = load().pdh_wave_plan_create(ctypes.byref(space), nt, dt, precision, _P(stream),
+                                     ctypes.byref(out))
+    return st, out.value
+
+
+def pdh_wave_build_rhs(plan, u0, v0, f, b):
+    return load().pdh_wave_build_rhs(plan, u0, v0, f, b)
 
 
 def pdh_plan_destroy(plan):
@@ -791,14 +805,16 @@ class PlanHybrid:
     uniform steps of size dt.  ``space`` as for Plan; tensors are CUDA float64
     of shape (nt, S)."""
 
-    def __init__(self, space, nt, dt, precision=PD_FP64, stream=None):
+    def __init__(self, space, nt, dt, precision=PD_FP64, stream=None, order=1):
+        """order 1: U' + K U = f; order 2: U'' + K U = f (B_2nd = B^2)."""
         import torch
         self.space = _space_of(space)
         self.nt, self.dt, self.precision = int(nt), float(dt), int(precision)
+        self.order = int(order)
         self.S = self.space.nx * (self.space.ny if self.space.dim == 2 else 1)
         self.stream = stream if stream is not None else torch.cuda.current_stream()
-        st, h = pdh_plan_create(self.space, self.nt, self.dt, self.precision,
-                                self.stream.cuda_stream)
+        create = pdh_wave_plan_create if self.order == 2 else pdh_plan_create
+        st, h = create(self.space, self.nt, self.dt, self.precision, self.stream.cuda_stream)
         if st != PD_OK:
             raise PDError(st, "pdh_plan_create")
         self._h = h
@@ -857,6 +873,18 @@ class PlanHybrid:
             self._check_t(f, (self.nt + 1) * self.S)
         b = torch.empty((self.nt, self.S), dtype=torch.float64, device=u0.device) if b is None else b
         self._check(pdh_build_rhs(self._h, _ptr(u0), _ptr(f), _ptr(b)), "pdh_build_rhs")
+        return b
+
+    def build_rhs_wave(self, u0, v0, f=None, b=None):
+        """Second-order plans: b = F_v + B F_u from u0, v0 and f ([nt+1, S])."""
+        import torch
+        self._check_t(u0, self.S)
+        self._check_t(v0, self.S)
+        if f is not None:
+            self._check_t(f, (self.nt + 1) * self.S)
+        b = torch.empty((self.nt, self.S), dtype=torch.float64, device=u0.device) if b is None else b
+        self._check(pdh_wave_build_rhs(self._h, _ptr(u0), _ptr(v0), _ptr(f), _ptr(b)),
+                    "pdh_wave_build_rhs")
         return b
 
     def profile_sweep(self, b, u, reps=5):

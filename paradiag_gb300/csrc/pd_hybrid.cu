@@ -22,6 +22,13 @@
 // one member of each pair is solved: Nh = ceil(Nt/2) spectrum rows, and
 // u = sum_{k in half} w_k Re(v_k S2_k), w_k = 2 for a pair, 1 otherwise.
 //
+// Second-order problems U'' + K U = f (eq. neq2.14a/b, B_2nd = B^2 of eq.
+// neq2.15): eliminating the velocity from the hybrid discretisation of the
+// first-order form gives (B^2 (x) I + I (x) K) u = F_v + B F_u with the same
+// eigenvectors and the eigenvalues lambda_n^2 (pdh_wave_plan_create).  B^2 is
+// banded (offsets -2..2, small-integer multiples of 1/(4 dt^2)); its row
+// weights come from the host.
+//
 // Device side: steps (a) and (c) are dense contractions over the time index
 // (2 Nh x Nt and Nt x 2 Nh real forms of V^{-1} and V), about 2 Nt FMAs per
 // space-time unknown each, computed by a register-tiled SIMT GEMM (FP32 on the
@@ -265,9 +272,14 @@ __global__ void __launch_bounds__(HG_TB, 2) k_hy_gemm(const HGemm a) {
 // float arithmetic, r rounded to FP32; FP64 otherwise.
 struct HResid {
   int N, S;
+  int order;                    // 1: B; 2: B^2 (second-order problems)
   Stencil st;
   double c2, c1;                // 1/(2 dt) (midpoint rows), 1/dt (last row)
   dfc c2d, c1d;
+  double c4;                    // order 2: 1/(4 dt^2)
+  dfc c4d;
+  const signed char* w2;        // order 2: [N][5] integer weights of B^2 row n, offsets -2..2
+  double b2_0, b2_1;            // order 2: (B F_u) = (B[0][0], B[1][0]) u0/(2 dt)
   dfc kap[5];
   const double* b64;
   const double* u64;
@@ -421,6 +433,127 @@ __global__ void k_hy_rhs(const HResid a, const double* u0, const double* f, doub
   }
 }
 
+// Residual of the second-order system: r_n = b_n - c4 sum_m w[n][m] U_{n+m}
+// - (K U)_n, one thread per spatial point and chunk of HR_CH rows, a window of
+// five rows U_{n-2..n+2}.  Mixed: double-float; FP64 otherwise.
+template <int PREC, int MODE>
+__global__ void __launch_bounds__(HR_TB) k_hy2_resid(const HResid a) {
+  const int s = blockIdx.x * HR_TB + threadIdx.x;
+  const bool valid = s < a.S;
+  const int N = a.N, S = a.S;
+  const int n0 = blockIdx.y * HR_CH;
+  const int n1 = min(N, n0 + HR_CH);
+  const Stencil& st = a.st;
+  const Nbh g = nbh(st, valid ? s : 0);
+  double nrm = 0.0;
+  float nrmf = 0.f;
+  if (valid) {
+    if constexpr (MODE == HY_DIRECT) {
+      for (int n = n0; n < n1; ++n) {
+        const size_t i = (size_t)n * S + s;
+        const double bv = a.b64[i];
+        if constexpr (PREC == 1) {
+          reinterpret_cast<double*>(a.r)[i] = bv;
+          nrm = fma(bv, bv, nrm);
+        } else {
+          const df d = df_from_double(bv);
+          a.Bdf[i] = make_float2(d.hi, d.lo);
+          reinterpret_cast<float*>(a.r)[i] = d.hi;
+          nrmf = fmaf(d.hi, d.hi, nrmf);
+        }
+      }
+    } else if constexpr (PREC == 1) {
+      const double* U = a.u64;
+      auto at = [&](int n) { return (n >= 0 && n < N) ? U[(size_t)n * S + s] : 0.0; };
+      double w[5] = {at(n0 - 2), at(n0 - 1), at(n0), at(n0 + 1), at(n0 + 2)};
+      for (int n = n0; n < n1; ++n) {
+        const size_t base = (size_t)n * S;
+        const double* Un = U + base;
+        double ku = st.kc * w[2];
+        if (g.l >= 0) ku = fma(st.kxl, Un[g.l], ku);
+        if (g.r >= 0) ku = fma(st.kxu, Un[g.r], ku);
+        if (g.d >= 0) ku = fma(st.kyl, Un[g.d], ku);
+        if (g.u >= 0) ku = fma(st.kyu, Un[g.u], ku);
+        const signed char* wn = a.w2 + 5 * n;
+        double bu = 0.0;
+#pragma unroll
+        for (int m = 0; m < 5; ++m) bu = fma((double)wn[m], w[m], bu);
+        const double r = a.b64[base + s] - a.c4 * bu - ku;
+        nrm = fma(r, r, nrm);
+        if constexpr (MODE == HY_RESID) reinterpret_cast<double*>(a.r)[base + s] = r;
+        w[0] = w[1]; w[1] = w[2]; w[2] = w[3]; w[3] = w[4]; w[4] = at(n + 3);
+      }
+    } else {
+      const float2* U = a.Udf;
+      auto at = [&](int n) {
+        return (n >= 0 && n < N) ? U[(size_t)n * S + s] : make_float2(0.f, 0.f);
+      };
+      float2 w[5] = {at(n0 - 2), at(n0 - 1), at(n0), at(n0 + 1), at(n0 + 2)};
+      for (int n = n0; n < n1; ++n) {
+        const size_t base = (size_t)n * S;
+        const float2* Un = U + base;
+        const float2 bb = a.Bdf[base + s];
+        // sum_m w[n][m] U_{n+m}: integer weights, exact products
+        const signed char* wn = a.w2 + 5 * n;
+        AccH T = {0.f, 0.f};
+#pragma unroll
+        for (int m = 0; m < 5; ++m) acch_add_prod(T, dfc{(float)wn[m], 0.f}, w[m]);
+        const df tv = fast_two_sum(T.s, T.e);
+        AccH A = {bb.x, bb.y};
+        acch_add_prod(A, dfc{-a.c4d.hi, -a.c4d.lo}, make_float2(tv.hi, tv.lo));
+        acch_add_prod(A, dfc{-a.kap[0].hi, -a.kap[0].lo}, w[2]);
+        if (g.l >= 0) acch_add_prod(A, dfc{-a.kap[1].hi, -a.kap[1].lo}, Un[g.l]);
+        if (g.r >= 0) acch_add_prod(A, dfc{-a.kap[2].hi, -a.kap[2].lo}, Un[g.r]);
+        if (g.d >= 0) acch_add_prod(A, dfc{-a.kap[3].hi, -a.kap[3].lo}, Un[g.d]);
+        if (g.u >= 0) acch_add_prod(A, dfc{-a.kap[4].hi, -a.kap[4].lo}, Un[g.u]);
+        const float r = fast_two_sum(A.s, A.e).hi;
+        nrmf = fmaf(r, r, nrmf);
+        if constexpr (MODE == HY_RESID) reinterpret_cast<float*>(a.r)[base + s] = r;
+        w[0] = w[1]; w[1] = w[2]; w[2] = w[3]; w[3] = w[4]; w[4] = at(n + 3);
+      }
+    }
+    if constexpr (PREC == 0) nrm = (double)nrmf;
+  }
+  for (int o = 16; o > 0; o >>= 1) nrm += __shfl_xor_sync(0xffffffffu, nrm, o);
+  if ((threadIdx.x & 31) == 0 && a.norm2 != nullptr) atomicAdd(a.norm2, nrm);
+}
+
+// y = (B^2 (x) I + I (x) K) u (FP64)
+__global__ void k_hy2_apply(const HResid a, const double* u, double* y) {
+  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= a.S) return;
+  const Stencil& st = a.st;
+  const Nbh g = nbh(st, s);
+  const int N = a.N, S = a.S;
+  for (int n = 0; n < N; ++n) {
+    const double* U = u + (size_t)n * S;
+    double ku = st.kc * U[s];
+    if (g.l >= 0) ku = fma(st.kxl, U[g.l], ku);
+    if (g.r >= 0) ku = fma(st.kxu, U[g.r], ku);
+    if (g.d >= 0) ku = fma(st.kyl, U[g.d], ku);
+    if (g.u >= 0) ku = fma(st.kyu, U[g.u], ku);
+    double bu = 0.0;
+    for (int m = 0; m < 5; ++m) {
+      const int k = n + m - 2;
+      if (k >= 0 && k < N) bu = fma((double)a.w2[5 * n + m], u[(size_t)k * S + s], bu);
+    }
+    y[(size_t)n * S + s] = a.c4 * bu + ku;
+  }
+}
+
+// b = F_v + B F_u: b_n = f(t_n) + [n = 0] v0/(2 dt) + (B[n][0]) u0/(2 dt)
+__global__ void k_hy2_rhs(const HResid a, const double* u0, const double* v0, const double* f,
+                          double* b) {
+  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= a.S) return;
+  for (int n = 0; n < a.N; ++n) {
+    double v = f != nullptr ? f[(size_t)(n + 1) * a.S + s] : 0.0;
+    if (n == 0) v += a.c2 * v0[s] + a.b2_0 * u0[s];
+    if (n == 1) v += a.b2_1 * u0[s];
+    b[(size_t)n * a.S + s] = v;
+  }
+}
+
 template <typename R>
 cudaError_t launch_gemm(const HGemm& g, int mode, cudaStream_t st) {
   constexpr int BN = GemmTile<R>::BN;
@@ -433,6 +566,18 @@ cudaError_t launch_gemm(const HGemm& g, int mode, cudaStream_t st) {
 
 cudaError_t launch_resid(const HResid& a, int mode, bool fp64, cudaStream_t st) {
   const dim3 grid((a.S + HR_TB - 1) / HR_TB, (a.N + HR_CH - 1) / HR_CH), block(HR_TB);
+  if (a.order == 2) {
+    if (fp64) {
+      if (mode == HY_DIRECT) k_hy2_resid<1, HY_DIRECT><<<grid, block, 0, st>>>(a);
+      else if (mode == HY_RESID) k_hy2_resid<1, HY_RESID><<<grid, block, 0, st>>>(a);
+      else k_hy2_resid<1, HY_NORM><<<grid, block, 0, st>>>(a);
+    } else {
+      if (mode == HY_DIRECT) k_hy2_resid<0, HY_DIRECT><<<grid, block, 0, st>>>(a);
+      else if (mode == HY_RESID) k_hy2_resid<0, HY_RESID><<<grid, block, 0, st>>>(a);
+      else k_hy2_resid<0, HY_NORM><<<grid, block, 0, st>>>(a);
+    }
+    return cudaGetLastError();
+  }
   if (fp64) {
     if (mode == HY_DIRECT) k_hy_resid<1, HY_DIRECT><<<grid, block, 0, st>>>(a);
     else if (mode == HY_RESID) k_hy_resid<1, HY_RESID><<<grid, block, 0, st>>>(a);
@@ -453,6 +598,9 @@ cudaError_t launch_resid(const HResid& a, int mode, bool fp64, cudaStream_t st) 
 struct pdh_plan {
   pd_plan* sp = nullptr;          // spatial operators, step (b) on Nh rows
   int nt = 0, nh = 0, precision = 0;
+  int order = 1;                  // 1: B; 2: B^2 (second-order problems)
+  signed char* w2 = nullptr;      // order 2: [Nt][5] integer weights of B^2 (device)
+  double b2_0 = 0, b2_1 = 0;      // order 2: B[0][0], B[1][0] (times dt)
   bool fp64 = false;
   double dt = 0;
   std::vector<cdh> x;             // all Nt roots
@@ -495,7 +643,7 @@ pd_status ph_cuda(pdh_plan* q, cudaError_t e, const char* what) {
 
 void free_ph(pdh_plan* q) {
   if (!q) return;
-  void* ptrs[] = {q->Af, q->Ai, q->r, q->Udf, q->Bdf, q->dnorm};
+  void* ptrs[] = {q->Af, q->Ai, q->r, q->Udf, q->Bdf, q->dnorm, q->w2};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (q->hnorm) cudaFreeHost(q->hnorm);
@@ -589,6 +737,12 @@ HResid resid_args(const pdh_plan* q) {
   a.Bdf = q->Bdf;
   a.Udf = q->Udf;
   a.r = q->r;
+  a.order = q->order;
+  a.c4 = 0.25 / (q->dt * q->dt);
+  a.c4d = dfc_from(a.c4);
+  a.w2 = q->w2;
+  a.b2_0 = q->b2_0 / (2.0 * q->dt * q->dt);
+  a.b2_1 = q->b2_1 / (2.0 * q->dt * q->dt);
   return a;
 }
 
@@ -652,8 +806,21 @@ pd_status pass(pdh_plan* q, double* u, int inv_mode) {
 
 extern "C" {
 
+pd_status pdh_create_impl(const pd_space* sp, int nt, double dt, int precision, void* stream,
+                          int order, pdh_plan** out);
+
 pd_status pdh_plan_create(const pd_space* sp, int nt, double dt, int precision, void* stream,
                           pdh_plan** out) {
+  return pdh_create_impl(sp, nt, dt, precision, stream, 1, out);
+}
+
+pd_status pdh_wave_plan_create(const pd_space* sp, int nt, double dt, int precision,
+                               void* stream, pdh_plan** out) {
+  return pdh_create_impl(sp, nt, dt, precision, stream, 2, out);
+}
+
+pd_status pdh_create_impl(const pd_space* sp, int nt, double dt, int precision, void* stream,
+                          int order, pdh_plan** out) {
   if (!out) return PD_ERR_ARG;
   *out = nullptr;
   if (!sp) return PD_ERR_ARG;
@@ -668,6 +835,7 @@ pd_status pdh_plan_create(const pd_space* sp, int nt, double dt, int precision, 
   q->dt = dt;
   q->precision = precision;
   q->fp64 = precision == PD_FP64;
+  q->order = order;
   hybrid_roots(nt, q->x);
 
   // one root of every pair x, -conj(x) (the one with Re x > 0), and the
@@ -741,7 +909,8 @@ pd_status pdh_plan_create(const pd_space* sp, int nt, double dt, int precision, 
   // step (b): lambda_1 = i x / dt, lambda_2 = 1 on the solved rows
   std::vector<double> lam((size_t)4 * nh, 0.0);
   for (int k = 0; k < nh; ++k) {
-    const cdh l1 = I * q->x[q->half[k]] / dt;
+    cdh l1 = I * q->x[q->half[k]] / dt;
+    if (order == 2) l1 = l1 * l1;
     lam[4 * k] = l1.real();
     lam[4 * k + 1] = l1.imag();
     lam[4 * k + 2] = 1.0;
@@ -767,6 +936,32 @@ pd_status pdh_plan_create(const pd_space* sp, int nt, double dt, int precision, 
     if (e == cudaSuccess && !q->fp64) e = cudaMalloc((void**)&q->Bdf, ns * sizeof(float2));
     if (e == cudaSuccess) e = cudaMalloc((void**)&q->dnorm, 2 * sizeof(double));
     if (e == cudaSuccess) e = cudaMallocHost((void**)&q->hnorm, 2 * sizeof(double) + sizeof(int));
+    if (e != cudaSuccess) s = ph_cuda(q, e, "allocation");
+  }
+  if (s == PD_OK && order == 2) {
+    // B^2 (dt B = Bh: rows (-1/2, 0, 1/2), last row (-1, 1)) as integer
+    // weights of 1/(4 dt^2) at offsets -2..2, and Bh[0][0], Bh[1][0]
+    std::vector<double> Bh((size_t)nt * nt, 0.0);
+    for (int l = 0; l + 1 < nt; ++l) {
+      if (l > 0) Bh[(size_t)l * nt + l - 1] = -0.5;
+      Bh[(size_t)l * nt + l + 1] = 0.5;
+    }
+    Bh[(size_t)(nt - 1) * nt + nt - 1] = 1.0;
+    if (nt > 1) Bh[(size_t)(nt - 1) * nt + nt - 2] = -1.0;
+    std::vector<signed char> w((size_t)5 * nt, 0);
+    for (int n = 0; n < nt; ++n)
+      for (int m = -2; m <= 2; ++m) {
+        const int k = n + m;
+        if (k < 0 || k >= nt) continue;
+        double v = 0.0;
+        for (int j = std::max(0, n - 1); j <= std::min(nt - 1, n + 1); ++j)
+          v += Bh[(size_t)n * nt + j] * Bh[(size_t)j * nt + k];
+        w[(size_t)5 * n + (m + 2)] = (signed char)std::lround(4.0 * v);
+      }
+    q->b2_0 = Bh[0];
+    q->b2_1 = nt > 1 ? Bh[(size_t)nt] : 0.0;
+    cudaError_t e = cudaMalloc((void**)&q->w2, w.size());
+    if (e == cudaSuccess) e = cudaMemcpy(q->w2, w.data(), w.size(), cudaMemcpyHostToDevice);
     if (e != cudaSuccess) s = ph_cuda(q, e, "allocation");
   }
   if (s != PD_OK) {
@@ -805,13 +1000,25 @@ pd_status pdh_condition(const pdh_plan* q, double* cond) {
 pd_status pdh_apply_A(pdh_plan* q, const double* u, double* y) {
   if (!q || !u || !y) return PD_ERR_ARG;
   const HResid a = resid_args(q);
-  k_hy_apply<<<(a.S + HR_TB - 1) / HR_TB, HR_TB, 0, q->sp->stream>>>(a, u, y);
+  if (q->order == 2) k_hy2_apply<<<(a.S + HR_TB - 1) / HR_TB, HR_TB, 0, q->sp->stream>>>(a, u, y);
+  else k_hy_apply<<<(a.S + HR_TB - 1) / HR_TB, HR_TB, 0, q->sp->stream>>>(a, u, y);
+  PHLK(cudaGetLastError());
+  return PD_OK;
+}
+
+pd_status pdh_wave_build_rhs(pdh_plan* q, const double* u0, const double* v0, const double* f,
+                             double* b) {
+  if (!q || !u0 || !v0 || !b) return PD_ERR_ARG;
+  if (q->order != 2) return ph_err(q, PD_ERR_ARG, "not a second-order plan");
+  const HResid a = resid_args(q);
+  k_hy2_rhs<<<(a.S + HR_TB - 1) / HR_TB, HR_TB, 0, q->sp->stream>>>(a, u0, v0, f, b);
   PHLK(cudaGetLastError());
   return PD_OK;
 }
 
 pd_status pdh_build_rhs(pdh_plan* q, const double* u0, const double* f, double* b) {
   if (!q || !u0 || !b) return PD_ERR_ARG;
+  if (q->order != 1) return ph_err(q, PD_ERR_ARG, "second-order plans take pdh_wave_build_rhs");
   const HResid a = resid_args(q);
   k_hy_rhs<<<(a.S + HR_TB - 1) / HR_TB, HR_TB, 0, q->sp->stream>>>(a, u0, f, b);
   PHLK(cudaGetLastError());

@@ -17,6 +17,7 @@ import pytest
 import workloads as W
 from helpers import EPS32, dev, host, lib_ready, space_dict
 from oracle import hybrid as H
+from oracle.operators import stencil
 
 pytestmark = pytest.mark.gpu
 
@@ -156,4 +157,92 @@ def test_hybrid_full_size_window(pd):
     assert rel <= 1e-12
     r = bd - plan.apply_A(u)
     assert float(torch.linalg.norm(r) / torch.linalg.norm(bd)) <= 2e-12
+    plan.close()
+
+
+# ---- second-order problems (B_2nd = B^2) ----
+
+WAVE = {
+    "2d_dirichlet_15x15x16": W.HybridProblem(space=W.Space(dim=2, nx=15, ny=15, nu=1.0),
+                                             nt=16, dt=2.0 / 16),
+    "1d_dirichlet_63x33": W.HybridProblem(space=W.Space(dim=1, nx=63, nu=1.0), nt=33, dt=1.0 / 33),
+    "2d_xper_33x20x8": W.HybridProblem(space=W.Space(dim=2, nx=33, ny=20, nu=0.5,
+                                                     bc_x=W.PERIODIC), nt=8, dt=0.05),
+    "1d_nt2": W.HybridProblem(space=W.Space(dim=1, nx=20, nu=1.0), nt=2, dt=0.1),
+}
+
+
+def make2(pb, precision):
+    import paradiag_gb300 as pd
+    return pd.PlanHybrid(space_dict(pb.space), pb.nt, pb.dt, precision, order=2)
+
+
+def refine_tol(pb, b, exact, precision):
+    """Residual tolerance the refinement can reach: the residual is formed in
+    double-float (unit roundoff 2^-48) for the mixed path, so its floor is a few
+    units times || |A| |u| || / || b ||, which B^2's (1/dt^2) entries make
+    ~1e2..1e3 for these problems."""
+    if precision == PD_FP64:
+        return 1e-13
+    K = stencil(pb.space)
+    Au = np.abs(H.time_matrix_2nd(pb.nt, pb.dt)) @ np.abs(exact) + (abs(K) @ np.abs(exact).T).T
+    return max(1e-13, 8 * 2.0 ** -48 * np.linalg.norm(Au) / np.linalg.norm(b))
+
+
+@pytest.mark.parametrize("name", sorted(WAVE))
+def test_wave_apply_and_rhs_match_oracle(pd, name):
+    pb = WAVE[name]
+    S = pb.space.size
+    u0 = W.uniform(W.SEED_BASE + 310, S, -1, 1)
+    v0 = W.uniform(W.SEED_BASE + 311, S, -1, 1)
+    f = W.uniform(W.SEED_BASE + 312, (pb.nt + 1) * S, -1, 1).reshape(pb.nt + 1, S)
+    plan = make2(pb, PD_FP64)
+    br = H.build_rhs_2nd(pb, u0, v0, f)
+    bg = host(plan.build_rhs_wave(dev(u0), dev(v0), dev(f)))
+    assert np.abs(bg - br).max() <= 1e-13 * np.abs(br).max()
+    U = W.uniform(W.SEED_BASE + 313, pb.nt * S, -1, 1).reshape(pb.nt, S)
+    yr = H.apply_A_2nd(pb, U)
+    assert np.abs(host(plan.apply_A(dev(U))) - yr).max() <= 1e-13 * np.abs(yr).max()
+    plan.close()
+
+
+@pytest.mark.parametrize("name", sorted(WAVE))
+@pytest.mark.parametrize("prec", [PD_FP64, PD_MIXED])
+def test_wave_solve_matches_exact(pd, name, prec):
+    pb = WAVE[name]
+    S = pb.space.size
+    b = H.build_rhs_2nd(pb, W.uniform(W.SEED_BASE + 314, S, -1, 1),
+                        W.uniform(W.SEED_BASE + 315, S, -1, 1),
+                        W.uniform(W.SEED_BASE + 316, (pb.nt + 1) * S, -1, 1).reshape(pb.nt + 1, S))
+    exact = H.solve_exact_2nd(pb, b)
+    plan = make2(pb, prec)
+    u, it, _ = plan.solve(dev(b))
+    cond = cond_v(pb)
+    scale = np.abs(exact).max()
+    eps = EPS64 if prec == PD_FP64 else EPS32
+    assert np.abs(host(u) - exact).max() <= 16 * pb.nt * eps * cond * scale + 1e-12 * scale
+    tol = refine_tol(pb, b, exact, prec)
+    u, it, rel = plan.solve(dev(b), tol=tol, max_refine=20)
+    assert rel <= tol
+    assert np.abs(host(u) - exact).max() <= 1e-10 * scale
+    plan.close()
+
+
+@pytest.mark.parametrize("nt", [16, 64])
+def test_wave_table_ex2tab1_errors(pd, nt):
+    # the errors of Table Ex2Tab1 (2D wave equation, T = 2), GPU mixed solve
+    # refined to a 1e-10 residual on a 31 x 31 grid (the spatial discretisation is exact
+    # for the solution's spatial factor)
+    import json, os
+    gold = json.load(open(os.path.join(os.path.dirname(__file__), "golden",
+                                       "ex2tab1_wave_hybrid.json")))
+    err_ref = dict(zip(gold["nt"], gold["error"]))[nt]
+    wl = W.hybrid_wave2d(n=32, nt=nt)
+    pb = wl.problem
+    plan = make2(pb, PD_MIXED)
+    b = plan.build_rhs_wave(dev(wl.u0), dev(wl.u1), dev(wl.f))
+    u, it, rel = plan.solve(b, tol=1e-10, max_refine=20)
+    t = pb.dt * np.arange(1, nt + 1)
+    err = np.abs(host(u) - np.outer(np.sin(2 * np.pi * t), wl.extra["phi"])).max()
+    assert abs(err - err_ref) <= 0.01 * err_ref, (nt, err, err_ref)
     plan.close()
