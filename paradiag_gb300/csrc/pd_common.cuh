@@ -133,6 +133,15 @@ PD_D void acc2_add_prod(Acc2& A, const K2& k, const DF2& u) {
   A.e = f2sub(f2add(A.e, err), npe);
 }
 
+// the sum k u started from nothing: the product and its rounding error
+PD_D Acc2 acc2_of_prod(const K2& k, const DF2& u) {
+  const float2 p = f2mul(u.hi, k.h);
+  float2 npe = f2fma(u.hi, k.nh, p);
+  npe = f2fma(u.hi, k.nl, npe);
+  npe = f2fma(u.lo, k.nh, npe);
+  return Acc2{p, f2mul(npe, make_float2(-1.f, -1.f))};
+}
+
 // Split an FP64 value into hi + lo FP32 parts with integer operations only.
 // hi keeps the leading 24 significand bits (truncated), lo the next 24 bits
 // (rounded by the integer-to-float conversion), so |x - hi - lo| <= 2^-47 |x|.

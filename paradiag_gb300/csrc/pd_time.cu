@@ -122,7 +122,7 @@ PD_D void dft_r(C* v) {
 // and writes rows (j - q) R + q + k Ns; with every size a power of two all the
 // index arithmetic is shifts and masks.  Every butterfly is read into
 // registers before the barrier and written after it, so the pass runs in place.
-template <typename C, bool INV, int LR, int BPT>
+template <typename C, bool INV, int LR, int BPT, bool FIRST = false>
 PD_D void fft_pass(C* sm, int lgN, int lgTXc, int lgNs, const C* tw) {
   constexpr int R = 1 << LR;
   const int lgNB = lgN - LR + lgTXc;        // butterflies: (N / R) TXc
@@ -142,7 +142,7 @@ PD_D void fft_pass(C* sm, int lgN, int lgTXc, int lgNs, const C* tw) {
 #pragma unroll
       for (int r = 0; r < R; ++r) {
         C x = sm[b + (r << lgNB)];
-        if (r > 0) x = cmul(x, twid<C, INV>(tw, tq * r));
+        if (!FIRST && r > 0) x = cmul(x, twid<C, INV>(tw, tq * r));
         v[t][r] = x;
       }
       dft_r<C, INV, R>(v[t]);
@@ -171,12 +171,13 @@ PD_D void fft_tile(C* sm, int N, int logN, int lgTXc, const C* tw) {
   constexpr int B8 = EPT / 8 > 0 ? EPT / 8 : 1;
   constexpr int B4 = EPT / 4 > 0 ? EPT / 4 : 1;
   constexpr int B2 = EPT / 2 > 0 ? EPT / 2 : 1;
-  int lgNs = 0;
+  // the first pass (sub-transform length 1) has unit twiddles
   const int rem = logN & 3;
-  if (rem == 1) fft_pass<C, INV, 1, B2>(sm, logN, lgTXc, lgNs, tw);
-  else if (rem == 2) fft_pass<C, INV, 2, B4>(sm, logN, lgTXc, lgNs, tw);
-  else if (rem == 3) fft_pass<C, INV, 3, B8>(sm, logN, lgTXc, lgNs, tw);
-  lgNs = rem;
+  if (rem == 1) fft_pass<C, INV, 1, B2, true>(sm, logN, lgTXc, 0, tw);
+  else if (rem == 2) fft_pass<C, INV, 2, B4, true>(sm, logN, lgTXc, 0, tw);
+  else if (rem == 3) fft_pass<C, INV, 3, B8, true>(sm, logN, lgTXc, 0, tw);
+  else if (logN >= 4) fft_pass<C, INV, 4, B16, true>(sm, logN, lgTXc, 0, tw);
+  int lgNs = rem != 0 ? rem : (logN >= 4 ? 4 : 0);
   for (; lgNs < logN; lgNs += 4) fft_pass<C, INV, 4, B16>(sm, logN, lgTXc, lgNs, tw);
 }
 
@@ -344,8 +345,7 @@ PD_D void stencil_df2(const FwdArgs& a, const ColGeom& g, const RowLd<float2>& L
   rt.lo.y = __shfl_down_sync(FULL, Uc.lo.y, 1, TX);
   if (g.left != 1) lf = df2_pack(LA.l, LB.l);
   if (g.right != 1) rt = df2_pack(LA.r, LB.r);
-  Acc2 A = {make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
-  acc2_add_prod(A, kk[0], Uc);
+  Acc2 A = acc2_of_prod(kk[0], Uc);
   acc2_add_prod(A, kk[1], lf);
   acc2_add_prod(A, kk[2], rt);
   if (a.st.dim == 2) {
@@ -460,13 +460,34 @@ PD_D void time_fwd_body(const FwdArgs& a, int tile) {
                     U2, K2v);
       stencil_df2(a, g, load_row(a.Udf, a, g, nA - 1), load_row(a.Udf, a, g, nB - 1), TX, kk, U1,
                   K1);
-      auto ldb = [&](int n) -> float2 {
-        return (n >= 0 && n < N && g.valid) ? __ldg(&a.Bdf[(size_t)n * S + s])
-                                            : make_float2(0.f, 0.f);
+      // In the loop every row index is clamped to the last level: rows at or
+      // past N (possible in the last chunks) are computed from in-range data
+      // and discarded, so the loads carry no row checks.  Padding columns
+      // (s >= S) read column 0 and write zeros; no valid column takes an
+      // x-neighbour from a padding lane (the last grid point has none to its
+      // right, or a wrapped one that is loaded).
+      const int sc = g.valid ? s : 0;
+      const bool hasL = g.left == 2, hasR = g.right == 2, hasD = g.down, hasU = g.up;
+      const int dL = hasL ? g.s_left - s : 0, dR = hasR ? g.s_right - s : 0;
+      const int nx = a.st.nx, Nm1 = N - 1;
+      const size_t Sz = (size_t)S;
+      const float2* __restrict__ Ucol = a.Udf + sc;
+      const float2* __restrict__ Bcol = a.Bdf + sc;
+      const float2 z2 = make_float2(0.f, 0.f);
+      auto ldrow = [&](int n) -> RowLd<float2> {
+        const float2* p = Ucol + (size_t)n * Sz;
+        RowLd<float2> L;
+        L.c = __ldg(p);
+        L.l = hasL ? __ldg(p + dL) : z2;
+        L.r = hasR ? __ldg(p + dR) : z2;
+        L.d = hasD ? __ldg(p - nx) : z2;
+        L.u = hasU ? __ldg(p + nx) : z2;
+        return L;
       };
       // one row of loads in flight ahead of the row being computed
-      RowLd<float2> cA = load_row(a.Udf, a, g, nA), cB = load_row(a.Udf, a, g, nB);
-      float2 bA = ldb(nA), bB = ldb(nB);
+      RowLd<float2> cA = ldrow(min(nA, Nm1)), cB = ldrow(min(nB, Nm1));
+      float2 bA = __ldg(Bcol + (size_t)min(nA, Nm1) * Sz);
+      float2 bB = __ldg(Bcol + (size_t)min(nB, Nm1) * Sz);
       // the c2 weights negated once; when every c2[m] is 0 or a power of two
       // (backward Euler, Crank-Nicolson, leap-frog) the weighted terms are exact
       // scalings
@@ -474,16 +495,18 @@ PD_D void time_fwd_body(const FwdArgs& a, int tile) {
       m0.hi = -m0.hi; m0.lo = -m0.lo;
       mb.hi = -mb.hi; mb.lo = -mb.lo;
       const bool exact = a.c2exact != 0;
+      const bool has_mb = mb.hi != 0.f;
       const K2 km0 = k2_of(m0), kmb = k2_of(mb);
       const float2 sm0 = make_float2(m0.hi, m0.hi), smb = make_float2(mb.hi, mb.hi);
       const float2 two = make_float2(2.f, 2.f);
       float2 part = make_float2(0.f, 0.f);
+      float* srow = smr + x;
+#pragma unroll 1
       for (int i = 0; i < rpc2; ++i) {
         const int na = nA + i, nb = nB + i;
-        const bool more = i + 1 < rpc2;
-        const RowLd<float2> xA = load_row(a.Udf, a, g, more ? na + 1 : -1);
-        const RowLd<float2> xB = load_row(a.Udf, a, g, more ? nb + 1 : -1);
-        const float2 yA = ldb(more ? na + 1 : -1), yB = ldb(more ? nb + 1 : -1);
+        const int pa = min(na + 1, Nm1), pb = min(nb + 1, Nm1);
+        const RowLd<float2> xA = ldrow(pa), xB = ldrow(pb);
+        const float2 yA = __ldg(Bcol + (size_t)pa * Sz), yB = __ldg(Bcol + (size_t)pb * Sz);
         stencil_df2(a, g, cA, cB, TX, kk, U0, K0);  // uniform across the warp
         // r' = s b - U_n + U_{n-1} - c2[0] (sK)U_n - c2[1] (sK)U_{n-1}        (theta)
         // r' = s b - U_n + 2 U_{n-1} - U_{n-2} - c2[0] (sK)U_n - c2[2] (sK)U_{n-2} (leap-frog)
@@ -499,7 +522,7 @@ PD_D void time_fwd_body(const FwdArgs& a, int tile) {
         const Acc2& Kb = BAND == 1 ? K1 : K2v;
         if (exact) {
           acc2_add(A, f2mul(sm0, K0.s), f2mul(sm0, K0.e));
-          if (mb.hi != 0.f) acc2_add(A, f2mul(smb, Kb.s), f2mul(smb, Kb.e));
+          if (has_mb) acc2_add(A, f2mul(smb, Kb.s), f2mul(smb, Kb.e));
         } else {
           acc2_add_prod(A, km0, DF2{K0.s, K0.e});
           acc2_add_prod(A, kmb, DF2{Kb.s, Kb.e});
@@ -507,15 +530,17 @@ PD_D void time_fwd_body(const FwdArgs& a, int tile) {
         // value = s + e, renormalised
         const float2 rh = f2add(A.s, A.e);
         const float2 rl = f2sub(A.e, f2sub(rh, A.s));
-        // rows at or past N (lane B of the last chunks) add nothing
-        const float2 rn = make_float2(na < N && g.valid ? rh.x : 0.f, nb < N && g.valid ? rh.y : 0.f);
+        // rows at or past N (lanes of the last chunks) add nothing
+        const bool va = na < N && g.valid, vb = nb < N && g.valid;
+        const float2 rn = make_float2(va ? rh.x : 0.f, vb ? rh.y : 0.f);
         part = f2fma(rn, rn, part);
-        if (g.valid) {
-          if (na < N) smr[na * TX + x] = fmaf(rh.x, gam[na], rl.x * gam[na]);
-          if (nb < N) smr[nb * TX + x] = fmaf(rh.y, gam[nb], rl.y * gam[nb]);
-        } else {
-          if (na < N) smr[na * TX + x] = 0.f;
-          if (nb < N) smr[nb * TX + x] = 0.f;
+        if (na < N) {
+          const float gg = gam[na];
+          srow[na * TX] = va ? fmaf(rh.x, gg, rl.x * gg) : 0.f;
+        }
+        if (nb < N) {
+          const float gg = gam[nb];
+          srow[nb * TX] = vb ? fmaf(rh.y, gg, rl.y * gg) : 0.f;
         }
         U2 = U1; K2v = K1; U1 = U0; K1 = K0;
         cA = xA; cB = xB;
