@@ -32,6 +32,10 @@ Modules
   control_wave  O9: optimal control of the wave equation (Section 4): the
                 saddle-point leap-frog system, the gamma-balanced block
                 circulant preconditioner by Theorem 4, flexible GMRES.
+  nonlinear     O10: U' + K U + phi(U) = f with a cubic reaction (eq. 1.4): the
+                all-at-once residual, the exact solution by stepping with
+                Newton per step, the simplified Newton iteration eq. 1.5 with
+                the space-time averaged Jacobian K + sigma I.
 
 Every function is pinned by a test in tests/test_oracle_*.py against a
 closed form, an invariant, a bound of the paper, a worked example the paper

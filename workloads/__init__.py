@@ -344,6 +344,33 @@ def hybrid_wave2d(n=512, nt=512, T=2.0, seed=SEED_BASE + 9, name="hybrid_wave2d"
                     extra={"phi": phi, "T": T})
 
 
+def nl_manufactured1d(nx=63, nt=32, T=1.0, nu=1.0, reaction=(0.5, 1.0, 2.0), scheme=CN,
+                      alpha=1e-2, seed=SEED_BASE + 10, name="nl_manufactured1d") -> Workload:
+    """U' + K U + phi(U) = f on (0,1), Dirichlet, K = -nu d_xx, with the cubic
+    reaction phi(u) = a1 u + a2 u^2 + a3 u^3 and f chosen so that the exact
+    solution is u = exp(-t) sin(pi x).  ``extra``: the reaction coefficients
+    and the exact solution at t_1..t_nt."""
+    sp = Space(dim=1, nx=nx, nu=nu, bc_x=DIRICHLET)
+    pb = Problem(space=sp, nt=nt, dt=T / nt, scheme=scheme, alpha=alpha)
+    x = sp.xs()
+    t = (T / nt) * np.arange(nt + 1)
+    u = np.outer(np.exp(-t), np.sin(np.pi * x))
+    a1, a2, a3 = reaction
+    f = -u + nu * np.pi**2 * u + u * (a1 + u * (a2 + u * a3))
+    return Workload(name, pb, u[0].copy(), None, f, seed,
+                    extra={"reaction": tuple(reaction), "exact": u[1:].copy()})
+
+
+def nl_ade2d(nx=255, ny=255, nt=256, T=1.0, nu=1e-3, ax=1.0, ay=0.5, scheme=CN, alpha=1e-3,
+             reaction=(0.0, 0.0, 1.0), seed=SEED_BASE + 1, name="nl_ade2d") -> Workload:
+    """The ade2d grid and data (Gaussian bump, zero source) with a cubic
+    reaction, by default phi(u) = u^3 (coefficients (a1, a2, a3) in ``extra``)."""
+    w = ade2d(nx=nx, ny=ny, nt=nt, T=T, nu=nu, ax=ax, ay=ay, scheme=scheme, alpha=alpha,
+              seed=seed, name=name)
+    return Workload(name, w.problem, w.u0, None, None, seed,
+                    extra={"reaction": tuple(reaction), "center": w.extra["center"]})
+
+
 def named(name: str, **kw) -> Workload:
     """The five named workloads at their full sizes (keyword overrides allowed)."""
     table = {
@@ -356,6 +383,8 @@ def named(name: str, **kw) -> Workload:
         "hybrid_ade1d": lambda: hybrid_ade1d(**kw),
         "hybrid_ade2d": lambda: hybrid_ade2d(**kw),
         "hybrid_wave2d": lambda: hybrid_wave2d(**kw),
+        "nl_manufactured1d": lambda: nl_manufactured1d(**kw),
+        "nl_ade2d": lambda: nl_ade2d(**kw),
     }
     return table[name]()
 
