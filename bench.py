@@ -54,6 +54,10 @@ def parse():
     ap.add_argument("--no-control", action="store_true", help="skip the optimal-control leg")
     ap.add_argument("--no-wave", action="store_true",
                     help="skip the second-order (wave) hybrid ParaDiag-I leg")
+    ap.add_argument("--no-nonlinear", action="store_true",
+                    help="skip the nonlinear (simplified Newton) leg")
+    ap.add_argument("--nonlinear-only", action="store_true",
+                    help="only the nonlinear (simplified Newton) leg (one JSON object)")
     ap.add_argument("--wave-only", action="store_true",
                     help="only the second-order (wave) hybrid ParaDiag-I leg (one JSON object)")
     ap.add_argument("--control-only", action="store_true",
@@ -537,6 +541,83 @@ def wave_leg(pd, torch, dev, args):
             "paper_cpu_seconds_context": {"1_core": 1328.6, "256_cores": 20.3}}
 
 
+def nonlinear_leg(pd, torch, dev, args):
+    """Nonlinear problems by simplified Newton with the averaged Jacobian (eq.
+    1.4, eq. 1.5) on the bench grid: the ade2d problem (255 x 255, Nt = 256,
+    CN, alpha = 1e-3, Gaussian bump) with the reaction phi(u) = u^3.  Timed: a
+    mixed-plan solve (FP64 residual, FP32 preconditioner with the averaged
+    shift) from a zero guess to ||r|| <= 1e-10 ||b||, the zero fill of the
+    iterate included; beside it one FP64-plan solve and the FP64 residual
+    kernel on its own (FP64 ALU bound: 29 flops per unknown)."""
+    import workloads as W
+    wl = W.nl_ade2d()
+    pb = wl.problem
+    sp = pb.space
+    a = wl.extra["reaction"]
+    space = dict(dim=2, nx=sp.nx, ny=sp.ny, nu=sp.nu, ax=sp.ax, ay=sp.ay, bc_x=sp.bc_x,
+                 bc_y=sp.bc_y)
+    stream = torch.cuda.current_stream()
+    NS = pb.unknowns
+    tol = 1e-10
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    plan = pd.Plan(space, pb.nt, pb.dt, pb.alpha, pd.PD_CN, 0.5, pd.PD_MIXED, stream)
+    b = plan.nl_build_rhs(a, torch.from_numpy(wl.u0).to(dev))
+    u = torch.zeros_like(b)
+    plan.nl_solve(a, b, u, tol=tol, maxit=80)
+    k = max(1, min(args.steps, 3))
+    l0 = plan.launches()
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(k):
+        u.zero_()
+        _, it, rel = plan.nl_solve(a, b, u, tol=tol, maxit=80)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / k
+    launches = (plan.launches() - l0) // k
+    _, sigma, _ = plan.nl_residual(a, b, u)
+    # the residual kernel alone
+    r = torch.empty_like(b)
+    plan.nl_residual(a, b, u, r)
+    kr = 5
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(kr):
+        pd.pd_nl_residual(plan._h, a, b.data_ptr(), u.data_ptr(), r.data_ptr(), scalars=False)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms_r = e0.elapsed_time(e1) / kr
+    plan.close()
+    flops = 29.0 * NS
+    fp64_peak = FP32_ALU_PEAK / 64.0
+    tf = flops / (ms_r / 1e3) / 1e12
+    plan64 = pd.Plan(space, pb.nt, pb.dt, pb.alpha, pd.PD_CN, 0.5, pd.PD_FP64, stream)
+    u64 = torch.zeros_like(b)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    _, it64, rel64 = plan64.nl_solve(a, b, u64, tol=tol, maxit=80)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms64 = e0.elapsed_time(e1)
+    diff = float((u - u64).abs().max() / u64.abs().max())
+    plan64.close()
+    return {"workload": "nl_ade2d_255x255x256: u_t - nu Lap u + a.grad u + u^3 = 0 on the "
+                        "ade2d grid (x periodic, y Dirichlet, nu = 1e-3, velocity (1, 0.5)), "
+                        "Crank-Nicolson, alpha = 1e-3, Gaussian bump",
+            "unknowns": NS, "ms_per_solve": ms, "value": NS / (ms / 1e3), "unit": UNIT,
+            "newton_corrections": it, "relres": rel, "residual_tol": tol,
+            "sigma_at_solution": sigma, "gpu_launches": launches,
+            "residual_kernel": {"ms": ms_r, "bound": "alu", "achieved": tf, "peak": fp64_peak,
+                                "unit": "TFLOP/s (FP64)", "frac": tf / fp64_peak,
+                                "algorithmic_flops": flops,
+                                "peak_source": "FP64 CUDA-core rate taken as 1/64 of 152 SMs x "
+                                               "128 FP32 lanes x 2 flops x 2070 MHz (derived)"},
+            "fp64_plan": {"ms_per_solve": ms64, "value": NS / (ms64 / 1e3),
+                          "newton_corrections": it64, "relres": rel64,
+                          "max_rel_diff_vs_mixed": diff}}
+
+
 def control_leg(pd, torch, dev, args):
     """Optimal control of the 2D wave equation (Section 4) on the largest mesh of
     Table T2A, (256, 256, 257): 255 x 255 interior points, Nt = 257, T = 2,
@@ -685,6 +766,12 @@ def main():
     torch.cuda.synchronize()
     if args.control_only:
         out = control_leg(pd, torch, dev, args)
+        if rank == 0:
+            print(json.dumps(out), flush=True)
+        plan.close()
+        return
+    if args.nonlinear_only:
+        out = nonlinear_leg(pd, torch, dev, args)
         if rank == 0:
             print(json.dumps(out), flush=True)
         plan.close()
@@ -844,6 +931,9 @@ def main():
     hybrid = None
     if not args.no_hybrid:
         hybrid = hybrid_leg(pd, torch, dev, args)
+    nonlinear = None
+    if not args.no_nonlinear:
+        nonlinear = nonlinear_leg(pd, torch, dev, args)
     wave = None
     if not args.no_wave:
         wave = wave_leg(pd, torch, dev, args)
@@ -893,6 +983,7 @@ def main():
                "paradiag1": pd1,
                "paradiag1_hybrid": hybrid,
                "paradiag1_hybrid_wave": wave,
+               "nonlinear_simplified_newton": nonlinear,
                "optimal_control_wave": control,
                "gpu_launches": launches}
         print(json.dumps(out), flush=True)

@@ -162,6 +162,38 @@ PD_API pd_status pd_solve_windows(pd_plan* plan, const double* u0, const double*
                                   double* u, int mode, double tol, int maxit, int restart,
                                   int* iters_total, double* relres_max);
 
+/* Nonlinear problems U' + K U + phi(U) = f (Section 1, eq. 1.4 with M = I and
+ * f(U) = K U + phi(U)) on a theta-method plan; phi(u) = a[0] u + a[1] u^2 +
+ * a[2] u^3 acts pointwise.  a: 3 doubles in HOST memory (finite); every other
+ * array is device FP64 in the time-major layout [Nt][S] (u0: [S], f: [Nt+1][S]
+ * or NULL), caller-owned.  Leap-frog plans return PD_ERR_UNSUPPORTED.
+ *
+ * pd_nl_build_rhs: b of eq. 1.4, the linear right-hand side of
+ * pd_build_rhs with -(1 - theta) phi(u0) added to the first row.
+ *
+ * pd_nl_residual: r = b - (B1 (x) I) u - (B2 (x) I) F(u), F(u)_n = K U_n +
+ * phi(U_n), in FP64.  sigma (host, may be NULL) receives the mean of phi'(U)
+ * over all time levels and grid points, rnorm2 (host, may be NULL) ||r||^2;
+ * asking for either synchronises the plan's stream.
+ *
+ * pd_nl_solve: the simplified Newton iteration of eq. 1.5 from the initial
+ * guess in u (overwritten by the iterate): r as above, z = P_alpha(u)^{-1} r
+ * with P_alpha(u) = C1 (x) I + C2 (x) (K + sigma I), sigma the mean of
+ * phi'(U) (the averaged Jacobian), u += z; until ||r|| <= tol ||b|| or maxit
+ * corrections.  The plan's preconditioner precision applies (FP32 on mixed
+ * plans, the residual is always FP64).  iters: corrections applied; relres:
+ * the last ||r|| / ||b|| (either may be NULL).  Returns PD_ERR_NOT_CONVERGED
+ * after maxit corrections, PD_ERR_NONFINITE on a NaN or Inf (a diverging
+ * iteration).  Allocates two [Nt][S] FP64 work arrays in the plan on first
+ * use; synchronises the plan's stream once per correction; the plan's own
+ * eigenvalue table is restored before it returns. */
+PD_API pd_status pd_nl_build_rhs(pd_plan* plan, const double* a, const double* u0,
+                                 const double* f, double* b);
+PD_API pd_status pd_nl_residual(pd_plan* plan, const double* a, const double* b, const double* u,
+                                double* r, double* sigma, double* rnorm2);
+PD_API pd_status pd_nl_solve(pd_plan* plan, const double* a, const double* b, double* u,
+                             double tol, int maxit, int* iters, double* relres);
+
 /* Solve A^T lambda = g (the transposed all-at-once system, backward in time).
  * Uses J A^T J = B1 (x) I + B2 (x) K^T (J = time reversal, B1, B2 Toeplitz):
  * a forward ParaDiag solve with K^T on time-reversed data.  lambda: initial

@@ -98,6 +98,9 @@ _SIGS = {
                                          _I, _D]),
     "pd_solve_windows": (ctypes.c_int, [_P, _P, _P, ctypes.c_int, _P, ctypes.c_int, ctypes.c_double,
                                         ctypes.c_int, ctypes.c_int, _I, _D]),
+    "pd_nl_build_rhs": (ctypes.c_int, [_P, _D, _P, _P, _P]),
+    "pd_nl_residual": (ctypes.c_int, [_P, _D, _P, _P, _P, _D, _D]),
+    "pd_nl_solve": (ctypes.c_int, [_P, _D, _P, _P, ctypes.c_double, ctypes.c_int, _I, _D]),
     "pd1_profile_sweep": (ctypes.c_int, [_P, _P, _P, ctypes.c_int, ctypes.POINTER(ctypes.c_float)]),
     "pd1_workspace": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_ulonglong)]),
     "pd1_last_error": (ctypes.c_char_p, [_P]),
@@ -376,6 +379,34 @@ def pd_solve_windows(plan, u0, f, nwin, u, mode, tol, maxit, restart):
     rr = ctypes.c_double(0.0)
     st = load().pd_solve_windows(plan, u0, f, nwin, u, mode, tol, maxit, restart,
                                  ctypes.byref(it), ctypes.byref(rr))
+    return st, it.value, rr.value
+
+
+def _reaction(a):
+    if len(a) != 3:
+        raise ValueError("reaction coefficients: (a1, a2, a3)")
+    return (ctypes.c_double * 3)(*[float(v) for v in a])
+
+
+def pd_nl_build_rhs(plan, a, u0, f, b):
+    return load().pd_nl_build_rhs(plan, _reaction(a), u0, f, b)
+
+
+def pd_nl_residual(plan, a, b, u, r, scalars=True):
+    """scalars=False: no sigma / ||r||^2 read-back (no stream synchronisation)."""
+    if not scalars:
+        return load().pd_nl_residual(plan, _reaction(a), b, u, r, None, None), None, None
+    sig = ctypes.c_double(0.0)
+    rn2 = ctypes.c_double(0.0)
+    st = load().pd_nl_residual(plan, _reaction(a), b, u, r, ctypes.byref(sig), ctypes.byref(rn2))
+    return st, sig.value, rn2.value
+
+
+def pd_nl_solve(plan, a, b, u, tol, maxit):
+    it = ctypes.c_int(0)
+    rr = ctypes.c_double(0.0)
+    st = load().pd_nl_solve(plan, _reaction(a), b, u, tol, maxit, ctypes.byref(it),
+                            ctypes.byref(rr))
     return st, it.value, rr.value
 
 
@@ -671,6 +702,36 @@ class Plan:
         st, it, rel = pd_solve_windows(self._h, _ptr(u0), _ptr(f), nwin, _ptr(u), mode, tol,
                                        maxit, restart)
         self._check(st, "pd_solve_windows")
+        return u, it, rel
+
+    # nonlinear problems U' + K U + phi(U) = f, phi(u) = a1 u + a2 u^2 + a3 u^3
+    def nl_build_rhs(self, a, u0, f=None, b=None):
+        import torch
+        self._check_t(u0, self.S)
+        if f is not None:
+            self._check_t(f, (self.nt + 1) * self.S)
+        b = torch.empty((self.nt, self.S), dtype=torch.float64, device=u0.device) if b is None else b
+        self._check(pd_nl_build_rhs(self._h, a, _ptr(u0), _ptr(f), _ptr(b)), "pd_nl_build_rhs")
+        return b
+
+    def nl_residual(self, a, b, u, r=None):
+        """(r, sigma = mean phi'(u), ||r||^2)"""
+        import torch
+        self._check_t(b); self._check_t(u)
+        r = torch.empty_like(b) if r is None else r
+        st, sig, rn2 = pd_nl_residual(self._h, a, _ptr(b), _ptr(u), _ptr(r))
+        self._check(st, "pd_nl_residual")
+        return r, sig, rn2
+
+    def nl_solve(self, a, b, u=None, tol=1e-10, maxit=100, allow_not_converged=False):
+        """Simplified Newton (eq. 1.5) from u (zeros if None); (u, corrections, relres)."""
+        import torch
+        self._check_t(b)
+        u = torch.zeros_like(b) if u is None else u
+        self._check_t(u)
+        st, it, rel = pd_nl_solve(self._h, a, _ptr(b), _ptr(u), tol, maxit)
+        if not (st == PD_OK or (allow_not_converged and st == PD_ERR_NOT_CONVERGED)):
+            self._check(st, "pd_nl_solve")
         return u, it, rel
 
     def adjoint_solve(self, g, lam=None, mode=PD_STATIONARY, tol=1e-10, maxit=50, restart=30):

@@ -130,7 +130,7 @@ void free_plan(pd_plan* p) {
                   p->mu,   p->spec, p->spec2, p->Udf,  p->Bdf,   p->w64a,  p->w64b,
                   p->dsc,  p->dflag, p->V,   p->Z,      p->dh,    p->Gf_hi, p->Gf_lo,
                   p->Gi_hi, p->Gi_lo, const_cast<void*>(p->xf.chirp),
-                  const_cast<void*>(p->xf.bhat), p->amax};
+                  const_cast<void*>(p->xf.bhat), p->amax, p->nl_r, p->nl_z};
   for (void* q : ptrs)
     if (q) cudaFree(q);
   if (p->hsc) cudaFreeHost(p->hsc);
@@ -816,6 +816,7 @@ InvArgs plan_inv_args(const pd_plan* p) { return inv_base_impl(p); }
 TriArgs plan_tri_args(const pd_plan* p, void* data) { return tri_args_impl(p, data); }
 pd_status plan_step_b(pd_plan* p) { return step_b(p); }
 pd_status plan_fail_cuda(pd_plan* p, cudaError_t e, const char* what) { return fail_cuda(p, e, what); }
+pd_status plan_precond(pd_plan* p, const double* r, double* z) { return precond_into(p, r, z); }
 
 extern "C" {
 

@@ -53,6 +53,9 @@ struct pd_plan {
   double* Z = nullptr;
   double* dh = nullptr;
   int gm_cap = 0;
+  // simplified Newton workspace (nonlinear problems), allocated on first use
+  double* nl_r = nullptr;
+  double* nl_z = nullptr;
   pd_plan* adj = nullptr;
   // the mixed stationary iteration as one CUDA graph (built on first use;
   // graph_state 0 untried, 1 ready, -1 unavailable: the host loop runs)
@@ -75,6 +78,8 @@ TriArgs plan_tri_args(const pd_plan* p, void* data);
 // x-transform) on p->spec
 pd_status plan_step_b(pd_plan* p);
 pd_status plan_fail_cuda(pd_plan* p, cudaError_t e, const char* what);
+// z = P_alpha^{-1} r (FP64 in and out) with the plan's current eigenvalue table
+pd_status plan_precond(pd_plan* p, const double* r, double* z);
 // Plan creation.  With row_lam (2 nt complex numbers as re, im pairs) the plan
 // holds no time transform: its step (b) solves one system per time row n,
 // (lambda_1n I + lambda_2n K) z_n = s_n, with lambda_1n = row_lam[4n] +

@@ -87,3 +87,11 @@ def test_pdc_plan_create_rejects_bad_arguments_without_gpu():
     assert pd.pdc_plan_create(sp, 16, 2.0, 1e-4, 0, None)[0] == pd.PD_ERR_UNSUPPORTED  # 4 | nt
     assert pd.pdc_plan_create(sp, 17, 2.0, 0.0, 0, None)[0] == pd.PD_ERR_ARG          # gamma
     assert pd.pdc_plan_create(sp, 17, -1.0, 1e-4, 0, None)[0] == pd.PD_ERR_ARG        # T
+
+
+def test_nonlinear_entry_points_reject_a_null_plan_without_gpu():
+    import paradiag_gb300 as pd
+    pd.build()
+    assert pd.pd_nl_build_rhs(None, (0, 0, 1), None, None, None) == pd.PD_ERR_ARG
+    assert pd.pd_nl_residual(None, (0, 0, 1), None, None, None)[0] == pd.PD_ERR_ARG
+    assert pd.pd_nl_solve(None, (0, 0, 1), None, None, 1e-10, 10)[0] == pd.PD_ERR_ARG
