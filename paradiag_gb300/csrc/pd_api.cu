@@ -29,7 +29,9 @@ using cd = std::complex<double>;
 struct LoopState {
   double tol, s_scale, prev_rel, rel;
   int maxit, it, status, norm_only, n_body, n_update;
-  int kmode;  // mode of the next forward kernel (read by it from device memory)
+  int kmode;       // mode of the next forward kernel (read by it from device memory)
+  int imode;       // mode of the next inverse kernel (likewise)
+  int zero_guess;  // the solve started from u = 0
 };
 struct SolveGraph {
   cudaGraph_t g = nullptr;
@@ -387,6 +389,8 @@ __global__ void k_loop_check(LoopState* st, double* dsc, const int* flag,
       stop = false;
       ++s.it;
       ++s.n_update;
+      // the first update of a zero iterate stores the correction
+      s.imode = (s.zero_guess && s.n_update == 1) ? INV_SET_DF : INV_UPDATE_DF;
       if (s.prev_rel > 0.0) {
         const double rho = rel / s.prev_rel;
         s.norm_only = (rho < 1.0 && rel * rho <= 0.25 * s.tol) ? 1 : 0;
@@ -402,15 +406,20 @@ __global__ void k_loop_check(LoopState* st, double* dsc, const int* flag,
 }
 
 // start of a graph solve: the loop state set on the device (no host buffer
-// that a queued copy could still be reading)
-__global__ void k_loop_init(LoopState* st, double tol, double s_scale, int maxit) {
+// that a queued copy could still be reading).  nonzero: raised by the entry
+// kernel when the initial guess has a nonzero entry; from a zero guess the
+// first forward kernel forms r = s b without reading the iterate
+__global__ void k_loop_init(LoopState* st, double tol, double s_scale, int maxit,
+                            const int* nonzero) {
   LoopState s;
   memset(&s, 0, sizeof(s));
   s.tol = tol;
   s.s_scale = s_scale;
   s.prev_rel = -1.0;
   s.maxit = maxit;
-  s.kmode = FWD_RESIDUAL;
+  s.zero_guess = *nonzero == 0 ? 1 : 0;
+  s.kmode = s.zero_guess ? FWD_ZERO_GUESS : FWD_RESIDUAL;
+  s.imode = INV_UPDATE_DF;
   *st = s;
 }
 
@@ -504,6 +513,7 @@ pd_status build_graph_impl(pd_plan* p, SolveGraph* G) {
     if (st == PD_OK) {
       InvArgs ia = inv_base_impl(p);
       ia.mode = INV_UPDATE_DF;
+      ia.mode_dev = &G->dst->imode;
       ia.Udf = p->Udf;
       ia.igam = p->igam_s;
       const cudaError_t e3 = launch_time_inv(ia, false, G->cs);
@@ -548,10 +558,12 @@ SolveGraph* plan_graph(pd_plan* p) {
 pd_status enqueue_graph_solve(pd_plan* p, SolveGraph* G, const double* b, double* u, double tol,
                               int maxit) {
   const size_t ns = NS(p);
-  CU(cudaMemsetAsync(p->dsc, 0, 2 * sizeof(double), p->stream));
+  // dsc[0]: ||s b||^2, dsc[1]: ||r'||^2, dsc[3] (as int): nonzero initial guess
+  int* nonzero = reinterpret_cast<int*>(p->dsc + 3);
+  CU(cudaMemsetAsync(p->dsc, 0, 4 * sizeof(double), p->stream));
   CU(cudaMemsetAsync(p->dflag, 0, sizeof(int), p->stream));
-  LK(launch_entry_df(u, b, p->s_scale, p->Udf, p->Bdf, ns, p->dsc, p->stream));
-  k_loop_init<<<1, 1, 0, p->stream>>>(G->dst, tol, p->s_scale, maxit);
+  LK(launch_entry_df(u, b, p->s_scale, p->Udf, p->Bdf, ns, p->dsc, p->stream, nonzero));
+  k_loop_init<<<1, 1, 0, p->stream>>>(G->dst, tol, p->s_scale, maxit, nonzero);
   LK(cudaGetLastError());
   CU(cudaGraphLaunch(G->ge, p->stream));
   const int grid = (int)std::min<size_t>((ns + 255) / 256, (size_t)152 * 16);

@@ -87,11 +87,16 @@ struct InvArgs {
   float2* Udf;                    // mixed: iterate (double-float), updated in place
   double* out64;                  // FP64 output (z) or FP64 iterate (updated)
   int* flag;                      // bit 0 set on a non-finite value (may be null)
+  const int* mode_dev = nullptr;  // if set, the mode is read from device memory
 };
 
 // FWD_RESIDUAL_NORM: the residual and its norm only (no transform, no spectrum)
-enum { FWD_STANDALONE = 0, FWD_RESIDUAL = 1, FWD_RESIDUAL_NORM = 2 };
-enum { INV_UPDATE_DF = 0, INV_OUT64 = 1, INV_UPDATE64 = 2 };
+// FWD_ZERO_GUESS: the residual of a zero iterate, r = s b (no iterate loads,
+// no stencil; the same arithmetic as FWD_RESIDUAL with U = 0, mixed path only)
+enum { FWD_STANDALONE = 0, FWD_RESIDUAL = 1, FWD_RESIDUAL_NORM = 2, FWD_ZERO_GUESS = 3 };
+// INV_SET_DF: U = z (the first update of a zero iterate; equal to INV_UPDATE_DF
+// on U = 0 without reading U)
+enum { INV_UPDATE_DF = 0, INV_OUT64 = 1, INV_UPDATE64 = 2, INV_SET_DF = 3 };
 
 // Arguments of the batched shifted tridiagonal solve (K2, step (b)).
 // System q = k*J + j (k < nh time frequencies, j < J spatial modes) of length n:
@@ -155,8 +160,9 @@ cudaError_t launch_build_rhs(const Stencil& st, const TimeBand& tb, int scheme, 
 cudaError_t launch_to_df(const double* x, double scale, float2* y, size_t n, cudaStream_t s);
 cudaError_t launch_from_df(const float2* x, double* y, size_t n, cudaStream_t s);
 // U = split(u), B = split(scale b), *norm2 += ||scale b||^2 (FP32 partial sums)
+// nonzero (may be null): set to 1 when some entry of u is not zero
 cudaError_t launch_entry_df(const double* u, const double* b, double scale, float2* U, float2* B,
-                            size_t n, double* norm2, cudaStream_t s);
+                            size_t n, double* norm2, cudaStream_t s, int* nonzero = nullptr);
 cudaError_t launch_norm2(const double* x, size_t n, double* out, cudaStream_t s);
 cudaError_t launch_flip_time(const double* x, double* y, int N, int S, cudaStream_t s);
 cudaError_t launch_dots(const double* V, int nv, size_t n, const double* w, double* h,

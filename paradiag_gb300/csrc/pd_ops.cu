@@ -98,17 +98,21 @@ __global__ void k_to_df(const double* __restrict__ x, dfc scale, float2* __restr
 // on this GPU; a few significant digits suffice for the relative residual).
 __global__ void k_entry_df(const double* __restrict__ u, const double* __restrict__ b, dfc scale,
                            float2* __restrict__ U, float2* __restrict__ B, size_t n,
-                           double* norm2) {
+                           double* norm2, int* nonzero) {
   __shared__ double red[TB / 32];
   float part = 0.f;
+  bool nz = false;
   for (size_t i = blockIdx.x * (size_t)TB + threadIdx.x; i < n; i += (size_t)gridDim.x * TB) {
     const double ui = u[i], bi = b[i];
+    nz |= ui != 0.0;
     const df uv = df_from_double(ui);
     const df bv = df_mul(df_from_double(bi), df_make(scale.hi, scale.lo));
     U[i] = make_float2(uv.hi, uv.lo);
     B[i] = make_float2(bv.hi, bv.lo);
     part = fmaf(bv.hi, bv.hi, part);
   }
+  if (nonzero != nullptr && __any_sync(0xffffffffu, nz) && (threadIdx.x & 31) == 0)
+    atomicOr(nonzero, 1);
   double pd = (double)part;
   for (int o = 16; o > 0; o >>= 1) pd += __shfl_down_sync(0xffffffffu, pd, o);
   if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = pd;
@@ -229,8 +233,8 @@ cudaError_t launch_to_df(const double* x, double scale, float2* y, size_t n, cud
 }
 
 cudaError_t launch_entry_df(const double* u, const double* b, double scale, float2* U, float2* B,
-                            size_t n, double* norm2, cudaStream_t s) {
-  k_entry_df<<<grid_for(n), TB, 0, s>>>(u, b, dfc_from(scale), U, B, n, norm2);
+                            size_t n, double* norm2, cudaStream_t s, int* nonzero) {
+  k_entry_df<<<grid_for(n), TB, 0, s>>>(u, b, dfc_from(scale), U, B, n, norm2, nonzero);
   return cudaGetLastError();
 }
 

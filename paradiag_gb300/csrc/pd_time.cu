@@ -450,6 +450,31 @@ PD_D void time_fwd_body(const FwdArgs& a, int tile) {
       // Rows before the first level are zero, so the carried terms need no checks.
       const int rpc2 = (N + 2 * nchunks - 1) / (2 * nchunks);
       const int nA = chunk * rpc2, nB = nA + nchunks * rpc2;
+      if (mode == FWD_ZERO_GUESS) {
+        // r' = s b: the residual loop below with U = 0 (every term it adds to
+        // the accumulator is an exact zero), row for row, so the spectrum and
+        // the norm are those of FWD_RESIDUAL on a zero iterate
+        const int Nm1 = N - 1;
+        const float2* __restrict__ Bcol = a.Bdf + (g.valid ? s : 0);
+        float2 part = make_float2(0.f, 0.f);
+        float* srow = smr + x;
+#pragma unroll 4
+        for (int i = 0; i < rpc2; ++i) {
+          const int na = nA + i, nb = nB + i;
+          const float2 bA = __ldg(Bcol + (size_t)min(na, Nm1) * S);
+          const float2 bB = __ldg(Bcol + (size_t)min(nb, Nm1) * S);
+          const DF2 Bv = df2_pack(bA, bB);
+          const float2 rh = f2add(Bv.hi, Bv.lo);
+          const float2 rl = f2sub(Bv.lo, f2sub(rh, Bv.hi));
+          const bool va = na < N && g.valid, vb = nb < N && g.valid;
+          const float2 rn = make_float2(va ? rh.x : 0.f, vb ? rh.y : 0.f);
+          part = f2fma(rn, rn, part);
+          if (na < N) srow[na * TX] = va ? fmaf(rh.x, gam[na], rl.x * gam[na]) : 0.f;
+          if (nb < N) srow[nb * TX] = vb ? fmaf(rh.y, gam[nb], rl.y * gam[nb]) : 0.f;
+        }
+        const float part1 = part.x + part.y;
+        nrm = (double)part1 * a.rscale2;
+      } else {
       K2 kk[5];
 #pragma unroll
       for (int q = 0; q < 5; ++q) kk[q] = k2_of(a.kap[q]);
@@ -548,6 +573,7 @@ PD_D void time_fwd_body(const FwdArgs& a, int tile) {
       }
       const float part1 = part.x + part.y;
       nrm = (double)part1 * a.rscale2;
+      }
     } else {
       double U1 = 0, U2 = 0, K1 = 0, K2 = 0, U0, K0;
       const TimeBand& tb = a.tb;
@@ -693,6 +719,8 @@ PD_D void time_inv_body(const InvArgs& a, int tile) {
   else bluestein_tile<C, true, EPT>(sm, N, a.xf, lgTXc, stw);
 
   const R* ig = reinterpret_cast<const R*>(a.igam);
+  // the mode may come from device memory (the solver's graph decides it)
+  const int mode = a.mode_dev != nullptr ? *a.mode_dev : a.mode;
   bool bad = false;
   {
     // every element of this thread lies in the same column x (TT % TX == 0)
@@ -704,7 +732,7 @@ PD_D void time_inv_body(const InvArgs& a, int tile) {
       for (int nb = n0; nb < N; nb += U * nstep) {
         if constexpr (PREC == 0) {
           float2 uv[U];
-          if (a.mode == INV_UPDATE_DF) {
+          if (mode == INV_UPDATE_DF) {
 #pragma unroll
             for (int u = 0; u < U; ++u) {
               const int n = nb + u * nstep;
@@ -718,17 +746,19 @@ PD_D void time_inv_body(const InvArgs& a, int tile) {
             const float dz = smr[n * TX + x] * ig[n];
             if (!isfinite(dz)) bad = true;
             const size_t idx = (size_t)n * S + s;
-            if (a.mode == INV_UPDATE_DF) {
+            if (mode == INV_UPDATE_DF) {
               df t = two_sum(uv[u].x, dz);
               t = fast_two_sum(t.hi, t.lo + uv[u].y);
               a.Udf[idx] = make_float2(t.hi, t.lo);
+            } else if (mode == INV_SET_DF) {
+              a.Udf[idx] = make_float2(dz, 0.f);
             } else {
               a.out64[idx] = double_from_float(dz);
             }
           }
         } else {
           double uv[U];
-          if (a.mode == INV_UPDATE64) {
+          if (mode == INV_UPDATE64) {
 #pragma unroll
             for (int u = 0; u < U; ++u) {
               const int n = nb + u * nstep;
@@ -742,7 +772,7 @@ PD_D void time_inv_body(const InvArgs& a, int tile) {
             const double dz = smr[n * TX + x] * ig[n];
             if (!isfinite(dz)) bad = true;
             const size_t idx = (size_t)n * S + s;
-            a.out64[idx] = (a.mode == INV_UPDATE64) ? uv[u] + dz : dz;
+            a.out64[idx] = (mode == INV_UPDATE64) ? uv[u] + dz : dz;
           }
         }
       }
