@@ -143,8 +143,12 @@ PD_API pd_status pd_solve_async(pd_plan* plan, const double* b, double* u, doubl
  * as the last one's. */
 PD_API pd_status pd_solve_result(pd_plan* plan, int* iters, double* relres);
 
-/* The same solve with HOST buffers: copies b and the initial guess to the
- * device, solves, and copies u back (all on the plan's stream). */
+/* The same solve with HOST buffers.  Mixed-precision stationary solves on
+ * pinned (device-mapped) host buffers read b and the initial guess, and write
+ * u, directly from the solver's entry and exit kernels over the host link;
+ * otherwise b and the initial guess are copied to the device, the solve runs
+ * and u is copied back (all on the plan's stream).  Returns when u_host holds
+ * the result. */
 PD_API pd_status pd_solve_host(pd_plan* plan, const double* b_host, double* u_host, int mode,
                         double tol, int maxit, int restart, int* iters, double* relres);
 

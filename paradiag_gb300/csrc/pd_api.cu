@@ -447,6 +447,17 @@ cudaGraphNode_t graph_leaf(cudaGraph_t g) {
   return nullptr;
 }
 
+// device address of pinned, device-mapped host memory (null for any other
+// host pointer, which then goes through staging copies)
+void* mapped_alias(const void* h) {
+  cudaPointerAttributes at;
+  if (cudaPointerGetAttributes(&at, h) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  return at.type == cudaMemoryTypeHost ? at.devicePointer : nullptr;
+}
+
 pd_status build_graph_impl(pd_plan* p, SolveGraph* G) {
   CU(cudaStreamCreateWithFlags(&G->cs, cudaStreamNonBlocking));
   CU(cudaMalloc(&G->dst, sizeof(LoopState)));
@@ -1410,6 +1421,18 @@ pd_status pd_solve_result(pd_plan* p, int* iters, double* relres) {
 pd_status pd_solve_host(pd_plan* p, const double* b_host, double* u_host, int mode, double tol,
                         int maxit, int restart, int* iters, double* relres) {
   if (!p || !b_host || !u_host) return set_err(p, PD_ERR_ARG, "null argument");
+  // Mixed stationary solves on pinned (device-mapped) host buffers read b and
+  // the initial guess in the entry kernel and write u in the exit kernel
+  // directly over the host link, with no staging copies.
+  if (!p->fp64 && mode == PD_STATIONARY && tol >= 0.0 && maxit >= 0) {
+    const double* bd = static_cast<const double*>(mapped_alias(b_host));
+    double* ud = static_cast<double*>(mapped_alias(u_host));
+    SolveGraph* G = (bd && ud) ? plan_graph(p) : nullptr;
+    if (G) {
+      CHK(enqueue_graph_solve(p, G, bd, ud, tol, maxit));
+      return finish_graph_solves(p, G, iters, relres);
+    }
+  }
   const size_t bytes = NS(p) * sizeof(double);
   if (!p->w64a) CHK(dalloc(p, (void**)&p->w64a, bytes));
   if (!p->w64b) CHK(dalloc(p, (void**)&p->w64b, bytes));

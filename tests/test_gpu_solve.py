@@ -93,6 +93,32 @@ def test_solve_host_buffers(pd):
     plan.close()
 
 
+@pytest.mark.parametrize("pinned", [True, False])
+@pytest.mark.parametrize("prec", ["mixed", "fp64"])
+def test_solve_host_buffers_guess_and_memory_kinds(pd, pinned, prec):
+    # pinned buffers of a mixed plan are read and written by the solver's own
+    # kernels (no staging copies); pageable buffers and FP64 plans are staged;
+    # a nonzero initial guess must be read from the host either way
+    import torch
+    w = W.ade2d(nx=31, ny=20, nt=32)
+    pb = w.problem
+    b = _rhs(w)
+    uref = S.solve_sequential(pb, b)
+    plan = make_plan(pb, pd.PD_FP64 if prec == "fp64" else pd.PD_MIXED)
+    guess = uref + 1e-3 * W.uniform(W.SEED_BASE + 420, uref.size, -1, 1).reshape(uref.shape)
+    bh = torch.from_numpy(b.copy())
+    uh = torch.from_numpy(guess.copy())
+    if pinned:
+        bh, uh = bh.pin_memory(), uh.pin_memory()
+    _, it, rel = plan.solve_host(bh, uh, tol=1e-12, maxit=30)
+    assert rel <= 1e-12
+    assert rel2(uh.numpy(), uref) <= 1e-10
+    # the same solve on device buffers takes the same iterations
+    _, it_dev, _ = plan.solve(dev(b), dev(guess), tol=1e-12, maxit=30)
+    assert it == it_dev
+    plan.close()
+
+
 def test_not_converged_and_zero_rhs(pd):
     import torch
     w = W.ade1d(nx=31, nt=16)
