@@ -549,8 +549,9 @@ def nonlinear_leg(pd, torch, dev, args):
     CN, alpha = 1e-3, Gaussian bump) with the reaction phi(u) = u^3.  Timed: a
     mixed-plan solve (FP64 residual, FP32 preconditioner with the averaged
     shift) from a zero guess to ||r|| <= 1e-10 ||b||, the zero fill of the
-    iterate included; beside it one FP64-plan solve and the FP64 residual
-    kernel on its own (FP64 ALU bound: 29 flops per unknown)."""
+    iterate included; beside it one FP64-plan solve, and the residual kernels
+    on their own (double-float on mixed plans: 24 bytes per unknown; FP64 on
+    FP64 plans: 29 flops per unknown)."""
     import workloads as W
     wl = W.nl_ade2d()
     pb = wl.problem
@@ -579,22 +580,28 @@ def nonlinear_leg(pd, torch, dev, args):
     ms = e0.elapsed_time(e1) / k
     launches = (plan.launches() - l0) // k
     _, sigma, _ = plan.nl_residual(a, b, u)
-    # the residual kernel alone
-    r = torch.empty_like(b)
-    plan.nl_residual(a, b, u, r)
-    kr = 5
-    torch.cuda.synchronize()
-    e0.record(stream)
-    for _ in range(kr):
-        pd.pd_nl_residual(plan._h, a, b.data_ptr(), u.data_ptr(), r.data_ptr(), scalars=False)
-    e1.record(stream)
-    torch.cuda.synchronize()
-    ms_r = e0.elapsed_time(e1) / kr
+    def time_resid(pl, reps=5):
+        r = torch.empty_like(b)
+        pl.nl_residual(a, b, u, r)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(reps):
+            pd.pd_nl_residual(pl._h, a, b.data_ptr(), u.data_ptr(), r.data_ptr(), scalars=False)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / reps
+
+    # the residual kernel alone: double-float on the mixed plan
+    ms_r = time_resid(plan)
     plan.close()
+    hbm, _, src = peaks()
+    rbytes = 24.0 * NS
+    gbs = rbytes / (ms_r / 1e3) / 1e9
+    plan64 = pd.Plan(space, pb.nt, pb.dt, pb.alpha, pd.PD_CN, 0.5, pd.PD_FP64, stream)
+    ms_r64 = time_resid(plan64, reps=3)
     flops = 29.0 * NS
     fp64_peak = FP32_ALU_PEAK / 64.0
-    tf = flops / (ms_r / 1e3) / 1e12
-    plan64 = pd.Plan(space, pb.nt, pb.dt, pb.alpha, pd.PD_CN, 0.5, pd.PD_FP64, stream)
+    tf = flops / (ms_r64 / 1e3) / 1e12
     u64 = torch.zeros_like(b)
     torch.cuda.synchronize()
     e0.record(stream)
@@ -610,12 +617,18 @@ def nonlinear_leg(pd, torch, dev, args):
             "unknowns": NS, "ms_per_solve": ms, "value": NS / (ms / 1e3), "unit": UNIT,
             "newton_corrections": it, "relres": rel, "residual_tol": tol,
             "sigma_at_solution": sigma, "gpu_launches": launches,
-            "residual_kernel": {"ms": ms_r, "bound": "alu", "achieved": tf, "peak": fp64_peak,
-                                "traffic": 374.4e6,
-                                "unit": "TFLOP/s (FP64)", "frac": tf / fp64_peak,
-                                "algorithmic_flops": flops,
-                                "peak_source": "FP64 CUDA-core rate taken as 1/64 of 152 SMs x "
-                                               "128 FP32 lanes x 2 flops x 2070 MHz (derived)"},
+            "residual_kernel": {"kernel": "k_nl_resid_df (double-float on the FP32 pipes)",
+                                "ms": ms_r, "algorithmic_bytes": rbytes, "achieved_GBps": gbs,
+                                "frac_of_measured_hbm": gbs / hbm, "peak_source": src,
+                                "limiter": "instruction issue (double-float arithmetic and the "
+                                           "integer splits of the FP64 inputs)"},
+            "residual_kernel_fp64_plan": {"kernel": "k_nl_resid (FP64)", "ms": ms_r64,
+                                          "bound": "alu", "achieved": tf, "peak": fp64_peak,
+                                          "unit": "TFLOP/s (FP64)", "frac": tf / fp64_peak,
+                                          "algorithmic_flops": flops, "traffic": 374.4e6,
+                                          "peak_source": "FP64 CUDA-core rate taken as 1/64 of "
+                                                         "152 SMs x 128 FP32 lanes x 2 flops x "
+                                                         "2070 MHz (derived)"},
             "fp64_plan": {"ms_per_solve": ms64, "value": NS / (ms64 / 1e3),
                           "newton_corrections": it64, "relres": rel64,
                           "max_rel_diff_vs_mixed": diff}}

@@ -11,11 +11,11 @@
 // sigma lambda_2k) + lambda_2k K: only the plan's table of lambda_1k changes.
 //
 // One Newton step: r = b - (B1 (x) I) u - (B2 (x) I) F(u) with ||r||^2 and the
-// sum of phi'(U) (one FP64 kernel), the shifted table, z = P_alpha^{-1} r (the
-// plan's three steps of eq. 1.3), u += z.
+// sum of phi'(U) (one kernel: FP64 on FP64 plans, double-float on mixed ones),
+// the shifted table (a small kernel reading the sum on the device), z =
+// P_alpha^{-1} r (the plan's three steps of eq. 1.3), u += z.
 #include <cmath>
-#include <complex>
-#include <vector>
+#include <cstdio>
 
 #include "pd_plan.h"
 
@@ -109,6 +109,92 @@ __global__ void __launch_bounds__(NB) k_nl_resid(Stencil st, TimeBand tb, int N,
   block_add((double)pd, red, acc + 1);
 }
 
+// ---- double-float residual (mixed plans): the same r on the FP32 pipes ----
+
+// coefficients of the double-float residual (host-rounded double-float pairs)
+struct NlDf {
+  df kc, kxl, kxu, kyl, kyu;  // stencil
+  df c10, c11, c20, c21;      // time weights c1[0], c1[1], c2[0], c2[1]
+  df a1, a2, a3;              // reaction
+};
+
+__device__ __forceinline__ df ld_df(const double* __restrict__ x, size_t i) {
+  return df_from_double(x[i]);
+}
+
+// (K U)(s) in double-float
+__device__ __forceinline__ df k_apply_df(const Stencil& st, const NlDf& c,
+                                         const double* __restrict__ U, int s, df uc) {
+  const int xg = s % st.nx, y = s / st.nx;
+  df v = df_mul(c.kc, uc);
+  if (xg > 0) v = df_add(v, df_mul(c.kxl, ld_df(U, s - 1)));
+  else if (st.bcx == PD_PERIODIC && st.nx > 1) v = df_add(v, df_mul(c.kxl, ld_df(U, s + st.nx - 1)));
+  if (xg < st.nx - 1) v = df_add(v, df_mul(c.kxu, ld_df(U, s + 1)));
+  else if (st.bcx == PD_PERIODIC && st.nx > 1) v = df_add(v, df_mul(c.kxu, ld_df(U, s - st.nx + 1)));
+  if (st.dim == 2) {
+    if (y > 0) v = df_add(v, df_mul(c.kyl, ld_df(U, s - st.nx)));
+    if (y < st.ny - 1) v = df_add(v, df_mul(c.kyu, ld_df(U, s + st.nx)));
+  }
+  return v;
+}
+
+// phi(u) = u (a1 + u (a2 + u a3)) in double-float (Horner)
+__device__ __forceinline__ df phi_df(const NlDf& c, df u) {
+  df t = df_add(df_mul(c.a3, u), c.a2);
+  t = df_add(df_mul(t, u), c.a1);
+  return df_mul(t, u);
+}
+
+// k_nl_resid with every term in double-float (unit roundoff about 2^-48):
+// the FP64 inputs are split with integer operations and r is written as
+// hi + lo (one FP64 addition per element)
+__global__ void __launch_bounds__(NB) k_nl_resid_df(Stencil st, NlDf c, Reaction cr, int N,
+                                                    const double* __restrict__ u,
+                                                    const double* __restrict__ b,
+                                                    double* __restrict__ r, double* acc) {
+  __shared__ double red[NB / 32];
+  const int s = blockIdx.x * NB + threadIdx.x;
+  const int n0 = blockIdx.y * NL_ROWS;
+  const size_t S = (size_t)st.S;
+  float pr = 0.f, pd = 0.f;
+  if (s < st.S) {
+    df Up = df_make(0.f, 0.f), Fp = Up;
+    if (n0 > 0) {
+      const double* U = u + (size_t)(n0 - 1) * S;
+      Up = ld_df(U, s);
+      Fp = df_add(k_apply_df(st, c, U, s, Up), phi_df(c, Up));
+    }
+    const int n1 = min(N, n0 + NL_ROWS);
+    for (int n = n0; n < n1; ++n) {
+      const double* U = u + (size_t)n * S;
+      const df Un = ld_df(U, s);
+      const df Fn = df_add(k_apply_df(st, c, U, s, Un), phi_df(c, Un));
+      df v = ld_df(b, (size_t)n * S + s);
+      v = df_sub(v, df_mul(c.c10, Un));
+      v = df_sub(v, df_mul(c.c20, Fn));
+      if (n > 0) {
+        v = df_sub(v, df_mul(c.c11, Up));
+        v = df_sub(v, df_mul(c.c21, Fp));
+      }
+      r[(size_t)n * S + s] = double_from_float(v.hi) + double_from_float(v.lo);
+      pr = fmaf(v.hi, v.hi, pr);
+      pd += dphi_of(cr, Un.hi);
+      Up = Un;
+      Fp = Fn;
+    }
+  }
+  block_add((double)pr, red, acc);
+  block_add((double)pd, red, acc + 1);
+}
+
+df df_host(double v) {
+  const dfc c = dfc_from(v);
+  df d;
+  d.hi = c.hi;
+  d.lo = c.lo;
+  return d;
+}
+
 // first row of the right-hand side: b_0 -= c2[1] phi(U_0)
 __global__ void k_nl_rhs(int S, double w, Reaction c, const double* __restrict__ u0,
                          double* __restrict__ b) {
@@ -119,6 +205,22 @@ __global__ void k_nl_rhs(int S, double w, Reaction c, const double* __restrict__
 __global__ void k_nl_update(double* __restrict__ u, const double* __restrict__ z, size_t n) {
   for (size_t i = blockIdx.x * (size_t)NB + threadIdx.x; i < n; i += (size_t)gridDim.x * NB)
     u[i] += z[i];
+}
+
+// lam[2k] = lam0[2k] + sigma lam0[2k+1], lam[2k+1] = lam0[2k+1] with sigma =
+// acc[1] / ns read from device memory (left there by the residual kernel)
+template <typename C>
+__global__ void k_nl_shift(C* __restrict__ lam, const C* __restrict__ lam0,
+                           const double* __restrict__ acc, double ns, int nh) {
+  const double sigma = acc[1] / ns;
+  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < nh; k += gridDim.x * blockDim.x) {
+    const C l1 = lam0[2 * k], l2 = lam0[2 * k + 1];
+    C o;
+    o.x = l1.x + (decltype(o.x))sigma * l2.x;
+    o.y = l1.y + (decltype(o.y))sigma * l2.y;
+    lam[2 * k] = o;
+    lam[2 * k + 1] = l2;
+  }
 }
 
 pd_status nl_err(pd_plan* p, pd_status s, const char* what) {
@@ -163,53 +265,17 @@ pd_status nl_resid_launch(pd_plan* p, const Reaction& c, const double* b, const 
                           double* r, double* acc) {
   NLCU(cudaMemsetAsync(acc, 0, 2 * sizeof(double), p->stream));
   const dim3 grid((unsigned)ceil_div(p->S, NB), (unsigned)ceil_div(p->nt, NL_ROWS));
-  NLLK(k_nl_resid<<<grid, NB, 0, p->stream>>>(p->st, p->tb, p->nt, c, u, b, r, acc));
-  return PD_OK;
-}
-
-// the plan's (lambda_1k, lambda_2k) in FP64, as the plan computed them:
-// lambda_jk = sum_m c_j[m] w_k^m, w_k = alpha^{1/Nt} exp(-2 pi i k / Nt) (Lemma 1)
-std::vector<std::complex<double>> plan_lambdas(const pd_plan* p) {
-  using cd = std::complex<double>;
-  const double PI = 3.14159265358979323846;
-  const double ar = std::pow(p->alpha, 1.0 / p->nt);
-  std::vector<cd> lam((size_t)2 * p->nh);
-  for (int k = 0; k < p->nh; ++k) {
-    const double th = -2.0 * PI * k / p->nt;
-    const cd w = ar * cd(std::cos(th), std::sin(th));
-    cd l1 = 0, l2 = 0, wm = 1;
-    for (int m = 0; m <= p->tb.band && m < p->nt; ++m) {
-      l1 += p->tb.c1[m] * wm;
-      l2 += p->tb.c2[m] * wm;
-      wm *= w;
-    }
-    lam[2 * k] = l1;
-    lam[2 * k + 1] = l2;
-  }
-  return lam;
-}
-
-// device table <- (lambda_1k + sigma lambda_2k, lambda_2k), in the plan's precision
-pd_status upload_shifted(pd_plan* p, const std::vector<std::complex<double>>& lam, double sigma) {
-  const size_t m = lam.size();
   if (p->fp64) {
-    std::vector<double2> h(m);
-    for (size_t i = 0; i < m; i += 2) {
-      const std::complex<double> l1 = lam[i] + sigma * lam[i + 1];
-      h[i] = make_double2(l1.real(), l1.imag());
-      h[i + 1] = make_double2(lam[i + 1].real(), lam[i + 1].imag());
-    }
-    NLCU(cudaMemcpyAsync(p->lam, h.data(), m * sizeof(double2), cudaMemcpyHostToDevice, p->stream));
-    NLCU(cudaStreamSynchronize(p->stream));
+    NLLK(k_nl_resid<<<grid, NB, 0, p->stream>>>(p->st, p->tb, p->nt, c, u, b, r, acc));
   } else {
-    std::vector<float2> h(m);
-    for (size_t i = 0; i < m; i += 2) {
-      const std::complex<double> l1 = lam[i] + sigma * lam[i + 1];
-      h[i] = make_float2((float)l1.real(), (float)l1.imag());
-      h[i + 1] = make_float2((float)lam[i + 1].real(), (float)lam[i + 1].imag());
-    }
-    NLCU(cudaMemcpyAsync(p->lam, h.data(), m * sizeof(float2), cudaMemcpyHostToDevice, p->stream));
-    NLCU(cudaStreamSynchronize(p->stream));
+    // mixed plans: the same residual in double-float on the FP32 pipes
+    NlDf d;
+    d.kc = df_host(p->st.kc); d.kxl = df_host(p->st.kxl); d.kxu = df_host(p->st.kxu);
+    d.kyl = df_host(p->st.kyl); d.kyu = df_host(p->st.kyu);
+    d.c10 = df_host(p->tb.c1[0]); d.c11 = df_host(p->tb.c1[1]);
+    d.c20 = df_host(p->tb.c2[0]); d.c21 = df_host(p->tb.c2[1]);
+    d.a1 = df_host(c.a1); d.a2 = df_host(c.a2); d.a3 = df_host(c.a3);
+    NLLK(k_nl_resid_df<<<grid, NB, 0, p->stream>>>(p->st, d, c, p->nt, u, b, r, acc));
   }
   return PD_OK;
 }
@@ -223,6 +289,13 @@ pd_status ensure_nl_buffers(pd_plan* p) {
   if (!p->nl_z) {
     NLCU(cudaMalloc((void**)&p->nl_z, bytes));
     p->bytes += bytes;
+  }
+  if (!p->nl_lam0) {
+    // the plan's own eigenvalue table (unshifted: every solve restores it)
+    const size_t lb = (size_t)2 * p->nh * (p->fp64 ? sizeof(double2) : sizeof(float2));
+    NLCU(cudaMalloc(&p->nl_lam0, lb));
+    p->bytes += lb;
+    NLCU(cudaMemcpyAsync(p->nl_lam0, p->lam, lb, cudaMemcpyDeviceToDevice, p->stream));
   }
   return PD_OK;
 }
@@ -282,7 +355,6 @@ extern "C" pd_status pd_nl_solve(pd_plan* p, const double* a, const double* b, d
   NLCU(cudaMemcpyAsync(&nb2, p->dsc + 2, sizeof(double), cudaMemcpyDeviceToHost, p->stream));
   NLCU(cudaStreamSynchronize(p->stream));
   const double nb = std::sqrt(nb2);
-  const std::vector<std::complex<double>> lam = plan_lambdas(p);
   int it = 0;
   double rel = 0.0;
   pd_status out = PD_OK;
@@ -302,16 +374,28 @@ extern "C" pd_status pd_nl_solve(pd_plan* p, const double* a, const double* b, d
       out = nl_err(p, PD_ERR_NOT_CONVERGED, "simplified Newton did not reach the tolerance");
       break;
     }
-    const double sigma = h[1] / (double)ns;
-    s = upload_shifted(p, lam, sigma);
-    if (s != PD_OK) { out = s; break; }
+    // the shifted table on the device, from the residual kernel's sum
+    if (p->fp64)
+      NLLK(k_nl_shift<<<ceil_div(p->nh, NB), NB, 0, p->stream>>>(
+          static_cast<double2*>(p->lam), static_cast<const double2*>(p->nl_lam0), p->dsc,
+          (double)ns, p->nh));
+    else
+      NLLK(k_nl_shift<<<ceil_div(p->nh, NB), NB, 0, p->stream>>>(
+          static_cast<float2*>(p->lam), static_cast<const float2*>(p->nl_lam0), p->dsc,
+          (double)ns, p->nh));
     s = plan_precond(p, p->nl_r, p->nl_z);
     if (s != PD_OK) { out = s; break; }
     NLLK(k_nl_update<<<2 * 152, NB, 0, p->stream>>>(u, p->nl_z, ns));
     ++it;
   }
   // the plan's own table back (its linear solves use it)
-  const pd_status s2 = upload_shifted(p, lam, 0.0);
+  pd_status s2 = PD_OK;
+  {
+    const size_t lb = (size_t)2 * p->nh * (p->fp64 ? sizeof(double2) : sizeof(float2));
+    const cudaError_t e = cudaMemcpyAsync(p->lam, p->nl_lam0, lb, cudaMemcpyDeviceToDevice,
+                                          p->stream);
+    if (e != cudaSuccess) s2 = nl_cuda(p, e, "restoring the eigenvalue table");
+  }
   if (iters) *iters = it;
   if (relres) *relres = rel;
   return out != PD_OK ? out : s2;

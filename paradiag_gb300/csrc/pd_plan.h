@@ -56,6 +56,7 @@ struct pd_plan {
   // simplified Newton workspace (nonlinear problems), allocated on first use
   double* nl_r = nullptr;
   double* nl_z = nullptr;
+  void* nl_lam0 = nullptr;   // copy of the plan's eigenvalue table
   pd_plan* adj = nullptr;
   // the mixed stationary iteration as one CUDA graph (built on first use;
   // graph_state 0 untried, 1 ready, -1 unavailable: the host loop runs)

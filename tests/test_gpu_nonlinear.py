@@ -3,8 +3,8 @@ simplified Newton iteration of eq. 1.5 with the averaged Jacobian) against the
 nonlinear oracle (O10).
 
   * right-hand side and residual: FP64 parity with the oracle to 1e-13
-    (relative to the largest entry); the averaged shift sigma and ||r||^2,
-    summed in FP32, to 1e-5;
+    (relative to the largest entry), the double-float residual of mixed plans
+    to 1e-12; the averaged shift sigma and ||r||^2, summed in FP32, to 1e-5;
   * solves (FP64 and mixed plans) to a relative residual of 1e-11 equal the
     exact solution (sequential stepping with Newton per step) to 1e-9 of
     max|u|; on FP64 plans the number of corrections matches the oracle's
@@ -63,6 +63,13 @@ def test_rhs_residual_sigma_match_oracle(pd, name):
     assert sig == pytest.approx(NL.average_jacobian_shift(U, a), rel=1e-5, abs=1e-6)
     assert rn2 == pytest.approx(float(np.sum(rref * rref)), rel=1e-5)
     plan.close()
+    # mixed plans form the same residual in double-float arithmetic (unit
+    # roundoff ~2^-48 against the largest term, here within 1e-12 of max |r|)
+    pm = make_plan(pb, PD_MIXED)
+    rm, sigm, _ = pm.nl_residual(a, dev(bref), dev(U))
+    assert np.abs(host(rm) - rref).max() <= 1e-12 * np.abs(rref).max()
+    assert sigm == pytest.approx(NL.average_jacobian_shift(U, a), rel=1e-5, abs=1e-6)
+    pm.close()
 
 
 @pytest.mark.parametrize("name", sorted(CASES))
