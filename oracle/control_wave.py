@@ -215,9 +215,13 @@ def fgmres_op(A, Pinv, b: np.ndarray, tol=1e-7, restart=50, maxit=200):
     return x, total, rel
 
 
-def solve(space, nt: int, T: float, gamma: float, rhs1, rhs2, tol=1e-7, K=None):
-    """FGMRES on the balanced system with P^{-1}: returns (u, p, iterations,
-    relres) for the right-hand side (rhs1, rhs2) of the unbalanced system."""
+def solve(space, nt: int, T: float, gamma: float, rhs1, rhs2, tol=1e-7, K=None, side="right",
+          restart=50):
+    """GMRES on the balanced system with P^{-1}: returns (u, p, iterations,
+    relres) for the right-hand side (rhs1, rhs2) of the unbalanced system.
+    side="right": flexible GMRES on A P^{-1}, stopping on ||b - A x|| / ||b||;
+    side="left": GMRES on P^{-1} A x = P^{-1} b, stopping on the preconditioned
+    residual ||P^{-1}(b - A x)|| / ||P^{-1} b|| (relres is that ratio)."""
     K = stencil(space) if K is None else K
     dt = T / nt
     A = saddle_matrix(nt, dt, gamma, K, balanced=True)
@@ -229,5 +233,9 @@ def solve(space, nt: int, T: float, gamma: float, rhs1, rhs2, tol=1e-7, K=None):
     Aop = lambda v: A @ v
     Pop = lambda v: np.concatenate([q.reshape(-1) for q in
                                     P.apply(v[:n].reshape(nt, S), v[n:].reshape(nt, S))])
-    x, it, rel = fgmres_op(Aop, Pop, b, tol=tol)
+    if side == "left":
+        x, it, rel = fgmres_op(lambda v: Pop(Aop(v)), lambda v: v, Pop(b), tol=tol,
+                               restart=restart)
+    else:
+        x, it, rel = fgmres_op(Aop, Pop, b, tol=tol, restart=restart)
     return x[:n].reshape(nt, S) / sg, x[n:].reshape(nt, S), it, rel
