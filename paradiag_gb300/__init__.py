@@ -124,6 +124,8 @@ _SIGS = {
     "pdc_apply_A": (ctypes.c_int, [_P, _P, _P]),
     "pdc_apply_precond": (ctypes.c_int, [_P, _P, _P]),
     "pdc_solve": (ctypes.c_int, [_P, _P, _P, ctypes.c_double, ctypes.c_int, ctypes.c_int, _I, _D]),
+    "pdc_solve_left": (ctypes.c_int, [_P, _P, _P, ctypes.c_double, ctypes.c_int, ctypes.c_int, _I,
+                                      _D]),
     "pdc_launches": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_ulonglong)]),
     "pdc_last_error": (ctypes.c_char_p, [_P]),
     "pd_status_string": (ctypes.c_char_p, [ctypes.c_int]),
@@ -510,11 +512,16 @@ def pdc_apply_precond(plan, r, z):
     return load().pdc_apply_precond(plan, r, z)
 
 
-def pdc_solve(plan, b, x, tol, maxit, restart):
+def pdc_solve(plan, b, x, tol, maxit, restart, left=False):
     it = ctypes.c_int(0)
     rr = ctypes.c_double(0.0)
-    st = load().pdc_solve(plan, b, x, tol, maxit, restart, ctypes.byref(it), ctypes.byref(rr))
+    fn = load().pdc_solve_left if left else load().pdc_solve
+    st = fn(plan, b, x, tol, maxit, restart, ctypes.byref(it), ctypes.byref(rr))
     return st, it.value, rr.value
+
+
+def pdc_solve_left(plan, b, x, tol, maxit, restart):
+    return pdc_solve(plan, b, x, tol, maxit, restart, left=True)
 
 
 def pdc_launches(plan):
@@ -1033,13 +1040,15 @@ class PlanControl:
         self._check(pdc_apply_precond(self._h, _ptr(r), _ptr(z)), "pdc_apply_precond")
         return z
 
-    def solve(self, b, x=None, tol=1e-7, maxit=100, restart=30, allow_not_converged=False):
-        """(u, p) for the right-hand side (f, g); returns (x, iterations, relres)."""
+    def solve(self, b, x=None, tol=1e-7, maxit=100, restart=30, allow_not_converged=False,
+              left=False):
+        """(u, p) for the right-hand side (f, g); returns (x, iterations, relres).
+        left=True: left preconditioning, relres on the preconditioned residual."""
         import torch
         self._check_t(b)
         x = torch.empty_like(b) if x is None else x
         self._check_t(x)
-        st, it, rel = pdc_solve(self._h, _ptr(b), _ptr(x), tol, maxit, restart)
+        st, it, rel = pdc_solve(self._h, _ptr(b), _ptr(x), tol, maxit, restart, left)
         if not (st == PD_OK or (allow_not_converged and st == PD_ERR_NOT_CONVERGED)):
             self._check(st, "pdc_solve")
         return x, it, rel

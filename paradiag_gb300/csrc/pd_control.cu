@@ -344,9 +344,12 @@ int flag_of(const pdc_plan* q) {
   return f | g;
 }
 
-// FGMRES(m), right preconditioned, on the balanced system A x = b (FP64)
+// GMRES(m) on the balanced system A x = b (FP64).  right: flexible GMRES on
+// A P^{-1}, stopping on ||b - A x|| / ||b||.  left: GMRES on P^{-1} A x =
+// P^{-1} b, stopping on ||P^{-1}(b - A x)|| / ||P^{-1} b||, x = x0 + V y (Z
+// serves as scratch).
 pd_status fgmres(pdc_plan* q, const double* b, double* x, double tol, int maxit, int restart,
-                 int* iters, double* relres) {
+                 int* iters, double* relres, bool left = false) {
   const size_t n = n2(q);
   cudaStream_t st = q->tp->stream;
   int m = restart > 0 ? restart : 30;
@@ -355,7 +358,13 @@ pd_status fgmres(pdc_plan* q, const double* b, double* x, double tol, int maxit,
   PCCU(cudaMemsetAsync(q->dsc, 0, 3 * sizeof(double), st));
   PCCU(cudaMemsetAsync(q->tp->dflag, 0, sizeof(int), st));
   PCCU(cudaMemsetAsync(q->rp->dflag, 0, sizeof(int), st));
-  PCLK(launch_norm2(b, n, q->dsc, st));
+  if (left) {
+    // ||P^{-1} b||
+    PCCHK(precond(q, b, q->Z));
+    PCLK(launch_norm2(q->Z, n, q->dsc, st));
+  } else {
+    PCLK(launch_norm2(b, n, q->dsc, st));
+  }
   PCCHK(sync_scalars(q, 0, 1));
   const double nb = std::sqrt(q->hsc[0]);
   if (nb == 0.0) {
@@ -372,7 +381,14 @@ pd_status fgmres(pdc_plan* q, const double* b, double* x, double tol, int maxit,
   pd_status status = PD_OK;
   for (;;) {
     PCCU(cudaMemsetAsync(q->dsc + 1, 0, sizeof(double), st));
-    PCCHK(apply(q, x, q->V, b, q->dsc + 1));
+    if (left) {
+      // V_0 = P^{-1}(b - A x)
+      PCCHK(apply(q, x, q->Z, b, nullptr));
+      PCCHK(precond(q, q->Z, q->V));
+      PCLK(launch_norm2(q->V, n, q->dsc + 1, st));
+    } else {
+      PCCHK(apply(q, x, q->V, b, q->dsc + 1));
+    }
     PCCHK(sync_scalars(q, 1, 1));
     const double beta = std::sqrt(q->hsc[1]);
     rel = beta / nb;
@@ -388,8 +404,13 @@ pd_status fgmres(pdc_plan* q, const double* b, double* x, double tol, int maxit,
       double* Vj = q->V + (size_t)j * n;
       double* Zj = q->Z + (size_t)j * n;
       double* w = q->V + (size_t)(j + 1) * n;
-      PCCHK(precond(q, Vj, Zj));
-      PCCHK(apply(q, Zj, w, nullptr, nullptr));
+      if (left) {
+        PCCHK(apply(q, Vj, Zj, nullptr, nullptr));
+        PCCHK(precond(q, Zj, w));
+      } else {
+        PCCHK(precond(q, Vj, Zj));
+        PCCHK(apply(q, Zj, w, nullptr, nullptr));
+      }
       for (int pass = 0; pass < 2; ++pass) {
         PCCU(cudaMemsetAsync(q->dsc + 8, 0, (j + 1) * sizeof(double), st));
         PCLK(launch_dots(q->V, j + 1, n, w, q->dsc + 8, st));
@@ -429,7 +450,7 @@ pd_status fgmres(pdc_plan* q, const double* b, double* x, double tol, int maxit,
     }
     for (int i = 0; i < jdone; ++i) q->hsc[8 + i] = y[i];
     PCCU(cudaMemcpyAsync(q->dsc + 8, q->hsc + 8, jdone * sizeof(double), cudaMemcpyHostToDevice, st));
-    PCLK(launch_combine(q->Z, jdone, n, q->dsc + 8, x, st));
+    PCLK(launch_combine(left ? q->V : q->Z, jdone, n, q->dsc + 8, x, st));
   }
   PCCU(cudaStreamSynchronize(st));
   if (iters) *iters = total;
@@ -530,8 +551,23 @@ pd_status pdc_apply_precond(pdc_plan* q, const double* r, double* z) {
   return precond(q, r, z);
 }
 
+pd_status solve_side(pdc_plan* q, const double* b, double* x, double tol, int maxit,
+                     int restart, int* iters, double* relres, bool left);
+
 pd_status pdc_solve(pdc_plan* q, const double* b, double* x, double tol, int maxit, int restart,
                     int* iters, double* relres) {
+  return solve_side(q, b, x, tol, maxit, restart, iters, relres, false);
+}
+
+pd_status pdc_solve_left(pdc_plan* q, const double* b, double* x, double tol, int maxit,
+                         int restart, int* iters, double* relres) {
+  return solve_side(q, b, x, tol, maxit, restart, iters, relres, true);
+}
+
+}  // extern "C"
+
+pd_status solve_side(pdc_plan* q, const double* b, double* x, double tol, int maxit,
+                     int restart, int* iters, double* relres, bool left) {
   if (!q || !b || !x) return PD_ERR_ARG;
   if (!(tol >= 0.0) || maxit < 0 || restart < 0 || restart > 64) return PD_ERR_ARG;
   const size_t ns = (size_t)q->nt * q->S;
@@ -542,13 +578,15 @@ pd_status pdc_solve(pdc_plan* q, const double* b, double* x, double tol, int max
   k_ctl_scale_half<<<grid, CT_TB, 0, st>>>(sg, b, q->w, ns);
   PCLK(cudaGetLastError());
   PCCU(cudaMemsetAsync(q->x, 0, 2 * ns * sizeof(double), st));
-  const pd_status s = fgmres(q, q->w, q->x, tol, maxit, restart, iters, relres);
+  const pd_status s = fgmres(q, q->w, q->x, tol, maxit, restart, iters, relres, left);
   if (s != PD_OK && s != PD_ERR_NOT_CONVERGED) return s;
   k_ctl_scale_half<<<grid, CT_TB, 0, st>>>(1.0 / sg, q->x, x, ns);
   PCLK(cudaGetLastError());
   PCCU(cudaStreamSynchronize(st));
   return s;
 }
+
+extern "C" {
 
 pd_status pdc_launches(const pdc_plan* q, unsigned long long* count) {
   if (!q || !count) return PD_ERR_ARG;

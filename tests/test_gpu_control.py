@@ -124,3 +124,29 @@ def test_control_full_size_gamma_1e4(pd):
     r = bb - pl.apply_A(xs)
     assert float(torch.linalg.norm(r) / torch.linalg.norm(bb)) <= 1.5e-7
     pl.close()
+
+
+@pytest.mark.parametrize("mesh", [0, 1, 2])
+def test_control_table_t2a_left_preconditioned(pd, mesh):
+    # GMRES on P^{-1} A x = P^{-1} b, stopping on the preconditioned residual:
+    # the table's counts on the (16,16,17), (32,32,33) and (64,64,65) meshes
+    # for every gamma (FP64 preconditioner); the iterate equals the oracle's
+    # left-preconditioned solve
+    gold = json.load(open(os.path.join(GOLDEN, "t2a_wave_control.json")))
+    n = (16, 32, 64)[mesh]
+    nt = n + 1
+    sp = space(n)
+    m = nt * sp.size
+    for g, it_ref in zip(gold["gammas"], gold["iterations"][mesh]):
+        Ah, xe, b = exact_rhs(n, nt, g)
+        pl = plan(pd, n, nt, g, 0)
+        x, it, rel = pl.solve(dev(b), tol=1e-7, maxit=200, restart=50, left=True)
+        pl.close()
+        assert rel <= 1e-7
+        assert it == it_ref, (n, g, it, it_ref)
+        if n <= 32 or g == 1e-2:
+            u, p, it_o, _ = CW.solve(sp, nt, 2.0, g, b[:m].reshape(nt, -1),
+                                     b[m:].reshape(nt, -1), tol=1e-7, side="left")
+            assert it_o == it
+            xo = np.concatenate([u.reshape(-1), p.reshape(-1)])
+            assert np.abs(host(x).reshape(-1) - xo).max() <= 1e-8 * np.abs(xo).max()

@@ -105,11 +105,11 @@ def test_table_t2a_iterations(mesh):
         assert it == it_ref, (n, g, it, it_ref)
 
 
-@pytest.mark.parametrize("g_index", [0, 1])
+@pytest.mark.parametrize("g_index", [0, 1, 2, 3, 4])
 def test_table_t2a_left_preconditioned_64(g_index):
-    # On the (64,64,65) mesh the table prints 5 iterations for gamma = 1e-2 and 1e-4.
-    # Left preconditioning, stopping on the preconditioned residual, reproduces them.
-    # The right-preconditioned count on the true residual is 7 at gamma = 1e-2.
+    # On the (64,64,65) mesh the table prints 5, 5, 5, 5, 4 iterations.  Left
+    # preconditioning, stopping on the preconditioned residual, reproduces every
+    # one.  The right-preconditioned count on the true residual is 7 at gamma = 1e-2.
     gold = json.load(open(os.path.join(GOLDEN, "t2a_wave_control.json")))
     n = 64
     nt = n + 1
