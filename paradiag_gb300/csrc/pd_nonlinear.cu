@@ -121,61 +121,94 @@ struct NlDf {
 __device__ __forceinline__ df ld_df(const double* __restrict__ x, size_t i) {
   return df_from_double(x[i]);
 }
+__device__ __forceinline__ df ld_df(const float2* __restrict__ x, size_t i) {
+  const float2 v = __ldg(&x[i]);
+  return df_make(v.x, v.y);
+}
 
-// (K U)(s) in double-float
-__device__ __forceinline__ df k_apply_df(const Stencil& st, const NlDf& c,
-                                         const double* __restrict__ U, int s, df uc) {
+// compensated sum (value = s + e): every term enters with one two-sum of its
+// high part; low parts and rounding errors gather in e
+struct NlAcc {
+  float s, e;
+};
+__device__ __forceinline__ void nl_add(NlAcc& A, float h, float l) {
+  const float t = __fadd_rn(A.s, h);
+  const float bb = __fsub_rn(t, A.s);
+  const float err = __fadd_rn(__fsub_rn(A.s, __fsub_rn(t, bb)), __fsub_rn(h, bb));
+  A.s = t;
+  A.e = __fadd_rn(A.e, __fadd_rn(err, l));
+}
+// A += k u: the product of the high parts exactly (FMA), the cross terms into e
+__device__ __forceinline__ void nl_add_prod(NlAcc& A, df k, df u) {
+  const float p = __fmul_rn(k.hi, u.hi);
+  float pe = __fmaf_rn(k.hi, u.hi, -p);
+  pe = __fmaf_rn(k.hi, u.lo, pe);
+  pe = __fmaf_rn(k.lo, u.hi, pe);
+  nl_add(A, p, pe);
+}
+__device__ __forceinline__ df nl_val(const NlAcc& A) { return fast_two_sum(A.s, A.e); }
+
+// F(U)(s) = (K U)(s) + phi(U(s)) as one compensated sum of eight terms
+template <typename T>
+__device__ __forceinline__ df f_of_df(const Stencil& st, const NlDf& c, const T* __restrict__ U,
+                                      int s, df uc) {
   const int xg = s % st.nx, y = s / st.nx;
-  df v = df_mul(c.kc, uc);
-  if (xg > 0) v = df_add(v, df_mul(c.kxl, ld_df(U, s - 1)));
-  else if (st.bcx == PD_PERIODIC && st.nx > 1) v = df_add(v, df_mul(c.kxl, ld_df(U, s + st.nx - 1)));
-  if (xg < st.nx - 1) v = df_add(v, df_mul(c.kxu, ld_df(U, s + 1)));
-  else if (st.bcx == PD_PERIODIC && st.nx > 1) v = df_add(v, df_mul(c.kxu, ld_df(U, s - st.nx + 1)));
+  NlAcc A = {0.f, 0.f};
+  nl_add_prod(A, c.kc, uc);
+  if (xg > 0) nl_add_prod(A, c.kxl, ld_df(U, s - 1));
+  else if (st.bcx == PD_PERIODIC && st.nx > 1) nl_add_prod(A, c.kxl, ld_df(U, s + st.nx - 1));
+  if (xg < st.nx - 1) nl_add_prod(A, c.kxu, ld_df(U, s + 1));
+  else if (st.bcx == PD_PERIODIC && st.nx > 1) nl_add_prod(A, c.kxu, ld_df(U, s - st.nx + 1));
   if (st.dim == 2) {
-    if (y > 0) v = df_add(v, df_mul(c.kyl, ld_df(U, s - st.nx)));
-    if (y < st.ny - 1) v = df_add(v, df_mul(c.kyu, ld_df(U, s + st.nx)));
+    if (y > 0) nl_add_prod(A, c.kyl, ld_df(U, s - st.nx));
+    if (y < st.ny - 1) nl_add_prod(A, c.kyu, ld_df(U, s + st.nx));
   }
-  return v;
+  // phi(u) = a1 u + a2 u^2 + a3 u^3
+  const df u2 = df_mul(uc, uc);
+  const df u3 = df_mul(u2, uc);
+  nl_add_prod(A, c.a1, uc);
+  nl_add_prod(A, c.a2, u2);
+  nl_add_prod(A, c.a3, u3);
+  return nl_val(A);
 }
 
-// phi(u) = u (a1 + u (a2 + u a3)) in double-float (Horner)
-__device__ __forceinline__ df phi_df(const NlDf& c, df u) {
-  df t = df_add(df_mul(c.a3, u), c.a2);
-  t = df_add(df_mul(t, u), c.a1);
-  return df_mul(t, u);
-}
-
-// k_nl_resid with every term in double-float (unit roundoff about 2^-48):
-// the FP64 inputs are split with integer operations and r is written as
-// hi + lo (one FP64 addition per element)
+// k_nl_resid with double-float inputs and compensated sums (unit roundoff
+// about 2^-48 against the largest term): the FP64 inputs are split with
+// integer operations and r is written as hi + lo (one FP64 addition)
+// T = double: FP64 inputs, split on load; T = float2: double-float inputs
+template <typename T>
 __global__ void __launch_bounds__(NB) k_nl_resid_df(Stencil st, NlDf c, Reaction cr, int N,
-                                                    const double* __restrict__ u,
-                                                    const double* __restrict__ b,
+                                                    const T* __restrict__ u,
+                                                    const T* __restrict__ b,
                                                     double* __restrict__ r, double* acc) {
   __shared__ double red[NB / 32];
   const int s = blockIdx.x * NB + threadIdx.x;
   const int n0 = blockIdx.y * NL_ROWS;
   const size_t S = (size_t)st.S;
+  // the time weights negated once: v = b - c1[0] U_n - c2[0] F_n - c1[1] U_{n-1} - c2[1] F_{n-1}
+  const df m10 = df_neg(c.c10), m20 = df_neg(c.c20), m11 = df_neg(c.c11), m21 = df_neg(c.c21);
   float pr = 0.f, pd = 0.f;
   if (s < st.S) {
     df Up = df_make(0.f, 0.f), Fp = Up;
     if (n0 > 0) {
-      const double* U = u + (size_t)(n0 - 1) * S;
+      const T* U = u + (size_t)(n0 - 1) * S;
       Up = ld_df(U, s);
-      Fp = df_add(k_apply_df(st, c, U, s, Up), phi_df(c, Up));
+      Fp = f_of_df(st, c, U, s, Up);
     }
     const int n1 = min(N, n0 + NL_ROWS);
     for (int n = n0; n < n1; ++n) {
-      const double* U = u + (size_t)n * S;
+      const T* U = u + (size_t)n * S;
       const df Un = ld_df(U, s);
-      const df Fn = df_add(k_apply_df(st, c, U, s, Un), phi_df(c, Un));
-      df v = ld_df(b, (size_t)n * S + s);
-      v = df_sub(v, df_mul(c.c10, Un));
-      v = df_sub(v, df_mul(c.c20, Fn));
+      const df Fn = f_of_df(st, c, U, s, Un);
+      const df bn = ld_df(b, (size_t)n * S + s);
+      NlAcc V = {bn.hi, bn.lo};
+      nl_add_prod(V, m10, Un);
+      nl_add_prod(V, m20, Fn);
       if (n > 0) {
-        v = df_sub(v, df_mul(c.c11, Up));
-        v = df_sub(v, df_mul(c.c21, Fp));
+        nl_add_prod(V, m11, Up);
+        nl_add_prod(V, m21, Fp);
       }
+      const df v = nl_val(V);
       r[(size_t)n * S + s] = double_from_float(v.hi) + double_from_float(v.lo);
       pr = fmaf(v.hi, v.hi, pr);
       pd += dphi_of(cr, Un.hi);
@@ -202,9 +235,17 @@ __global__ void k_nl_rhs(int S, double w, Reaction c, const double* __restrict__
   if (s < S) b[s] = fma(-w, phi_of(c, u0[s]), b[s]);
 }
 
-__global__ void k_nl_update(double* __restrict__ u, const double* __restrict__ z, size_t n) {
-  for (size_t i = blockIdx.x * (size_t)NB + threadIdx.x; i < n; i += (size_t)gridDim.x * NB)
-    u[i] += z[i];
+// u += z; with udf, also the double-float copy of the new u
+__global__ void k_nl_update(double* __restrict__ u, const double* __restrict__ z,
+                            float2* __restrict__ udf, size_t n) {
+  for (size_t i = blockIdx.x * (size_t)NB + threadIdx.x; i < n; i += (size_t)gridDim.x * NB) {
+    const double v = u[i] + z[i];
+    u[i] = v;
+    if (udf != nullptr) {
+      const df d = df_from_double(v);
+      udf[i] = make_float2(d.hi, d.lo);
+    }
+  }
 }
 
 // lam[2k] = lam0[2k] + sigma lam0[2k+1], lam[2k+1] = lam0[2k+1] with sigma =
@@ -260,9 +301,11 @@ pd_status nl_args(pd_plan* p, const double* a, Reaction* c) {
   return PD_OK;
 }
 
-// residual into r with acc[0..1] (device) accumulated; no synchronisation
+// residual into r with acc[0..1] (device) accumulated; no synchronisation.
+// Mixed plans with double-float copies (udf, bdf) of u and b read those.
 pd_status nl_resid_launch(pd_plan* p, const Reaction& c, const double* b, const double* u,
-                          double* r, double* acc) {
+                          double* r, double* acc, const float2* udf = nullptr,
+                          const float2* bdf = nullptr) {
   NLCU(cudaMemsetAsync(acc, 0, 2 * sizeof(double), p->stream));
   const dim3 grid((unsigned)ceil_div(p->S, NB), (unsigned)ceil_div(p->nt, NL_ROWS));
   if (p->fp64) {
@@ -275,7 +318,10 @@ pd_status nl_resid_launch(pd_plan* p, const Reaction& c, const double* b, const 
     d.c10 = df_host(p->tb.c1[0]); d.c11 = df_host(p->tb.c1[1]);
     d.c20 = df_host(p->tb.c2[0]); d.c21 = df_host(p->tb.c2[1]);
     d.a1 = df_host(c.a1); d.a2 = df_host(c.a2); d.a3 = df_host(c.a3);
-    NLLK(k_nl_resid_df<<<grid, NB, 0, p->stream>>>(p->st, d, c, p->nt, u, b, r, acc));
+    if (udf != nullptr && bdf != nullptr)
+      NLLK(k_nl_resid_df<float2><<<grid, NB, 0, p->stream>>>(p->st, d, c, p->nt, udf, bdf, r, acc));
+    else
+      NLLK(k_nl_resid_df<double><<<grid, NB, 0, p->stream>>>(p->st, d, c, p->nt, u, b, r, acc));
   }
   return PD_OK;
 }
@@ -355,11 +401,19 @@ extern "C" pd_status pd_nl_solve(pd_plan* p, const double* a, const double* b, d
   NLCU(cudaMemcpyAsync(&nb2, p->dsc + 2, sizeof(double), cudaMemcpyDeviceToHost, p->stream));
   NLCU(cudaStreamSynchronize(p->stream));
   const double nb = std::sqrt(nb2);
+  // mixed plans: u and b split into double-float once (the plan's solver
+  // state); the update keeps the copy of u current
+  float2* udf = (!p->fp64 && p->Udf && p->Bdf) ? p->Udf : nullptr;
+  if (udf) {
+    NLCU(cudaMemsetAsync(p->dsc + 4, 0, sizeof(double), p->stream));
+    ++p->launches;
+    NLCU(launch_entry_df(u, b, 1.0, p->Udf, p->Bdf, ns, p->dsc + 4, p->stream));
+  }
   int it = 0;
   double rel = 0.0;
   pd_status out = PD_OK;
   for (;;) {
-    s = nl_resid_launch(p, c, b, u, p->nl_r, p->dsc);
+    s = nl_resid_launch(p, c, b, u, p->nl_r, p->dsc, udf, udf ? p->Bdf : nullptr);
     if (s != PD_OK) { out = s; break; }
     double h[2];
     NLCU(cudaMemcpyAsync(h, p->dsc, 2 * sizeof(double), cudaMemcpyDeviceToHost, p->stream));
@@ -385,7 +439,7 @@ extern "C" pd_status pd_nl_solve(pd_plan* p, const double* a, const double* b, d
           (double)ns, p->nh));
     s = plan_precond(p, p->nl_r, p->nl_z);
     if (s != PD_OK) { out = s; break; }
-    NLLK(k_nl_update<<<2 * 152, NB, 0, p->stream>>>(u, p->nl_z, ns));
+    NLLK(k_nl_update<<<2 * 152, NB, 0, p->stream>>>(u, p->nl_z, udf, ns));
     ++it;
   }
   // the plan's own table back (its linear solves use it)
