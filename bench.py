@@ -181,8 +181,8 @@ def flops_per_launch_xform(rows, nx):
 # kernels as recaptured after their last change, with the 16-column tile that
 # the autotuner keeps under the profiler); a kernel's entry goes back to None
 # whenever that kernel changes.
-NCU_TRAFFIC = {"resid_gamma_fft": 319.6e6, "xform_fwd": 81.4e6, "tridiag": 79.5e6,
-               "xform_inv": 81.4e6, "ifft_gamma_update": 279.8e6}
+NCU_TRAFFIC = {"resid_gamma_fft": 319.4e6, "xform_fwd": 81.4e6, "tridiag": 79.5e6,
+               "xform_inv": 81.4e6, "ifft_gamma_update": 279.7e6}
 
 
 def cpu_oracle_sample(w, seconds_hint=20.0):
