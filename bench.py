@@ -54,6 +54,8 @@ def parse():
     ap.add_argument("--no-control", action="store_true", help="skip the optimal-control leg")
     ap.add_argument("--no-wave", action="store_true",
                     help="skip the second-order (wave) hybrid ParaDiag-I leg")
+    ap.add_argument("--clocks-dir", default=os.path.join(ROOT, "bench_out"),
+                    help="folder for the nvidia-smi clock samples of the timed region")
     ap.add_argument("--no-nonlinear", action="store_true",
                     help="skip the nonlinear (simplified Newton) leg")
     ap.add_argument("--nonlinear-only", action="store_true",
@@ -87,10 +89,10 @@ class ClockSampler:
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
-    def __init__(self, index):
+    def __init__(self, index, outdir):
         self.index = index
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{index}.csv")
+        self.path = os.path.join(outdir, f"clocks_rank{index}.csv")
 
     def start(self):
         try:
@@ -845,7 +847,7 @@ def main():
         plan.close()
         return
 
-    clk = ClockSampler(local)
+    clk = ClockSampler(local, args.clocks_dir)
     clk.start()
     for _ in range(max(args.warmup, 3)):
         u.zero_()
