@@ -198,6 +198,19 @@ PD_API pd_status pd_nl_residual(pd_plan* plan, const double* a, const double* b,
 PD_API pd_status pd_nl_solve(pd_plan* plan, const double* a, const double* b, double* u,
                              double tol, int maxit, int* iters, double* relres);
 
+/* Windowing with simplified Newton (Section 1): nwin consecutive windows of the
+ * plan's nt steps, window w starting from the last time level of window w-1
+ * (u0 for w = 0), each built by pd_nl_build_rhs and solved by pd_nl_solve from
+ * a zero guess.  f: [nwin nt + 1][S] source values at t_0 .. t_{nwin nt}, or
+ * NULL; u: [nwin][nt][S] output.  iters_total: corrections summed over the
+ * windows; relres_max: the largest final relative residual (either may be
+ * NULL).  Stops at the first window that fails and returns its status.  Short
+ * windows keep the averaged-Jacobian iteration contracting where one long
+ * window diverges. */
+PD_API pd_status pd_nl_solve_windows(pd_plan* plan, const double* a, const double* u0,
+                                     const double* f, int nwin, double* u, double tol,
+                                     int maxit, int* iters_total, double* relres_max);
+
 /* Solve A^T lambda = g (the transposed all-at-once system, backward in time).
  * Uses J A^T J = B1 (x) I + B2 (x) K^T (J = time reversal, B1, B2 Toeplitz):
  * a forward ParaDiag solve with K^T on time-reversed data.  lambda: initial

@@ -101,6 +101,8 @@ _SIGS = {
     "pd_nl_build_rhs": (ctypes.c_int, [_P, _D, _P, _P, _P]),
     "pd_nl_residual": (ctypes.c_int, [_P, _D, _P, _P, _P, _D, _D]),
     "pd_nl_solve": (ctypes.c_int, [_P, _D, _P, _P, ctypes.c_double, ctypes.c_int, _I, _D]),
+    "pd_nl_solve_windows": (ctypes.c_int, [_P, _D, _P, _P, ctypes.c_int, _P, ctypes.c_double,
+                                           ctypes.c_int, _I, _D]),
     "pd1_profile_sweep": (ctypes.c_int, [_P, _P, _P, ctypes.c_int, ctypes.POINTER(ctypes.c_float)]),
     "pd1_workspace": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_ulonglong)]),
     "pd1_last_error": (ctypes.c_char_p, [_P]),
@@ -409,6 +411,14 @@ def pd_nl_solve(plan, a, b, u, tol, maxit):
     rr = ctypes.c_double(0.0)
     st = load().pd_nl_solve(plan, _reaction(a), b, u, tol, maxit, ctypes.byref(it),
                             ctypes.byref(rr))
+    return st, it.value, rr.value
+
+
+def pd_nl_solve_windows(plan, a, u0, f, nwin, u, tol, maxit):
+    it = ctypes.c_int(0)
+    rr = ctypes.c_double(0.0)
+    st = load().pd_nl_solve_windows(plan, _reaction(a), u0, f, nwin, u, tol, maxit,
+                                    ctypes.byref(it), ctypes.byref(rr))
     return st, it.value, rr.value
 
 
@@ -739,6 +749,21 @@ class Plan:
         st, it, rel = pd_nl_solve(self._h, a, _ptr(b), _ptr(u), tol, maxit)
         if not (st == PD_OK or (allow_not_converged and st == PD_ERR_NOT_CONVERGED)):
             self._check(st, "pd_nl_solve")
+        return u, it, rel
+
+    def nl_solve_windows(self, a, u0, nwin, f=None, u=None, tol=1e-10, maxit=100):
+        """nwin nonlinear windows of the plan's nt steps (window w starts from the
+        last level of window w-1); returns (u [nwin, nt, S], total corrections,
+        largest relative residual)."""
+        import torch
+        self._check_t(u0, self.S)
+        if f is not None:
+            self._check_t(f, (nwin * self.nt + 1) * self.S)
+        u = torch.empty((nwin, self.nt, self.S), dtype=torch.float64, device=u0.device) \
+            if u is None else u
+        self._check_t(u, nwin * self.nt * self.S)
+        st, it, rel = pd_nl_solve_windows(self._h, a, _ptr(u0), _ptr(f), nwin, _ptr(u), tol, maxit)
+        self._check(st, "pd_nl_solve_windows")
         return u, it, rel
 
     def adjoint_solve(self, g, lam=None, mode=PD_STATIONARY, tol=1e-10, maxit=50, restart=30):

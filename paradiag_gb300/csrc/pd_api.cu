@@ -132,7 +132,7 @@ void free_plan(pd_plan* p) {
                   p->mu,   p->spec, p->spec2, p->Udf,  p->Bdf,   p->w64a,  p->w64b,
                   p->dsc,  p->dflag, p->V,   p->Z,      p->dh,    p->Gf_hi, p->Gf_lo,
                   p->Gi_hi, p->Gi_lo, const_cast<void*>(p->xf.chirp),
-                  const_cast<void*>(p->xf.bhat), p->amax, p->nl_r, p->nl_z, p->nl_lam0};
+                  const_cast<void*>(p->xf.bhat), p->amax, p->nl_r, p->nl_z, p->nl_lam0, p->nl_b};
   for (void* q : ptrs)
     if (q) cudaFree(q);
   if (p->hsc) cudaFreeHost(p->hsc);

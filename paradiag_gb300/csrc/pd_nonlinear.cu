@@ -14,6 +14,7 @@
 // sum of phi'(U) (one kernel: FP64 on FP64 plans, double-float on mixed ones),
 // the shifted table (a small kernel reading the sum on the device), z =
 // P_alpha^{-1} r (the plan's three steps of eq. 1.3), u += z.
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 
@@ -454,3 +455,40 @@ extern "C" pd_status pd_nl_solve(pd_plan* p, const double* a, const double* b, d
   if (relres) *relres = rel;
   return out != PD_OK ? out : s2;
 }
+
+extern "C" pd_status pd_nl_solve_windows(pd_plan* p, const double* a, const double* u0,
+                                         const double* f, int nwin, double* u, double tol,
+                                         int maxit, int* iters_total, double* relres_max) {
+  if (!p) return PD_ERR_ARG;
+  if (!u0 || !u || nwin < 1) return nl_err(p, PD_ERR_ARG, "bad argument");
+  Reaction c;
+  pd_status s = nl_args(p, a, &c);
+  if (s != PD_OK) return s;
+  const size_t ns = (size_t)p->nt * p->S;
+  const size_t S = (size_t)p->S;
+  if (!p->nl_b) {
+    NLCU(cudaMalloc((void**)&p->nl_b, ns * sizeof(double)));
+    p->bytes += ns * sizeof(double);
+  }
+  int total = 0;
+  double worst = 0.0;
+  for (int w = 0; w < nwin; ++w) {
+    double* uw = u + (size_t)w * ns;
+    const double* start = w == 0 ? u0 : uw - S;  // last time level of the previous window
+    const double* fw = f ? f + (size_t)w * p->nt * S : nullptr;
+    s = pd_nl_build_rhs(p, a, start, fw, p->nl_b);
+    if (s == PD_OK) {
+      NLCU(cudaMemsetAsync(uw, 0, ns * sizeof(double), p->stream));
+      int it = 0;
+      double rel = 0.0;
+      s = pd_nl_solve(p, a, p->nl_b, uw, tol, maxit, &it, &rel);
+      total += it;
+      worst = std::max(worst, rel);
+    }
+    if (s != PD_OK) break;
+  }
+  if (iters_total) *iters_total = total;
+  if (relres_max) *relres_max = worst;
+  return s;
+}
+

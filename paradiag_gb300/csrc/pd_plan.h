@@ -57,6 +57,7 @@ struct pd_plan {
   double* nl_r = nullptr;
   double* nl_z = nullptr;
   void* nl_lam0 = nullptr;   // copy of the plan's eigenvalue table
+  double* nl_b = nullptr;    // right-hand side of one window (windowed solves)
   pd_plan* adj = nullptr;
   // the mixed stationary iteration as one CUDA graph (built on first use;
   // graph_state 0 untried, 1 ready, -1 unavailable: the host loop runs)

@@ -155,3 +155,38 @@ def test_full_size_bench_workload(pd):
     assert np.abs(bh - bref).max() <= 1e-13 * np.abs(bref).max()
     plan.close()
     torch.cuda.empty_cache()
+
+
+@pytest.mark.parametrize("prec", [PD_FP64, PD_MIXED])
+def test_windows_bistable_match_oracle(pd, prec):
+    # the bistable reaction phi = u^3 - u over T = 1 diverges as one window
+    # (the averaged Jacobian's contraction grows with the window length) and
+    # converges in four windows of T = 0.25; the windows equal the oracle's
+    # exact windows (stepping with Newton per step)
+    from oracle import windows as WIN
+    a = (-1.0, 0.0, 1.0)
+    nwin = 4
+    wl = W.nl_ade2d(nx=15, ny=13, nt=16, T=0.25, nu=1e-3, alpha=1e-2, reaction=a)
+    pb = wl.problem
+    ref = WIN.windows_nl(pb, wl.u0, nwin, a)
+    plan = make_plan(pb, prec)
+    u, it, rel = plan.nl_solve_windows(a, dev(wl.u0), nwin, tol=1e-11, maxit=80)
+    assert rel <= 1e-11 and it >= nwin
+    assert np.abs(host(u) - ref).max() <= 1e-9 * np.abs(ref).max()
+    plan.close()
+
+
+def test_windows_with_source_match_oracle(pd):
+    from oracle import windows as WIN
+    a = (0.3, -0.5, 1.0)
+    nwin, nt = 3, 12
+    sp = W.Space(dim=1, nx=40, nu=1e-2, ax=0.5, bc_x=W.PERIODIC)
+    pb = W.Problem(space=sp, nt=nt, dt=1.0 / 36, scheme=W.CN, alpha=1e-2)
+    u0 = np.sin(2 * np.pi * sp.xs())
+    f = W.uniform(W.SEED_BASE + 431, (nwin * nt + 1) * 40, -1, 1).reshape(-1, 40)
+    ref = WIN.windows_nl(pb, u0, nwin, a, f)
+    plan = make_plan(pb, PD_MIXED)
+    u, it, rel = plan.nl_solve_windows(a, dev(u0), nwin, dev(f), tol=1e-12, maxit=80)
+    assert rel <= 1e-12
+    assert np.abs(host(u) - ref).max() <= 1e-10 * np.abs(ref).max()
+    plan.close()

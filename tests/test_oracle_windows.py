@@ -37,3 +37,20 @@ def test_geometric_windows_mode_amplification(scheme):
     amp = np.cumprod(np.tile(R, 3))
     ref = np.real(np.outer(amp, v))
     assert np.abs(U.reshape(18, n) - ref).max() < 1e-13
+
+
+def test_nonlinear_windows_equal_long_horizon_stepping():
+    # nonlinear windows solved exactly chain into the one-window stepping
+    # solution over the whole horizon (the windows only cut the all-at-once
+    # system; each step's equation is unchanged)
+    from oracle import nonlinear as NL
+    a = (-1.0, 0.5, 1.0)
+    nwin, nt = 3, 8
+    sp = W.Space(dim=1, nx=31, nu=1e-2, ax=0.5, bc_x=W.PERIODIC)
+    pw = W.Problem(space=sp, nt=nt, dt=1.0 / 32, scheme=W.CN, alpha=1e-2)
+    pl = W.Problem(space=sp, nt=nwin * nt, dt=1.0 / 32, scheme=W.CN, alpha=1e-2)
+    u0 = np.sin(2 * np.pi * sp.xs())
+    f = W.uniform(W.SEED_BASE + 430, (nwin * nt + 1) * 31, -1, 1).reshape(-1, 31)
+    Uw = WIN.windows_nl(pw, u0, nwin, a, f)
+    Ul = NL.solve_sequential_nl(pl, NL.build_rhs_nl(pl, u0, a, f=f), a)
+    assert np.abs(Uw.reshape(nwin * nt, -1) - Ul).max() <= 1e-12 * np.abs(Ul).max()
