@@ -95,3 +95,11 @@ def test_nonlinear_entry_points_reject_a_null_plan_without_gpu():
     assert pd.pd_nl_build_rhs(None, (0, 0, 1), None, None, None) == pd.PD_ERR_ARG
     assert pd.pd_nl_residual(None, (0, 0, 1), None, None, None)[0] == pd.PD_ERR_ARG
     assert pd.pd_nl_solve(None, (0, 0, 1), None, None, 1e-10, 10)[0] == pd.PD_ERR_ARG
+
+
+def test_window_and_left_gmres_entry_points_reject_a_null_plan_without_gpu():
+    import paradiag_gb300 as pd
+    pd.build()
+    assert pd.pd_nl_solve_windows(None, (0, 0, 1), None, None, 2, None, 1e-10, 10)[0] == \
+        pd.PD_ERR_ARG
+    assert pd.pdc_solve_left(None, None, None, 1e-7, 10, 20)[0] == pd.PD_ERR_ARG
