@@ -34,6 +34,7 @@ CASES = {
                                reaction=(0.0, 0.0, 1.0)), None),
     "1d_cn_manufactured": (W.nl_manufactured1d(nx=63, nt=32), "f"),
     "1d_cn_nt12": (W.nl_manufactured1d(nx=40, nt=12, reaction=(0.3, -0.5, 1.0)), "f"),
+    "1d_theta07": (W.nl_manufactured1d(nx=50, nt=20, scheme=W.THETA, theta=0.7), "f"),
 }
 
 

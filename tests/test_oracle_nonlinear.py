@@ -7,7 +7,7 @@ The pins that tie it to something other than itself:
     O2): same right-hand side, same solution, and -- because the averaged
     Jacobian is then exactly K + a1 I -- the same iterates;
   * the manufactured solution u = exp(-t) sin(pi x): errors fall as dt^2 + h^2
-    for Crank-Nicolson and as dt for backward Euler;
+    for Crank-Nicolson and as dt for backward Euler and theta = 0.7;
   * sequential stepping with Newton per step equals a full Newton solve of the
     whole all-at-once system (an independent algorithm for eq. 1.4);
   * the averaged shift of a constant field is phi' at that value.
@@ -24,8 +24,13 @@ from oracle import paradiag as PD
 from oracle import stepping as ST
 
 
-def small2d(nt=16, scheme=W.CN, reaction=(-1.0, 0.0, 1.0)):
-    return W.nl_ade2d(nx=15, ny=13, nt=nt, nu=1e-2, scheme=scheme, alpha=1e-2, reaction=reaction)
+def small2d(nt=16, scheme=W.CN, reaction=(-1.0, 0.0, 1.0), theta=None):
+    wl = W.nl_ade2d(nx=15, ny=13, nt=nt, nu=1e-2, scheme=scheme, alpha=1e-2, reaction=reaction)
+    if theta is not None:   # a general theta-method on the same data
+        pb = W.Problem(space=wl.problem.space, nt=nt, dt=wl.problem.dt, scheme=W.THETA,
+                       alpha=1e-2, theta=theta)
+        wl = W.Workload(wl.name, pb, wl.u0, None, None, wl.seed, extra=wl.extra)
+    return wl
 
 
 def test_reaction_and_derivative():
@@ -46,10 +51,11 @@ def test_average_shift_of_constant_field():
         == pytest.approx(0.8, abs=1e-15)
 
 
-@pytest.mark.parametrize("scheme", [W.BE, W.CN])
+@pytest.mark.parametrize("scheme", [W.BE, W.CN, W.THETA])
 def test_linear_reaction_is_the_shifted_linear_problem(scheme):
     a1 = 0.7
-    wl = small2d(scheme=scheme, reaction=(a1, 0.0, 0.0))
+    wl = small2d(scheme=scheme, reaction=(a1, 0.0, 0.0),
+                 theta=0.7 if scheme == W.THETA else None)
     pb = wl.problem
     K = O.stencil(pb.space)
     Ks = (K + a1 * sps.identity(K.shape[0])).tocsr()
@@ -72,11 +78,13 @@ def test_linear_reaction_is_the_shifted_linear_problem(scheme):
 @pytest.mark.parametrize("scheme,sizes,ratio,first", [
     (W.CN, [(15, 8), (31, 16), (63, 32)], (3.6, 4.5), 2.5e-3),
     (W.BE, [(255, 8), (255, 16), (255, 32)], (1.8, 2.2), 4e-3),
+    (W.THETA, [(255, 8), (255, 16), (255, 32)], (1.8, 2.2), 1.5e-3),   # theta = 0.7
 ])
 def test_manufactured_solution_convergence(scheme, sizes, ratio, first):
     errs = []
     for nx, nt in sizes:
-        wl = W.nl_manufactured1d(nx=nx, nt=nt, scheme=scheme)
+        wl = W.nl_manufactured1d(nx=nx, nt=nt, scheme=scheme,
+                                 theta=0.7 if scheme == W.THETA else 1.0)
         pb = wl.problem
         a = wl.extra["reaction"]
         b = NL.build_rhs_nl(pb, wl.u0, a, f=wl.f)
@@ -111,9 +119,9 @@ def test_sequential_equals_full_newton_on_the_all_at_once_system():
     assert np.abs(X - U).max() <= 1e-12 * np.abs(U).max()
 
 
-@pytest.mark.parametrize("scheme", [W.BE, W.CN])
+@pytest.mark.parametrize("scheme", [W.BE, W.CN, W.THETA])
 def test_simplified_newton_reaches_the_exact_solution(scheme):
-    wl = small2d(scheme=scheme)
+    wl = small2d(scheme=scheme, theta=0.7 if scheme == W.THETA else None)
     pb = wl.problem
     a = wl.extra["reaction"]
     b = NL.build_rhs_nl(pb, wl.u0, a)

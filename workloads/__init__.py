@@ -345,13 +345,14 @@ def hybrid_wave2d(n=512, nt=512, T=2.0, seed=SEED_BASE + 9, name="hybrid_wave2d"
 
 
 def nl_manufactured1d(nx=63, nt=32, T=1.0, nu=1.0, reaction=(0.5, 1.0, 2.0), scheme=CN,
-                      alpha=1e-2, seed=SEED_BASE + 10, name="nl_manufactured1d") -> Workload:
+                      alpha=1e-2, theta=1.0, seed=SEED_BASE + 10,
+                      name="nl_manufactured1d") -> Workload:
     """U' + K U + phi(U) = f on (0,1), Dirichlet, K = -nu d_xx, with the cubic
     reaction phi(u) = a1 u + a2 u^2 + a3 u^3 and f chosen so that the exact
     solution is u = exp(-t) sin(pi x).  ``extra``: the reaction coefficients
     and the exact solution at t_1..t_nt."""
     sp = Space(dim=1, nx=nx, nu=nu, bc_x=DIRICHLET)
-    pb = Problem(space=sp, nt=nt, dt=T / nt, scheme=scheme, alpha=alpha)
+    pb = Problem(space=sp, nt=nt, dt=T / nt, scheme=scheme, alpha=alpha, theta=theta)
     x = sp.xs()
     t = (T / nt) * np.arange(nt + 1)
     u = np.outer(np.exp(-t), np.sin(np.pi * x))
