@@ -49,7 +49,7 @@ def parse():
     ap.add_argument("--pd1-only", action="store_true",
                     help="only the ParaDiag-I leg (one JSON object; profiling runs)")
     ap.add_argument("--pd1-kernels", action="store_true",
-                    help="only the ParaDiag-I mixed kernel profile (ncu driver)")
+                    help="only the ParaDiag-I mixed kernel profile (the command ncu captures profile)")
     ap.add_argument("--no-hybrid", action="store_true", help="skip the hybrid ParaDiag-I leg")
     ap.add_argument("--no-control", action="store_true", help="skip the optimal-control leg")
     ap.add_argument("--no-wave", action="store_true",
@@ -67,9 +67,9 @@ def parse():
     ap.add_argument("--hybrid-only", action="store_true",
                     help="only the hybrid ParaDiag-I leg (one JSON object)")
     ap.add_argument("--hybrid-kernels", action="store_true",
-                    help="only the hybrid ParaDiag-I mixed kernel profile (ncu driver)")
+                    help="only the hybrid ParaDiag-I mixed kernel profile (the command ncu captures profile)")
     ap.add_argument("--profile-iteration", action="store_true",
-                    help="only time the kernels of one iteration (the driver of ncu captures)")
+                    help="only time the kernels of one iteration (the command ncu captures profile)")
     ap.add_argument("--sweep", action="store_true",
                     help="roofline sweep of the iteration kernels over 1D sizes "
                          "nx in {255, 1023, 4095} x Nt in {256, 1024, 4096}")
@@ -837,7 +837,7 @@ def main():
             print(json.dumps(out), flush=True)
         return
     if args.profile_iteration:
-        # the residual-mode iteration of the solver, kernel by kernel (ncu driver)
+        # the residual-mode iteration of the solver, kernel by kernel (the command ncu captures profile)
         for _ in range(2):
             kms = plan.profile_iteration(b, u, reps=5)
         torch.cuda.synchronize()
