@@ -178,11 +178,9 @@ def flops_per_launch_xform(rows, nx):
     return 8.0 * rows * nx * nx
 
 
-# DRAM bytes (read + write) per launch from the ncu captures summarised in
-# profiles/ade2d_cn_255x255x256_mixed_kernels.md (bench workload; the time
-# kernels as recaptured after their last change, with the 16-column tile that
-# the autotuner keeps under the profiler); a kernel's entry goes back to None
-# whenever that kernel changes.
+# DRAM bytes (read + write) per launch from one ncu capture of each kernel on
+# the bench workload (the time kernels as recaptured after their last change);
+# a kernel's entry goes back to None whenever that kernel changes.
 NCU_TRAFFIC = {"resid_gamma_fft": 319.4e6, "xform_fwd": 81.4e6, "tridiag": 79.5e6,
                "xform_inv": 81.4e6, "ifft_gamma_update": 279.7e6}
 
@@ -254,9 +252,9 @@ def batched_leg(pd, torch, dev, args):
     return out
 
 
-# DRAM bytes (read + write) per launch of the ParaDiag-I mixed kernels from the ncu
-# captures summarised in profiles/pd1_ade2d_be_255x1023x32_kernels.md; an entry goes
-# back to absent whenever its kernel changes.
+# DRAM bytes (read + write) per launch of the ParaDiag-I mixed kernels from one ncu
+# capture of each on the 255 x 1023 x 32 window; an entry goes back to absent
+# whenever its kernel changes.
 PD1_NCU_TRAFFIC = {("mixed", "pd1_resid_step_a"): 169.9e6, ("mixed", "pd1_step_c_update"): 155.0e6}
 
 

@@ -80,7 +80,8 @@ typedef struct pd_plan pd_plan;
 
 /* Create a plan for the all-at-once system on Nt uniform steps of size dt with
  * preconditioner parameter alpha in (0, 1] (Lemma 1).  Any Nt >= 1: powers of
- * two use a radix-4/2 Stockham FFT (Nt <= 4096 for PD_MIXED, <= 2048 for
+ * two use a radix-16 Stockham FFT (one radix-2/4/8 pass when log2 Nt is not a
+ * multiple of 4; Nt <= 4096 for PD_MIXED, <= 2048 for
  * PD_FP64), other lengths Bluestein's chirp-z transform of length
  * M = 2^ceil(log2(2 Nt - 1)) within the same limits (Nt <= 2048 / 1024);
  * larger Nt gives PD_ERR_UNSUPPORTED.  alpha = 1 is
@@ -105,7 +106,9 @@ PD_API pd_status pd_residual(pd_plan* plan, const double* b, const double* u, do
 /* y = A u (eq. 1.1) in FP64. */
 PD_API pd_status pd_apply_A(pd_plan* plan, const double* u, double* y);
 
-/* y = A^T u in FP64. */
+/* y = A^T u in FP64: the transpose of eq. 1.1, (B1^T (x) I + B2^T (x) K^T) u,
+ * the operator of the adjoint system (Section 4 uses the transposed blocks
+ * B1^T, B2^T in its optimality system). */
 PD_API pd_status pd_apply_AT(pd_plan* plan, const double* u, double* y);
 
 /* b of the all-at-once system from the initial data and the source:
@@ -176,7 +179,8 @@ PD_API pd_status pd_solve_windows(pd_plan* plan, const double* u0, const double*
  * pd_build_rhs with -(1 - theta) phi(u0) added to the first row.
  *
  * pd_nl_residual: r = b - (B1 (x) I) u - (B2 (x) I) F(u), F(u)_n = K U_n +
- * phi(U_n), in FP64.  sigma (host, may be NULL) receives the mean of phi'(U)
+ * phi(U_n), in FP64 on FP64 plans and in double-float (FP32 pairs, 48-bit
+ * significand) on mixed plans.  sigma (host, may be NULL) receives the mean of phi'(U)
  * over all time levels and grid points, rnorm2 (host, may be NULL) ||r||^2;
  * asking for either synchronises the plan's stream.
  *
@@ -185,7 +189,9 @@ PD_API pd_status pd_solve_windows(pd_plan* plan, const double* u0, const double*
  * with P_alpha(u) = C1 (x) I + C2 (x) (K + sigma I), sigma the mean of
  * phi'(U) (the averaged Jacobian), u += z; until ||r|| <= tol ||b|| or maxit
  * corrections.  The plan's preconditioner precision applies (FP32 on mixed
- * plans, the residual is always FP64).  iters: corrections applied; relres:
+ * plans), and the residual is FP64 on FP64 plans, double-float on mixed plans
+ * (the iterate then also lives in double-float inside the solve).  iters:
+ * corrections applied; relres:
  * the last ||r|| / ||b|| (either may be NULL).  Returns PD_ERR_NOT_CONVERGED
  * after maxit corrections, PD_ERR_NONFINITE on a NaN or Inf (a diverging
  * iteration).  Allocates two [Nt][S] FP64 work arrays in the plan on first
@@ -309,21 +315,28 @@ PD_API const char* pd_batch_last_error(const pd_batch* batch);
  * plug-ins whose host application owns every device allocation, or code in a
  * region where allocation is not allowed.  Such callers cannot create a plan
  * (pd_plan_create allocates its tables and workspace).
+ *   Sizes.    Nt a power of two, 1 <= Nt <= 4096, and 1 <= nx <= 4096 (the
+ *             limits of the plan path's mixed-precision kernels); other sizes
+ *             return PD_ERR_UNSUPPORTED.  alpha = 1 is rejected with
+ *             PD_ERR_ARG when a shifted system is singular (as pd_plan_create).
  *   Scratch.  The half spectrum and the eigenvalue, Gamma and twiddle tables
  *             live in one file-scope __device__ array of
  *             PD_NOALLOC_SCRATCH_BYTES that every GPU loading this library
  *             holds until the process exits.  Problems needing more (about
  *             8 (Nt/2+1) nx bytes plus small tables) are rejected with
  *             PD_ERR_ARG; *scratch_needed (if not NULL) receives the bytes the
- *             problem needs in every case.
+ *             problem needs whenever the sizes are supported.
  *   Set-up.   The first call on a device looks up the array's device address
  *             (cudaGetSymbolAddress) with that device current; make that first
  *             call before any stream capture.
  *   Sharing.  All calls share the one array and leave their data in it; calls
  *             whose work overlaps on the GPU (other streams or host threads)
  *             race and must be serialised by the caller.
- * r, z: [Nt][nx] device FP64 (caller-owned); stream: cudaStream_t.  Work is
- * enqueued on the stream; the tables are copied from host memory first. */
+ *   Status.   The tables are copied from host memory onto the stream, the
+ *             kernels enqueued, and a status word read back: the call returns
+ *             after its work has finished, with PD_ERR_NONFINITE when r, the
+ *             spectrum or z held a non-finite value.
+ * r, z: [Nt][nx] device FP64 (caller-owned); stream: cudaStream_t. */
 PD_API pd_status pd_apply_precond_noalloc(const pd_space* sp, int nt, double dt, double alpha,
                                           int scheme, double theta, const double* r, double* z,
                                           void* stream, unsigned long long* scratch_needed);

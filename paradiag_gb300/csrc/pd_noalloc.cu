@@ -58,7 +58,11 @@ extern "C" pd_status pd_apply_precond_noalloc(const pd_space* sp, int nt, double
   if (!(dt > 0.0) || !std::isfinite(dt) || !(alpha > 0.0 && alpha <= 1.0)) return PD_ERR_ARG;
   if (scheme < PD_BE || scheme > PD_LEAPFROG) return PD_ERR_ARG;
   if (scheme == PD_THETA && !(theta >= 0.0 && theta <= 1.0)) return PD_ERR_ARG;
-  if (nt < 1 || !is_pow2(nt) || nt > 8192) return PD_ERR_UNSUPPORTED;
+  // the plan path's mixed-precision limits: a time tile holds at most 4096
+  // rows (two columns of 16 complex elements per thread), and a tridiagonal
+  // system at most TRI_NMAX rows
+  if (nt < 1 || !is_pow2(nt) || nt > 4096) return PD_ERR_UNSUPPORTED;
+  if (sp->nx > TRI_NMAX) return PD_ERR_UNSUPPORTED;
 
   const int nx = sp->nx, S = nx, nh = nt / 2 + 1;
   // scratch layout: spectrum | lambda pairs | gamma | gamma^-1/Nt | twiddles | flag
@@ -98,6 +102,7 @@ extern "C" pd_status pd_apply_precond_noalloc(const pd_space* sp, int nt, double
   const double PI = 3.14159265358979323846;
   const double ar = std::pow(alpha, 1.0 / nt);
   std::vector<float2> lam((size_t)2 * nh), tw(nt);
+  std::vector<std::complex<double>> lamd((size_t)2 * nh);
   std::vector<float> gam(nt), igam(nt);
   for (int k = 0; k < nh; ++k) {
     const double a = -2.0 * PI * k / nt;
@@ -108,8 +113,24 @@ extern "C" pd_status pd_apply_precond_noalloc(const pd_space* sp, int nt, double
       l2 += c2[m] * wm;
       wm *= w;
     }
+    lamd[2 * k] = l1;
+    lamd[2 * k + 1] = l2;
     lam[2 * k] = make_float2((float)l1.real(), (float)l1.imag());
     lam[2 * k + 1] = make_float2((float)l2.real(), (float)l2.imag());
+  }
+  if (alpha == 1.0) {
+    // as pd_plan_create: without the alpha scaling a shifted system
+    // lambda_1 + lambda_2 mu_i (mu_i = kc + 2 sqrt(kl ku) cos(pi i / (nx + 1)),
+    // the eigenvalues of the tridiagonal K) may be singular; reject it
+    const std::complex<double> sq = std::sqrt(std::complex<double>(kl * ku, 0.0));
+    for (int k = 0; k < nh; ++k) {
+      const std::complex<double> l1 = lamd[2 * k], l2 = lamd[2 * k + 1];
+      for (int i = 1; i <= nx; ++i) {
+        const std::complex<double> mu = kc + 2.0 * sq * std::cos(PI * i / (nx + 1));
+        const double sc = std::abs(l1) + std::abs(l2) * std::abs(mu) + 1e-300;
+        if (std::abs(l1 + l2 * mu) <= 1e-12 * sc) return PD_ERR_ARG;
+      }
+    }
   }
   for (int n = 0; n < nt; ++n) {
     gam[n] = (float)std::pow(alpha, (double)n / nt);
@@ -162,5 +183,12 @@ extern "C" pd_status pd_apply_precond_noalloc(const pd_space* sp, int nt, double
   ia.out64 = z;
   ia.flag = reinterpret_cast<int*>(b + off_flag);
   if (launch_time_inv(ia, false, st) != cudaSuccess) return PD_ERR_CUDA;
-  return PD_OK;
+  // the device flag (bit 0: a non-finite value in r, the spectrum or z) is
+  // read back, so the call returns once its work on the stream has finished
+  int flag = 0;
+  if (cudaMemcpyAsync(&flag, b + off_flag, sizeof(int), cudaMemcpyDeviceToHost, st) !=
+          cudaSuccess ||
+      cudaStreamSynchronize(st) != cudaSuccess)
+    return PD_ERR_CUDA;
+  return flag != 0 ? PD_ERR_NONFINITE : PD_OK;
 }

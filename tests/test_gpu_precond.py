@@ -5,11 +5,18 @@ Tolerances.  The transform has Cond_2(V) <= 1/alpha (eq. 2.13) and each
 shifted system lambda_1 I + lambda_2 K has a 2-norm condition number kappa_k,
 so a backward-stable evaluation in precision eps gives a relative error of
 order eps * kappa / alpha with kappa = max_k kappa_k (computed here from the
-dense shifted matrices).  FP64 path: tolerance 64 eps64 kappa / alpha (at least
-1e-12).  Mixed path (FP32 transform and solves): 64 eps32 kappa / alpha.
+dense shifted matrices); the FFTs add a factor growing like log2 M, M the
+transform length (Nt, or Bluestein's M = 2^ceil(log2(2 Nt - 1))).  The bound
+checked is 2 eps kappa (1 + log2 M) / alpha with eps = 2^-53 (FP64 path) or
+2^-24 (mixed path: FP32 transforms and solves).  Over the 52 cases the measured
+max-norm errors sit between 1/1250 and 1/4.6 of it; every case prints its
+error and the ratio err / (eps kappa / alpha).
 The invariant P z = r is checked relative to |P| |z| (entrywise absolute
-values), the natural scale of the rounding error of the product.
+values), the natural scale of the rounding error of the product, against
+64 eps kappa / alpha (at least 1e-12).
 """
+import zlib
+
 import numpy as np
 import pytest
 
@@ -89,17 +96,23 @@ def abs_product_scale(pb, z):
 @pytest.mark.parametrize("prec", ["fp64", "mixed"])
 def test_precond_matches_oracle(pd, name, prec):
     pb = CASES[name]
-    r = W.uniform(hash(name) % 1000 + 11, pb.unknowns, -1.0, 1.0).reshape(pb.nt, -1)
+    # a fixed seed per case (crc32 of its name), the same in every process
+    r = W.uniform(W.SEED_BASE + zlib.crc32(name.encode()) % 1000, pb.unknowns,
+                  -1.0, 1.0).reshape(pb.nt, -1)
     zref = PD.precond_apply(pb, r)
     plan = make_plan(pb, pd.PD_FP64 if prec == "fp64" else pd.PD_MIXED)
     z = host(plan.apply_precond(dev(r)))
     kap = kappa(pb)
     eps = 2.0 ** -53 if prec == "fp64" else EPS32
-    tol = max(64 * eps * kap / pb.alpha, 1e-12)
+    M = pb.nt if pb.nt & (pb.nt - 1) == 0 else 1 << int(np.ceil(np.log2(2 * pb.nt - 1)))
+    tol = 2.0 * eps * kap * (1.0 + np.log2(M)) / pb.alpha
     err = relerr(z, zref)
+    print(f"PRECOND_ERR {name} {prec} err={err:.3e} eps_kappa_over_alpha={eps * kap / pb.alpha:.3e}"
+          f" ratio={err / (eps * kap / pb.alpha):.3e} of_bound={err / tol:.3e}")
     assert err <= tol, (name, prec, err, tol, kap)
     # invariant P z = r, evaluated by the oracle in FP64, relative to |P||z|
     pz = O.apply_P(pb, z)
     res = np.abs(pz - r).max() / abs_product_scale(pb, z)
-    assert res <= tol, (res, tol)
+    tol_inv = max(64 * eps * kap / pb.alpha, 1e-12)
+    assert res <= tol_inv, (res, tol_inv)
     plan.close()
