@@ -66,57 +66,66 @@ def solve_adjoint_sequential(problem: Problem, g: np.ndarray, K=None) -> np.ndar
 
 def _xmode_chunk(args):
     """Sequential time stepping of a share of the x-Fourier modes (one worker's
-    part of solve_sequential_xmodes).  args = (c1, c2, band, Ky, share, b) with
-    share a list of (j, mu_j); returns this share's terms of the inverse DFT
-    along x, a real array of shape (Nt, ny, nx)."""
-    c1, c2, band, Ky, share, b = args
-    nt, ny, nx = b.shape
-    idx = np.arange(nx)
-    out = np.zeros((nt, ny, nx))
-    I = np.eye(ny)
-    for j, muj in share:
-        # the naive DFT of every b_n along x at frequency j
-        bh = b @ np.exp(-2j * np.pi * j * idx / nx)                     # (nt, ny)
-        Kj = muj * I + Ky                                                 # K on mode j
-        lu = sla.lu_factor(c1[0] * I + c2[0] * Kj)
-        Uh = np.zeros((nt, ny), dtype=np.complex128)
+    part of solve_sequential_xmodes).  args = (c1, c2, band, Ky, mus, bh) with
+    Ky the tridiagonal K_y (sparse), mus the eigenvalues mu_j of the share's
+    modes and bh their transformed right-hand sides, shape (Nt, ny, len(mus));
+    returns the transformed solution of the same shape.  The tridiagonal step
+    matrix of each mode is factored once by LAPACK's LU with partial pivoting
+    (zgttrf) and solved at every step (zgttrs)."""
+    c1, c2, band, Ky, mus, bh = args
+    nt, ny, _ = bh.shape
+    Uh = np.zeros(bh.shape, dtype=np.complex128)
+    Kd = Ky.diagonal(0).astype(np.complex128)
+    Kl = Ky.diagonal(-1).astype(np.complex128)
+    Ku = Ky.diagonal(1).astype(np.complex128)
+    for q, muj in enumerate(mus):
+        # step matrix c1[0] I + c2[0] (mu_j I + K_y) as its three diagonals
+        dl, d, du = c2[0] * Kl, c1[0] + c2[0] * (muj + Kd), c2[0] * Ku
+        dl, d, du, du2, ipiv, info = sla.lapack.zgttrf(dl, d, du)
+        if info != 0:
+            raise np.linalg.LinAlgError(f"singular step matrix for x-mode {q}")
         for n in range(nt):
-            rhs = bh[n].copy()
+            rhs = bh[n, :, q].copy()
             for m in band:
                 if n - m >= 0:
-                    rhs -= c1[m] * Uh[n - m] + c2[m] * (Kj @ Uh[n - m])
-            Uh[n] = sla.lu_solve(lu, rhs)
-        # this mode's term of the inverse DFT along x
-        out += np.real(Uh[:, :, None] * np.exp(2j * np.pi * j * idx / nx)[None, None, :]) / nx
-    return out
+                    v = Uh[n - m, :, q]
+                    rhs -= c1[m] * v + c2[m] * (muj * v + Ky @ v)
+            Uh[n, :, q], info = sla.lapack.zgttrs(dl, d, du, du2, ipiv, rhs)
+    return Uh
 
 
 def solve_sequential_xmodes(problem: Problem, b: np.ndarray, pool=None, chunks=1) -> np.ndarray:
     """O1 for 2D problems with x periodic, mode by mode: u = A^{-1} b.
 
     K = I_y (x) K_x + K_y (x) I_x with a circulant K_x, so the naive DFT along x
-    (exp(-2 pi i j x / nx)) turns A u = b into nx independent all-at-once
-    systems, one per x-mode j, with K replaced by mu_j I + K_y, mu_j the
-    eigenvalue of K_x for the mode exp(2 pi i j x / nx) (read off K_x's first
-    row).  Each is solved by forward substitution in time with a dense LU with
-    partial pivoting of its step matrix, then the modes are summed back by the
-    inverse DFT.  The modes are independent, so they can be spread over the
-    processes of ``pool`` (any object with a ``map``) in ``chunks`` shares; time
-    stays sequential within each mode.  b, u of shape (Nt, S).
+    (a dense matrix of exp(-2 pi i j x / nx) entries) turns A u = b into nx
+    independent all-at-once systems, one per x-mode j, with K replaced by
+    mu_j I + K_y, mu_j the eigenvalue of K_x for the mode exp(2 pi i j x / nx)
+    (read off K_x's first row).  Each is solved by forward substitution in time
+    with a tridiagonal LU with partial pivoting of its step matrix (LAPACK's
+    zgttrf / zgttrs, the library primitive used as the spatial solve); the inverse DFT
+    along x sums the modes back.  The modes are independent, so their time
+    stepping can be spread over the processes of ``pool`` (any object with a
+    ``map``) in ``chunks`` shares; time stays sequential within each mode.
+    b, u of shape (Nt, S).
     """
     sp = problem.space
     if sp.dim != 2 or sp.bc_x != PERIODIC:
         raise ValueError("solve_sequential_xmodes needs a 2D problem with x periodic")
     nx, ny = sp.nx, sp.ny
     Kx = stencil_1d(nx, sp.hx, sp.nu, sp.ax, sp.bc_x).toarray()
-    Ky = stencil_1d(ny, sp.hy, sp.nu, sp.ay, sp.bc_y).toarray()
+    Ky = stencil_1d(ny, sp.hy, sp.nu, sp.ay, sp.bc_y)
     x = np.arange(nx)
-    mu = [(j, complex(Kx[0] @ np.exp(2j * np.pi * j * x / nx))) for j in range(nx)]
+    F = np.exp(-2j * np.pi * np.outer(x, x) / nx)                         # [x][j]
+    mu = np.array([Kx[0] @ np.exp(2j * np.pi * j * x / nx) for j in range(nx)])
     c1, c2 = first_columns(problem)
     nt = b.shape[0]
     band = [m for m in range(1, nt) if c1[m] != 0.0 or c2[m] != 0.0]
-    b3 = np.asarray(b, dtype=np.float64).reshape(nt, ny, nx)
-    shares = [mu[i::chunks] for i in range(chunks)]
-    args = [(c1, c2, band, Ky, share, b3) for share in shares if share]
+    bh = np.asarray(b, dtype=np.float64).reshape(nt, ny, nx) @ F            # (nt, ny, nx modes)
+    shares = [np.arange(i, nx, chunks) for i in range(chunks) if i < nx]
+    args = [(c1, c2, band, Ky, mu[js], np.ascontiguousarray(bh[:, :, js])) for js in shares]
     parts = list(pool.map(_xmode_chunk, args)) if pool is not None else [_xmode_chunk(a) for a in args]
-    return np.sum(parts, axis=0).reshape(nt, ny * nx)
+    Uh = np.empty_like(bh)
+    for js, part in zip(shares, parts):
+        Uh[:, :, js] = part
+    return (np.real(Uh @ F.conj().T) / nx).reshape(nt, ny * nx)
