@@ -132,7 +132,8 @@ void free_plan(pd_plan* p) {
                   p->mu,   p->spec, p->spec2, p->Udf,  p->Bdf,   p->w64a,  p->w64b,
                   p->dsc,  p->dflag, p->V,   p->Z,      p->dh,    p->Gf_hi, p->Gf_lo,
                   p->Gi_hi, p->Gi_lo, const_cast<void*>(p->xf.chirp),
-                  const_cast<void*>(p->xf.bhat), p->amax, p->nl_r, p->nl_z, p->nl_lam0, p->nl_b};
+                  const_cast<void*>(p->xf.bhat), p->amax, p->nl_r, p->nl_z, p->nl_lam0, p->nl_b,
+                  p->xq_tw, const_cast<void*>(p->xq_xf.chirp), const_cast<void*>(p->xq_xf.bhat)};
   for (void* q : ptrs)
     if (q) cudaFree(q);
   if (p->hsc) cudaFreeHost(p->hsc);
@@ -194,6 +195,22 @@ InvArgs inv_base_impl(const pd_plan* p) {
 pd_status xform_dir(pd_plan* p, bool fwd) {
   if (p->xform_tc) {
     LK(launch_xform_tc(fwd ? p->xtc_fwd : p->xtc_inv, p->dflag, p->stream));
+    return PD_OK;
+  }
+  if (p->xq) {
+    XfftArgs xa;
+    xa.rows = p->nh * (p->S / p->sp.nx);
+    xa.nx = p->sp.nx;
+    xa.ld = p->sg.nxp;
+    xa.L = p->xq_L;
+    xa.logL = ilog2(p->xq_L);
+    xa.dst = p->xq_dst;
+    xa.inv = fwd ? 0 : 1;
+    xa.xf = p->xq_xf;
+    xa.tw = p->xq_tw;
+    xa.in = fwd ? p->spec : p->spec2;
+    xa.out = fwd ? p->spec2 : p->spec;
+    LK(launch_xform_fft64(xa, p->stream));
     return PD_OK;
   }
   XformArgs xa;
@@ -831,6 +848,42 @@ void host_fft(std::vector<cd>& a) {
 
 double hstep(int n, double L, int bc) { return L / (bc == PD_PERIODIC ? n : n + 1); }
 
+// Tables of a length-L DFT on the GPU: for a power-of-two L the L twiddles
+// e^{-2 pi i m / L}; otherwise Bluestein's form with M = 2^ceil(log2(2L - 1)):
+// the chirp w_m = e^{-i pi m^2 / L} (m^2 reduced mod 2L for an accurate
+// angle), the transformed filter bhat = FFT_M(conj w, wrapped) / M and the M
+// twiddles.  M = 0 for a power-of-two L.
+struct DftTables {
+  int M = 0;
+  std::vector<cd> tw, chirp, bhat;
+};
+DftTables dft_tables(int L) {
+  const double PI = 3.14159265358979323846;
+  DftTables t;
+  if (!is_pow2(L)) {
+    t.M = 1;
+    while (t.M < 2 * L - 1) t.M <<= 1;
+    t.chirp.resize(L);
+    for (int n = 0; n < L; ++n) {
+      const long long q = ((long long)n * n) % (2LL * L);
+      const double th = -PI * (double)q / L;
+      t.chirp[n] = cd(std::cos(th), std::sin(th));
+    }
+    t.bhat.assign(t.M, cd(0.0, 0.0));
+    t.bhat[0] = std::conj(t.chirp[0]);
+    for (int m = 1; m < L; ++m) t.bhat[m] = t.bhat[t.M - m] = std::conj(t.chirp[m]);
+    host_fft(t.bhat);
+    for (cd& v : t.bhat) v /= (double)t.M;
+  }
+  const int ntw = t.M ? t.M : L;
+  t.tw.resize(ntw);
+  for (int m = 0; m < ntw; ++m) {
+    const double th = -2.0 * PI * m / ntw;
+    t.tw[m] = cd(std::cos(th), std::sin(th));
+  }
+  return t;
+}
+
 }  // namespace
 
 // internal helpers shared with the batched solver (pd_batch.cu)
@@ -1117,6 +1170,29 @@ pd_status plan_create_internal(const pd_space* sp, int nt, double dt, double alp
     pd_status s1 = upload_cplx(p, &p->Qf, Qf, p->fp64);
     if (s1 == PD_OK) s1 = upload_cplx(p, &p->Qi, Qi, p->fp64);
     if (s1 == PD_OK) s1 = upload_cplx(p, &p->mu, mux, p->fp64);
+    if (s1 == PD_OK && p->fp64) {
+      // the FFT form of the transform: DFT of length n (periodic x) or of the
+      // odd extension, length 2 (n + 1) (Dirichlet x); the kernel's tile
+      // holds up to 1024 transform points
+      const int L = sp->bc_x == PD_PERIODIC ? n : 2 * (n + 1);
+      DftTables t = dft_tables(L);
+      if ((t.M ? t.M : L) <= 1024) {
+        p->xq_L = L;
+        p->xq_dst = sp->bc_x == PD_PERIODIC ? 0 : 1;
+        s1 = upload_cplx(p, &p->xq_tw, t.tw, true);
+        if (s1 == PD_OK && t.M) {
+          void* c = nullptr;
+          void* bh = nullptr;
+          s1 = upload_cplx(p, &c, t.chirp, true);
+          p->xq_xf.chirp = c;
+          if (s1 == PD_OK) s1 = upload_cplx(p, &bh, t.bhat, true);
+          p->xq_xf.bhat = bh;
+          p->xq_xf.M = t.M;
+          p->xq_xf.logM = ilog2(t.M);
+        }
+        p->xq = s1 == PD_OK;
+      }
+    }
     const int rows = p->nh * (int)(S / n);
     p->xform_tc = !p->fp64 && n >= 16 && rows >= 128;
     if (s1 == PD_OK && p->xform_tc) {

@@ -126,7 +126,25 @@ struct XformArgs {
   void* out;
 };
 
+// Arguments of the FP64 x-eigentransform by FFT: every row of the half
+// spectrum (nx complex values, row stride ld) is transformed by a length-L
+// DFT, L = nx for a periodic x direction (the DFT diagonalises the circulant
+// K_x) or L = 2 (nx + 1) for a symmetric Dirichlet x direction (the sine
+// transform as the DFT of the odd extension).  A power-of-two L uses the
+// Stockham FFT directly (xf.M = 0, tw: L twiddles); other lengths Bluestein's
+// form with xf (M-point twiddles in tw).
+struct XfftArgs {
+  int rows, nx, ld, L, logL;
+  int dst;                        // 1: sine transform (Dirichlet x), 0: DFT (periodic x)
+  int inv;                        // 1: inverse transform (scaled), 0: forward
+  TimeXf xf;
+  const void* tw;                 // double2
+  const void* in;
+  void* out;
+};
+
 // Launchers (return a cudaError_t).
+cudaError_t launch_xform_fft64(const XfftArgs& a, cudaStream_t st);
 cudaError_t launch_time_fwd(const FwdArgs& a, bool fp64, cudaStream_t st);
 cudaError_t launch_time_inv(const InvArgs& a, bool fp64, cudaStream_t st);
 cudaError_t launch_tridiag(const TriArgs& a, bool fp64, cudaStream_t st);

@@ -38,6 +38,12 @@ struct pd_plan {
   TimeXf xf = {0, 0, nullptr, nullptr};   // Bluestein tables for non-power-of-two Nt
   void* Qf = nullptr;
   void* Qi = nullptr;
+  // FP64 plans: the x-eigentransform by FFT (length xq_L DFT per row; sine
+  // transform for a Dirichlet x direction), with its twiddle / Bluestein tables
+  bool xq = false;
+  int xq_L = 0, xq_dst = 0;
+  TimeXf xq_xf = {0, 0, nullptr, nullptr};
+  void* xq_tw = nullptr;
   void* mu = nullptr;
   // workspace
   void* spec = nullptr;

@@ -792,6 +792,91 @@ __global__ void __launch_bounds__(TT, PREC == 0 ? 4 : 2) k_time_inv_batch(const 
   time_inv_body<PREC, EPT>(descs[w.x], w.y);
 }
 
+// ---------------------------------------------------------------------------
+// FP64 x-eigentransform by FFT (step (b) of 2D problems on FP64 plans, and of
+// periodic 1D problems): every row of the half spectrum is transformed along
+// x by the DFT (periodic x: the eigenvectors of the circulant K_x) or by the
+// sine transform (symmetric Dirichlet x), in O(nx log nx) instead of the dense
+// O(nx^2) product.  A block holds XR rows transposed in shared memory (element
+// m of row r at m XR + r, the layout of the time kernels' tiles) and runs the
+// same Stockham / Bluestein routines on them.
+//   periodic, forward: Y_j = sum_x X_x e^{-2 pi i j x / nx}
+//   periodic, inverse: X_x = (1/nx) sum_j Y_j e^{+2 pi i j x / nx}
+//   sine transform:    Y_j = sum_x sin(pi (j+1)(x+1)/(nx+1)) X_x
+//                          = (i/2) V_{j+1}, V the length-2(nx+1) DFT of the odd
+//                            extension v = (0, X, 0, -X reversed);
+//                      the inverse is the same transform times 2/(nx+1).
+// ---------------------------------------------------------------------------
+constexpr int XR = 4;   // rows per block
+
+template <int EPT>
+__global__ void __launch_bounds__(TT) k_xform_fft64(XfftArgs a) {
+  using C = double2;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  C* sm = reinterpret_cast<C*>(smraw);
+  const int rows_fft = a.xf.M ? a.xf.M : a.L;
+  C* stw = sm + (size_t)rows_fft * XR;
+  for (int i = threadIdx.x; i < rows_fft; i += TT) stw[i] = reinterpret_cast<const C*>(a.tw)[i];
+  const int r0 = blockIdx.x * XR;
+  const C* in = reinterpret_cast<const C*>(a.in);
+  C* out = reinterpret_cast<C*>(a.out);
+  const int L = a.L, nx = a.nx;
+  // input rows (zero rows past the end), transposed into the tile
+  for (int e = threadIdx.x; e < XR * L; e += TT) {
+    const int r = e / L, m = e - r * L;
+    const int row = r0 + r;
+    C v = czero<C>();
+    if (row < a.rows) {
+      if (!a.dst) {
+        v = in[(size_t)row * a.ld + m];
+      } else if (m >= 1 && m <= nx) {
+        v = in[(size_t)row * a.ld + (m - 1)];                     // v_{x+1} = X_x
+      } else if (m >= nx + 2) {
+        const C w = in[(size_t)row * a.ld + (L - 1 - m)];         // v_{L-1-x} = -X_x
+        v = mk(-w.x, -w.y);
+      }
+    }
+    sm[m * XR + r] = v;
+  }
+  __syncthreads();
+  constexpr int lgXR = 2;
+  const bool inv = a.inv != 0 && !a.dst;                         // the sine transform is its own kind
+  if (a.xf.M == 0) {
+    if (inv) fft_tile<C, true, EPT>(sm, L, a.logL, lgXR, stw);
+    else fft_tile<C, false, EPT>(sm, L, a.logL, lgXR, stw);
+  } else {
+    if (inv) bluestein_tile<C, true, EPT>(sm, L, a.xf, lgXR, stw);
+    else bluestein_tile<C, false, EPT>(sm, L, a.xf, lgXR, stw);
+  }
+  // outputs
+  const double sc = a.dst ? (a.inv ? 1.0 / (nx + 1) : 0.5) : (a.inv ? 1.0 / nx : 1.0);
+  for (int e = threadIdx.x; e < XR * nx; e += TT) {
+    const int r = e / nx, j = e - r * nx;
+    const int row = r0 + r;
+    if (row >= a.rows) continue;
+    C y;
+    if (!a.dst) {
+      y = sm[j * XR + r];
+      y = mk(y.x * sc, y.y * sc);
+    } else {
+      const C v = sm[(j + 1) * XR + r];                          // (i/2) V_{j+1}, scaled
+      y = mk(-v.y * sc, v.x * sc);
+    }
+    out[(size_t)row * a.ld + j] = y;
+  }
+}
+
+template <int EPT>
+cudaError_t launch_xfft_e(const XfftArgs& a, cudaStream_t st) {
+  const int rows_fft = a.xf.M ? a.xf.M : a.L;
+  const size_t smem = (size_t)rows_fft * (XR + 1) * sizeof(double2);
+  auto kern = k_xform_fft64<EPT>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  kern<<<ceil_div(a.rows, XR), TT, smem, st>>>(a);
+  return cudaGetLastError();
+}
+
 // complex elements per thread needed by a tile of N x TX/2 columns
 // complex elements per thread of a tile; the tile budgets of the plans
 // (N TX <= 8192 mixed, <= 2048 FP64) keep it at 16 or less
@@ -860,6 +945,17 @@ cudaError_t launch_time_fwd(const FwdArgs& a, bool fp64, cudaStream_t st) {
 
 cudaError_t launch_time_inv(const InvArgs& a, bool fp64, cudaStream_t st) {
   return fp64 ? launch_inv_t<1>(a, st) : launch_inv_t<0>(a, st);
+}
+
+cudaError_t launch_xform_fft64(const XfftArgs& a, cudaStream_t st) {
+  if (a.rows == 0) return cudaSuccess;
+  // complex elements per thread of a tile: (M or L) x XR / TT
+  const int rows_fft = a.xf.M ? a.xf.M : a.L;
+  const int e = (rows_fft * XR + TT - 1) / TT;
+  if (e <= 4) return launch_xfft_e<4>(a, st);
+  if (e <= 8) return launch_xfft_e<8>(a, st);
+  if (e <= 16) return launch_xfft_e<16>(a, st);
+  return cudaErrorInvalidValue;   // M x XR above 4096 elements: not supported
 }
 
 namespace {
