@@ -237,6 +237,7 @@ TriArgs tri_args_impl(const pd_plan* p, void* data) {
 
 // step (b), with the x-eigentransform around it for 2D / periodic-x problems
 pd_status step_b(pd_plan* p) {
+  PdRange range("pd.step_b");
   void* data = p->spec;
   if (p->xform) {
     CHK(xform_dir(p, true));
@@ -248,11 +249,15 @@ pd_status step_b(pd_plan* p) {
 }
 
 pd_status precond_into(pd_plan* p, const double* r, double* z) {
-  FwdArgs fa = fwd_base_impl(p);
-  fa.mode = FWD_STANDALONE;
-  fa.r64 = r;
-  LK(launch_time_fwd(fa, p->fp64, p->stream));
+  {
+    PdRange range("pd.step_a");
+    FwdArgs fa = fwd_base_impl(p);
+    fa.mode = FWD_STANDALONE;
+    fa.r64 = r;
+    LK(launch_time_fwd(fa, p->fp64, p->stream));
+  }
   CHK(step_b(p));
+  PdRange range("pd.step_c");
   InvArgs ia = inv_base_impl(p);
   ia.mode = INV_OUT64;
   ia.out64 = z;
@@ -649,12 +654,15 @@ pd_status solve_stationary(pd_plan* p, const double* b, double* u, double tol, i
   pd_status st = PD_OK;
   for (;;) {
     CU(cudaMemsetAsync(p->dsc + 1, 0, sizeof(double), p->stream));
-    FwdArgs fa = fwd_base_impl(p);
-    fa.mode = norm_only ? FWD_RESIDUAL_NORM : FWD_RESIDUAL;
-    fa.norm2 = p->dsc + 1;
-    if (p->fp64) { fa.U64 = u; fa.B64 = b; }
-    else { fa.Udf = p->Udf; fa.Bdf = p->Bdf; }
-    LK(launch_time_fwd(fa, p->fp64, p->stream));
+    {
+      PdRange range("pd.residual");
+      FwdArgs fa = fwd_base_impl(p);
+      fa.mode = norm_only ? FWD_RESIDUAL_NORM : FWD_RESIDUAL;
+      fa.norm2 = p->dsc + 1;
+      if (p->fp64) { fa.U64 = u; fa.B64 = b; }
+      else { fa.Udf = p->Udf; fa.Bdf = p->Bdf; }
+      LK(launch_time_fwd(fa, p->fp64, p->stream));
+    }
     CHK(sync_scalars(p, 2));
     const double nb = std::sqrt(p->hsc[0]) / (p->fp64 ? 1.0 : p->s_scale);
     if (nb == 0.0) {
@@ -679,10 +687,13 @@ pd_status solve_stationary(pd_plan* p, const double* b, double* u, double tol, i
       continue;
     }
     CHK(step_b(p));
-    InvArgs ia = inv_base_impl(p);
-    if (p->fp64) { ia.mode = INV_UPDATE64; ia.out64 = u; }
-    else { ia.mode = INV_UPDATE_DF; ia.Udf = p->Udf; ia.igam = p->igam_s; }
-    LK(launch_time_inv(ia, p->fp64, p->stream));
+    {
+      PdRange range("pd.step_c");
+      InvArgs ia = inv_base_impl(p);
+      if (p->fp64) { ia.mode = INV_UPDATE64; ia.out64 = u; }
+      else { ia.mode = INV_UPDATE_DF; ia.Udf = p->Udf; ia.igam = p->igam_s; }
+      LK(launch_time_inv(ia, p->fp64, p->stream));
+    }
     ++it;
     if (prev_rel > 0.0) {
       const double rho = rel / prev_rel;
@@ -815,6 +826,7 @@ pd_status solve_any(pd_plan* p, const double* b, double* u, int mode, double tol
                     int restart, int* iters, double* relres) {
   if (!p || !b || !u) return set_err(p, PD_ERR_ARG, "null argument");
   if (!(tol >= 0.0) || maxit < 0) return set_err(p, PD_ERR_ARG, "tol must be >= 0 and maxit >= 0");
+  PdRange range(mode == PD_GMRES ? "pd.solve.gmres" : "pd.solve.stationary");
   if (mode == PD_STATIONARY) return solve_stationary(p, b, u, tol, maxit, iters, relres);
   if (mode == PD_GMRES) {
     if (restart < 0 || restart > 64) return set_err(p, PD_ERR_ARG, "restart must be in [0, 64]");
@@ -1475,6 +1487,7 @@ pd_status pd_solve_windows(pd_plan* p, const double* u0, const double* f, int nw
 
 pd_status pd_solve_async(pd_plan* p, const double* b, double* u, double tol, int maxit) {
   if (!p || !b || !u) return set_err(p, PD_ERR_ARG, "null argument");
+  PdRange range("pd.solve.enqueue");
   if (!(tol >= 0.0) || maxit < 0) return set_err(p, PD_ERR_ARG, "tol must be >= 0 and maxit >= 0");
   if (!p->fp64) {
     SolveGraph* G = plan_graph(p);
@@ -1524,6 +1537,7 @@ pd_status pd_solve_host(pd_plan* p, const double* b_host, double* u_host, int mo
 pd_status pd_adjoint_solve(pd_plan* p, const double* g, double* lam, int mode, double tol,
                            int maxit, int restart, int* iters, double* relres) {
   if (!p || !g || !lam) return set_err(p, PD_ERR_ARG, "null argument");
+  PdRange range("pd.adjoint_solve");
   if (!p->adj) {
     pd_space sp2 = p->sp;
     sp2.ax = -sp2.ax;  // centred advection: K^T is K with the velocity reversed

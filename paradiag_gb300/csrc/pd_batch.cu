@@ -497,6 +497,7 @@ pd_status pd_batch_build_rhs(pd_batch* b, const double* u0, const double* f, dou
 
 pd_status pd_batch_solve(pd_batch* b, const double* bvec, double* u, double tol, int maxit,
                          int* iters, double* relres_max) {
+  PdRange range("pd.batch_solve");
   if (!b || !bvec || !u) return berr(b, PD_ERR_ARG, "null argument");
   if (!(tol >= 0.0) || maxit < 0) return berr(b, PD_ERR_ARG, "tol must be >= 0 and maxit >= 0");
   const int np = b->np;

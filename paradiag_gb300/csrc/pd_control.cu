@@ -556,6 +556,7 @@ pd_status solve_side(pdc_plan* q, const double* b, double* x, double tol, int ma
 
 pd_status pdc_solve(pdc_plan* q, const double* b, double* x, double tol, int maxit, int restart,
                     int* iters, double* relres) {
+  PdRange range("pd.control_solve");
   return solve_side(q, b, x, tol, maxit, restart, iters, relres, false);
 }
 

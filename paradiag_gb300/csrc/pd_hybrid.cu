@@ -1027,6 +1027,7 @@ pd_status pdh_build_rhs(pdh_plan* q, const double* u0, const double* f, double* 
 
 pd_status pdh_solve(pdh_plan* q, const double* b, double* u, double tol, int max_refine,
                     int* refinements, double* relres) {
+  PdRange range("pd.hybrid_solve");
   if (!q || !b || !u || max_refine < 0 || !(tol >= 0.0)) return PD_ERR_ARG;
   pd_plan* p = q->sp;
   cudaStream_t st = p->stream;

@@ -6,6 +6,20 @@
 #include "../../include/paradiag.h"
 #include "pd_common.cuh"
 
+// NVTX ranges around the solver phases (header-only NVTX 3: a range costs a
+// few instructions unless a profiling tool is attached, which then records
+// it).  Names are prefixed "pd." and follow the paper's steps: "pd.residual"
+// (r = b - A u, eq. 5.1, fused with step (a)), "pd.step_a" (Gamma and the FFT
+// along time), "pd.step_b" (the shifted solves, with the x-eigentransform),
+// "pd.step_c" (inverse FFT, Gamma^{-1}, update), and one range per solve.
+#include <nvtx3/nvToolsExt.h>
+struct PdRange {
+  explicit PdRange(const char* name) { nvtxRangePushA(name); }
+  ~PdRange() { nvtxRangePop(); }
+  PdRange(const PdRange&) = delete;
+  PdRange& operator=(const PdRange&) = delete;
+};
+
 // Double-float constant (value = hi + lo) prepared on the host.
 struct dfc { float hi, lo; };
 static inline dfc dfc_from(double v) {

@@ -750,6 +750,7 @@ pd_status pd1_build_rhs(pd1_plan* q, const double* u0, const double* f, double* 
 
 pd_status pd1_solve(pd1_plan* q, const double* b, double* u, double tol, int max_refine,
                     int* refinements, double* relres) {
+  PdRange range("pd.pd1_solve");
   if (!q || !b || !u || max_refine < 0 || !(tol >= 0.0)) return PD_ERR_ARG;
   pd_plan* p = q->sp;
   cudaStream_t st = p->stream;
