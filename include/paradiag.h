@@ -254,11 +254,28 @@ PD_API pd_status pd_plan_uses_graph(const pd_plan* plan, int* uses);
 
 /* The kernel shapes of this plan: *tile_columns = spatial columns per block of
  * the time kernels, *tri_lanes = lanes per shifted tridiagonal system.  Mixed
- * plans with at least 2^18 unknowns choose both at creation by timing two
- * candidates each on the GPU (8 or 16 complex elements per thread; the
- * default lane count or twice it); others use the default rules.  No paper
+ * plans with at least 2^18 unknowns choose them at creation by timing
+ * candidates on the GPU (8 or 16 complex elements per thread for the time
+ * kernels; for the tridiagonal solves the default lane count, twice it, and
+ * the 16-rows-per-lane form); others use the default rules.  No paper
  * counterpart; introspection. */
 PD_API pd_status pd_plan_tuning(const pd_plan* plan, int* tile_columns, int* tri_lanes);
+
+/* The same shapes with the rows per lane that the tridiagonal solver keeps in
+ * registers (*tri_rows: 32 or 16 on mixed plans, 16 on FP64 plans). */
+PD_API pd_status pd_plan_get_tuning(const pd_plan* plan, int* tile_columns, int* tri_lanes,
+                                    int* tri_rows);
+
+/* Pin the kernel shapes of a mixed plan instead of the autotuner's choice:
+ * tile_columns a power of two with 2 <= tile_columns <= 32 and tile_columns
+ * times the transform length (Nt, or Bluestein's M) at most 8192; tri_rows 32
+ * or 16; tri_lanes a power of two at least the default for that row count
+ * (ceil(n / tri_rows) rounded up to a power of two, n the tridiagonal
+ * length) and at most 256.  Invalid shapes return PD_ERR_ARG and change
+ * nothing; FP64 plans return PD_ERR_UNSUPPORTED.  Any CUDA graph the plan
+ * holds is rebuilt at the next solve.  Every shape computes the same
+ * preconditioner up to FP32 rounding.  No paper counterpart. */
+PD_API pd_status pd_plan_set_tuning(pd_plan* plan, int tile_columns, int tri_lanes, int tri_rows);
 
 /* ---- batched solves: many independent problems of uneven size ----------
  * One problem of a batch (1D, Dirichlet, any scheme; all members of one batch

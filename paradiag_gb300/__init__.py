@@ -70,6 +70,9 @@ _SIGS = {
                                           ctypes.POINTER(ctypes.c_float)]),
     "pd_plan_uses_graph": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int)]),
     "pd_plan_tuning": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]),
+    "pd_plan_get_tuning": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
+                                          ctypes.POINTER(ctypes.c_int)]),
+    "pd_plan_set_tuning": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int, ctypes.c_int]),
     "pd_apply_precond_noalloc": (ctypes.c_int, [ctypes.POINTER(pd_space), ctypes.c_int,
                                                 ctypes.c_double, ctypes.c_double, ctypes.c_int,
                                                 ctypes.c_double, _P, _P, _P,
@@ -214,6 +217,18 @@ def pd_plan_tuning(plan):
     lanes = ctypes.c_int(0)
     st = load().pd_plan_tuning(plan, ctypes.byref(tx), ctypes.byref(lanes))
     return st, tx.value, lanes.value
+
+
+def pd_plan_get_tuning(plan):
+    tx = ctypes.c_int(0)
+    lanes = ctypes.c_int(0)
+    rows = ctypes.c_int(0)
+    st = load().pd_plan_get_tuning(plan, ctypes.byref(tx), ctypes.byref(lanes), ctypes.byref(rows))
+    return st, tx.value, lanes.value, rows.value
+
+
+def pd_plan_set_tuning(plan, tile_columns, tri_lanes, tri_rows):
+    return load().pd_plan_set_tuning(plan, int(tile_columns), int(tri_lanes), int(tri_rows))
 
 
 def pd_batch_uses_graph(batch):
@@ -620,6 +635,18 @@ class Plan:
         st, tx, lanes = pd_plan_tuning(self._h)
         self._check(st, "pd_plan_tuning")
         return tx, lanes
+
+    def get_tuning(self):
+        """(spatial columns per time-kernel block, lanes per tridiagonal system,
+        rows per lane the tridiagonal solver holds in registers)"""
+        st, tx, lanes, rows = pd_plan_get_tuning(self._h)
+        self._check(st, "pd_plan_get_tuning")
+        return tx, lanes, rows
+
+    def set_tuning(self, tile_columns, tri_lanes, tri_rows):
+        """Pin the kernel shapes (see pd_plan_set_tuning)."""
+        self._check(pd_plan_set_tuning(self._h, tile_columns, tri_lanes, tri_rows),
+                    "pd_plan_set_tuning")
 
     def uses_graph(self):
         st, v = pd_plan_uses_graph(self._h)

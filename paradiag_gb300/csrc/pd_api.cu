@@ -232,6 +232,7 @@ TriArgs tri_args_impl(const pd_plan* p, void* data) {
   ta.amax = p->xform_tc ? p->amax + 1 : nullptr;
   ta.amax_reset = p->xform_tc ? p->amax : nullptr;
   ta.cls = p->tri_cls;
+  ta.rows = p->tri_rows;
   return ta;
 }
 
@@ -344,25 +345,32 @@ pd_status autotune_plan(pd_plan* p) {
     }
     p->TX = best_tx;
   }
-  // tridiagonal: the default lane class and one more PCR level (chunks of at
-  // least two rows)
+  // tridiagonal: the default lane class, one more PCR level (chunks of at
+  // least two rows), and the 16-rows-per-lane form at its own default class
   const int c0 = tridiag_class(p->tri_n, false);
-  if (c0 >= 0 && c0 + 1 < TRI_NCLASS && (2 << c0) * 2 <= p->tri_n) {
+  const int c16 = tridiag_class(p->tri_n, false, 16);
+  if (c0 >= 0) {
     void* data = p->xform ? p->spec2 : p->spec;
     const size_t specb = (size_t)p->nh * p->sg.specS * sizeof(float2);
     CU(cudaMemsetAsync(data, 0, specb, p->stream));
+    struct Cand { int cls, rows; };
+    std::vector<Cand> cands = {{c0, 0}};
+    if (c0 + 1 < TRI_NCLASS && (2 << c0) * 2 <= p->tri_n) cands.push_back({c0 + 1, 0});
+    if (c16 >= 0 && c16 > c0) cands.push_back({c16, 16});
     float best = 0.f;
-    int best_c = -1;
-    for (int c : {c0, c0 + 1}) {
-      p->tri_cls = c;
+    Cand pick = cands[0];
+    for (const Cand& c : cands) {
+      p->tri_cls = c.cls;
+      p->tri_rows = c.rows;
       float ms = 0.f;
       CHK(time_ms(p, 3, &ms, [&]() -> pd_status {
         LK(launch_tridiag(tri_args_impl(p, data), false, p->stream));
         return PD_OK;
       }));
-      if (best == 0.f || ms < best) { best = ms; best_c = c; }
+      if (best == 0.f || ms < best) { best = ms; pick = c; }
     }
-    p->tri_cls = best_c == c0 ? -1 : best_c;
+    p->tri_rows = pick.rows;
+    p->tri_cls = (pick.rows == 0 && pick.cls == c0) || (pick.rows == 16 && pick.cls == c16) ? -1 : pick.cls;
   }
   CU(cudaMemsetAsync(p->dflag, 0, sizeof(int), p->stream));
   CU(cudaStreamSynchronize(p->stream));
@@ -917,9 +925,43 @@ pd_status pd_plan_launches(const pd_plan* plan, unsigned long long* count) {
 pd_status pd_plan_tuning(const pd_plan* plan, int* tile_columns, int* tri_lanes) {
   if (!plan || !tile_columns || !tri_lanes) return PD_ERR_ARG;
   *tile_columns = plan->TX;
-  const int c0 = tridiag_class(plan->tri_n, plan->fp64);
+  const int c0 = tridiag_class(plan->tri_n, plan->fp64, plan->fp64 ? 0 : plan->tri_rows);
   const int c = plan->tri_cls > c0 ? plan->tri_cls : c0;
   *tri_lanes = c >= 0 ? 1 << c : 0;
+  return PD_OK;
+}
+
+pd_status pd_plan_get_tuning(const pd_plan* plan, int* tile_columns, int* tri_lanes,
+                             int* tri_rows) {
+  if (!plan || !tri_rows) return PD_ERR_ARG;
+  const pd_status s = pd_plan_tuning(plan, tile_columns, tri_lanes);
+  if (s != PD_OK) return s;
+  *tri_rows = plan->fp64 ? 16 : (plan->tri_rows == 16 ? 16 : 32);
+  return PD_OK;
+}
+
+pd_status pd_plan_set_tuning(pd_plan* plan, int tile_columns, int tri_lanes, int tri_rows) {
+  if (!plan) return PD_ERR_ARG;
+  if (plan->fp64) return set_err(plan, PD_ERR_UNSUPPORTED, "FP64 plans use the default shapes");
+  const int rows_fft = plan->xf.M ? plan->xf.M : plan->nt;
+  if (tile_columns < 2 || tile_columns > 32 || !is_pow2(tile_columns) ||
+      (long long)tile_columns * rows_fft > 8192)
+    return set_err(plan, PD_ERR_ARG, "tile_columns out of range");
+  if (tri_rows != 16 && tri_rows != 32) return set_err(plan, PD_ERR_ARG, "tri_rows must be 16 or 32");
+  const int c0 = tridiag_class(plan->tri_n, false, tri_rows);
+  if (c0 < 0 || tri_lanes < (1 << c0) || tri_lanes > 256 || !is_pow2(tri_lanes))
+    return set_err(plan, PD_ERR_ARG, "tri_lanes out of range");
+  // the plan's stream may still run a solve with the old shapes
+  if (plan->stream) cudaStreamSynchronize(plan->stream);
+  else cudaDeviceSynchronize();
+  if (plan->graph) {
+    destroy_graph(plan->graph);
+    plan->graph = nullptr;
+  }
+  plan->graph_state = 0;
+  plan->TX = tile_columns;
+  plan->tri_rows = tri_rows == 16 ? 16 : 0;
+  plan->tri_cls = ilog2(tri_lanes) == c0 ? -1 : ilog2(tri_lanes);
   return PD_OK;
 }
 

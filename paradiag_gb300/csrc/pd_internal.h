@@ -129,6 +129,9 @@ struct TriArgs {
   // lane class (2^cls lanes per system) chosen by the plan's autotuner, or -1
   // for the default tridiag_class(n); never below the default
   int cls = -1;
+  // FP32 only: rows per lane held in registers, 16 for the short-chunk form
+  // (lane classes then count from tridiag_class(n, false, 16)), 0 for the default
+  int rows = 0;
 };
 
 // Arguments of the dense x-eigentransform (2D, step (a') / (c')): along x, for
@@ -176,7 +179,7 @@ cudaError_t launch_time_inv_batch(const InvArgs* descs, const int2* work, int nb
 // class and launches tiles of tridiag_batch_sb(cls) systems of one problem.
 constexpr int TRI_NMAX = 4096;
 constexpr int TRI_NCLASS = 9;
-int tridiag_class(int n, bool fp64);
+int tridiag_class(int n, bool fp64, int rows = 0);
 int tridiag_batch_sb(int cls, bool fp64);
 cudaError_t launch_tridiag_batch(const TriArgs* descs, const int2* work, int ntiles, int cls,
                                  bool fp64, cudaStream_t st);

@@ -27,6 +27,7 @@ struct pd_plan {
   unsigned* amax = nullptr;           // max |input| of the forward / inverse transform
   int J = 1, tri_n = 0, tri_stride = 1;
   int tri_cls = -1;                   // tridiagonal lane class (autotuned, -1: default)
+  int tri_rows = 0;                   // rows per lane in registers (autotuned, 0: default)
   int tuned = 0;                      // 1 once the plan-time autotuner has run
   double tri_cl = 0, tri_cd = 0, tri_cu = 0;
   // device tables

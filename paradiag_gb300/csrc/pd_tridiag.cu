@@ -32,7 +32,10 @@
 
 namespace {
 
-// rows per chunk held in registers (compile-time bound of the unrolled sweeps)
+// rows per chunk held in registers (compile-time bound of the unrolled sweeps):
+// 32 (FP32) or 16 (FP64) by default; FP32 plans may also take the 16-row form
+// (half the registers, twice the lanes per system), which the plan-time
+// autotuner weighs against the default
 template <typename R> struct ChunkRows;
 template <> struct ChunkRows<float> { static constexpr int MM = 32; };
 template <> struct ChunkRows<double> { static constexpr int MM = 16; };
@@ -183,10 +186,9 @@ PD_D void ld_pair<double2>(const double2* p, double2& x, double2& y) {
 
 // Solve the SB systems of one tile: q0 + sb for sb < SB.  Block threads:
 // sb = threadIdx.x / L, lane G = threadIdx.x % L.
-template <typename R, int L>
+template <typename R, int L, int MM>
 PD_D void solve_tile(const TriArgs& a, long long q0, unsigned char* smraw) {
   using C = cplx_t<R>;
-  constexpr int MM = ChunkRows<R>::MM;
   constexpr int SB = tri_sb(L);
   TabRow<C>* tab = reinterpret_cast<TabRow<C>*>(smraw);                   // [SB][MM-2]
   SysInfo<C>* sinfo = reinterpret_cast<SysInfo<C>*>(tab + SB * (MM - 2));  // [SB]
@@ -385,58 +387,58 @@ PD_D void solve_tile(const TriArgs& a, long long q0, unsigned char* smraw) {
 
 // One tile of SB systems per block.  Batch: work[block] = (problem, tile)
 // selects the descriptor.
-template <typename R, int L, bool BATCH>
-__global__ void __launch_bounds__(tri_threads(L), L >= 64 ? 1 : (sizeof(R) == 4 ? 4 : 2))
+template <typename R, int L, bool BATCH, int MM>
+__global__ void __launch_bounds__(tri_threads(L),
+                                  L >= 64 ? 1 : (sizeof(R) == 4 ? (MM <= 16 ? 5 : 4) : 2))
     k_tridiag(TriArgs a1, const TriArgs* __restrict__ descs, const int2* __restrict__ work) {
   extern __shared__ __align__(16) unsigned char smraw[];
   const TriArgs& a = BATCH ? descs[work[blockIdx.x].x] : a1;
   const long long tile = BATCH ? work[blockIdx.x].y : (long long)blockIdx.x;
-  solve_tile<R, L>(a, tile * tri_sb(L), smraw);
+  solve_tile<R, L, MM>(a, tile * tri_sb(L), smraw);
 }
 
-template <typename R, int L>
+template <typename R, int L, int MM>
 size_t tile_smem() {
   using C = cplx_t<R>;
-  constexpr int MM = ChunkRows<R>::MM;
   constexpr int SB = tri_sb(L);
   size_t b = (size_t)SB * (MM - 2) * sizeof(TabRow<C>) + (size_t)SB * sizeof(SysInfo<C>);
   if (L > 32) b += (size_t)4 * SB * 2 * L * sizeof(C);
   return b;
 }
 
-template <typename R, int L>
+template <typename R, int L, int MM>
 cudaError_t launch_l(const TriArgs& a1, const TriArgs* descs, const int2* work, long long ntiles,
                      cudaStream_t st) {
   if (ntiles == 0) return cudaSuccess;
-  const size_t smem = tile_smem<R, L>();
-  auto kern = descs ? k_tridiag<R, L, true> : k_tridiag<R, L, false>;
+  const size_t smem = tile_smem<R, L, MM>();
+  auto kern = descs ? k_tridiag<R, L, true, MM> : k_tridiag<R, L, false, MM>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   kern<<<(unsigned)ntiles, tri_threads(L), smem, st>>>(a1, descs, work);
   return cudaGetLastError();
 }
 
-template <typename R>
+template <typename R, int MM = ChunkRows<R>::MM>
 cudaError_t launch_cls(int cls, const TriArgs& a1, const TriArgs* descs, const int2* work,
                        long long ntiles, cudaStream_t st) {
   switch (cls) {
-    case 0: return launch_l<R, 1>(a1, descs, work, ntiles, st);
-    case 1: return launch_l<R, 2>(a1, descs, work, ntiles, st);
-    case 2: return launch_l<R, 4>(a1, descs, work, ntiles, st);
-    case 3: return launch_l<R, 8>(a1, descs, work, ntiles, st);
-    case 4: return launch_l<R, 16>(a1, descs, work, ntiles, st);
-    case 5: return launch_l<R, 32>(a1, descs, work, ntiles, st);
-    case 6: return launch_l<R, 64>(a1, descs, work, ntiles, st);
-    case 7: return launch_l<R, 128>(a1, descs, work, ntiles, st);
-    case 8: return launch_l<R, 256>(a1, descs, work, ntiles, st);
+    case 0: return launch_l<R, 1, MM>(a1, descs, work, ntiles, st);
+    case 1: return launch_l<R, 2, MM>(a1, descs, work, ntiles, st);
+    case 2: return launch_l<R, 4, MM>(a1, descs, work, ntiles, st);
+    case 3: return launch_l<R, 8, MM>(a1, descs, work, ntiles, st);
+    case 4: return launch_l<R, 16, MM>(a1, descs, work, ntiles, st);
+    case 5: return launch_l<R, 32, MM>(a1, descs, work, ntiles, st);
+    case 6: return launch_l<R, 64, MM>(a1, descs, work, ntiles, st);
+    case 7: return launch_l<R, 128, MM>(a1, descs, work, ntiles, st);
+    case 8: return launch_l<R, 256, MM>(a1, descs, work, ntiles, st);
   }
   return cudaErrorInvalidValue;
 }
 
 }  // namespace
 
-int tridiag_class(int n, bool fp64) {
-  const int mm = fp64 ? ChunkRows<double>::MM : ChunkRows<float>::MM;
+int tridiag_class(int n, bool fp64, int rows) {
+  const int mm = rows > 0 ? rows : (fp64 ? ChunkRows<double>::MM : ChunkRows<float>::MM);
   if (n < 1 || n > TRI_NMAX) return -1;
   int cls = 0;
   while ((1 << cls) * mm < n) ++cls;
@@ -449,13 +451,15 @@ int tridiag_batch_sb(int cls, bool fp64) {
 }
 
 cudaError_t launch_tridiag(const TriArgs& a, bool fp64, cudaStream_t st) {
-  const int c0 = tridiag_class(a.n, fp64);
+  const bool short_rows = !fp64 && a.rows == 16;       // the 16-row FP32 form
+  const int c0 = tridiag_class(a.n, fp64, short_rows ? 16 : 0);
   if (c0 < 0) return cudaErrorInvalidValue;
   const int cls = a.cls > c0 && a.cls < TRI_NCLASS ? a.cls : c0;
   const long long total = (long long)a.nh * a.J;
   const long long ntiles = (total + tri_sb(1 << cls) - 1) / tri_sb(1 << cls);
-  return fp64 ? launch_cls<double>(cls, a, nullptr, nullptr, ntiles, st)
-              : launch_cls<float>(cls, a, nullptr, nullptr, ntiles, st);
+  if (fp64) return launch_cls<double>(cls, a, nullptr, nullptr, ntiles, st);
+  if (short_rows) return launch_cls<float, 16>(cls, a, nullptr, nullptr, ntiles, st);
+  return launch_cls<float>(cls, a, nullptr, nullptr, ntiles, st);
 }
 
 cudaError_t launch_tridiag_batch(const TriArgs* descs, const int2* work, int ntiles, int cls,

@@ -10,7 +10,7 @@ import numpy as np
 import pytest
 
 import workloads as W
-from helpers import dev, host, lib_ready, make_plan, rel2
+from helpers import dev, host, lib_ready, make_plan, rel2, relerr
 from oracle import operators as O
 from oracle import stepping as S
 
@@ -153,15 +153,17 @@ def test_plan_autotuner_choices(pd):
     w = W.ade2d(nx=63, ny=63, nt=128, scheme=W.CN, alpha=1e-3)
     pb = w.problem
     plan = make_plan(pb, pd.PD_MIXED)
-    tx, lanes = plan.tuning()
+    tx, lanes, tri_rows = plan.get_tuning()
+    assert (tx, lanes) == plan.tuning()
     rows = pb.nt
     assert tx in (max(2, min(32, 4096 // rows)), max(2, min(32, 8192 // rows)))
     default_lanes = 1 << int(np.ceil(np.log2(-(-pb.space.ny // 32))))
-    assert lanes in (default_lanes, 2 * default_lanes)
+    lanes16 = 1 << int(np.ceil(np.log2(-(-pb.space.ny // 16))))
+    assert (lanes, tri_rows) in ((default_lanes, 32), (2 * default_lanes, 32), (lanes16, 16))
     b = _rhs(w)
     uref = S.solve_sequential(pb, b)
     u, it, rel = plan.solve(dev(b), tol=1e-12, maxit=30)
-    assert rel2(host(u), uref) <= 1e-10, (rel2(host(u), uref), it, tx, lanes)
+    assert rel2(host(u), uref) <= 1e-10, (rel2(host(u), uref), it, tx, lanes, tri_rows)
     plan.close()
     # FP64 plans keep the default rules (chunks of at most 16 rows)
     plan64 = make_plan(pb, pd.PD_FP64)
@@ -190,4 +192,58 @@ def test_async_solves_match_synchronous(pd):
     assert it == ref[-1][1] and abs(rel - ref[-1][2]) <= 1e-12 * ref[-1][2]
     for u, (r, _, _) in zip(us, ref):
         assert np.array_equal(host(u), r)
+    plan.close()
+
+
+@pytest.mark.parametrize("ny", [63, 255])
+def test_every_pinned_shape_matches_oracle(pd, ny):
+    """Every kernel shape a mixed plan may take (the autotuner's candidates:
+    time-kernel tiles of both widths, the default and doubled lane counts of
+    the 32-row tridiagonal form, the 16-row form) gives the oracle's
+    preconditioner within the parity bound and a solve to the oracle's
+    solution; shapes are pinned with pd_plan_set_tuning, which also rebuilds
+    the solver's CUDA graph."""
+    from oracle import closed_forms as CF
+    from oracle import operators as O
+    from oracle import paradiag as PD
+    w = W.ade2d(nx=16, ny=ny, nt=32, scheme=W.CN, alpha=1e-3, nu=1e-2)
+    pb = w.problem
+    sp = pb.space
+    plan = make_plan(pb, pd.PD_MIXED)
+    r = W.uniform(W.SEED_BASE + 70, pb.unknowns, -1.0, 1.0).reshape(pb.nt, -1)
+    zref = PD.precond_apply(pb, r)
+    # kappa of the shifted systems: the unitary DFT along the periodic x splits
+    # lambda_1 I + lambda_2 K into the ny x ny blocks lambda_1 I + lambda_2
+    # (mu_j I + K_y), so its singular values are those of the blocks together
+    Kx = O.stencil_1d(sp.nx, sp.hx, sp.nu, sp.ax, sp.bc_x).toarray()
+    Ky = O.stencil_1d(sp.ny, sp.hy, sp.nu, sp.ay, sp.bc_y).toarray()
+    x = np.arange(sp.nx)
+    mu = np.array([Kx[0] @ np.exp(2j * np.pi * j * x / sp.nx) for j in range(sp.nx)])
+    l1, l2 = CF.lemma1_eigenvalues(pb)
+    I = np.eye(sp.ny)
+    blocks = np.stack([l1[k] * I + l2[k] * (m * I + Ky)
+                       for k in range(pb.nt // 2 + 1) for m in mu])
+    sv = np.linalg.svd(blocks, compute_uv=False)
+    kap = sv.max() / sv.min()
+    tol_p = 2.0 * 2.0 ** -24 * kap * (1.0 + np.log2(pb.nt)) / pb.alpha
+    b = _rhs(w)
+    uref = S.solve_sequential(pb, b)
+    shapes = []
+    for tx in (16, 32):
+        for rows in (32, 16):
+            base = 1 << int(np.ceil(np.log2(-(-ny // rows))))
+            for lanes in (base, 2 * base):
+                shapes.append((tx, lanes, rows))
+    with pytest.raises(pd.PDError):
+        plan.set_tuning(64, 2, 32)             # tile too wide
+    with pytest.raises(pd.PDError):
+        plan.set_tuning(32, 1, 16)             # fewer lanes than the 16-row form needs
+    for tx, lanes, rows in shapes:
+        plan.set_tuning(tx, lanes, rows)
+        assert plan.get_tuning() == (tx, lanes, rows)
+        z = host(plan.apply_precond(dev(r)))
+        err = relerr(z, zref)
+        assert err <= tol_p, (tx, lanes, rows, err, tol_p)
+        u, it, rel = plan.solve(dev(b), tol=1e-12, maxit=30)
+        assert rel2(host(u), uref) <= 1e-10, (tx, lanes, rows, rel2(host(u), uref))
     plan.close()
