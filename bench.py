@@ -331,6 +331,21 @@ def batched_leg(pd, torch, dev, args):
         byts += n * (32.0 + it * (32.0 + 32.0 * h) + 16.0 + 16.0)
     hbm, _, src = peaks()
     gbs = byts / (ms / 1e3) / 1e9
+    # per-kernel times of one sweep (persistent launches over all members) and
+    # their algorithmic bytes: forward 16 + 8h, tridiagonal 16h, inverse 8h + 16
+    kms = batch.profile_sweep(b, torch.zeros_like(b), reps=5)
+    kb = [0.0, 0.0, 0.0]
+    for w in wls:
+        n = w.problem.nt * w.problem.space.nx
+        h = (w.problem.nt // 2 + 1) / w.problem.nt
+        kb[0] += n * (16.0 + 8.0 * h)
+        kb[1] += n * 16.0 * h
+        kb[2] += n * (8.0 * h + 16.0)
+    kroof = {}
+    for name, t, by in zip(("time_fwd", "tridiag", "time_inv"), kms, kb):
+        g = by / (t / 1e3) / 1e9
+        kroof[name] = {"ms": t, "bound": "hbm", "achieved": g, "peak": hbm, "unit": "GB/s",
+                       "frac": g / hbm, "algorithmic_bytes": by}
     out = {"workload": "64 x 1D advection-diffusion, nx ~ U{63..1023}, Nt ~ U{32..1024} "
                        "(Bluestein for non-powers of two), BE, alpha = 1e-2",
            "unknowns": int(batch.total), "ms_per_step": ms,
@@ -340,6 +355,7 @@ def batched_leg(pd, torch, dev, args):
                         "frac": gbs / hbm, "traffic": None, "algorithmic_bytes": byts,
                         "scope": "the whole solve (every kernel) over its CUDA-event time",
                         "peak_source": f"{src} (MEASURED_PEAKS.json)"},
+           "kernel_roofline": kroof, "autotuned": batch.tuned(),
            "gpu_launches": (batch.launches() - l0) // k}
     batch.close()
     return out

@@ -322,6 +322,22 @@ PD_API pd_status pd_batch_launches(const pd_batch* batch, unsigned long long* co
 PD_API pd_status pd_batch_uses_graph(const pd_batch* batch, int* uses);
 PD_API const char* pd_batch_last_error(const pd_batch* batch);
 
+/* *tuned = 1 when the batch's kernel shapes were chosen by timing at
+ * creation (mixed batches of at least 2^18 unknowns: per group of members
+ * with one transform length, the time-kernel tile width at the default or at
+ * half of it; per group with one default tridiagonal lane class, that lane
+ * count or twice it), else 0.  No paper counterpart; introspection. */
+PD_API pd_status pd_batch_tuned(const pd_batch* batch, int* tuned);
+
+/* Per-kernel timing of one sweep of the batched iteration on the batch's
+ * stream (CUDA events, `reps` launches each after one warm-up): ms[0] the
+ * forward time kernels (residual, Gamma, FFT) over all members, ms[1] the
+ * tridiagonal solves, ms[2] the inverse time kernels with the update.  b and
+ * u as for pd_batch_solve; u is overwritten by iterates that carry no
+ * meaning.  No paper counterpart; measurement. */
+PD_API pd_status pd_batch_profile_sweep(pd_batch* batch, const double* b, double* u, int reps,
+                                        float* ms);
+
 /* Size of the device array used by pd_apply_precond_noalloc (8 MiB). */
 #define PD_NOALLOC_SCRATCH_BYTES (8u << 20)
 

@@ -86,6 +86,8 @@ _SIGS = {
     "pd_batch_launches": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_ulonglong)]),
     "pd_batch_uses_graph": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int)]),
     "pd_batch_relres": (ctypes.c_int, [_P, _D]),
+    "pd_batch_tuned": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int)]),
+    "pd_batch_profile_sweep": (ctypes.c_int, [_P, _P, _P, ctypes.c_int, ctypes.POINTER(ctypes.c_float)]),
     "pd_batch_last_error": (ctypes.c_char_p, [_P]),
     "pd1_plan_create": (ctypes.c_int, [ctypes.POINTER(pd_space), ctypes.c_int, ctypes.c_double,
                                        ctypes.c_double, ctypes.c_int, ctypes.c_int, ctypes.c_int,
@@ -288,6 +290,18 @@ def pd_batch_relres(batch, nprob):
     arr = (ctypes.c_double * nprob)()
     st = load().pd_batch_relres(batch, arr)
     return st, list(arr)
+
+
+def pd_batch_tuned(batch):
+    v = ctypes.c_int(0)
+    st = load().pd_batch_tuned(batch, ctypes.byref(v))
+    return st, v.value
+
+
+def pd_batch_profile_sweep(batch, b, u, reps):
+    ms = (ctypes.c_float * 3)()
+    st = load().pd_batch_profile_sweep(batch, b, u, int(reps), ms)
+    return st, list(ms)
 
 
 def pd_batch_last_error(batch):
@@ -1171,6 +1185,21 @@ class Batch:
     def relres(self):
         """Relative residual of every problem at the last check of solve()."""
         return pd_batch_relres(self._h, self.np)[1]
+
+    def tuned(self):
+        """True when the kernel shapes were chosen by timing at creation."""
+        st, v = pd_batch_tuned(self._h)
+        if st != PD_OK:
+            raise PDError(st, "pd_batch_tuned")
+        return bool(v)
+
+    def profile_sweep(self, b, u, reps=5):
+        """[forward time kernels, tridiagonal solves, inverse time kernels] in ms
+        per sweep (u is overwritten)."""
+        st, ms = pd_batch_profile_sweep(self._h, _ptr(b), _ptr(u), reps)
+        if st != PD_OK:
+            raise PDError(st, pd_batch_last_error(self._h))
+        return ms
 
 
 def _make_pdsolve():

@@ -14,6 +14,8 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <functional>
+#include <map>
 #include <new>
 #include <vector>
 
@@ -38,13 +40,22 @@ struct pd_batch {
   FwdArgs* d_fwd = nullptr;
   InvArgs* d_inv = nullptr;
   TriArgs* d_tri = nullptr;
-  int2* d_work_time = nullptr;
-  int nblk_time = 0;
-  size_t smem_time = 0;
-  size_t smem_inv = 0;
-  int ept = 4;
+  // time-kernel work, one persistent launch per class of tile footprint
+  // (complex elements per thread: 4, 8 or 16)
+  struct TimeClass {
+    int ept = 0;
+    size_t smem_fwd = 0, smem_inv = 0;
+    int nwork = 0;
+    int2* d_work = nullptr;
+  };
+  static constexpr int NTC = 3;
+  TimeClass tcls[NTC];
   int2* d_work_tri[TRI_NCLASS] = {};
   int ntiles_tri[TRI_NCLASS] = {};
+  // work counters of the persistent tridiagonal launches, one per lane class
+  static constexpr int NCTR = TRI_NCLASS;
+  int* d_ctr = nullptr;
+  int tuned = 0;                // 1 once the batch autotuner has run
   double* d_norms = nullptr;    // [0, np): ||b_i||^2, [np, 2np): ||r_i||^2
   double* h_norms = nullptr;    // pinned, 2np doubles + flag
   int* d_flag = nullptr;
@@ -71,6 +82,7 @@ struct BatchGraph {
   BLoop* hst = nullptr;
   double* d_rel = nullptr;   // per-problem relative residual of the last check
   int update_kernels = 0;
+  int fwd_kernels = 0;
 };
 void destroy_batch_graph(BatchGraph* G) {
   if (!G) return;
@@ -149,6 +161,11 @@ pd_status bcuda(pd_batch* b, cudaError_t e, const char* what) {
     cudaError_t e_ = (call);                               \
     if (e_ != cudaSuccess) return bcuda(b, e_, #call);     \
   } while (0)
+#define BCHK(call)                                         \
+  do {                                                     \
+    pd_status s_ = (call);                                 \
+    if (s_ != PD_OK) return s_;                            \
+  } while (0)
 #define BLK(call)                                          \
   do {                                                     \
     cudaError_t e_ = (call);                               \
@@ -173,14 +190,238 @@ void free_batch(pd_batch* b) {
   for (pd_plan* p : b->plans)
     if (p) pd_plan_destroy(p);
   void* ptrs[] = {b->d_off, b->d_bscale, b->d_one, b->Udf,     b->Bdf,
-                  b->d_fwd, b->d_inv,    b->d_tri, b->d_work_time, b->d_norms, b->d_flag};
+                  b->d_fwd, b->d_inv,    b->d_tri, b->d_norms, b->d_flag, b->d_ctr};
   for (void* q : ptrs)
     if (q) cudaFree(q);
+  for (auto& c : b->tcls)
+    if (c.d_work) cudaFree(c.d_work);
   for (int w = 0; w < TRI_NCLASS; ++w)
     if (b->d_work_tri[w]) cudaFree(b->d_work_tri[w]);
   if (b->h_norms) cudaFreeHost(b->h_norms);
   if (b->graph) destroy_batch_graph(b->graph);
   delete b;
+}
+
+// time-kernel class of a tile footprint (complex elements per thread)
+int time_class(int ept) { return ept <= 4 ? 0 : ept <= 8 ? 1 : 2; }
+int class_ept(int c) { return c == 0 ? 4 : c == 1 ? 8 : 16; }
+
+// Descriptors and work tables from the members' current kernel shapes (tile
+// width p->TX, tridiagonal lane class p->tri_cls): time-kernel tiles grouped
+// by footprint class, tridiagonal tiles by lane class; uploaded to the device
+// (replacing any earlier tables).  Per-call fields of the descriptors (state
+// pointers, norms, flag) are filled by set_call_descs.
+pd_status batch_tables(pd_batch* b) {
+  const int np = b->np;
+  const bool fp64 = b->fp64;
+  std::vector<int2> wt[pd_batch::NTC];
+  std::vector<int2> wtri[TRI_NCLASS];
+  for (auto& c : b->tcls) {
+    c.smem_fwd = c.smem_inv = 0;
+    c.nwork = 0;
+  }
+  for (int i = 0; i < np; ++i) {
+    pd_plan* p = b->plans[i];
+    b->h_fwd[i] = plan_fwd_args(p);
+    b->h_fwd[i].mode = FWD_RESIDUAL;
+    b->h_inv[i] = plan_inv_args(p);
+    b->h_tri[i] = plan_tri_args(p, p->spec);
+    const int rows = p->xf.M ? p->xf.M : p->nt;
+    const int c = time_class(time_tile_ept(rows, p->TX));
+    pd_batch::TimeClass& tc = b->tcls[c];
+    tc.ept = class_ept(c);
+    const int tiles = ceil_div(p->S, p->TX);
+    for (int t = 0; t < tiles; ++t) wt[c].push_back(make_int2(i, t));
+    tc.smem_fwd = std::max(tc.smem_fwd, time_inv_smem(p->nt, rows, p->TX, fp64, false));
+    tc.smem_inv = std::max(tc.smem_inv, time_inv_smem(p->nt, rows, p->TX, fp64, true));
+    const int c0 = tridiag_class(p->tri_n, fp64);
+    const int wc = p->tri_cls > c0 ? p->tri_cls : c0;
+    const int SB = tridiag_batch_sb(wc, fp64);
+    const long long systems = (long long)p->nh * p->J;
+    const int ttiles = (int)((systems + SB - 1) / SB);
+    for (int t = 0; t < ttiles; ++t) wtri[wc].push_back(make_int2(i, t));
+  }
+  // the costliest tiles first (Bluestein members, then longer transforms), so
+  // the dynamically assigned tail of a launch is made of short tiles
+  auto cost = [&](const int2& w) {
+    const pd_plan* p = b->plans[w.x];
+    return (p->xf.M ? 2LL : 1LL) * (p->xf.M ? p->xf.M : p->nt);
+  };
+  for (auto& v : wt)
+    std::stable_sort(v.begin(), v.end(),
+                     [&](const int2& x, const int2& y) { return cost(x) > cost(y); });
+  for (int c = 0; c < pd_batch::NTC; ++c) {
+    pd_batch::TimeClass& tc = b->tcls[c];
+    if (tc.d_work) { cudaFree(tc.d_work); tc.d_work = nullptr; }
+    tc.nwork = (int)wt[c].size();
+    if (tc.nwork == 0) continue;
+    BCU(cudaMalloc(&tc.d_work, wt[c].size() * sizeof(int2)));
+    BCU(cudaMemcpy(tc.d_work, wt[c].data(), wt[c].size() * sizeof(int2), cudaMemcpyHostToDevice));
+  }
+  for (int w = 0; w < TRI_NCLASS; ++w) {
+    if (b->d_work_tri[w]) { cudaFree(b->d_work_tri[w]); b->d_work_tri[w] = nullptr; }
+    b->ntiles_tri[w] = (int)wtri[w].size();
+    if (wtri[w].empty()) continue;
+    BCU(cudaMalloc(&b->d_work_tri[w], wtri[w].size() * sizeof(int2)));
+    BCU(cudaMemcpy(b->d_work_tri[w], wtri[w].data(), wtri[w].size() * sizeof(int2),
+                   cudaMemcpyHostToDevice));
+  }
+  return PD_OK;
+}
+
+// per-call descriptor fields: the state the kernels read and write (FP64:
+// the caller's arrays; mixed: the batch's double-float state), the norm
+// accumulators and the flag; uploaded on the batch's stream
+pd_status set_call_descs(pd_batch* b, const double* bvec, double* u) {
+  const int np = b->np;
+  cudaStream_t st = b->stream;
+  for (int i = 0; i < np; ++i) {
+    FwdArgs& fa = b->h_fwd[i];
+    InvArgs& ia = b->h_inv[i];
+    fa.norm2 = b->d_norms + np + i;
+    if (b->fp64) {
+      fa.U64 = u + b->off[i];
+      fa.B64 = bvec + b->off[i];
+      ia.mode = INV_UPDATE64;
+      ia.out64 = u + b->off[i];
+    } else {
+      fa.Udf = b->Udf + b->off[i];
+      fa.Bdf = b->Bdf + b->off[i];
+      ia.mode = INV_UPDATE_DF;
+      ia.Udf = b->Udf + b->off[i];
+      ia.igam = b->plans[i]->igam_s;
+    }
+    ia.flag = b->d_flag;
+    b->h_tri[i].flag = b->d_flag;
+  }
+  BCU(cudaMemcpyAsync(b->d_fwd, b->h_fwd.data(), np * sizeof(FwdArgs), cudaMemcpyHostToDevice, st));
+  BCU(cudaMemcpyAsync(b->d_inv, b->h_inv.data(), np * sizeof(InvArgs), cudaMemcpyHostToDevice, st));
+  BCU(cudaMemcpyAsync(b->d_tri, b->h_tri.data(), np * sizeof(TriArgs), cudaMemcpyHostToDevice, st));
+  return PD_OK;
+}
+
+// the three kernel types of one sweep over all classes (each kernel launch
+// counted; the tridiagonal work counters are zeroed first)
+cudaError_t launch_fwd_all(pd_batch* b, cudaStream_t st, int* nk) {
+  cudaError_t e = cudaSuccess;
+  for (int c = 0; c < pd_batch::NTC && e == cudaSuccess; ++c) {
+    const auto& tc = b->tcls[c];
+    if (tc.nwork == 0) continue;
+    e = launch_time_fwd_batch(b->d_fwd, tc.d_work, tc.nwork, b->band, tc.smem_fwd, tc.ept,
+                              b->fp64, st);
+    ++*nk;
+  }
+  return e;
+}
+cudaError_t launch_tri_all(pd_batch* b, cudaStream_t st, int* nk) {
+  cudaError_t e = cudaMemsetAsync(b->d_ctr, 0, TRI_NCLASS * sizeof(int), st);
+  for (int w = 0; w < TRI_NCLASS && e == cudaSuccess; ++w) {
+    if (b->ntiles_tri[w] == 0) continue;
+    e = launch_tridiag_batch(b->d_tri, b->d_work_tri[w], b->ntiles_tri[w], w, b->fp64,
+                             b->d_ctr + w, st);
+    ++*nk;
+  }
+  return e;
+}
+cudaError_t launch_inv_all(pd_batch* b, cudaStream_t st, int* nk) {
+  cudaError_t e = cudaSuccess;
+  for (int c = 0; c < pd_batch::NTC && e == cudaSuccess; ++c) {
+    const auto& tc = b->tcls[c];
+    if (tc.nwork == 0) continue;
+    e = launch_time_inv_batch(b->d_inv, tc.d_work, tc.nwork, tc.smem_inv, tc.ept, b->fp64, st);
+    ++*nk;
+  }
+  return e;
+}
+
+// milliseconds per call of `body` on the batch's stream (one warm-up call,
+// then `reps` timed with CUDA events)
+pd_status batch_time_ms(pd_batch* b, int reps, float* ms, const std::function<cudaError_t()>& body) {
+  cudaEvent_t e0, e1;
+  BCU(cudaEventCreate(&e0));
+  BCU(cudaEventCreate(&e1));
+  cudaError_t e = body();
+  if (e == cudaSuccess) {
+    cudaEventRecord(e0, b->stream);
+    for (int r = 0; r < reps && e == cudaSuccess; ++r) e = body();
+    cudaEventRecord(e1, b->stream);
+    cudaEventSynchronize(e1);
+    cudaEventElapsedTime(ms, e0, e1);
+    *ms /= (float)reps;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (e != cudaSuccess) return bcuda(b, e, "batch autotuner launch");
+  return PD_OK;
+}
+
+// The batch autotuner (mixed batches): on the batch's own zeroed state, for
+// every group of members sharing a transform length it times the forward and
+// inverse time kernels of the whole sweep with the group's tile width at the
+// default (8192 reals per tile) and at half of it, and for every group sharing
+// a default tridiagonal lane class the tridiagonal launches with the default
+// lane count and with twice it; each group keeps its faster choice.  Every
+// candidate computes the same preconditioner up to FP32 rounding.
+pd_status batch_autotune(pd_batch* b) {
+  if (b->fp64) return PD_OK;
+  cudaStream_t st = b->stream;
+  BCU(cudaMemsetAsync(b->Udf, 0, b->total * sizeof(float2), st));
+  BCU(cudaMemsetAsync(b->Bdf, 0, b->total * sizeof(float2), st));
+  BCU(cudaMemsetAsync(b->d_norms, 0, 2 * b->np * sizeof(double), st));
+  BCU(cudaMemsetAsync(b->d_flag, 0, sizeof(int), st));
+  const unsigned long long launches = b->launches;
+  int nk = 0;
+  std::map<int, std::vector<int>> by_rows, by_cls;
+  for (int i = 0; i < b->np; ++i) {
+    pd_plan* p = b->plans[i];
+    by_rows[p->xf.M ? p->xf.M : p->nt].push_back(i);
+    by_cls[tridiag_class(p->tri_n, false)].push_back(i);
+  }
+  for (const auto& g : by_rows) {
+    const int rows = g.first;
+    const int tx_a = std::max(2, std::min(32, 8192 / rows)), tx_b = std::max(2, std::min(32, 4096 / rows));
+    if (tx_a == tx_b) continue;
+    float best = 0.f;
+    int best_tx = tx_a;
+    for (int tx : {tx_a, tx_b}) {
+      for (int i : g.second) b->plans[i]->TX = tx;
+      BCHK(batch_tables(b));
+      BCHK(set_call_descs(b, nullptr, nullptr));
+      float ms = 0.f;
+      BCHK(batch_time_ms(b, 3, &ms, [&]() -> cudaError_t {
+        cudaError_t e = launch_fwd_all(b, st, &nk);
+        return e == cudaSuccess ? launch_inv_all(b, st, &nk) : e;
+      }));
+      if (best == 0.f || ms < best) { best = ms; best_tx = tx; }
+    }
+    for (int i : g.second) b->plans[i]->TX = best_tx;
+  }
+  BCHK(batch_tables(b));
+  BCHK(set_call_descs(b, nullptr, nullptr));
+  for (const auto& g : by_cls) {
+    const int c0 = g.first;
+    if (c0 < 0 || c0 + 1 >= TRI_NCLASS) continue;
+    bool ok = true;
+    for (int i : g.second) ok = ok && (2 << c0) * 2 <= b->plans[i]->tri_n;
+    if (!ok) continue;
+    float best = 0.f;
+    int best_c = c0;
+    for (int c : {c0, c0 + 1}) {
+      for (int i : g.second) b->plans[i]->tri_cls = c;
+      BCHK(batch_tables(b));
+      BCHK(set_call_descs(b, nullptr, nullptr));
+      float ms = 0.f;
+      BCHK(batch_time_ms(b, 3, &ms, [&]() -> cudaError_t { return launch_tri_all(b, st, &nk); }));
+      if (best == 0.f || ms < best) { best = ms; best_c = c; }
+    }
+    for (int i : g.second) b->plans[i]->tri_cls = best_c == c0 ? -1 : best_c;
+  }
+  BCHK(batch_tables(b));
+  BCU(cudaMemsetAsync(b->d_flag, 0, sizeof(int), st));
+  BCU(cudaStreamSynchronize(st));
+  b->launches = launches;
+  b->tuned = 1;
+  return PD_OK;
 }
 
 enum { BS_RUNNING = 0, BS_CONVERGED, BS_MAXIT, BS_NONFINITE };
@@ -281,8 +522,9 @@ pd_status build_batch_graph(pd_batch* b, BatchGraph* G) {
   BCU(cudaGraphConditionalHandleCreate(&hif, body, 0u, cudaGraphCondAssignDefault));
   const int np = b->np;
   BCU(cudaStreamBeginCaptureToGraph(G->cs, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
-  cudaError_t e = launch_time_fwd_batch(b->d_fwd, b->d_work_time, b->nblk_time, b->band,
-                                        b->smem_time, b->ept, false, G->cs);
+  int nf = 0;
+  cudaError_t e = launch_fwd_all(b, G->cs, &nf);
+  G->fwd_kernels = nf;
   if (e == cudaSuccess) {
     k_batch_check<<<1, TB, 0, G->cs>>>(G->dst, b->d_norms, np, b->d_flag, G->d_rel, hw, hif);
     e = cudaGetLastError();
@@ -305,17 +547,8 @@ pd_status build_batch_graph(pd_batch* b, BatchGraph* G) {
   cudaGraph_t ubody = ip.conditional.phGraph_out[0];
   BCU(cudaStreamBeginCaptureToGraph(G->cs, ubody, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
   int nk = 0;
-  e = cudaSuccess;
-  for (int w = 0; w < TRI_NCLASS && e == cudaSuccess; ++w)
-    if (b->ntiles_tri[w] > 0) {
-      e = launch_tridiag_batch(b->d_tri, b->d_work_tri[w], b->ntiles_tri[w], w, false, G->cs);
-      ++nk;
-    }
-  if (e == cudaSuccess) {
-    e = launch_time_inv_batch(b->d_inv, b->d_work_time, b->nblk_time, b->smem_inv, b->ept, false,
-                              G->cs);
-    ++nk;
-  }
+  e = launch_tri_all(b, G->cs, &nk);
+  if (e == cudaSuccess) e = launch_inv_all(b, G->cs, &nk);
   const cudaError_t e3 = cudaStreamEndCapture(G->cs, &out);
   if (e == cudaSuccess) e = e3;
   if (e != cudaSuccess) return bcuda(b, e, "batch graph capture");
@@ -380,36 +613,16 @@ pd_status pd_batch_create(const pd_problem* probs, int nprob, int precision, voi
   }
   b->total = b->off[nprob];
   const bool fp64 = b->fp64;
-  const size_t cb = fp64 ? sizeof(double2) : sizeof(float2);
 
-  // descriptors, time-kernel work table and tridiagonal work tables
-  std::vector<int2> wt;
-  std::vector<int2> wtri[TRI_NCLASS];
+  // descriptors (the work tables follow the members' kernel shapes)
   std::vector<float2> bscale(nprob), one(nprob, make_float2(1.f, 0.f));
   b->h_fwd.resize(nprob);
   b->h_inv.resize(nprob);
   b->h_tri.resize(nprob);
   for (int i = 0; i < nprob; ++i) {
-    pd_plan* p = b->plans[i];
-    const dfc sc = dfc_from(p->s_scale);
+    const dfc sc = dfc_from(b->plans[i]->s_scale);
     bscale[i] = make_float2(sc.hi, sc.lo);
-    b->h_fwd[i] = plan_fwd_args(p);
-    b->h_fwd[i].mode = FWD_RESIDUAL;
-    b->h_inv[i] = plan_inv_args(p);
-    b->h_tri[i] = plan_tri_args(p, p->spec);
-    const int tiles = ceil_div(p->S, p->TX);
-    for (int t = 0; t < tiles; ++t) wt.push_back(make_int2(i, t));
-    const int rows = p->xf.M ? p->xf.M : p->nt;
-    b->smem_time = std::max(b->smem_time, (size_t)rows * (p->TX / 2 + 1) * cb);
-    b->smem_inv = std::max(b->smem_inv, time_inv_smem(p->nt, rows, p->TX, fp64, true));
-    b->ept = std::max(b->ept, time_tile_ept(rows, p->TX));
-    const int wc = tridiag_class(p->tri_n, fp64);
-    const int SB = tridiag_batch_sb(wc, fp64);
-    const long long systems = (long long)p->nh * p->J;
-    const int ttiles = (int)((systems + SB - 1) / SB);
-    for (int t = 0; t < ttiles; ++t) wtri[wc].push_back(make_int2(i, t));
   }
-  b->nblk_time = (int)wt.size();
   pd_status s = PD_OK;
   auto up = [&](void** dst, const void* src, size_t bytes) {
     if (s != PD_OK) return;
@@ -422,22 +635,21 @@ pd_status pd_batch_create(const pd_problem* probs, int nprob, int precision, voi
   up((void**)&b->d_off, b->off.data(), b->off.size() * sizeof(unsigned long long));
   up((void**)&b->d_bscale, bscale.data(), nprob * sizeof(float2));
   up((void**)&b->d_one, one.data(), nprob * sizeof(float2));
-  up((void**)&b->d_work_time, wt.data(), wt.size() * sizeof(int2));
-  for (int w = 0; w < TRI_NCLASS; ++w) {
-    b->ntiles_tri[w] = (int)wtri[w].size();
-    if (!wtri[w].empty()) up((void**)&b->d_work_tri[w], wtri[w].data(), wtri[w].size() * sizeof(int2));
-  }
-  up((void**)&b->d_tri, b->h_tri.data(), nprob * sizeof(TriArgs));
+  if (s == PD_OK) s = balloc(b, &b->d_tri, nprob * sizeof(TriArgs));
   if (s == PD_OK) s = balloc(b, &b->d_fwd, nprob * sizeof(FwdArgs));
   if (s == PD_OK) s = balloc(b, &b->d_inv, nprob * sizeof(InvArgs));
   if (s == PD_OK) s = balloc(b, &b->d_norms, 2 * nprob * sizeof(double));
   if (s == PD_OK) s = balloc(b, &b->d_flag, sizeof(int));
+  if (s == PD_OK) s = balloc(b, &b->d_ctr, pd_batch::NCTR * sizeof(int));
   if (s == PD_OK && !fp64) s = balloc(b, &b->Udf, b->total * sizeof(float2));
   if (s == PD_OK && !fp64) s = balloc(b, &b->Bdf, b->total * sizeof(float2));
   if (s == PD_OK) {
     cudaError_t e = cudaMallocHost((void**)&b->h_norms, (2 * nprob + 1) * sizeof(double));
     if (e != cudaSuccess) s = bcuda(b, e, "cudaMallocHost");
   }
+  if (s == PD_OK) s = batch_tables(b);
+  // mixed batches of at least 2^18 unknowns: tile widths and lane counts by timing
+  if (s == PD_OK && !fp64 && b->total >= (1ull << 18)) s = batch_autotune(b);
   if (s != PD_OK) {
     free_batch(b);
     return s;
@@ -495,6 +707,37 @@ pd_status pd_batch_build_rhs(pd_batch* b, const double* u0, const double* f, dou
   return PD_OK;
 }
 
+pd_status pd_batch_tuned(const pd_batch* b, int* tuned) {
+  if (!b || !tuned) return PD_ERR_ARG;
+  *tuned = b->tuned;
+  return PD_OK;
+}
+
+pd_status pd_batch_profile_sweep(pd_batch* b, const double* bvec, double* u, int reps, float* ms) {
+  if (!b || !bvec || !u || !ms || reps < 1) return berr(b, PD_ERR_ARG, "bad argument");
+  const int np = b->np;
+  cudaStream_t st = b->stream;
+  BCHK(set_call_descs(b, bvec, u));
+  BCU(cudaMemsetAsync(b->d_norms, 0, 2 * np * sizeof(double), st));
+  BCU(cudaMemsetAsync(b->d_flag, 0, sizeof(int), st));
+  if (!b->fp64) {
+    k_batch_to_df<<<grid_for(b->total), TB, 0, st>>>(u, b->Udf, b->d_off, b->d_one, np, b->total);
+    BCU(cudaGetLastError());
+    k_batch_to_df<<<grid_for(b->total), TB, 0, st>>>(bvec, b->Bdf, b->d_off, b->d_bscale, np,
+                                                     b->total);
+    BCU(cudaGetLastError());
+  }
+  const unsigned long long launches = b->launches;
+  int nk = 0;
+  BCHK(batch_time_ms(b, reps, &ms[0], [&]() -> cudaError_t { return launch_fwd_all(b, st, &nk); }));
+  BCHK(batch_time_ms(b, reps, &ms[1], [&]() -> cudaError_t { return launch_tri_all(b, st, &nk); }));
+  BCHK(batch_time_ms(b, reps, &ms[2], [&]() -> cudaError_t { return launch_inv_all(b, st, &nk); }));
+  if (!b->fp64) BCU(launch_from_df(b->Udf, u, b->total, st));
+  BCU(cudaStreamSynchronize(st));
+  b->launches = launches;
+  return PD_OK;
+}
+
 pd_status pd_batch_solve(pd_batch* b, const double* bvec, double* u, double tol, int maxit,
                          int* iters, double* relres_max) {
   PdRange range("pd.batch_solve");
@@ -504,28 +747,7 @@ pd_status pd_batch_solve(pd_batch* b, const double* bvec, double* u, double tol,
   const bool fp64 = b->fp64;
   cudaStream_t st = b->stream;
   // descriptors for this call (FP64: they point into the caller's arrays)
-  for (int i = 0; i < np; ++i) {
-    FwdArgs& fa = b->h_fwd[i];
-    InvArgs& ia = b->h_inv[i];
-    fa.norm2 = b->d_norms + np + i;
-    if (fp64) {
-      fa.U64 = u + b->off[i];
-      fa.B64 = bvec + b->off[i];
-      ia.mode = INV_UPDATE64;
-      ia.out64 = u + b->off[i];
-    } else {
-      fa.Udf = b->Udf + b->off[i];
-      fa.Bdf = b->Bdf + b->off[i];
-      ia.mode = INV_UPDATE_DF;
-      ia.Udf = b->Udf + b->off[i];
-      ia.igam = b->plans[i]->igam_s;
-    }
-    ia.flag = b->d_flag;
-  }
-  BCU(cudaMemcpyAsync(b->d_fwd, b->h_fwd.data(), np * sizeof(FwdArgs), cudaMemcpyHostToDevice, st));
-  BCU(cudaMemcpyAsync(b->d_inv, b->h_inv.data(), np * sizeof(InvArgs), cudaMemcpyHostToDevice, st));
-  for (int i = 0; i < np; ++i) b->h_tri[i].flag = b->d_flag;
-  BCU(cudaMemcpyAsync(b->d_tri, b->h_tri.data(), np * sizeof(TriArgs), cudaMemcpyHostToDevice, st));
+  BCHK(set_call_descs(b, bvec, u));
   BCU(cudaMemsetAsync(b->d_norms, 0, 2 * np * sizeof(double), st));
   BCU(cudaMemsetAsync(b->d_flag, 0, sizeof(int), st));
   k_batch_norm2<<<grid_for(b->total), TB, np * sizeof(double), st>>>(bvec, b->d_off, np, b->total,
@@ -560,7 +782,8 @@ pd_status pd_batch_solve(pd_batch* b, const double* bvec, double* u, double tol,
                         st));
     BLK(launch_from_df(b->Udf, u, b->total, st));
     BCU(cudaStreamSynchronize(st));
-    b->launches += (unsigned long long)h->n_body * 2 + (unsigned long long)h->n_update * G->update_kernels;
+    b->launches += (unsigned long long)h->n_body * (G->fwd_kernels + 1) +
+                   (unsigned long long)h->n_update * G->update_kernels;
     if (iters) *iters = h->it;
     if (relres_max) *relres_max = h->rmax;
     if (h->status == BS_CONVERGED) return PD_OK;
@@ -572,8 +795,10 @@ pd_status pd_batch_solve(pd_batch* b, const double* bvec, double* u, double tol,
   pd_status status = PD_OK;
   for (;;) {
     BCU(cudaMemsetAsync(b->d_norms + np, 0, np * sizeof(double), st));
-    BLK(launch_time_fwd_batch(b->d_fwd, b->d_work_time, b->nblk_time, b->band, b->smem_time, b->ept,
-                              fp64, st));
+    int nk = 0;
+    const cudaError_t ef = launch_fwd_all(b, st, &nk);
+    b->launches += nk;
+    if (ef != cudaSuccess) return bcuda(b, ef, "batched forward time kernels");
     BCU(cudaMemcpyAsync(b->h_norms, b->d_norms, 2 * np * sizeof(double), cudaMemcpyDeviceToHost, st));
     BCU(cudaMemcpyAsync(b->h_norms + 2 * np, b->d_flag, sizeof(int), cudaMemcpyDeviceToHost, st));
     BCU(cudaStreamSynchronize(st));
@@ -599,11 +824,11 @@ pd_status pd_batch_solve(pd_batch* b, const double* bvec, double* u, double tol,
       status = berr(b, PD_ERR_NOT_CONVERGED, "batched iteration reached maxit");
       break;
     }
-    for (int w = 0; w < TRI_NCLASS; ++w)
-      if (b->ntiles_tri[w] > 0)
-        BLK(launch_tridiag_batch(b->d_tri, b->d_work_tri[w], b->ntiles_tri[w], w, fp64, st));
-    BLK(launch_time_inv_batch(b->d_inv, b->d_work_time, b->nblk_time, b->smem_inv, b->ept, fp64,
-                              st));
+    nk = 0;
+    cudaError_t eu = launch_tri_all(b, st, &nk);
+    if (eu == cudaSuccess) eu = launch_inv_all(b, st, &nk);
+    b->launches += nk;
+    if (eu != cudaSuccess) return bcuda(b, eu, "batched tridiagonal / inverse time kernels");
     ++it;
   }
   if (!fp64) BLK(launch_from_df(b->Udf, u, b->total, st));

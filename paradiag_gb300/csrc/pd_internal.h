@@ -181,8 +181,9 @@ constexpr int TRI_NMAX = 4096;
 constexpr int TRI_NCLASS = 9;
 int tridiag_class(int n, bool fp64, int rows = 0);
 int tridiag_batch_sb(int cls, bool fp64);
+// persistent: *counter (device, zeroed before the launch) hands out the tiles
 cudaError_t launch_tridiag_batch(const TriArgs* descs, const int2* work, int ntiles, int cls,
-                                 bool fp64, cudaStream_t st);
+                                 bool fp64, int* counter, cudaStream_t st);
 #include "pd_xform_tc.h"
 
 // Auxiliary kernels (pd_ops.cu)

@@ -390,11 +390,25 @@ PD_D void solve_tile(const TriArgs& a, long long q0, unsigned char* smraw) {
 template <typename R, int L, bool BATCH, int MM>
 __global__ void __launch_bounds__(tri_threads(L),
                                   L >= 64 ? 1 : (sizeof(R) == 4 ? (MM <= 16 ? 5 : 4) : 2))
-    k_tridiag(TriArgs a1, const TriArgs* __restrict__ descs, const int2* __restrict__ work) {
+    k_tridiag(TriArgs a1, const TriArgs* __restrict__ descs, const int2* __restrict__ work,
+              int nwork, int* counter) {
   extern __shared__ __align__(16) unsigned char smraw[];
-  const TriArgs& a = BATCH ? descs[work[blockIdx.x].x] : a1;
-  const long long tile = BATCH ? work[blockIdx.x].y : (long long)blockIdx.x;
-  solve_tile<R, L, MM>(a, tile * tri_sb(L), smraw);
+  if (!BATCH) {
+    solve_tile<R, L, MM>(a1, (long long)blockIdx.x * tri_sb(L), smraw);
+    return;
+  }
+  // batch: persistent, every block takes the next tile from the device
+  // counter (zeroed before the launch) until the table is exhausted
+  __shared__ int slot;
+  for (;;) {
+    __syncthreads();                            // the previous tile is done (shared memory, slot)
+    if (threadIdx.x == 0) slot = atomicAdd(counter, 1);
+    __syncthreads();
+    const int i = slot;
+    if (i >= nwork) break;
+    const int2 w = work[i];
+    solve_tile<R, L, MM>(descs[w.x], (long long)w.y * tri_sb(L), smraw);
+  }
 }
 
 template <typename R, int L, int MM>
@@ -408,29 +422,45 @@ size_t tile_smem() {
 
 template <typename R, int L, int MM>
 cudaError_t launch_l(const TriArgs& a1, const TriArgs* descs, const int2* work, long long ntiles,
-                     cudaStream_t st) {
+                     int* counter, cudaStream_t st) {
   if (ntiles == 0) return cudaSuccess;
   const size_t smem = tile_smem<R, L, MM>();
   auto kern = descs ? k_tridiag<R, L, true, MM> : k_tridiag<R, L, false, MM>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  kern<<<(unsigned)ntiles, tri_threads(L), smem, st>>>(a1, descs, work);
+  long long grid = ntiles;
+  if (descs) {
+    // persistent batch launch: the resident blocks of the whole GPU
+    static int nsm = 0;
+    if (nsm == 0) {
+      int dev = 0;
+      cudaGetDevice(&dev);
+      cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+      if (nsm <= 0) nsm = 1;
+    }
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, tri_threads(L), smem) !=
+            cudaSuccess || per_sm < 1)
+      per_sm = 1;
+    grid = std::min<long long>(ntiles, (long long)per_sm * nsm);
+  }
+  kern<<<(unsigned)grid, tri_threads(L), smem, st>>>(a1, descs, work, (int)ntiles, counter);
   return cudaGetLastError();
 }
 
 template <typename R, int MM = ChunkRows<R>::MM>
 cudaError_t launch_cls(int cls, const TriArgs& a1, const TriArgs* descs, const int2* work,
-                       long long ntiles, cudaStream_t st) {
+                       long long ntiles, cudaStream_t st, int* counter = nullptr) {
   switch (cls) {
-    case 0: return launch_l<R, 1, MM>(a1, descs, work, ntiles, st);
-    case 1: return launch_l<R, 2, MM>(a1, descs, work, ntiles, st);
-    case 2: return launch_l<R, 4, MM>(a1, descs, work, ntiles, st);
-    case 3: return launch_l<R, 8, MM>(a1, descs, work, ntiles, st);
-    case 4: return launch_l<R, 16, MM>(a1, descs, work, ntiles, st);
-    case 5: return launch_l<R, 32, MM>(a1, descs, work, ntiles, st);
-    case 6: return launch_l<R, 64, MM>(a1, descs, work, ntiles, st);
-    case 7: return launch_l<R, 128, MM>(a1, descs, work, ntiles, st);
-    case 8: return launch_l<R, 256, MM>(a1, descs, work, ntiles, st);
+    case 0: return launch_l<R, 1, MM>(a1, descs, work, ntiles, counter, st);
+    case 1: return launch_l<R, 2, MM>(a1, descs, work, ntiles, counter, st);
+    case 2: return launch_l<R, 4, MM>(a1, descs, work, ntiles, counter, st);
+    case 3: return launch_l<R, 8, MM>(a1, descs, work, ntiles, counter, st);
+    case 4: return launch_l<R, 16, MM>(a1, descs, work, ntiles, counter, st);
+    case 5: return launch_l<R, 32, MM>(a1, descs, work, ntiles, counter, st);
+    case 6: return launch_l<R, 64, MM>(a1, descs, work, ntiles, counter, st);
+    case 7: return launch_l<R, 128, MM>(a1, descs, work, ntiles, counter, st);
+    case 8: return launch_l<R, 256, MM>(a1, descs, work, ntiles, counter, st);
   }
   return cudaErrorInvalidValue;
 }
@@ -463,10 +493,10 @@ cudaError_t launch_tridiag(const TriArgs& a, bool fp64, cudaStream_t st) {
 }
 
 cudaError_t launch_tridiag_batch(const TriArgs* descs, const int2* work, int ntiles, int cls,
-                                 bool fp64, cudaStream_t st) {
+                                 bool fp64, int* counter, cudaStream_t st) {
   if (ntiles == 0) return cudaSuccess;
   TriArgs dummy;
   memset(&dummy, 0, sizeof(dummy));
-  return fp64 ? launch_cls<double>(cls, dummy, descs, work, ntiles, st)
-              : launch_cls<float>(cls, dummy, descs, work, ntiles, st);
+  return fp64 ? launch_cls<double>(cls, dummy, descs, work, ntiles, st, counter)
+              : launch_cls<float>(cls, dummy, descs, work, ntiles, st, counter);
 }

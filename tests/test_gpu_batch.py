@@ -54,7 +54,17 @@ def test_batch_matches_sequential(prec):
     # (mixed) or 16 rows (FP64).
     rows = 32 if prec == "mixed" else 16
     classes = {int(np.ceil(np.log2(max(1, -(-w.problem.space.nx // rows))))) for w in wls}
-    per_sweep = 1 + 1 + len(classes) + 1
+    # the time kernels run one persistent launch per tile-footprint class
+    # (4, 8 or 16 complex elements per thread; tiles of N x TX reals with
+    # TX = min(32, budget / N), budget 8192 mixed / 2048 FP64)
+    budget = 8192 if prec == "mixed" else 2048
+    tcls = set()
+    for w in wls:
+        n = w.problem.nt
+        tx = max(2, min(32, budget // n))
+        e = -(-(n * (tx // 2)) // 256)
+        tcls.add(0 if e <= 4 else 1 if e <= 8 else 2)
+    per_sweep = len(tcls) + 1 + len(classes) + len(tcls)
     assert batch.launches() - l0 <= per_sweep * it + len(classes) + 6
     assert batch.uses_graph() == (prec == "mixed")
     uh = host(u)
@@ -99,6 +109,42 @@ def test_batch_integer_nt_reading(prec):
     off = batch.offsets
     for i, w in enumerate(wls):
         pb = w.problem
+        uref = S.solve_sequential(pb, O.build_rhs(pb, w.u0, None, w.f))
+        err = rel2(uh[off[i]:off[i + 1]].reshape(pb.nt, -1), uref)
+        assert err <= 1e-10, (i, pb.space.nx, pb.nt, err)
+    batch.close()
+
+
+def test_batch_autotuned_matches_sequential():
+    """A mixed batch of more than 2^18 unknowns chooses its tile widths and
+    tridiagonal lane counts by timing at creation (per group of members with
+    one transform length / one lane class); the solve with those shapes must
+    still give every member the oracle's solution, and the per-kernel sweep
+    profile reports three positive times."""
+    pd = lib_ready()
+    wls = W.batched(count=12, seed=31337, pow2=False)
+    assert sum(w.problem.unknowns for w in wls) >= 1 << 18
+    probs = [dict(space=dict(nx=w.problem.space.nx, nu=w.problem.space.nu, ax=w.problem.space.ax),
+                  nt=w.problem.nt, dt=w.problem.dt, alpha=w.problem.alpha, scheme=0, theta=1.0)
+             for w in wls]
+    batch = pd.Batch(probs, pd.PD_MIXED)
+    assert batch.tuned()
+    u0 = np.concatenate([w.u0 for w in wls])
+    f = np.concatenate([w.f.reshape(-1) for w in wls])
+    b = batch.build_rhs(dev(u0), dev(f))
+    import torch
+    ms = batch.profile_sweep(b, torch.zeros_like(b), reps=2)
+    assert len(ms) == 3 and all(t > 0 for t in ms), ms
+    # as in the first test: run to the double-float residual floor of every
+    # member, then compare with the oracle
+    u, it, rel = batch.solve(b, tol=0.0, maxit=12, allow_not_converged=True)
+    uh = host(u)
+    off = batch.offsets
+    for i, w in enumerate(wls):
+        pb = w.problem
+        K = O.stencil(pb.space)
+        floor = 2.0 ** -48 * (1.0 + pb.dt * abs(K).sum(axis=1).max())
+        assert batch.relres()[i] <= 16 * floor, (i, batch.relres()[i], floor)
         uref = S.solve_sequential(pb, O.build_rhs(pb, w.u0, None, w.f))
         err = rel2(uh[off[i]:off[i + 1]].reshape(pb.nt, -1), uref)
         assert err <= 1e-10, (i, pb.space.nx, pb.nt, err)
