@@ -52,6 +52,11 @@ def parse():
                     help="only the ParaDiag-I mixed kernel profile (the command ncu captures profile)")
     ap.add_argument("--no-hybrid", action="store_true", help="skip the hybrid ParaDiag-I leg")
     ap.add_argument("--no-control", action="store_true", help="skip the optimal-control leg")
+    ap.add_argument("--mode", default="replicas", choices=["replicas", "sharded"],
+                    help="replicas: one whole problem per GPU (weak scaling, the default); "
+                         "sharded: one problem split over the GPUs, grid-line slabs for the "
+                         "time steps and frequency slabs for step (b), all-to-all between "
+                         "(strong scaling)")
     ap.add_argument("--no-configs", action="store_true",
                     help="skip the 1D advection-diffusion, heat-source adjoint and 1D wave "
                          "GMRES legs")
@@ -1030,10 +1035,82 @@ def run_reference(args):
     print(json.dumps(out), flush=True)
 
 
+def run_sharded(args, ws, rank, local):
+    """The headline workload as one problem split over the ranks
+    (paradiag_gb300.shard): rank r owns a slab of grid lines (y) for the
+    residual, the time transforms and the x-transforms, and a slab of time
+    frequencies for the shifted solves; an all-to-all of the spectrum (NCCL)
+    sits on either side of step (b) and an all-reduce of ||r||^2 decides the
+    stopping test.  Timed like the main leg: W warm-up solves, K timed solves
+    between barriers, the slowest rank's time."""
+    import numpy as np
+    import torch
+    import paradiag_gb300 as pd
+    from paradiag_gb300 import shard
+    pd.build()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    w = workload(args.small)
+    pb = w.problem
+    sp = pb.space
+    space = dict(dim=2, nx=sp.nx, ny=sp.ny, nu=sp.nu, ax=sp.ax, ay=sp.ay, bc_x=sp.bc_x,
+                 bc_y=sp.bc_y)
+    layout = shard.SlabLayout(sp.ny, sp.nx, pb.nt // 2 + 1, ws)
+    rk = shard.RankState(pd, torch, space, pb.nt, pb.dt, pb.alpha, pd.PD_CN, 0.5, pd.PD_MIXED,
+                         layout, rank, dev)
+    if ws > 1:
+        ex = shard.DistExchange(torch)
+    else:
+        ex = shard.LocalExchange(torch)
+    solver = shard.ShardedSolver(pd, torch, [rk], ex)
+    bw = rk.whole.build_rhs(torch.from_numpy(w.u0).to(dev))
+    solver.set_rhs([bw.view(pb.nt, sp.ny, sp.nx)[:, rk.l0:rk.l1, :].reshape(pb.nt, -1)])
+    for _ in range(max(args.warmup, 3)):
+        solver.solve(tol=TOL, maxit=40)
+    stream = torch.cuda.current_stream()
+    barrier(ws)
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        it, rel = solver.solve(tol=TOL, maxit=40)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier(ws)
+    ms = max_over_ranks(ws, e0.elapsed_time(e1) / args.steps, dev)
+    NS = pb.unknowns
+    err = None
+    if ws == 1 and not args.no_check:
+        from oracle import operators as O
+        from oracle import stepping as S
+        uref = S.solve_sequential(pb, O.build_rhs(pb, w.u0, None, None))
+        un = solver.owned(rk, rk.u).cpu().numpy()
+        err = float(np.linalg.norm(un - uref) / np.linalg.norm(uref))
+    if rank == 0:
+        cfg = bench_config(w, args.small, ws)
+        cfg["parallelism"] = (f"one problem over {ws} GPU(s): y slabs for the residual and the "
+                              f"time transforms, frequency slabs for step (b), all-to-all of the "
+                              f"FP32 spectrum between them")
+        out = {"metric": METRIC, "value": NS / (ms / 1e3), "unit": UNIT, "n_gpus": ws,
+               "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+               "higher_is_better": True, "scaling": "strong", "vs_baseline": None,
+               "dtype": "f32 preconditioner + f64 residual", "data": "synthetic",
+               "config": cfg, "mode": "sharded", "iterations": it, "relres": rel,
+               "error_vs_oracle": err,
+               "exchange_bytes_per_iteration": 2 * 8 * (pb.nt // 2 + 1) * sp.ny * (sp.nx + sp.nx % 2)}
+        print(json.dumps(out), flush=True)
+    rk.close()
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
+        return
+    if args.mode == "sharded":
+        ws, rank, local = dist_setup()
+        run_sharded(args, ws, rank, local)
         return
     ws, rank, local = dist_setup()
     import numpy as np

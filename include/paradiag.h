@@ -338,6 +338,58 @@ PD_API pd_status pd_batch_tuned(const pd_batch* batch, int* tuned);
 PD_API pd_status pd_batch_profile_sweep(pd_batch* batch, const double* b, double* u, int reps,
                                         float* ms);
 
+/* ---- the preconditioner in parts, for a solve spread over several GPUs ----
+ * Steps (a) and (c) of eq. 1.3 act on every spatial point independently and
+ * step (b) on every time frequency k independently (the discussion after
+ * Lemma 1: the Nt shifted systems are "completely independent"), so a
+ * distributed solve gives each rank a slab of grid lines for the residual and
+ * the time transforms, and a slab of frequencies for step (b), with an
+ * all-to-all transpose of the spectrum between them (the caller's: the
+ * Python binding does it with torch.distributed).  A rank's slab plan is an
+ * ordinary plan for its lines plus one halo line on each side (grid spacing
+ * kept by scaling ly, or lx in 1D); the frequency-slab solves use a plan of
+ * the whole grid.  2D problems slab y, 1D Dirichlet problems slab x; 1D
+ * periodic plans return PD_ERR_UNSUPPORTED.  All arrays are device memory;
+ * work goes on the plan's stream.  No paper counterpart for the split. */
+
+/* Step (a) of P_alpha^{-1} r: Gamma scaling and FFT along t, then (2D) the
+ * forward x-eigentransform.  r: [Nt][S] FP64.  The result is the plan's
+ * step-(b) spectrum (pd_plan_spectrum). */
+PD_API pd_status pd_precond_forward(pd_plan* plan, const double* r);
+
+/* The step-(b) spectrum of the plan: *data -> complex [nh][lines][pitch]
+ * (FP32 pairs on mixed plans, FP64 pairs on FP64 plans: *elem_bytes 8 or
+ * 16), nh = Nt/2 + 1 frequencies, lines = ny (2D) or nx (1D), pitch = the
+ * padded nx (2D) or 1 (1D). */
+PD_API pd_status pd_plan_spectrum(pd_plan* plan, void** data, int* nh, int* lines, int* pitch,
+                                  int* elem_bytes);
+
+/* Copy the block k0 <= k < k1, l0 <= line < l1 of the plan's step-(b)
+ * spectrum to (get) or from (put) a contiguous device buffer laid out
+ * [k1-k0][l1-l0][pitch]; put with src NULL writes zeros. */
+PD_API pd_status pd_spectrum_get(pd_plan* plan, int k0, int k1, int l0, int l1, void* dst);
+PD_API pd_status pd_spectrum_put(pd_plan* plan, int k0, int k1, int l0, int l1, const void* src);
+
+/* Step (b) for the frequencies k0 <= k < k1 on a caller-owned slab laid out
+ * like the plan's spectrum with k1 - k0 frequencies ([k1-k0][lines][pitch]),
+ * in place: the shifted systems (lambda_1k I + lambda_2k K) z = s of eq. 1.3
+ * (2D: after the x-eigentransform, tridiagonal in y). */
+PD_API pd_status pd_precond_solve_rows(pd_plan* plan, int k0, int k1, void* data);
+
+/* Step (c): (2D) the inverse x-eigentransform of the plan's step-(b)
+ * spectrum, the inverse FFT along t and Gamma^{-1}: z [Nt][S] FP64. */
+PD_API pd_status pd_precond_backward(pd_plan* plan, double* z);
+
+/* *out (host) = sum over time levels and the grid lines first_line ..
+ * first_line + nlines - 1 of x^2 (x: [Nt][S]); synchronises the stream. */
+PD_API pd_status pd_shard_norm2(pd_plan* plan, const double* x, int first_line, int nlines,
+                                double* out);
+
+/* u += z on the grid lines first_line .. first_line + nlines - 1 of every
+ * time level (u, z: [Nt][S]). */
+PD_API pd_status pd_shard_update(pd_plan* plan, const double* z, double* u, int first_line,
+                                 int nlines);
+
 /* Size of the device array used by pd_apply_precond_noalloc (8 MiB). */
 #define PD_NOALLOC_SCRATCH_BYTES (8u << 20)
 

@@ -86,6 +86,16 @@ _SIGS = {
     "pd_batch_launches": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_ulonglong)]),
     "pd_batch_uses_graph": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int)]),
     "pd_batch_relres": (ctypes.c_int, [_P, _D]),
+    "pd_precond_forward": (ctypes.c_int, [_P, _P]),
+    "pd_plan_spectrum": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_void_p), ctypes.POINTER(ctypes.c_int),
+                                        ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
+                                        ctypes.POINTER(ctypes.c_int)]),
+    "pd_precond_solve_rows": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int, _P]),
+    "pd_spectrum_get": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, _P]),
+    "pd_spectrum_put": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, _P]),
+    "pd_precond_backward": (ctypes.c_int, [_P, _P]),
+    "pd_shard_norm2": (ctypes.c_int, [_P, _P, ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_double)]),
+    "pd_shard_update": (ctypes.c_int, [_P, _P, _P, ctypes.c_int, ctypes.c_int]),
     "pd_batch_tuned": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int)]),
     "pd_batch_profile_sweep": (ctypes.c_int, [_P, _P, _P, ctypes.c_int, ctypes.POINTER(ctypes.c_float)]),
     "pd_batch_last_error": (ctypes.c_char_p, [_P]),
@@ -290,6 +300,44 @@ def pd_batch_relres(batch, nprob):
     arr = (ctypes.c_double * nprob)()
     st = load().pd_batch_relres(batch, arr)
     return st, list(arr)
+
+
+def pd_precond_forward(plan, r):
+    return load().pd_precond_forward(plan, r)
+
+
+def pd_plan_spectrum(plan):
+    data = ctypes.c_void_p(0)
+    nh, lines, pitch, eb = ctypes.c_int(0), ctypes.c_int(0), ctypes.c_int(0), ctypes.c_int(0)
+    st = load().pd_plan_spectrum(plan, ctypes.byref(data), ctypes.byref(nh), ctypes.byref(lines),
+                                 ctypes.byref(pitch), ctypes.byref(eb))
+    return st, data.value, nh.value, lines.value, pitch.value, eb.value
+
+
+def pd_spectrum_get(plan, k0, k1, l0, l1, dst):
+    return load().pd_spectrum_get(plan, int(k0), int(k1), int(l0), int(l1), dst)
+
+
+def pd_spectrum_put(plan, k0, k1, l0, l1, src):
+    return load().pd_spectrum_put(plan, int(k0), int(k1), int(l0), int(l1), src)
+
+
+def pd_precond_solve_rows(plan, k0, k1, data):
+    return load().pd_precond_solve_rows(plan, int(k0), int(k1), data)
+
+
+def pd_precond_backward(plan, z):
+    return load().pd_precond_backward(plan, z)
+
+
+def pd_shard_norm2(plan, x, first_line, nlines):
+    v = ctypes.c_double(0.0)
+    st = load().pd_shard_norm2(plan, x, int(first_line), int(nlines), ctypes.byref(v))
+    return st, v.value
+
+
+def pd_shard_update(plan, z, u, first_line, nlines):
+    return load().pd_shard_update(plan, z, u, int(first_line), int(nlines))
 
 
 def pd_batch_tuned(batch):

@@ -911,6 +911,7 @@ FwdArgs plan_fwd_args(const pd_plan* p) { return fwd_base_impl(p); }
 InvArgs plan_inv_args(const pd_plan* p) { return inv_base_impl(p); }
 TriArgs plan_tri_args(const pd_plan* p, void* data) { return tri_args_impl(p, data); }
 pd_status plan_step_b(pd_plan* p) { return step_b(p); }
+pd_status plan_xform(pd_plan* p, bool fwd) { return xform_dir(p, fwd); }
 pd_status plan_fail_cuda(pd_plan* p, cudaError_t e, const char* what) { return fail_cuda(p, e, what); }
 pd_status plan_precond(pd_plan* p, const double* r, double* z) { return precond_into(p, r, z); }
 

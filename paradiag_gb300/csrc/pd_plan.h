@@ -86,6 +86,9 @@ TriArgs plan_tri_args(const pd_plan* p, void* data);
 // step (b) of the plan (x-eigentransform, shifted tridiagonal solves, inverse
 // x-transform) on p->spec
 pd_status plan_step_b(pd_plan* p);
+// the x-eigentransform of the plan's spectrum: forward spec -> spec2, inverse
+// spec2 -> spec (2D and periodic-x plans)
+pd_status plan_xform(pd_plan* p, bool fwd);
 pd_status plan_fail_cuda(pd_plan* p, cudaError_t e, const char* what);
 // z = P_alpha^{-1} r (FP64 in and out) with the plan's current eigenvalue table
 pd_status plan_precond(pd_plan* p, const double* r, double* z);

@@ -1,7 +1,9 @@
 """The multi-process path of bench.py on CPU (gloo, world size 2): process-group
 set-up from the torchrun environment, the barrier, and the max-over-ranks
-reduction of the per-rank times.  The benchmark runs independent replicas (one
-problem per GPU, no data-path collective), so these are the only collectives."""
+reduction of the per-rank times.  By default the benchmark runs independent
+replicas (one problem per GPU, no data-path collective); its sharded mode's
+collectives (halo exchange, all-to-all of the spectrum, all-reduce of the
+residual norm) are tested in test_shard_exchange.py."""
 import os
 import socket
 import sys
