@@ -491,8 +491,14 @@ FP32_ALU_PEAK = 152 * 128 * 2 * 2.07e9 / 1e12   # TFLOP/s: SMs x FP32 lanes x FM
 def hybrid_kernel_profile(pd, torch, dev, precisions):
     """Per-stage times of a hybrid ParaDiag-I refinement sweep on the bench
     workload (255 x 255 x 256): the residual (HBM: 20 bytes per unknown on the
-    mixed path, 24 on the FP64 path), the two dense time GEMMs (FP32 / FP64
-    CUDA-core FLOPs: 2 Nt flops per unknown each) and step (b)."""
+    mixed path, 24 on the FP64 path), the two dense time contractions and step
+    (b).  Mixed plans run the contractions on the tensor cores (tcgen05); they
+    are then HBM-bound (step (a): 4 B of r in + 4 B of spectrum out per
+    unknown; step (c): 4 B of spectrum in + 16 B of double-float iterate in and
+    out per unknown; the spectrum transpose of step (c) is extra traffic, not
+    algorithmic).  The CUDA-core engine of the same plan is timed beside it
+    ("mixed_cuda_cores"), and the FP64 plan (CUDA cores), against the FP32 /
+    FP64 ALU rate: 2 Nt flops per unknown each."""
     import workloads as W
     wl = W.hybrid_ade2d()
     pb = wl.problem
@@ -503,9 +509,17 @@ def hybrid_kernel_profile(pd, torch, dev, precisions):
     hbm, _, src = peaks()
     ns = pb.unknowns
     out = {}
+    runs = []
     for prec in precisions:
+        runs.append((prec, None))
+        if prec == pd.PD_MIXED:
+            runs.append((prec, False))
+    for prec, tc in runs:
         fp64 = prec == pd.PD_FP64
         pl = pd.PlanHybrid(space, pb.nt, pb.dt, prec, stream)
+        if tc is not None:
+            pl.set_tensor_cores(tc)
+        on_tc = pl.tensor_cores
         b = pl.build_rhs(torch.from_numpy(wl.u0).to(dev))
         u = torch.empty_like(b)
         pl.profile_sweep(b, u, reps=1)
@@ -514,18 +528,28 @@ def hybrid_kernel_profile(pd, torch, dev, precisions):
         flops = 2.0 * (2 * nh) * pb.nt * sp.nx * sp.ny
         rb = (24.0 if fp64 else 20.0) * ns
         gbs = rb / (kms[0] / 1e3) / 1e9
-        ent = {"resid": {"ms": kms[0], "bound": "hbm", "achieved": gbs, "peak": hbm,
+        ent = {"engine": "tcgen05" if on_tc else "cuda_cores",
+               "resid": {"ms": kms[0], "bound": "hbm", "achieved": gbs, "peak": hbm,
                          "unit": "GB/s", "frac": gbs / hbm, "algorithmic_bytes": rb,
                          "peak_source": f"{src} (MEASURED_PEAKS.json)"},
                "step_b_ms": kms[2]}
-        for name, t in (("gemm_step_a", kms[1]), ("gemm_step_c_update", kms[3])):
+        for name, t, bpu in (("gemm_step_a", kms[1], 8.0), ("gemm_step_c_update", kms[3], 20.0)):
             tf = flops / (t / 1e3) / 1e12
+            if on_tc:
+                ab = bpu * ns
+                ach = ab / (t / 1e3) / 1e9
+                ent[name] = {"ms": t, "bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s",
+                             "frac": ach / hbm, "algorithmic_bytes": ab,
+                             "peak_source": f"{src} (MEASURED_PEAKS.json)",
+                             "tensor_tflops_algorithmic": tf}
+                continue
             pk = FP32_ALU_PEAK / 64.0 if fp64 else FP32_ALU_PEAK
             ent[name] = {"ms": t, "bound": "alu", "achieved": tf, "peak": pk, "unit": "TFLOP/s",
                          "frac": tf / pk, "algorithmic_flops": flops,
                          "peak_source": ("FP64 CUDA-core rate taken as 1/64 of " if fp64 else "")
                          + "152 SMs x 128 FP32 lanes x 2 flops x 2070 MHz (derived, nominal)"}
-        out["fp64" if fp64 else "mixed"] = ent
+        key = "fp64" if fp64 else ("mixed" if tc is None else "mixed_cuda_cores")
+        out[key] = ent
         pl.close()
     return out
 

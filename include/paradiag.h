@@ -521,11 +521,15 @@ typedef struct pdh_plan pdh_plan;
 
 /* Plan for nt uniform steps of size dt (1 <= nt <= 4096; PD_ERR_UNSUPPORTED
  * above).  precision PD_FP64: steps (a)-(c) and the residual in FP64;
- * PD_MIXED: steps (a)-(c) in FP32 (the tensor-core x-transform in 2D), the
- * residual of the refinement sweeps in double-float.  sp: as for
- * pd_plan_create.  stream: cudaStream_t (NULL: the default stream).  Finds
- * the eigenvalues and the eigenvector matrices on the host (O(nt^2) work) and
- * allocates all device memory the solves need. */
+ * PD_MIXED: steps (a)-(c) at FP32 level (the tensor-core x-transform in 2D),
+ * the residual of the refinement sweeps in double-float.  On mixed first-order
+ * plans with nt a multiple of 16, 32 <= nt, and at least 128 spatial points, the
+ * dense time contractions of steps (a) and (c) (the real forms of V^{-1} and V)
+ * run on the tensor cores as GEMMs over the spatial points, with FP16 operands
+ * split in two terms and FP32 accumulation (pdh_set_tensor_cores); otherwise
+ * on the CUDA cores.  sp: as for pd_plan_create.  stream: cudaStream_t (NULL:
+ * the default stream).  Finds the eigenvalues and the eigenvector matrices on
+ * the host (O(nt^2) work) and allocates all device memory the solves need. */
 PD_API pd_status pdh_plan_create(const pd_space* sp, int nt, double dt, int precision,
                                  void* stream, pdh_plan** out);
 PD_API pd_status pdh_plan_destroy(pdh_plan* plan);
@@ -573,6 +577,14 @@ PD_API pd_status pdh_profile_sweep(pdh_plan* plan, const double* b, double* u, i
                                    float* ms);
 PD_API pd_status pdh_launches(const pdh_plan* plan, unsigned long long* count);
 PD_API const char* pdh_last_error(const pdh_plan* plan);
+
+/* Engine of the time contractions of steps (a) and (c): on = 1 the tcgen05
+ * GEMMs (the default where the plan allows them), on = 0 the CUDA-core GEMMs.
+ * on = 1 on a plan that does not allow them (FP64, second-order, nt not a
+ * multiple of 16 or below 32, fewer than 128 spatial points): PD_ERR_UNSUPPORTED.
+ * Waits for the plan's stream.  pdh_tensor_cores: *on = the engine in use. */
+PD_API pd_status pdh_set_tensor_cores(pdh_plan* plan, int on);
+PD_API pd_status pdh_tensor_cores(const pdh_plan* plan, int* on);
 
 /* ---------------------------------------------------------------------------
  * ParaDiag-II for the optimal control of the wave equation (Section 4): the

@@ -135,6 +135,8 @@ _SIGS = {
     "pdh_profile_sweep": (ctypes.c_int, [_P, _P, _P, ctypes.c_int, ctypes.POINTER(ctypes.c_float)]),
     "pdh_launches": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_ulonglong)]),
     "pdh_last_error": (ctypes.c_char_p, [_P]),
+    "pdh_set_tensor_cores": (ctypes.c_int, [_P, ctypes.c_int]),
+    "pdh_tensor_cores": (ctypes.c_int, [_P, _I]),
     "pdc_plan_create": (ctypes.c_int, [ctypes.POINTER(pd_space), ctypes.c_int, ctypes.c_double,
                                        ctypes.c_double, ctypes.c_int, _P, ctypes.POINTER(_P)]),
     "pdc_plan_destroy": (ctypes.c_int, [_P]),
@@ -578,6 +580,16 @@ def pdh_launches(plan):
 
 def pdh_last_error(plan) -> str:
     return load().pdh_last_error(plan).decode()
+
+
+def pdh_set_tensor_cores(plan, on):
+    return load().pdh_set_tensor_cores(plan, int(on))
+
+
+def pdh_tensor_cores(plan):
+    v = ctypes.c_int(0)
+    st = load().pdh_tensor_cores(plan, ctypes.byref(v))
+    return st, v.value
 
 
 def pdc_plan_create(space: pd_space, nt, T, gamma, precision, stream):
@@ -1040,6 +1052,18 @@ class PlanHybrid:
         st, v = pdh_launches(self._h)
         self._check(st, "pdh_launches")
         return v
+
+    @property
+    def tensor_cores(self):
+        """True when steps (a) and (c) run as tcgen05 GEMMs."""
+        st, v = pdh_tensor_cores(self._h)
+        self._check(st, "pdh_tensor_cores")
+        return bool(v)
+
+    def set_tensor_cores(self, on):
+        """Pick the engine of the time contractions (raises on plans without
+        the tensor-core form)."""
+        self._check(pdh_set_tensor_cores(self._h, on), "pdh_set_tensor_cores")
 
     def apply_A(self, u, y=None):
         import torch

@@ -285,8 +285,10 @@ struct HResid {
   const double* u64;
   float2* Bdf;
   const float2* Udf;
-  void* r;                      // [N][S] float / double
+  void* r;                      // [N][S] float / double; transposed variant: [S][N] float
   double* norm2;
+  unsigned* ramax;              // transposed variant: max |r| (float bits)
+  unsigned* ramax_reset;        // transposed variant: word zeroed by block (0, 0)
 };
 
 struct Nbh {
@@ -320,9 +322,37 @@ PD_D void acch_add_prod(AccH& A, dfc k, float2 u) {
   acch_add(A, p, pe);
 }
 
+// Mixed residual of time row n at point s (double-float accumulation of
+// b - B u - K u, rounded to FP32); um, u0, up = U_{n-1}, U_n, U_{n+1} at s.
+PD_D float hy_resid_row(const HResid& a, const Nbh& g, int n, int s, float2 um, float2 u0,
+                        float2 up) {
+  const size_t base = (size_t)n * a.S;
+  const float2* U = a.Udf + base;
+  const float2 bb = a.Bdf[base + s];
+  AccH A = {bb.x, bb.y};
+  acch_add_prod(A, dfc{-a.kap[0].hi, -a.kap[0].lo}, u0);
+  if (g.l >= 0) acch_add_prod(A, dfc{-a.kap[1].hi, -a.kap[1].lo}, U[g.l]);
+  if (g.r >= 0) acch_add_prod(A, dfc{-a.kap[2].hi, -a.kap[2].lo}, U[g.r]);
+  if (g.d >= 0) acch_add_prod(A, dfc{-a.kap[3].hi, -a.kap[3].lo}, U[g.d]);
+  if (g.u >= 0) acch_add_prod(A, dfc{-a.kap[4].hi, -a.kap[4].lo}, U[g.u]);
+  if (n + 1 < a.N) {
+    acch_add_prod(A, dfc{-a.c2d.hi, -a.c2d.lo}, up);
+    acch_add_prod(A, a.c2d, um);
+  } else {
+    acch_add_prod(A, dfc{-a.c1d.hi, -a.c1d.lo}, u0);
+    acch_add_prod(A, a.c1d, um);
+  }
+  return fast_two_sum(A.s, A.e).hi;
+}
+
 // One thread per spatial point and chunk of HR_CH time rows (grid.y: chunks),
-// so that many rows of a point are in flight at once.
-template <int PREC, int MODE>
+// so that many rows of a point are in flight at once.  TR (mixed only, N a
+// multiple of 16): r is written as the A operand of the tensor-core time
+// contraction, r^T in blocks of 128 points x 16 time rows (element (s, n) at
+// ((s / 128) (N / 16) + n / 16) 2048 + (s % 128) 16 + n % 16): block (x, y)
+// of this grid writes one contiguous 8 KB block, zeros for points beyond S;
+// max |r| goes to *ramax.
+template <int PREC, int MODE, bool TR = false>
 __global__ void __launch_bounds__(HR_TB) k_hy_resid(const HResid a) {
   const int s = blockIdx.x * HR_TB + threadIdx.x;
   const bool valid = s < a.S;
@@ -333,7 +363,50 @@ __global__ void __launch_bounds__(HR_TB) k_hy_resid(const HResid a) {
   const Nbh g = nbh(st, valid ? s : 0);
   double nrm = 0.0;
   float nrmf = 0.f;
-  if (valid) {
+  float amx = 0.f;
+  if constexpr (TR) {
+    if (blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0 && a.ramax_reset) *a.ramax_reset = 0u;
+  }
+  if (TR && MODE != HY_NORM) {
+    // mixed, blocked transposed output: the chunk's rows in registers, then
+    // four 16-byte stores per thread (a warp covers 2 KB of its block)
+    static_assert(HR_TB == 128 && HR_CH == 16, "one 128 x 16 block of r^T per thread block");
+    float rv[HR_CH];
+    float2 um = make_float2(0.f, 0.f), u0 = um;
+    if constexpr (MODE == HY_RESID) {
+      if (valid) {
+        um = n0 > 0 ? a.Udf[(size_t)(n0 - 1) * S + s] : make_float2(0.f, 0.f);
+        u0 = a.Udf[(size_t)n0 * S + s];
+      }
+    }
+#pragma unroll
+    for (int c = 0; c < HR_CH; ++c) {
+      const int n = n0 + c;
+      rv[c] = 0.f;
+      if (!valid || n >= n1) continue;
+      if constexpr (MODE == HY_DIRECT) {
+        const size_t i = (size_t)n * S + s;
+        const df d = df_from_double(a.b64[i]);
+        a.Bdf[i] = make_float2(d.hi, d.lo);
+        rv[c] = d.hi;
+      } else {
+        const float2 up = n + 1 < N ? a.Udf[(size_t)(n + 1) * S + s] : make_float2(0.f, 0.f);
+        rv[c] = hy_resid_row(a, g, n, s, um, u0, up);
+        um = u0;
+        u0 = up;
+      }
+      nrmf = fmaf(rv[c], rv[c], nrmf);
+      amx = fmaxf(amx, fabsf(rv[c]));
+    }
+    float* rt = reinterpret_cast<float*>(a.r) +
+                ((size_t)blockIdx.x * (N / HR_CH) + blockIdx.y) * (HR_TB * HR_CH) +
+                (size_t)threadIdx.x * HR_CH;
+#pragma unroll
+    for (int q = 0; q < HR_CH / 4; ++q)
+      reinterpret_cast<float4*>(rt)[q] =
+          make_float4(rv[4 * q], rv[4 * q + 1], rv[4 * q + 2], rv[4 * q + 3]);
+    nrm = (double)nrmf;
+  } else if (valid) {
     if constexpr (MODE == HY_DIRECT) {
       for (int n = n0; n < n1; ++n) {
         const size_t i = (size_t)n * S + s;
@@ -374,23 +447,8 @@ __global__ void __launch_bounds__(HR_TB) k_hy_resid(const HResid a) {
 #pragma unroll 4
       for (int n = n0; n < n1; ++n) {
         const size_t base = (size_t)n * S;
-        const float2* U = a.Udf + base;
         const float2 up = n + 1 < N ? a.Udf[base + S + s] : make_float2(0.f, 0.f);
-        const float2 bb = a.Bdf[base + s];
-        AccH A = {bb.x, bb.y};
-        acch_add_prod(A, dfc{-a.kap[0].hi, -a.kap[0].lo}, u0);
-        if (g.l >= 0) acch_add_prod(A, dfc{-a.kap[1].hi, -a.kap[1].lo}, U[g.l]);
-        if (g.r >= 0) acch_add_prod(A, dfc{-a.kap[2].hi, -a.kap[2].lo}, U[g.r]);
-        if (g.d >= 0) acch_add_prod(A, dfc{-a.kap[3].hi, -a.kap[3].lo}, U[g.d]);
-        if (g.u >= 0) acch_add_prod(A, dfc{-a.kap[4].hi, -a.kap[4].lo}, U[g.u]);
-        if (n + 1 < N) {
-          acch_add_prod(A, dfc{-a.c2d.hi, -a.c2d.lo}, up);
-          acch_add_prod(A, a.c2d, um);
-        } else {
-          acch_add_prod(A, dfc{-a.c1d.hi, -a.c1d.lo}, u0);
-          acch_add_prod(A, a.c1d, um);
-        }
-        const float r = fast_two_sum(A.s, A.e).hi;
+        const float r = hy_resid_row(a, g, n, s, um, u0, up);
         nrmf = fmaf(r, r, nrmf);
         if constexpr (MODE == HY_RESID) reinterpret_cast<float*>(a.r)[base + s] = r;
         um = u0;
@@ -401,6 +459,18 @@ __global__ void __launch_bounds__(HR_TB) k_hy_resid(const HResid a) {
   }
   for (int o = 16; o > 0; o >>= 1) nrm += __shfl_xor_sync(0xffffffffu, nrm, o);
   if ((threadIdx.x & 31) == 0 && a.norm2 != nullptr) atomicAdd(a.norm2, nrm);
+  if constexpr (TR && MODE != HY_NORM) {
+    // one atomic per block for the maximum
+    __shared__ float wmax[HR_TB / 32];
+    for (int o = 16; o > 0; o >>= 1) amx = fmaxf(amx, __shfl_xor_sync(0xffffffffu, amx, o));
+    if ((threadIdx.x & 31) == 0) wmax[threadIdx.x >> 5] = amx;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      float m = wmax[0];
+      for (int w = 1; w < HR_TB / 32; ++w) m = fmaxf(m, wmax[w]);
+      atomicMax(a.ramax, __float_as_uint(m));
+    }
+  }
 }
 
 // y = A u (FP64) and the right-hand side b_n = f(t_n) (+ u0/(2 dt) in row 1)
@@ -554,6 +624,49 @@ __global__ void k_hy2_rhs(const HResid a, const double* u0, const double* v0, co
   }
 }
 
+// Step-(b) spectrum (complex rows k, SpecGeom offsets) -> the A operand of the
+// tensor-core step (c): specT, the real [s][m] matrix with m = 2k + c (c = 0:
+// Re, 1: Im) in blocks of 128 points x 16 columns (8 spectrum rows), element
+// (s, m) at ((s / 128) (2 nh / 16) + m / 16) 2048 + (s % 128) 16 + m % 16
+// (nh a multiple of 8; zeros for points beyond S); max |.| into *amax and
+// *amax_reset = 0.  Block (x, y) reads 8 spectrum rows of 128 points (1 KB
+// segments) and writes its one contiguous 8 KB block.
+constexpr int HT_K = 8, HT_S = 128, HT_TB = 256;
+__global__ void __launch_bounds__(HT_TB) k_hy_spec_t(const float2* __restrict__ spec, SpecGeom sg,
+                                                    int nh, int S, float2* __restrict__ specT,
+                                                    unsigned* amax, unsigned* amax_reset) {
+  __shared__ float2 tile[HT_K][HT_S + 1];
+  __shared__ float wmax[HT_TB / 32];
+  const int s0 = blockIdx.x * HT_S, k0 = blockIdx.y * HT_K;
+  const int t = threadIdx.x;
+  if (blockIdx.x == 0 && blockIdx.y == 0 && t == 0 && amax_reset) *amax_reset = 0u;
+  float amx = 0.f;
+#pragma unroll
+  for (int q = 0; q < HT_K * HT_S / HT_TB; ++q) {
+    const int kk = q * (HT_TB / HT_S) + t / HT_S, ss = t % HT_S;
+    const int k = k0 + kk, s = s0 + ss;
+    float2 v = make_float2(0.f, 0.f);
+    if (s < S) v = spec[spec_index(sg, k, s)];
+    tile[kk][ss] = v;
+    amx = fmaxf(amx, fmaxf(fabsf(v.x), fabsf(v.y)));
+  }
+  __syncthreads();
+  float2* blk = specT + ((size_t)blockIdx.x * (nh / HT_K) + blockIdx.y) * (HT_S * HT_K);
+#pragma unroll
+  for (int q = 0; q < HT_K * HT_S / HT_TB; ++q) {
+    const int e = q * HT_TB + t;            // float2 index within the block: (s % 128) 8 + k % 8
+    blk[e] = tile[e % HT_K][e / HT_K];
+  }
+  for (int o = 16; o > 0; o >>= 1) amx = fmaxf(amx, __shfl_xor_sync(0xffffffffu, amx, o));
+  if ((t & 31) == 0) wmax[t >> 5] = amx;
+  __syncthreads();
+  if (t == 0) {
+    float m = wmax[0];
+    for (int w = 1; w < HT_TB / 32; ++w) m = fmaxf(m, wmax[w]);
+    atomicMax(amax, __float_as_uint(m));
+  }
+}
+
 template <typename R>
 cudaError_t launch_gemm(const HGemm& g, int mode, cudaStream_t st) {
   constexpr int BN = GemmTile<R>::BN;
@@ -582,6 +695,10 @@ cudaError_t launch_resid(const HResid& a, int mode, bool fp64, cudaStream_t st) 
     if (mode == HY_DIRECT) k_hy_resid<1, HY_DIRECT><<<grid, block, 0, st>>>(a);
     else if (mode == HY_RESID) k_hy_resid<1, HY_RESID><<<grid, block, 0, st>>>(a);
     else k_hy_resid<1, HY_NORM><<<grid, block, 0, st>>>(a);
+  } else if (a.ramax != nullptr) {
+    if (mode == HY_DIRECT) k_hy_resid<0, HY_DIRECT, true><<<grid, block, 0, st>>>(a);
+    else if (mode == HY_RESID) k_hy_resid<0, HY_RESID, true><<<grid, block, 0, st>>>(a);
+    else k_hy_resid<0, HY_NORM, true><<<grid, block, 0, st>>>(a);
   } else {
     if (mode == HY_DIRECT) k_hy_resid<0, HY_DIRECT><<<grid, block, 0, st>>>(a);
     else if (mode == HY_RESID) k_hy_resid<0, HY_RESID><<<grid, block, 0, st>>>(a);
@@ -614,6 +731,16 @@ struct pdh_plan {
   double* dnorm = nullptr;
   double* hnorm = nullptr;
   int* hflag = nullptr;
+  // tensor-core time contractions (mixed, first order, nt % 16 == 0): r is
+  // kept transposed, r^T [S][Nt] in blocks of 128 x 16; step (a) is
+  // D[s][2k+c] = sum_n r^T[s][n] Gf[2k+c][n] into the spectrum, step (c)
+  // transposes the spectrum to specT [S][2 Nh] (same blocking) and updates
+  // Udf[n][s] with D[s][n] = sum_m specT[s][m] Gi[n][m]
+  bool tc_ok = false, tc = false;
+  void* Gtc[4] = {nullptr, nullptr, nullptr, nullptr};   // FP16 hi, lo of Gf; hi, lo of Gi
+  float2* specT = nullptr;
+  unsigned* hamax = nullptr;      // [0]: max |r|, [1]: max |specT| (float bits)
+  XformTc xf_fwd, xf_inv;
   unsigned long long launches = 0;
   char msg[256] = {0};
 };
@@ -643,7 +770,8 @@ pd_status ph_cuda(pdh_plan* q, cudaError_t e, const char* what) {
 
 void free_ph(pdh_plan* q) {
   if (!q) return;
-  void* ptrs[] = {q->Af, q->Ai, q->r, q->Udf, q->Bdf, q->dnorm, q->w2};
+  void* ptrs[] = {q->Af, q->Ai, q->r, q->Udf, q->Bdf, q->dnorm, q->w2,
+                  q->Gtc[0], q->Gtc[1], q->Gtc[2], q->Gtc[3], q->specT, q->hamax};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (q->hnorm) cudaFreeHost(q->hnorm);
@@ -743,6 +871,10 @@ HResid resid_args(const pdh_plan* q) {
   a.w2 = q->w2;
   a.b2_0 = q->b2_0 / (2.0 * q->dt * q->dt);
   a.b2_1 = q->b2_1 / (2.0 * q->dt * q->dt);
+  if (q->tc) {
+    a.ramax = q->hamax;
+    a.ramax_reset = q->hamax + 1;
+  }
   return a;
 }
 
@@ -793,13 +925,89 @@ pd_status gemm(pdh_plan* q, const HGemm& g, int mode) {
   return PD_OK;
 }
 
+// step (a) on the residual buffer
+pd_status time_fwd(pdh_plan* q) {
+  if (q->tc) {
+    PHLK(launch_xform_tc(q->xf_fwd, q->sp->dflag, q->sp->stream));
+    return PD_OK;
+  }
+  return gemm(q, gemm_fwd(q), HY_FWD);
+}
+
+// step (c) with the update mode inv_mode
+pd_status time_inv(pdh_plan* q, double* u, int inv_mode) {
+  if (!q->tc) return gemm(q, gemm_inv(q, u), inv_mode);
+  const pd_plan* p = q->sp;
+  const dim3 grid((p->S + HT_S - 1) / HT_S, q->nh / HT_K);
+  k_hy_spec_t<<<grid, HT_TB, 0, p->stream>>>(static_cast<const float2*>(p->spec), p->sg, q->nh,
+                                             p->S, q->specT, q->hamax + 1, q->hamax);
+  PHLK(cudaGetLastError());
+  XformTc x = q->xf_inv;
+  x.epi = inv_mode == HY_INV_SET ? XTC_UDF_SET : XTC_UDF_ADD;
+  PHLK(launch_xform_tc(x, p->dflag, p->stream));
+  return PD_OK;
+}
+
 // one pass of eq. 2.7 on the residual buffer; the update mode of step (c)
 pd_status pass(pdh_plan* q, double* u, int inv_mode) {
-  pd_status s = gemm(q, gemm_fwd(q), HY_FWD);
+  pd_status s = time_fwd(q);
   if (s != PD_OK) return s;
   s = step_b(q);
   if (s != PD_OK) return s;
-  return gemm(q, gemm_inv(q, u), inv_mode);
+  return time_inv(q, u, inv_mode);
+}
+
+// FP16 two-term split of the real operator rows G[n][k] (n < N, k < K) padded
+// to P x P, uploaded as hi, lo
+pd_status upload_split(pdh_plan* q, const std::vector<double>& G, int N, int K, size_t P,
+                       void** hi, void** lo, float* g_inv) {
+  std::vector<float> Gp(P * P, 0.f);
+  for (int n = 0; n < N; ++n)
+    for (int k = 0; k < K; ++k) Gp[(size_t)n * P + k] = (float)G[(size_t)n * K + k];
+  std::vector<uint16_t> h, l;
+  *g_inv = xform_tc_split(Gp, h, l);
+  PHCU(cudaMalloc(hi, P * P * 2));
+  PHCU(cudaMalloc(lo, P * P * 2));
+  PHCU(cudaMemcpy(*hi, h.data(), P * P * 2, cudaMemcpyHostToDevice));
+  PHCU(cudaMemcpy(*lo, l.data(), P * P * 2, cudaMemcpyHostToDevice));
+  return PD_OK;
+}
+
+// the tensor-core operands and launches of a mixed first-order plan
+pd_status setup_tc(pdh_plan* q, const std::vector<double>& Af, const std::vector<double>& Ai) {
+  const pd_plan* p = q->sp;
+  const int nt = q->nt, nh = q->nh;
+  const size_t P = xform_tc_bpad(nt / 2);
+  float gf = 1.f, gi = 1.f;
+  pd_status s = upload_split(q, Af, 2 * nh, nt, P, &q->Gtc[0], &q->Gtc[1], &gf);
+  if (s == PD_OK) s = upload_split(q, Ai, nt, 2 * nh, P, &q->Gtc[2], &q->Gtc[3], &gi);
+  if (s != PD_OK) return s;
+  // A operands in whole blocks of 128 points (see xform_tc_prepare_blocked)
+  const size_t spad = (size_t)(p->S + 127) / 128 * 128;
+  PHCU(cudaMalloc((void**)&q->specT, spad * nh * sizeof(float2)));
+  PHCU(cudaMalloc((void**)&q->hamax, 2 * sizeof(unsigned)));
+  PHCU(cudaMemset(q->hamax, 0, 2 * sizeof(unsigned)));
+  PHCU(xform_tc_prepare_blocked(&q->xf_fwd, p->S, nt, static_cast<const float*>(q->r), q->Gtc[0],
+                                q->Gtc[1], gf, q->hamax));
+  PHCU(xform_tc_prepare_blocked(&q->xf_inv, p->S, nt, reinterpret_cast<const float*>(q->specT),
+                                q->Gtc[2], q->Gtc[3], gi, q->hamax + 1));
+  XformTc* xs[2] = {&q->xf_fwd, &q->xf_inv};
+  for (XformTc* x : xs) {
+    x->specS = p->sg.specS;
+    x->sx_nx = p->sg.nx;
+    x->sx_nxp = p->sg.nxp;
+    x->flag = p->dflag;
+  }
+  q->xf_fwd.epi = XTC_SPEC;
+  q->xf_fwd.spec = static_cast<float2*>(p->spec);
+  if (p->xform_tc) {
+    q->xf_fwd.spec_amax = p->amax;
+    q->xf_fwd.spec_amax_reset = p->amax + 1;
+  }
+  q->xf_inv.epi = XTC_UDF_ADD;
+  q->xf_inv.Udf = q->Udf;
+  q->tc_ok = q->tc = true;
+  return PD_OK;
 }
 
 }  // namespace
@@ -931,13 +1139,17 @@ pd_status pdh_create_impl(const pd_space* sp, int nt, double dt, int precision, 
   s = q->fp64 ? upload_real<double>(q, &q->Af, AfT) : upload_real<float>(q, &q->Af, AfT);
   if (s == PD_OK) s = q->fp64 ? upload_real<double>(q, &q->Ai, AiT) : upload_real<float>(q, &q->Ai, AiT);
   if (s == PD_OK) {
-    cudaError_t e = cudaMalloc(&q->r, ns * (q->fp64 ? sizeof(double) : sizeof(float)));
+    // mixed: room for r^T in whole blocks of 128 points (tensor-core layout)
+    const size_t nr = q->fp64 ? ns : (size_t)nt * ((q->sp->S + 127) / 128 * 128);
+    cudaError_t e = cudaMalloc(&q->r, nr * (q->fp64 ? sizeof(double) : sizeof(float)));
     if (e == cudaSuccess && !q->fp64) e = cudaMalloc((void**)&q->Udf, ns * sizeof(float2));
     if (e == cudaSuccess && !q->fp64) e = cudaMalloc((void**)&q->Bdf, ns * sizeof(float2));
     if (e == cudaSuccess) e = cudaMalloc((void**)&q->dnorm, 2 * sizeof(double));
     if (e == cudaSuccess) e = cudaMallocHost((void**)&q->hnorm, 2 * sizeof(double) + sizeof(int));
     if (e != cudaSuccess) s = ph_cuda(q, e, "allocation");
   }
+  if (s == PD_OK && order == 1 && !q->fp64 && nt % 16 == 0 && nt >= 32 && q->sp->S >= 128)
+    s = setup_tc(q, Af, Ai);
   if (s == PD_OK && order == 2) {
     // B^2 (dt B = Bh: rows (-1/2, 0, 1/2), last row (-1, 1)) as integer
     // weights of 1/(4 dt^2) at offsets -2..2, and Bh[0][0], Bh[1][0]
@@ -1034,6 +1246,7 @@ pd_status pdh_solve(pdh_plan* q, const double* b, double* u, double tol, int max
   const bool fp64 = q->fp64;
   PHCU(cudaMemsetAsync(q->dnorm, 0, 2 * sizeof(double), st));
   PHCU(cudaMemsetAsync(p->dflag, 0, sizeof(int), st));
+  if (q->hamax) PHCU(cudaMemsetAsync(q->hamax, 0, 2 * sizeof(unsigned), st));
   HResid ra = resid_args(q);
   ra.b64 = b;
   ra.u64 = u;
@@ -1054,6 +1267,10 @@ pd_status pdh_solve(pdh_plan* q, const double* b, double* u, double tol, int max
     PHCU(cudaStreamSynchronize(st));
     const double nb = std::sqrt(q->hnorm[0]);
     rel = nb > 0.0 ? std::sqrt(q->hnorm[1]) / nb : std::sqrt(q->hnorm[1]);
+    if (*q->hflag & 2) {
+      if (refinements) *refinements = done;
+      return ph_err(q, PD_ERR_CUDA, "a tensor-core wait timed out (pipeline stalled)");
+    }
     if (*q->hflag != 0 || !std::isfinite(rel)) {
       if (refinements) *refinements = done;
       if (relres) *relres = rel;
@@ -1078,6 +1295,7 @@ pd_status pdh_profile_sweep(pdh_plan* q, const double* b, double* u, int reps, f
   pd_plan* p = q->sp;
   cudaStream_t st = p->stream;
   const bool fp64 = q->fp64;
+  if (q->hamax) PHCU(cudaMemsetAsync(q->hamax, 0, 2 * sizeof(unsigned), st));
   HResid ra = resid_args(q);
   ra.b64 = b;
   ra.u64 = u;
@@ -1093,13 +1311,13 @@ pd_status pdh_profile_sweep(pdh_plan* q, const double* b, double* u, int reps, f
     PHCU(cudaEventRecord(ev[0], st));
     PHLK(launch_resid(ra, HY_RESID, fp64, st));
     PHCU(cudaEventRecord(ev[1], st));
-    s = gemm(q, gemm_fwd(q), HY_FWD);
+    s = time_fwd(q);
     if (s != PD_OK) return s;
     PHCU(cudaEventRecord(ev[2], st));
     s = step_b(q);
     if (s != PD_OK) return s;
     PHCU(cudaEventRecord(ev[3], st));
-    s = gemm(q, gemm_inv(q, u), HY_INV_ADD);
+    s = time_inv(q, u, HY_INV_ADD);
     if (s != PD_OK) return s;
     PHCU(cudaEventRecord(ev[4], st));
     PHCU(cudaEventSynchronize(ev[4]));
@@ -1123,5 +1341,19 @@ pd_status pdh_launches(const pdh_plan* q, unsigned long long* count) {
 }
 
 const char* pdh_last_error(const pdh_plan* q) { return q ? q->msg : "null plan"; }
+
+pd_status pdh_set_tensor_cores(pdh_plan* q, int on) {
+  if (!q) return PD_ERR_ARG;
+  if (on && !q->tc_ok) return ph_err(q, PD_ERR_UNSUPPORTED, "plan has no tensor-core time contractions");
+  PHCU(cudaStreamSynchronize(q->sp->stream));
+  q->tc = on != 0;
+  return PD_OK;
+}
+
+pd_status pdh_tensor_cores(const pdh_plan* q, int* on) {
+  if (!q || !on) return PD_ERR_ARG;
+  *on = q->tc ? 1 : 0;
+  return PD_OK;
+}
 
 }  // extern "C"

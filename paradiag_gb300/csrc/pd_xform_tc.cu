@@ -96,6 +96,15 @@ __device__ __forceinline__ void mbar_drain(uint32_t bar, uint32_t phase) {
     if (mbar_try(bar, phase)) return;
 }
 
+__device__ __forceinline__ void tma_load_4d(uint32_t dst, const CUtensorMap* map, int c0, int c1,
+                                            int c2, int c3, uint32_t bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.4d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, "
+      "%3, %4, %5}], [%6];" ::"r"(dst),
+      "l"(map), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(bar)
+      : "memory");
+}
+
 __device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map, int c0, int c1,
                                             uint32_t bar) {
   asm volatile(
@@ -163,11 +172,23 @@ __device__ __forceinline__ void split8(const float* v, float s, uint4& hi, uint4
   lo = make_uint4(l[0], l[1], l[2], l[3]);
 }
 
+// epilogue targets of the time contractions (XformTc, modes XTC_SPEC / XTC_UDF_*)
+struct XtcEpi {
+  int a_blocked;    // A in 128 x 16 blocks (xform_tc_prepare_blocked), loaded by a 4D map
+  SpecGeom sg;
+  float2* spec;
+  unsigned* spec_amax;
+  unsigned* spec_amax_reset;
+  float2* Udf;
+  int* flag;
+};
+
+template <int EPI>
 __global__ void __launch_bounds__(NTHREADS, 1)
     k_xform_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmBhi,
                const __grid_constant__ CUtensorMap tmBlo, float* __restrict__ out, int rows,
                int ncols, int ldo, int kchunks, int nblk_n, int ntiles,
-               const unsigned* __restrict__ amax_bits, float g_inv, int* err) {
+               const unsigned* __restrict__ amax_bits, float g_inv, int* err, const XtcEpi ep) {
   extern __shared__ __align__(1024) unsigned char smraw[];
   // 1024-byte aligned operand stages (the swizzle patterns repeat every 512 bytes)
   unsigned char* base = (unsigned char*)(((uintptr_t)smraw + 1023) & ~(uintptr_t)1023);
@@ -232,8 +253,14 @@ __global__ void __launch_bounds__(NTHREADS, 1)
           }
           const uint32_t fb = smem_u32(&bar_full[s]);
           mbar_expect_tx(fb, (uint32_t)(A_BYTES + 2 * B_BYTES));
-          tma_load_2d(smem_u32(stage_ptr(s, 0)), &tmA, c * KH, r0, fb);
-          tma_load_2d(smem_u32(stage_ptr(s, 1)), &tmA, c * KH + AF_BOX, r0, fb);
+          if (ep.a_blocked) {
+            // blocks (k / 16, row / 128) of 128 rows x 16 floats, contiguous
+            tma_load_4d(smem_u32(stage_ptr(s, 0)), &tmA, 0, 0, 2 * c, r0 / BM, fb);
+            tma_load_4d(smem_u32(stage_ptr(s, 1)), &tmA, 0, 0, 2 * c + 1, r0 / BM, fb);
+          } else {
+            tma_load_2d(smem_u32(stage_ptr(s, 0)), &tmA, c * KH, r0, fb);
+            tma_load_2d(smem_u32(stage_ptr(s, 1)), &tmA, c * KH + AF_BOX, r0, fb);
+          }
           tma_load_2d(smem_u32(stage_ptr(s, 2)), &tmBhi, c * KH, n0, fb);
           tma_load_2d(smem_u32(stage_ptr(s, 3)), &tmBlo, c * KH, n0, fb);
         }
@@ -317,6 +344,11 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     // hold rows r0 + that range of the tile
     const float oscale = g_inv / sa;  // exact: both are powers of two
     const int q4 = warp & 3;
+    float amx = 0.f;                  // XTC_SPEC: max |D| over this thread's outputs
+    bool bad = false;                 // XTC_UDF_*: a non-finite increment
+    if constexpr (EPI == XTC_SPEC) {
+      if (blockIdx.x == 0 && warp == 6 && lane == 0 && ep.spec_amax_reset) *ep.spec_amax_reset = 0u;
+    }
     for (int i = 0; i < my_tiles; ++i) {
       const int ab = i & 1;
       const uint32_t v2 = (uint32_t)(i >> 1);
@@ -325,7 +357,24 @@ __global__ void __launch_bounds__(NTHREADS, 1)
       const int T = blockIdx.x + i * gridDim.x;
       const int r0 = (T / nblk_n) * BM, n0 = (T % nblk_n) * BN;
       const int row = r0 + q4 * 32 + lane;
+      // XTC_UDF_ADD: the iterate of the next 16 columns is loaded before the
+      // current ones are stored, so that 16 to 32 loads per thread are in flight
+      float2 cur[16], nxt[16];
+      if constexpr (EPI == XTC_UDF_ADD) {
+#pragma unroll
+        for (int u = 0; u < 16; ++u)
+          cur[u] = (row < rows && n0 + u < ncols) ? ep.Udf[(size_t)(n0 + u) * rows + row]
+                                                  : make_float2(0.f, 0.f);
+      }
       for (int j = 0; j < BN; j += 16) {
+        if constexpr (EPI == XTC_UDF_ADD) {
+#pragma unroll
+          for (int u = 0; u < 16; ++u) {
+            const int nn = n0 + j + 16 + u;
+            nxt[u] = (j + 16 < BN && row < rows && nn < ncols)
+                         ? ep.Udf[(size_t)nn * rows + row] : make_float2(0.f, 0.f);
+          }
+        }
         uint32_t v[16];
         const uint32_t taddr = tmem + ((uint32_t)(q4 * 32) << 16) + (uint32_t)(ab * BN + j);
         asm volatile(
@@ -337,7 +386,8 @@ __global__ void __launch_bounds__(NTHREADS, 1)
             : "r"(taddr));
         asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
         const int n = n0 + j;
-        if (row < rows) {
+        if (row >= rows) continue;
+        if constexpr (EPI == XTC_ROWS) {
           float* o = out + (size_t)row * ldo + n;
           if (n + 16 <= ncols) {
 #pragma unroll
@@ -350,12 +400,51 @@ __global__ void __launch_bounds__(NTHREADS, 1)
             for (int u = 0; u < 16; ++u)
               if (n + u < ncols) o[u] = __uint_as_float(v[u]) * oscale;
           }
+        } else if constexpr (EPI == XTC_SPEC) {
+          // row = spatial point s; columns n, n + 1 = (re, im) of spectrum row n / 2
+          // (n even): the lanes of a warp write consecutive points of one row
+          const size_t off = spec_index(ep.sg, 0, row);
+#pragma unroll
+          for (int u = 0; u < 8; ++u) {
+            if (n + 2 * u >= ncols) break;
+            const float re = __uint_as_float(v[2 * u]) * oscale;
+            const float im = __uint_as_float(v[2 * u + 1]) * oscale;
+            ep.spec[(size_t)((n >> 1) + u) * ep.sg.specS + off] = make_float2(re, im);
+            amx = fmaxf(amx, fmaxf(fabsf(re), fabsf(im)));
+          }
+        } else {
+          // row = spatial point s, column = time level: Udf[(n + u) rows + s]
+#pragma unroll
+          for (int u = 0; u < 16; ++u) {
+            if (n + u >= ncols) break;
+            const float d = __uint_as_float(v[u]) * oscale;
+            bad |= !isfinite(d);
+            float2* up = ep.Udf + (size_t)(n + u) * rows + row;
+            if constexpr (EPI == XTC_UDF_SET) {
+              *up = make_float2(d, 0.f);
+            } else {
+              const float2 uo = cur[u];
+              df t = two_sum(uo.x, d);
+              t = fast_two_sum(t.hi, t.lo + uo.y);
+              *up = make_float2(t.hi, t.lo);
+            }
+          }
+          if constexpr (EPI == XTC_UDF_ADD) {
+#pragma unroll
+            for (int u = 0; u < 16; ++u) cur[u] = nxt[u];
+          }
         }
       }
       // this warp's reads of accumulator ab are complete: hand it back
       asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
       __syncwarp();
       if (lane == 0) mbar_arrive(smem_u32(&bar_acce[ab]));
+    }
+    if constexpr (EPI == XTC_SPEC) {
+      for (int o = 16; o > 0; o >>= 1) amx = fmaxf(amx, __shfl_xor_sync(0xffffffffu, amx, o));
+      if (lane == 0 && ep.spec_amax) atomicMax(ep.spec_amax, __float_as_uint(amx));
+    } else if constexpr (EPI == XTC_UDF_SET || EPI == XTC_UDF_ADD) {
+      if (__any_sync(0xffffffffu, bad) && lane == 0 && ep.flag) atomicOr(ep.flag, 1);
     }
   }
 
@@ -450,12 +539,52 @@ cudaError_t xform_tc_prepare(XformTc* x, int rows, int nx, int ldo_floats, const
   return cudaSuccess;
 }
 
+template <int EPI>
+cudaError_t launch_epi(const XformTc& x, int* err, cudaStream_t st, int grid, int ntiles,
+                       size_t smem) {
+  cudaError_t e =
+      cudaFuncSetAttribute(k_xform_tc<EPI>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  if (grid == 0) return cudaSuccess;
+  XtcEpi ep;
+  ep.a_blocked = x.a_blocked;
+  ep.sg.specS = x.specS;
+  ep.sg.nx = x.sx_nx;
+  ep.sg.nxp = x.sx_nxp;
+  ep.spec = x.spec;
+  ep.spec_amax = x.spec_amax;
+  ep.spec_amax_reset = x.spec_amax_reset;
+  ep.Udf = x.Udf;
+  ep.flag = x.flag;
+  k_xform_tc<EPI><<<grid, NTHREADS, smem, st>>>(x.tmA, x.tmBhi, x.tmBlo, x.out, x.rows, x.ncols,
+                                                x.ldo, x.kchunks, x.nblk_n, ntiles, x.amax,
+                                                x.g_inv, err, ep);
+  return cudaGetLastError();
+}
+
+cudaError_t xform_tc_prepare_blocked(XformTc* x, int rows, int K, const float* in,
+                                     const void* Ghi, const void* Glo, float g_inv,
+                                     const unsigned* amax) {
+  if (K % 16 != 0 || K < 32) return cudaErrorInvalidValue;
+  cudaError_t e = xform_tc_prepare(x, rows, K / 2, K, in, nullptr, Ghi, Glo, g_inv, amax);
+  if (e != cudaSuccess) return e;
+  EncodeTiledFn fn = encode_fn();
+  if (!fn) return cudaErrorInvalidValue;
+  const uint64_t rblk = (uint64_t)(rows + BM - 1) / BM;
+  const cuuint64_t dims[4] = {16, (cuuint64_t)BM, (cuuint64_t)(K / 16), rblk};
+  const cuuint64_t strides[3] = {16 * 4, (cuuint64_t)BM * 16 * 4, (cuuint64_t)(K / 16) * BM * 16 * 4};
+  const cuuint32_t box[4] = {16, (cuuint32_t)BM, 1, 1};
+  const cuuint32_t estr[4] = {1, 1, 1, 1};
+  if (fn(&x->tmA, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, const_cast<float*>(in), dims, strides, box,
+         estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B,
+         CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+    return cudaErrorInvalidValue;
+  x->a_blocked = 1;
+  return cudaSuccess;
+}
+
 cudaError_t launch_xform_tc(const XformTc& x, int* err, cudaStream_t st) {
   const size_t smem = (size_t)STAGES * STAGE_BYTES + 1024 + GUARD_BYTES;
-  cudaError_t e =
-      cudaFuncSetAttribute(k_xform_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (e != cudaSuccess) return e;
-  if (x.rows == 0) return cudaSuccess;
   // persistent: one CTA per SM over all tiles
   static int nsm = 0;
   if (nsm == 0) {
@@ -466,7 +595,11 @@ cudaError_t launch_xform_tc(const XformTc& x, int* err, cudaStream_t st) {
   }
   const int ntiles = x.nblk_n * ((x.rows + BM - 1) / BM);
   const int grid = ntiles < nsm ? ntiles : nsm;
-  k_xform_tc<<<grid, NTHREADS, smem, st>>>(x.tmA, x.tmBhi, x.tmBlo, x.out, x.rows, x.ncols, x.ldo,
-                                           x.kchunks, x.nblk_n, ntiles, x.amax, x.g_inv, err);
-  return cudaGetLastError();
+  switch (x.epi) {
+    case XTC_ROWS: return launch_epi<XTC_ROWS>(x, err, st, grid, ntiles, smem);
+    case XTC_SPEC: return launch_epi<XTC_SPEC>(x, err, st, grid, ntiles, smem);
+    case XTC_UDF_SET: return launch_epi<XTC_UDF_SET>(x, err, st, grid, ntiles, smem);
+    case XTC_UDF_ADD: return launch_epi<XTC_UDF_ADD>(x, err, st, grid, ntiles, smem);
+    default: return cudaErrorInvalidValue;
+  }
 }

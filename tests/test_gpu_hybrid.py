@@ -40,7 +40,16 @@ CASES = {
     "1d_nt300_127": HP(nx=127, nu=1e-2, ax=1.0, nt=300, T=1.0),
     "2d_xper_33x20x40": HP(dim=2, nx=33, ny=20, nu=1e-2, ax=1.0, ay=0.5, bcx=W.PERIODIC, nt=40),
     "2d_xdir_17x15x9": HP(dim=2, nx=17, ny=15, nu=0.05, ay=0.3, nt=9),
+    # tensor-core time contractions: K = Nt of 304 (ragged K chunk, two N
+    # blocks), 131 points (ragged row block); 2D Dirichlet x with Nt = 64
+    "1d_nt304_131": HP(nx=131, nu=1e-2, ax=1.0, nt=304, T=1.0),
+    "2d_xdir_17x9x64": HP(dim=2, nx=17, ny=9, nu=0.05, ay=0.3, nt=64),
 }
+
+# cases whose mixed plan runs steps (a) and (c) on the tensor cores (mixed,
+# Nt a multiple of 16 and at least 32, at least 128 spatial points)
+TC_CASES = sorted(n for n, pb in CASES.items()
+                  if pb.nt % 16 == 0 and pb.nt >= 32 and pb.space.size >= 128)
 
 
 @pytest.fixture(scope="module")
@@ -48,9 +57,12 @@ def pd():
     return lib_ready()
 
 
-def make(pb, precision):
+def make(pb, precision, tc=None):
     import paradiag_gb300 as pd
-    return pd.PlanHybrid(space_dict(pb.space), pb.nt, pb.dt, precision)
+    plan = pd.PlanHybrid(space_dict(pb.space), pb.nt, pb.dt, precision)
+    if tc is not None:
+        plan.set_tensor_cores(tc)
+    return plan
 
 
 def data(pb, seed):
@@ -127,6 +139,48 @@ def test_hybrid_refined_matches_exact(pd, name, prec):
     plan.close()
 
 
+def test_hybrid_tensor_core_engine_selection(pd):
+    import paradiag_gb300 as lib
+    assert TC_CASES == ["1d_nt304_131", "1d_periodic_paper_256x64", "2d_xdir_17x9x64"]
+    for name, pb in CASES.items():
+        plan = make(pb, PD_MIXED)
+        assert plan.tensor_cores == (name in TC_CASES)
+        if name not in TC_CASES:
+            with pytest.raises(lib.PDError) as e:
+                plan.set_tensor_cores(True)
+            assert e.value.status == lib.PD_ERR_UNSUPPORTED
+        plan.set_tensor_cores(False)
+        assert not plan.tensor_cores
+        plan.close()
+        p64 = make(pb, PD_FP64)
+        assert not p64.tensor_cores
+        p64.close()
+
+
+@pytest.mark.parametrize("name", TC_CASES)
+def test_hybrid_tensor_core_and_cuda_core_engines_agree(pd, name):
+    """Direct mixed solves with either engine of the time contractions: both
+    within the FP32 bound of the exact solution, and within twice that bound
+    of each other; refined with either engine to the same residual."""
+    pb = CASES[name]
+    u0, f = data(pb, W.SEED_BASE + 305)
+    b = H.build_rhs(pb, u0, f)
+    exact = H.solve_exact(pb, b)
+    scale = np.abs(exact).max()
+    bound = 8 * pb.nt * EPS32 * cond_v(pb) * scale
+    out = {}
+    for tc in (True, False):
+        plan = make(pb, PD_MIXED, tc)
+        u, _, _ = plan.solve(dev(b))
+        out[tc] = host(u)
+        assert np.abs(out[tc] - exact).max() <= bound, tc
+        u, it, rel = plan.solve(dev(b), tol=1e-13, max_refine=20)
+        assert rel <= 1e-13
+        assert np.abs(host(u) - exact).max() <= 1e-10 * scale
+        plan.close()
+    assert np.abs(out[True] - out[False]).max() <= 2 * bound
+
+
 @pytest.mark.parametrize("name", ["1d_dirichlet_adv_31x16", "1d_periodic_paper_256x64",
                                   "2d_xper_33x20x40", "1d_nt1"])
 def test_hybrid_apply_A_and_rhs_match_oracle(pd, name):
@@ -153,6 +207,7 @@ def test_hybrid_full_size_window(pd):
     pb = wl.problem
     plan = make(pb, PD_MIXED)
     bd = plan.build_rhs(dev(wl.u0))
+    assert plan.tensor_cores
     u, it, rel = plan.solve(bd, tol=1e-12, max_refine=20)
     assert rel <= 1e-12
     r = bd - plan.apply_A(u)
