@@ -100,6 +100,17 @@ PD_API pd_status pd_plan_workspace(const pd_plan* plan, unsigned long long* byte
 /* z = P_alpha^{-1} r (eq. 1.3, steps (a)-(c)); r, z: [Nt][S] device FP64. */
 PD_API pd_status pd_apply_precond(pd_plan* plan, const double* r, double* z);
 
+/* Testing aid (no paper counterpart): pd_apply_precond with the first thread
+ * block of the forward tensor-core x-transform withholding all its operand
+ * loads, so that its consumers' bounded waits run out (after 2^16 polls in
+ * this launch).  That block then waits for the work it had issued, frees its
+ * tensor memory and raises bit 1 of the plan's device flag; the call waits for
+ * the stream and returns PD_ERR_CUDA ("... timed out") with z undefined, and
+ * clears the flag, so that the plan stays usable.  PD_ERR_UNSUPPORTED on plans
+ * without the tensor-core x-transform (1D, FP64, fewer than 16 x points or
+ * 128 spectrum rows). */
+PD_API pd_status pd_debug_xform_timeout(pd_plan* plan, const double* r, double* z);
+
 /* r = b - A u (eq. 5.1); b, u, r: [Nt][S] device FP64, computed in FP64. */
 PD_API pd_status pd_residual(pd_plan* plan, const double* b, const double* u, double* r);
 

@@ -51,6 +51,7 @@ _SIGS = {
     "pd_plan_destroy": (ctypes.c_int, [_P]),
     "pd_plan_workspace": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_ulonglong)]),
     "pd_apply_precond": (ctypes.c_int, [_P, _P, _P]),
+    "pd_debug_xform_timeout": (ctypes.c_int, [_P, _P, _P]),
     "pd_residual": (ctypes.c_int, [_P, _P, _P, _P]),
     "pd_apply_A": (ctypes.c_int, [_P, _P, _P]),
     "pd_apply_AT": (ctypes.c_int, [_P, _P, _P]),
@@ -253,6 +254,10 @@ def pd_batch_uses_graph(batch):
 
 def pd_apply_precond(plan, r, z):
     return load().pd_apply_precond(plan, r, z)
+
+
+def pd_debug_xform_timeout(plan, r, z):
+    return load().pd_debug_xform_timeout(plan, r, z)
 
 
 def pd_apply_precond_noalloc(space, nt, dt, alpha, scheme, theta, r, z, stream):

@@ -1464,6 +1464,20 @@ pd_status pd_apply_precond(pd_plan* p, const double* r, double* z) {
   return precond_into(p, r, z);
 }
 
+pd_status pd_debug_xform_timeout(pd_plan* p, const double* r, double* z) {
+  if (!p || !r || !z) return set_err(p, PD_ERR_ARG, "null argument");
+  if (!p->xform || !p->xform_tc) return set_err(p, PD_ERR_UNSUPPORTED, "no tensor-core x-transform");
+  CU(cudaMemsetAsync(p->dflag, 0, sizeof(int), p->stream));
+  p->xtc_fwd.stall_chunk = 0;
+  const pd_status s = precond_into(p, r, z);
+  p->xtc_fwd.stall_chunk = -1;
+  if (s != PD_OK) return s;
+  CHK(sync_scalars(p, 0));
+  CU(cudaMemsetAsync(p->dflag, 0, sizeof(int), p->stream));
+  CU(cudaStreamSynchronize(p->stream));
+  return flag_value(p) != 0 ? flag_status(p) : PD_OK;
+}
+
 pd_status pd_residual(pd_plan* p, const double* b, const double* u, double* r) {
   if (!p || !b || !u || !r) return set_err(p, PD_ERR_ARG, "null argument");
   CU(launch_apply_A(p->st, p->tb, p->nt, u, b, r, nullptr, 0, p->stream));

@@ -80,8 +80,9 @@ __device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t phase) {
   return ok != 0;
 }
 // bounded wait; returns false (and raises the CTA abort flag) on timeout
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t phase, volatile int* abort_flag) {
-  for (long long i = 0; i < WAIT_LIMIT; ++i) {
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t phase, volatile int* abort_flag,
+                                          long long limit) {
+  for (long long i = 0; i < limit; ++i) {
     if (mbar_try(bar, phase)) return true;
     if ((i & 255) == 255 && *abort_flag) return false;
   }
@@ -175,6 +176,8 @@ __device__ __forceinline__ void split8(const float* v, float s, uint4& hi, uint4
 // epilogue targets of the time contractions (XformTc, modes XTC_SPEC / XTC_UDF_*)
 struct XtcEpi {
   int a_blocked;    // A in 128 x 16 blocks (xform_tc_prepare_blocked), loaded by a 4D map
+  int stall_chunk;  // testing aid: CTA 0 issues no loads from this chunk on (-1: none)
+  long long wait_limit;   // iterations of a bounded mbarrier wait
   SpecGeom sg;
   float2* spec;
   unsigned* spec_amax;
@@ -247,7 +250,13 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         for (int c = 0; c < kchunks; ++c, ++g) {
           const int s = g % STAGES;
           const uint32_t u = (uint32_t)(g / STAGES);
-          if (g >= STAGES && !mbar_wait(smem_u32(&bar_empty[s]), (u & 1u) ^ 1u, abortp)) {
+          if (blockIdx.x == 0 && g == ep.stall_chunk) {
+            // withheld: nothing of this chunk is in flight, so the consumers'
+            // bounded waits run out and the CTA takes its abort path
+            ok = false;
+            break;
+          }
+          if (g >= STAGES && !mbar_wait(smem_u32(&bar_empty[s]), (u & 1u) ^ 1u, abortp, ep.wait_limit)) {
             ok = false;
             break;
           }
@@ -277,7 +286,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
       for (int i = 0; i < my_tiles && ok; ++i) {
         const int ab = i & 1;
         const uint32_t v = (uint32_t)(i >> 1);
-        if (i >= 2 && !mbar_wait(smem_u32(&bar_acce[ab]), (v & 1u) ^ 1u, abortp)) {
+        if (i >= 2 && !mbar_wait(smem_u32(&bar_acce[ab]), (v & 1u) ^ 1u, abortp, ep.wait_limit)) {
           ok = false;
           break;
         }
@@ -286,7 +295,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         for (int c = 0; c < kchunks; ++c, ++g) {
           const int s = g % STAGES;
           const uint32_t u = (uint32_t)(g / STAGES);
-          if (!mbar_wait(smem_u32(&bar_split[s]), u & 1u, abortp)) { ok = false; break; }
+          if (!mbar_wait(smem_u32(&bar_split[s]), u & 1u, abortp, ep.wait_limit)) { ok = false; break; }
           asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
           const uint32_t ahi = smem_u32(stage_ptr(s, 0)), alo = smem_u32(stage_ptr(s, 1));
           const uint32_t bhi = smem_u32(stage_ptr(s, 2)), blo = smem_u32(stage_ptr(s, 3));
@@ -316,7 +325,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     for (int g = 0; g < nchunks; ++g) {
       const int s = g % STAGES;
       const uint32_t u = (uint32_t)(g / STAGES);
-      if (!mbar_wait(smem_u32(&bar_full[s]), u & 1u, abortp)) break;
+      if (!mbar_wait(smem_u32(&bar_full[s]), u & 1u, abortp, ep.wait_limit)) break;
       unsigned char* a0 = stage_ptr(s, 0) + t * 64;  // row t of box 0 / of A_hi
       unsigned char* a1 = stage_ptr(s, 1) + t * 64;  // row t of box 1 / of A_lo
       // the whole row (32 FP32 values) into registers before it is overwritten
@@ -352,7 +361,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     for (int i = 0; i < my_tiles; ++i) {
       const int ab = i & 1;
       const uint32_t v2 = (uint32_t)(i >> 1);
-      if (!mbar_wait(smem_u32(&bar_accf[ab]), v2 & 1u, abortp)) break;
+      if (!mbar_wait(smem_u32(&bar_accf[ab]), v2 & 1u, abortp, ep.wait_limit)) break;
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
       const int T = blockIdx.x + i * gridDim.x;
       const int r0 = (T / nblk_n) * BM, n0 = (T % nblk_n) * BN;
@@ -548,6 +557,8 @@ cudaError_t launch_epi(const XformTc& x, int* err, cudaStream_t st, int grid, in
   if (grid == 0) return cudaSuccess;
   XtcEpi ep;
   ep.a_blocked = x.a_blocked;
+  ep.stall_chunk = x.stall_chunk;
+  ep.wait_limit = x.stall_chunk >= 0 ? (1LL << 16) : WAIT_LIMIT;
   ep.sg.specS = x.specS;
   ep.sg.nx = x.sx_nx;
   ep.sg.nxp = x.sx_nxp;

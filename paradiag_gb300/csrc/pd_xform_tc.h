@@ -27,6 +27,10 @@ struct XformTc {
   //                of *flag).
   int epi = 0;
   int a_blocked = 0;      // A in blocks (xform_tc_prepare_blocked)
+  // testing aid: CTA 0 withholds the loads of this chunk (its g-th K chunk)
+  // and all later ones, with bounded waits of 2^16 polls, so that its
+  // consumers time out and the launch reports bit 1 in *err (-1: off)
+  int stall_chunk = -1;
   int specS = 0, sx_nx = 1, sx_nxp = 1;
   float2* spec = nullptr;
   unsigned* spec_amax = nullptr;
