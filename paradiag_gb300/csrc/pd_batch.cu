@@ -40,8 +40,8 @@ struct pd_batch {
   FwdArgs* d_fwd = nullptr;
   InvArgs* d_inv = nullptr;
   TriArgs* d_tri = nullptr;
-  // time-kernel work, one persistent launch per class of tile footprint
-  // (complex elements per thread: 4, 8 or 16)
+  // time-kernel work, one launch per class of tile footprint (complex
+  // elements per thread: 4, 8 or 16), one block per tile of the work table
   struct TimeClass {
     int ept = 0;
     size_t smem_fwd = 0, smem_inv = 0;
