@@ -217,6 +217,18 @@ def cpu_info():
     except OSError:
         pass
     if model is None:
+        # Arm hosts: /proc/cpuinfo names only the part number; lscpu names the core
+        try:
+            import subprocess
+            out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+            info = dict(l.split(":", 1) for l in out.splitlines() if ":" in l)
+            name = info.get("Model name", "").strip()
+            vendor = info.get("Vendor ID", "").strip()
+            if name:
+                model = f"{vendor} {name}".strip()
+        except (OSError, ValueError, subprocess.SubprocessError):
+            pass
+    if model is None:
         import platform
         model = platform.processor() or platform.machine()
     return os.cpu_count() or 1, model
@@ -958,8 +970,9 @@ def wave_gmres_leg(pd, torch, dev, args):
     leap-frog (eq. 3.2b), Nt = 1024, T = 2, u0 = exp(-100 (x - 1/2)^2), u_t(0) = 0;
     FGMRES(30) right-preconditioned by P_alpha, alpha = 0.1, FP64 Krylov
     vectors, to a relative residual of 1e-10 from a zero guess (Section 3; Table
-    T4A reports 3 iterations at alpha = 0.1).  Both plans (FP32 or FP64
-    preconditioner); error against the oracle's sequential stepping."""
+    T4A reports 3 iterations at alpha = 0.1), and to 1e-12, which brings the
+    error below 1e-10.  Both plans (FP32 or FP64 preconditioner); error against
+    the oracle's sequential stepping."""
     import numpy as np
     import workloads as W
     from oracle import operators as O
@@ -983,8 +996,17 @@ def wave_gmres_leg(pd, torch, dev, args):
             torch, stream,
             lambda: plan.solve(b, u.zero_(), mode=pd.PD_GMRES, tol=1e-10, maxit=60, restart=30), k)
         err = float(np.linalg.norm(u.cpu().numpy() - uref) / np.linalg.norm(uref))
+        # the same solve to 1e-12: the leap-frog system amplifies the residual
+        # about tenfold into the error, so this is the solve that meets 1e-10
+        ms12, (_, it12, rel12) = timed_solves(
+            torch, stream,
+            lambda: plan.solve(b, u.zero_(), mode=pd.PD_GMRES, tol=1e-12, maxit=60, restart=30), k)
+        err12 = float(np.linalg.norm(u.cpu().numpy() - uref) / np.linalg.norm(uref))
         out[tag] = {"ms_per_solve": ms, "value": pb.unknowns / (ms / 1e3), "unit": UNIT,
-                    "gmres_iterations": it, "relres": rel, "error_vs_oracle": err}
+                    "gmres_iterations": it, "relres": rel, "error_vs_oracle": err,
+                    "tol_1e-12": {"ms_per_solve": ms12, "value": pb.unknowns / (ms12 / 1e3),
+                                  "gmres_iterations": it12, "relres": rel12,
+                                  "error_vs_oracle": err12}}
         plan.close()
     return out
 
@@ -1250,7 +1272,13 @@ def main():
     rows = (pb.nt // 2 + 1) * sp.ny
     roofs = {}
     for name, pk in per_kernel.items():
-        if name.startswith("xform"):
+        if name.startswith("xform") and plan.xform_engine != pd.PD_XFORM_TENSOR:
+            # the FFT along x: HBM-bound, 8 B in + 8 B out per complex spectrum value
+            roofs[name] = {"bound": "hbm", "achieved": pk["GB/s"], "peak": hbm, "unit": "GB/s",
+                           "frac": pk["GB/s"] / hbm, "traffic": None, "engine": "fft",
+                           "algorithmic_bytes": bpu[name] * NS,
+                           "peak_source": f"{src} (MEASURED_PEAKS.json)"}
+        elif name.startswith("xform"):
             # FP16 tensor-core GEMM (three products per k-step); FP16 runs at the bf16 rate
             ach = flops_per_launch_xform(rows, sp.nx) / (pk["ms"] / 1e3) / 1e12
             executed = 3 * 2.0 * rows * (2 * sp.nx) ** 2 / (pk["ms"] / 1e3) / 1e12
@@ -1369,7 +1397,10 @@ def main():
                "kernel_ms": {k: v["ms"] for k, v in per_kernel.items()},
                "solver": {"iterations": iters_all[-1], "relres": rel,
                           "cuda_graph": plan.uses_graph(),
-                          "autotuned": dict(zip(("tile_columns", "tri_lanes"), plan.tuning()))},
+                          "autotuned": dict(zip(("tile_columns", "tri_lanes", "tri_rows"),
+                                                plan.get_tuning()),
+                                            xform_engine={0: "tensor", 1: "fft", 2: "dense"}.get(
+                                                plan.xform_engine, "none"))},
                "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
                "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
                "scaling": "weak", "vs_baseline": None, "dtype": "f32 preconditioner + df64 residual",

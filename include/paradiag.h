@@ -268,8 +268,8 @@ PD_API pd_status pd_plan_uses_graph(const pd_plan* plan, int* uses);
  * plans with at least 2^18 unknowns choose them at creation by timing
  * candidates on the GPU (8 or 16 complex elements per thread for the time
  * kernels; for the tridiagonal solves the default lane count, twice it, and
- * the 16-rows-per-lane form); others use the default rules.  No paper
- * counterpart; introspection. */
+ * the 16-rows-per-lane form; the x-transform engine, pd_plan_xform_engine);
+ * others use the default rules.  No paper counterpart; introspection. */
 PD_API pd_status pd_plan_tuning(const pd_plan* plan, int* tile_columns, int* tri_lanes);
 
 /* The same shapes with the rows per lane that the tridiagonal solver keeps in
@@ -287,6 +287,29 @@ PD_API pd_status pd_plan_get_tuning(const pd_plan* plan, int* tile_columns, int*
  * holds is rebuilt at the next solve.  Every shape computes the same
  * preconditioner up to FP32 rounding.  No paper counterpart. */
 PD_API pd_status pd_plan_set_tuning(pd_plan* plan, int tile_columns, int tri_lanes, int tri_rows);
+
+/* Engines of the x-eigentransform of 2D (and periodic 1D) plans (step (b)'s
+ * diagonalisation of K_x, Section 2.2's periodic 2D experiment):
+ *   PD_XFORM_TENSOR  dense product with the eigenvector matrix on the tensor
+ *                    cores (tcgen05, FP16 two-term split, FP32 accumulation);
+ *                    mixed plans with nx >= 16 and >= 128 spectrum rows;
+ *   PD_XFORM_FFT     FFT along x in the plan's precision: the DFT (periodic x)
+ *                    or the sine transform through the odd extension
+ *                    (Dirichlet x), Bluestein's form for lengths that are not
+ *                    powers of two; transform lengths up to 1024;
+ *   PD_XFORM_DENSE   dense product on the CUDA cores (the remaining cases).
+ * Mixed plans with both of the first two and at least 2^18 unknowns pick the
+ * faster at creation (timed on the GPU); otherwise the tensor cores where
+ * available, else the FFT, else the dense form.  pd_plan_xform_engine: *engine
+ * = the engine in use (-1: no x-transform).  pd_plan_set_xform_engine pins
+ * PD_XFORM_TENSOR or PD_XFORM_FFT (PD_ERR_UNSUPPORTED where the plan lacks it,
+ * PD_ERR_ARG for other values); it waits for the plan's stream, and any CUDA
+ * graph the plan holds is rebuilt at the next solve.  No paper counterpart. */
+#define PD_XFORM_TENSOR 0
+#define PD_XFORM_FFT 1
+#define PD_XFORM_DENSE 2
+PD_API pd_status pd_plan_xform_engine(const pd_plan* plan, int* engine);
+PD_API pd_status pd_plan_set_xform_engine(pd_plan* plan, int engine);
 
 /* ---- batched solves: many independent problems of uneven size ----------
  * One problem of a batch (1D, Dirichlet, any scheme; all members of one batch

@@ -74,6 +74,8 @@ _SIGS = {
     "pd_plan_get_tuning": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
                                           ctypes.POINTER(ctypes.c_int)]),
     "pd_plan_set_tuning": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int, ctypes.c_int]),
+    "pd_plan_xform_engine": (ctypes.c_int, [_P, _I]),
+    "pd_plan_set_xform_engine": (ctypes.c_int, [_P, ctypes.c_int]),
     "pd_apply_precond_noalloc": (ctypes.c_int, [ctypes.POINTER(pd_space), ctypes.c_int,
                                                 ctypes.c_double, ctypes.c_double, ctypes.c_int,
                                                 ctypes.c_double, _P, _P, _P,
@@ -244,6 +246,19 @@ def pd_plan_get_tuning(plan):
 
 def pd_plan_set_tuning(plan, tile_columns, tri_lanes, tri_rows):
     return load().pd_plan_set_tuning(plan, int(tile_columns), int(tri_lanes), int(tri_rows))
+
+
+PD_XFORM_TENSOR, PD_XFORM_FFT, PD_XFORM_DENSE = 0, 1, 2
+
+
+def pd_plan_xform_engine(plan):
+    v = ctypes.c_int(0)
+    st = load().pd_plan_xform_engine(plan, ctypes.byref(v))
+    return st, v.value
+
+
+def pd_plan_set_xform_engine(plan, engine):
+    return load().pd_plan_set_xform_engine(plan, int(engine))
 
 
 def pd_batch_uses_graph(batch):
@@ -726,6 +741,17 @@ class Plan:
         """Pin the kernel shapes (see pd_plan_set_tuning)."""
         self._check(pd_plan_set_tuning(self._h, tile_columns, tri_lanes, tri_rows),
                     "pd_plan_set_tuning")
+
+    @property
+    def xform_engine(self):
+        """PD_XFORM_TENSOR, PD_XFORM_FFT or PD_XFORM_DENSE (-1: no x-transform)."""
+        st, v = pd_plan_xform_engine(self._h)
+        self._check(st, "pd_plan_xform_engine")
+        return v
+
+    def set_xform_engine(self, engine):
+        """Pin the engine of the x-eigentransform (see pd_plan_set_xform_engine)."""
+        self._check(pd_plan_set_xform_engine(self._h, engine), "pd_plan_set_xform_engine")
 
     def uses_graph(self):
         st, v = pd_plan_uses_graph(self._h)

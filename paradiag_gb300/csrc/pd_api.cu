@@ -193,7 +193,7 @@ InvArgs inv_base_impl(const pd_plan* p) {
 // x-eigentransform of every spectrum row: forward (spec -> spec2) or inverse
 // (spec2 -> spec); tensor cores on the mixed path, CUDA cores on the FP64 path
 pd_status xform_dir(pd_plan* p, bool fwd) {
-  if (p->xform_tc) {
+  if (p->xform_tc && p->xeng == PD_XFORM_TENSOR) {
     LK(launch_xform_tc(fwd ? p->xtc_fwd : p->xtc_inv, p->dflag, p->stream));
     return PD_OK;
   }
@@ -210,7 +210,7 @@ pd_status xform_dir(pd_plan* p, bool fwd) {
     xa.tw = p->xq_tw;
     xa.in = fwd ? p->spec : p->spec2;
     xa.out = fwd ? p->spec2 : p->spec;
-    LK(launch_xform_fft64(xa, p->stream));
+    LK(launch_xform_fft(xa, p->fp64, p->stream));
     return PD_OK;
   }
   XformArgs xa;
@@ -371,6 +371,25 @@ pd_status autotune_plan(pd_plan* p) {
     }
     p->tri_rows = pick.rows;
     p->tri_cls = (pick.rows == 0 && pick.cls == c0) || (pick.rows == 16 && pick.cls == c16) ? -1 : pick.cls;
+  }
+  // x-eigentransform: the tensor-core GEMM against the FP32 FFT
+  if (p->xform_tc && p->xq) {
+    const size_t specb = (size_t)p->nh * p->sg.specS * sizeof(float2);
+    CU(cudaMemsetAsync(p->spec, 0, specb, p->stream));
+    CU(cudaMemsetAsync(p->spec2, 0, specb, p->stream));
+    CU(cudaMemsetAsync(p->amax, 0, 2 * sizeof(unsigned), p->stream));
+    float best = 0.f;
+    int pick = PD_XFORM_TENSOR;
+    for (int eng : {PD_XFORM_TENSOR, PD_XFORM_FFT}) {
+      p->xeng = eng;
+      float ms = 0.f;
+      CHK(time_ms(p, 3, &ms, [&]() -> pd_status {
+        CHK(xform_dir(p, true));
+        return xform_dir(p, false);
+      }));
+      if (best == 0.f || ms < best) { best = ms; pick = eng; }
+    }
+    p->xeng = pick;
   }
   CU(cudaMemsetAsync(p->dflag, 0, sizeof(int), p->stream));
   CU(cudaStreamSynchronize(p->stream));
@@ -966,6 +985,35 @@ pd_status pd_plan_set_tuning(pd_plan* plan, int tile_columns, int tri_lanes, int
   return PD_OK;
 }
 
+pd_status pd_plan_set_xform_engine(pd_plan* plan, int engine) {
+  if (!plan) return PD_ERR_ARG;
+  if (engine != PD_XFORM_TENSOR && engine != PD_XFORM_FFT)
+    return set_err(plan, PD_ERR_ARG, "engine must be PD_XFORM_TENSOR or PD_XFORM_FFT");
+  if (!plan->xform) return set_err(plan, PD_ERR_UNSUPPORTED, "the plan has no x-eigentransform");
+  if (engine == PD_XFORM_TENSOR && !plan->xform_tc)
+    return set_err(plan, PD_ERR_UNSUPPORTED, "the plan has no tensor-core x-transform");
+  if (engine == PD_XFORM_FFT && !plan->xq)
+    return set_err(plan, PD_ERR_UNSUPPORTED, "the plan has no FFT x-transform");
+  if (plan->stream) cudaStreamSynchronize(plan->stream);
+  else cudaDeviceSynchronize();
+  if (plan->graph) {
+    destroy_graph(plan->graph);
+    plan->graph = nullptr;
+  }
+  plan->graph_state = 0;
+  plan->xeng = engine;
+  return PD_OK;
+}
+
+pd_status pd_plan_xform_engine(const pd_plan* plan, int* engine) {
+  if (!plan || !engine) return PD_ERR_ARG;
+  if (!plan->xform) *engine = -1;
+  else if (plan->xform_tc && plan->xeng == PD_XFORM_TENSOR) *engine = PD_XFORM_TENSOR;
+  else if (plan->xq) *engine = PD_XFORM_FFT;
+  else *engine = PD_XFORM_DENSE;
+  return PD_OK;
+}
+
 pd_status pd_plan_uses_graph(const pd_plan* plan, int* uses) {
   if (!plan || !uses) return PD_ERR_ARG;
   *uses = plan->graph_state == 1 ? 1 : 0;
@@ -1225,22 +1273,22 @@ pd_status plan_create_internal(const pd_space* sp, int nt, double dt, double alp
     pd_status s1 = upload_cplx(p, &p->Qf, Qf, p->fp64);
     if (s1 == PD_OK) s1 = upload_cplx(p, &p->Qi, Qi, p->fp64);
     if (s1 == PD_OK) s1 = upload_cplx(p, &p->mu, mux, p->fp64);
-    if (s1 == PD_OK && p->fp64) {
+    if (s1 == PD_OK) {
       // the FFT form of the transform: DFT of length n (periodic x) or of the
       // odd extension, length 2 (n + 1) (Dirichlet x); the kernel's tile
-      // holds up to 1024 transform points
+      // holds up to 1024 transform points; tables in the plan's precision
       const int L = sp->bc_x == PD_PERIODIC ? n : 2 * (n + 1);
       DftTables t = dft_tables(L);
       if ((t.M ? t.M : L) <= 1024) {
         p->xq_L = L;
         p->xq_dst = sp->bc_x == PD_PERIODIC ? 0 : 1;
-        s1 = upload_cplx(p, &p->xq_tw, t.tw, true);
+        s1 = upload_cplx(p, &p->xq_tw, t.tw, p->fp64);
         if (s1 == PD_OK && t.M) {
           void* c = nullptr;
           void* bh = nullptr;
-          s1 = upload_cplx(p, &c, t.chirp, true);
+          s1 = upload_cplx(p, &c, t.chirp, p->fp64);
           p->xq_xf.chirp = c;
-          if (s1 == PD_OK) s1 = upload_cplx(p, &bh, t.bhat, true);
+          if (s1 == PD_OK) s1 = upload_cplx(p, &bh, t.bhat, p->fp64);
           p->xq_xf.bhat = bh;
           p->xq_xf.M = t.M;
           p->xq_xf.logM = ilog2(t.M);
@@ -1250,6 +1298,7 @@ pd_status plan_create_internal(const pd_space* sp, int nt, double dt, double alp
     }
     const int rows = p->nh * (int)(S / n);
     p->xform_tc = !p->fp64 && n >= 16 && rows >= 128;
+    p->xeng = p->xform_tc ? PD_XFORM_TENSOR : PD_XFORM_FFT;
     if (s1 == PD_OK && p->xform_tc) {
       // real form of the complex operators, split into FP16 high and low parts:
       // G[2o][2i] = Re Q[o][i], G[2o][2i+1] = -Im, G[2o+1][2i] = Im, G[2o+1][2i+1] = Re

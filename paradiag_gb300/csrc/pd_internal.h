@@ -155,13 +155,13 @@ struct XfftArgs {
   int dst;                        // 1: sine transform (Dirichlet x), 0: DFT (periodic x)
   int inv;                        // 1: inverse transform (scaled), 0: forward
   TimeXf xf;
-  const void* tw;                 // double2
+  const void* tw;                 // complex twiddles (double2 / float2, as the data)
   const void* in;
   void* out;
 };
 
 // Launchers (return a cudaError_t).
-cudaError_t launch_xform_fft64(const XfftArgs& a, cudaStream_t st);
+cudaError_t launch_xform_fft(const XfftArgs& a, bool fp64, cudaStream_t st);
 cudaError_t launch_time_fwd(const FwdArgs& a, bool fp64, cudaStream_t st);
 cudaError_t launch_time_inv(const InvArgs& a, bool fp64, cudaStream_t st);
 cudaError_t launch_tridiag(const TriArgs& a, bool fp64, cudaStream_t st);

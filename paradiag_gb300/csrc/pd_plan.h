@@ -39,9 +39,12 @@ struct pd_plan {
   TimeXf xf = {0, 0, nullptr, nullptr};   // Bluestein tables for non-power-of-two Nt
   void* Qf = nullptr;
   void* Qi = nullptr;
-  // FP64 plans: the x-eigentransform by FFT (length xq_L DFT per row; sine
-  // transform for a Dirichlet x direction), with its twiddle / Bluestein tables
+  // the x-eigentransform by FFT (length xq_L DFT per row; sine transform for
+  // a Dirichlet x direction), with its twiddle / Bluestein tables in the
+  // plan's precision; mixed plans with the tensor-core transform too pick one
+  // engine (xeng: PD_XFORM_TENSOR or PD_XFORM_FFT, autotuned)
   bool xq = false;
+  int xeng = 0;
   int xq_L = 0, xq_dst = 0;
   TimeXf xq_xf = {0, 0, nullptr, nullptr};
   void* xq_tw = nullptr;

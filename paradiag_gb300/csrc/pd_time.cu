@@ -798,8 +798,9 @@ __global__ void __launch_bounds__(TT, PREC == 0 ? 4 : 2) k_time_inv_batch(const 
 }
 
 // ---------------------------------------------------------------------------
-// FP64 x-eigentransform by FFT (step (b) of 2D problems on FP64 plans, and of
-// periodic 1D problems): every row of the half spectrum is transformed along
+// x-eigentransform by FFT (step (b) of 2D problems and of periodic 1D
+// problems; FP64 on FP64 plans, FP32 on mixed plans, where it competes with the
+// tensor-core GEMM): every row of the half spectrum is transformed along
 // x by the DFT (periodic x: the eigenvectors of the circulant K_x) or by the
 // sine transform (symmetric Dirichlet x), in O(nx log nx) instead of the dense
 // O(nx^2) product.  A block holds XR rows transposed in shared memory (element
@@ -814,9 +815,9 @@ __global__ void __launch_bounds__(TT, PREC == 0 ? 4 : 2) k_time_inv_batch(const 
 // ---------------------------------------------------------------------------
 constexpr int XR = 4;   // rows per block
 
-template <int EPT>
-__global__ void __launch_bounds__(TT) k_xform_fft64(XfftArgs a) {
-  using C = double2;
+template <typename C, int EPT>
+__global__ void __launch_bounds__(TT) k_xform_fft(XfftArgs a) {
+  using R = decltype(C::x);
   extern __shared__ __align__(16) unsigned char smraw[];
   C* sm = reinterpret_cast<C*>(smraw);
   const int rows_fft = a.xf.M ? a.xf.M : a.L;
@@ -854,7 +855,7 @@ __global__ void __launch_bounds__(TT) k_xform_fft64(XfftArgs a) {
     else bluestein_tile<C, false, EPT>(sm, L, a.xf, lgXR, stw);
   }
   // outputs
-  const double sc = a.dst ? (a.inv ? 1.0 / (nx + 1) : 0.5) : (a.inv ? 1.0 / nx : 1.0);
+  const R sc = (R)(a.dst ? (a.inv ? 1.0 / (nx + 1) : 0.5) : (a.inv ? 1.0 / nx : 1.0));
   for (int e = threadIdx.x; e < XR * nx; e += TT) {
     const int r = e / nx, j = e - r * nx;
     const int row = r0 + r;
@@ -871,11 +872,11 @@ __global__ void __launch_bounds__(TT) k_xform_fft64(XfftArgs a) {
   }
 }
 
-template <int EPT>
+template <typename C, int EPT>
 cudaError_t launch_xfft_e(const XfftArgs& a, cudaStream_t st) {
   const int rows_fft = a.xf.M ? a.xf.M : a.L;
-  const size_t smem = (size_t)rows_fft * (XR + 1) * sizeof(double2);
-  auto kern = k_xform_fft64<EPT>;
+  const size_t smem = (size_t)rows_fft * (XR + 1) * sizeof(C);
+  auto kern = k_xform_fft<C, EPT>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   kern<<<ceil_div(a.rows, XR), TT, smem, st>>>(a);
@@ -952,14 +953,20 @@ cudaError_t launch_time_inv(const InvArgs& a, bool fp64, cudaStream_t st) {
   return fp64 ? launch_inv_t<1>(a, st) : launch_inv_t<0>(a, st);
 }
 
-cudaError_t launch_xform_fft64(const XfftArgs& a, cudaStream_t st) {
+cudaError_t launch_xform_fft(const XfftArgs& a, bool fp64, cudaStream_t st) {
   if (a.rows == 0) return cudaSuccess;
   // complex elements per thread of a tile: (M or L) x XR / TT
   const int rows_fft = a.xf.M ? a.xf.M : a.L;
   const int e = (rows_fft * XR + TT - 1) / TT;
-  if (e <= 4) return launch_xfft_e<4>(a, st);
-  if (e <= 8) return launch_xfft_e<8>(a, st);
-  if (e <= 16) return launch_xfft_e<16>(a, st);
+  if (fp64) {
+    if (e <= 4) return launch_xfft_e<double2, 4>(a, st);
+    if (e <= 8) return launch_xfft_e<double2, 8>(a, st);
+    if (e <= 16) return launch_xfft_e<double2, 16>(a, st);
+  } else {
+    if (e <= 4) return launch_xfft_e<float2, 4>(a, st);
+    if (e <= 8) return launch_xfft_e<float2, 8>(a, st);
+    if (e <= 16) return launch_xfft_e<float2, 16>(a, st);
+  }
   return cudaErrorInvalidValue;   // M x XR above 4096 elements: not supported
 }
 

@@ -116,3 +116,61 @@ def test_precond_matches_oracle(pd, name, prec):
     tol_inv = max(64 * eps * kap / pb.alpha, 1e-12)
     assert res <= tol_inv, (res, tol_inv)
     plan.close()
+
+
+# every case with an x-eigentransform (2D, or periodic 1D) under each engine
+# its mixed plan offers: the tensor-core GEMM where available and the FP32 FFT
+XFORM_CASES = sorted(n for n, pb in CASES.items()
+                     if pb.space.dim == 2 or pb.space.bc_x == W.PERIODIC)
+
+
+@pytest.mark.parametrize("name", XFORM_CASES)
+def test_precond_each_xform_engine_matches_oracle(pd, name):
+    pb = CASES[name]
+    r = W.uniform(W.SEED_BASE + zlib.crc32(name.encode()) % 1000, pb.unknowns,
+                  -1.0, 1.0).reshape(pb.nt, -1)
+    zref = PD.precond_apply(pb, r)
+    kap = kappa(pb)
+    M = pb.nt if pb.nt & (pb.nt - 1) == 0 else 1 << int(np.ceil(np.log2(2 * pb.nt - 1)))
+    tol = 2.0 * EPS32 * kap * (1.0 + np.log2(M)) / pb.alpha
+    plan = make_plan(pb, pd.PD_MIXED)
+    nx, rows = pb.space.nx, (pb.nt // 2 + 1) * (pb.space.ny if pb.space.dim == 2 else 1)
+    has_tc = nx >= 16 and rows >= 128
+    engines = [pd.PD_XFORM_FFT] + ([pd.PD_XFORM_TENSOR] if has_tc else [])
+    assert plan.xform_engine == (pd.PD_XFORM_TENSOR if has_tc else pd.PD_XFORM_FFT)
+    zs = {}
+    for eng in engines:
+        plan.set_xform_engine(eng)
+        assert plan.xform_engine == eng
+        zs[eng] = host(plan.apply_precond(dev(r)))
+        err = relerr(zs[eng], zref)
+        print(f"XFORM_ENGINE {name} engine={eng} err={err:.3e} of_bound={err / tol:.3e}")
+        assert err <= tol, (name, eng, err, tol)
+    if not has_tc:
+        with pytest.raises(pd.PDError) as e:
+            plan.set_xform_engine(pd.PD_XFORM_TENSOR)
+        assert e.value.status == pd.PD_ERR_UNSUPPORTED
+    plan.close()
+
+
+def test_xform_engine_rules(pd):
+    # FP64 2D plans take the FFT; plans without an x-transform report -1 and
+    # refuse either engine; invalid engine values are argument errors
+    sp = W.Space(dim=2, nx=33, ny=20, nu=1e-2, ax=1.0, ay=0.5, bc_x=W.PERIODIC)
+    pb = W.Problem(space=sp, nt=32, dt=1.0 / 32, scheme=W.CN, alpha=1e-3)
+    p64 = make_plan(pb, pd.PD_FP64)
+    assert p64.xform_engine == pd.PD_XFORM_FFT
+    with pytest.raises(pd.PDError) as e:
+        p64.set_xform_engine(pd.PD_XFORM_TENSOR)
+    assert e.value.status == pd.PD_ERR_UNSUPPORTED
+    with pytest.raises(pd.PDError) as e:
+        p64.set_xform_engine(7)
+    assert e.value.status == pd.PD_ERR_ARG
+    p64.close()
+    p1 = make_plan(CASES["1d_be_ade_127x64"], pd.PD_MIXED)
+    assert p1.xform_engine == -1
+    for eng in (pd.PD_XFORM_TENSOR, pd.PD_XFORM_FFT):
+        with pytest.raises(pd.PDError) as e:
+            p1.set_xform_engine(eng)
+        assert e.value.status == pd.PD_ERR_UNSUPPORTED
+    p1.close()
