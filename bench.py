@@ -305,6 +305,13 @@ def cpu_oracle_sample(w, seconds_hint=10.0):
             "nproc": nproc, "cpu_model": model, "single_core": one}
 
 
+def cpu_oracle_entry(seconds, unknowns, what):
+    """The oracle's wall time on this host (one core) for a configuration."""
+    nproc, model = cpu_info()
+    return {"s": seconds, "value": unknowns / seconds, "unit": UNIT, "cores": 1,
+            "kind": "oracle", "sample": what, "nproc": nproc, "cpu_model": model}
+
+
 def batched_leg(pd, torch, dev, args):
     """64 independent 1D advection-diffusion problems (nx uniform on 63..1023,
     Nt uniform on 32..1024, nu = 10^U[-3,-1], BE, alpha = 1e-2) solved together
@@ -363,8 +370,27 @@ def batched_leg(pd, torch, dev, args):
         g = by / (t / 1e3) / 1e9
         kroof[name] = {"ms": t, "bound": "hbm", "achieved": g, "peak": hbm, "unit": "GB/s",
                        "frac": g / hbm, "algorithmic_bytes": by}
+    # the oracle (O1, sequential stepping) for every member: its time on this
+    # host and the largest relative error of the batch's solution
+    from oracle import operators as O
+    from oracle import stepping as S
+    uh = u.cpu().numpy()
+    t_cpu, err_max, off = 0.0, 0.0, 0
+    for w in wls:
+        pbw = w.problem
+        n = pbw.nt * pbw.space.nx
+        bw = O.build_rhs(pbw, w.u0, None, w.f)
+        t0 = time.perf_counter()
+        uw = S.solve_sequential(pbw, bw)
+        t_cpu += time.perf_counter() - t0
+        err_max = max(err_max, float(np.linalg.norm(uh[off:off + n] - uw.reshape(-1))
+                                     / np.linalg.norm(uw)))
+        off += n
     out = {"workload": "64 x 1D advection-diffusion, nx ~ U{63..1023}, Nt ~ U{32..1024} "
                        "(Bluestein for non-powers of two), BE, alpha = 1e-2",
+           "error_vs_oracle_max": err_max,
+           "cpu_oracle": cpu_oracle_entry(t_cpu, int(batch.total),
+                                          "O1 sequential stepping of all 64 members"),
            "unknowns": int(batch.total), "ms_per_step": ms,
            "value": batch.total / (ms / 1e3), "unit": UNIT, "iterations": it,
            "relres_max": rel, "residual_tol": 1e-10,
@@ -878,11 +904,16 @@ def ade1d_leg(pd, torch, dev, args):
     w = W.ade1d()
     pb = w.problem
     sp = pb.space
-    uref = S.solve_sequential(pb, O.build_rhs(pb, w.u0, None, w.f))
+    bref = O.build_rhs(pb, w.u0, None, w.f)
+    t0 = time.perf_counter()
+    for _ in range(20):
+        uref = S.solve_sequential(pb, bref)
+    t_cpu = (time.perf_counter() - t0) / 20
     stream = torch.cuda.current_stream()
     out = {"workload": "ade1d_be_127x64: 1D advection-diffusion, Dirichlet, nu = 1e-2, a = 1, "
                        "backward Euler, alpha = 1e-2", "unknowns": pb.unknowns,
-           "residual_tol": 1e-12, "roofline": "none (latency-bound size)"}
+           "residual_tol": 1e-12, "roofline": "none (latency-bound size)",
+           "cpu_oracle": cpu_oracle_entry(t_cpu, pb.unknowns, "O1 sequential stepping, 20 repetitions")}
     for prec, tag in ((pd.PD_FP64, "fp64"), (pd.PD_MIXED, "mixed")):
         plan = pd.Plan(dict(dim=1, nx=sp.nx, nu=sp.nu, ax=sp.ax), pb.nt, pb.dt, pb.alpha,
                        pd.PD_BE, 1.0, prec, stream)
@@ -920,10 +951,14 @@ def adjoint_leg(pd, torch, dev, args):
     f0 = w.extra["f_probe"]
     stream = torch.cuda.current_stream()
     space = dict(dim=2, nx=sp.nx, ny=sp.ny, nu=sp.nu, bc_x=sp.bc_x, bc_y=sp.bc_y)
+    t0 = time.perf_counter()
     J_ref, g_ref, _, _ = C.gradient(pb, f0, w.extra["u_target"], reg)
+    t_cpu = time.perf_counter() - t0
     out = {"workload": "heat2d_adjoint_127x127x128: 2D heat equation source inversion, "
                        "backward Euler, Dirichlet", "unknowns_per_solve": pb.unknowns,
-           "residual_tol": 1e-11}
+           "residual_tol": 1e-11,
+           "cpu_oracle": cpu_oracle_entry(t_cpu, 2 * pb.unknowns,
+                                          "O5 gradient: forward and backward sequential stepping")}
     for prec, tag in ((pd.PD_MIXED, "mixed"), (pd.PD_FP64, "fp64")):
         plan = pd.Plan(space, pb.nt, pb.dt, pb.alpha, pd.PD_BE, 1.0, prec, stream)
 
@@ -980,11 +1015,14 @@ def wave_gmres_leg(pd, torch, dev, args):
     w = W.wave1d()
     pb = w.problem
     sp = pb.space
+    t0 = time.perf_counter()
     uref = S.solve_sequential(pb, O.build_rhs(pb, w.u0, w.u1, None))
+    t_cpu = time.perf_counter() - t0
     stream = torch.cuda.current_stream()
     out = {"workload": "wave1d_leapfrog_1023x1024: 1D wave, Dirichlet, leap-frog, T = 2, "
                        "alpha = 0.1, FGMRES(30)", "unknowns": pb.unknowns, "residual_tol": 1e-10,
-           "paper_iterations_T4A": 3, "l2": "working set ~0.3 GB (30 Krylov vectors) > L2"}
+           "paper_iterations_T4A": 3, "l2": "working set ~0.3 GB (30 Krylov vectors) > L2",
+           "cpu_oracle": cpu_oracle_entry(t_cpu, pb.unknowns, "O1 sequential leap-frog stepping")}
     for prec, tag in ((pd.PD_MIXED, "mixed"), (pd.PD_FP64, "fp64")):
         plan = pd.Plan(dict(dim=1, nx=sp.nx, nu=sp.nu), pb.nt, pb.dt, pb.alpha, pd.PD_LEAPFROG,
                        1.0, prec, stream)
