@@ -52,6 +52,10 @@ constexpr int STAGES = 4;
 // tensor cores stays inside the CTA's allocation
 constexpr int GUARD_BYTES = 32 * 1024;
 constexpr int TMEM_COLS = 2 * BN;   // two accumulators: epilogue of one tile under the MMAs of the next
+// XTC_UDF_ADD: a ring of EG slots per epilogue warp, each the iterate of 16
+// time levels for the warp's 32 points (4 KB), filled by cp.async
+constexpr int EG = 3;
+constexpr int EPI_STAGE_BYTES = 4 * EG * 16 * 32 * 8;
 constexpr int NTHREADS = 320;
 constexpr long long WAIT_LIMIT = 1LL << 22;
 
@@ -192,10 +196,13 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                const __grid_constant__ CUtensorMap tmBlo, float* __restrict__ out, int rows,
                int ncols, int ldo, int kchunks, int nblk_n, int ntiles,
                const unsigned* __restrict__ amax_bits, float g_inv, int* err, const XtcEpi ep) {
+  // operand stages: two in the update mode, whose epilogue stages the iterate
+  // in the memory the other two would take
+  constexpr int NS = EPI == XTC_UDF_ADD ? 2 : STAGES;
   extern __shared__ __align__(1024) unsigned char smraw[];
   // 1024-byte aligned operand stages (the swizzle patterns repeat every 512 bytes)
   unsigned char* base = (unsigned char*)(((uintptr_t)smraw + 1023) & ~(uintptr_t)1023);
-  __shared__ __align__(8) uint64_t bar_full[STAGES], bar_split[STAGES], bar_empty[STAGES];
+  __shared__ __align__(8) uint64_t bar_full[NS], bar_split[NS], bar_empty[NS];
   __shared__ __align__(8) uint64_t bar_accf[2], bar_acce[2], bar_done;
   __shared__ uint32_t tmem_slot;
   __shared__ int abort_flag;
@@ -204,7 +211,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
   const float sa = a_scale(__uint_as_float(*amax_bits));
 
   if (threadIdx.x == 0) {
-    for (int s = 0; s < STAGES; ++s) {
+    for (int s = 0; s < NS; ++s) {
       mbar_init(smem_u32(&bar_full[s]), 1);
       mbar_init(smem_u32(&bar_split[s]), 4);
       mbar_init(smem_u32(&bar_empty[s]), 1);
@@ -248,15 +255,15 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         const int T = blockIdx.x + i * gridDim.x;
         const int r0 = (T / nblk_n) * BM, n0 = (T % nblk_n) * BN;
         for (int c = 0; c < kchunks; ++c, ++g) {
-          const int s = g % STAGES;
-          const uint32_t u = (uint32_t)(g / STAGES);
+          const int s = g % NS;
+          const uint32_t u = (uint32_t)(g / NS);
           if (blockIdx.x == 0 && g == ep.stall_chunk) {
             // withheld: nothing of this chunk is in flight, so the consumers'
             // bounded waits run out and the CTA takes its abort path
             ok = false;
             break;
           }
-          if (g >= STAGES && !mbar_wait(smem_u32(&bar_empty[s]), (u & 1u) ^ 1u, abortp, ep.wait_limit)) {
+          if (g >= NS && !mbar_wait(smem_u32(&bar_empty[s]), (u & 1u) ^ 1u, abortp, ep.wait_limit)) {
             ok = false;
             break;
           }
@@ -275,8 +282,8 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         }
       }
       // drain: wait for the loads still in flight before the CTA may exit
-      for (int q = (g > STAGES ? g - STAGES : 0); q < g; ++q)
-        mbar_drain(smem_u32(&bar_full[q % STAGES]), (uint32_t)((q / STAGES) & 1));
+      for (int q = (g > NS ? g - NS : 0); q < g; ++q)
+        mbar_drain(smem_u32(&bar_full[q % NS]), (uint32_t)((q / NS) & 1));
     }
   } else if (warp == 1) {
     // ---------------- MMA issuer: accumulator buffer i & 1 for local tile i
@@ -293,8 +300,8 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         const uint32_t acc = tmem + (uint32_t)(ab * BN);
         for (int c = 0; c < kchunks; ++c, ++g) {
-          const int s = g % STAGES;
-          const uint32_t u = (uint32_t)(g / STAGES);
+          const int s = g % NS;
+          const uint32_t u = (uint32_t)(g / NS);
           if (!mbar_wait(smem_u32(&bar_split[s]), u & 1u, abortp, ep.wait_limit)) { ok = false; break; }
           asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
           const uint32_t ahi = smem_u32(stage_ptr(s, 0)), alo = smem_u32(stage_ptr(s, 1));
@@ -323,8 +330,8 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     const int sw = (t >> 1) & 3;
     const int nchunks = my_tiles * kchunks;
     for (int g = 0; g < nchunks; ++g) {
-      const int s = g % STAGES;
-      const uint32_t u = (uint32_t)(g / STAGES);
+      const int s = g % NS;
+      const uint32_t u = (uint32_t)(g / NS);
       if (!mbar_wait(smem_u32(&bar_full[s]), u & 1u, abortp, ep.wait_limit)) break;
       unsigned char* a0 = stage_ptr(s, 0) + t * 64;  // row t of box 0 / of A_hi
       unsigned char* a1 = stage_ptr(s, 1) + t * 64;  // row t of box 1 / of A_lo
@@ -358,6 +365,35 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     if constexpr (EPI == XTC_SPEC) {
       if (blockIdx.x == 0 && warp == 6 && lane == 0 && ep.spec_amax_reset) *ep.spec_amax_reset = 0u;
     }
+    // XTC_UDF_ADD: the iterate of the CTA's column blocks (16 time levels of
+    // one tile; block q = local tile q / 16, columns 16 (q % 16)) streams
+    // through ring slot q % EG of this warp by cp.async, EG - 1 blocks ahead of
+    // its update and across tile boundaries (the iterate does not depend on
+    // the MMAs, and tiles cover disjoint parts of it).  Each lane copies and
+    // later reads only its own point: no cross-lane synchronisation.
+    constexpr int QB = BN / 16;
+    float2* ring = reinterpret_cast<float2*>(base + (size_t)NS * STAGE_BYTES + GUARD_BYTES) +
+                   (size_t)(warp - 6) * (EG * 16 * 32) + lane;
+    auto fill = [&](int q) {
+      const int ti = q / QB, jb = q % QB;
+      if (ti < my_tiles) {
+        const int Tq = blockIdx.x + ti * gridDim.x;
+        const int rq = (Tq / nblk_n) * BM + q4 * 32 + lane, nq = (Tq % nblk_n) * BN + jb * 16;
+        if (rq < rows) {
+          float2* d = ring + (q % EG) * (16 * 32);
+#pragma unroll
+          for (int u = 0; u < 16; ++u)
+            if (nq + u < ncols)
+              asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(smem_u32(d + u * 32)),
+                           "l"(ep.Udf + (size_t)(nq + u) * rows + rq)
+                           : "memory");
+        }
+      }
+      asm volatile("cp.async.commit_group;" ::: "memory");
+    };
+    if constexpr (EPI == XTC_UDF_ADD) {
+      for (int q = 0; q < EG - 1; ++q) fill(q);
+    }
     for (int i = 0; i < my_tiles; ++i) {
       const int ab = i & 1;
       const uint32_t v2 = (uint32_t)(i >> 1);
@@ -366,23 +402,12 @@ __global__ void __launch_bounds__(NTHREADS, 1)
       const int T = blockIdx.x + i * gridDim.x;
       const int r0 = (T / nblk_n) * BM, n0 = (T % nblk_n) * BN;
       const int row = r0 + q4 * 32 + lane;
-      // XTC_UDF_ADD: the iterate of the next 16 columns is loaded before the
-      // current ones are stored, so that 16 to 32 loads per thread are in flight
-      float2 cur[16], nxt[16];
-      if constexpr (EPI == XTC_UDF_ADD) {
-#pragma unroll
-        for (int u = 0; u < 16; ++u)
-          cur[u] = (row < rows && n0 + u < ncols) ? ep.Udf[(size_t)(n0 + u) * rows + row]
-                                                  : make_float2(0.f, 0.f);
-      }
       for (int j = 0; j < BN; j += 16) {
+        const int qc = i * QB + j / 16;     // this column block's place in the stream
         if constexpr (EPI == XTC_UDF_ADD) {
-#pragma unroll
-          for (int u = 0; u < 16; ++u) {
-            const int nn = n0 + j + 16 + u;
-            nxt[u] = (j + 16 < BN && row < rows && nn < ncols)
-                         ? ep.Udf[(size_t)nn * rows + row] : make_float2(0.f, 0.f);
-          }
+          fill(qc + EG - 1);
+          // the groups of blocks up to qc are complete
+          asm volatile("cp.async.wait_group %0;" ::"n"(EG - 1) : "memory");
         }
         uint32_t v[16];
         const uint32_t taddr = tmem + ((uint32_t)(q4 * 32) << 16) + (uint32_t)(ab * BN + j);
@@ -432,23 +457,23 @@ __global__ void __launch_bounds__(NTHREADS, 1)
             if constexpr (EPI == XTC_UDF_SET) {
               *up = make_float2(d, 0.f);
             } else {
-              const float2 uo = cur[u];
+              const float2 uo = ring[(qc % EG) * (16 * 32) + u * 32];
               df t = two_sum(uo.x, d);
               t = fast_two_sum(t.hi, t.lo + uo.y);
               *up = make_float2(t.hi, t.lo);
             }
           }
-          if constexpr (EPI == XTC_UDF_ADD) {
-#pragma unroll
-            for (int u = 0; u < 16; ++u) cur[u] = nxt[u];
-          }
         }
       }
+
       // this warp's reads of accumulator ab are complete: hand it back
       asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
       __syncwarp();
       if (lane == 0) mbar_arrive(smem_u32(&bar_acce[ab]));
     }
+    // copies still in flight (blocks past the last tile are empty groups; after
+    // an abort, blocks of tiles not reached) finish before the CTA exits
+    if constexpr (EPI == XTC_UDF_ADD) asm volatile("cp.async.wait_group 0;" ::: "memory");
     if constexpr (EPI == XTC_SPEC) {
       for (int o = 16; o > 0; o >>= 1) amx = fmaxf(amx, __shfl_xor_sync(0xffffffffu, amx, o));
       if (lane == 0 && ep.spec_amax) atomicMax(ep.spec_amax, __float_as_uint(amx));
@@ -549,8 +574,10 @@ cudaError_t xform_tc_prepare(XformTc* x, int rows, int nx, int ldo_floats, const
 }
 
 template <int EPI>
-cudaError_t launch_epi(const XformTc& x, int* err, cudaStream_t st, int grid, int ntiles,
-                       size_t smem) {
+cudaError_t launch_epi(const XformTc& x, int* err, cudaStream_t st, int grid, int ntiles) {
+  const size_t smem = EPI == XTC_UDF_ADD
+                          ? (size_t)2 * STAGE_BYTES + 1024 + GUARD_BYTES + EPI_STAGE_BYTES
+                          : (size_t)STAGES * STAGE_BYTES + 1024 + GUARD_BYTES;
   cudaError_t e =
       cudaFuncSetAttribute(k_xform_tc<EPI>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
@@ -595,7 +622,6 @@ cudaError_t xform_tc_prepare_blocked(XformTc* x, int rows, int K, const float* i
 }
 
 cudaError_t launch_xform_tc(const XformTc& x, int* err, cudaStream_t st) {
-  const size_t smem = (size_t)STAGES * STAGE_BYTES + 1024 + GUARD_BYTES;
   // persistent: one CTA per SM over all tiles
   static int nsm = 0;
   if (nsm == 0) {
@@ -607,10 +633,10 @@ cudaError_t launch_xform_tc(const XformTc& x, int* err, cudaStream_t st) {
   const int ntiles = x.nblk_n * ((x.rows + BM - 1) / BM);
   const int grid = ntiles < nsm ? ntiles : nsm;
   switch (x.epi) {
-    case XTC_ROWS: return launch_epi<XTC_ROWS>(x, err, st, grid, ntiles, smem);
-    case XTC_SPEC: return launch_epi<XTC_SPEC>(x, err, st, grid, ntiles, smem);
-    case XTC_UDF_SET: return launch_epi<XTC_UDF_SET>(x, err, st, grid, ntiles, smem);
-    case XTC_UDF_ADD: return launch_epi<XTC_UDF_ADD>(x, err, st, grid, ntiles, smem);
+    case XTC_ROWS: return launch_epi<XTC_ROWS>(x, err, st, grid, ntiles);
+    case XTC_SPEC: return launch_epi<XTC_SPEC>(x, err, st, grid, ntiles);
+    case XTC_UDF_SET: return launch_epi<XTC_UDF_SET>(x, err, st, grid, ntiles);
+    case XTC_UDF_ADD: return launch_epi<XTC_UDF_ADD>(x, err, st, grid, ntiles);
     default: return cudaErrorInvalidValue;
   }
 }
