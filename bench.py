@@ -78,6 +78,10 @@ def parse():
                     help="only the hybrid ParaDiag-I mixed kernel profile (the command ncu captures profile)")
     ap.add_argument("--profile-iteration", action="store_true",
                     help="only time the kernels of one iteration (the command ncu captures profile)")
+    ap.add_argument("--profile-precision", default="mixed", choices=["mixed", "fp64"],
+                    help="--profile-iteration: the plan's precision")
+    ap.add_argument("--profile-xform", default="auto", choices=["auto", "tensor", "fft"],
+                    help="--profile-iteration: pin the x-transform engine of a mixed plan")
     ap.add_argument("--sweep", action="store_true",
                     help="roofline sweep of the iteration kernels over 1D sizes "
                          "nx in {255, 1023, 4095} x Nt in {256, 1024, 4096}")
@@ -904,16 +908,26 @@ def ade1d_leg(pd, torch, dev, args):
     w = W.ade1d()
     pb = w.problem
     sp = pb.space
+    from oracle import paradiag as PDO
     bref = O.build_rhs(pb, w.u0, None, w.f)
     t0 = time.perf_counter()
     for _ in range(20):
         uref = S.solve_sequential(pb, bref)
     t_cpu = (time.perf_counter() - t0) / 20
+    # the naive-DFT ParaDiag (O2, the stationary iteration with a dense Fourier
+    # matrix and a sparse LU per frequency) on the host: a CPU ParaDiag reference
+    t0 = time.perf_counter()
+    for _ in range(5):
+        _, it_o2, _ = PDO.stationary(pb, bref, tol=1e-12, maxit=30)
+    t_o2 = (time.perf_counter() - t0) / 5
     stream = torch.cuda.current_stream()
     out = {"workload": "ade1d_be_127x64: 1D advection-diffusion, Dirichlet, nu = 1e-2, a = 1, "
                        "backward Euler, alpha = 1e-2", "unknowns": pb.unknowns,
            "residual_tol": 1e-12, "roofline": "none (latency-bound size)",
-           "cpu_oracle": cpu_oracle_entry(t_cpu, pb.unknowns, "O1 sequential stepping, 20 repetitions")}
+           "cpu_oracle": cpu_oracle_entry(t_cpu, pb.unknowns, "O1 sequential stepping, 20 repetitions"),
+           "cpu_paradiag_o2": dict(cpu_oracle_entry(t_o2, pb.unknowns,
+                                                    "O2 naive-DFT ParaDiag, stationary to 1e-12, "
+                                                    "5 repetitions"), iterations=it_o2)}
     for prec, tag in ((pd.PD_FP64, "fp64"), (pd.PD_MIXED, "mixed")):
         plan = pd.Plan(dict(dim=1, nx=sp.nx, nu=sp.nu, ax=sp.ax), pb.nt, pb.dt, pb.alpha,
                        pd.PD_BE, 1.0, prec, stream)
@@ -1260,6 +1274,12 @@ def main():
         return
     if args.profile_iteration:
         # the residual-mode iteration of the solver, kernel by kernel (the command ncu captures profile)
+        if args.profile_precision == "fp64":
+            plan.close()
+            plan = pd.Plan(space, pb.nt, pb.dt, pb.alpha, pd.PD_CN, 0.5, pd.PD_FP64, stream)
+        elif args.profile_xform != "auto":
+            plan.set_xform_engine(pd.PD_XFORM_TENSOR if args.profile_xform == "tensor"
+                                  else pd.PD_XFORM_FFT)
         for _ in range(2):
             kms = plan.profile_iteration(b, u, reps=5)
         torch.cuda.synchronize()
