@@ -205,8 +205,8 @@ def flops_per_launch_xform(rows, nx):
 # DRAM bytes (read + write) per launch from one ncu capture of each kernel on
 # the bench workload (the time kernels as recaptured after their last change);
 # a kernel's entry goes back to None whenever that kernel changes.
-NCU_TRAFFIC = {"resid_gamma_fft": 319.4e6, "xform_fwd": 81.4e6, "tridiag": 79.5e6,
-               "xform_inv": 81.4e6, "ifft_gamma_update": 279.7e6}
+NCU_TRAFFIC = {"resid_gamma_fft": 319.4e6, "xform_fwd": 78.3e6, "tridiag": 79.5e6,
+               "xform_inv": 79.0e6, "ifft_gamma_update": 279.7e6}
 
 
 def cpu_info():

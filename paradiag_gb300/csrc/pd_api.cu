@@ -323,7 +323,7 @@ pd_status autotune_plan(pd_plan* p) {
   // time kernels: tile budgets of 4096 and 8192 reals
   const int tx_a = std::max(2, std::min(32, 4096 / rows)), tx_b = std::max(2, std::min(32, 8192 / rows));
   if (tx_a != tx_b) {
-    float best = 0.f;
+    float best = -1.f;  // no candidate timed yet
     int best_tx = p->TX;
     for (int tx : {tx_b, tx_a}) {
       p->TX = tx;
@@ -341,7 +341,7 @@ pd_status autotune_plan(pd_plan* p) {
         LK(launch_time_inv(ia, false, p->stream));
         return PD_OK;
       }));
-      if (best == 0.f || ms < best) { best = ms; best_tx = tx; }
+      if (best < 0.f || ms < best) { best = ms; best_tx = tx; }
     }
     p->TX = best_tx;
   }
@@ -357,7 +357,7 @@ pd_status autotune_plan(pd_plan* p) {
     std::vector<Cand> cands = {{c0, 0}};
     if (c0 + 1 < TRI_NCLASS && (2 << c0) * 2 <= p->tri_n) cands.push_back({c0 + 1, 0});
     if (c16 >= 0 && c16 > c0) cands.push_back({c16, 16});
-    float best = 0.f;
+    float best = -1.f;  // no candidate timed yet
     Cand pick = cands[0];
     for (const Cand& c : cands) {
       p->tri_cls = c.cls;
@@ -367,7 +367,7 @@ pd_status autotune_plan(pd_plan* p) {
         LK(launch_tridiag(tri_args_impl(p, data), false, p->stream));
         return PD_OK;
       }));
-      if (best == 0.f || ms < best) { best = ms; pick = c; }
+      if (best < 0.f || ms < best) { best = ms; pick = c; }
     }
     p->tri_rows = pick.rows;
     p->tri_cls = (pick.rows == 0 && pick.cls == c0) || (pick.rows == 16 && pick.cls == c16) ? -1 : pick.cls;
@@ -378,7 +378,7 @@ pd_status autotune_plan(pd_plan* p) {
     CU(cudaMemsetAsync(p->spec, 0, specb, p->stream));
     CU(cudaMemsetAsync(p->spec2, 0, specb, p->stream));
     CU(cudaMemsetAsync(p->amax, 0, 2 * sizeof(unsigned), p->stream));
-    float best = 0.f;
+    float best = -1.f;  // no candidate timed yet
     int pick = PD_XFORM_TENSOR;
     for (int eng : {PD_XFORM_TENSOR, PD_XFORM_FFT}) {
       p->xeng = eng;
@@ -387,7 +387,7 @@ pd_status autotune_plan(pd_plan* p) {
         CHK(xform_dir(p, true));
         return xform_dir(p, false);
       }));
-      if (best == 0.f || ms < best) { best = ms; pick = eng; }
+      if (best < 0.f || ms < best) { best = ms; pick = eng; }
     }
     p->xeng = pick;
   }

@@ -381,7 +381,7 @@ pd_status batch_autotune(pd_batch* b) {
     const int rows = g.first;
     const int tx_a = std::max(2, std::min(32, 8192 / rows)), tx_b = std::max(2, std::min(32, 4096 / rows));
     if (tx_a == tx_b) continue;
-    float best = 0.f;
+    float best = -1.f;  // no candidate timed yet
     int best_tx = tx_a;
     for (int tx : {tx_a, tx_b}) {
       for (int i : g.second) b->plans[i]->TX = tx;
@@ -392,7 +392,7 @@ pd_status batch_autotune(pd_batch* b) {
         cudaError_t e = launch_fwd_all(b, st, &nk);
         return e == cudaSuccess ? launch_inv_all(b, st, &nk) : e;
       }));
-      if (best == 0.f || ms < best) { best = ms; best_tx = tx; }
+      if (best < 0.f || ms < best) { best = ms; best_tx = tx; }
     }
     for (int i : g.second) b->plans[i]->TX = best_tx;
   }
@@ -404,7 +404,7 @@ pd_status batch_autotune(pd_batch* b) {
     bool ok = true;
     for (int i : g.second) ok = ok && (2 << c0) * 2 <= b->plans[i]->tri_n;
     if (!ok) continue;
-    float best = 0.f;
+    float best = -1.f;  // no candidate timed yet
     int best_c = c0;
     for (int c : {c0, c0 + 1}) {
       for (int i : g.second) b->plans[i]->tri_cls = c;
@@ -412,7 +412,7 @@ pd_status batch_autotune(pd_batch* b) {
       BCHK(set_call_descs(b, nullptr, nullptr));
       float ms = 0.f;
       BCHK(batch_time_ms(b, 3, &ms, [&]() -> cudaError_t { return launch_tri_all(b, st, &nk); }));
-      if (best == 0.f || ms < best) { best = ms; best_c = c; }
+      if (best < 0.f || ms < best) { best = ms; best_c = c; }
     }
     for (int i : g.second) b->plans[i]->tri_cls = best_c == c0 ? -1 : best_c;
   }
