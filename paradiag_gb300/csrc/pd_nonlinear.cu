@@ -149,21 +149,31 @@ __device__ __forceinline__ void nl_add_prod(NlAcc& A, df k, df u) {
 }
 __device__ __forceinline__ df nl_val(const NlAcc& A) { return fast_two_sum(A.s, A.e); }
 
+// The stencil neighbours of point s (offsets from s; 0: no neighbour), fixed
+// for every time row of a thread
+struct NlNbh {
+  int l, r, d, u;
+};
+__device__ __forceinline__ NlNbh nl_nbh(const Stencil& st, int s) {
+  const int xg = s % st.nx, y = s / st.nx;
+  NlNbh g;
+  g.l = xg > 0 ? -1 : (st.bcx == PD_PERIODIC && st.nx > 1 ? st.nx - 1 : 0);
+  g.r = xg < st.nx - 1 ? 1 : (st.bcx == PD_PERIODIC && st.nx > 1 ? -(st.nx - 1) : 0);
+  g.d = (st.dim == 2 && y > 0) ? -st.nx : 0;
+  g.u = (st.dim == 2 && y < st.ny - 1) ? st.nx : 0;
+  return g;
+}
+
 // F(U)(s) = (K U)(s) + phi(U(s)) as one compensated sum of eight terms
 template <typename T>
-__device__ __forceinline__ df f_of_df(const Stencil& st, const NlDf& c, const T* __restrict__ U,
-                                      int s, df uc) {
-  const int xg = s % st.nx, y = s / st.nx;
+__device__ __forceinline__ df f_of_df(const NlDf& c, const T* __restrict__ U, int s,
+                                      const NlNbh& g, df uc) {
   NlAcc A = {0.f, 0.f};
   nl_add_prod(A, c.kc, uc);
-  if (xg > 0) nl_add_prod(A, c.kxl, ld_df(U, s - 1));
-  else if (st.bcx == PD_PERIODIC && st.nx > 1) nl_add_prod(A, c.kxl, ld_df(U, s + st.nx - 1));
-  if (xg < st.nx - 1) nl_add_prod(A, c.kxu, ld_df(U, s + 1));
-  else if (st.bcx == PD_PERIODIC && st.nx > 1) nl_add_prod(A, c.kxu, ld_df(U, s - st.nx + 1));
-  if (st.dim == 2) {
-    if (y > 0) nl_add_prod(A, c.kyl, ld_df(U, s - st.nx));
-    if (y < st.ny - 1) nl_add_prod(A, c.kyu, ld_df(U, s + st.nx));
-  }
+  if (g.l) nl_add_prod(A, c.kxl, ld_df(U, s + g.l));
+  if (g.r) nl_add_prod(A, c.kxu, ld_df(U, s + g.r));
+  if (g.d) nl_add_prod(A, c.kyl, ld_df(U, s + g.d));
+  if (g.u) nl_add_prod(A, c.kyu, ld_df(U, s + g.u));
   // phi(u) = a1 u + a2 u^2 + a3 u^3
   const df u2 = df_mul(uc, uc);
   const df u3 = df_mul(u2, uc);
@@ -190,17 +200,18 @@ __global__ void __launch_bounds__(NB) k_nl_resid_df(Stencil st, NlDf c, Reaction
   const df m10 = df_neg(c.c10), m20 = df_neg(c.c20), m11 = df_neg(c.c11), m21 = df_neg(c.c21);
   float pr = 0.f, pd = 0.f;
   if (s < st.S) {
+    const NlNbh g = nl_nbh(st, s);
     df Up = df_make(0.f, 0.f), Fp = Up;
     if (n0 > 0) {
       const T* U = u + (size_t)(n0 - 1) * S;
       Up = ld_df(U, s);
-      Fp = f_of_df(st, c, U, s, Up);
+      Fp = f_of_df(c, U, s, g, Up);
     }
     const int n1 = min(N, n0 + NL_ROWS);
     for (int n = n0; n < n1; ++n) {
       const T* U = u + (size_t)n * S;
       const df Un = ld_df(U, s);
-      const df Fn = f_of_df(st, c, U, s, Un);
+      const df Fn = f_of_df(c, U, s, g, Un);
       const df bn = ld_df(b, (size_t)n * S + s);
       NlAcc V = {bn.hi, bn.lo};
       nl_add_prod(V, m10, Un);
