@@ -45,6 +45,8 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU baseline leg")
     ap.add_argument("--small", action="store_true", help="a small case (profiling runs)")
     ap.add_argument("--no-batch", action="store_true", help="skip the batched-workload leg")
+    ap.add_argument("--batch-only", action="store_true",
+                    help="only the batched-workload leg (the command ncu captures profile)")
     ap.add_argument("--no-pd1", action="store_true", help="skip the ParaDiag-I leg")
     ap.add_argument("--pd1-only", action="store_true",
                     help="only the ParaDiag-I leg (one JSON object; profiling runs)")
@@ -1230,6 +1232,12 @@ def main():
     b = plan.build_rhs(u0)
     u = torch.zeros_like(b)
     torch.cuda.synchronize()
+    if args.batch_only:
+        out = batched_leg(pd, torch, dev, args)
+        if rank == 0:
+            print(json.dumps(out), flush=True)
+        plan.close()
+        return
     if args.control_only:
         out = control_leg(pd, torch, dev, args)
         if rank == 0:

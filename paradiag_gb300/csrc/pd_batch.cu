@@ -110,30 +110,54 @@ __device__ __forceinline__ int find_problem(const unsigned long long* off, int n
   return lo;
 }
 
-// y = df(x) * scale[problem of the element]
+// y = df(x) * scale[problem of the element]; block b converts the contiguous
+// range [b chunk, (b+1) chunk), each thread tracking its problem incrementally
 __global__ void k_batch_to_df(const double* __restrict__ x, float2* __restrict__ y,
                               const unsigned long long* __restrict__ off,
                               const float2* __restrict__ scale, int np, unsigned long long total) {
-  for (unsigned long long e = blockIdx.x * (unsigned long long)TB + threadIdx.x; e < total;
-       e += (unsigned long long)gridDim.x * TB) {
-    const int p = find_problem(off, np, e);
-    const float2 sc = scale[p];
+  const unsigned long long chunk = ((total + gridDim.x - 1) / gridDim.x + TB - 1) / TB * TB;
+  const unsigned long long e0 = blockIdx.x * chunk;
+  const unsigned long long e1 = min(total, e0 + chunk);
+  int p = -1;
+  float2 sc = make_float2(1.f, 0.f);
+  for (unsigned long long e = e0 + threadIdx.x; e < e1; e += TB) {
+    if (p < 0 || (p + 1 < np && off[p + 1] <= e)) {
+      p = p < 0 ? find_problem(off, np, e) : p;
+      while (p + 1 < np && off[p + 1] <= e) ++p;
+      sc = scale[p];
+    }
     const df v = df_mul(df_from_double(x[e]), df_make(sc.x, sc.y));
     y[e] = make_float2(v.hi, v.lo);
   }
 }
 
-// out[p] += ||x_p||^2, with a per-block shared accumulator for every problem
+// out[p] += ||x_p||^2.  Block b sums the contiguous range [b chunk, (b+1) chunk)
+// with coalesced loads; each thread keeps its running sum in a register and
+// tracks its problem incrementally (its elements only increase), adding the
+// sum into the block's shared slot of that problem when the problem changes,
+// so the shared atomics are per problem boundary, not per element.
 __global__ void k_batch_norm2(const double* __restrict__ x, const unsigned long long* __restrict__ off,
                               int np, unsigned long long total, double* out) {
   extern __shared__ double acc[];
   for (int i = threadIdx.x; i < np; i += TB) acc[i] = 0.0;
   __syncthreads();
-  for (unsigned long long e = blockIdx.x * (unsigned long long)TB + threadIdx.x; e < total;
-       e += (unsigned long long)gridDim.x * TB) {
-    const int p = find_problem(off, np, e);
-    atomicAdd(&acc[p], x[e] * x[e]);
+  const unsigned long long chunk = ((total + gridDim.x - 1) / gridDim.x + TB - 1) / TB * TB;
+  const unsigned long long e0 = blockIdx.x * chunk;
+  const unsigned long long e1 = min(total, e0 + chunk);
+  int p = -1;
+  double sum = 0.0;
+  for (unsigned long long e = e0 + threadIdx.x; e < e1; e += TB) {
+    if (p < 0) {
+      p = find_problem(off, np, e);
+    } else if (p + 1 < np && off[p + 1] <= e) {
+      atomicAdd(&acc[p], sum);
+      sum = 0.0;
+      while (p + 1 < np && off[p + 1] <= e) ++p;
+    }
+    const double v = x[e];
+    sum = fma(v, v, sum);
   }
+  if (p >= 0) atomicAdd(&acc[p], sum);
   __syncthreads();
   for (int i = threadIdx.x; i < np; i += TB)
     if (acc[i] != 0.0) atomicAdd(&out[i], acc[i]);
