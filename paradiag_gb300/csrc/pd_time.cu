@@ -330,6 +330,7 @@ PD_D void stencil_df(const FwdArgs& a, const ColGeom& g, const RowLd<float2>& L,
 }
 
 // Packed form of stencil_df: two time rows (lanes A, B) of this thread's column.
+template <bool D1 = false>
 PD_D void stencil_df2(const FwdArgs& a, const ColGeom& g, const RowLd<float2>& LA,
                       const RowLd<float2>& LB, int TX, const K2* kk, DF2& Uc, Acc2& KU) {
   const unsigned FULL = 0xffffffffu;
@@ -348,7 +349,7 @@ PD_D void stencil_df2(const FwdArgs& a, const ColGeom& g, const RowLd<float2>& L
   Acc2 A = acc2_of_prod(kk[0], Uc);
   acc2_add_prod(A, kk[1], lf);
   acc2_add_prod(A, kk[2], rt);
-  if (a.st.dim == 2) {
+  if (!D1 && a.st.dim == 2) {
     acc2_add_prod(A, kk[3], df2_pack(LA.d, LB.d));
     acc2_add_prod(A, kk[4], df2_pack(LA.u, LB.u));
   }
@@ -388,7 +389,10 @@ PD_D T block_sum(T v, T* red) {
 // K1: residual (optional) + Gamma scaling + forward real FFT along t.
 // PREC 0: mixed (double-float residual, FP32 transform); PREC 1: FP64.
 // ---------------------------------------------------------------------------
-template <int PREC, int BAND, int EPT>
+// PF: time rows of loads in flight ahead of the row being computed in the
+// mixed residual loop (1, or 2 for the batched kernels' long narrow tiles);
+// D1: 1D problems only (no y-neighbour loads or registers)
+template <int PREC, int BAND, int EPT, int PF = 1, bool D1 = false>
 PD_D void time_fwd_body(const FwdArgs& a, int tile) {
   using R = typename std::conditional<PREC == 0, float, double>::type;
   using C = cplx_t<R>;
@@ -481,9 +485,9 @@ PD_D void time_fwd_body(const FwdArgs& a, int tile) {
       DF2 U1 = {make_float2(0.f, 0.f), make_float2(0.f, 0.f)}, U2 = U1, U0;
       Acc2 K1 = {make_float2(0.f, 0.f), make_float2(0.f, 0.f)}, K2v = K1, K0;
       if (BAND == 2)
-        stencil_df2(a, g, load_row(a.Udf, a, g, nA - 2), load_row(a.Udf, a, g, nB - 2), TX, kk,
+        stencil_df2<D1>(a, g, load_row(a.Udf, a, g, nA - 2), load_row(a.Udf, a, g, nB - 2), TX, kk,
                     U2, K2v);
-      stencil_df2(a, g, load_row(a.Udf, a, g, nA - 1), load_row(a.Udf, a, g, nB - 1), TX, kk, U1,
+      stencil_df2<D1>(a, g, load_row(a.Udf, a, g, nA - 1), load_row(a.Udf, a, g, nB - 1), TX, kk, U1,
                   K1);
       // In the loop every row index is clamped to the last level: rows at or
       // past N (possible in the last chunks) are computed from in-range data
@@ -505,14 +509,23 @@ PD_D void time_fwd_body(const FwdArgs& a, int tile) {
         L.c = __ldg(p);
         L.l = hasL ? __ldg(p + dL) : z2;
         L.r = hasR ? __ldg(p + dR) : z2;
-        L.d = hasD ? __ldg(p - nx) : z2;
-        L.u = hasU ? __ldg(p + nx) : z2;
+        L.d = (!D1 && hasD) ? __ldg(p - nx) : z2;
+        L.u = (!D1 && hasU) ? __ldg(p + nx) : z2;
         return L;
       };
-      // one row of loads in flight ahead of the row being computed
+      // PF rows of loads in flight ahead of the row being computed (with PF = 2
+      // the row after next waits in zA, zB, wA, wB)
       RowLd<float2> cA = ldrow(min(nA, Nm1)), cB = ldrow(min(nB, Nm1));
       float2 bA = __ldg(Bcol + (size_t)min(nA, Nm1) * Sz);
       float2 bB = __ldg(Bcol + (size_t)min(nB, Nm1) * Sz);
+      RowLd<float2> zA, zB;
+      float2 wA = make_float2(0.f, 0.f), wB = wA;
+      if constexpr (PF == 2) {
+        zA = ldrow(min(nA + 1, Nm1));
+        zB = ldrow(min(nB + 1, Nm1));
+        wA = __ldg(Bcol + (size_t)min(nA + 1, Nm1) * Sz);
+        wB = __ldg(Bcol + (size_t)min(nB + 1, Nm1) * Sz);
+      }
       // the c2 weights negated once; when every c2[m] is 0 or a power of two
       // (backward Euler, Crank-Nicolson, leap-frog) the weighted terms are exact
       // scalings
@@ -529,10 +542,10 @@ PD_D void time_fwd_body(const FwdArgs& a, int tile) {
 #pragma unroll 1
       for (int i = 0; i < rpc2; ++i) {
         const int na = nA + i, nb = nB + i;
-        const int pa = min(na + 1, Nm1), pb = min(nb + 1, Nm1);
+        const int pa = min(na + PF, Nm1), pb = min(nb + PF, Nm1);
         const RowLd<float2> xA = ldrow(pa), xB = ldrow(pb);
         const float2 yA = __ldg(Bcol + (size_t)pa * Sz), yB = __ldg(Bcol + (size_t)pb * Sz);
-        stencil_df2(a, g, cA, cB, TX, kk, U0, K0);  // uniform across the warp
+        stencil_df2<D1>(a, g, cA, cB, TX, kk, U0, K0);  // uniform across the warp
         // r' = s b - U_n + U_{n-1} - c2[0] (sK)U_n - c2[1] (sK)U_{n-1}        (theta)
         // r' = s b - U_n + 2 U_{n-1} - U_{n-2} - c2[0] (sK)U_n - c2[2] (sK)U_{n-2} (leap-frog)
         const DF2 Bv = df2_pack(bA, bB);
@@ -568,8 +581,15 @@ PD_D void time_fwd_body(const FwdArgs& a, int tile) {
           srow[nb * TX] = vb ? fmaf(rh.y, gg, rl.y * gg) : 0.f;
         }
         U2 = U1; K2v = K1; U1 = U0; K1 = K0;
-        cA = xA; cB = xB;
-        bA = yA; bB = yB;
+        if constexpr (PF == 2) {
+          cA = zA; cB = zB;
+          bA = wA; bB = wB;
+          zA = xA; zB = xB;
+          wA = yA; wB = yB;
+        } else {
+          cA = xA; cB = xB;
+          bA = yA; bB = yB;
+        }
       }
       const float part1 = part.x + part.y;
       nrm = (double)part1 * a.rscale2;
@@ -665,7 +685,8 @@ template <int PREC, int BAND, int EPT>
 __global__ void __launch_bounds__(TT, PREC == 0 ? 3 : 2) k_time_fwd_batch(const FwdArgs* __restrict__ descs,
                                                           const int2* __restrict__ work) {
   const int2 w = work[blockIdx.x];
-  time_fwd_body<PREC, BAND, EPT>(descs[w.x], w.y);
+  // batches hold 1D problems only
+  time_fwd_body<PREC, BAND, EPT, EPT == 16 ? 2 : 1, true>(descs[w.x], w.y);
 }
 
 // ---------------------------------------------------------------------------
