@@ -389,10 +389,8 @@ PD_D T block_sum(T v, T* red) {
 // K1: residual (optional) + Gamma scaling + forward real FFT along t.
 // PREC 0: mixed (double-float residual, FP32 transform); PREC 1: FP64.
 // ---------------------------------------------------------------------------
-// PF: time rows of loads in flight ahead of the row being computed in the
-// mixed residual loop (1, or 2 for the batched kernels' long narrow tiles);
 // D1: 1D problems only (no y-neighbour loads or registers)
-template <int PREC, int BAND, int EPT, int PF = 1, bool D1 = false>
+template <int PREC, int BAND, int EPT, bool D1 = false>
 PD_D void time_fwd_body(const FwdArgs& a, int tile) {
   using R = typename std::conditional<PREC == 0, float, double>::type;
   using C = cplx_t<R>;
@@ -513,19 +511,10 @@ PD_D void time_fwd_body(const FwdArgs& a, int tile) {
         L.u = (!D1 && hasU) ? __ldg(p + nx) : z2;
         return L;
       };
-      // PF rows of loads in flight ahead of the row being computed (with PF = 2
-      // the row after next waits in zA, zB, wA, wB)
+      // one row of loads in flight ahead of the row being computed
       RowLd<float2> cA = ldrow(min(nA, Nm1)), cB = ldrow(min(nB, Nm1));
       float2 bA = __ldg(Bcol + (size_t)min(nA, Nm1) * Sz);
       float2 bB = __ldg(Bcol + (size_t)min(nB, Nm1) * Sz);
-      RowLd<float2> zA, zB;
-      float2 wA = make_float2(0.f, 0.f), wB = wA;
-      if constexpr (PF == 2) {
-        zA = ldrow(min(nA + 1, Nm1));
-        zB = ldrow(min(nB + 1, Nm1));
-        wA = __ldg(Bcol + (size_t)min(nA + 1, Nm1) * Sz);
-        wB = __ldg(Bcol + (size_t)min(nB + 1, Nm1) * Sz);
-      }
       // the c2 weights negated once; when every c2[m] is 0 or a power of two
       // (backward Euler, Crank-Nicolson, leap-frog) the weighted terms are exact
       // scalings
@@ -542,7 +531,7 @@ PD_D void time_fwd_body(const FwdArgs& a, int tile) {
 #pragma unroll 1
       for (int i = 0; i < rpc2; ++i) {
         const int na = nA + i, nb = nB + i;
-        const int pa = min(na + PF, Nm1), pb = min(nb + PF, Nm1);
+        const int pa = min(na + 1, Nm1), pb = min(nb + 1, Nm1);
         const RowLd<float2> xA = ldrow(pa), xB = ldrow(pb);
         const float2 yA = __ldg(Bcol + (size_t)pa * Sz), yB = __ldg(Bcol + (size_t)pb * Sz);
         stencil_df2<D1>(a, g, cA, cB, TX, kk, U0, K0);  // uniform across the warp
@@ -581,15 +570,8 @@ PD_D void time_fwd_body(const FwdArgs& a, int tile) {
           srow[nb * TX] = vb ? fmaf(rh.y, gg, rl.y * gg) : 0.f;
         }
         U2 = U1; K2v = K1; U1 = U0; K1 = K0;
-        if constexpr (PF == 2) {
-          cA = zA; cB = zB;
-          bA = wA; bB = wB;
-          zA = xA; zB = xB;
-          wA = yA; wB = yB;
-        } else {
-          cA = xA; cB = xB;
-          bA = yA; bB = yB;
-        }
+        cA = xA; cB = xB;
+        bA = yA; bB = yB;
       }
       const float part1 = part.x + part.y;
       nrm = (double)part1 * a.rscale2;
@@ -686,7 +668,7 @@ __global__ void __launch_bounds__(TT, PREC == 0 ? 3 : 2) k_time_fwd_batch(const 
                                                           const int2* __restrict__ work) {
   const int2 w = work[blockIdx.x];
   // batches hold 1D problems only
-  time_fwd_body<PREC, BAND, EPT, EPT == 16 ? 2 : 1, true>(descs[w.x], w.y);
+  time_fwd_body<PREC, BAND, EPT, true>(descs[w.x], w.y);
 }
 
 // ---------------------------------------------------------------------------
