@@ -29,9 +29,15 @@ from .operators import apply_A, first_columns, stencil
 
 
 def fourier_matrix(nt: int) -> np.ndarray:
-    """Unitary F of Lemma 1 with omega = exp(2 pi i / Nt)."""
-    idx = np.arange(nt)
-    return np.exp(2j * np.pi * np.outer(idx, idx) / nt) / np.sqrt(nt)
+    """Unitary F of Lemma 1 with omega = exp(2 pi i / Nt).
+
+    omega^Nt = 1, so the exponent (l1-1)(l2-1) is reduced modulo Nt in exact
+    integer arithmetic before the phase is formed: the phase then stays below
+    2 pi and carries one rounding of a number below 2 pi, where the unreduced
+    product (up to (Nt-1)^2) would put an absolute error of about
+    eps 2 pi Nt into the entries."""
+    idx = np.arange(nt, dtype=np.int64)
+    return np.exp(2j * np.pi * (np.outer(idx, idx) % nt) / nt) / np.sqrt(nt)
 
 
 def gamma(problem: Problem) -> np.ndarray:
