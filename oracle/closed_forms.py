@@ -3,7 +3,8 @@
 * Lemma 1 eigenvalues in closed form.  With w_n = alpha^{1/Nt} omega^n,
   omega = exp(2 pi i/Nt), the diagonal of D_j is sum_m c_j[m] w_n^m, so
     theta-method: lambda_1 = (1 - w)/dt,      lambda_2 = theta + (1-theta) w,
-    leap-frog:    lambda_1 = (1 - w)^2/dt^2,  lambda_2 = (1 + w^2)/2.
+    leap-frog:    lambda_1 = (1 - w)^2/dt^2,  lambda_2 = (1 + w^2)/2
+  (every band entry of the first columns inside the matrix: Nt > band).
 * Eigenvalues of the centred 1D operators: periodic (circulant)
     mu_j = (2 nu/h^2)(1 - cos(2 pi j/n)) + i (a/h) sin(2 pi j/n),
   and Dirichlet (tridiagonal Toeplitz tridiag(l, d, u))
@@ -29,12 +30,30 @@ from workloads import LEAPFROG, Problem
 
 
 def lemma1_eigenvalues(problem: Problem):
+    """The closed forms above, evaluated so that no digits cancel.
+
+    w = e^{x + i y} with x = ln(alpha)/Nt, y = 2 pi n/Nt.  For the slow modes
+    w is close to 1 (|1 - w_0| is about |ln alpha|/Nt), and 1 - w formed by
+    subtraction would carry a relative error of about eps Nt/|ln alpha|.  The
+    real parts are written as sums of terms of one sign instead:
+      Re(1 - w)            = 2 sin^2(y/2) - expm1(x) cos y,
+      Re(theta + (1-theta) w) = 2 theta cos^2(y/2) + (1 - 2 theta) cos y
+                                + (1 - theta) expm1(x) cos y,
+      Re((1 + w^2)/2)      = cos^2 y + expm1(2x) cos(2y)/2,
+    and the imaginary parts are -e^x sin y, (1-theta) e^x sin y and
+    e^{2x} sin(2y)/2."""
     nt, dt, a = problem.nt, problem.dt, problem.alpha
-    w = a ** (1.0 / nt) * np.exp(2j * np.pi * np.arange(nt) / nt)
+    x = np.log(a) / nt
+    y = 2.0 * np.pi * np.arange(nt) / nt
+    one_m_w = (2.0 * np.sin(y / 2) ** 2 - np.expm1(x) * np.cos(y)) - 1j * np.exp(x) * np.sin(y)
     if problem.scheme == LEAPFROG:
-        return (1.0 - w) ** 2 / dt**2, (1.0 + w**2) / 2.0
+        l2 = (np.cos(y) ** 2 + 0.5 * np.expm1(2 * x) * np.cos(2 * y)
+              + 0.5j * np.exp(2 * x) * np.sin(2 * y))
+        return one_m_w ** 2 / dt**2, l2
     th = problem.theta_eff
-    return (1.0 - w) / dt, th + (1.0 - th) * w
+    l2 = (2 * th * np.cos(y / 2) ** 2 + (1 - 2 * th) * np.cos(y) + (1 - th) * np.expm1(x) * np.cos(y)
+          + 1j * (1 - th) * np.exp(x) * np.sin(y))
+    return one_m_w / dt, l2
 
 
 def mu_periodic(n: int, h: float, nu: float, a: float) -> np.ndarray:

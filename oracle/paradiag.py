@@ -4,7 +4,9 @@ P_alpha^{-1} r follows Lemma 1 and the three steps of eq. 1.3 literally:
   F     = N^{-1/2} [omega^{(l1-1)(l2-1)}], omega = exp(+2 pi i / Nt)  (unitary),
   Gamma = diag(alpha^{(n-1)/Nt}), n = 1..Nt,
   V     = Gamma^{-1} F^*,  V^{-1} = F Gamma,
-  D_j   = diag(sqrt(Nt) F Gamma c_j), c_j = first column of C_j^(alpha),
+  D_j   = diag(sqrt(Nt) F Gamma c_j), c_j = first column of C_j^(alpha)
+          (the shifted systems are factored with the closed forms of these
+          diagonals, evaluated without cancellation, closed_forms.py),
   step (a) S_1 = (V^{-1} (x) I) r,
   step (b) S_{2,n} = (lambda_{1,n} I + lambda_{2,n} K)^{-1} S_{1,n}, all n = 1..Nt,
   step (c) u = (V (x) I) S_2.
@@ -23,8 +25,9 @@ import numpy as np
 import scipy.sparse as sps
 import scipy.sparse.linalg as spla
 
-from workloads import Problem
+from workloads import LEAPFROG, Problem
 
+from . import closed_forms as CF
 from .operators import apply_A, first_columns, stencil
 
 
@@ -54,6 +57,18 @@ def eigenvalues(problem: Problem):
     return s * (F @ (g * c1)), s * (F @ (g * c2))
 
 
+def shift_eigenvalues(problem: Problem):
+    """The diagonals of Lemma 1 that step (b)'s systems are factored with:
+    the closed forms (closed_forms.lemma1_eigenvalues, no cancelling digits)
+    where every band entry of the first columns lies inside the matrix, else
+    the definition.  The definition's sum c_j[0] + c_j[1] w + ... loses about
+    log10(Nt/|ln alpha|) digits on the slow modes, where w is close to 1."""
+    band = 2 if problem.scheme == LEAPFROG else 1
+    if problem.nt > band:
+        return CF.lemma1_eigenvalues(problem)
+    return eigenvalues(problem)
+
+
 class Preconditioner:
     """P_alpha^{-1} with the Nt complex shifted systems factored once."""
 
@@ -62,7 +77,7 @@ class Preconditioner:
         self.K = stencil(problem.space) if K is None else K
         self.F = fourier_matrix(problem.nt)
         self.g = gamma(problem)
-        self.lam1, self.lam2 = eigenvalues(problem)
+        self.lam1, self.lam2 = shift_eigenvalues(problem)
         S = problem.space.size
         I = sps.identity(S, dtype=np.complex128)
         Kc = self.K.astype(np.complex128)
