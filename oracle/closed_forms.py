@@ -44,7 +44,10 @@ def lemma1_eigenvalues(problem: Problem):
     e^{2x} sin(2y)/2."""
     nt, dt, a = problem.nt, problem.dt, problem.alpha
     x = np.log(a) / nt
-    y = 2.0 * np.pi * np.arange(nt) / nt
+    # omega^n = omega^(n - Nt): the angle is taken in (-pi, pi], so that the
+    # slow modes near n = Nt get small, exactly scaled arguments too
+    n = np.arange(nt)
+    y = 2.0 * np.pi * np.where(2 * n <= nt, n, n - nt) / nt
     one_m_w = (2.0 * np.sin(y / 2) ** 2 - np.expm1(x) * np.cos(y)) - 1j * np.exp(x) * np.sin(y)
     if problem.scheme == LEAPFROG:
         l2 = (np.cos(y) ** 2 + 0.5 * np.expm1(2 * x) * np.cos(2 * y)
