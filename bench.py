@@ -1091,7 +1091,25 @@ def run_sweep(pd, torch, dev):
                 if t > 0:
                     gbs = bpu[name] * ns / (t / 1e3) / 1e9
                     ker[name] = {"ms": t, "GB/s": gbs, "frac": gbs / hbm}
-            rows.append({"nx": nx, "nt": nt, "unknowns": ns, "kernels": ker})
+            row = {"nx": nx, "nt": nt, "unknowns": ns, "time_cluster": plan.time_cluster,
+                   "tile_columns": plan.tuning()[0], "kernels": ker}
+            # the time kernels with each tile split the plan allows (one block,
+            # or a cluster of 2, 4 or 8 blocks)
+            if nt >= 1024:
+                chosen = plan.time_cluster
+                by = {}
+                for cr in (1, 2, 4, 8):
+                    try:
+                        plan.set_time_cluster(cr)
+                    except pd.PDError:
+                        continue
+                    plan.profile_iteration(b, u, reps=1)
+                    km = plan.profile_iteration(b, u, reps=5)
+                    by[str(cr)] = {"tile_columns": plan.tuning()[0],
+                                   "resid_gamma_fft_ms": km[0], "ifft_gamma_update_ms": km[-1]}
+                row["time_kernels_by_cluster"] = by
+                plan.set_time_cluster(chosen)
+            rows.append(row)
             plan.close()
     return {"sweep": rows, "peak_GBps": hbm, "peak_source": src}
 

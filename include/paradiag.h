@@ -81,9 +81,11 @@ typedef struct pd_plan pd_plan;
 /* Create a plan for the all-at-once system on Nt uniform steps of size dt with
  * preconditioner parameter alpha in (0, 1] (Lemma 1).  Any Nt >= 1: powers of
  * two use a radix-16 Stockham FFT (one radix-2/4/8 pass when log2 Nt is not a
- * multiple of 4; Nt <= 4096 for PD_MIXED, <= 2048 for
- * PD_FP64), other lengths Bluestein's chirp-z transform of length
- * M = 2^ceil(log2(2 Nt - 1)) within the same limits (Nt <= 2048 / 1024);
+ * multiple of 4; Nt <= 32768 for PD_MIXED, <= 8192 for PD_FP64; from
+ * Nt = 2048 (mixed) or 512 (FP64) on, each time tile's transform is split
+ * over a thread-block cluster, pd_plan_time_cluster), other lengths
+ * Bluestein's chirp-z transform of length M = 2^ceil(log2(2 Nt - 1)) with
+ * M <= 4096 (mixed) or <= 2048 (FP64), i.e. Nt <= 2048 / 1024;
  * larger Nt gives PD_ERR_UNSUPPORTED.  alpha = 1 is
  * accepted only when no shifted system is singular (checked here).
  * stream: a cudaStream_t (NULL = legacy default stream).
@@ -279,7 +281,9 @@ PD_API pd_status pd_plan_get_tuning(const pd_plan* plan, int* tile_columns, int*
 
 /* Pin the kernel shapes of a mixed plan instead of the autotuner's choice:
  * tile_columns a power of two with 2 <= tile_columns <= 32 and tile_columns
- * times the transform length (Nt, or Bluestein's M) at most 8192; tri_rows 32
+ * times the transform length (Nt, or Bluestein's M) at most 8192 (plans whose
+ * time tiles span a cluster, pd_plan_time_cluster, keep their width: only
+ * the current tile_columns is accepted); tri_rows 32
  * or 16; tri_lanes a power of two at least the default for that row count
  * (ceil(n / tri_rows) rounded up to a power of two, n the tridiagonal
  * length) and at most 256.  Invalid shapes return PD_ERR_ARG and change
@@ -310,6 +314,27 @@ PD_API pd_status pd_plan_set_tuning(pd_plan* plan, int tile_columns, int tri_lan
 #define PD_XFORM_DENSE 2
 PD_API pd_status pd_plan_xform_engine(const pd_plan* plan, int* engine);
 PD_API pd_status pd_plan_set_xform_engine(pd_plan* plan, int engine);
+
+/* Blocks per time tile of the time kernels (steps (a) and (c) of eq. 1.3:
+ * the FFT along t of TX spatial columns).  One block holds a tile of at most
+ * 8192 (mixed) or 2048 (FP64) reals, N TX.  With *blocks = CR in {2, 4, 8}
+ * a tile of CR times that is split over a thread-block cluster: block c forms
+ * the time rows [c N/CR, (c+1) N/CR), one radix-CR step of the FFT exchanges
+ * values through distributed shared memory, and each block finishes a
+ * length-N/CR FFT and writes the spectrum rows k = CR k' + c (decimation in
+ * frequency; the inverse runs the steps in reverse).  Power-of-two Nt only,
+ * with 2 <= TX = CR budget / N <= 32.  Plans where one block's tile would be
+ * narrower than 8 columns take the smallest CR giving 8 (the largest, 8,
+ * beyond); mixed plans with at least 2^18 unknowns time the candidates at
+ * creation with the tile widths of pd_plan_tuning.  pd_plan_set_time_cluster
+ * pins CR (1, 2, 4 or 8; PD_ERR_UNSUPPORTED where the plan's Nt allows no
+ * such tile, PD_ERR_ARG for other values) and sets TX to the budget's width;
+ * it waits for the plan's stream, and any CUDA graph the plan holds is
+ * rebuilt at the next solve.  Every CR computes the same transform up to
+ * rounding.  No paper counterpart (the paper's FFT runs on one processor
+ * per time step or sequentially). */
+PD_API pd_status pd_plan_time_cluster(const pd_plan* plan, int* blocks);
+PD_API pd_status pd_plan_set_time_cluster(pd_plan* plan, int blocks);
 
 /* ---- batched solves: many independent problems of uneven size ----------
  * One problem of a batch (1D, Dirichlet, any scheme; all members of one batch

@@ -76,6 +76,8 @@ _SIGS = {
     "pd_plan_set_tuning": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int, ctypes.c_int]),
     "pd_plan_xform_engine": (ctypes.c_int, [_P, _I]),
     "pd_plan_set_xform_engine": (ctypes.c_int, [_P, ctypes.c_int]),
+    "pd_plan_time_cluster": (ctypes.c_int, [_P, _I]),
+    "pd_plan_set_time_cluster": (ctypes.c_int, [_P, ctypes.c_int]),
     "pd_apply_precond_noalloc": (ctypes.c_int, [ctypes.POINTER(pd_space), ctypes.c_int,
                                                 ctypes.c_double, ctypes.c_double, ctypes.c_int,
                                                 ctypes.c_double, _P, _P, _P,
@@ -259,6 +261,16 @@ def pd_plan_xform_engine(plan):
 
 def pd_plan_set_xform_engine(plan, engine):
     return load().pd_plan_set_xform_engine(plan, int(engine))
+
+
+def pd_plan_time_cluster(plan):
+    v = ctypes.c_int(0)
+    st = load().pd_plan_time_cluster(plan, ctypes.byref(v))
+    return st, v.value
+
+
+def pd_plan_set_time_cluster(plan, blocks):
+    return load().pd_plan_set_time_cluster(plan, int(blocks))
 
 
 def pd_batch_uses_graph(batch):
@@ -752,6 +764,17 @@ class Plan:
     def set_xform_engine(self, engine):
         """Pin the engine of the x-eigentransform (see pd_plan_set_xform_engine)."""
         self._check(pd_plan_set_xform_engine(self._h, engine), "pd_plan_set_xform_engine")
+
+    @property
+    def time_cluster(self):
+        """Blocks per time tile (1, or a cluster of 2, 4 or 8; see pd_plan_time_cluster)."""
+        st, v = pd_plan_time_cluster(self._h)
+        self._check(st, "pd_plan_time_cluster")
+        return v
+
+    def set_time_cluster(self, blocks):
+        """Pin the blocks per time tile (see pd_plan_set_time_cluster)."""
+        self._check(pd_plan_set_time_cluster(self._h, blocks), "pd_plan_set_time_cluster")
 
     def uses_graph(self):
         st, v = pd_plan_uses_graph(self._h)

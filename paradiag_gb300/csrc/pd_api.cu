@@ -148,7 +148,7 @@ size_t cbytes(const pd_plan* p) { return p->fp64 ? sizeof(double2) : sizeof(floa
 FwdArgs fwd_base_impl(const pd_plan* p) {
   FwdArgs a;
   memset(&a, 0, sizeof(a));
-  a.N = p->nt; a.logN = p->logN; a.nh = p->nh; a.S = p->S; a.TX = p->TX;
+  a.N = p->nt; a.logN = p->logN; a.nh = p->nh; a.S = p->S; a.TX = p->TX; a.CR = p->CR;
   a.sg = p->sg;
   a.xf = p->xf;
   a.st = p->st; a.tb = p->tb;
@@ -180,7 +180,7 @@ FwdArgs fwd_base_impl(const pd_plan* p) {
 InvArgs inv_base_impl(const pd_plan* p) {
   InvArgs a;
   memset(&a, 0, sizeof(a));
-  a.N = p->nt; a.logN = p->logN; a.nh = p->nh; a.S = p->S; a.TX = p->TX;
+  a.N = p->nt; a.logN = p->logN; a.nh = p->nh; a.S = p->S; a.TX = p->TX; a.CR = p->CR;
   a.sg = p->sg;
   a.xf = p->xf;
   a.in = p->spec;
@@ -320,13 +320,26 @@ pd_status autotune_plan(pd_plan* p) {
   CU(cudaMemsetAsync(p->Udf, 0, NS(p) * sizeof(float2), p->stream));
   CU(cudaMemsetAsync(p->Bdf, 0, NS(p) * sizeof(float2), p->stream));
   const int rows = p->xf.M ? p->xf.M : p->nt;
-  // time kernels: tile budgets of 4096 and 8192 reals
-  const int tx_a = std::max(2, std::min(32, 4096 / rows)), tx_b = std::max(2, std::min(32, 8192 / rows));
-  if (tx_a != tx_b) {
+  // time kernels: one block per tile with budgets of 4096 and 8192 reals, or
+  // the tile split over a cluster of 2, 4 or 8 blocks
+  struct TimeCand { int cr, tx; };
+  std::vector<TimeCand> tcands;
+  int tx1 = 0;
+  if (time_shape_ok(p, 1, &tx1)) {
+    tcands.push_back({1, tx1});
+    const int tx_a = std::max(2, std::min(32, 4096 / rows));
+    if (tx_a != tx1) tcands.push_back({1, tx_a});
+  }
+  for (int cr : {2, 4, 8}) {
+    int tx = 0;
+    if (time_shape_ok(p, cr, &tx)) tcands.push_back({cr, tx});
+  }
+  if (tcands.size() > 1) {
     float best = -1.f;  // no candidate timed yet
-    int best_tx = p->TX;
-    for (int tx : {tx_b, tx_a}) {
-      p->TX = tx;
+    int best_tx = p->TX, best_cr = p->CR;
+    for (const TimeCand& tcn : tcands) {
+      p->TX = tcn.tx;
+      p->CR = tcn.cr;
       float ms = 0.f;
       CHK(time_ms(p, 3, &ms, [&]() -> pd_status {
         FwdArgs fa = fwd_base_impl(p);
@@ -341,9 +354,10 @@ pd_status autotune_plan(pd_plan* p) {
         LK(launch_time_inv(ia, false, p->stream));
         return PD_OK;
       }));
-      if (best < 0.f || ms < best) { best = ms; best_tx = tx; }
+      if (best < 0.f || ms < best) { best = ms; best_tx = tcn.tx; best_cr = tcn.cr; }
     }
     p->TX = best_tx;
+    p->CR = best_cr;
   }
   // tridiagonal: the default lane class, one more PCR level (chunks of at
   // least two rows), and the 16-rows-per-lane form at its own default class
@@ -934,6 +948,28 @@ pd_status plan_xform(pd_plan* p, bool fwd) { return xform_dir(p, fwd); }
 pd_status plan_fail_cuda(pd_plan* p, cudaError_t e, const char* what) { return fail_cuda(p, e, what); }
 pd_status plan_precond(pd_plan* p, const double* r, double* z) { return precond_into(p, r, z); }
 
+int time_budget(bool fp64) { return fp64 ? 2048 : 8192; }
+
+bool time_shape_ok(const pd_plan* p, int cr, int* tx) {
+  const int budget = time_budget(p->fp64);
+  const int rows = p->xf.M ? p->xf.M : p->nt;
+  if (cr == 1) {
+    // one block of at least two columns: rows <= 4096 (mixed: 16 complex
+    // elements per thread) or 2048 (FP64: 8)
+    if (rows > (p->fp64 ? 2048 : 4096)) return false;
+    *tx = std::max(2, std::min(32, budget / rows));
+    return true;
+  }
+  // a cluster of cr blocks: power-of-two Nt with the half spectrum (no
+  // Bluestein tables, no per-row eigenvalues), N TX = cr x budget, 2 <= TX <= 32
+  if (cr != 2 && cr != 4 && cr != 8) return false;
+  if (p->xf.M != 0 || !is_pow2(p->nt) || p->nh != p->nt / 2 + 1) return false;
+  const long long t = (long long)budget * cr / p->nt;
+  if (t < 2 || t > 32) return false;
+  *tx = (int)t;
+  return true;
+}
+
 extern "C" {
 
 pd_status pd_plan_launches(const pd_plan* plan, unsigned long long* count) {
@@ -964,9 +1000,13 @@ pd_status pd_plan_set_tuning(pd_plan* plan, int tile_columns, int tri_lanes, int
   if (!plan) return PD_ERR_ARG;
   if (plan->fp64) return set_err(plan, PD_ERR_UNSUPPORTED, "FP64 plans use the default shapes");
   const int rows_fft = plan->xf.M ? plan->xf.M : plan->nt;
-  if (tile_columns < 2 || tile_columns > 32 || !is_pow2(tile_columns) ||
-      (long long)tile_columns * rows_fft > 8192)
+  if (plan->CR > 1) {
+    if (tile_columns != plan->TX)
+      return set_err(plan, PD_ERR_ARG, "tile_columns is fixed by the time cluster size");
+  } else if (tile_columns < 2 || tile_columns > 32 || !is_pow2(tile_columns) ||
+             (long long)tile_columns * rows_fft > 8192) {
     return set_err(plan, PD_ERR_ARG, "tile_columns out of range");
+  }
   if (tri_rows != 16 && tri_rows != 32) return set_err(plan, PD_ERR_ARG, "tri_rows must be 16 or 32");
   const int c0 = tridiag_class(plan->tri_n, false, tri_rows);
   if (c0 < 0 || tri_lanes < (1 << c0) || tri_lanes > 256 || !is_pow2(tri_lanes))
@@ -982,6 +1022,31 @@ pd_status pd_plan_set_tuning(pd_plan* plan, int tile_columns, int tri_lanes, int
   plan->TX = tile_columns;
   plan->tri_rows = tri_rows == 16 ? 16 : 0;
   plan->tri_cls = ilog2(tri_lanes) == c0 ? -1 : ilog2(tri_lanes);
+  return PD_OK;
+}
+
+pd_status pd_plan_time_cluster(const pd_plan* plan, int* blocks) {
+  if (!plan || !blocks) return PD_ERR_ARG;
+  *blocks = plan->CR;
+  return PD_OK;
+}
+
+pd_status pd_plan_set_time_cluster(pd_plan* plan, int blocks) {
+  if (!plan) return PD_ERR_ARG;
+  int tx = 0;
+  if (blocks != 1 && blocks != 2 && blocks != 4 && blocks != 8)
+    return set_err(plan, PD_ERR_ARG, "blocks must be 1, 2, 4 or 8");
+  if (!time_shape_ok(plan, blocks, &tx))
+    return set_err(plan, PD_ERR_UNSUPPORTED, "no time tile of this many blocks for the plan's Nt");
+  if (plan->stream) cudaStreamSynchronize(plan->stream);
+  else cudaDeviceSynchronize();
+  if (plan->graph) {
+    destroy_graph(plan->graph);
+    plan->graph = nullptr;
+  }
+  plan->graph_state = 0;
+  plan->CR = blocks;
+  plan->TX = tx;
   return PD_OK;
 }
 
@@ -1159,13 +1224,17 @@ pd_status plan_create_internal(const pd_space* sp, int nt, double dt, double alp
   if (nt < 1) return PD_ERR_ARG;
   // power-of-two Nt: Stockham FFT (tile rows = Nt); otherwise Bluestein with
   // M = 2^ceil(log2(2 Nt - 1)) rows; the tile must hold 2 columns at least
+  // (a power-of-two Nt may be longer: the transform split over a cluster of up
+  // to 8 blocks, each with two columns at least, takes Nt <= 4 x the budget)
   const int budget_rows = precision == PD_MIXED ? 4096 : 2048;
+  const int max_split = 4 * time_budget(precision != PD_MIXED);
   int Mb = 0;
   if (!is_pow2(nt) && !row_lam) {
     Mb = 1;
     while (Mb < 2 * nt - 1) Mb <<= 1;
   }
-  if ((Mb ? Mb : nt) > budget_rows) return PD_ERR_UNSUPPORTED;
+  if ((Mb ? Mb : nt) > (Mb || row_lam ? budget_rows : std::max(budget_rows, max_split)))
+    return PD_ERR_UNSUPPORTED;
   if (sp->dim == 2) {
     if (sp->bc_y != PD_DIRICHLET) return PD_ERR_UNSUPPORTED;
     if (sp->bc_x == PD_DIRICHLET && sp->ax != 0.0) return PD_ERR_UNSUPPORTED;
@@ -1194,9 +1263,24 @@ pd_status plan_create_internal(const pd_space* sp, int nt, double dt, double alp
   p->stream = (cudaStream_t)stream;
   // tile of TX columns x Nt rows: 16 complex elements per thread in the mixed
   // path (one radix-16 butterfly per thread and pass, 32 KB of shared memory
-  // for Nt >= 256), 4 in the FP64 path
-  const int budget = p->fp64 ? 2048 : 8192;
-  p->TX = std::max(2, std::min(32, budget / (Mb ? Mb : nt)));
+  // for Nt >= 256), 4 in the FP64 path.  Where one block's tile would be
+  // narrower than 8 columns, a power-of-two Nt is split over a cluster of
+  // CR <= 8 blocks with 8 columns (or the narrowest that CR = 8 allows).
+  p->xf.M = Mb;
+  {
+    int tx = 0;
+    p->CR = 1;
+    if (!time_shape_ok(p, 1, &tx) || tx < 8) {
+      for (int cr : {2, 4, 8}) {
+        int t = 0;
+        if (!time_shape_ok(p, cr, &t)) continue;
+        p->CR = cr;
+        tx = t;
+        if (t >= 8) break;
+      }
+    }
+    p->TX = tx;
+  }
 
   // spatial stencil
   Stencil& st = p->st;
@@ -1386,16 +1470,47 @@ pd_status plan_create_internal(const pd_space* sp, int nt, double dt, double alp
     return PD_OK;
   }
   const double PI = 3.14159265358979323846;
-  const double ar = std::pow(alpha, 1.0 / nt);
+  // lambda_{j,k} = sum_m c_j[m] w_k^m with w_k = e^{x + i y}, x = ln(alpha)/Nt,
+  // y = -2 pi k/Nt.  For the slow modes w_k is close to 1 (|1 - w_0| is about
+  // |ln alpha|/Nt), and summing the first columns as they stand would lose
+  // the digits that cancel (a relative error of about eps Nt/|ln alpha| in
+  // lambda_1).  The sums are therefore written with expm1 and half-angle
+  // terms whose real parts add without cancellation:
+  //   1 - w     = (2 sin^2(y/2) - expm1(x) cos y) - i e^x sin y,
+  //   theta + (1 - theta) w: real part 2 theta cos^2(y/2) + (1 - 2 theta) cos y
+  //                          + (1 - theta) expm1(x) cos y,
+  //   (1 + w^2)/2: real part cos^2 y + expm1(2x) cos(2y)/2;
+  // theta-schemes: lambda_1 = (1 - w)/dt, lambda_2 = theta + (1 - theta) w;
+  // leap-frog: lambda_1 = (1 - w)^2/dt^2, lambda_2 = (1 + w^2)/2.
+  const double lx = std::log(alpha) / nt;
+  const double ex = std::exp(lx), em1 = std::expm1(lx);
+  const double ex2 = std::exp(2.0 * lx), em2 = std::expm1(2.0 * lx);
+  const double th_s = p->theta;
   for (int k = 0; k < p->nh; ++k) {
-    const double th = -2.0 * PI * k / nt;
-    const cd w = ar * cd(std::cos(th), std::sin(th));
-    cd l1 = 0, l2 = 0, wm = 1;
-    // only the first min(band+1, Nt) entries of the first column exist
-    for (int m = 0; m <= tb.band && m < nt; ++m) {
-      l1 += tb.c1[m] * wm;
-      l2 += tb.c2[m] * wm;
-      wm *= w;
+    const double y = -2.0 * PI * k / nt;
+    const double cy = std::cos(y), sy = std::sin(y);
+    const double sh = std::sin(0.5 * y), ch = std::cos(0.5 * y);
+    const cd omw(2.0 * sh * sh - em1 * cy, -ex * sy);
+    cd l1, l2;
+    if (tb.band == 2) {
+      l1 = omw * omw / (dt * dt);
+      l2 = cd(cy * cy + 0.5 * em2 * std::cos(2.0 * y), 0.5 * ex2 * std::sin(2.0 * y));
+    } else {
+      l1 = omw / dt;
+      l2 = cd(2.0 * th_s * ch * ch + (1.0 - 2.0 * th_s) * cy + (1.0 - th_s) * em1 * cy,
+              (1.0 - th_s) * ex * sy);
+    }
+    if (nt <= tb.band) {
+      // fewer levels than the band: only the first Nt entries of the first
+      // columns exist (no cancellation to guard against at these sizes)
+      const cd w = ex * cd(cy, sy);
+      cd wm = 1;
+      l1 = l2 = 0;
+      for (int m = 0; m < nt; ++m) {
+        l1 += tb.c1[m] * wm;
+        l2 += tb.c2[m] * wm;
+        wm *= w;
+      }
     }
     lam[2 * k] = l1;
     lam[2 * k + 1] = l2;

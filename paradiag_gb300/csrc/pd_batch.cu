@@ -628,6 +628,17 @@ pd_status pd_batch_create(const pd_problem* probs, int nprob, int precision, voi
     pd_plan* p = nullptr;
     pd_status s = plan_create_internal(&q.space, q.nt, q.dt, q.alpha, q.scheme, q.theta,
                                        precision, stream, false, &p);
+    // the batched time kernels take one block per tile
+    if (s == PD_OK && p->CR != 1) {
+      int tx = 0;
+      if (time_shape_ok(p, 1, &tx)) {
+        p->CR = 1;
+        p->TX = tx;
+      } else {
+        pd_plan_destroy(p);
+        s = PD_ERR_UNSUPPORTED;
+      }
+    }
     if (s != PD_OK) {
       free_batch(b);
       return s;

@@ -87,6 +87,7 @@ struct FwdArgs {
   unsigned* amax = nullptr;
   unsigned* amax_reset = nullptr;
   const int* mode_dev = nullptr;  // if set, the mode is read from device memory
+  int CR = 1;                     // blocks per tile (a cluster; 0 or 1: one block)
 };
 
 // Arguments of the inverse time kernel (K3).
@@ -102,6 +103,7 @@ struct InvArgs {
   double* out64;                  // FP64 output (z) or FP64 iterate (updated)
   int* flag;                      // bit 0 set on a non-finite value (may be null)
   const int* mode_dev = nullptr;  // if set, the mode is read from device memory
+  int CR = 1;                     // blocks per tile (a cluster; 0 or 1: one block)
 };
 
 // FWD_RESIDUAL_NORM: the residual and its norm only (no transform, no spectrum)

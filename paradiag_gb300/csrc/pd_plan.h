@@ -5,6 +5,9 @@
 struct pd_plan {
   pd_space sp;
   int nt = 0, nh = 0, S = 0, logN = 0, TX = 0;
+  // blocks per time tile: CR > 1 splits each tile's transform over a cluster
+  // of CR blocks (power-of-two Nt), with N TX = CR x the one-block budget
+  int CR = 1;
   int scheme = 0;
   double theta = 1.0, dt = 0.0, alpha = 0.0;
   int precision = 0;
@@ -99,6 +102,11 @@ pd_status plan_precond(pd_plan* p, const double* r, double* z);
 // holds no time transform: its step (b) solves one system per time row n,
 // (lambda_1n I + lambda_2n K) z_n = s_n, with lambda_1n = row_lam[4n] +
 // i row_lam[4n+1] and lambda_2n = row_lam[4n+2] + i row_lam[4n+3].
+// Time-tile shapes: one block holds at most time_budget reals (N TX); a tile
+// split over CR blocks holds CR x that.  time_shape_ok says whether the plan
+// can take cr blocks per tile and, if so, gives the tile's columns.
+int time_budget(bool fp64);
+bool time_shape_ok(const pd_plan* p, int cr, int* tx);
 pd_status plan_create_internal(const pd_space* sp, int nt, double dt, double alpha, int scheme,
                                double theta, int precision, void* stream, bool with_state,
                                pd_plan** out, const double* row_lam = nullptr);

@@ -27,6 +27,41 @@ PD_D void cp_async_commit_wait_all() {
   asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;" ::: "memory");
 }
 
+// ---- thread-block clusters: rank, barrier, distributed shared memory
+PD_D int cluster_rank() {
+  unsigned r;
+  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+  return (int)r;
+}
+// every thread of every block of the cluster; orders the shared-memory
+// writes before it (local and remote) before the reads after it
+PD_D void cluster_sync() {
+  asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+// shared::cluster address of the same shared-memory offset in block `rank`
+PD_D uint32_t dsm_map(const void* p, int rank) {
+  uint32_t r;
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;"
+               : "=r"(r) : "r"((uint32_t)__cvta_generic_to_shared(p)), "r"(rank));
+  return r;
+}
+PD_D float2 dsm_ld(uint32_t a, float2) {
+  float2 v;
+  asm volatile("ld.shared::cluster.v2.f32 {%0, %1}, [%2];" : "=f"(v.x), "=f"(v.y) : "r"(a) : "memory");
+  return v;
+}
+PD_D double2 dsm_ld(uint32_t a, double2) {
+  double2 v;
+  asm volatile("ld.shared::cluster.v2.f64 {%0, %1}, [%2];" : "=d"(v.x), "=d"(v.y) : "r"(a) : "memory");
+  return v;
+}
+PD_D void dsm_st(uint32_t a, float2 v) {
+  asm volatile("st.shared::cluster.v2.f32 [%0], {%1, %2};" ::"r"(a), "f"(v.x), "f"(v.y) : "memory");
+}
+PD_D void dsm_st(uint32_t a, double2 v) {
+  asm volatile("st.shared::cluster.v2.f64 [%0], {%1, %2};" ::"r"(a), "d"(v.x), "d"(v.y) : "memory");
+}
+
 template <typename C, bool INV>
 PD_D C twid(const C* tw, int idx) {
   C w = tw[idx];
@@ -213,6 +248,48 @@ PD_D void bluestein_tile(C* sm, int N, const TimeXf& xf, int lgTXc, const C* twM
   __syncthreads();
 }
 
+// One radix-CR step of a length-N transform split over the CR blocks of a
+// thread-block cluster; block c holds rows [c L, c L + L) (L = N / CR) of the
+// tile [L][TXc] in its shared memory.  With n = t + L c and k = CR k' + j:
+//   forward  X_{CR k' + j} = sum_t W_L^{t k'} (W_N^{t j} sum_c x_{t + L c} W_CR^{c j}),
+//   inverse  x_{t + L c}   = sum_j W_CR^{-c j} W_N^{-t j} (sum_k' X_{CR k' + j} W_L^{-t k'}),
+// W_m = exp(-2 pi i / m).  Forward: this step forms the bracket and writes
+// its j-th value of row t into block j; every block then transforms its L
+// rows (output k' in natural order).  Inverse: every block first
+// inverse-transforms its L rows (k' -> t); this step applies the twiddle and
+// the length-CR sum and writes x_{t + L c} into block c.  Block b takes the
+// rows t in [b L/CR, (b+1) L/CR) of every block, and the thread that reads
+// element (t, column) of each block is the one that writes it, so the step
+// runs in place.  The caller brackets it with cluster barriers.  tw is the
+// length-N table W_N^m, m < N.
+template <typename C, bool INV, int CR>
+PD_D void cluster_radix(C* sm, int L, int lgTXc, const C* __restrict__ tw, int rank) {
+  const int per = (L / CR) << lgTXc;
+  const int e0 = rank * per;
+  uint32_t rb[CR];
+#pragma unroll
+  for (int c = 0; c < CR; ++c) rb[c] = dsm_map(sm, c);
+  for (int e = threadIdx.x; e < per; e += TT) {
+    const int idx = e0 + e;
+    const int t = idx >> lgTXc;
+    const uint32_t off = (uint32_t)idx * (uint32_t)sizeof(C);
+    C v[CR];
+#pragma unroll
+    for (int c = 0; c < CR; ++c) v[c] = dsm_ld(rb[c] + off, C{});
+    if (!INV) {
+      dft_r<C, false, CR>(v);
+#pragma unroll
+      for (int j = 1; j < CR; ++j) v[j] = cmul(v[j], tw[t * j]);
+    } else {
+#pragma unroll
+      for (int j = 1; j < CR; ++j) v[j] = cmul(v[j], twid<C, true>(tw, t * j));
+      dft_r<C, true, CR>(v);
+    }
+#pragma unroll
+    for (int c = 0; c < CR; ++c) dsm_st(rb[c] + off, v[c]);
+  }
+}
+
 // ---------------------------------------------------------------------------
 // Spatial stencil of one time row at this thread's column, x-neighbours from
 // the lanes of the same TX-wide segment (warp shuffles), y-neighbours and
@@ -389,8 +466,11 @@ PD_D T block_sum(T v, T* red) {
 // K1: residual (optional) + Gamma scaling + forward real FFT along t.
 // PREC 0: mixed (double-float residual, FP32 transform); PREC 1: FP64.
 // ---------------------------------------------------------------------------
-// D1: 1D problems only (no y-neighbour loads or registers)
-template <int PREC, int BAND, int EPT, bool D1 = false>
+// D1: 1D problems only (no y-neighbour loads or registers).
+// CR > 1: the tile's transform is split over a cluster of CR blocks (power-of-
+// two N, see cluster_radix); this block forms the residual of the time rows
+// [n_lo, n_lo + N/CR) and writes the spectrum rows k = CR k' + rank.
+template <int PREC, int BAND, int EPT, bool D1 = false, int CR = 1>
 PD_D void time_fwd_body(const FwdArgs& a, int tile) {
   using R = typename std::conditional<PREC == 0, float, double>::type;
   using C = cplx_t<R>;
@@ -403,14 +483,18 @@ PD_D void time_fwd_body(const FwdArgs& a, int tile) {
   const int lgTX = ilog2(TX);
   const int x0 = tile * TX;
   const int x = threadIdx.x & (TX - 1);
+  // time rows of this block: [n_lo, n_hi), NL of them
+  const int rank = CR > 1 ? cluster_rank() : 0;
+  const int NL = N / CR, n_lo = rank * NL, n_hi = n_lo + NL;
   // the transform's twiddle table, staged in shared memory after the tile
-  const int rows_fft = a.xf.M ? a.xf.M : N;
+  // (split transform: the length-NL table W_N^{CR i})
+  const int rows_fft = CR > 1 ? NL : (a.xf.M ? a.xf.M : N);
   C* stw = sm + (size_t)rows_fft * (TX / 2);
-  for (int i = threadIdx.x; i < rows_fft; i += TT) stw[i] = reinterpret_cast<const C*>(a.tw)[i];
+  for (int i = threadIdx.x; i < rows_fft; i += TT) stw[i] = reinterpret_cast<const C*>(a.tw)[i * CR];
   const int chunk = threadIdx.x >> lgTX;
   const int nchunks = TT / TX;
-  const int rpc = (N + nchunks - 1) / nchunks;
-  const int n_beg = chunk * rpc;
+  const int rpc = (NL + nchunks - 1) / nchunks;
+  const int n_beg = n_lo + chunk * rpc;
   const int s = x0 + x;
   const R* gam = reinterpret_cast<const R*>(a.gam);
   double nrm = 0.0;
@@ -422,24 +506,24 @@ PD_D void time_fwd_body(const FwdArgs& a, int tile) {
     // eight loads in flight per thread
     constexpr int U = 8;
     const int n0 = threadIdx.x >> lgTX, nstep = TT >> lgTX;
-    for (int nb = n0; nb < N; nb += U * nstep) {
+    for (int nb = n0; nb < NL; nb += U * nstep) {
       double rv[U];
 #pragma unroll
       for (int u = 0; u < U; ++u) {
         const int n = nb + u * nstep;
-        rv[u] = (n < N && s < S) ? a.r64[(size_t)n * S + s] : 0.0;
+        rv[u] = (n < NL && s < S) ? a.r64[(size_t)(n_lo + n) * S + s] : 0.0;
       }
 #pragma unroll
       for (int u = 0; u < U; ++u) {
         const int n = nb + u * nstep;
-        if (n >= N) break;
+        if (n >= NL) break;
         R v;
         if constexpr (PREC == 0) {
           const df r = df_from_double(rv[u]);
-          const float gg = gam[n];
+          const float gg = gam[n_lo + n];
           v = fmaf(r.hi, gg, r.lo * gg);
         } else {
-          v = gam[n] * rv[u];
+          v = gam[n_lo + n] * rv[u];
         }
         smr[n * TX + x] = v;
       }
@@ -450,8 +534,8 @@ PD_D void time_fwd_body(const FwdArgs& a, int tile) {
       // Two row chunks per thread, computed together in the two lanes of
       // float2 values: lane A rows nA + i, lane B rows nB + i (i < rpc2).
       // Rows before the first level are zero, so the carried terms need no checks.
-      const int rpc2 = (N + 2 * nchunks - 1) / (2 * nchunks);
-      const int nA = chunk * rpc2, nB = nA + nchunks * rpc2;
+      const int rpc2 = (NL + 2 * nchunks - 1) / (2 * nchunks);
+      const int nA = n_lo + chunk * rpc2, nB = nA + nchunks * rpc2;
       if (mode == FWD_ZERO_GUESS) {
         // r' = s b: the residual loop below with U = 0 (every term it adds to
         // the accumulator is an exact zero), row for row, so the spectrum and
@@ -468,11 +552,11 @@ PD_D void time_fwd_body(const FwdArgs& a, int tile) {
           const DF2 Bv = df2_pack(bA, bB);
           const float2 rh = f2add(Bv.hi, Bv.lo);
           const float2 rl = f2sub(Bv.lo, f2sub(rh, Bv.hi));
-          const bool va = na < N && g.valid, vb = nb < N && g.valid;
+          const bool va = na < n_hi && g.valid, vb = nb < n_hi && g.valid;
           const float2 rn = make_float2(va ? rh.x : 0.f, vb ? rh.y : 0.f);
           part = f2fma(rn, rn, part);
-          if (na < N) srow[na * TX] = va ? fmaf(rh.x, gam[na], rl.x * gam[na]) : 0.f;
-          if (nb < N) srow[nb * TX] = vb ? fmaf(rh.y, gam[nb], rl.y * gam[nb]) : 0.f;
+          if (na < n_hi) srow[(na - n_lo) * TX] = va ? fmaf(rh.x, gam[na], rl.x * gam[na]) : 0.f;
+          if (nb < n_hi) srow[(nb - n_lo) * TX] = vb ? fmaf(rh.y, gam[nb], rl.y * gam[nb]) : 0.f;
         }
         const float part1 = part.x + part.y;
         nrm = (double)part1 * a.rscale2;
@@ -557,17 +641,17 @@ PD_D void time_fwd_body(const FwdArgs& a, int tile) {
         // value = s + e, renormalised
         const float2 rh = f2add(A.s, A.e);
         const float2 rl = f2sub(A.e, f2sub(rh, A.s));
-        // rows at or past N (lanes of the last chunks) add nothing
-        const bool va = na < N && g.valid, vb = nb < N && g.valid;
+        // rows at or past n_hi (lanes of the last chunks) add nothing
+        const bool va = na < n_hi && g.valid, vb = nb < n_hi && g.valid;
         const float2 rn = make_float2(va ? rh.x : 0.f, vb ? rh.y : 0.f);
         part = f2fma(rn, rn, part);
-        if (na < N) {
+        if (na < n_hi) {
           const float gg = gam[na];
-          srow[na * TX] = va ? fmaf(rh.x, gg, rl.x * gg) : 0.f;
+          srow[(na - n_lo) * TX] = va ? fmaf(rh.x, gg, rl.x * gg) : 0.f;
         }
-        if (nb < N) {
+        if (nb < n_hi) {
           const float gg = gam[nb];
-          srow[nb * TX] = vb ? fmaf(rh.y, gg, rl.y * gg) : 0.f;
+          srow[(nb - n_lo) * TX] = vb ? fmaf(rh.y, gg, rl.y * gg) : 0.f;
         }
         U2 = U1; K2v = K1; U1 = U0; K1 = K0;
         cA = xA; cB = xB;
@@ -589,7 +673,7 @@ PD_D void time_fwd_body(const FwdArgs& a, int tile) {
         const double bnxt = (i + 1 < rpc && n + 1 < N && g.valid)
                                 ? __ldg(&a.B64[(size_t)(n + 1) * S + s]) : 0.0;
         stencil_64(a, g, cur, TX, U0, K0);
-        if (n < N) {
+        if (n < n_hi) {
           double v = 0.0;
           if (g.valid) {
             double r = bcur;
@@ -600,7 +684,7 @@ PD_D void time_fwd_body(const FwdArgs& a, int tile) {
             nrm = fma(r, r, nrm);
             v = gam[n] * r;
           }
-          smr[n * TX + x] = v;
+          smr[(n - n_lo) * TX + x] = v;
         }
         U2 = U1; K2 = K1; U1 = U0; K1 = K0;
         cur = nxt;
@@ -617,8 +701,17 @@ PD_D void time_fwd_body(const FwdArgs& a, int tile) {
 
   const int lgTXc = lgTX - 1;
   const int TXc = TX / 2;
-  if (a.xf.M == 0) fft_tile<C, false, EPT>(sm, N, a.logN, lgTXc, stw);
-  else bluestein_tile<C, false, EPT>(sm, N, a.xf, lgTXc, stw);
+  if constexpr (CR > 1) {
+    // the radix-CR step over the cluster, then this block's length-NL part
+    cluster_sync();
+    cluster_radix<C, false, CR>(sm, NL, lgTXc, reinterpret_cast<const C*>(a.tw), rank);
+    cluster_sync();
+    fft_tile<C, false, EPT>(sm, NL, a.logN - ilog2(CR), lgTXc, stw);
+    cluster_sync();   // every block's spectrum rows, for the partner reads below
+  } else {
+    if (a.xf.M == 0) fft_tile<C, false, EPT>(sm, N, a.logN, lgTXc, stw);
+    else bluestein_tile<C, false, EPT>(sm, N, a.xf, lgTXc, stw);
+  }
 
   C* out = reinterpret_cast<C*>(a.out);
   const R half = (R)0.5;
@@ -632,14 +725,32 @@ PD_D void time_fwd_body(const FwdArgs& a, int tile) {
     const size_t ob = vb ? spec_index(a.sg, 0, sa + 1) : 0;
     const size_t kst = (size_t)a.sg.specS;
     R mx = 0;
-    for (int k = threadIdx.x >> lgTXc; k < a.nh; k += TT >> lgTXc) {
-      const C Zk = sm[(k << lgTXc) + c];
-      const C Zm = cconj(sm[((k == 0 ? 0 : N - k) << lgTXc) + c]);
-      const C A = cscale(cadd(Zk, Zm), half);
-      const C B = cscale(cmul_mi(csub(Zk, Zm)), half);
-      if (va) out[k * kst + oa] = A;
-      if (vb) out[k * kst + ob] = B;
-      mx = fmax(mx, fmax(fmax(fabs(A.x), fabs(A.y)), fmax(fabs(B.x), fabs(B.y))));
+    if constexpr (CR > 1) {
+      // row k' of this block is Z_k, k = CR k' + rank; Z_{N-k} is row
+      // (NL - k') mod NL of block 0 (rank 0) or row NL - 1 - k' of block CR - rank
+      const uint32_t pb = dsm_map(sm, rank == 0 ? 0 : CR - rank);
+      for (int kp = threadIdx.x >> lgTXc; CR * kp + rank < a.nh; kp += TT >> lgTXc) {
+        const int k = CR * kp + rank;
+        const int pr = rank == 0 ? ((NL - kp) & (NL - 1)) : NL - 1 - kp;
+        const C Zk = sm[(kp << lgTXc) + c];
+        const C Zm = cconj(dsm_ld(pb + (uint32_t)(((pr << lgTXc) + c) * (int)sizeof(C)), C{}));
+        const C A = cscale(cadd(Zk, Zm), half);
+        const C B = cscale(cmul_mi(csub(Zk, Zm)), half);
+        if (va) out[k * kst + oa] = A;
+        if (vb) out[k * kst + ob] = B;
+        mx = fmax(mx, fmax(fmax(fabs(A.x), fabs(A.y)), fmax(fabs(B.x), fabs(B.y))));
+      }
+      cluster_sync();   // no block leaves while its rows may still be read
+    } else {
+      for (int k = threadIdx.x >> lgTXc; k < a.nh; k += TT >> lgTXc) {
+        const C Zk = sm[(k << lgTXc) + c];
+        const C Zm = cconj(sm[((k == 0 ? 0 : N - k) << lgTXc) + c]);
+        const C A = cscale(cadd(Zk, Zm), half);
+        const C B = cscale(cmul_mi(csub(Zk, Zm)), half);
+        if (va) out[k * kst + oa] = A;
+        if (vb) out[k * kst + ob] = B;
+        mx = fmax(mx, fmax(fmax(fabs(A.x), fabs(A.y)), fmax(fabs(B.x), fabs(B.y))));
+      }
     }
     if constexpr (PREC == 0) {
       // largest |value| for the scaling of the tensor-core x-transform
@@ -658,6 +769,13 @@ template <int PREC, int BAND, int EPT>
 __global__ void __launch_bounds__(TT, PREC == 0 ? 3 : 2) k_time_fwd(FwdArgs a) {
   time_fwd_body<PREC, BAND, EPT>(a, blockIdx.x);
 }
+// a tile per cluster of CR blocks (the transform split as in cluster_radix)
+// (D1: 1D problems, no y-neighbour registers)
+template <int PREC, int BAND, int EPT, int CR, bool D1>
+__global__ void __cluster_dims__(CR, 1, 1) __launch_bounds__(TT, PREC == 0 ? 3 : 2)
+    k_time_fwd_cl(FwdArgs a) {
+  time_fwd_body<PREC, BAND, EPT, D1, CR>(a, blockIdx.x / CR);
+}
 // batch: one block per entry of the work table (problem, tile).  A persistent
 // form (blocks taking entries from a device counter) was measured slower for
 // these kernels (forward 0.70 against 0.57 ms, inverse 0.51 against 0.35 ms
@@ -674,7 +792,10 @@ __global__ void __launch_bounds__(TT, PREC == 0 ? 3 : 2) k_time_fwd_batch(const 
 // ---------------------------------------------------------------------------
 // K3: inverse real FFT along t + Gamma^{-1}/Nt + write or update.
 // ---------------------------------------------------------------------------
-template <int PREC, int EPT>
+// CR > 1: the transform is split over a cluster of CR blocks (power-of-two N,
+// see cluster_radix); this block reads the spectrum rows k = CR k' + rank (or
+// their mirrors N - k) and writes the time rows [n_lo, n_lo + N/CR).
+template <int PREC, int EPT, int CR = 1>
 PD_D void time_inv_body(const InvArgs& a, int tile) {
   using R = typename std::conditional<PREC == 0, float, double>::type;
   using C = cplx_t<R>;
@@ -685,11 +806,49 @@ PD_D void time_inv_body(const InvArgs& a, int tile) {
   const int TX = a.TX, N = a.N, S = a.S;
   const int lgTX = ilog2(TX), lgTXc = lgTX - 1, TXc = TX / 2;
   const int x0 = tile * TX;
+  const int rank = CR > 1 ? cluster_rank() : 0;
+  const int NL = N / CR, n_lo = rank * NL;
   const C* in = reinterpret_cast<const C*>(a.in);
-  const int rows_fft = a.xf.M ? a.xf.M : N;
+  const int rows_fft = CR > 1 ? NL : (a.xf.M ? a.xf.M : N);
   C* stw = sm + (size_t)rows_fft * TXc;
-  for (int i = threadIdx.x; i < rows_fft; i += TT) stw[i] = reinterpret_cast<const C*>(a.tw)[i];
-  {
+  for (int i = threadIdx.x; i < rows_fft; i += TT) stw[i] = reinterpret_cast<const C*>(a.tw)[i * CR];
+  if constexpr (CR > 1) {
+    // Z_k = A_k + i B_k for k = CR k' + rank; past N/2 from the mirror row
+    // N - k: Z_k = conj(A_{N-k}) + i conj(B_{N-k})
+    const int c = threadIdx.x & (TXc - 1);
+    const int sa = x0 + 2 * c;
+    const bool va = sa < S, vb = sa + 1 < S;
+    const size_t oa = va ? spec_index(a.sg, 0, sa) : 0;
+    const size_t ob = vb ? spec_index(a.sg, 0, sa + 1) : 0;
+    const size_t kst = (size_t)a.sg.specS;
+    const int k0 = threadIdx.x >> lgTXc, kstep = TT >> lgTXc;
+    constexpr int U = 8;  // loads in flight per thread
+    for (int kb = k0; kb < NL; kb += U * kstep) {
+      C A[U], B[U];
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const int kp = kb + u * kstep;
+        const int k = CR * kp + rank;
+        const int kr = k < a.nh ? k : N - k;
+        A[u] = czero<C>();
+        B[u] = czero<C>();
+        if (kp < NL) {
+          if (va) A[u] = in[kr * kst + oa];
+          if (vb) B[u] = in[kr * kst + ob];
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const int kp = kb + u * kstep;
+        if (kp >= NL) break;
+        const int k = CR * kp + rank;
+        C Au = A[u], Bu = B[u];
+        if (k == 0 || 2 * k == N) { Au.y = 0; Bu.y = 0; }
+        sm[(kp << lgTXc) + c] = k < a.nh ? mk(Au.x - Bu.y, Au.y + Bu.x)   // A + i B
+                                         : mk(Au.x + Bu.y, Bu.x - Au.y);  // conj(A) + i conj(B)
+      }
+    }
+  } else {
     const int c = threadIdx.x & (TXc - 1);
     const int sa = x0 + 2 * c;
     const bool va = sa < S, vb = sa + 1 < S;
@@ -723,8 +882,15 @@ PD_D void time_inv_body(const InvArgs& a, int tile) {
     }
   }
   __syncthreads();
-  if (a.xf.M == 0) fft_tile<C, true, EPT>(sm, N, a.logN, lgTXc, stw);
-  else bluestein_tile<C, true, EPT>(sm, N, a.xf, lgTXc, stw);
+  if constexpr (CR > 1) {
+    fft_tile<C, true, EPT>(sm, NL, a.logN - ilog2(CR), lgTXc, stw);
+    cluster_sync();
+    cluster_radix<C, true, CR>(sm, NL, lgTXc, reinterpret_cast<const C*>(a.tw), rank);
+    cluster_sync();
+  } else {
+    if (a.xf.M == 0) fft_tile<C, true, EPT>(sm, N, a.logN, lgTXc, stw);
+    else bluestein_tile<C, true, EPT>(sm, N, a.xf, lgTXc, stw);
+  }
 
   const R* ig = reinterpret_cast<const R*>(a.igam);
   // the mode may come from device memory (the solver's graph decides it)
@@ -737,23 +903,23 @@ PD_D void time_inv_body(const InvArgs& a, int tile) {
     const int n0 = threadIdx.x >> lgTX, nstep = TT >> lgTX;
     constexpr int U = 8;
     if (s < S) {
-      for (int nb = n0; nb < N; nb += U * nstep) {
+      for (int nb = n0; nb < NL; nb += U * nstep) {
         if constexpr (PREC == 0) {
           float2 uv[U];
           if (mode == INV_UPDATE_DF) {
 #pragma unroll
             for (int u = 0; u < U; ++u) {
               const int n = nb + u * nstep;
-              uv[u] = n < N ? a.Udf[(size_t)n * S + s] : make_float2(0.f, 0.f);
+              uv[u] = n < NL ? a.Udf[(size_t)(n_lo + n) * S + s] : make_float2(0.f, 0.f);
             }
           }
 #pragma unroll
           for (int u = 0; u < U; ++u) {
-            const int n = nb + u * nstep;
-            if (n >= N) break;
-            const float dz = smr[n * TX + x] * ig[n];
+            const int n = nb + u * nstep;   // row n_lo + n
+            if (n >= NL) break;
+            const float dz = smr[n * TX + x] * ig[n_lo + n];
             if (!isfinite(dz)) bad = true;
-            const size_t idx = (size_t)n * S + s;
+            const size_t idx = (size_t)(n_lo + n) * S + s;
             if (mode == INV_UPDATE_DF) {
               df t = two_sum(uv[u].x, dz);
               t = fast_two_sum(t.hi, t.lo + uv[u].y);
@@ -770,16 +936,16 @@ PD_D void time_inv_body(const InvArgs& a, int tile) {
 #pragma unroll
             for (int u = 0; u < U; ++u) {
               const int n = nb + u * nstep;
-              uv[u] = n < N ? a.out64[(size_t)n * S + s] : 0.0;
+              uv[u] = n < NL ? a.out64[(size_t)(n_lo + n) * S + s] : 0.0;
             }
           }
 #pragma unroll
           for (int u = 0; u < U; ++u) {
-            const int n = nb + u * nstep;
-            if (n >= N) break;
-            const double dz = smr[n * TX + x] * ig[n];
+            const int n = nb + u * nstep;   // row n_lo + n
+            if (n >= NL) break;
+            const double dz = smr[n * TX + x] * ig[n_lo + n];
             if (!isfinite(dz)) bad = true;
-            const size_t idx = (size_t)n * S + s;
+            const size_t idx = (size_t)(n_lo + n) * S + s;
             a.out64[idx] = (mode == INV_UPDATE64) ? uv[u] + dz : dz;
           }
         }
@@ -792,6 +958,11 @@ PD_D void time_inv_body(const InvArgs& a, int tile) {
 template <int PREC, int EPT>
 __global__ void __launch_bounds__(TT, PREC == 0 ? 4 : 2) k_time_inv(InvArgs a) {
   time_inv_body<PREC, EPT>(a, blockIdx.x);
+}
+template <int PREC, int EPT, int CR>
+__global__ void __cluster_dims__(CR, 1, 1) __launch_bounds__(TT, PREC == 0 ? 4 : 2)
+    k_time_inv_cl(InvArgs a) {
+  time_inv_body<PREC, EPT, CR>(a, blockIdx.x / CR);
 }
 template <int PREC, int EPT>
 __global__ void __launch_bounds__(TT, PREC == 0 ? 4 : 2) k_time_inv_batch(const InvArgs* __restrict__ descs,
@@ -944,15 +1115,71 @@ cudaError_t launch_inv_t(const InvArgs& a, cudaStream_t st) {
   }
 }
 
+// split transforms: a cluster of CR blocks per tile, each with N/CR rows and
+// the full element budget (N TX = CR 8192 mixed, CR 2048 FP64)
+template <int PREC> constexpr int cl_ept() { return PREC == 0 ? 16 : 4; }
+
+template <int PREC, int BAND, int CR>
+cudaError_t launch_fwd_cl(const FwdArgs& a, cudaStream_t st) {
+  constexpr int EPT = cl_ept<PREC>();
+  const int NL = a.N / CR;
+  if (a.xf.M != 0 || NL * CR != a.N || ept_for(NL, a.TX) != EPT) return cudaErrorInvalidValue;
+  const size_t smem = (size_t)NL * (a.TX / 2 + 1) * (PREC == 0 ? sizeof(float2) : sizeof(double2));
+  // the 1D form only where it changes the code (the mixed residual)
+  auto kern = (PREC == 0 && a.st.dim == 1) ? k_time_fwd_cl<PREC, BAND, EPT, CR, true>
+                                           : k_time_fwd_cl<PREC, BAND, EPT, CR, false>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  kern<<<ceil_div(a.S, a.TX) * CR, TT, smem, st>>>(a);
+  return cudaGetLastError();
+}
+
+template <int PREC, int CR>
+cudaError_t launch_inv_cl(const InvArgs& a, cudaStream_t st) {
+  constexpr int EPT = cl_ept<PREC>();
+  const int NL = a.N / CR;
+  if (a.xf.M != 0 || NL * CR != a.N || ept_for(NL, a.TX) != EPT) return cudaErrorInvalidValue;
+  const size_t smem = inv_smem(a.N, NL, a.TX, PREC == 1, true);
+  auto kern = k_time_inv_cl<PREC, EPT, CR>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  kern<<<ceil_div(a.S, a.TX) * CR, TT, smem, st>>>(a);
+  return cudaGetLastError();
+}
+
+template <int PREC, int BAND>
+cudaError_t launch_fwd_cl_t(const FwdArgs& a, cudaStream_t st) {
+  switch (a.CR) {
+    case 2: return launch_fwd_cl<PREC, BAND, 2>(a, st);
+    case 4: return launch_fwd_cl<PREC, BAND, 4>(a, st);
+    case 8: return launch_fwd_cl<PREC, BAND, 8>(a, st);
+    default: return cudaErrorInvalidValue;
+  }
+}
+template <int PREC>
+cudaError_t launch_inv_cl_t(const InvArgs& a, cudaStream_t st) {
+  switch (a.CR) {
+    case 2: return launch_inv_cl<PREC, 2>(a, st);
+    case 4: return launch_inv_cl<PREC, 4>(a, st);
+    case 8: return launch_inv_cl<PREC, 8>(a, st);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
 }  // namespace
 
 cudaError_t launch_time_fwd(const FwdArgs& a, bool fp64, cudaStream_t st) {
   const bool lf = a.tb.band == 2;
+  if (a.CR > 1) {
+    if (fp64) return lf ? launch_fwd_cl_t<1, 2>(a, st) : launch_fwd_cl_t<1, 1>(a, st);
+    return lf ? launch_fwd_cl_t<0, 2>(a, st) : launch_fwd_cl_t<0, 1>(a, st);
+  }
   if (fp64) return lf ? launch_fwd_t<1, 2>(a, st) : launch_fwd_t<1, 1>(a, st);
   return lf ? launch_fwd_t<0, 2>(a, st) : launch_fwd_t<0, 1>(a, st);
 }
 
 cudaError_t launch_time_inv(const InvArgs& a, bool fp64, cudaStream_t st) {
+  if (a.CR > 1) return fp64 ? launch_inv_cl_t<1>(a, st) : launch_inv_cl_t<0>(a, st);
   return fp64 ? launch_inv_t<1>(a, st) : launch_inv_t<0>(a, st);
 }
 

@@ -69,6 +69,14 @@ CASES = {
     "2d_tc_cn_periodic_255x4x64": P(dim=2, nx=255, ny=4, nu=1e-3, ax=1.0, ay=0.5,
                                     bcx=W.PERIODIC, nt=64, scheme=W.CN, alpha=1e-3),
     "1d_tc_periodic_200x256": P(nx=200, nu=1e-2, ax=1.0, bcx=W.PERIODIC, nt=256, alpha=1e-2),
+    # time tiles split over a thread-block cluster (the plans' default shapes:
+    # mixed Nt = 2048 / 4096 take 2 / 4 blocks per tile; FP64 Nt = 1024 / 2048
+    # / 4096 take 4 / 8 / 8, Nt = 512 two)
+    "1d_cluster_cn_nt2048": P(nx=9, nu=0.05, ax=1.0, nt=2048, scheme=W.CN, alpha=1e-2),
+    "1d_cluster_be_nt4096": P(nx=13, nu=0.02, ax=1.0, nt=4096, alpha=1e-2),
+    "1d_cluster_leapfrog_nt1024": P(nx=21, nu=1.0, nt=1024, T=2.0, scheme=W.LEAPFROG, alpha=0.1),
+    "2d_cluster_cn_periodic_9x3x2048": P(dim=2, nx=9, ny=3, nu=1e-2, ax=1.0, ay=0.5,
+                                         bcx=W.PERIODIC, nt=2048, scheme=W.CN, alpha=1e-3),
 }
 
 
