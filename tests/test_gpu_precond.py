@@ -8,9 +8,9 @@ order eps * kappa / alpha with kappa = max_k kappa_k (computed here from the
 dense shifted matrices); the FFTs add a factor growing like log2 M, M the
 transform length (Nt, or Bluestein's M = 2^ceil(log2(2 Nt - 1))).  The bound
 checked is 2 eps kappa (1 + log2 M) / alpha with eps = 2^-53 (FP64 path) or
-2^-24 (mixed path: FP32 transforms and solves).  Over the 52 cases the measured
-max-norm errors sit between 1/1270 and 1/4.7 of it; every case prints its
-error and the ratio err / (eps kappa / alpha).
+2^-24 (mixed path: FP32 transforms and solves).  The measured max-norm
+errors sit between about 1/1300 and 1/5 of it; every case prints its error and
+the ratio err / (eps kappa / alpha).
 The invariant P z = r is checked relative to |P| |z| (entrywise absolute
 values), the natural scale of the rounding error of the product, against
 64 eps kappa / alpha (at least 1e-12).
