@@ -87,6 +87,8 @@ def parse():
     ap.add_argument("--sweep", action="store_true",
                     help="roofline sweep of the iteration kernels over 1D sizes "
                          "nx in {255, 1023, 4095} x Nt in {256, 1024, 4096}")
+    ap.add_argument("--sweep-size", default=None,
+                    help="--sweep: one size only, given as NXxNT (e.g. 4095x4096)")
     return ap.parse_args()
 
 
@@ -1065,52 +1067,54 @@ def wave_gmres_leg(pd, torch, dev, args):
     return out
 
 
-def run_sweep(pd, torch, dev):
+def run_sweep(pd, torch, dev, only=None):
     """Per-kernel time and algorithmic HBM throughput of one mixed iteration on
     1D advection-diffusion problems (nu = 1e-2, a = 1, BE, alpha = 1e-2) of
     growing size, so that the working set passes the 129 MB L2."""
     import workloads as W
     hbm, _, src = peaks()
     rows = []
-    for nx in (255, 1023, 4095):
-        for nt in (256, 1024, 4096):
-            w = W.ade1d(nx=nx, nt=nt, nu=1e-2, a=1.0, scheme=W.BE, alpha=1e-2)
-            pb = w.problem
-            sp = pb.space
-            plan = pd.Plan(dict(dim=1, nx=sp.nx, nu=sp.nu, ax=sp.ax), pb.nt, pb.dt, pb.alpha,
-                           pd.PD_BE, 1.0, pd.PD_MIXED, torch.cuda.current_stream())
-            b = plan.build_rhs(torch.from_numpy(w.u0).to(dev), None,
-                               torch.from_numpy(w.f).to(dev))
-            u = torch.zeros_like(b)
-            plan.profile_iteration(b, u, reps=2)
-            kms = plan.profile_iteration(b, u, reps=5)
-            bpu = bytes_per_unknown(nt, False)
-            ns = nx * nt
-            ker = {}
-            for name, t in zip(KERNELS, kms):
-                if t > 0:
-                    gbs = bpu[name] * ns / (t / 1e3) / 1e9
-                    ker[name] = {"ms": t, "GB/s": gbs, "frac": gbs / hbm}
-            row = {"nx": nx, "nt": nt, "unknowns": ns, "time_cluster": plan.time_cluster,
-                   "tile_columns": plan.tuning()[0], "kernels": ker}
-            # the time kernels with each tile split the plan allows (one block,
-            # or a cluster of 2, 4 or 8 blocks)
-            if nt >= 1024:
-                chosen = plan.time_cluster
-                by = {}
-                for cr in (1, 2, 4, 8):
-                    try:
-                        plan.set_time_cluster(cr)
-                    except pd.PDError:
-                        continue
-                    plan.profile_iteration(b, u, reps=1)
-                    km = plan.profile_iteration(b, u, reps=5)
-                    by[str(cr)] = {"tile_columns": plan.tuning()[0],
-                                   "resid_gamma_fft_ms": km[0], "ifft_gamma_update_ms": km[-1]}
-                row["time_kernels_by_cluster"] = by
-                plan.set_time_cluster(chosen)
-            rows.append(row)
-            plan.close()
+    sizes = [(nx, nt) for nx in (255, 1023, 4095) for nt in (256, 1024, 4096)]
+    if only:
+        sizes = [tuple(int(v) for v in only.lower().split("x"))]
+    for nx, nt in sizes:
+        w = W.ade1d(nx=nx, nt=nt, nu=1e-2, a=1.0, scheme=W.BE, alpha=1e-2)
+        pb = w.problem
+        sp = pb.space
+        plan = pd.Plan(dict(dim=1, nx=sp.nx, nu=sp.nu, ax=sp.ax), pb.nt, pb.dt, pb.alpha,
+                       pd.PD_BE, 1.0, pd.PD_MIXED, torch.cuda.current_stream())
+        b = plan.build_rhs(torch.from_numpy(w.u0).to(dev), None,
+                           torch.from_numpy(w.f).to(dev))
+        u = torch.zeros_like(b)
+        plan.profile_iteration(b, u, reps=2)
+        kms = plan.profile_iteration(b, u, reps=5)
+        bpu = bytes_per_unknown(nt, False)
+        ns = nx * nt
+        ker = {}
+        for name, t in zip(KERNELS, kms):
+            if t > 0:
+                gbs = bpu[name] * ns / (t / 1e3) / 1e9
+                ker[name] = {"ms": t, "GB/s": gbs, "frac": gbs / hbm}
+        row = {"nx": nx, "nt": nt, "unknowns": ns, "time_cluster": plan.time_cluster,
+               "tile_columns": plan.tuning()[0], "kernels": ker}
+        # the time kernels with each tile split the plan allows (one block,
+        # or a cluster of 2, 4 or 8 blocks)
+        if nt >= 1024:
+            chosen = plan.time_cluster
+            by = {}
+            for cr in (1, 2, 4, 8):
+                try:
+                    plan.set_time_cluster(cr)
+                except pd.PDError:
+                    continue
+                plan.profile_iteration(b, u, reps=1)
+                km = plan.profile_iteration(b, u, reps=5)
+                by[str(cr)] = {"tile_columns": plan.tuning()[0],
+                               "resid_gamma_fft_ms": km[0], "ifft_gamma_update_ms": km[-1]}
+            row["time_kernels_by_cluster"] = by
+            plan.set_time_cluster(chosen)
+        rows.append(row)
+        plan.close()
     return {"sweep": rows, "peak_GBps": hbm, "peak_source": src}
 
 
@@ -1294,7 +1298,7 @@ def main():
         plan.close()
         return
     if args.sweep:
-        out = run_sweep(pd, torch, dev)
+        out = run_sweep(pd, torch, dev, args.sweep_size)
         if rank == 0:
             print(json.dumps(out), flush=True)
         return

@@ -208,6 +208,8 @@ pd_status xform_dir(pd_plan* p, bool fwd) {
     xa.inv = fwd ? 0 : 1;
     xa.xf = p->xq_xf;
     xa.tw = p->xq_tw;
+    xa.L1 = p->xq_L1;
+    xa.L2 = p->xq_L2;
     xa.in = fwd ? p->spec : p->spec2;
     xa.out = fwd ? p->spec2 : p->spec;
     LK(launch_xform_fft(xa, p->fp64, p->stream));
@@ -902,18 +904,28 @@ void host_fft(std::vector<cd>& a) {
 double hstep(int n, double L, int bc) { return L / (bc == PD_PERIODIC ? n : n + 1); }
 
 // Tables of a length-L DFT on the GPU: for a power-of-two L the L twiddles
-// e^{-2 pi i m / L}; otherwise Bluestein's form with M = 2^ceil(log2(2L - 1)):
-// the chirp w_m = e^{-i pi m^2 / L} (m^2 reduced mod 2L for an accurate
-// angle), the transformed filter bhat = FFT_M(conj w, wrapped) / M and the M
-// twiddles.  M = 0 for a power-of-two L.
+// e^{-2 pi i m / L}; for L = L1 L2 with L1 <= L2 <= 32 (L1 the largest such
+// divisor) the same L twiddles, for one Cooley-Tukey step of two direct DFTs;
+// otherwise Bluestein's form with M = 2^ceil(log2(2L - 1)): the chirp
+// w_m = e^{-i pi m^2 / L} (m^2 reduced mod 2L for an accurate angle), the
+// transformed filter bhat = FFT_M(conj w, wrapped) / M and the M twiddles.
+// M = 0 for the first two forms.
 struct DftTables {
   int M = 0;
+  int L1 = 0, L2 = 0;
   std::vector<cd> tw, chirp, bhat;
 };
 DftTables dft_tables(int L) {
   const double PI = 3.14159265358979323846;
   DftTables t;
   if (!is_pow2(L)) {
+    for (int l1 = 1; l1 * l1 <= L; ++l1)
+      if (L % l1 == 0 && L / l1 <= 32) {
+        t.L1 = l1;
+        t.L2 = L / l1;
+      }
+  }
+  if (!is_pow2(L) && t.L1 == 0) {
     t.M = 1;
     while (t.M < 2 * L - 1) t.M <<= 1;
     t.chirp.resize(L);
@@ -1365,6 +1377,8 @@ pd_status plan_create_internal(const pd_space* sp, int nt, double dt, double alp
       DftTables t = dft_tables(L);
       if ((t.M ? t.M : L) <= 1024) {
         p->xq_L = L;
+        p->xq_L1 = t.L1;
+        p->xq_L2 = t.L2;
         p->xq_dst = sp->bc_x == PD_PERIODIC ? 0 : 1;
         s1 = upload_cplx(p, &p->xq_tw, t.tw, p->fp64);
         if (s1 == PD_OK && t.M) {

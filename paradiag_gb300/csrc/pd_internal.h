@@ -160,6 +160,9 @@ struct XfftArgs {
   const void* tw;                 // complex twiddles (double2 / float2, as the data)
   const void* in;
   void* out;
+  // L = L1 L2 (both <= 32, L not a power of two): one Cooley-Tukey step with
+  // two direct DFTs, tw = W_L^m for m < L; 0: Stockham / Bluestein
+  int L1 = 0, L2 = 0;
 };
 
 // Launchers (return a cudaError_t).

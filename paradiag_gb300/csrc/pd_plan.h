@@ -49,6 +49,7 @@ struct pd_plan {
   bool xq = false;
   int xeng = 0;
   int xq_L = 0, xq_dst = 0;
+  int xq_L1 = 0, xq_L2 = 0;   // L = L1 L2: two direct DFTs (0: Stockham / Bluestein)
   TimeXf xq_xf = {0, 0, nullptr, nullptr};
   void* xq_tw = nullptr;
   void* mu = nullptr;

@@ -1057,6 +1057,307 @@ cudaError_t launch_xfft_e(const XfftArgs& a, cudaStream_t st) {
   return cudaGetLastError();
 }
 
+// ---------------------------------------------------------------------------
+// The same transforms for lengths L = L1 L2 with both factors at most 32 and L
+// not a power of two (periodic nx = 255 = 15 x 17, for one): one Cooley-Tukey
+// step with two direct DFTs instead of Bluestein's two length-M FFTs.  With
+// n = L2 n1 + n2 and j = k1 + L1 k2,
+//   X_j = sum_{n2} W_{L2}^{n2 k2} [ W_L^{n2 k1} sum_{n1} x_{L2 n1 + n2} W_{L1}^{n1 k1} ],
+// W_m = exp(-2 pi i / m) (the conjugate root for the inverse).  A block holds
+// XB = 256 / L2 rows in shared memory, [row][L].  Step 1: item (row, n2) sums
+// its L1 inputs (stride L2) into L1 accumulators, applies W_L^{n2 k1} and
+// writes them back to the positions it read, L2 k1 + n2 (so the step runs in
+// place).  Step 2: item (row, k1) sums the L2 contiguous values of its group
+// into L2 accumulators and stores X_{k1 + L1 k2} (scaled; for the sine
+// transform the odd extension's entries 1..nx) to global memory.  B >= L1, L2
+// bounds the accumulator arrays at compile time.  Every twiddle is an entry
+// of the length-L table W_L^m, m < L, held in shared memory; the index of
+// W_{L1}^{n1 k1} = W_L^{L2 (n1 k1 mod L1)} steps by n1 L2 modulo L.
+// ---------------------------------------------------------------------------
+template <typename C, int B>
+__global__ void __launch_bounds__(TT) k_xform_dft2(XfftArgs a) {
+  using R = decltype(C::x);
+  extern __shared__ __align__(16) unsigned char smraw[];
+  const int L = a.L, L1 = a.L1, L2 = a.L2, nx = a.nx;
+  const int XB = TT / L2;
+  C* sm = reinterpret_cast<C*>(smraw);          // [XB][L]
+  C* stw = sm + (size_t)XB * L;                 // W_L^m, m < L
+  for (int i = threadIdx.x; i < L; i += TT) stw[i] = reinterpret_cast<const C*>(a.tw)[i];
+  const int r0 = blockIdx.x * XB;
+  const C* in = reinterpret_cast<const C*>(a.in);
+  C* out = reinterpret_cast<C*>(a.out);
+  // input rows (zero rows past the end; the sine transform's odd extension)
+  for (int e = threadIdx.x; e < XB * L; e += TT) {
+    const int r = e / L, m = e - r * L;
+    const int row = r0 + r;
+    C v = czero<C>();
+    if (row < a.rows) {
+      if (!a.dst) {
+        v = in[(size_t)row * a.ld + m];
+      } else if (m >= 1 && m <= nx) {
+        v = in[(size_t)row * a.ld + (m - 1)];                     // v_{x+1} = X_x
+      } else if (m >= nx + 2) {
+        const C w = in[(size_t)row * a.ld + (L - 1 - m)];         // v_{L-1-x} = -X_x
+        v = mk(-w.x, -w.y);
+      }
+    }
+    sm[e] = v;
+  }
+  __syncthreads();
+  const bool inv = a.inv != 0 && !a.dst;
+  auto tw_at = [&](int m) -> C {
+    C w = stw[m];
+    if (inv) w.y = -w.y;
+    return w;
+  };
+  // step 1: length-L1 DFTs over n1, then the twiddle W_L^{n2 k1}
+  {
+    const int item = threadIdx.x;
+    if (item < XB * L2) {
+      const int r = item / L2, n2 = item - r * L2;
+      C* row = sm + (size_t)r * L;
+      C acc[B];
+#pragma unroll
+      for (int k = 0; k < B; ++k) acc[k] = czero<C>();
+      for (int n1 = 0; n1 < L1; ++n1) {
+        const C x = row[L2 * n1 + n2];
+        const int step = n1 * L2;
+        int q = 0;
+#pragma unroll
+        for (int k = 0; k < B; ++k) {
+          if (k < L1) {
+            const C w = tw_at(q);
+            acc[k].x = fma(x.x, w.x, fma(-x.y, w.y, acc[k].x));
+            acc[k].y = fma(x.x, w.y, fma(x.y, w.x, acc[k].y));
+            q += step;
+            if (q >= L) q -= L;
+          }
+        }
+      }
+      int q = 0;
+#pragma unroll
+      for (int k = 0; k < B; ++k) {
+        if (k < L1) {
+          row[L2 * k + n2] = cmul(acc[k], tw_at(q));
+          q += n2;
+        }
+      }
+    }
+  }
+  __syncthreads();
+  // step 2: length-L2 DFTs over n2, outputs j = k1 + L1 k2
+  {
+    const R sc = (R)(a.dst ? (a.inv ? 1.0 / (nx + 1) : 0.5) : (a.inv ? 1.0 / nx : 1.0));
+    const int item = threadIdx.x;
+    if (item < XB * L1) {
+      const int r = item / L1, k1 = item - r * L1;
+      const int row = r0 + r;
+      const C* grp = sm + (size_t)r * L + (size_t)L2 * k1;
+      C acc[B];
+#pragma unroll
+      for (int k = 0; k < B; ++k) acc[k] = czero<C>();
+      for (int n2 = 0; n2 < L2; ++n2) {
+        const C y = grp[n2];
+        const int step = n2 * L1;
+        int q = 0;
+#pragma unroll
+        for (int k = 0; k < B; ++k) {
+          if (k < L2) {
+            const C w = tw_at(q);
+            acc[k].x = fma(y.x, w.x, fma(-y.y, w.y, acc[k].x));
+            acc[k].y = fma(y.x, w.y, fma(y.y, w.x, acc[k].y));
+            q += step;
+            if (q >= L) q -= L;
+          }
+        }
+      }
+      if (row < a.rows) {
+        C* orow = out + (size_t)row * a.ld;
+#pragma unroll
+        for (int k = 0; k < B; ++k) {
+          if (k < L2) {
+            const int j = k1 + L1 * k;
+            if (!a.dst) {
+              if (j < nx) orow[j] = mk(acc[k].x * sc, acc[k].y * sc);
+            } else if (j >= 1 && j <= nx) {
+              orow[j - 1] = mk(-acc[k].y * sc, acc[k].x * sc);     // (i/2) V_j, scaled
+            }
+          }
+        }
+      }
+    }
+  }
+}
+
+// The same two steps with the factors fixed at compile time (the loops fully
+// unrolled, every twiddle index W_{L1}^{(n1 k) mod L1} a constant) and RPI
+// rows per item, so that one twiddle load serves RPI complex products.  FP32:
+// the table holds (Re w, Im w, Im w, Re w) per entry and a product takes two
+// paired FMAs, (x.re, x.re) (Re w, Im w) + (-x.im, x.im) (Im w, Re w).
+template <typename C> struct TwS;
+template <> struct TwS<float2> { using T = float4; };
+template <> struct TwS<double2> { using T = double2; };
+
+PD_D void cmac_tw(float2& acc, const float2& xa, const float2& xb, const float4& w) {
+  acc = f2fma(xa, make_float2(w.x, w.y), acc);
+  acc = f2fma(xb, make_float2(w.z, w.w), acc);
+}
+PD_D void cmac_tw(double2& acc, const double2& x, const double2&, const double2& w) {
+  acc.x = fma(x.x, w.x, fma(-x.y, w.y, acc.x));
+  acc.y = fma(x.x, w.y, fma(x.y, w.x, acc.y));
+}
+PD_D void cmac_split(const float2& x, float2& xa, float2& xb) {
+  xa = make_float2(x.x, x.x);
+  xb = make_float2(-x.y, x.y);
+}
+PD_D void cmac_split(const double2& x, double2& xa, double2& xb) { xa = x; xb = x; }
+PD_D float2 tw_c(const float4& w) { return make_float2(w.x, w.y); }
+PD_D double2 tw_c(const double2& w) { return w; }
+
+// (FP32: three blocks per SM, 80 registers; FP64: two, without spills)
+template <typename C, int L1, int L2, int RPI>
+__global__ void __launch_bounds__(TT, sizeof(C) == 8 ? 3 : 2) k_xform_dft2s(XfftArgs a) {
+  using R = decltype(C::x);
+  using T = typename TwS<C>::T;
+  constexpr int L = L1 * L2;
+  constexpr int NI = TT / L2;            // row groups per block
+  constexpr int XB = NI * RPI;           // rows per block
+  extern __shared__ __align__(16) unsigned char smraw[];
+  T* stw = reinterpret_cast<T*>(smraw);                  // W_L^m (conjugated for the inverse)
+  C* sm = reinterpret_cast<C*>(stw + L);                 // [XB][L]
+  const int nx = a.nx;
+  const bool inv = a.inv != 0 && !a.dst;
+  for (int i = threadIdx.x; i < L; i += TT) {
+    C w = reinterpret_cast<const C*>(a.tw)[i];
+    if (inv) w.y = -w.y;
+    if constexpr (sizeof(T) == 16 && sizeof(C) == 8) stw[i] = make_float4(w.x, w.y, w.y, w.x);
+    else stw[i] = w;
+  }
+  const int r0 = blockIdx.x * XB;
+  const C* in = reinterpret_cast<const C*>(a.in);
+  C* out = reinterpret_cast<C*>(a.out);
+  for (int e = threadIdx.x; e < XB * L; e += TT) {
+    const int r = e / L, m = e - r * L;
+    const int row = r0 + r;
+    C v = czero<C>();
+    if (row < a.rows) {
+      if (!a.dst) {
+        v = in[(size_t)row * a.ld + m];
+      } else if (m >= 1 && m <= nx) {
+        v = in[(size_t)row * a.ld + (m - 1)];
+      } else if (m >= nx + 2) {
+        const C w = in[(size_t)row * a.ld + (L - 1 - m)];
+        v = mk(-w.x, -w.y);
+      }
+    }
+    sm[e] = v;
+  }
+  __syncthreads();
+  // step 1: item (group g, n2) over the rows g RPI + i
+  if (threadIdx.x < NI * L2) {
+    const int g = threadIdx.x / L2, n2 = threadIdx.x - g * L2;
+    C acc[RPI][L1];
+#pragma unroll
+    for (int i = 0; i < RPI; ++i)
+#pragma unroll
+      for (int k = 0; k < L1; ++k) acc[i][k] = czero<C>();
+#pragma unroll
+    for (int n1 = 0; n1 < L1; ++n1) {
+      C xa[RPI], xb[RPI];
+#pragma unroll
+      for (int i = 0; i < RPI; ++i)
+        cmac_split(sm[(size_t)(g * RPI + i) * L + L2 * n1 + n2], xa[i], xb[i]);
+#pragma unroll
+      for (int k = 0; k < L1; ++k) {
+        const T w = stw[L2 * ((n1 * k) % L1)];
+#pragma unroll
+        for (int i = 0; i < RPI; ++i) cmac_tw(acc[i][k], xa[i], xb[i], w);
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < L1; ++k) {
+      const C w = tw_c(stw[n2 * k]);
+#pragma unroll
+      for (int i = 0; i < RPI; ++i)
+        sm[(size_t)(g * RPI + i) * L + L2 * k + n2] = cmul(acc[i][k], w);
+    }
+  }
+  __syncthreads();
+  // step 2: item (group g, k1): outputs j = k1 + L1 k2
+  if (threadIdx.x < NI * L1) {
+    const int g = threadIdx.x / L1, k1 = threadIdx.x - g * L1;
+    C acc[RPI][L2];
+#pragma unroll
+    for (int i = 0; i < RPI; ++i)
+#pragma unroll
+      for (int k = 0; k < L2; ++k) acc[i][k] = czero<C>();
+#pragma unroll
+    for (int n2 = 0; n2 < L2; ++n2) {
+      C xa[RPI], xb[RPI];
+#pragma unroll
+      for (int i = 0; i < RPI; ++i)
+        cmac_split(sm[(size_t)(g * RPI + i) * L + L2 * k1 + n2], xa[i], xb[i]);
+#pragma unroll
+      for (int k = 0; k < L2; ++k) {
+        const T w = stw[L1 * ((n2 * k) % L2)];
+#pragma unroll
+        for (int i = 0; i < RPI; ++i) cmac_tw(acc[i][k], xa[i], xb[i], w);
+      }
+    }
+    const R sc = (R)(a.dst ? (a.inv ? 1.0 / (nx + 1) : 0.5) : (a.inv ? 1.0 / nx : 1.0));
+#pragma unroll
+    for (int i = 0; i < RPI; ++i) {
+      const int row = r0 + g * RPI + i;
+      if (row >= a.rows) continue;
+      C* orow = out + (size_t)row * a.ld;
+#pragma unroll
+      for (int k = 0; k < L2; ++k) {
+        const int j = k1 + L1 * k;
+        if (!a.dst) {
+          if (j < nx) orow[j] = mk(acc[i][k].x * sc, acc[i][k].y * sc);
+        } else if (j >= 1 && j <= nx) {
+          orow[j - 1] = mk(-acc[i][k].y * sc, acc[i][k].x * sc);
+        }
+      }
+    }
+  }
+}
+
+template <typename C, int L1, int L2, int RPI>
+cudaError_t launch_xdft2s(const XfftArgs& a, cudaStream_t st) {
+  constexpr int XB = (TT / L2) * RPI;
+  const size_t smem = (size_t)XB * a.L * sizeof(C) + (size_t)a.L * sizeof(typename TwS<C>::T);
+  auto kern = k_xform_dft2s<C, L1, L2, RPI>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  kern<<<ceil_div(a.rows, XB), TT, smem, st>>>(a);
+  return cudaGetLastError();
+}
+
+template <typename C, int B>
+cudaError_t launch_xdft2_b(const XfftArgs& a, cudaStream_t st) {
+  const int XB = TT / a.L2;
+  const size_t smem = ((size_t)XB * a.L + a.L) * sizeof(C);
+  auto kern = k_xform_dft2<C, B>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  kern<<<ceil_div(a.rows, XB), TT, smem, st>>>(a);
+  return cudaGetLastError();
+}
+
+template <typename C>
+cudaError_t launch_xdft2(const XfftArgs& a, cudaStream_t st) {
+  // L1 <= L2 <= 32: every item of both steps has a thread (XB L1 <= XB L2 <= 256)
+  const int b = a.L2;
+  if (a.L1 < 1 || a.L1 > a.L2 || a.L1 * a.L2 != a.L || b > 32) return cudaErrorInvalidValue;
+  // the periodic grid of 255 points: factors fixed at compile time
+  if (a.L1 == 15 && a.L2 == 17) return launch_xdft2s<C, 15, 17, sizeof(C) == 8 ? 2 : 1>(a, st);
+  if (b <= 8) return launch_xdft2_b<C, 8>(a, st);
+  if (b <= 16) return launch_xdft2_b<C, 16>(a, st);
+  if (b <= 24) return launch_xdft2_b<C, 24>(a, st);
+  return launch_xdft2_b<C, 32>(a, st);
+}
+
 // complex elements per thread needed by a tile of N x TX/2 columns
 // complex elements per thread of a tile; the tile budgets of the plans
 // (N TX <= 8192 mixed, <= 2048 FP64) keep it at 16 or less
@@ -1185,6 +1486,7 @@ cudaError_t launch_time_inv(const InvArgs& a, bool fp64, cudaStream_t st) {
 
 cudaError_t launch_xform_fft(const XfftArgs& a, bool fp64, cudaStream_t st) {
   if (a.rows == 0) return cudaSuccess;
+  if (a.L1 > 0) return fp64 ? launch_xdft2<double2>(a, st) : launch_xdft2<float2>(a, st);
   // complex elements per thread of a tile: (M or L) x XR / TT
   const int rows_fft = a.xf.M ? a.xf.M : a.L;
   const int e = (rows_fft * XR + TT - 1) / TT;
