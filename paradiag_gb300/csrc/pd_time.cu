@@ -1224,7 +1224,8 @@ __global__ void __launch_bounds__(TT, sizeof(C) == 8 ? 3 : 2) k_xform_dft2s(Xfft
   constexpr int XB = NI * RPI;           // rows per block
   extern __shared__ __align__(16) unsigned char smraw[];
   T* stw = reinterpret_cast<T*>(smraw);                  // W_L^m (conjugated for the inverse)
-  C* sm = reinterpret_cast<C*>(stw + L);                 // [XB][L]
+  C* stp = reinterpret_cast<C*>(stw + L);                // [k][n2]: W_L^{n2 k}, the step-1 twiddle
+  C* sm = stp + L;                                       // [XB][L]
   const int nx = a.nx;
   const bool inv = a.inv != 0 && !a.dst;
   for (int i = threadIdx.x; i < L; i += TT) {
@@ -1232,6 +1233,12 @@ __global__ void __launch_bounds__(TT, sizeof(C) == 8 ? 3 : 2) k_xform_dft2s(Xfft
     if (inv) w.y = -w.y;
     if constexpr (sizeof(T) == 16 && sizeof(C) == 8) stw[i] = make_float4(w.x, w.y, w.y, w.x);
     else stw[i] = w;
+    // laid out so that the threads of a step-1 store (consecutive n2) read
+    // consecutive entries
+    const int k = i / L2, n2 = i - k * L2;
+    C v = reinterpret_cast<const C*>(a.tw)[n2 * k];
+    if (inv) v.y = -v.y;
+    stp[i] = v;
   }
   const int r0 = blockIdx.x * XB;
   const C* in = reinterpret_cast<const C*>(a.in);
@@ -1276,7 +1283,7 @@ __global__ void __launch_bounds__(TT, sizeof(C) == 8 ? 3 : 2) k_xform_dft2s(Xfft
     }
 #pragma unroll
     for (int k = 0; k < L1; ++k) {
-      const C w = tw_c(stw[n2 * k]);
+      const C w = stp[k * L2 + n2];
 #pragma unroll
       for (int i = 0; i < RPI; ++i)
         sm[(size_t)(g * RPI + i) * L + L2 * k + n2] = cmul(acc[i][k], w);
@@ -1326,7 +1333,7 @@ __global__ void __launch_bounds__(TT, sizeof(C) == 8 ? 3 : 2) k_xform_dft2s(Xfft
 template <typename C, int L1, int L2, int RPI>
 cudaError_t launch_xdft2s(const XfftArgs& a, cudaStream_t st) {
   constexpr int XB = (TT / L2) * RPI;
-  const size_t smem = (size_t)XB * a.L * sizeof(C) + (size_t)a.L * sizeof(typename TwS<C>::T);
+  const size_t smem = (size_t)(XB + 1) * a.L * sizeof(C) + (size_t)a.L * sizeof(typename TwS<C>::T);
   auto kern = k_xform_dft2s<C, L1, L2, RPI>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
