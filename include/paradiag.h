@@ -299,8 +299,10 @@ PD_API pd_status pd_plan_set_tuning(pd_plan* plan, int tile_columns, int tri_lan
  *                    mixed plans with nx >= 16 and >= 128 spectrum rows;
  *   PD_XFORM_FFT     FFT along x in the plan's precision: the DFT (periodic x)
  *                    or the sine transform through the odd extension
- *                    (Dirichlet x), Bluestein's form for lengths that are not
- *                    powers of two; transform lengths up to 1024;
+ *                    (Dirichlet x); a radix-16 Stockham FFT for powers of
+ *                    two, one Cooley-Tukey step of two direct DFTs for
+ *                    lengths L1 L2 with L1 <= L2 <= 32 (nx = 255 = 15 x 17),
+ *                    Bluestein's form otherwise; transform lengths up to 1024;
  *   PD_XFORM_DENSE   dense product on the CUDA cores (the remaining cases).
  * Mixed plans with both of the first two and at least 2^18 unknowns pick the
  * faster at creation (timed on the GPU); otherwise the tensor cores where
