@@ -29,6 +29,22 @@ import numpy as np
 from workloads import LEAPFROG, Problem
 
 
+def cos_sin_2pi(n, den):
+    """(cos, sin)(2 pi n / den) for integers n, den, with the angle reduced exactly:
+    4 n = q den + r with |r| <= den/2 (integers), so the angle is q quarter turns
+    plus pi r / (2 den), |pi r / (2 den)| <= pi/4, whose cosine and sine keep their
+    full relative accuracy (also where the result is small, e.g. sin near pi)."""
+    n = np.asarray(n, dtype=np.int64)
+    q = (4 * n + den // 2) // den
+    r = 4 * n - q * den
+    t = np.pi * r / (2.0 * den)
+    c, s = np.cos(t), np.sin(t)
+    q = q % 4
+    cos = np.select([q == 0, q == 1, q == 2], [c, -s, -c], s)
+    sin = np.select([q == 0, q == 1, q == 2], [s, c, -s], -c)
+    return cos, sin
+
+
 def lemma1_eigenvalues(problem: Problem):
     """The closed forms above, evaluated so that no digits cancel.
 
@@ -41,21 +57,21 @@ def lemma1_eigenvalues(problem: Problem):
                                 + (1 - theta) expm1(x) cos y,
       Re((1 + w^2)/2)      = cos^2 y + expm1(2x) cos(2y)/2,
     and the imaginary parts are -e^x sin y, (1-theta) e^x sin y and
-    e^{2x} sin(2y)/2."""
+    e^{2x} sin(2y)/2.  The sines and cosines of y/2, y and 2y come from
+    cos_sin_2pi, the angle reduced in integers."""
     nt, dt, a = problem.nt, problem.dt, problem.alpha
     x = np.log(a) / nt
-    # omega^n = omega^(n - Nt): the angle is taken in (-pi, pi], so that the
-    # slow modes near n = Nt get small, exactly scaled arguments too
     n = np.arange(nt)
-    y = 2.0 * np.pi * np.where(2 * n <= nt, n, n - nt) / nt
-    one_m_w = (2.0 * np.sin(y / 2) ** 2 - np.expm1(x) * np.cos(y)) - 1j * np.exp(x) * np.sin(y)
+    cy, sy = cos_sin_2pi(n, nt)
+    ch, sh = cos_sin_2pi(n, 2 * nt)
+    one_m_w = (2.0 * sh ** 2 - np.expm1(x) * cy) - 1j * np.exp(x) * sy
     if problem.scheme == LEAPFROG:
-        l2 = (np.cos(y) ** 2 + 0.5 * np.expm1(2 * x) * np.cos(2 * y)
-              + 0.5j * np.exp(2 * x) * np.sin(2 * y))
+        c2, s2 = cos_sin_2pi(2 * n, nt)
+        l2 = cy ** 2 + 0.5 * np.expm1(2 * x) * c2 + 0.5j * np.exp(2 * x) * s2
         return one_m_w ** 2 / dt**2, l2
     th = problem.theta_eff
-    l2 = (2 * th * np.cos(y / 2) ** 2 + (1 - 2 * th) * np.cos(y) + (1 - th) * np.expm1(x) * np.cos(y)
-          + 1j * (1 - th) * np.exp(x) * np.sin(y))
+    l2 = (2 * th * ch ** 2 + (1 - 2 * th) * cy + (1 - th) * np.expm1(x) * cy
+          + 1j * (1 - th) * np.exp(x) * sy)
     return one_m_w / dt, l2
 
 
