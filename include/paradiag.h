@@ -358,7 +358,10 @@ typedef struct pd_batch pd_batch;
  * [Nt_i][nx_i] (see pd_batch_offsets).  The kernels of one iteration run as one
  * launch per kernel type over all problems (the tridiagonal solve: one launch
  * per class of system length), driven by per-problem descriptors and a
- * block-to-(problem, tile) work table in device memory. */
+ * block-to-(problem, tile) work table in device memory.  Every member's time
+ * tile must fit one block (pd_plan_time_cluster 1: Nt <= 4096 mixed, 2048
+ * FP64 for powers of two; Bluestein lengths half that); a member beyond it
+ * returns PD_ERR_UNSUPPORTED. */
 PD_API pd_status pd_batch_create(const pd_problem* probs, int nprob, int precision, void* stream,
                                  pd_batch** out);
 PD_API pd_status pd_batch_destroy(pd_batch* batch);
@@ -461,9 +464,9 @@ PD_API pd_status pd_shard_update(pd_plan* plan, const double* z, double* u, int 
  * plug-ins whose host application owns every device allocation, or code in a
  * region where allocation is not allowed.  Such callers cannot create a plan
  * (pd_plan_create allocates its tables and workspace).
- *   Sizes.    Nt a power of two, 1 <= Nt <= 4096, and 1 <= nx <= 4096 (the
- *             limits of the plan path's mixed-precision kernels); other sizes
- *             return PD_ERR_UNSUPPORTED.  alpha = 1 is rejected with
+ *   Sizes.    Nt a power of two, 1 <= Nt <= 4096, and 1 <= nx <= 4096 (one
+ *             block per time tile: the one-block limits of the plan path's
+ *             mixed-precision kernels); other sizes return PD_ERR_UNSUPPORTED.  alpha = 1 is rejected with
  *             PD_ERR_ARG when a shifted system is singular (as pd_plan_create).
  *   Scratch.  The half spectrum and the eigenvalue, Gamma and twiddle tables
  *             live in one file-scope __device__ array of
